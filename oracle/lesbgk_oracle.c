@@ -1,0 +1,550 @@
+/*
+ * lesbgk_oracle.c -- plain FP64 CPU oracle for the lattice ES-BGK time step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the timed CPU
+ * baseline in bench.py load this file's library.  The product (the CUDA
+ * library under paper_1209_6548_gb300/csrc) never links, calls or includes it,
+ * and this file includes nothing from the product.
+ *
+ * What it computes, each function citing the passage it follows (Meng, Zhang,
+ * Hadjiconstantinou, Radtke & Shan, "Lattice ellipsoidal statistical BGK model
+ * for thermal non-equilibrium flows", arXiv 1209.6548):
+ *
+ *   - 1D Gauss-Hermite abscissae = roots of He_n, weights by Eq. (weight)
+ *     w = n!/[n He_{n-1}(c)]^2, and the 2D tensor-product set (Sec. 2.2).
+ *   - Tensor Hermite polynomials chi^(n)_{i1..in}, n <= 4, in full index form
+ *     (the basis of Eq. approxf; Grad's definitions).
+ *   - Moments rho, u, P_ij, T, sigma_ij, q_i of Eq. (mac) with D = 2.
+ *   - tau = (Kn/Pr) mu/p, mu = T^varpi, p = rho T, Pr = 1/(1-b) (Sec. 2.1-2.2).
+ *   - lambda_ij = T delta_ij + b sigma_ij / rho (Eq. cfeq).
+ *   - a_ES^(0..4) as printed in Sec. 2.2 and f_ES,a = w_a sum_n a:chi/n!.
+ *   - Body force F = omega sum_{n=1}^{N} g a^(n-1):chi^(n)/(n-1)! (Sec. 2.2),
+ *     with a^(k) the distribution's own Hermite moments.
+ *   - Forward Euler + second-order TVD/minmod fluxes (Sec. 3.1).
+ *   - Truncated Maxwellian S(T,u), Eq. (feq0), and the diffuse wall of
+ *     Sec. 3.2 (outgoing half = rho_W S, ghosts = wall node).
+ *
+ * Readings where the paper is silent (each restated where it is used):
+ *   D = 2 (the lattice dimension) in T, Eq. (feq0) and chi traces;
+ *   for c < 0 the flux is the mirror image of the printed c > 0 formula;
+ *   Psi(Theta)*(f_{i+1}-f_i) is 0 when f_{i+1} = f_i (Psi is bounded);
+ *   walls sit on nodes j = 0 and j = ny-1; the wall node is first updated like
+ *   any node, then rho_W is formed from its updated incoming half and its
+ *   outgoing half is replaced; S carries the same order N as f_ES.
+ *
+ * Everything is double precision and written for a reader to check against
+ * the paper by eye: no blocking, no fusion, no product-basis factorisation.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_D 2          /* lattice dimension (reading: D = 2) */
+#define ORC_MAXR 64      /* largest 1D rule the root finder is asked for */
+#define ORC_MAXQ 64      /* largest 2D velocity set the step handles (8x8) */
+#define ORC_MAXN 4       /* highest Hermite order */
+
+typedef struct orc_params {
+  int32_t nroots;   /* roots of He_nroots per axis: Q = nroots^2 */
+  int32_t order;    /* Hermite truncation order N (0..4) */
+  int32_t nx, ny;   /* nodes in x (periodic) and y */
+  int32_t bc_y;     /* 0 = periodic in y, 1 = diffuse walls on j=0, j=ny-1 */
+  int32_t pad_;
+  double kn;        /* Kn of Sec. 2.2 */
+  double b;         /* ES parameter, Pr = 1/(1-b) */
+  double visc_exp;  /* varpi in mu = T^varpi */
+  double dt, dx, dy;
+  double wall_T[2];   /* [0] bottom (j=0), [1] top (j=ny-1) */
+  double wall_ux[2];
+  double g[2];        /* body force */
+} orc_params;
+
+static int orc_threads = 1;
+void orc_set_threads(int n) { orc_threads = n > 0 ? n : 1; }
+int orc_get_threads(void) { return orc_threads; }
+
+/* ------------------------------------------------------------------ */
+/* 1D probabilists' Hermite polynomial He_n(x) by the three-term       */
+/* recurrence He_{k+1} = x He_k - k He_{k-1}.                          */
+/* ------------------------------------------------------------------ */
+double orc_hermite_he(int n, double x) {
+  if (n == 0) return 1.0;
+  double hm1 = 1.0, h = x;
+  for (int k = 1; k < n; ++k) {
+    double hp1 = x * h - (double)k * hm1;
+    hm1 = h;
+    h = hp1;
+  }
+  return h;
+}
+
+/* Roots of He_n by sign-change scan + bisection; weights by Eq. (weight):
+ * w = n! / [n He_{n-1}(c)]^2.  Abscissae ascending.  Returns 0 or -1. */
+int orc_gauss_hermite_1d(int n, double *c, double *w) {
+  if (n < 1 || n > ORC_MAXR) return -1;
+  double lim = 2.0 * sqrt((double)n) + 2.0;
+  int found = 0;
+  double step = 1e-3;
+  double x0 = -lim, f0 = orc_hermite_he(n, x0);
+  while (x0 < lim && found < n) {
+    double x1 = x0 + step, f1 = orc_hermite_he(n, x1);
+    if (f1 == 0.0) {
+      c[found++] = x1;
+      x0 = x1 + step * 0.5;
+      f0 = orc_hermite_he(n, x0);
+      continue;
+    }
+    if ((f0 < 0.0) != (f1 < 0.0)) {
+      double lo = x0, hi = x1, flo = f0;
+      for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi) break;
+        double fm = orc_hermite_he(n, mid);
+        if (fm == 0.0) { lo = hi = mid; break; }
+        if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; } else { hi = mid; }
+      }
+      c[found++] = 0.5 * (lo + hi);
+    }
+    x0 = x1;
+    f0 = f1;
+  }
+  if (found != n) return -1;
+  double nfact = 1.0;
+  for (int k = 2; k <= n; ++k) nfact *= (double)k;
+  for (int a = 0; a < n; ++a) {
+    double h = (double)n * orc_hermite_he(n - 1, c[a]);
+    w[a] = nfact / (h * h);
+  }
+  return 0;
+}
+
+/* 2D tensor-product ("production") set, Sec. 2.2: alpha = ix*nroots + iy,
+ * c_alpha = (c_ix, c_iy), w_alpha = w_ix w_iy. */
+int orc_velocity_set(int nroots, double *cx, double *cy, double *w) {
+  double c1[ORC_MAXR], w1[ORC_MAXR];
+  if (orc_gauss_hermite_1d(nroots, c1, w1)) return -1;
+  for (int ix = 0; ix < nroots; ++ix)
+    for (int iy = 0; iy < nroots; ++iy) {
+      int a = ix * nroots + iy;
+      cx[a] = c1[ix];
+      cy[a] = c1[iy];
+      w[a] = w1[ix] * w1[iy];
+    }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Tensor Hermite polynomials in D = 2, full index form.               */
+/* A rank-n tensor is stored flat with index sum_k i_k 2^(n-1-k).       */
+/*   chi0 = 1                                                           */
+/*   chi1_i = c_i                                                       */
+/*   chi2_ij = c_i c_j - d_ij                                           */
+/*   chi3_ijk = c_i c_j c_k - (c_i d_jk + c_j d_ik + c_k d_ij)          */
+/*   chi4_ijkl = c_i c_j c_k c_l - (six c c d terms) + (three d d terms) */
+/* ------------------------------------------------------------------ */
+static double dl(int i, int j) { return i == j ? 1.0 : 0.0; }
+
+static int rank_size(int n) { return 1 << n; }
+
+static void idx_of(int n, int flat, int *ix) {
+  for (int k = 0; k < n; ++k) ix[k] = (flat >> (n - 1 - k)) & 1;
+}
+
+void orc_chi(int n, const double *c, double *out) {
+  int sz = rank_size(n);
+  for (int f = 0; f < sz; ++f) {
+    int I[4];
+    idx_of(n, f, I);
+    double v = 0.0;
+    if (n == 0) {
+      v = 1.0;
+    } else if (n == 1) {
+      v = c[I[0]];
+    } else if (n == 2) {
+      v = c[I[0]] * c[I[1]] - dl(I[0], I[1]);
+    } else if (n == 3) {
+      int i = I[0], j = I[1], k = I[2];
+      v = c[i] * c[j] * c[k] - (c[i] * dl(j, k) + c[j] * dl(i, k) + c[k] * dl(i, j));
+    } else if (n == 4) {
+      int i = I[0], j = I[1], k = I[2], l = I[3];
+      v = c[i] * c[j] * c[k] * c[l]
+          - (c[i] * c[j] * dl(k, l) + c[i] * c[k] * dl(j, l) + c[i] * c[l] * dl(j, k)
+             + c[j] * c[k] * dl(i, l) + c[j] * c[l] * dl(i, k) + c[k] * c[l] * dl(i, j))
+          + (dl(i, j) * dl(k, l) + dl(i, k) * dl(j, l) + dl(i, l) * dl(j, k));
+    }
+    out[f] = v;
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* a_ES^(n), Sec. 2.2, exactly as printed (D = 2 index loops).         */
+/* lam is the 2x2 ES tensor, row-major.                                */
+/* ------------------------------------------------------------------ */
+void orc_a_es(int n, double rho, const double *u, const double *lam, double *out) {
+  int sz = rank_size(n);
+#define L(p, q) (lam[(p) * 2 + (q)])
+#define LM(p, q) (L(p, q) - dl(p, q))
+  for (int f = 0; f < sz; ++f) {
+    int I[4];
+    idx_of(n, f, I);
+    double v = 0.0;
+    if (n == 0) {
+      v = rho;
+    } else if (n == 1) {
+      v = rho * u[I[0]];
+    } else if (n == 2) {
+      int i = I[0], j = I[1];
+      v = rho * (u[i] * u[j] + L(i, j) - dl(i, j));
+    } else if (n == 3) {
+      int i = I[0], j = I[1], k = I[2];
+      v = rho * (u[i] * u[j] * u[k] + L(i, j) * u[k] + L(i, k) * u[j] + L(j, k) * u[i]
+                 - dl(i, j) * u[k] - dl(i, k) * u[j] - dl(j, k) * u[i]);
+    } else if (n == 4) {
+      int i = I[0], j = I[1], k = I[2], l = I[3];
+      v = rho * (u[i] * u[j] * u[l] * u[k]
+                 + LM(i, l) * u[j] * u[k] + LM(i, j) * u[l] * u[k] + LM(i, k) * u[j] * u[l]
+                 + LM(j, l) * u[i] * u[k] + LM(j, k) * u[i] * u[l] + LM(k, l) * u[i] * u[j]
+                 + LM(i, j) * LM(k, l) + LM(i, k) * LM(j, l) + LM(i, l) * LM(k, j));
+    }
+    out[f] = v;
+  }
+#undef L
+#undef LM
+}
+
+static double factorial(int n) {
+  double r = 1.0;
+  for (int k = 2; k <= n; ++k) r *= (double)k;
+  return r;
+}
+
+/* Full contraction a:chi of two rank-n tensors. */
+static double contract(int n, const double *a, const double *chi) {
+  double s = 0.0;
+  for (int f = 0; f < rank_size(n); ++f) s += a[f] * chi[f];
+  return s;
+}
+
+/* Velocity-set tables shared by one call: c, w and chi^(n)(c_alpha). */
+typedef struct orc_lattice {
+  int Q, nroots;
+  double cx[ORC_MAXQ], cy[ORC_MAXQ], w[ORC_MAXQ];
+  double chi[ORC_MAXN + 1][ORC_MAXQ][16];
+} orc_lattice;
+
+static int lattice_init(orc_lattice *L, int nroots) {
+  if (nroots < 1 || nroots * nroots > ORC_MAXQ) return -1;
+  L->nroots = nroots;
+  L->Q = nroots * nroots;
+  if (orc_velocity_set(nroots, L->cx, L->cy, L->w)) return -1;
+  for (int a = 0; a < L->Q; ++a) {
+    double c[2] = {L->cx[a], L->cy[a]};
+    for (int n = 0; n <= ORC_MAXN; ++n) orc_chi(n, c, L->chi[n][a]);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Moments of Eq. (mac), D = 2.                                        */
+/* out: rho, ux, uy, T, sxx, sxy, syy, qx, qy                           */
+/* P_ij = sum f C_i C_j;  T = P_ii/(D rho);  sigma = P - delta P_ii/D;  */
+/* q_i = 1/2 sum f C_i C^2.                                             */
+/* ------------------------------------------------------------------ */
+static void cell_moments(const orc_lattice *L, const double *f, double *out, double P[4]) {
+  double rho = 0.0, mx = 0.0, my = 0.0;
+  for (int a = 0; a < L->Q; ++a) {
+    rho += f[a];
+    mx += f[a] * L->cx[a];
+    my += f[a] * L->cy[a];
+  }
+  double ux = mx / rho, uy = my / rho;
+  double pxx = 0, pxy = 0, pyy = 0, qx = 0, qy = 0;
+  for (int a = 0; a < L->Q; ++a) {
+    double Cx = L->cx[a] - ux, Cy = L->cy[a] - uy;
+    double C2 = Cx * Cx + Cy * Cy;
+    pxx += f[a] * Cx * Cx;
+    pxy += f[a] * Cx * Cy;
+    pyy += f[a] * Cy * Cy;
+    qx += 0.5 * f[a] * Cx * C2;
+    qy += 0.5 * f[a] * Cy * C2;
+  }
+  double T = (pxx + pyy) / (ORC_D * rho);
+  double tr = (pxx + pyy) / ORC_D;
+  out[0] = rho; out[1] = ux; out[2] = uy; out[3] = T;
+  out[4] = pxx - tr; out[5] = pxy; out[6] = pyy - tr;
+  out[7] = qx; out[8] = qy;
+  if (P) { P[0] = pxx; P[1] = pxy; P[2] = pxy; P[3] = pyy; }
+}
+
+/* ------------------------------------------------------------------ */
+/* Per-cell collision ingredients:                                     */
+/*   f_ES,a = w_a sum_{n<=N} a_ES^(n):chi^(n)(c_a)/n!                   */
+/*   g_a    = w_a sum_{n=1..N} g a^(n-1):chi^(n)(c_a)/(n-1)!            */
+/*   tau    = (Kn/Pr) mu/p                                              */
+/* ------------------------------------------------------------------ */
+static void cell_collision(const orc_lattice *L, const orc_params *p, const double *f,
+                           double *fes, double *gf, double *tau_out) {
+  double m[9], P[4];
+  cell_moments(L, f, m, P);
+  double rho = m[0], u[2] = {m[1], m[2]}, T = m[3];
+  /* lambda = T delta + b sigma / rho, sigma trace-free (Eq. cfeq, Eq. mac) */
+  double sig[4] = {m[4], m[5], m[5], m[6]};
+  double lam[4];
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) lam[i * 2 + j] = T * dl(i, j) + p->b * sig[i * 2 + j] / rho;
+  int N = p->order;
+  double aes[ORC_MAXN + 1][16];
+  for (int n = 0; n <= N; ++n) orc_a_es(n, rho, u, lam, aes[n]);
+  /* the distribution's own Hermite moments a^(k) = sum_b f_b chi^(k)(c_b) */
+  double af[ORC_MAXN + 1][16];
+  for (int n = 0; n < N; ++n) {
+    for (int k = 0; k < rank_size(n); ++k) {
+      double s = 0.0;
+      for (int b = 0; b < L->Q; ++b) s += f[b] * L->chi[n][b][k];
+      af[n][k] = s;
+    }
+  }
+  for (int a = 0; a < L->Q; ++a) {
+    double s = 0.0;
+    for (int n = 0; n <= N; ++n) s += contract(n, aes[n], L->chi[n][a]) / factorial(n);
+    fes[a] = L->w[a] * s;
+    double gs = 0.0;
+    for (int n = 1; n <= N; ++n) {
+      /* g_{i1} a^(n-1)_{i2..in} chi^(n)_{i1 i2..in} */
+      double t = 0.0;
+      int szm = rank_size(n - 1);
+      for (int i1 = 0; i1 < 2; ++i1)
+        for (int r = 0; r < szm; ++r) t += p->g[i1] * af[n - 1][r] * L->chi[n][a][(i1 << (n - 1)) | r];
+      gs += t / factorial(n - 1);
+    }
+    gf[a] = L->w[a] * gs;
+  }
+  double Pr = 1.0 / (1.0 - p->b);
+  double mu = pow(T, p->visc_exp);
+  double pr = rho * T;
+  *tau_out = (p->kn / Pr) * mu / pr;
+}
+
+/* Exported for the tests: f_ES, g_a and tau of one cell. */
+int orc_cell_terms(const orc_params *p, const double *f, double *fes, double *gf, double *tau) {
+  orc_lattice L;
+  if (lattice_init(&L, p->nroots)) return -1;
+  cell_collision(&L, p, f, fes, gf, tau);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Truncated Maxwellian S(T,u), Eq. (feq0), carried to order N <= 4.   */
+/* Lines of Eq. (feq0): orders 0,1,2 | order 3 | order 4 (three lines). */
+/* ------------------------------------------------------------------ */
+static double feq0_S(int N, double T, const double *u, double cx, double cy, double w) {
+  const double D = ORC_D;
+  double cu = cx * u[0] + cy * u[1];
+  double uu = u[0] * u[0] + u[1] * u[1];
+  double cc = cx * cx + cy * cy;
+  double th = T - 1.0;
+  double s = 1.0;
+  if (N >= 1) s += cu;
+  if (N >= 2) s += 0.5 * (cu * cu - uu + th * (cc - D));
+  if (N >= 3) s += cu / 6.0 * (cu * cu - 3.0 * uu + 3.0 * th * (cc - D - 2.0));
+  if (N >= 4) {
+    s += (cu * cu * cu * cu - 6.0 * cu * cu * uu + 3.0 * uu * uu) / 24.0;
+    s += th / 4.0 * ((cc - D - 2.0) * (cu * cu - uu) - 2.0 * cu * cu);
+    s += th * th / 8.0 * (cc * cc - 2.0 * (D + 2.0) * cc + D * (D + 2.0));
+  }
+  return w * s;
+}
+
+int orc_feq0(int nroots, int N, double T, double ux, double uy, double *out) {
+  orc_lattice L;
+  if (lattice_init(&L, nroots)) return -1;
+  double u[2] = {ux, uy};
+  for (int a = 0; a < L.Q; ++a) out[a] = feq0_S(N, T, u, L.cx[a], L.cy[a], L.w[a]);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* TVD interface flux of Sec. 3.1 for one velocity along one axis.     */
+/* fm2..fp2 = f at i-2..i+2; nu = |c| dt / delta.                       */
+/* Returns F_{i+1/2} - F_{i-1/2}.                                       */
+/* ------------------------------------------------------------------ */
+static double limited(double num, double den) {
+  /* [f_{i+1}-f_i] Psi(Theta), Theta = num/den, Psi = max(0, min(1, Theta)).
+   * Reading: when den = 0 the product is 0 (Psi is bounded). */
+  if (den == 0.0) return 0.0;
+  double th = num / den;
+  double psi = fmax(0.0, fmin(1.0, th));
+  return den * psi;
+}
+
+static double flux_difference(double c, double nu, double fm2, double fm1, double f0, double fp1,
+                              double fp2) {
+  double k = 0.5 * (1.0 - nu);
+  double Fp, Fm;
+  if (c > 0.0) {
+    /* F_{i+1/2} = f_i + k [f_{i+1}-f_i] Psi((f_i - f_{i-1})/(f_{i+1}-f_i)) */
+    Fp = f0 + k * limited(f0 - fm1, fp1 - f0);
+    /* F_{i-1/2} = F_{(i-1)+1/2} */
+    Fm = fm1 + k * limited(fm1 - fm2, f0 - fm1);
+  } else {
+    /* mirror image (reading): upwind node is i+1 */
+    Fp = fp1 + k * limited(fp1 - fp2, f0 - fp1);
+    Fm = f0 + k * limited(f0 - fp1, fm1 - f0);
+  }
+  return Fp - Fm;
+}
+
+/* Exported for the tests: one velocity, periodic 1D line. */
+int orc_advect_1d(int n, double c, double nu, const double *f, double *diff) {
+  for (int i = 0; i < n; ++i) {
+#define AT(k) f[(((i) + (k)) % n + n) % n]
+    diff[i] = flux_difference(c, nu, AT(-2), AT(-1), AT(0), AT(1), AT(2));
+#undef AT
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Grid helpers.  Layout: f[alpha][j][i] (alpha-major, then row j,      */
+/* then column i).                                                      */
+/* ------------------------------------------------------------------ */
+static size_t fidx(const orc_params *p, int a, int j, int i) {
+  return ((size_t)a * p->ny + (size_t)j) * p->nx + (size_t)i;
+}
+
+static int wrap(int i, int n) { return ((i % n) + n) % n; }
+
+/* Row index of neighbour j+dj: periodic wrap, or ghosts = wall node. */
+static int row_of(const orc_params *p, int j) {
+  if (p->bc_y == 0) return wrap(j, p->ny);
+  if (j < 0) return 0;
+  if (j >= p->ny) return p->ny - 1;
+  return j;
+}
+
+/* Diffuse wall of Sec. 3.2 at wall node (i, j) with inward normal ny_sign:
+ * rho_W = sum_{c.n<0} |c.n| f / sum_{c.n>0} |c.n| S ; f_out = rho_W S. */
+static void wall_node(const orc_lattice *L, const orc_params *p, double *f, int i, int j,
+                      int side) {
+  double n_y = side == 0 ? 1.0 : -1.0;
+  double u[2] = {p->wall_ux[side], 0.0};
+  double S[ORC_MAXQ];
+  for (int a = 0; a < L->Q; ++a) S[a] = feq0_S(p->order, p->wall_T[side], u, L->cx[a], L->cy[a], L->w[a]);
+  double num = 0.0, den = 0.0;
+  for (int a = 0; a < L->Q; ++a) {
+    double cn = L->cy[a] * n_y;
+    if (cn < 0.0) num += fabs(cn) * f[fidx(p, a, j, i)];
+    if (cn > 0.0) den += fabs(cn) * S[a];
+  }
+  double rw = num / den;
+  for (int a = 0; a < L->Q; ++a)
+    if (L->cy[a] * n_y > 0.0) f[fidx(p, a, j, i)] = rw * S[a];
+}
+
+static void apply_walls(const orc_lattice *L, const orc_params *p, double *f) {
+  if (p->bc_y != 1) return;
+  for (int i = 0; i < p->nx; ++i) {
+    wall_node(L, p, f, i, 0, 0);
+    wall_node(L, p, f, i, p->ny - 1, 1);
+  }
+}
+
+static int check_params(const orc_params *p) {
+  if (p->nroots < 2 || p->nroots * p->nroots > ORC_MAXQ) return -1;
+  if (p->order < 0 || p->order > ORC_MAXN) return -1;
+  if (p->nx < 1 || p->ny < 1) return -1;
+  if (p->bc_y == 1 && p->ny < 2) return -1;
+  return 0;
+}
+
+/* Initial state: f = rho S(T,u) from fields[4][ny][nx] = rho, ux, uy, T;
+ * then the wall rule once so the state satisfies the boundary condition. */
+int orc_init(const orc_params *p, const double *fields, double *f) {
+  orc_lattice L;
+  if (check_params(p) || lattice_init(&L, p->nroots)) return -1;
+  size_t cells = (size_t)p->nx * p->ny;
+  for (int j = 0; j < p->ny; ++j)
+    for (int i = 0; i < p->nx; ++i) {
+      size_t c = (size_t)j * p->nx + i;
+      double rho = fields ? fields[c] : 1.0;
+      double u[2] = {fields ? fields[cells + c] : 0.0, fields ? fields[2 * cells + c] : 0.0};
+      double T = fields ? fields[3 * cells + c] : 1.0;
+      for (int a = 0; a < L.Q; ++a)
+        f[fidx(p, a, j, i)] = rho * feq0_S(p->order, T, u, L.cx[a], L.cy[a], L.w[a]);
+    }
+  apply_walls(&L, p, f);
+  return 0;
+}
+
+/* One time step n -> n+1 of the scheme in Sec. 3.1 followed by the walls of
+ * Sec. 3.2.  f_in and f_out must not alias. */
+int orc_step(const orc_params *p, const double *fin, double *fout) {
+  orc_lattice L;
+  if (check_params(p) || lattice_init(&L, p->nroots)) return -1;
+  const int Q = L.Q;
+#pragma omp parallel for schedule(static) num_threads(orc_threads)
+  for (int j = 0; j < p->ny; ++j) {
+    double f[ORC_MAXQ], fes[ORC_MAXQ], gf[ORC_MAXQ], tau;
+    for (int i = 0; i < p->nx; ++i) {
+      for (int a = 0; a < Q; ++a) f[a] = fin[fidx(p, a, j, i)];
+      cell_collision(&L, p, f, fes, gf, &tau);
+      for (int a = 0; a < Q; ++a) {
+        double cx = L.cx[a], cy = L.cy[a];
+        double fx[5], fy[5];
+        for (int k = -2; k <= 2; ++k) {
+          fx[k + 2] = fin[fidx(p, a, j, wrap(i + k, p->nx))];
+          fy[k + 2] = fin[fidx(p, a, row_of(p, j + k), i)];
+        }
+        double nux = fabs(cx) * p->dt / p->dx, nuy = fabs(cy) * p->dt / p->dy;
+        double dFx = flux_difference(cx, nux, fx[0], fx[1], fx[2], fx[3], fx[4]);
+        double dFy = flux_difference(cy, nuy, fy[0], fy[1], fy[2], fy[3], fy[4]);
+        fout[fidx(p, a, j, i)] = f[a] - cx * p->dt / p->dx * dFx - cy * p->dt / p->dy * dFy
+                                 + p->dt / tau * (fes[a] - f[a]) + gf[a] * p->dt;
+      }
+    }
+  }
+  apply_walls(&L, p, fout);
+  return 0;
+}
+
+/* nsteps steps; f is updated in place (work is a scratch array of the same
+ * size). */
+int orc_run(const orc_params *p, double *f, double *work, int64_t nsteps) {
+  size_t n = (size_t)p->nroots * p->nroots * p->nx * p->ny;
+  for (int64_t s = 0; s < nsteps; ++s) {
+    if (orc_step(p, f, work)) return -1;
+    memcpy(f, work, n * sizeof(double));
+  }
+  return 0;
+}
+
+/* Moments of every node: out[9][ny][nx]; sums = {mass, x-mom, y-mom, energy}
+ * with energy = sum_cells 1/2 sum_a f_a c_a^2. */
+int orc_moments(const orc_params *p, const double *f, double *out, double *sums) {
+  orc_lattice L;
+  if (check_params(p) || lattice_init(&L, p->nroots)) return -1;
+  size_t cells = (size_t)p->nx * p->ny;
+  double s[4] = {0, 0, 0, 0};
+  for (int j = 0; j < p->ny; ++j)
+    for (int i = 0; i < p->nx; ++i) {
+      double fc[ORC_MAXQ], m[9];
+      for (int a = 0; a < L.Q; ++a) fc[a] = f[fidx(p, a, j, i)];
+      cell_moments(&L, fc, m, NULL);
+      size_t c = (size_t)j * p->nx + i;
+      if (out)
+        for (int k = 0; k < 9; ++k) out[k * cells + c] = m[k];
+      for (int a = 0; a < L.Q; ++a) {
+        s[0] += fc[a];
+        s[1] += fc[a] * L.cx[a];
+        s[2] += fc[a] * L.cy[a];
+        s[3] += 0.5 * fc[a] * (L.cx[a] * L.cx[a] + L.cy[a] * L.cy[a]);
+      }
+    }
+  if (sums)
+    for (int k = 0; k < 4; ++k) sums[k] = s[k];
+  return 0;
+}

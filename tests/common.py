@@ -1,0 +1,71 @@
+"""Test-side helpers: turn a seeded Problem into oracle parameters.
+
+The grid spacing and time step are fixed here, on the test side, from the
+problem statement, and passed explicitly to both the oracle and the CUDA
+library, so that neither side's input comes from the other.
+
+Spacing: a periodic axis of n nodes has delta = 1/n; with walls on rows 0 and
+ny-1 the channel width is 1, delta_y = 1/(ny-1) and delta_x = delta_y.
+Time step: dt = min(cfl * min(dx, dy) / c_max, tau_ref) with
+tau_ref = (Kn/Pr) T_max^(varpi-1) / rho_max (forward-Euler relaxation stays
+at dt/tau <= 1 at the reference state).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+from paper_1209_6548_gb300.inputs import PERIODIC, Problem
+
+DEFAULT_ORDER = {4: 3, 6: 4}
+
+
+def order_of(p: Problem) -> int:
+    return p.order if p.order else DEFAULT_ORDER[p.nroots]
+
+
+def spacing(p: Problem):
+    if p.bc_y == PERIODIC:
+        return 1.0 / p.nx, 1.0 / p.ny
+    d = 1.0 / (p.ny - 1)
+    return d, d
+
+
+def time_step(p: Problem, fields=None) -> float:
+    dx, dy = spacing(p)
+    c, _ = O.gauss_hermite_1d(p.nroots)
+    dt_cfl = p.cfl * min(dx, dy) / float(np.max(np.abs(c)))
+    tmax = max(p.wall_T) if p.bc_y != PERIODIC else 1.0
+    rmax = 1.0
+    if fields is not None:
+        tmax = max(tmax, float(fields[3].max()))
+        rmax = float(fields[0].max())
+    pr = 1.0 / (1.0 - p.b)
+    tau_ref = (p.kn / pr) * tmax ** (p.visc_exp - 1.0) / rmax
+    return min(dt_cfl, tau_ref)
+
+
+def oracle_params(p: Problem, dt: float, nx=None, ny=None, bc_y=None):
+    dx, dy = spacing(p)
+    return O.make_params(nroots=p.nroots, order=order_of(p), nx=nx or p.nx, ny=ny or p.ny,
+                         bc_y=p.bc_y if bc_y is None else bc_y, kn=p.kn, b=p.b,
+                         visc_exp=p.visc_exp, dt=dt, dx=dx, dy=dy, wall_T=tuple(p.wall_T),
+                         wall_ux=tuple(p.wall_ux), g=tuple(p.g))
+
+
+def field_errors(gpu: np.ndarray, ref: np.ndarray, rest=None):
+    """Per-field relative error e = max|gpu-ref| / max|ref| over the nine
+    moment fields, and the perturbation-relative e' = max|gpu-ref| /
+    max|ref - rest| where the reference's deviation from rest exceeds 1e-6."""
+    out = {}
+    for k, name in enumerate(O.MOMENT_NAMES):
+        d = float(np.max(np.abs(gpu[k].astype(np.float64) - ref[k])))
+        scale = float(np.max(np.abs(ref[k])))
+        e = d / scale if scale > 0 else d
+        ep = None
+        if rest is not None:
+            dev = float(np.max(np.abs(ref[k] - rest[k])))
+            if dev > 1e-6:
+                ep = d / dev
+        out[name] = (e, ep, d)
+    return out
