@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the lattice ES-BGK solver.
+
+Workload: a 4096 x 4096 fully periodic Taylor-Green vortex (Ma 0.05, 1% T
+perturbation, 1e-4 density noise, seed 0), D2Q16, Hermite order 3, Kn 0.05,
+b = -1/2, FP32 compute and storage.  One benchmark step is one whole solve:
+initial populations from device-resident fields, 1000 fused time steps, and
+the nine moment fields.  value = lattice updates per second / 1e6 (MLUPS)
+with the fields already in HBM; e2e = the same solve through the C ABI with
+host buffers (create from pinned host fields, moments copied back to pinned
+host memory) timed on the wall clock.
+
+Under torchrun each rank runs its own replica of the solve (independent
+problems, no collective on the data path): scaling "weak", value = all
+ranks' updates / the slowest rank's time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6800.0
+BYTES_PER_LUP = 2 * 16 * 4  # read f^n once, write f^{n+1} once, Q = 16 FP32
+METRIC = "ES-BGK MLUPS"
+UNIT = "MLUPS"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=4096, help="grid is n x n")
+    ap.add_argument("--lattice-steps", type=int, default=1000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def committed_traffic(source_digest: str):
+    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_step_tgv4096_d2q16.md")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    vals = {}
+    for ln in lines:
+        if ln.startswith("- ") and ":" in ln:
+            k, v = ln[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel source sha256") != source_digest:
+        return None
+    try:
+        return float(vals["dram bytes per launch (scaled to 4096^2)"])
+    except (KeyError, ValueError):
+        return None
+
+
+def source_digest():
+    import hashlib
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1209_6548_gb300", "csrc", "lesbgk.cu"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in (self.out or "").splitlines():
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(n: int, rows: int = 128, steps: int = 8):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: the
+    first `rows` rows of the n x n Taylor-Green initial state, periodic, for
+    `steps` time steps, on all host cores the process may use."""
+    import numpy as np
+    import oracle as O
+    from paper_1209_6548_gb300 import inputs as I
+    prob = I.tgv(n)
+    fields = I.initial_fields(prob)[:, :rows, :].copy()
+    cores = len(os.sched_getaffinity(0))
+    O.set_threads(cores)
+    dx = dy = 1.0 / n
+    c, _ = O.gauss_hermite_1d(4)
+    dt = 0.5 * dx / float(np.abs(c).max())
+    op = O.make_params(nroots=4, order=3, nx=n, ny=rows, bc_y=0, kn=prob.kn, b=prob.b,
+                       visc_exp=prob.visc_exp, dt=dt, dx=dx, dy=dy)
+    f = O.init(op, fields)
+    t0 = time.perf_counter()
+    O.run(op, f, steps)
+    sec = time.perf_counter() - t0
+    return {"value": n * rows * steps / sec / 1e6, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
+            "sample": f"{n}x{rows} periodic rows of the Taylor-Green state, {steps} FP64 oracle steps ({sec:.1f} s)"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    samples = []
+    t_all = time.perf_counter()
+    base = None
+    for k in range(args.warmup + args.steps):
+        base = cpu_baseline(args.n, rows=32, steps=2)
+        if k >= args.warmup:
+            samples.append(base["value"])
+    value = statistics.median(samples)
+    base["value"] = value
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"tgv_{args.n}x{args.n}_d2q16", "sample_rows": 32, "lattice_steps": 2},
+        "cpu_baseline": base,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": time.perf_counter() - t_all,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+    from paper_1209_6548_gb300 import build as B
+    from paper_1209_6548_gb300 import inputs as I
+    from paper_1209_6548_gb300 import lesbgk as L
+
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if pg is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
+    B.build()
+    n, nsteps = args.n, args.lattice_steps
+    prob = I.tgv(n, steps=nsteps)
+    fields = I.initial_fields(prob)
+    params = L.params_from_problem(prob, dt=0.0)
+    stream = torch.cuda.current_stream()
+    d_fields = torch.from_numpy(fields).cuda()
+    solver = L.Solver(params, h_init=fields, stream=stream)
+    d_mom = torch.empty((9, n, n), dtype=torch.float32, device="cuda")
+    cells = n * n
+    launches_per_step = 1 + nsteps + 2
+
+    def one_solve(ev=None):
+        solver.reinit(d_fields)
+        if ev is not None:
+            ev[0].record(stream)
+        solver.step(nsteps)
+        if ev is not None:
+            ev[1].record(stream)
+        L.moments(solver.handle, d_mom.data_ptr(), None, stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        one_solve()
+    barrier()
+    step_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t0.record(stream)
+        for k in range(args.steps):
+            one_solve(step_events[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = max_over_ranks(t0.elapsed_time(t1))
+    kernel_ms = sum(a.elapsed_time(b) for a, b in step_events) / (args.steps * nsteps)
+    kernel_ms = max_over_ranks(kernel_ms)
+    lups = cells * nsteps * args.steps * world
+    value = lups / (ms / 1e3) / 1e6
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_fields = torch.from_numpy(fields).pin_memory()
+        h_out = torch.empty((9, n, n), dtype=torch.float32).pin_memory()
+        h_sums = np.zeros(4)
+        ws = solver.workspace
+        nbytes = solver.nbytes
+        solver.close()
+        h2d = fields.nbytes
+        d2h = h_out.numel() * 4 + h_sums.nbytes
+
+        def e2e_solve():
+            h = L.create(params, ws.data_ptr(), nbytes, h_fields.numpy(), stream.cuda_stream)
+            L.step(h, nsteps, stream.cuda_stream)
+            L.moments_host(h, h_out.numpy(), h_sums, stream.cuda_stream)
+            L.destroy(h)
+
+        for _ in range(max(1, args.warmup // 2)):
+            e2e_solve()
+        barrier()
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_solve()
+        barrier()
+        wsec = max_over_ranks(time.perf_counter() - w0)
+        e2e = {"value": cells * nsteps * args.steps * world / wsec / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    peak, peak_kind = measured_peak()
+    achieved = BYTES_PER_LUP * cells / (kernel_ms / 1e3) / 1e9
+    digest = source_digest()
+    traffic = committed_traffic(digest)
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(n)
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"tgv_{n}x{n}_d2q16_fp32", "nx": n, "ny": n, "velocity_set": "D2Q16",
+                       "order": 3, "kn": prob.kn, "b": prob.b, "lattice_steps_per_step": nsteps,
+                       "l2": "inputs larger than L2 (two 1.07 GB population buffers)",
+                       "parallelism": f"replica x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                         "kernel": "k_step<4,3,2>", "kernel_ms": kernel_ms,
+                         "bytes_per_lup": BYTES_PER_LUP, "source_sha256": digest},
+            "cpu_baseline": base,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
+                       "reasons": clocks["reasons"]},
+        }
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

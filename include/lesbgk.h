@@ -1,0 +1,177 @@
+/*
+ * lesbgk.h -- C ABI of the GB300 lattice ES-BGK solver (liblesbgk.so).
+ *
+ * The method is the lattice ellipsoidal-statistical BGK model of Meng, Zhang,
+ * Hadjiconstantinou, Radtke & Shan (arXiv 1209.6548):
+ *
+ *   f_a(n+1) = f_a - (c_ax dt/dx)[F_{i+1/2} - F_{i-1/2}]
+ *                  - (c_ay dt/dy)[F_{j+1/2} - F_{j-1/2}]
+ *                  + (dt/tau)(f_ES,a - f_a) + dt g_a                 (Sec. 3.1)
+ *
+ * on a tensor-product Gauss-Hermite velocity set (Sec. 2.2, Eq. weight), with
+ * f_ES the Hermite expansion of the anisotropic Gaussian (Eq. cfeq, a_ES^(n)
+ * of Sec. 2.2) to order N, tau = (Kn/Pr) mu/p with Pr = 1/(1-b) and
+ * mu = T^varpi (Sec. 2.1-2.2), second-order TVD fluxes with the minmod
+ * limiter (Sec. 3.1), the projected body force (Sec. 2.2) and fully diffuse
+ * walls (Sec. 3.2, Eq. feq0).
+ *
+ * Conventions (non-dimensional units of Sec. 2.2: R = T0 = rho0 = L = 1):
+ *   - D = 2 (the lattice dimension) in T, in Eq. (feq0) and in Pr.
+ *   - Velocity index a = ix*nroots + iy, c_a = (c_ix, c_iy), the 1D roots of
+ *     He_nroots sorted ascending.
+ *   - Grid nx x ny nodes, x periodic.  bc_y = LESBGK_PERIODIC, or
+ *     LESBGK_DIFFUSE with walls on nodes j = 0 (bottom, inward normal +y) and
+ *     j = ny-1 (top); ghost rows beyond a wall hold the wall node's values.
+ *   - Spacing: periodic y: dx = 1/nx, dy = 1/ny; walls: dy = 1/(ny-1), dx = dy.
+ *   - Populations are stored as deviations f_a - w_a (w_a the quadrature
+ *     weight, i.e. the rest equilibrium at rho0 = 1, T0 = 1), layout
+ *     [a][j][i] (a-major, then row j, then column i), float32.
+ *
+ * Memory: the caller owns every device buffer.  lesbgk_workspace_size tells
+ * how many bytes of device memory one solve needs; the caller allocates them
+ * (e.g. a torch uint8 tensor) and passes the pointer to lesbgk_create, and
+ * keeps them alive until lesbgk_destroy.  The library allocates no device
+ * memory.  Every call is asynchronous on the given CUDA stream (a
+ * cudaStream_t passed as void*; NULL = legacy default stream) except where
+ * a host output is written, which synchronises that stream.
+ *
+ * Errors: every function returns 0 on success or a negative LESBGK_E* code;
+ * lesbgk_last_error() returns a thread-local message for the last failure.
+ * The library never aborts and has no CPU fallback.
+ */
+#ifndef LESBGK_H
+#define LESBGK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LESBGK_OK 0
+#define LESBGK_EINVAL (-1)    /* invalid argument */
+#define LESBGK_EUNSTABLE (-2) /* CFL > 1, or explicit dt with dt/tau_ref >= 2 */
+#define LESBGK_ESPACE (-3)    /* workspace too small or misaligned */
+#define LESBGK_ECUDA (-4)     /* CUDA error (message in lesbgk_last_error) */
+#define LESBGK_EDIVERGED (-5) /* NaN/Inf found in the moments */
+
+#define LESBGK_PERIODIC 0
+#define LESBGK_DIFFUSE 1
+
+#define LESBGK_F32 0
+
+/* Advection schemes.  LESBGK_UNSPLIT is the update of Sec. 3.1 as printed:
+ * both flux differences are taken from f^n.  For flows that vary in both x
+ * and y that sum of two one-dimensional second-order operators has an
+ * amplification factor above 1 at every Courant number (the paper only runs
+ * flows uniform in x, where it is exact); LESBGK_SPLIT takes the y-sweep
+ * first, f* = f^n - (c_y dt/dy)[F_{j+1/2} - F_{j-1/2}](f^n), then the x-fluxes
+ * of f*, with collision and force from f^n.  For flows uniform in x the two
+ * give the same update. */
+#define LESBGK_UNSPLIT 0
+#define LESBGK_SPLIT 1
+
+typedef struct lesbgk_params {
+  uint32_t struct_size; /* sizeof(lesbgk_params), checked */
+  int32_t nroots;       /* Gauss-Hermite roots per axis: 4 (D2Q16) or 6 (D2Q36) */
+  int32_t order;        /* Hermite order N of f_ES (3 or 4); 0 = 3 for D2Q16, 4 for D2Q36 */
+  int32_t nx, ny;       /* nodes; nx >= 1; ny >= 1 (>= 2 with walls) */
+  int32_t bc_y;         /* LESBGK_PERIODIC or LESBGK_DIFFUSE */
+  int32_t storage;      /* LESBGK_F32 */
+  int32_t scheme;       /* LESBGK_UNSPLIT (default) or LESBGK_SPLIT */
+  double kn;            /* Knudsen number of Sec. 2.2, > 0 */
+  double b;             /* ES parameter, -1/2 <= b < 1 (b = 1 gives tau = 0) */
+  double visc_exp;      /* varpi in mu = T^varpi (0.5 hard sphere, 1 Maxwell) */
+  double cfl;           /* used when dt == 0: dt = min(cfl min(dx,dy)/c_max, tau_ref) */
+  double dt;            /* explicit time step, or 0 */
+  double wall_T[2];     /* wall temperatures, [0] = bottom (j=0), [1] = top */
+  double wall_ux[2];    /* wall x-velocities (walls do not move in y) */
+  double g[2];          /* body force (g_x, g_y) */
+} lesbgk_params;
+
+/* Read-only facts about a created solver. */
+typedef struct lesbgk_info {
+  double dt, dx, dy;  /* time step and spacing in use */
+  double c_max;       /* largest |root| of He_nroots */
+  double cfl;         /* effective Courant number c_max dt / min(dx,dy) */
+  double tau_ref;     /* (Kn/Pr) T_max^(varpi-1) / rho_max at set-up */
+  int64_t steps_done; /* time steps taken since create */
+  int32_t q, order;   /* number of velocities, Hermite order in use */
+  int32_t cells_per_thread, rows_per_segment; /* launch shape of the step kernel */
+} lesbgk_info;
+
+typedef struct lesbgk lesbgk;
+
+/* Bytes of device workspace one solve with these parameters needs
+ * (two population buffers of Q*nx*ny floats each, the second also large enough
+ * to stage the initial fields and the nine moment fields, plus 4 KiB of
+ * reduction scratch per 1024 blocks).  Returns LESBGK_EINVAL on bad params. */
+int lesbgk_workspace_size(const lesbgk_params *p, size_t *bytes);
+
+/* Validate p, build the quadrature and Hermite tables in FP64 on the host
+ * (Sec. 2.2), pick dt, and write the initial populations
+ * f = rho S(T,u) (Eq. feq0 at order N), followed once by the wall rule.
+ *   d_workspace: device memory of >= lesbgk_workspace_size bytes, 256-byte
+ *                aligned, owned by the caller.
+ *   h_init:      HOST array double[4][ny][nx] = rho, u_x, u_y, T per node, or
+ *                NULL for rest (rho = 1, u = 0, T = 1).  It is copied before
+ *                the call returns.
+ *   out:         receives the handle (host memory owned by the library until
+ *                lesbgk_destroy). */
+int lesbgk_create(const lesbgk_params *p, void *d_workspace, size_t bytes, const double *h_init,
+                  void *stream, lesbgk **out);
+
+/* Re-initialise the populations in place from DEVICE fields d_fields,
+ * double[4][ny][nx] = rho, u_x, u_y, T (or NULL for rest): f = rho S(T,u)
+ * then the wall rule, exactly as lesbgk_create does; the step counter restarts
+ * at 0.  dt and the tables chosen at creation are kept.  d_fields must not
+ * overlap the workspace. */
+int lesbgk_reinit(lesbgk *h, const double *d_fields, void *stream);
+
+/* Take nsteps >= 0 time steps: each is one launch of the fused kernel
+ * (moments -> tau -> lambda -> a_ES -> force -> Hermite evaluation -> TVD
+ * advection -> update -> diffuse walls), ping-ponging the two buffers. */
+int lesbgk_step(lesbgk *h, int64_t nsteps, void *stream);
+
+/* Moments of Eq. (mac) per node into DEVICE memory d_out, float[9][ny][nx]:
+ * rho, u_x, u_y, T, sigma_xx, sigma_xy, sigma_yy, q_x, q_y
+ * (sigma trace-free, q_i = 1/2 sum f C_i C^2, D = 2).
+ * If h_sums is not NULL it receives, in HOST memory, double[4]: total mass,
+ * x- and y-momentum and energy (sum over nodes of sum_a f_a {1, c_x, c_y,
+ * c^2/2}), accumulated in FP64 in a fixed order (bitwise reproducible); this
+ * synchronises the stream, and returns LESBGK_EDIVERGED if any is not
+ * finite. */
+int lesbgk_moments(lesbgk *h, float *d_out, double *h_sums, void *stream);
+
+/* As lesbgk_moments, but into HOST memory h_out (float[9][ny][nx]); the
+ * moments are staged in the workspace and copied back before returning. */
+int lesbgk_moments_host(lesbgk *h, float *h_out, double *h_sums, void *stream);
+
+/* Copy the current populations (deviations f_a - w_a, float[Q][ny][nx]) into
+ * DEVICE memory d_out; with lesbgk_set_populations this is a checkpoint. */
+int lesbgk_get_populations(lesbgk *h, float *d_out, void *stream);
+
+/* Overwrite the current populations from DEVICE memory d_in (same layout);
+ * the step counter is set to steps_done. */
+int lesbgk_set_populations(lesbgk *h, const float *d_in, int64_t steps_done, void *stream);
+
+/* Choose the launch shape of the step kernel: cells_per_thread (1 or 2
+ * consecutive x-nodes per lane; 2 needs nx even and nroots = 4) and
+ * rows_per_segment (rows one warp marches through, >= 1).  0 keeps the current
+ * value.  Results do not depend on the shape (bitwise). */
+int lesbgk_set_launch(lesbgk *h, int32_t cells_per_thread, int32_t rows_per_segment);
+
+/* Fill *out with the solver's time step, spacing and launch shape. */
+int lesbgk_get_info(const lesbgk *h, lesbgk_info *out);
+
+/* Release the handle (not the caller's workspace).  NULL is a no-op. */
+int lesbgk_destroy(lesbgk *h);
+
+/* Thread-local message of the last error ("" if none). */
+const char *lesbgk_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LESBGK_H */

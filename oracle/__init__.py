@@ -30,7 +30,7 @@ _lib = None
 class OrcParams(C.Structure):
     _fields_ = [
         ("nroots", C.c_int32), ("order", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32),
-        ("bc_y", C.c_int32), ("pad_", C.c_int32),
+        ("bc_y", C.c_int32), ("scheme", C.c_int32),
         ("kn", C.c_double), ("b", C.c_double), ("visc_exp", C.c_double),
         ("dt", C.c_double), ("dx", C.c_double), ("dy", C.c_double),
         ("wall_T", C.c_double * 2), ("wall_ux", C.c_double * 2), ("g", C.c_double * 2),
@@ -107,10 +107,13 @@ def a_es(n: int, rho: float, u, lam) -> np.ndarray:
     return out.reshape((2,) * n) if n else out
 
 
+UNSPLIT, SPLIT = 0, 1
+
+
 def make_params(*, nroots, order, nx, ny, bc_y, kn, b, visc_exp, dt, dx, dy,
-                wall_T=(1.0, 1.0), wall_ux=(0.0, 0.0), g=(0.0, 0.0)) -> OrcParams:
+                wall_T=(1.0, 1.0), wall_ux=(0.0, 0.0), g=(0.0, 0.0), scheme=UNSPLIT) -> OrcParams:
     p = OrcParams()
-    p.nroots, p.order, p.nx, p.ny, p.bc_y = nroots, order, nx, ny, bc_y
+    p.nroots, p.order, p.nx, p.ny, p.bc_y, p.scheme = nroots, order, nx, ny, bc_y, scheme
     p.kn, p.b, p.visc_exp, p.dt, p.dx, p.dy = kn, b, visc_exp, dt, dx, dy
     p.wall_T[0], p.wall_T[1] = wall_T
     p.wall_ux[0], p.wall_ux[1] = wall_ux

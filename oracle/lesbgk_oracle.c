@@ -20,7 +20,9 @@
  *   - a_ES^(0..4) as printed in Sec. 2.2 and f_ES,a = w_a sum_n a:chi/n!.
  *   - Body force F = omega sum_{n=1}^{N} g a^(n-1):chi^(n)/(n-1)! (Sec. 2.2),
  *     with a^(k) the distribution's own Hermite moments.
- *   - Forward Euler + second-order TVD/minmod fluxes (Sec. 3.1).
+ *   - Forward Euler + second-order TVD/minmod fluxes (Sec. 3.1), as printed
+ *     (both flux differences from f^n), or dimensionally split (y-sweep then
+ *     x-sweep) for flows that vary in both x and y.
  *   - Truncated Maxwellian S(T,u), Eq. (feq0), and the diffuse wall of
  *     Sec. 3.2 (outgoing half = rho_W S, ghosts = wall node).
  *
@@ -53,7 +55,9 @@ typedef struct orc_params {
   int32_t order;    /* Hermite truncation order N (0..4) */
   int32_t nx, ny;   /* nodes in x (periodic) and y */
   int32_t bc_y;     /* 0 = periodic in y, 1 = diffuse walls on j=0, j=ny-1 */
-  int32_t pad_;
+  int32_t scheme;   /* 0 = the update of Sec. 3.1 as printed (both flux
+                       differences from f^n); 1 = split: a y-sweep, then an
+                       x-sweep of the y-swept values (reading for 2D flows) */
   double kn;        /* Kn of Sec. 2.2 */
   double b;         /* ES parameter, Pr = 1/(1-b) */
   double visc_exp;  /* varpi in mu = T^varpi */
@@ -458,6 +462,7 @@ static int check_params(const orc_params *p) {
   if (p->order < 0 || p->order > ORC_MAXN) return -1;
   if (p->nx < 1 || p->ny < 1) return -1;
   if (p->bc_y == 1 && p->ny < 2) return -1;
+  if (p->scheme != 0 && p->scheme != 1) return -1;
   return 0;
 }
 
@@ -481,11 +486,34 @@ int orc_init(const orc_params *p, const double *fields, double *f) {
 }
 
 /* One time step n -> n+1 of the scheme in Sec. 3.1 followed by the walls of
- * Sec. 3.2.  f_in and f_out must not alias. */
+ * Sec. 3.2.  f_in and f_out must not alias.
+ *
+ * scheme 0 is the printed update: both flux differences are taken from f^n.
+ * scheme 1 (a reading, for flows that vary in x and y, where the printed
+ * unsplit sum of two one-dimensional second-order fluxes has an amplification
+ * factor above 1): first the y-sweep f* = f^n - (c_y dt/dy) dF_y(f^n), then
+ * the x-sweep of f*; collision and force are evaluated from f^n as printed.
+ * For fields that do not vary in x both schemes give the same update. */
 int orc_step(const orc_params *p, const double *fin, double *fout) {
   orc_lattice L;
   if (check_params(p) || lattice_init(&L, p->nroots)) return -1;
   const int Q = L.Q;
+  const size_t n = (size_t)Q * p->nx * p->ny;
+  double *fstar = NULL;
+  if (p->scheme == 1) {
+    fstar = (double *)malloc(n * sizeof(double));
+    if (!fstar) return -1;
+#pragma omp parallel for schedule(static) num_threads(orc_threads)
+    for (int j = 0; j < p->ny; ++j)
+      for (int i = 0; i < p->nx; ++i)
+        for (int a = 0; a < Q; ++a) {
+          double cy = L.cy[a], fy[5];
+          for (int k = -2; k <= 2; ++k) fy[k + 2] = fin[fidx(p, a, row_of(p, j + k), i)];
+          double nuy = fabs(cy) * p->dt / p->dy;
+          double dFy = flux_difference(cy, nuy, fy[0], fy[1], fy[2], fy[3], fy[4]);
+          fstar[fidx(p, a, j, i)] = fin[fidx(p, a, j, i)] - cy * p->dt / p->dy * dFy;
+        }
+  }
 #pragma omp parallel for schedule(static) num_threads(orc_threads)
   for (int j = 0; j < p->ny; ++j) {
     double f[ORC_MAXQ], fes[ORC_MAXQ], gf[ORC_MAXQ], tau;
@@ -494,19 +522,26 @@ int orc_step(const orc_params *p, const double *fin, double *fout) {
       cell_collision(&L, p, f, fes, gf, &tau);
       for (int a = 0; a < Q; ++a) {
         double cx = L.cx[a], cy = L.cy[a];
-        double fx[5], fy[5];
-        for (int k = -2; k <= 2; ++k) {
-          fx[k + 2] = fin[fidx(p, a, j, wrap(i + k, p->nx))];
-          fy[k + 2] = fin[fidx(p, a, row_of(p, j + k), i)];
-        }
         double nux = fabs(cx) * p->dt / p->dx, nuy = fabs(cy) * p->dt / p->dy;
-        double dFx = flux_difference(cx, nux, fx[0], fx[1], fx[2], fx[3], fx[4]);
-        double dFy = flux_difference(cy, nuy, fy[0], fy[1], fy[2], fy[3], fy[4]);
-        fout[fidx(p, a, j, i)] = f[a] - cx * p->dt / p->dx * dFx - cy * p->dt / p->dy * dFy
-                                 + p->dt / tau * (fes[a] - f[a]) + gf[a] * p->dt;
+        double fx[5], fy[5];
+        double coll = p->dt / tau * (fes[a] - f[a]) + gf[a] * p->dt;
+        if (p->scheme == 1) {
+          for (int k = -2; k <= 2; ++k) fx[k + 2] = fstar[fidx(p, a, j, wrap(i + k, p->nx))];
+          double dFx = flux_difference(cx, nux, fx[0], fx[1], fx[2], fx[3], fx[4]);
+          fout[fidx(p, a, j, i)] = fx[2] - cx * p->dt / p->dx * dFx + coll;
+        } else {
+          for (int k = -2; k <= 2; ++k) {
+            fx[k + 2] = fin[fidx(p, a, j, wrap(i + k, p->nx))];
+            fy[k + 2] = fin[fidx(p, a, row_of(p, j + k), i)];
+          }
+          double dFx = flux_difference(cx, nux, fx[0], fx[1], fx[2], fx[3], fx[4]);
+          double dFy = flux_difference(cy, nuy, fy[0], fy[1], fy[2], fy[3], fy[4]);
+          fout[fidx(p, a, j, i)] = f[a] - cx * p->dt / p->dx * dFx - cy * p->dt / p->dy * dFy + coll;
+        }
       }
     }
   }
+  free(fstar);
   apply_walls(&L, p, fout);
   return 0;
 }

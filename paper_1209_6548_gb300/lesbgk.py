@@ -1,0 +1,254 @@
+"""ctypes binding of liblesbgk.so (include/lesbgk.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library.
+PyTorch supplies device memory (the caller-owned workspace and output
+buffers) and the CUDA stream handle.  If the library has not been built, the
+first call raises; there is no fallback.
+
+The module-level functions keep the C names without the ``lesbgk_`` prefix;
+``Solver`` wraps one handle together with its torch-allocated workspace.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from .build import LIB
+
+OK, EINVAL, EUNSTABLE, ESPACE, ECUDA, EDIVERGED = 0, -1, -2, -3, -4, -5
+PERIODIC, DIFFUSE = 0, 1
+F32 = 0
+UNSPLIT, SPLIT = 0, 1
+MOMENT_NAMES = ("rho", "ux", "uy", "T", "sxx", "sxy", "syy", "qx", "qy")
+
+# Every entry point declared in include/lesbgk.h.
+SYMBOLS = ("lesbgk_workspace_size", "lesbgk_create", "lesbgk_reinit", "lesbgk_step", "lesbgk_moments",
+           "lesbgk_moments_host", "lesbgk_get_populations", "lesbgk_set_populations",
+           "lesbgk_set_launch", "lesbgk_get_info", "lesbgk_destroy", "lesbgk_last_error")
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("struct_size", C.c_uint32), ("nroots", C.c_int32), ("order", C.c_int32),
+        ("nx", C.c_int32), ("ny", C.c_int32), ("bc_y", C.c_int32), ("storage", C.c_int32),
+        ("scheme", C.c_int32),
+        ("kn", C.c_double), ("b", C.c_double), ("visc_exp", C.c_double),
+        ("cfl", C.c_double), ("dt", C.c_double),
+        ("wall_T", C.c_double * 2), ("wall_ux", C.c_double * 2), ("g", C.c_double * 2),
+    ]
+
+
+class Info(C.Structure):
+    _fields_ = [
+        ("dt", C.c_double), ("dx", C.c_double), ("dy", C.c_double), ("c_max", C.c_double),
+        ("cfl", C.c_double), ("tau_ref", C.c_double), ("steps_done", C.c_int64),
+        ("q", C.c_int32), ("order", C.c_int32),
+        ("cells_per_thread", C.c_int32), ("rows_per_segment", C.c_int32),
+    ]
+
+
+class LesbgkError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"liblesbgk error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load liblesbgk.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB):
+                raise RuntimeError(f"{LIB} is missing: build it with "
+                                   "`python -m paper_1209_6548_gb300.build` (no CPU fallback exists)")
+            L = C.CDLL(LIB)
+            vp, i64 = C.c_void_p, C.c_int64
+            L.lesbgk_workspace_size.argtypes = [C.POINTER(Params), C.POINTER(C.c_size_t)]
+            L.lesbgk_create.argtypes = [C.POINTER(Params), vp, C.c_size_t, vp, vp, C.POINTER(vp)]
+            L.lesbgk_reinit.argtypes = [vp, vp, vp]
+            L.lesbgk_step.argtypes = [vp, i64, vp]
+            L.lesbgk_moments.argtypes = [vp, vp, vp, vp]
+            L.lesbgk_moments_host.argtypes = [vp, vp, vp, vp]
+            L.lesbgk_get_populations.argtypes = [vp, vp, vp]
+            L.lesbgk_set_populations.argtypes = [vp, vp, i64, vp]
+            L.lesbgk_set_launch.argtypes = [vp, C.c_int32, C.c_int32]
+            L.lesbgk_get_info.argtypes = [vp, C.POINTER(Info)]
+            L.lesbgk_destroy.argtypes = [vp]
+            L.lesbgk_last_error.restype = C.c_char_p
+            L.lesbgk_last_error.argtypes = []
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().lesbgk_last_error().decode()
+
+
+def _check(rc: int) -> None:
+    if rc != OK:
+        raise LesbgkError(rc, last_error())
+
+
+def make_params(*, nroots=4, order=0, nx, ny, bc_y=DIFFUSE, kn, b, visc_exp=0.5, cfl=0.5, dt=0.0,
+                wall_T=(1.0, 1.0), wall_ux=(0.0, 0.0), g=(0.0, 0.0), storage=F32, scheme=UNSPLIT) -> Params:
+    p = Params()
+    p.struct_size = C.sizeof(Params)
+    p.nroots, p.order, p.nx, p.ny, p.bc_y, p.storage = nroots, order, nx, ny, bc_y, storage
+    p.scheme = scheme
+    p.kn, p.b, p.visc_exp, p.cfl, p.dt = kn, b, visc_exp, cfl, dt
+    p.wall_T[0], p.wall_T[1] = wall_T
+    p.wall_ux[0], p.wall_ux[1] = wall_ux
+    p.g[0], p.g[1] = g
+    return p
+
+
+def params_from_problem(prob, dt: float = 0.0) -> Params:
+    return make_params(nroots=prob.nroots, order=prob.order, nx=prob.nx, ny=prob.ny, bc_y=prob.bc_y,
+                       kn=prob.kn, b=prob.b, visc_exp=prob.visc_exp, cfl=prob.cfl, dt=dt,
+                       wall_T=tuple(prob.wall_T), wall_ux=tuple(prob.wall_ux), g=tuple(prob.g),
+                       scheme=prob.scheme)
+
+
+def workspace_size(p: Params) -> int:
+    n = C.c_size_t()
+    _check(lib().lesbgk_workspace_size(C.byref(p), C.byref(n)))
+    return int(n.value)
+
+
+def create(p: Params, d_workspace: int, nbytes: int, h_init, stream: int) -> int:
+    h = C.c_void_p()
+    ptr = None
+    if h_init is not None:
+        arr = np.ascontiguousarray(h_init, dtype=np.float64)
+        if arr.shape != (4, p.ny, p.nx):
+            raise ValueError(f"h_init must have shape (4, {p.ny}, {p.nx})")
+        ptr = arr.ctypes.data
+    _check(lib().lesbgk_create(C.byref(p), C.c_void_p(d_workspace), C.c_size_t(nbytes),
+                               C.c_void_p(ptr), C.c_void_p(stream), C.byref(h)))
+    return h.value
+
+
+def reinit(h: int, d_fields, stream: int) -> None:
+    _check(lib().lesbgk_reinit(C.c_void_p(h), C.c_void_p(d_fields), C.c_void_p(stream)))
+
+
+def step(h: int, nsteps: int, stream: int) -> None:
+    _check(lib().lesbgk_step(C.c_void_p(h), C.c_int64(nsteps), C.c_void_p(stream)))
+
+
+def moments(h: int, d_out: int, h_sums, stream: int) -> None:
+    sp = None if h_sums is None else h_sums.ctypes.data
+    _check(lib().lesbgk_moments(C.c_void_p(h), C.c_void_p(d_out), C.c_void_p(sp), C.c_void_p(stream)))
+
+
+def moments_host(h: int, h_out: np.ndarray, h_sums, stream: int) -> None:
+    assert h_out.dtype == np.float32 and h_out.flags.c_contiguous
+    sp = None if h_sums is None else h_sums.ctypes.data
+    _check(lib().lesbgk_moments_host(C.c_void_p(h), C.c_void_p(h_out.ctypes.data), C.c_void_p(sp),
+                                     C.c_void_p(stream)))
+
+
+def get_populations(h: int, d_out: int, stream: int) -> None:
+    _check(lib().lesbgk_get_populations(C.c_void_p(h), C.c_void_p(d_out), C.c_void_p(stream)))
+
+
+def set_populations(h: int, d_in: int, steps_done: int, stream: int) -> None:
+    _check(lib().lesbgk_set_populations(C.c_void_p(h), C.c_void_p(d_in), C.c_int64(steps_done),
+                                        C.c_void_p(stream)))
+
+
+def set_launch(h: int, cells_per_thread: int = 0, rows_per_segment: int = 0) -> None:
+    _check(lib().lesbgk_set_launch(C.c_void_p(h), C.c_int32(cells_per_thread), C.c_int32(rows_per_segment)))
+
+
+def get_info(h: int) -> Info:
+    out = Info()
+    _check(lib().lesbgk_get_info(C.c_void_p(h), C.byref(out)))
+    return out
+
+
+def destroy(h: int) -> None:
+    lib().lesbgk_destroy(C.c_void_p(h))
+
+
+@dataclass
+class Solver:
+    """One solve on the current CUDA device: torch-allocated workspace + handle."""
+
+    params: Params
+    h_init: object = None
+    stream: object = None
+
+    def __post_init__(self):
+        import torch
+        self._torch = torch
+        if self.stream is None:
+            self.stream = torch.cuda.current_stream()
+        self.nbytes = workspace_size(self.params)
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device="cuda")
+        self.handle = create(self.params, self.workspace.data_ptr(), self.nbytes, self.h_init,
+                             self.stream.cuda_stream)
+
+    @property
+    def q(self) -> int:
+        return self.params.nroots * self.params.nroots
+
+    def reinit(self, d_fields=None) -> None:
+        """Re-initialise from a (4, ny, nx) float64 CUDA tensor (or rest)."""
+        ptr = None
+        if d_fields is not None:
+            assert d_fields.is_cuda and d_fields.dtype == self._torch.float64 and d_fields.is_contiguous()
+            assert tuple(d_fields.shape) == (4, self.params.ny, self.params.nx)
+            ptr = d_fields.data_ptr()
+        reinit(self.handle, ptr, self.stream.cuda_stream)
+
+    def step(self, n: int) -> None:
+        step(self.handle, n, self.stream.cuda_stream)
+
+    def moments(self, sums: bool = False):
+        """(9, ny, nx) float32 device tensor; with sums=True also the FP64 totals."""
+        out = self._torch.empty((9, self.params.ny, self.params.nx), dtype=self._torch.float32, device="cuda")
+        hs = np.zeros(4) if sums else None
+        moments(self.handle, out.data_ptr(), hs, self.stream.cuda_stream)
+        return (out, hs) if sums else out
+
+    def moments_host(self):
+        out = np.empty((9, self.params.ny, self.params.nx), dtype=np.float32)
+        hs = np.zeros(4)
+        moments_host(self.handle, out, hs, self.stream.cuda_stream)
+        return out, hs
+
+    def populations(self):
+        out = self._torch.empty((self.q, self.params.ny, self.params.nx), dtype=self._torch.float32, device="cuda")
+        get_populations(self.handle, out.data_ptr(), self.stream.cuda_stream)
+        return out
+
+    def set_populations(self, t, steps_done: int) -> None:
+        t = t.contiguous()
+        set_populations(self.handle, t.data_ptr(), steps_done, self.stream.cuda_stream)
+
+    def set_launch(self, cells_per_thread: int = 0, rows_per_segment: int = 0) -> None:
+        set_launch(self.handle, cells_per_thread, rows_per_segment)
+
+    @property
+    def info(self) -> Info:
+        return get_info(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -50,22 +50,37 @@ def oracle_params(p: Problem, dt: float, nx=None, ny=None, bc_y=None):
     return O.make_params(nroots=p.nroots, order=order_of(p), nx=nx or p.nx, ny=ny or p.ny,
                          bc_y=p.bc_y if bc_y is None else bc_y, kn=p.kn, b=p.b,
                          visc_exp=p.visc_exp, dt=dt, dx=dx, dy=dy, wall_T=tuple(p.wall_T),
-                         wall_ux=tuple(p.wall_ux), g=tuple(p.g))
+                         wall_ux=tuple(p.wall_ux), g=tuple(p.g), scheme=p.scheme)
+
+
+GROUPS = {"rho": ("rho",), "T": ("T",), "u": ("ux", "uy"), "sigma": ("sxx", "sxy", "syy"),
+          "q": ("qx", "qy")}
+# Quantities whose magnitude is below FLOOR are compared in absolute terms at
+# tol * FLOOR: FP32 deviation storage resolves the second and third moments to
+# about 1e-9 absolute, so a stress or heat flux of 1e-4 (three steps after an
+# equilibrium start) cannot be held to 1e-5 of itself.
+FLOOR = {"rho": 0.0, "T": 0.0, "u": 1e-3, "sigma": 1e-3, "q": 1e-3}
 
 
 def field_errors(gpu: np.ndarray, ref: np.ndarray, rest=None):
-    """Per-field relative error e = max|gpu-ref| / max|ref| over the nine
-    moment fields, and the perturbation-relative e' = max|gpu-ref| /
-    max|ref - rest| where the reference's deviation from rest exceeds 1e-6."""
+    """Per-field errors against the oracle.
+
+    Returns {name: (e, e_own, abs)} where abs = max|gpu - ref| over the field,
+    e_own = abs / max|ref field| (component relative), and
+    e = abs / max(largest magnitude of the quantity the field belongs to, FLOOR)
+    with the quantities rho; T; the velocity vector; the stress tensor; the
+    heat-flux vector -- so a component that is near zero by symmetry is
+    measured against its own vector's scale, not its own rounding noise."""
+    names = list(O.MOMENT_NAMES)
+    scale = {}
+    for grp, members in GROUPS.items():
+        s = max(float(np.max(np.abs(ref[names.index(m)]))) for m in members)
+        for m in members:
+            scale[m] = max(s, FLOOR[grp])
     out = {}
-    for k, name in enumerate(O.MOMENT_NAMES):
+    for k, name in enumerate(names):
         d = float(np.max(np.abs(gpu[k].astype(np.float64) - ref[k])))
-        scale = float(np.max(np.abs(ref[k])))
-        e = d / scale if scale > 0 else d
-        ep = None
-        if rest is not None:
-            dev = float(np.max(np.abs(ref[k] - rest[k])))
-            if dev > 1e-6:
-                ep = d / dev
-        out[name] = (e, ep, d)
+        own = float(np.max(np.abs(ref[k])))
+        e = d / scale[name] if scale[name] > 0 else d
+        out[name] = (e, d / own if own > 0 else d, d)
     return out

@@ -1,0 +1,88 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and loads,
+exports every symbol include/lesbgk.h declares, and rejects bad arguments
+before touching the device."""
+from __future__ import annotations
+
+import ctypes as C
+import re
+import os
+
+import pytest
+
+from paper_1209_6548_gb300 import build as B
+from paper_1209_6548_gb300 import lesbgk as L
+
+HEADER = os.path.join(B.ROOT, "include", "lesbgk.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.lib()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(lesbgk_[a-z_]+)\s*\(", text)))
+
+
+def test_header_symbols_exported(lib):
+    names = declared_symbols()
+    assert set(names) == set(L.SYMBOLS)
+    for n in names:
+        assert getattr(lib, n) is not None
+
+
+def test_struct_sizes_match_header(lib):
+    # struct_size is checked by the library: a mismatch must be rejected
+    p = L.make_params(nx=4, ny=8, kn=0.1, b=0.0)
+    assert L.workspace_size(p) > 0
+    p.struct_size = C.sizeof(L.Params) - 8
+    with pytest.raises(L.LesbgkError) as e:
+        L.workspace_size(p)
+    assert e.value.code == L.EINVAL
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(b=1.0), L.EINVAL),
+    (dict(b=-0.6), L.EINVAL),
+    (dict(kn=0.0), L.EINVAL),
+    (dict(nroots=5), L.EINVAL),
+    (dict(order=5), L.EINVAL),
+    (dict(ny=1), L.EINVAL),          # walls need two rows
+    (dict(nx=0), L.EINVAL),
+    (dict(cfl=1.5), L.EINVAL),
+    (dict(visc_exp=1.5), L.EINVAL),
+    (dict(storage=7), L.EINVAL),
+])
+def test_invalid_arguments_rejected(lib, kw, code):
+    base = dict(nx=4, ny=8, kn=0.1, b=0.0, bc_y=L.DIFFUSE)
+    base.update(kw)
+    with pytest.raises(L.LesbgkError) as e:
+        L.workspace_size(L.make_params(**base))
+    assert e.value.code == code
+
+
+def test_workspace_size_formula(lib):
+    p = L.make_params(nx=64, ny=32, kn=0.1, b=0.0)
+    n = L.workspace_size(p)
+    # two buffers of Q*cells floats + reduction scratch
+    assert n >= 2 * 16 * 64 * 32 * 4
+    p6 = L.make_params(nroots=6, nx=64, ny=32, kn=0.1, b=0.0)
+    assert L.workspace_size(p6) >= 2 * 36 * 64 * 32 * 4
+
+
+def test_create_rejects_small_workspace_before_device_use(lib):
+    p = L.make_params(nx=4, ny=8, kn=0.1, b=0.0)
+    h = C.c_void_p()
+    rc = lib.lesbgk_create(C.byref(p), C.c_void_p(256), C.c_size_t(16), None, None, C.byref(h))
+    assert rc == L.ESPACE and h.value is None
+    assert "workspace" in L.last_error()
+    rc = lib.lesbgk_create(C.byref(p), C.c_void_p(257), C.c_size_t(1 << 30), None, None, C.byref(h))
+    assert rc == L.ESPACE and "aligned" in L.last_error()
+
+
+def test_null_handles_rejected(lib):
+    assert lib.lesbgk_step(None, 1, None) == L.EINVAL
+    assert lib.lesbgk_moments(None, None, None, None) == L.EINVAL
+    assert lib.lesbgk_destroy(None) == 0

@@ -1,0 +1,271 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerance (FP32 compute, FP32 deviation storage): for each of the nine moment
+fields, e = max|gpu - ref| / max|ref| <= 1e-5, the relative bar the solver is
+built to; raw populations within 2e-6 of the largest deviation.  Grids are
+chosen to span several warp strips (60 or 28 nodes wide) and row segments,
+with a ragged tail in both directions.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1209_6548_gb300 import build as B
+from paper_1209_6548_gb300 import inputs as I
+from paper_1209_6548_gb300 import lesbgk as L
+from tests.common import field_errors, oracle_params, time_step
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+
+
+def gpu_solver(prob, dt, fields):
+    return L.Solver(L.params_from_problem(prob, dt=dt), h_init=fields)
+
+
+def assert_fields_close(gpu, ref, tol=TOL, what=""):
+    errs = field_errors(gpu, ref)
+    bad = {k: v for k, v in errs.items() if not (v[0] <= tol)}
+    assert not bad, f"{what}: fields over {tol}: {bad}"
+    return errs
+
+
+def run_pair(prob, fields, checkpoints, dt=None):
+    dt = dt or time_step(prob, fields)
+    op = oracle_params(prob, dt)
+    f = O.init(op, fields)
+    s = gpu_solver(prob, dt, fields)
+    done = 0
+    out = []
+    for n in checkpoints:
+        f = O.run(op, f, n - done)
+        s.step(n - done)
+        done = n
+        ref, _ = O.moments(op, f)
+        out.append((n, s.moments().cpu().numpy(), ref, s.populations().cpu().numpy(), f))
+    return out, s, op
+
+
+def test_couette_4x64_2000_steps():
+    """Planar Couette, D2Q16, N = 3, Kn = 0.1, b = -1/2, walls -/+0.05: the
+    nine moment fields after 1, 10, 100 and 2000 steps."""
+    prob = I.couette_4x64()
+    res, s, _ = run_pair(prob, None, [1, 10, 100, 2000])
+    for n, g, r, *_ in res:
+        assert_fields_close(g, r, what=f"step {n}")
+    assert s.info.steps_done == 2000
+
+
+@pytest.mark.parametrize("scheme", [I.UNSPLIT, I.SPLIT])
+@pytest.mark.parametrize("nx,ny", [(70, 37), (71, 23), (130, 9), (1, 1), (2, 3), (5, 66)])
+def test_rough_periodic_fields(nx, ny, scheme):
+    """i.i.d. rough fields exercise every limiter branch; odd nx takes the
+    one-node-per-lane kernel, even nx the two-node one."""
+    prob = I.Problem(name="rough", nx=nx, ny=ny, bc_y=I.PERIODIC, kn=0.05, b=-0.5, scheme=scheme)
+    fields = I.random_fields(prob, seed=nx * 100 + ny)
+    res, *_ = run_pair(prob, fields, [1, 6])
+    for n, g, r, gp, fp in res:
+        assert_fields_close(g, r, what=f"{nx}x{ny} step {n}")
+        w = O.velocity_set(4)[2][:, None, None]
+        dev = fp - w
+        err = np.max(np.abs(gp - dev))
+        assert err <= 2e-6 * np.max(np.abs(dev)), f"populations: {err:.3e} vs {np.max(np.abs(dev)):.3e}"
+
+
+def test_taylor_green_split_128():
+    """The 2D Taylor-Green vortex with the split scheme, 300 steps."""
+    prob = I.tgv(128, steps=300)
+    res, *_ = run_pair(prob, I.initial_fields(prob), [1, 300])
+    for n, g, r, *_ in res:
+        assert_fields_close(g, r, what=f"tgv128 step {n}")
+
+
+@pytest.mark.parametrize("scheme", [I.UNSPLIT, I.SPLIT])
+def test_launch_shape_does_not_change_bits(scheme):
+    prob = I.Problem(name="shape", nx=128, ny=70, bc_y=I.DIFFUSE, kn=0.05, b=0.5, wall_ux=(-0.05, 0.05),
+                     g=(1e-3, 0.0), scheme=scheme)
+    fields = I.random_fields(prob, seed=5)
+    dt = time_step(prob, fields)
+    outs = []
+    for cpt, rows in [(1, 16), (2, 16), (2, 64), (1, 7), (2, 1000)]:
+        s = gpu_solver(prob, dt, fields)
+        s.set_launch(cpt, rows)
+        assert s.info.cells_per_thread == cpt and s.info.rows_per_segment == rows
+        s.step(9)
+        outs.append(s.populations().cpu().numpy())
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
+def _sampled_oracle(prob, fields, dt, k, cells):
+    """Moments after k steps at the given (j, i) nodes, each computed by the
+    oracle on its own periodic (4k+1)^2 patch (x and y periodic) or a
+    (4k+1)-wide full-height strip (walls in y): the wrapped-around values do
+    not reach the centre within k steps."""
+    r = 2 * k
+    out = []
+    for j, i in cells:
+        cols = np.arange(i - r, i + r + 1) % prob.nx
+        if prob.bc_y == I.PERIODIC:
+            rows = np.arange(j - r, j + r + 1) % prob.ny
+            jj = r
+        else:
+            rows = np.arange(prob.ny)
+            jj = j
+        patch = fields[:, rows][:, :, cols]
+        op = oracle_params(prob, dt, nx=len(cols), ny=len(rows))
+        f = O.run(op, O.init(op, patch), k)
+        m, _ = O.moments(op, f)
+        out.append(m[:, jj, r])
+    return np.array(out).T  # (9, ncells)
+
+
+@pytest.mark.parametrize("which", ["tgv4096", "poiseuille512x1024"])
+def test_full_size_sampled(which):
+    """At the full benchmark sizes and the default launch shape: moments after
+    3 steps at 24 seeded nodes against the oracle run node by node."""
+    prob = I.tgv(4096) if which == "tgv4096" else I.poiseuille(512, 1024)
+    fields = I.initial_fields(prob)
+    dt = time_step(prob, fields)
+    s = gpu_solver(prob, dt, fields)
+    k = 3
+    s.step(k)
+    mom = s.moments()
+    rng = np.random.default_rng(2024)
+    cells = [(int(rng.integers(prob.ny)), int(rng.integers(prob.nx))) for _ in range(20)]
+    cells += [(0, 5), (prob.ny - 1, 7), (1, 0), (prob.ny - 2, prob.nx - 1)]
+    import torch
+    jj = torch.tensor([c[0] for c in cells], device="cuda")
+    ii = torch.tensor([c[1] for c in cells], device="cuda")
+    g = mom[:, jj, ii].cpu().numpy()
+    ref = _sampled_oracle(prob, fields, dt, k, cells)
+    assert_fields_close(g[:, :, None], ref[:, :, None], what=which)
+
+
+def test_grid_sizes_near_strip_and_segment_edges():
+    """nx around one and two strip widths (60 and 120 nodes), ny not a multiple
+    of the segment length, walls."""
+    for nx in (58, 60, 62, 120, 122):
+        prob = I.Problem(name="edge", nx=nx, ny=35, bc_y=I.DIFFUSE, kn=0.1, b=-0.5, wall_ux=(0.0, 0.05),
+                         wall_T=(1.0, 1.02))
+        fields = I.random_fields(prob, seed=nx)
+        res, *_ = run_pair(prob, fields, [3])
+        for n, g, r, *_ in res:
+            assert_fields_close(g, r, what=f"nx={nx}")
+
+
+@pytest.mark.parametrize("b", [-0.5, 0.0, 0.5])
+def test_walls_force_and_temperature(b):
+    """Walls at different T and u_x, a body force and rough interior fields
+    (i.i.d. data: limiter-branch coverage over a few steps; long runs are on
+    the smooth flows)."""
+    prob = I.Problem(name="mix", nx=64, ny=45, bc_y=I.DIFFUSE, kn=0.08, b=b, wall_T=(0.96, 1.05),
+                     wall_ux=(-0.04, 0.03), g=(2e-3, -1e-3))
+    fields = I.random_fields(prob, seed=11, amp_u=0.03, amp_T=0.03, amp_rho=0.03)
+    res, *_ = run_pair(prob, fields, [1, 10])
+    for n, g, r, *_ in res:
+        assert_fields_close(g, r, what=f"b={b} step {n}")
+
+
+def test_poiseuille_small():
+    prob = I.poiseuille(nx=4, ny=40, steps=300)
+    res, *_ = run_pair(prob, None, [300])
+    for n, g, r, *_ in res:
+        assert_fields_close(g, r, what=f"poiseuille step {n}")
+
+
+def test_fourier_small():
+    prob = I.fourier(ny=33)
+    res, *_ = run_pair(prob, None, [500])
+    for n, g, r, *_ in res:
+        assert_fields_close(g, r, what="fourier")
+
+
+@pytest.mark.parametrize("visc", [0.5, 1.0, 0.75])
+def test_viscosity_exponents(visc):
+    prob = I.Problem(name="v", nx=8, ny=20, bc_y=I.DIFFUSE, kn=0.1, b=-0.5, visc_exp=visc,
+                     wall_T=(0.9, 1.1), wall_ux=(0.0, 0.05))
+    res, *_ = run_pair(prob, None, [200])
+    for n, g, r, *_ in res:
+        assert_fields_close(g, r, what=f"visc {visc}")
+
+
+def test_two_row_channel():
+    """ny = 2: both rows are walls."""
+    prob = I.Problem(name="t", nx=6, ny=2, bc_y=I.DIFFUSE, kn=0.2, b=0.0, wall_T=(0.98, 1.02),
+                     wall_ux=(-0.02, 0.02))
+    res, *_ = run_pair(prob, None, [1, 20])
+    for n, g, r, *_ in res:
+        assert_fields_close(g, r, what=f"two rows step {n}")
+
+
+def test_default_time_step_rule():
+    """dt = 0 asks the library for min(cfl min(dx,dy)/c_max, tau_ref); it must
+    agree with the rule restated on the test side."""
+    for prob, fields in [(I.couette_4x64(), None), (I.tgv(64), I.initial_fields(I.tgv(64))),
+                         (I.Problem(name="s", nx=4, ny=16, kn=0.01, b=0.5), None)]:
+        s = L.Solver(L.params_from_problem(prob, dt=0.0), h_init=fields)
+        assert abs(s.info.dt - time_step(prob, fields)) <= 1e-15 * time_step(prob, fields)
+
+
+def test_unstable_dt_rejected():
+    prob = I.Problem(name="s", nx=4, ny=16, kn=0.01, b=0.5)
+    with pytest.raises(L.LesbgkError) as e:
+        L.Solver(L.params_from_problem(prob, dt=0.02))
+    assert e.value.code == L.EUNSTABLE
+
+
+def test_checkpoint_restart_is_bitwise():
+    prob = I.Problem(name="c", nx=60, ny=30, bc_y=I.DIFFUSE, kn=0.05, b=-0.5, wall_ux=(-0.05, 0.05))
+    fields = I.random_fields(prob, seed=3)
+    dt = time_step(prob, fields)
+    a = gpu_solver(prob, dt, fields)
+    a.step(20)
+    ck = a.populations().clone()
+    a.step(15)
+    b = gpu_solver(prob, dt, fields)
+    b.set_populations(ck, 20)
+    b.step(15)
+    assert b.info.steps_done == 35
+    assert bool((a.populations() == b.populations()).all())
+
+
+def test_deterministic_and_host_moments():
+    prob = I.tgv(128, steps=10)
+    fields = I.initial_fields(prob)
+    dt = time_step(prob, fields)
+    a, b = gpu_solver(prob, dt, fields), gpu_solver(prob, dt, fields)
+    a.step(7)
+    b.step(7)
+    ma, sa = a.moments(sums=True)
+    mh, sh = b.moments_host()
+    assert np.array_equal(ma.cpu().numpy(), mh)
+    assert np.array_equal(sa, sh)
+
+
+def test_conservation_periodic_gpu():
+    """Periodic, no force: FP64 totals of mass, momentum and energy drift only
+    by FP32 rounding of the stored deviations."""
+    prob = I.tgv(256, steps=200)
+    fields = I.initial_fields(prob)
+    s = gpu_solver(prob, time_step(prob, fields), fields)
+    _, s0 = s.moments(sums=True)
+    s.step(200)
+    _, s1 = s.moments(sums=True)
+    cells = prob.cells
+    assert abs(s1[0] - s0[0]) < 1e-9 * cells
+    assert abs(s1[1] - s0[1]) < 1e-9 * cells
+    assert abs(s1[2] - s0[2]) < 1e-9 * cells
+    assert abs(s1[3] - s0[3]) < 1e-9 * cells

@@ -523,3 +523,82 @@ def test_navier_stokes_transport_coefficients(kind):
         flux = 0.5 * (m[8, c, 0] + m[8, c - 1, 0])
         coef = (2 + 2) / 2 * kn * (1 - b) * T ** 0.5
     assert abs(flux / grad / (-coef) - 1.0) < 5e-3
+
+
+# ---------------------------------------------------------------- 2D stability
+def test_unsplit_second_order_sum_is_unstable_in_2d():
+    """Von Neumann: in its smooth regime (Psi = 1) the printed update sums two
+    one-dimensional second-order flux differences of f^n; for waves that vary
+    in both x and y its amplification factor exceeds 1 at every Courant number,
+    while each one-dimensional operator, and hence their product (the split
+    scheme), stays within 1.  This is why 2D flows use the split scheme."""
+    th = np.linspace(-np.pi, np.pi, 201)
+    TX, TY = np.meshgrid(th, th)
+
+    def inc(nu, t):
+        return -nu * ((1 - np.exp(-1j * t)) + 0.5 * (1 - nu) * (np.exp(1j * t) - 2 + np.exp(-1j * t)))
+
+    for nu in (0.5, 0.2, 0.05):
+        unsplit = np.abs(1 + inc(nu, TX) + inc(nu, TY)).max()
+        split = np.abs((1 + inc(nu, TX)) * (1 + inc(nu, TY))).max()
+        assert unsplit > 1.0 + 1e-4 and split <= 1.0 + 1e-12
+
+
+def test_split_equals_printed_update_for_x_uniform_flows():
+    """For fields that do not vary in x (every flow the paper computes) the
+    split and the printed update agree to rounding."""
+    prob = Problem(name="t", nroots=4, nx=3, ny=20, bc_y=DIFFUSE, kn=0.1, b=-0.5,
+                   wall_ux=(-0.05, 0.05), wall_T=(0.97, 1.03), g=(1e-3, 0.0))
+    from paper_1209_6548_gb300.inputs import random_fields
+    fields = random_fields(prob, seed=8)
+    fields[:] = fields[:, :, :1]
+    dt = time_step(prob, fields)
+    pu = oracle_params(prob, dt)
+    ps = oracle_params(prob, dt)
+    ps.scheme = O.SPLIT
+    f = O.init(pu, fields)
+    a, b = O.run(pu, f, 10), O.run(ps, f, 10)
+    assert np.max(np.abs(a - b)) < 1e-15
+
+
+def test_split_is_y_sweep_then_x_sweep():
+    """Collision-free (Kn huge): one split step equals the pinned 1D TVD
+    operator applied along y to f^n, then along x to the result."""
+    n = 12
+    prob = Problem(name="t", nroots=4, nx=n, ny=n, bc_y=PERIODIC, kn=1e30, b=0.0, scheme=1)
+    dt = 0.4 / n / 2.3344142183389773
+    p = oracle_params(prob, dt)
+    cx, cy, w = O.velocity_set(4)
+    rng = np.random.default_rng(9)
+    f = w[:, None, None] * (1 + 0.1 * rng.random((16, n, n)))
+    got = O.step(p, f)
+    for a in range(16):
+        nuy, nux = abs(cy[a]) * dt * n, abs(cx[a]) * dt * n
+        fs = np.empty((n, n))
+        for i in range(n):
+            fs[:, i] = f[a, :, i] - np.sign(cy[a]) * nuy * O.advect_1d(cy[a], nuy, f[a, :, i])
+        ref = np.empty((n, n))
+        for j in range(n):
+            ref[j] = fs[j] - np.sign(cx[a]) * nux * O.advect_1d(cx[a], nux, fs[j])
+        assert np.max(np.abs(got[a] - ref)) < 1e-15
+
+
+def test_taylor_green_stable_only_split():
+    """The 2D Taylor-Green vortex grows without bound under the printed unsplit
+    update and stays bounded (and conservative) under the split scheme."""
+    from paper_1209_6548_gb300 import inputs as I
+    prob = I.tgv(48)
+    fields = I.initial_fields(prob)
+    dt = time_step(prob, fields)
+    ps = oracle_params(prob, dt)
+    pu = oracle_params(prob, dt)
+    pu.scheme = O.UNSPLIT
+    f = O.init(ps, fields)
+    _, s0 = O.moments(ps, f)
+    fs = O.run(ps, f, 400)
+    fu = O.run(pu, f, 400)
+    ms, s1 = O.moments(ps, fs)
+    assert np.abs(ms[1]).max() < 0.05 and np.allclose(s1, s0, atol=1e-11)
+    with np.errstate(invalid="ignore"):
+        mu, _ = O.moments(pu, fu)
+        assert not np.all(np.isfinite(mu)) or np.abs(mu[1]).max() > 0.1
