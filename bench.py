@@ -144,7 +144,7 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline(n: int, rows: int = 128, steps: int = 8):
+def cpu_baseline(n: int, rows: int = 1024, steps: int = 48):
     """The FP64 oracle, as it stands, on a bounded sample of the workload: the
     first `rows` rows of the n x n Taylor-Green initial state, periodic, for
     `steps` time steps, on all host cores the process may use."""
@@ -159,7 +159,7 @@ def cpu_baseline(n: int, rows: int = 128, steps: int = 8):
     c, _ = O.gauss_hermite_1d(4)
     dt = 0.5 * dx / float(np.abs(c).max())
     op = O.make_params(nroots=4, order=3, nx=n, ny=rows, bc_y=0, kn=prob.kn, b=prob.b,
-                       visc_exp=prob.visc_exp, dt=dt, dx=dx, dy=dy)
+                       visc_exp=prob.visc_exp, dt=dt, dx=dx, dy=dy, scheme=prob.scheme)
     f = O.init(op, fields)
     t0 = time.perf_counter()
     O.run(op, f, steps)
@@ -236,6 +236,8 @@ def main():
     d_mom = torch.empty((9, n, n), dtype=torch.float32, device="cuda")
     cells = n * n
     launches_per_step = 1 + nsteps + 2
+    info = solver.info
+    shape = (info.cells_per_thread, info.rows_per_segment)
 
     def one_solve(ev=None):
         solver.reinit(d_fields)
@@ -313,7 +315,7 @@ def main():
                        "parallelism": f"replica x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                         "kernel": "k_step<4,3,2>", "kernel_ms": kernel_ms,
+                         "kernel": f"k_step<4,3,{shape[0]},split> rows={shape[1]}", "kernel_ms": kernel_ms,
                          "bytes_per_lup": BYTES_PER_LUP, "source_sha256": digest},
             "cpu_baseline": base,
             "e2e": e2e,

@@ -343,46 +343,57 @@ __global__ void __launch_bounds__(kBlock) k_step(const float *__restrict__ fin, 
   const int y1 = min(y0 + A.rows, ny);
   const long long plane = A.plane;
 
-  auto load = [&](int a, int j, float (&v)[CPT]) {
-    const int r = map_row(j, ny, A.walls);
-    ld_cells<CPT>(fin + a * plane + (long long)r * nx + xw, v);
-  };
+  // Row addressing: the physical row of a stencil row (periodic wrap, or the
+  // wall node for ghost rows) is resolved once per row, never per population.
+  const float *fx = fin + xw;
+  auto row_ptr = [&](int j) { return fx + (long long)map_row(j, ny, A.walls) * nx; };
 
   // y-stencil state per population and node:
   //   c_y > 0: s0 = f_j - f_{j-1}, s1 = sigma_{j-1}; fc = f_j
   //   c_y < 0: s0 = f_{j+1},       s1 = sigma_j;     fc = f_j
   float fc[Q][CPT], s0[Q][CPT], s1[Q][CPT];
+  {
+    const float *pm2 = row_ptr(y0 - 2), *pm1 = row_ptr(y0 - 1), *pz = row_ptr(y0), *pp1 = row_ptr(y0 + 1);
 #pragma unroll
-  for (int a = 0; a < Q; ++a) {
-    const int iy = a % NR;
-    float m1[CPT], z0[CPT], p1[CPT];
-    load(a, y0 - 1, m1);
-    load(a, y0, z0);
-    if (iy >= H) {
-      float m2[CPT];
-      load(a, y0 - 2, m2);
+    for (int a = 0; a < Q; ++a) {
+      const int iy = a % NR;
+      const long long off = a * plane;
+      float m1[CPT], z0[CPT], p1[CPT];
+      ld_cells<CPT>(pm1 + off, m1);
+      ld_cells<CPT>(pz + off, z0);
+      if (iy >= H) {
+        float m2[CPT];
+        ld_cells<CPT>(pm2 + off, m2);
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) {
-        fc[a][c] = z0[c];
-        s0[a][c] = z0[c] - m1[c];
-        s1[a][c] = minmod(m1[c] - m2[c], z0[c] - m1[c]);
-      }
-    } else {
-      load(a, y0 + 1, p1);
+        for (int c = 0; c < CPT; ++c) {
+          fc[a][c] = z0[c];
+          s0[a][c] = z0[c] - m1[c];
+          s1[a][c] = minmod(m1[c] - m2[c], z0[c] - m1[c]);
+        }
+      } else {
+        ld_cells<CPT>(pp1 + off, p1);
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) {
-        fc[a][c] = z0[c];
-        s0[a][c] = p1[c];
-        s1[a][c] = minmod(z0[c] - m1[c], p1[c] - z0[c]);
+        for (int c = 0; c < CPT; ++c) {
+          fc[a][c] = z0[c];
+          s0[a][c] = p1[c];
+          s1[a][c] = minmod(z0[c] - m1[c], p1[c] - z0[c]);
+        }
       }
     }
   }
+  // physical rows of j+1 and j+2, advanced by one each row
+  int r1 = map_row(y0 + 1, ny, A.walls), r2 = map_row(y0 + 2, ny, A.walls);
 
   for (int j = y0; j < y1; ++j) {
     // rows this step consumes: f_{j+1} for c_y > 0, f_{j+2} for c_y < 0
     float ld[Q][CPT];
+    {
+      const float *q1 = fx + (long long)r1 * nx, *q2 = fx + (long long)r2 * nx;
 #pragma unroll
-    for (int a = 0; a < Q; ++a) load(a, (a % NR >= H) ? j + 1 : j + 2, ld[a]);
+      for (int a = 0; a < Q; ++a) ld_cells<CPT>(((a % NR >= H) ? q1 : q2) + a * plane, ld[a]);
+      r1 = r2;
+      r2 = r2 + 1 < ny ? r2 + 1 : (A.walls ? ny - 1 : 0);
+    }
 
     float acc[Q][CPT];
     float omw[CPT];
@@ -472,8 +483,9 @@ __global__ void __launch_bounds__(kBlock) k_step(const float *__restrict__ fin, 
     }
 
     if (writer) {
+      float *o = fout + (long long)j * nx + xw;
 #pragma unroll
-      for (int a = 0; a < Q; ++a) st_cells<CPT>(fout + a * plane + (long long)j * nx + xw, acc[a]);
+      for (int a = 0; a < Q; ++a) st_cells<CPT>(o + a * plane, acc[a]);
     }
   }
 }
@@ -675,18 +687,13 @@ namespace {
 
 int pick_launch(lesbgk *h) {
   const int nx = h->p.nx, ny = h->p.ny;
-  if (h->cpt <= 0) h->cpt = (nx % 2 == 0 && h->nr == 4) ? 2 : 1;
+  // default shape (measured on the 4096^2 periodic case): one node per lane,
+  // 32-row segments; short columns get one segment per warp
+  if (h->cpt <= 0) h->cpt = 1;
   const int hl = h->cpt >= 2 ? 1 : 2;
   const int U = (32 - 2 * hl) * h->cpt;
   const int nstrips = (nx + U - 1) / U;
-  if (h->rows <= 0) {
-    // enough warps for ~4 waves of 8 warps per SM, segments of 16..256 rows
-    const long long target = (long long)h->sm_count * 8 * 4;
-    long long r = ((long long)nstrips * ny + target - 1) / target;
-    int rows = 16;
-    while (rows < r && rows < 256) rows *= 2;
-    h->rows = rows;
-  }
+  if (h->rows <= 0) h->rows = ny < 32 ? ny : 32;
   h->args.rows = h->rows;
   h->args.nstrips = nstrips;
   h->args.nseg = (ny + h->rows - 1) / h->rows;

@@ -56,10 +56,12 @@ def oracle_params(p: Problem, dt: float, nx=None, ny=None, bc_y=None):
 GROUPS = {"rho": ("rho",), "T": ("T",), "u": ("ux", "uy"), "sigma": ("sxx", "sxy", "syy"),
           "q": ("qx", "qy")}
 # Quantities whose magnitude is below FLOOR are compared in absolute terms at
-# tol * FLOOR: FP32 deviation storage resolves the second and third moments to
-# about 1e-9 absolute, so a stress or heat flux of 1e-4 (three steps after an
-# equilibrium start) cannot be held to 1e-5 of itself.
-FLOOR = {"rho": 0.0, "T": 0.0, "u": 1e-3, "sigma": 1e-3, "q": 1e-3}
+# tol * FLOOR.  FP32 deviation storage resolves a moment sum_a df_a phi(c_a) to
+# about eps32 * sum_a |phi(c_a)| |df_a|: ~1e-9 for the second moments and
+# ~1e-8 for the heat flux, whose weights |c|^3 reach 12.7 on D2Q16.  A stress
+# or heat flux of 1e-4 (a few steps after an equilibrium start) therefore
+# cannot be held to 1e-5 of itself.
+FLOOR = {"rho": 0.0, "T": 0.0, "u": 1e-3, "sigma": 1e-3, "q": 3e-3}
 
 
 def field_errors(gpu: np.ndarray, ref: np.ndarray, rest=None):
