@@ -3,12 +3,13 @@
 // arXiv 1209.6548 (Sec. 2.2 lattice ES-BGK equation, Sec. 3.1 scheme,
 // Sec. 3.2 diffuse walls).
 //
-// Data layout in HBM: populations as deviations df_a = f_a - w_a, float32,
-// [a][j][i] (a = ix*NR + iy), two ping-pong buffers in the caller's
-// workspace.  One time step = one launch of k_step.
+// Data layout in HBM: populations as deviations df_a = f_a - w_a, float32, in
+// the grouped layout of Layout<NR> below (vectors of 4 (D2Q16) or 2 (D2Q36)
+// populations of one node that share the sign of c_y), two ping-pong buffers
+// in the caller's workspace.  One time step = one launch of k_step.
 //
-// k_step mapping: a warp owns a strip of 32*CPT consecutive x-nodes (the
-// outer HL lanes on each side are halo lanes that load but do not store) and
+// k_step mapping: a warp owns a strip of 32 consecutive x-nodes (the two
+// outer lanes on each side are halo lanes that load but do not store) and
 // marches up a segment of rows.  x-neighbours come from warp shuffles, the
 // y-stencil is carried in registers from row to row, so each population is
 // read from HBM once and written once per step (plus halo strips/rows that
@@ -73,6 +74,20 @@ __device__ __forceinline__ float minmod(float a, float b) {
   // signed smaller magnitude when a and b agree in sign, else 0 (= median(a, b, 0));
   // equals [f_{i+1}-f_i] Psi(Theta) of Sec. 3.1 with the minmod limiter.
   return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.0f));
+}
+
+// Hardware approximations (MUFU): relative error ~1 ulp, far below the FP32
+// rounding of the moments they act on.
+__device__ __forceinline__ float fast_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ float fast_sqrt(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
 
 __device__ __forceinline__ int map_row(int j, int ny, int walls) {
@@ -226,7 +241,7 @@ __device__ __forceinline__ void collide(const float (&F)[NR * NR], float (&S)[NR
   float a[KM + 1][KM + 1];
   hermite_moments<NR, KM>(F, a, A);
   const float rho = 1.0f + a[0][0];
-  const float ir = __frcp_rn(rho);
+  const float ir = fast_rcp(rho);
   const float ux = a[1][0] * ir, uy = a[0][1] * ir;
   // M = P - rho I (pressure tensor minus its rest value), from deviations
   const float Mxx = fmaf(-a[1][0], ux, a[2][0]);
@@ -235,7 +250,7 @@ __device__ __forceinline__ void collide(const float (&F)[NR * NR], float (&S)[NR
   const float trM = Mxx + Myy;
   const float T = fmaf(0.5f * trM, ir, 1.0f);  // T = tr P / (D rho), D = 2
   float Tp;
-  if (A.vmode == 1) Tp = sqrtf(T);
+  if (A.vmode == 1) Tp = fast_sqrt(T);
   else if (A.vmode == 2) Tp = 1.0f;
   else Tp = exp2f(A.visc_pow * __log2f(T));
   const float om = A.c_omega * rho * Tp;  // dt/tau, tau = (Kn/Pr) T^varpi / (rho T)
@@ -292,151 +307,201 @@ __device__ __forceinline__ void wall_fix(float (&O)[NR * NR], int side, const KA
     }
 }
 
-template <int CPT>
+// ---------------------------------------------------------------------------
+// Internal population layout in HBM ("grouped").  The Q populations of a node
+// are put in slot order: first the Q/2 with c_y < 0, then the Q/2 with
+// c_y > 0, each half in (ix, iy) order.  Consecutive slots form groups of V
+// (4 for D2Q16, 2 for D2Q36), and a group is stored as one V-vector per node:
+//   f[((g * ny + j) * nx + i) * V + k]  holds population alpha(g*V + k).
+// All populations of a group share the sign of c_y, so one vector load serves
+// one stencil row; a node's populations move as Q/V vector loads and stores.
+// ---------------------------------------------------------------------------
+template <int NR>
+struct Layout {
+  static constexpr int Q = NR * NR;
+  static constexpr int H = NR / 2;
+  static constexpr int HALF = Q / 2;
+  static constexpr int V = (HALF % 4 == 0) ? 4 : 2;
+  static constexpr int G = Q / V;
+  __host__ __device__ static constexpr int alpha(int s) {
+    return (s % HALF) / H * NR + ((s / HALF) ? H : 0) + (s % HALF) % H;
+  }
+};
+
+template <int V>
 struct VecT;
 template <>
-struct VecT<1> { using T = float; };
-template <>
 struct VecT<2> { using T = float2; };
+template <>
+struct VecT<4> { using T = float4; };
 
-template <int CPT>
-__device__ __forceinline__ void ld_cells(const float *p, float (&v)[CPT]) {
-  if constexpr (CPT == 1) {
-    v[0] = __ldg(p);
+// Load group g of one node (p points at the node's row, group 0) into F[alpha].
+template <int NR>
+__device__ __forceinline__ void ld_group(const float *p, long long gstride, int g, float (&F)[NR * NR]) {
+  using L = Layout<NR>;
+  using T = typename VecT<L::V>::T;
+  const T v = __ldg(reinterpret_cast<const T *>(p + g * gstride));
+  const float *e = reinterpret_cast<const float *>(&v);
+#pragma unroll
+  for (int k = 0; k < L::V; ++k) F[L::alpha(g * L::V + k)] = e[k];
+}
+
+template <int NR>
+__device__ __forceinline__ void st_group(float *p, long long gstride, int g, const float (&F)[NR * NR]) {
+  using L = Layout<NR>;
+  using T = typename VecT<L::V>::T;
+  T v;
+  float *e = reinterpret_cast<float *>(&v);
+#pragma unroll
+  for (int k = 0; k < L::V; ++k) e[k] = F[L::alpha(g * L::V + k)];
+  *reinterpret_cast<T *>(p + g * gstride) = v;
+}
+
+// Asynchronous global->shared copy of one V-vector (cp.async; 16-byte copies
+// bypass L1).
+template <int V>
+__device__ __forceinline__ void cp_async_vec(void *smem_dst, const float *gsrc) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  if constexpr (V == 4) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
   } else {
-    const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
-    v[0] = t.x;
-    v[1] = t.y;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
   }
 }
 
-template <int CPT>
-__device__ __forceinline__ void st_cells(float *p, const float (&v)[CPT]) {
-  if constexpr (CPT == 1) {
-    *p = v[0];
-  } else {
-    *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
-  }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
 }
 
 // ---------------------------------------------------------------------------
 // The fused time step (Sec. 3.1 + Sec. 3.2).
 // ---------------------------------------------------------------------------
-template <int NR, int N, int CPT, bool SPLIT>
+template <int NR, int N, bool SPLIT, int RING>
 __global__ void __launch_bounds__(kBlock) k_step(const float *__restrict__ fin, float *__restrict__ fout,
                                                  const KArgs A) {
-  constexpr int Q = NR * NR;
-  constexpr int H = NR / 2;
-  constexpr int HL = (CPT >= 2) ? 1 : 2;  // halo lanes per side
-  constexpr int U = (32 - 2 * HL) * CPT;  // nodes a strip updates
+  using Lay = Layout<NR>;
+  constexpr int Q = Lay::Q, H = Lay::H, V = Lay::V, G = Lay::G;
+  constexpr int HL = 2;           // halo lanes per side
+  constexpr int U = 32 - 2 * HL;  // nodes a strip updates
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int strip = warp % A.nstrips;
   const int seg = warp / A.nstrips;
   if (seg >= A.nseg) return;  // uniform over the warp
   const int nx = A.nx, ny = A.ny;
-  const int xl = strip * U - HL * CPT + lane * CPT;  // first node of this lane, unwrapped
+  const int xl = strip * U - HL + lane;  // this lane's node, unwrapped
   int xw = xl % nx;
   if (xw < 0) xw += nx;
   const bool writer = lane >= HL && lane < 32 - HL && xl < nx;
   const int y0 = seg * A.rows;
   const int y1 = min(y0 + A.rows, ny);
-  const long long plane = A.plane;
+  const long long gstride = (long long)V * A.plane;  // floats per group plane
+  const long long rstride = (long long)V * nx;       // floats per row
+  const float *fx = fin + (long long)xw * V;
+  // Rows are resolved once per row (periodic wrap, or the wall node for ghost
+  // rows), never per population.
+  auto row_ptr = [&](int j) { return fx + map_row(j, ny, A.walls) * rstride; };
 
-  // Row addressing: the physical row of a stencil row (periodic wrap, or the
-  // wall node for ghost rows) is resolved once per row, never per population.
-  const float *fx = fin + xw;
-  auto row_ptr = [&](int j) { return fx + (long long)map_row(j, ny, A.walls) * nx; };
-
-  // y-stencil state per population and node:
+  // y-stencil state per population:
   //   c_y > 0: s0 = f_j - f_{j-1}, s1 = sigma_{j-1}; fc = f_j
   //   c_y < 0: s0 = f_{j+1},       s1 = sigma_j;     fc = f_j
-  float fc[Q][CPT], s0[Q][CPT], s1[Q][CPT];
+  float fc[Q], s0[Q], s1[Q];
   {
+    float m2[Q], m1[Q], p1[Q];
     const float *pm2 = row_ptr(y0 - 2), *pm1 = row_ptr(y0 - 1), *pz = row_ptr(y0), *pp1 = row_ptr(y0 + 1);
 #pragma unroll
+    for (int g = 0; g < G; ++g) {
+      ld_group<NR>(pm1, gstride, g, m1);
+      ld_group<NR>(pz, gstride, g, fc);
+      if (g >= G / 2) ld_group<NR>(pm2, gstride, g, m2);
+      else ld_group<NR>(pp1, gstride, g, p1);
+    }
+#pragma unroll
     for (int a = 0; a < Q; ++a) {
-      const int iy = a % NR;
-      const long long off = a * plane;
-      float m1[CPT], z0[CPT], p1[CPT];
-      ld_cells<CPT>(pm1 + off, m1);
-      ld_cells<CPT>(pz + off, z0);
-      if (iy >= H) {
-        float m2[CPT];
-        ld_cells<CPT>(pm2 + off, m2);
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-          fc[a][c] = z0[c];
-          s0[a][c] = z0[c] - m1[c];
-          s1[a][c] = minmod(m1[c] - m2[c], z0[c] - m1[c]);
-        }
+      if (a % NR >= H) {
+        s0[a] = fc[a] - m1[a];
+        s1[a] = minmod(m1[a] - m2[a], fc[a] - m1[a]);
       } else {
-        ld_cells<CPT>(pp1 + off, p1);
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-          fc[a][c] = z0[c];
-          s0[a][c] = p1[c];
-          s1[a][c] = minmod(z0[c] - m1[c], p1[c] - z0[c]);
-        }
+        s0[a] = p1[a];
+        s1[a] = minmod(fc[a] - m1[a], p1[a] - fc[a]);
       }
     }
   }
-  // physical rows of j+1 and j+2, advanced by one each row
+  // Look-ahead rows go through a per-lane ring of RING row slots in shared
+  // memory, filled by asynchronous copies (cp.async, one vector per group):
+  // RING-1 rows are in flight while a row is processed, without holding
+  // registers.  Each lane copies and reads only its own node's vectors, so the
+  // ring needs no barrier; cp.async.wait_group paces it.  "Row-load k" holds
+  // what row y0+k consumes: f_{j+1} for c_y > 0 groups, f_{j+2} for c_y < 0.
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using T = typename VecT<V>::T;
+  T *ring = reinterpret_cast<T *>(smem_raw) + (size_t)(threadIdx.x >> 5) * RING * G * 32 + lane;
   int r1 = map_row(y0 + 1, ny, A.walls), r2 = map_row(y0 + 2, ny, A.walls);
-
-  for (int j = y0; j < y1; ++j) {
-    // rows this step consumes: f_{j+1} for c_y > 0, f_{j+2} for c_y < 0
-    float ld[Q][CPT];
-    {
-      const float *q1 = fx + (long long)r1 * nx, *q2 = fx + (long long)r2 * nx;
+  const int nrows = y1 - y0;
+  auto issue_rowload = [&](int k) {
+    if (k < nrows) {
+      const float *q1 = fx + r1 * rstride, *q2 = fx + r2 * rstride;
+      T *slot = ring + (k % RING) * G * 32;
 #pragma unroll
-      for (int a = 0; a < Q; ++a) ld_cells<CPT>(((a % NR >= H) ? q1 : q2) + a * plane, ld[a]);
+      for (int g = 0; g < G; ++g) cp_async_vec<V>(slot + g * 32, (g >= G / 2 ? q1 : q2) + g * gstride);
       r1 = r2;
       r2 = r2 + 1 < ny ? r2 + 1 : (A.walls ? ny - 1 : 0);
     }
+    cp_async_commit();  // (an empty group past the segment end keeps the count uniform)
+  };
+#pragma unroll
+  for (int k = 0; k < RING - 1; ++k) issue_rowload(k);
 
-    float acc[Q][CPT];
-    float omw[CPT];
+  for (int j = y0; j < y1; ++j) {
+    const int k = j - y0;
+    issue_rowload(k + RING - 1);
+    cp_async_wait<RING - 1>();  // row-load k has landed
+    float ld[Q];
+    {
+      const T *slot = ring + (k % RING) * G * 32;
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-      float F[Q], S[Q];
+      for (int g = 0; g < G; ++g) {
+        const T v = slot[g * 32];
+        const float *e = reinterpret_cast<const float *>(&v);
 #pragma unroll
-      for (int a = 0; a < Q; ++a) F[a] = fc[a][c];
-      collide<NR, N>(F, S, omw[c], A);
-#pragma unroll
-      for (int a = 0; a < Q; ++a) acc[a][c] = S[a];
+        for (int q = 0; q < V; ++q) ld[Lay::alpha(g * V + q)] = e[q];
+      }
     }
+
+    float acc[Q];
+    float omw;
+    collide<NR, N>(fc, acc, omw, A);
 
     // y-advection from the carried stencil of f^n; xs = the values the
     // x-fluxes are taken from: f^n_j (update as printed) or the y-swept
     // f*_j = f^n_j - (c_y dt/dy) dF_y (split scheme).
-    float xs[Q][CPT];
+    float xs[Q];
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
       const int iy = a % NR;
       const float ay = A.ay[iy], ky = A.ky[iy];
-#pragma unroll
-      for (int c = 0; c < CPT; ++c) {
-        float diff;
-        const float f0 = fc[a][c];
-        if (iy >= H) {  // c_y > 0: F_{j+1/2} = f_j + k sigma_j
-          const float dn = ld[a][c] - f0;
-          const float sg = minmod(s0[a][c], dn);
-          diff = fmaf(ky, sg - s1[a][c], s0[a][c]);
-          s0[a][c] = dn;
-          s1[a][c] = sg;
-          fc[a][c] = ld[a][c];
-        } else {  // c_y < 0: F_{j+1/2} = f_{j+1} - k sigma_{j+1}
-          const float d1 = s0[a][c] - f0;
-          const float sg = minmod(d1, ld[a][c] - s0[a][c]);
-          diff = fmaf(-ky, sg - s1[a][c], d1);
-          s1[a][c] = sg;
-          fc[a][c] = s0[a][c];
-          s0[a][c] = ld[a][c];
-        }
-        acc[a][c] = fmaf(omw[c], f0, fmaf(-ay, diff, acc[a][c]));
-        xs[a][c] = SPLIT ? fmaf(-ay, diff, f0) : f0;
+      float diff;
+      const float f0 = fc[a];
+      if (iy >= H) {  // c_y > 0: F_{j+1/2} = f_j + k sigma_j
+        const float dn = ld[a] - f0;
+        const float sg = minmod(s0[a], dn);
+        diff = fmaf(ky, sg - s1[a], s0[a]);
+        s0[a] = dn;
+        s1[a] = sg;
+        fc[a] = ld[a];
+      } else {  // c_y < 0: F_{j+1/2} = f_{j+1} - k sigma_{j+1}
+        const float d1 = s0[a] - f0;
+        const float sg = minmod(d1, ld[a] - s0[a]);
+        diff = fmaf(-ky, sg - s1[a], d1);
+        s1[a] = sg;
+        fc[a] = s0[a];
+        s0[a] = ld[a];
       }
+      acc[a] = fmaf(omw, f0, fmaf(-ay, diff, acc[a]));
+      xs[a] = SPLIT ? fmaf(-ay, diff, f0) : f0;
     }
 
     // x-advection: neighbours from adjacent lanes
@@ -444,50 +509,30 @@ __global__ void __launch_bounds__(kBlock) k_step(const float *__restrict__ fin, 
     for (int a = 0; a < Q; ++a) {
       const int ix = a / NR;
       const float ax = A.ax[ix], kx = A.kx[ix];
-      float d[CPT + 1], sg[CPT];
-      const float left = __shfl_up_sync(kFull, xs[a][CPT - 1], 1);
-      d[0] = xs[a][0] - left;
-#pragma unroll
-      for (int c = 1; c < CPT; ++c) d[c] = xs[a][c] - xs[a][c - 1];
-      d[CPT] = __shfl_down_sync(kFull, d[0], 1);
-#pragma unroll
-      for (int c = 0; c < CPT; ++c) sg[c] = minmod(d[c], d[c + 1]);
+      const float left = __shfl_up_sync(kFull, xs[a], 1);
+      const float dl = xs[a] - left;                       // f_i - f_{i-1}
+      const float dr = __shfl_down_sync(kFull, dl, 1);     // f_{i+1} - f_i
+      const float sg = minmod(dl, dr);                     // sigma_i
+      float diff;
       if (ix >= H) {  // c_x > 0: F_{i+1/2} = f_i + k sigma_i
-        const float sprev = __shfl_up_sync(kFull, sg[CPT - 1], 1);
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-          const float diff = fmaf(kx, sg[c] - (c == 0 ? sprev : sg[c - 1]), d[c]);
-          acc[a][c] = fmaf(-ax, diff, acc[a][c]);
-        }
+        const float sprev = __shfl_up_sync(kFull, sg, 1);
+        diff = fmaf(kx, sg - sprev, dl);
       } else {  // c_x < 0: F_{i+1/2} = f_{i+1} - k sigma_{i+1}
-        const float snext = __shfl_down_sync(kFull, sg[0], 1);
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-          const float diff = fmaf(-kx, (c == CPT - 1 ? snext : sg[c + 1]) - sg[c], d[c + 1]);
-          acc[a][c] = fmaf(-ax, diff, acc[a][c]);
-        }
+        const float snext = __shfl_down_sync(kFull, sg, 1);
+        diff = fmaf(-kx, snext - sg, dr);
       }
+      acc[a] = fmaf(-ax, diff, acc[a]);
     }
 
-    if (A.walls && (j == 0 || j == ny - 1)) {
-      const int side = (j == 0) ? 0 : 1;
-#pragma unroll
-      for (int c = 0; c < CPT; ++c) {
-        float O[Q];
-#pragma unroll
-        for (int a = 0; a < Q; ++a) O[a] = acc[a][c];
-        wall_fix<NR>(O, side, A);
-#pragma unroll
-        for (int a = 0; a < Q; ++a) acc[a][c] = O[a];
-      }
-    }
+    if (A.walls && (j == 0 || j == ny - 1)) wall_fix<NR>(acc, (j == 0) ? 0 : 1, A);
 
     if (writer) {
-      float *o = fout + (long long)j * nx + xw;
+      float *o = fout + (long long)j * rstride + (long long)xw * V;
 #pragma unroll
-      for (int a = 0; a < Q; ++a) st_cells<CPT>(o + a * plane, acc[a]);
+      for (int g = 0; g < G; ++g) st_group<NR>(o, gstride, g, acc);
     }
   }
+  cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -498,8 +543,10 @@ __global__ void __launch_bounds__(kBlock) k_step(const float *__restrict__ fin, 
 template <int NR, int N>
 __global__ void __launch_bounds__(kBlock) k_init(const double *__restrict__ fields, float *__restrict__ f,
                                                  const KArgs A) {
-  constexpr int Q = NR * NR;
+  using Lay = Layout<NR>;
+  constexpr int Q = Lay::Q;
   const long long cells = A.plane;
+  const long long gstride = (long long)Lay::V * cells;
   for (long long c = blockIdx.x * (long long)kBlock + threadIdx.x; c < cells; c += (long long)gridDim.x * kBlock) {
     float drho = 0.f, ux = 0.f, uy = 0.f, dT = 0.f;
     if (fields) {
@@ -518,7 +565,36 @@ __global__ void __launch_bounds__(kBlock) k_init(const double *__restrict__ fiel
     const int j = (int)(c / A.nx);
     if (A.walls && (j == 0 || j == A.ny - 1)) wall_fix<NR>(S, j == 0 ? 0 : 1, A);
 #pragma unroll
-    for (int a = 0; a < Q; ++a) f[a * cells + c] = S[a];
+    for (int g = 0; g < Lay::G; ++g) st_group<NR>(f + c * Lay::V, gstride, g, S);
+  }
+}
+
+// Populations between the grouped layout and the public [a][j][i] layout.
+template <int NR>
+__global__ void __launch_bounds__(kBlock) k_ungroup(const float *__restrict__ f, float *__restrict__ out,
+                                                    long long cells) {
+  using Lay = Layout<NR>;
+  const long long gstride = (long long)Lay::V * cells;
+  for (long long c = blockIdx.x * (long long)kBlock + threadIdx.x; c < cells; c += (long long)gridDim.x * kBlock) {
+    float F[Lay::Q];
+#pragma unroll
+    for (int g = 0; g < Lay::G; ++g) ld_group<NR>(f + c * Lay::V, gstride, g, F);
+#pragma unroll
+    for (int a = 0; a < Lay::Q; ++a) out[a * cells + c] = F[a];
+  }
+}
+
+template <int NR>
+__global__ void __launch_bounds__(kBlock) k_group(const float *__restrict__ in, float *__restrict__ f,
+                                                  long long cells) {
+  using Lay = Layout<NR>;
+  const long long gstride = (long long)Lay::V * cells;
+  for (long long c = blockIdx.x * (long long)kBlock + threadIdx.x; c < cells; c += (long long)gridDim.x * kBlock) {
+    float F[Lay::Q];
+#pragma unroll
+    for (int a = 0; a < Lay::Q; ++a) F[a] = __ldg(in + a * cells + c);
+#pragma unroll
+    for (int g = 0; g < Lay::G; ++g) st_group<NR>(f + c * Lay::V, gstride, g, F);
   }
 }
 
@@ -529,14 +605,16 @@ __global__ void __launch_bounds__(kBlock) k_init(const double *__restrict__ fiel
 template <int NR>
 __global__ void __launch_bounds__(kMomBlock) k_moments(const float *__restrict__ f, float *__restrict__ out,
                                                        double *__restrict__ partial, const KArgs A) {
-  constexpr int Q = NR * NR;
+  using Lay = Layout<NR>;
+  constexpr int Q = Lay::Q;
   const long long cells = A.plane;
+  const long long gstride = (long long)Lay::V * cells;
   double sm = 0.0, sx = 0.0, sy = 0.0, se = 0.0;
   for (long long c = blockIdx.x * (long long)kMomBlock + threadIdx.x; c < cells;
        c += (long long)gridDim.x * kMomBlock) {
     float F[Q];
 #pragma unroll
-    for (int a = 0; a < Q; ++a) F[a] = __ldg(f + a * cells + c);
+    for (int g = 0; g < Lay::G; ++g) ld_group<NR>(f + c * Lay::V, gstride, g, F);
     float m[4][4];
     hermite_moments<NR, 3>(F, m, A);
     const float rho = 1.0f + m[0][0];
@@ -687,12 +765,10 @@ namespace {
 
 int pick_launch(lesbgk *h) {
   const int nx = h->p.nx, ny = h->p.ny;
-  // default shape (measured on the 4096^2 periodic case): one node per lane,
-  // 32-row segments; short columns get one segment per warp
-  if (h->cpt <= 0) h->cpt = 1;
-  const int hl = h->cpt >= 2 ? 1 : 2;
-  const int U = (32 - 2 * hl) * h->cpt;
-  const int nstrips = (nx + U - 1) / U;
+  // one node per lane, 28 nodes per strip (two halo lanes per side); default
+  // 32-row segments (measured best on the 4096^2 periodic case)
+  h->cpt = 1;
+  const int nstrips = (nx + 27) / 28;
   if (h->rows <= 0) h->rows = ny < 32 ? ny : 32;
   h->args.rows = h->rows;
   h->args.nstrips = nstrips;
@@ -803,19 +879,38 @@ int build_tables(lesbgk *h, const double *h_init) {
   return 0;
 }
 
+constexpr int kRing = 4;
+
+template <int NR>
+constexpr size_t step_smem_bytes() {
+  return (size_t)(kBlock / 32) * kRing * Layout<NR>::G * 32 * Layout<NR>::V * sizeof(float);
+}
+
 template <int NR, int N>
 int launch_step_t(lesbgk *h, const float *fin, float *fout, cudaStream_t s) {
   const long long warps = (long long)h->args.nstrips * h->args.nseg;
   const unsigned grid = (unsigned)((warps * 32 + kBlock - 1) / kBlock);
-  const bool split = h->p.scheme == LESBGK_SPLIT;
-  if (h->cpt == 2) {
-    if (split) k_step<NR, N, 2, true><<<grid, kBlock, 0, s>>>(fin, fout, h->args);
-    else k_step<NR, N, 2, false><<<grid, kBlock, 0, s>>>(fin, fout, h->args);
-  } else {
-    if (split) k_step<NR, N, 1, true><<<grid, kBlock, 0, s>>>(fin, fout, h->args);
-    else k_step<NR, N, 1, false><<<grid, kBlock, 0, s>>>(fin, fout, h->args);
-  }
+  constexpr size_t smem = step_smem_bytes<NR>();
+  if (h->p.scheme == LESBGK_SPLIT) k_step<NR, N, true, kRing><<<grid, kBlock, smem, s>>>(fin, fout, h->args);
+  else k_step<NR, N, false, kRing><<<grid, kBlock, smem, s>>>(fin, fout, h->args);
   return 0;
+}
+
+// Opt in to more than 48 KiB of dynamic shared memory where a ring needs it.
+template <int NR, int N>
+cudaError_t allow_smem_t() {
+  constexpr int smem = (int)step_smem_bytes<NR>();
+  cudaError_t e = cudaFuncSetAttribute(k_step<NR, N, true, kRing>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_step<NR, N, false, kRing>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
+}
+
+cudaError_t allow_smem(const lesbgk *h) {
+  if (h->nr == 4 && h->order == 3) return allow_smem_t<4, 3>();
+  if (h->nr == 4 && h->order == 4) return allow_smem_t<4, 4>();
+  if (h->nr == 6 && h->order == 3) return allow_smem_t<6, 3>();
+  return allow_smem_t<6, 4>();
 }
 
 int launch_step(lesbgk *h, const float *fin, float *fout, cudaStream_t s) {
@@ -825,10 +920,15 @@ int launch_step(lesbgk *h, const float *fin, float *fout, cudaStream_t s) {
   return launch_step_t<6, 4>(h, fin, fout, s);
 }
 
+unsigned grid_for(const lesbgk *h, long long cells) {
+  long long g = (cells + kBlock - 1) / kBlock;
+  const long long cap = (long long)h->sm_count * 16;
+  if (g > cap) g = cap;
+  return g < 1 ? 1u : (unsigned)g;
+}
+
 int launch_init(lesbgk *h, const double *fields, float *f, cudaStream_t s) {
-  const long long cells = h->args.plane;
-  unsigned grid = (unsigned)std::min<long long>((cells + kBlock - 1) / kBlock, (long long)h->sm_count * 16);
-  if (grid == 0) grid = 1;
+  const unsigned grid = grid_for(h, h->args.plane);
   if (h->nr == 4 && h->order == 3) k_init<4, 3><<<grid, kBlock, 0, s>>>(fields, f, h->args);
   else if (h->nr == 4 && h->order == 4) k_init<4, 4><<<grid, kBlock, 0, s>>>(fields, f, h->args);
   else if (h->nr == 6 && h->order == 3) k_init<6, 3><<<grid, kBlock, 0, s>>>(fields, f, h->args);
@@ -883,6 +983,11 @@ extern "C" int lesbgk_create(const lesbgk_params *p, void *d_workspace, size_t b
     return rc;
   }
   pick_launch(h);
+  e = allow_smem(h);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "step kernel shared-memory opt-in");
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const double *dfields = nullptr;
   if (h_init) {
@@ -966,15 +1071,21 @@ extern "C" int lesbgk_moments_host(lesbgk *h, float *h_out, double *h_sums, void
 
 extern "C" int lesbgk_get_populations(lesbgk *h, float *d_out, void *stream) {
   if (!h || !d_out) return fail(LESBGK_EINVAL, "NULL argument");
-  cudaError_t e = cudaMemcpyAsync(d_out, h->buf[h->cur], (size_t)h->q * h->args.plane * sizeof(float),
-                                  cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long cells = h->args.plane;
+  if (h->nr == 4) k_ungroup<4><<<grid_for(h, cells), kBlock, 0, s>>>(h->buf[h->cur], d_out, cells);
+  else k_ungroup<6><<<grid_for(h, cells), kBlock, 0, s>>>(h->buf[h->cur], d_out, cells);
+  cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? 0 : cuda_fail(e, "get populations");
 }
 
 extern "C" int lesbgk_set_populations(lesbgk *h, const float *d_in, int64_t steps_done, void *stream) {
   if (!h || !d_in) return fail(LESBGK_EINVAL, "NULL argument");
-  cudaError_t e = cudaMemcpyAsync(h->buf[h->cur], d_in, (size_t)h->q * h->args.plane * sizeof(float),
-                                  cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long cells = h->args.plane;
+  if (h->nr == 4) k_group<4><<<grid_for(h, cells), kBlock, 0, s>>>(d_in, h->buf[h->cur], cells);
+  else k_group<6><<<grid_for(h, cells), kBlock, 0, s>>>(d_in, h->buf[h->cur], cells);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "set populations");
   h->steps = steps_done;
   return 0;
@@ -982,11 +1093,8 @@ extern "C" int lesbgk_set_populations(lesbgk *h, const float *d_in, int64_t step
 
 extern "C" int lesbgk_set_launch(lesbgk *h, int32_t cells_per_thread, int32_t rows_per_segment) {
   if (!h) return fail(LESBGK_EINVAL, "handle is NULL");
-  if (cells_per_thread < 0 || cells_per_thread > 2 || rows_per_segment < 0)
-    return fail(LESBGK_EINVAL, "bad launch shape");
-  if (cells_per_thread == 2 && (h->p.nx % 2 != 0 || h->nr != 4))
-    return fail(LESBGK_EINVAL, "two cells per thread need nx even and nroots = 4");
-  if (cells_per_thread) h->cpt = cells_per_thread;
+  if (cells_per_thread < 0 || cells_per_thread > 1 || rows_per_segment < 0)
+    return fail(LESBGK_EINVAL, "bad launch shape (cells_per_thread must be 0 or 1)");
   if (rows_per_segment) h->rows = rows_per_segment;
   return pick_launch(h);
 }
