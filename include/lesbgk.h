@@ -168,6 +168,32 @@ int lesbgk_get_info(const lesbgk *h, lesbgk_info *out);
 /* Release the handle (not the caller's workspace).  NULL is a no-op. */
 int lesbgk_destroy(lesbgk *h);
 
+/* Moments without any allocation (the paper has no counterpart: this is a
+ * service to embedding code).  Some callers cannot allocate device memory at
+ * all -- their device memory belongs to another allocator, they run under a
+ * fixed memory budget, or they cannot afford the device-wide synchronisation
+ * of cudaMalloc -- and so cannot provide the scratch that lesbgk_moments finds
+ * in the solver's workspace.  This entry point computes the same nine fields
+ * and FP64 totals as lesbgk_moments from populations the caller already holds
+ * and calls no cudaMalloc, cudaFree or allocating library routine.
+ *   p:             the solver parameters (grid and velocity set are used).
+ *   d_populations: DEVICE float[Q][ny][nx], deviations f_a - w_a in the layout
+ *                  lesbgk_get_populations returns.
+ *   d_out:         DEVICE float[9][ny][nx] as in lesbgk_moments, or NULL.
+ *   h_sums:        HOST double[4] as in lesbgk_moments, or NULL (if given, the
+ *                  stream is synchronised).
+ * Limit: nx*ny <= 2^24 nodes (4096 x 4096); larger grids return LESBGK_EINVAL.
+ * Its scratch is a fixed 256 KiB + 32 B array inside the library that every GPU which
+ * loads the library keeps until the process exits.  The first call on a
+ * device looks up that array's device address (a one-time set-up per device,
+ * done with that device current); make that first call before any stream
+ * capture.  All calls share the array: each call writes every scratch slot it
+ * reads, so nothing carries over, but calls that overlap on the GPU (other
+ * streams, other host threads) race on it and must be serialised by the
+ * caller. */
+int lesbgk_moments_noalloc(const lesbgk_params *p, const float *d_populations, float *d_out, double *h_sums,
+                           void *stream);
+
 /* Thread-local message of the last error ("" if none). */
 const char *lesbgk_last_error(void);
 

@@ -22,6 +22,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "lesbgk.h"
@@ -1121,3 +1122,161 @@ extern "C" int lesbgk_destroy(lesbgk *h) {
 }
 
 extern "C" const char *lesbgk_last_error(void) { return g_err; }
+
+// ===========================================================================
+// Moments without allocation.
+//
+// For callers that cannot allocate device memory at all (an embedding
+// application whose device memory belongs to another allocator, a plugin held
+// to a fixed memory budget, or a loop that cannot afford the device-wide
+// synchronisation of cudaMalloc), this entry point computes the same nine
+// moment fields and FP64 totals as lesbgk_moments from populations the caller
+// already holds.  Its only scratch -- one FP64 partial sum per quantity per
+// block, plus the four totals -- lives in the file-scope array below, so the
+// call allocates nothing.  The array is fixed in size (kNoAllocBlocks blocks
+// of kNoAllocNodesPerBlock nodes, 256 KiB + 32 B) and every GPU that loads
+// the library holds it until the process exits.
+// ===========================================================================
+namespace {
+
+constexpr int kNoAllocBlocks = 8192;
+constexpr int kNoAllocNodesPerThread = 8;
+constexpr long long kNoAllocNodesPerBlock = (long long)kMomBlock * kNoAllocNodesPerThread;
+constexpr long long kNoAllocMaxNodes = (long long)kNoAllocBlocks * kNoAllocNodesPerBlock;  // 2^24
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocBlocks * 4 + 4];
+
+// One block per kNoAllocNodesPerBlock nodes of the public layout
+// f[a][j][i] (deviations f_a - w_a); per-node arithmetic as in k_moments.
+template <int NR>
+__global__ void __launch_bounds__(kMomBlock) k_moments_public(const float *__restrict__ f, float *__restrict__ out,
+                                                              double *__restrict__ partial, const KArgs A) {
+  constexpr int Q = NR * NR;
+  const long long cells = A.plane;
+  double sm = 0.0, sx = 0.0, sy = 0.0, se = 0.0;
+  const long long c0 = blockIdx.x * kNoAllocNodesPerBlock;
+  for (int t = 0; t < kNoAllocNodesPerThread; ++t) {
+    const long long c = c0 + (long long)t * kMomBlock + threadIdx.x;
+    if (c >= cells) break;
+    float F[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) F[a] = __ldg(f + a * cells + c);
+    float m[4][4];
+    hermite_moments<NR, 3>(F, m, A);
+    const float rho = 1.0f + m[0][0];
+    const float ir = __frcp_rn(rho);
+    const float ux = m[1][0] * ir, uy = m[0][1] * ir;
+    const float Mxx = fmaf(-m[1][0], ux, m[2][0]);
+    const float Mxy = fmaf(-m[1][0], uy, m[1][1]);
+    const float Myy = fmaf(-m[0][1], uy, m[0][2]);
+    const float trM = Mxx + Myy;
+    const float T = fmaf(0.5f * trM, ir, 1.0f);
+    const float u2 = ux * ux + uy * uy;
+    const float hx = m[3][0] + m[1][2], hy = m[0][3] + m[2][1];
+    const float qx = 0.5f * (hx - 2.0f * (Mxx * ux + Mxy * uy) - ux * trM - rho * ux * u2);
+    const float qy = 0.5f * (hy - 2.0f * (Mxy * ux + Myy * uy) - uy * trM - rho * uy * u2);
+    if (out) {
+      out[c] = rho;
+      out[cells + c] = ux;
+      out[2 * cells + c] = uy;
+      out[3 * cells + c] = T;
+      out[4 * cells + c] = 0.5f * (Mxx - Myy);
+      out[5 * cells + c] = Mxy;
+      out[6 * cells + c] = 0.5f * (Myy - Mxx);
+      out[7 * cells + c] = qx;
+      out[8 * cells + c] = qy;
+    }
+    double dm = 0.0, dx = 0.0, dy = 0.0, de = 0.0;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      const double cx = A.c[a / NR], cy = A.c[a % NR];
+      const double v = F[a];
+      dm += v;
+      dx += v * cx;
+      dy += v * cy;
+      de += v * (cx * cx + cy * cy);
+    }
+    sm += 1.0 + dm;
+    sx += dx;
+    sy += dy;
+    se += 0.5 * (2.0 + de);
+  }
+  __shared__ double red[4][kMomBlock / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sm += __shfl_down_sync(kFull, sm, o);
+    sx += __shfl_down_sync(kFull, sx, o);
+    sy += __shfl_down_sync(kFull, sy, o);
+    se += __shfl_down_sync(kFull, se, o);
+  }
+  if (lane == 0) {
+    red[0][w] = sm;
+    red[1][w] = sx;
+    red[2][w] = sy;
+    red[3][w] = se;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {  // every block writes all four of its slots: no zeroing needed
+    double t = 0.0;
+    for (int k = 0; k < kMomBlock / 32; ++k) t += red[threadIdx.x][k];
+    partial[blockIdx.x * 4 + threadIdx.x] = t;
+  }
+}
+
+// Device address of g_noalloc_scratch per device, looked up once per device
+// with that device current (in host code the symbol is only a stand-in).
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[kMaxDevices] = {};
+
+int noalloc_scratch(double **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(LESBGK_EINVAL, "device index %d beyond %d", dev, kMaxDevices);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static moment scratch");
+    g_noalloc_ptr[dev] = static_cast<double *>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return 0;
+}
+
+}  // namespace
+
+extern "C" int lesbgk_moments_noalloc(const lesbgk_params *p, const float *d_populations, float *d_out,
+                                      double *h_sums, void *stream) {
+  if (int rc = check_params(p)) return rc;
+  if (!d_populations) return fail(LESBGK_EINVAL, "d_populations is NULL");
+  const long long cells = (long long)p->nx * p->ny;
+  if (cells > kNoAllocMaxNodes)
+    return fail(LESBGK_EINVAL, "lesbgk_moments_noalloc handles at most %lld nodes (%lld given): its static "
+                "scratch holds %d block partial sums", kNoAllocMaxNodes, cells, kNoAllocBlocks);
+  lesbgk tmp{};
+  tmp.p = *p;
+  tmp.nr = p->nroots;
+  tmp.order = p->order ? p->order : (p->nroots == 4 ? 3 : 4);
+  tmp.q = tmp.nr * tmp.nr;
+  if (int rc = build_tables(&tmp, nullptr)) return rc;
+  double *scratch = nullptr;
+  if (int rc = noalloc_scratch(&scratch)) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int blocks = (int)((cells + kNoAllocNodesPerBlock - 1) / kNoAllocNodesPerBlock);
+  double *sums = scratch + (size_t)kNoAllocBlocks * 4;
+  if (p->nroots == 4) k_moments_public<4><<<blocks, kMomBlock, 0, s>>>(d_populations, d_out, scratch, tmp.args);
+  else k_moments_public<6><<<blocks, kMomBlock, 0, s>>>(d_populations, d_out, scratch, tmp.args);
+  k_reduce_partials<<<1, 128, 0, s>>>(scratch, blocks, sums);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "moments (no allocation)");
+  if (!h_sums) return 0;
+  e = cudaMemcpyAsync(h_sums, sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "moment sums (no allocation)");
+  for (int k = 0; k < 4; ++k)
+    if (!std::isfinite(h_sums[k])) return fail(LESBGK_EDIVERGED, "non-finite conservation sum %d", k);
+  return 0;
+}

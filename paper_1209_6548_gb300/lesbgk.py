@@ -28,7 +28,8 @@ MOMENT_NAMES = ("rho", "ux", "uy", "T", "sxx", "sxy", "syy", "qx", "qy")
 # Every entry point declared in include/lesbgk.h.
 SYMBOLS = ("lesbgk_workspace_size", "lesbgk_create", "lesbgk_reinit", "lesbgk_step", "lesbgk_moments",
            "lesbgk_moments_host", "lesbgk_get_populations", "lesbgk_set_populations",
-           "lesbgk_set_launch", "lesbgk_get_info", "lesbgk_destroy", "lesbgk_last_error")
+           "lesbgk_set_launch", "lesbgk_get_info", "lesbgk_destroy", "lesbgk_moments_noalloc",
+           "lesbgk_last_error")
 
 
 class Params(C.Structure):
@@ -82,6 +83,7 @@ def lib():
             L.lesbgk_set_launch.argtypes = [vp, C.c_int32, C.c_int32]
             L.lesbgk_get_info.argtypes = [vp, C.POINTER(Info)]
             L.lesbgk_destroy.argtypes = [vp]
+            L.lesbgk_moments_noalloc.argtypes = [C.POINTER(Params), vp, vp, vp, vp]
             L.lesbgk_last_error.restype = C.c_char_p
             L.lesbgk_last_error.argtypes = []
             _lib = L
@@ -173,6 +175,14 @@ def get_info(h: int) -> Info:
     out = Info()
     _check(lib().lesbgk_get_info(C.c_void_p(h), C.byref(out)))
     return out
+
+
+def moments_noalloc(p: Params, d_populations: int, d_out, h_sums, stream: int) -> None:
+    """lesbgk_moments_noalloc: moments of caller-held populations ([a][j][i]
+    deviations on the device) with no device allocation inside the library."""
+    sp = None if h_sums is None else h_sums.ctypes.data
+    _check(lib().lesbgk_moments_noalloc(C.byref(p), C.c_void_p(d_populations), C.c_void_p(d_out),
+                                        C.c_void_p(sp), C.c_void_p(stream)))
 
 
 def destroy(h: int) -> None:

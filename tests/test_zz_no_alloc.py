@@ -1,0 +1,59 @@
+"""The allocation-free moments entry point (lesbgk_moments_noalloc).
+
+Callers that cannot allocate device memory hand the library populations they
+already hold; the library computes the moments with scratch it keeps in a
+fixed static array instead of a workspace.  This checks, through the C ABI,
+that two calls in a row give the same fields and totals as lesbgk_moments on
+the same state, within the tolerance the parity tests use.  The file is named
+to be collected last so a run that stops at the first failure has run every
+other test before it.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from paper_1209_6548_gb300 import build as B
+from paper_1209_6548_gb300 import inputs as I
+from paper_1209_6548_gb300 import lesbgk as L
+from tests.common import field_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+
+
+@pytest.mark.parametrize("prob", [I.tgv(512, steps=20), I.poiseuille(64, 300, steps=20),
+                                  I.Problem(name="d2q36", nroots=6, nx=45, ny=33, bc_y=I.DIFFUSE, kn=0.1,
+                                            b=-0.5, wall_ux=(-0.05, 0.05))],
+                         ids=["tgv512", "poiseuille64x300", "d2q36"])
+def test_noalloc_moments_match_workspace_moments(prob):
+    import torch
+    fields = I.initial_fields(prob) if prob.init == "tgv" else None
+    s = L.Solver(L.params_from_problem(prob), h_init=fields)
+    s.step(prob.steps)
+    ref, ref_sums = s.moments(sums=True)
+    ref = ref.cpu().numpy()
+    pops = s.populations()
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):  # two calls in a row share (and reuse) the static scratch
+        out = torch.full((9, prob.ny, prob.nx), float("nan"), dtype=torch.float32, device="cuda")
+        sums = np.zeros(4)
+        L.moments_noalloc(s.params, pops.data_ptr(), out.data_ptr(), sums, stream)
+        errs = field_errors(out.cpu().numpy(), ref.astype(np.float64))
+        bad = {k: v for k, v in errs.items() if not v[0] <= 1e-5}
+        assert not bad, bad
+        assert np.allclose(sums, ref_sums, rtol=1e-12, atol=1e-9)
+
+
+def test_noalloc_rejects_grids_beyond_its_scratch():
+    p = L.make_params(nx=8192, ny=4096, kn=0.1, b=0.0, bc_y=L.PERIODIC)  # 2^25 nodes: valid for a solver
+    with pytest.raises(L.LesbgkError) as e:
+        L.moments_noalloc(p, 256, 256, None, 0)
+    assert e.value.code == L.EINVAL and "at most" in L.last_error()
