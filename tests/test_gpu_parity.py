@@ -269,3 +269,44 @@ def test_conservation_periodic_gpu():
     assert abs(s1[1] - s0[1]) < 1e-9 * cells
     assert abs(s1[2] - s0[2]) < 1e-9 * cells
     assert abs(s1[3] - s0[3]) < 1e-9 * cells
+
+
+# ---------------------------------------------------------------- other lattices
+@pytest.mark.parametrize("scheme", [I.UNSPLIT, I.SPLIT])
+def test_d2q36_rough_periodic(scheme):
+    """D2Q36 (6 roots of He_6 per axis), Hermite order 4 -- the paper's own
+    setting -- on rough periodic fields spanning two strips and segments."""
+    prob = I.Problem(name="q36", nroots=6, nx=41, ny=37, bc_y=I.PERIODIC, kn=0.05, b=-0.5, scheme=scheme)
+    fields = I.random_fields(prob, seed=36)
+    res, *_ = run_pair(prob, fields, [1, 6])
+    for n, g, r, gp, fp in res:
+        assert_fields_close(g, r, what=f"d2q36 step {n}")
+        w = O.velocity_set(6)[2][:, None, None]
+        dev = fp - w
+        assert np.max(np.abs(gp - dev)) <= 2e-6 * np.max(np.abs(dev))
+
+
+def test_d2q36_couette_walls_force():
+    prob = I.Problem(name="q36c", nroots=6, nx=4, ny=40, bc_y=I.DIFFUSE, kn=0.1, b=-0.5,
+                     wall_ux=(-0.05, 0.05), wall_T=(0.98, 1.02), g=(1e-3, 0.0))
+    res, *_ = run_pair(prob, None, [1, 400])
+    for n, g, r, *_ in res:
+        assert_fields_close(g, r, what=f"d2q36 couette step {n}")
+
+
+def test_d2q16_order4():
+    """N = 4 on D2Q16 (projection not exact, still conservative)."""
+    prob = I.Problem(name="q16n4", nroots=4, order=4, nx=30, ny=25, bc_y=I.DIFFUSE, kn=0.1, b=0.5,
+                     wall_ux=(0.0, 0.05), g=(0.0, -1e-3))
+    fields = I.random_fields(prob, seed=4, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
+    res, *_ = run_pair(prob, fields, [1, 10])
+    for n, g, r, *_ in res:
+        assert_fields_close(g, r, what=f"d2q16 N=4 step {n}")
+
+
+def test_d2q36_order3():
+    prob = I.Problem(name="q36n3", nroots=6, order=3, nx=12, ny=20, bc_y=I.DIFFUSE, kn=0.2, b=0.0,
+                     wall_T=(0.95, 1.05))
+    res, *_ = run_pair(prob, None, [1, 100])
+    for n, g, r, *_ in res:
+        assert_fields_close(g, r, what=f"d2q36 N=3 step {n}")
