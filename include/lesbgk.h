@@ -168,6 +168,57 @@ int lesbgk_get_info(const lesbgk *h, lesbgk_info *out);
 /* Release the handle (not the caller's workspace).  NULL is a no-op. */
 int lesbgk_destroy(lesbgk *h);
 
+/* ------------------------------------------------------------------------
+ * Batched solver: many independent narrow solves advanced together.
+ *
+ * A batch holds up to `capacity` instances ("slots"), all with the same nx, a
+ * power of two <= 32 (the 1D-in-y flows of the paper's Sec. 4 run on nx = 4),
+ * each with its own ny, Kn, b, walls, force and time step, on D2Q16 (order 3)
+ * or D2Q36 (order 4).  Every lesbgk_batch_step advances every slot by the same
+ * number of steps: per step one launch per velocity set over a work list of
+ * (slot, row segment) items; steps in multiples of 64 replay a CUDA graph.
+ * Each slot's arithmetic is that of lesbgk_step on the same problem (results
+ * are bitwise equal), so a solve gives the same answer alone or in a batch.
+ *
+ * Memory: one caller-owned device workspace of lesbgk_batch_workspace_size
+ * bytes: fixed tables for `capacity` slots, then a pool of pool_bytes from
+ * which lesbgk_batch_add carves each slot's buffers
+ * (lesbgk_batch_slot_bytes); a full pool makes lesbgk_batch_add return
+ * LESBGK_ESPACE, which a caller can use as its admission test.
+ * ---------------------------------------------------------------------- */
+typedef struct lesbgk_batch lesbgk_batch;
+
+int lesbgk_batch_workspace_size(int32_t capacity, size_t pool_bytes, size_t *bytes);
+/* Pool bytes one slot with these parameters takes. */
+int lesbgk_batch_slot_bytes(const lesbgk_params *p, size_t *bytes);
+int lesbgk_batch_create(int32_t capacity, int32_t nx, void *d_workspace, size_t bytes, void *stream,
+                        lesbgk_batch **out);
+/* Admit a solve: tables, dt and the initial populations exactly as
+ * lesbgk_create (h_init: HOST double[4][ny][nx] or NULL); *slot receives its
+ * slot index.  Synchronises the stream. */
+int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const double *h_init, void *stream,
+                     int32_t *slot);
+/* Retire a slot and return its buffers to the pool. */
+int lesbgk_batch_remove(lesbgk_batch *b, int32_t slot, void *stream);
+int lesbgk_batch_step(lesbgk_batch *b, int64_t nsteps, void *stream);
+/* Steady-state residual of every slot since the previous call:
+ * r = max over nodes of (|d rho| + |d u_x| + |d u_y| + |d T|) / (steps * dt),
+ * into HOST double[capacity]; NaN for empty slots and for a slot's first call.
+ * Synchronises the stream. */
+int lesbgk_batch_residuals(lesbgk_batch *b, double *h_res, void *stream);
+/* As lesbgk_moments / lesbgk_get_populations / lesbgk_get_info, per slot. */
+int lesbgk_batch_moments(lesbgk_batch *b, int32_t slot, float *d_out, double *h_sums, void *stream);
+int lesbgk_batch_get_populations(lesbgk_batch *b, int32_t slot, float *d_out, void *stream);
+int lesbgk_batch_get_info(const lesbgk_batch *b, int32_t slot, lesbgk_info *out);
+/* Rows per work item (default 32); results do not depend on it. */
+int lesbgk_batch_set_rows(lesbgk_batch *b, int32_t rows, void *stream);
+/* Time one step for each candidate rows-per-item on the current slots (the
+ * state is left unchanged) and keep the fastest; *chosen receives it. */
+int lesbgk_batch_autotune(lesbgk_batch *b, const int32_t *candidates, int32_t n, int32_t *chosen, void *stream);
+/* Largest free block and total free bytes of the pool. */
+int lesbgk_batch_pool_free(const lesbgk_batch *b, size_t *largest, size_t *total);
+int lesbgk_batch_destroy(lesbgk_batch *b);
+
 /* Moments without any allocation (the paper has no counterpart: this is a
  * service to embedding code).  Some callers cannot allocate device memory at
  * all -- their device memory belongs to another allocator, they run under a

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "liblesbgk.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["lesbgk.cu", "tables.cpp"]
+SOURCES = ["lesbgk.cu", "batch.cu", "setup.cpp", "tables.cpp"]
 
 
 def nvcc() -> str:

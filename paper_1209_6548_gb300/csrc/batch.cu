@@ -1,0 +1,862 @@
+// Batched lattice ES-BGK solver: many independent narrow solves (nx a power of
+// two <= 32, e.g. the 1D-in-y channel flows of Sec. 4 of the paper) advanced
+// together, one launch per lattice per time step, replayed from CUDA graphs.
+//
+// Device memory: the caller's workspace holds fixed tables (per-slot
+// descriptors, the work list, residual and moment scratch) and a pool from
+// which each instance gets its two population buffers and a residual
+// snapshot; the pool is managed on the host (first fit, 256-byte aligned).
+//
+// k_batch_step: a warp holds 32/W lane groups of W = nx lanes; each group owns
+// one work item (an instance and a segment of its rows) and marches it like
+// the single-domain kernel (y-stencil in registers, look-ahead rows through a
+// per-lane cp.async ring), with the periodic x-neighbours taken by shuffles
+// inside the group.  Work items are sorted by length so the groups of a warp
+// run the same number of rows.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "device.cuh"
+#include "internal.h"
+#include "lesbgk.h"
+#include "setup.h"
+
+using namespace lesbgk_dev;
+using namespace lesbgk_setup;
+
+namespace {
+
+constexpr int kBBlock = 128;
+constexpr int kBRing = 4;
+constexpr int kNumClasses = 2;  // class 0: D2Q16 order 3, class 1: D2Q36 order 4
+constexpr int kGraphSteps = 64;
+
+// Per-instance descriptor (device memory).
+struct InstDesc {
+  float *f[2];  // population buffers, grouped layout
+  float *snap;  // residual snapshot: rho, ux, uy, T per node
+  int nx, ny, walls, split;
+  int vmode, has_force, pad0, pad1;
+  float c_omega, visc_pow, b, beta, dtgx, dtgy, dt, pad2;
+  float ax[kMaxR], kx[kMaxR], ay[kMaxR], ky[kMaxR];
+  float wS[2][kMaxQ], wSdev[2][kMaxQ], wA[2], wB[2];
+};
+
+struct WorkItem {
+  int inst, y0, rows, pad;
+};
+
+struct LatTables {
+  float c[kMaxR];
+  float he[kMaxR][kMaxN + 1];
+  float hw[kMaxR][kMaxN + 1];
+};
+
+struct BatchArgs {
+  LatTables lat;
+  const InstDesc *desc;
+  const WorkItem *items;
+  const int *range;  // {first item, item count} of this lattice class
+};
+
+// Per-solve scalars of one instance, held in registers (collide's TP).
+struct InstRegs {
+  float c_omega, visc_pow, b, beta, dtgx, dtgy;
+  int vmode, has_force;
+};
+
+template <int NR>
+constexpr size_t batch_smem_bytes() {
+  return (size_t)(kBBlock / 32) * kBRing * Layout<NR>::G * 32 * Layout<NR>::V * sizeof(float);
+}
+
+// One time step of every work item of a lattice class.
+template <int NR, int N, int W>
+__global__ void __launch_bounds__(kBBlock) k_batch_step(const BatchArgs B, const int par) {
+  using Lay = Layout<NR>;
+  constexpr int Q = Lay::Q, H = Lay::H, V = Lay::V, G = Lay::G;
+  constexpr int GPW = 32 / W;
+  const int lane = threadIdx.x & 31;
+  const int gi = lane / W, lx = lane % W;
+  const int warp = (blockIdx.x * kBBlock + threadIdx.x) >> 5;
+  const int first = B.range[0], count = B.range[1];
+  const int base = warp * GPW;
+  if (base >= count) return;  // uniform over the warp
+  int it = base + gi;
+  const bool live = it < count;
+  if (!live) it = base;  // idle group: repeats the warp's first item, stores nothing
+  const WorkItem wi = B.items[first + it];
+  const InstDesc &D = B.desc[wi.inst];
+  const int ny = D.ny, walls = D.walls;
+  const bool split = D.split != 0;
+  InstRegs P{D.c_omega, D.visc_pow, D.b, D.beta, D.dtgx, D.dtgy, D.vmode, D.has_force};
+  float ax[NR], kx[NR], ay[NR], ky[NR];
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    ax[i] = D.ax[i];
+    kx[i] = D.kx[i];
+    ay[i] = D.ay[i];
+    ky[i] = D.ky[i];
+  }
+  const float *fin = D.f[par];
+  float *fout = D.f[par ^ 1];
+  const long long gstride = (long long)V * W * ny;
+  const long long rstride = (long long)V * W;
+  const float *fx = fin + (long long)lx * V;
+  const int y0 = wi.y0;
+  const int rows = live ? wi.rows : 0;
+  int nrows = rows;  // the warp runs its longest item's rows
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nrows = max(nrows, __shfl_xor_sync(kFull, nrows, o));
+  const int srcL = gi * W + ((lx + W - 1) & (W - 1));
+  const int srcR = gi * W + ((lx + 1) & (W - 1));
+  auto row_ptr = [&](int j) { return fx + map_row(j, ny, walls) * rstride; };
+
+  float fc[Q], s0[Q], s1[Q];
+  {
+    float m2[Q], m1[Q], p1[Q];
+    const float *pm2 = row_ptr(y0 - 2), *pm1 = row_ptr(y0 - 1), *pz = row_ptr(y0), *pp1 = row_ptr(y0 + 1);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      ld_group<NR>(pm1, gstride, g, m1);
+      ld_group<NR>(pz, gstride, g, fc);
+      if (g >= G / 2) ld_group<NR>(pm2, gstride, g, m2);
+      else ld_group<NR>(pp1, gstride, g, p1);
+    }
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      if (a % NR >= H) {
+        s0[a] = fc[a] - m1[a];
+        s1[a] = minmod(m1[a] - m2[a], fc[a] - m1[a]);
+      } else {
+        s0[a] = p1[a];
+        s1[a] = minmod(fc[a] - m1[a], p1[a] - fc[a]);
+      }
+    }
+  }
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using T = typename VecT<V>::T;
+  T *ring = reinterpret_cast<T *>(smem_raw) + (size_t)(threadIdx.x >> 5) * kBRing * G * 32 + lane;
+  int r1 = map_row(y0 + 1, ny, walls), r2 = map_row(y0 + 2, ny, walls);
+  auto issue_rowload = [&](int k) {
+    if (k < nrows) {
+      const float *q1 = fx + r1 * rstride, *q2 = fx + r2 * rstride;
+      T *slot = ring + (k % kBRing) * G * 32;
+#pragma unroll
+      for (int g = 0; g < G; ++g) cp_async_vec<V>(slot + g * 32, (g >= G / 2 ? q1 : q2) + g * gstride);
+      r1 = r2;
+      r2 = r2 + 1 < ny ? r2 + 1 : (walls ? ny - 1 : 0);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int k = 0; k < kBRing - 1; ++k) issue_rowload(k);
+
+  for (int k = 0; k < nrows; ++k) {
+    const int j = y0 + k;
+    issue_rowload(k + kBRing - 1);
+    cp_async_wait<kBRing - 1>();
+    float ld[Q];
+    {
+      const T *slot = ring + (k % kBRing) * G * 32;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const T v = slot[g * 32];
+        const float *e = reinterpret_cast<const float *>(&v);
+#pragma unroll
+        for (int q = 0; q < V; ++q) ld[Lay::alpha(g * V + q)] = e[q];
+      }
+    }
+    float acc[Q];
+    float omw;
+    collide<NR, N>(fc, acc, omw, B.lat, P);
+    float xs[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      const int iy = a % NR;
+      float diff;
+      const float f0 = fc[a];
+      if (iy >= H) {
+        const float dn = ld[a] - f0;
+        const float sg = minmod(s0[a], dn);
+        diff = fmaf(ky[iy], sg - s1[a], s0[a]);
+        s0[a] = dn;
+        s1[a] = sg;
+        fc[a] = ld[a];
+      } else {
+        const float d1 = s0[a] - f0;
+        const float sg = minmod(d1, ld[a] - s0[a]);
+        diff = fmaf(-ky[iy], sg - s1[a], d1);
+        s1[a] = sg;
+        fc[a] = s0[a];
+        s0[a] = ld[a];
+      }
+      acc[a] = fmaf(omw, f0, fmaf(-ay[iy], diff, acc[a]));
+      xs[a] = split ? fmaf(-ay[iy], diff, f0) : f0;
+    }
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      const int ix = a / NR;
+      const float left = __shfl_sync(kFull, xs[a], srcL);
+      const float dl = xs[a] - left;
+      const float dr = __shfl_sync(kFull, dl, srcR);
+      const float sg = minmod(dl, dr);
+      float diff;
+      if (ix >= H) {
+        const float sprev = __shfl_sync(kFull, sg, srcL);
+        diff = fmaf(kx[ix], sg - sprev, dl);
+      } else {
+        const float snext = __shfl_sync(kFull, sg, srcR);
+        diff = fmaf(-kx[ix], snext - sg, dr);
+      }
+      acc[a] = fmaf(-ax[ix], diff, acc[a]);
+    }
+    if (walls && (j == 0 || j == ny - 1)) wall_fix<NR>(acc, (j == 0) ? 0 : 1, B.lat, D);
+    if (k < rows) {
+      float *o = fout + (long long)j * rstride + (long long)lx * V;
+#pragma unroll
+      for (int g = 0; g < G; ++g) st_group<NR>(o, gstride, g, acc);
+    }
+  }
+  cp_async_wait<0>();
+}
+
+// Residual of every work item: max over its nodes of
+// |d rho| + |d u_x| + |d u_y| + |d T| since the snapshot, folded into
+// res_bits[instance] (non-negative floats order like their bit patterns);
+// the snapshot is refreshed.  One block per item.
+template <int NR>
+__global__ void __launch_bounds__(kBBlock) k_batch_residual(const BatchArgs B, const int par,
+                                                            unsigned *__restrict__ res_bits) {
+  using Lay = Layout<NR>;
+  constexpr int Q = Lay::Q;
+  const int first = B.range[0], count = B.range[1];
+  if ((int)blockIdx.x >= count) return;
+  const WorkItem wi = B.items[first + blockIdx.x];
+  const InstDesc &D = B.desc[wi.inst];
+  const int nx = D.nx, ny = D.ny;
+  const long long cells = (long long)nx * ny;
+  const long long gstride = (long long)Lay::V * cells;
+  const float *f = D.f[par];
+  float r = 0.0f;
+  for (int t = threadIdx.x; t < wi.rows * nx; t += kBBlock) {
+    const long long c = (long long)wi.y0 * nx + t;
+    float F[Q];
+#pragma unroll
+    for (int g = 0; g < Lay::G; ++g) ld_group<NR>(f + c * Lay::V, gstride, g, F);
+    float m[3][3];
+    hermite_moments<NR, 2>(F, m, B.lat);
+    const float rho = 1.0f + m[0][0];
+    const float ir = 1.0f / rho;
+    const float ux = m[1][0] * ir, uy = m[0][1] * ir;
+    const float trM = fmaf(-m[1][0], ux, m[2][0]) + fmaf(-m[0][1], uy, m[0][2]);
+    const float T = fmaf(0.5f * trM, ir, 1.0f);
+    float *s = D.snap + 4 * c;
+    r = fmaxf(r, fabsf(rho - s[0]) + fabsf(ux - s[1]) + fabsf(uy - s[2]) + fabsf(T - s[3]));
+    s[0] = rho;
+    s[1] = ux;
+    s[2] = uy;
+    s[3] = T;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(kFull, r, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(res_bits + wi.inst, __float_as_uint(r));
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// First-fit allocator over [0, cap) in 256-byte units, coalescing on release.
+class Pool {
+ public:
+  explicit Pool(size_t cap = 0) : cap_(cap) {
+    if (cap) free_[0] = cap;
+  }
+  bool alloc(size_t bytes, size_t *off) {
+    bytes = align_up(bytes, 256);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const size_t rest = it->second - bytes, at = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[at] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = align_up(bytes, 256);
+    auto it = free_.emplace(off, bytes).first;
+    auto next = std::next(it);
+    if (next != free_.end() && it->first + it->second == next->first) {
+      it->second += next->second;
+      free_.erase(next);
+    }
+    if (it != free_.begin()) {
+      auto prev = std::prev(it);
+      if (prev->first + prev->second == it->first) {
+        prev->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  size_t largest_free() const {
+    size_t m = 0;
+    for (auto &kv : free_) m = std::max(m, kv.second);
+    return m;
+  }
+  size_t total_free() const {
+    size_t m = 0;
+    for (auto &kv : free_) m += kv.second;
+    return m;
+  }
+
+ private:
+  size_t cap_;
+  std::map<size_t, size_t> free_;
+};
+
+int class_of(int nr, int order) {
+  if (nr == 4 && order == 3) return 0;
+  if (nr == 6 && order == 4) return 1;
+  return -1;
+}
+
+}  // namespace
+
+struct lesbgk_batch {
+  struct Slot {
+    bool used = false;
+    lesbgk_params p;
+    int nr = 0, order = 0, cls = 0;
+    size_t off = 0, bytes = 0;
+    InstDesc desc;
+    KArgs args;
+    double dt = 0, dx = 0, dy = 0, cmax = 0, tau_ref = 0;
+    int64_t steps = 0, snap_step = -1;
+  };
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  int capacity = 0, nx = 0, W = 0;
+  InstDesc *d_desc = nullptr;
+  WorkItem *d_items = nullptr;
+  int *d_range = nullptr;
+  unsigned *d_res = nullptr;
+  double *d_partial = nullptr, *d_sums = nullptr;
+  char *pool_base = nullptr;
+  size_t pool_bytes = 0;
+  Pool pool;
+  std::vector<Slot> slots;
+  std::vector<WorkItem> items;
+  int range[kNumClasses][2] = {{0, 0}, {0, 0}};
+  int max_items = 0;
+  int rows = 32;
+  int par = 0;
+  int sm_count = 0;
+  LatTables lat[kNumClasses];
+  bool lat_ready[kNumClasses] = {false, false};
+  cudaGraphExec_t graph = nullptr;
+  int graph_grid[kNumClasses] = {0, 0};
+  bool graph_dirty = true;
+};
+
+namespace {
+
+constexpr size_t kItemsPerSlot = 1024;  // work-list room: items per slot (rows/8 for ny <= 8192)
+
+struct Layout0 {
+  size_t desc, items, range, res, partial, sums, pool;
+};
+
+Layout0 fixed_layout(int capacity) {
+  Layout0 L{};
+  size_t o = 0;
+  L.desc = o;
+  o = align_up(o + sizeof(InstDesc) * (size_t)capacity, 256);
+  L.items = o;
+  o = align_up(o + sizeof(WorkItem) * (size_t)capacity * kItemsPerSlot, 256);
+  L.range = o;
+  o = align_up(o + sizeof(int) * 2 * kNumClasses, 256);
+  L.res = o;
+  o = align_up(o + sizeof(unsigned) * (size_t)capacity, 256);
+  L.partial = o;
+  o = align_up(o + sizeof(double) * 4 * lesbgk_internal::kMomentPartials, 256);
+  L.sums = o;
+  o = align_up(o + sizeof(double) * 4, 256);
+  L.pool = o;
+  return L;
+}
+
+size_t slot_bytes(const lesbgk_params &p) {
+  const size_t cells = (size_t)p.nx * p.ny;
+  const size_t q = (size_t)p.nroots * p.nroots;
+  const size_t buf = align_up(cells * std::max<size_t>(q * sizeof(float), 36), 256);
+  return 2 * buf + align_up(cells * 4 * sizeof(float), 256);
+}
+
+bool pow2_le32(int n) { return n >= 1 && n <= 32 && (n & (n - 1)) == 0; }
+
+template <int NR, int N>
+void *step_fn(int W) {
+  switch (W) {
+    case 1: return (void *)k_batch_step<NR, N, 1>;
+    case 2: return (void *)k_batch_step<NR, N, 2>;
+    case 4: return (void *)k_batch_step<NR, N, 4>;
+    case 8: return (void *)k_batch_step<NR, N, 8>;
+    case 16: return (void *)k_batch_step<NR, N, 16>;
+    default: return (void *)k_batch_step<NR, N, 32>;
+  }
+}
+
+void *step_kernel(int cls, int W) { return cls == 0 ? step_fn<4, 3>(W) : step_fn<6, 4>(W); }
+
+size_t step_smem(int cls) { return cls == 0 ? batch_smem_bytes<4>() : batch_smem_bytes<6>(); }
+
+BatchArgs make_args(const lesbgk_batch *b, int cls) {
+  BatchArgs a;
+  a.lat = b->lat[cls];
+  a.desc = b->d_desc;
+  a.items = b->d_items;
+  a.range = b->d_range + 2 * cls;
+  return a;
+}
+
+unsigned step_grid(const lesbgk_batch *b, int n_items) {
+  const int gpw = 32 / b->W;
+  const long long warps = (n_items + gpw - 1) / gpw;
+  const long long blocks = (warps * 32 + kBBlock - 1) / kBBlock;
+  return (unsigned)std::max<long long>(blocks, 1);
+}
+
+cudaError_t launch_one_step(lesbgk_batch *b, int cls, int par, unsigned grid, cudaStream_t s) {
+  BatchArgs a = make_args(b, cls);
+  void *args[] = {&a, &par};
+  return cudaLaunchKernel(step_kernel(cls, b->W), dim3(grid), dim3(kBBlock), args, step_smem(cls), s);
+}
+
+// Rebuild the host work list (items sorted by class, then by length) and copy
+// it with the class ranges to the device.
+int rebuild_items(lesbgk_batch *b, cudaStream_t s) {
+  b->items.clear();
+  for (int cls = 0; cls < kNumClasses; ++cls) {
+    const int first = (int)b->items.size();
+    std::vector<WorkItem> mine;
+    for (int i = 0; i < b->capacity; ++i) {
+      const auto &sl = b->slots[i];
+      if (!sl.used || sl.cls != cls) continue;
+      for (int y0 = 0; y0 < sl.p.ny; y0 += b->rows) mine.push_back({i, y0, std::min(b->rows, sl.p.ny - y0), 0});
+    }
+    std::stable_sort(mine.begin(), mine.end(), [](const WorkItem &x, const WorkItem &y) { return x.rows > y.rows; });
+    b->items.insert(b->items.end(), mine.begin(), mine.end());
+    b->range[cls][0] = first;
+    b->range[cls][1] = (int)mine.size();
+  }
+  if ((long long)b->items.size() > (long long)b->capacity * (long long)kItemsPerSlot)
+    return fail(LESBGK_ESPACE, "work list of %zu items exceeds its room", b->items.size());
+  cudaError_t e = cudaSuccess;
+  if (!b->items.empty())
+    e = cudaMemcpyAsync(b->d_items, b->items.data(), sizeof(WorkItem) * b->items.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_range, b->range, sizeof(b->range), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host staging vectors are reused
+  if (e != cudaSuccess) return cuda_fail(e, "work list upload");
+  for (int cls = 0; cls < kNumClasses; ++cls)
+    if ((int)step_grid(b, b->range[cls][1]) > b->graph_grid[cls]) b->graph_dirty = true;
+  return 0;
+}
+
+void drop_graph(lesbgk_batch *b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_dirty = true;
+}
+
+// A graph of kGraphSteps steps: per step one launch per lattice class present,
+// each step after the previous one; grids sized with head room for the
+// current work list (kernels read their item counts from device memory, so
+// the graph stays valid while slots come and go).
+int build_graph(lesbgk_batch *b) {
+  drop_graph(b);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
+  BatchArgs args[kNumClasses];
+  int pars[2] = {0, 1};
+  std::vector<cudaGraphNode_t> prev;
+  for (int cls = 0; cls < kNumClasses; ++cls) {
+    const int n = b->range[cls][1];
+    b->graph_grid[cls] = n ? (int)step_grid(b, n + n / 4 + 64) : 0;
+    args[cls] = make_args(b, cls);
+  }
+  for (int st = 0; st < kGraphSteps && e == cudaSuccess; ++st) {
+    std::vector<cudaGraphNode_t> cur;
+    for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls) {
+      if (!b->graph_grid[cls]) continue;
+      cudaKernelNodeParams kp{};
+      void *kargs[] = {&args[cls], &pars[st & 1]};
+      kp.func = step_kernel(cls, b->W);
+      kp.gridDim = dim3(b->graph_grid[cls]);
+      kp.blockDim = dim3(kBBlock);
+      kp.sharedMemBytes = (unsigned)step_smem(cls);
+      kp.kernelParams = kargs;
+      cudaGraphNode_t node;
+      e = cudaGraphAddKernelNode(&node, g, prev.empty() ? nullptr : prev.data(), prev.size(), &kp);
+      cur.push_back(node);
+    }
+    if (!cur.empty()) prev = cur;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    b->graph = nullptr;
+    return cuda_fail(e, "building the step graph");
+  }
+  b->graph_dirty = false;
+  return 0;
+}
+
+}  // namespace
+
+extern "C" int lesbgk_batch_workspace_size(int32_t capacity, size_t pool_bytes, size_t *bytes) {
+  if (capacity < 1 || capacity > (1 << 20)) return fail(LESBGK_EINVAL, "capacity must be in [1, 2^20]");
+  if (!bytes) return fail(LESBGK_EINVAL, "bytes is NULL");
+  *bytes = fixed_layout(capacity).pool + align_up(pool_bytes, 256);
+  return 0;
+}
+
+extern "C" int lesbgk_batch_slot_bytes(const lesbgk_params *p, size_t *bytes) {
+  if (int rc = check_params(p)) return rc;
+  if (!bytes) return fail(LESBGK_EINVAL, "bytes is NULL");
+  *bytes = align_up(slot_bytes(*p), 256);
+  return 0;
+}
+
+extern "C" int lesbgk_batch_create(int32_t capacity, int32_t nx, void *d_workspace, size_t bytes, void *stream,
+                                   lesbgk_batch **out) {
+  clear_error();
+  if (!out) return fail(LESBGK_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (capacity < 1 || capacity > (1 << 20)) return fail(LESBGK_EINVAL, "capacity must be in [1, 2^20]");
+  if (!pow2_le32(nx)) return fail(LESBGK_EINVAL, "batched instances need nx in {1, 2, 4, 8, 16, 32}");
+  const Layout0 L = fixed_layout(capacity);
+  if (!d_workspace || bytes < L.pool + 256) return fail(LESBGK_ESPACE, "workspace %zu bytes < %zu", bytes, L.pool + 256);
+  if (reinterpret_cast<uintptr_t>(d_workspace) % 256) return fail(LESBGK_ESPACE, "workspace not 256-byte aligned");
+  lesbgk_batch *b = new (std::nothrow) lesbgk_batch();
+  if (!b) return fail(LESBGK_EINVAL, "out of host memory");
+  b->ws = static_cast<char *>(d_workspace);
+  b->ws_bytes = bytes;
+  b->capacity = capacity;
+  b->nx = nx;
+  b->W = nx;
+  b->d_desc = reinterpret_cast<InstDesc *>(b->ws + L.desc);
+  b->d_items = reinterpret_cast<WorkItem *>(b->ws + L.items);
+  b->d_range = reinterpret_cast<int *>(b->ws + L.range);
+  b->d_res = reinterpret_cast<unsigned *>(b->ws + L.res);
+  b->d_partial = reinterpret_cast<double *>(b->ws + L.partial);
+  b->d_sums = reinterpret_cast<double *>(b->ws + L.sums);
+  b->pool_base = b->ws + L.pool;
+  b->pool_bytes = bytes - L.pool;
+  b->pool = Pool(b->pool_bytes / 256 * 256);
+  b->slots.resize(capacity);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  for (int w : {1, 2, 4, 8, 16, 32}) {
+    if (e != cudaSuccess) break;
+    e = cudaFuncSetAttribute(step_fn<4, 3>(w), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes<4>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(step_fn<6, 4>(w), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)batch_smem_bytes<6>());
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_range, 0, sizeof(int) * 2 * kNumClasses, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "batch set-up");
+  }
+  *out = b;
+  return 0;
+}
+
+extern "C" int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const double *h_init, void *stream,
+                                int32_t *slot_out) {
+  if (!b || !slot_out) return fail(LESBGK_EINVAL, "NULL argument");
+  if (int rc = check_params(p)) return rc;
+  const int order = p->order ? p->order : default_order(p->nroots);
+  const int cls = class_of(p->nroots, order);
+  if (cls < 0) return fail(LESBGK_EINVAL, "batched instances take D2Q16 (order 3) or D2Q36 (order 4)");
+  if (p->nx != b->nx) return fail(LESBGK_EINVAL, "instance nx %d differs from the batch's %d", p->nx, b->nx);
+  if ((long long)(p->ny + b->rows - 1) / b->rows > (long long)kItemsPerSlot)
+    return fail(LESBGK_EINVAL, "ny %d too large for the batch work list", p->ny);
+  int slot = -1;
+  for (int i = 0; i < b->capacity; ++i)
+    if (!b->slots[i].used) {
+      slot = i;
+      break;
+    }
+  if (slot < 0) return fail(LESBGK_ESPACE, "all %d slots are in use", b->capacity);
+  Setup su;
+  if (int rc = build_setup(*p, order, h_init, &su)) return rc;
+  size_t off = 0;
+  const size_t need = slot_bytes(*p);
+  if (!b->pool.alloc(need, &off))
+    return fail(LESBGK_ESPACE, "pool has no free block of %zu bytes (largest %zu)", need, b->pool.largest_free());
+  auto &sl = b->slots[slot];
+  sl = lesbgk_batch::Slot();
+  sl.p = *p;
+  sl.nr = p->nroots;
+  sl.order = order;
+  sl.cls = cls;
+  sl.off = off;
+  sl.bytes = need;
+  sl.args = su.args;
+  sl.dt = su.dt;
+  sl.dx = su.dx;
+  sl.dy = su.dy;
+  sl.cmax = su.cmax;
+  sl.tau_ref = su.tau_ref;
+  const size_t cells = (size_t)p->nx * p->ny;
+  const size_t q = (size_t)p->nroots * p->nroots;
+  const size_t buf = align_up(cells * std::max<size_t>(q * sizeof(float), 36), 256);
+  char *base = b->pool_base + off;
+  InstDesc &D = sl.desc;
+  std::memset(&D, 0, sizeof D);
+  D.f[b->par] = reinterpret_cast<float *>(base);
+  D.f[b->par ^ 1] = reinterpret_cast<float *>(base + buf);
+  D.snap = reinterpret_cast<float *>(base + 2 * buf);
+  const KArgs &A = su.args;
+  D.nx = p->nx;
+  D.ny = p->ny;
+  D.walls = A.walls;
+  D.split = p->scheme == LESBGK_SPLIT;
+  D.vmode = A.vmode;
+  D.has_force = A.has_force;
+  D.c_omega = A.c_omega;
+  D.visc_pow = A.visc_pow;
+  D.b = A.b;
+  D.beta = A.beta;
+  D.dtgx = A.dtgx;
+  D.dtgy = A.dtgy;
+  D.dt = (float)su.dt;
+  std::memcpy(D.ax, A.ax, sizeof D.ax);
+  std::memcpy(D.kx, A.kx, sizeof D.kx);
+  std::memcpy(D.ay, A.ay, sizeof D.ay);
+  std::memcpy(D.ky, A.ky, sizeof D.ky);
+  std::memcpy(D.wS, A.wS, sizeof D.wS);
+  std::memcpy(D.wSdev, A.wSdev, sizeof D.wSdev);
+  std::memcpy(D.wA, A.wA, sizeof D.wA);
+  std::memcpy(D.wB, A.wB, sizeof D.wB);
+  if (!b->lat_ready[cls]) {
+    LatTables &lt = b->lat[cls];
+    std::memcpy(lt.c, A.c, sizeof lt.c);
+    std::memcpy(lt.he, A.he, sizeof lt.he);
+    std::memcpy(lt.hw, A.hw, sizeof lt.hw);
+    b->lat_ready[cls] = true;
+    drop_graph(b);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(b->d_desc + slot, &D, sizeof D, cudaMemcpyHostToDevice, s);
+  const double *dfields = nullptr;
+  if (e == cudaSuccess && h_init) {
+    e = cudaMemcpyAsync(D.f[b->par ^ 1], h_init, 4 * cells * sizeof(double), cudaMemcpyHostToDevice, s);
+    dfields = reinterpret_cast<const double *>(D.f[b->par ^ 1]);
+  }
+  if (e == cudaSuccess) e = lesbgk_internal::launch_init(A, sl.nr, order, dfields, D.f[b->par], b->sm_count, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host descriptor and h_init are reused
+  if (e != cudaSuccess) {
+    b->pool.release(off, need);
+    return cuda_fail(e, "slot initialisation");
+  }
+  sl.used = true;
+  if (int rc = rebuild_items(b, s)) {
+    sl.used = false;
+    b->pool.release(off, need);
+    return rc;
+  }
+  *slot_out = slot;
+  return 0;
+}
+
+extern "C" int lesbgk_batch_remove(lesbgk_batch *b, int32_t slot, void *stream) {
+  if (!b || slot < 0 || slot >= b->capacity || !b->slots[slot].used) return fail(LESBGK_EINVAL, "no such slot");
+  auto &sl = b->slots[slot];
+  sl.used = false;
+  if (int rc = rebuild_items(b, static_cast<cudaStream_t>(stream))) return rc;
+  b->pool.release(sl.off, sl.bytes);
+  return 0;
+}
+
+extern "C" int lesbgk_batch_step(lesbgk_batch *b, int64_t nsteps, void *stream) {
+  if (!b) return fail(LESBGK_EINVAL, "batch is NULL");
+  if (nsteps < 0) return fail(LESBGK_EINVAL, "nsteps < 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  auto direct_step = [&]() {
+    for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls)
+      if (b->range[cls][1]) e = launch_one_step(b, cls, b->par, step_grid(b, b->range[cls][1]), s);
+    if (e == cudaSuccess) {
+      b->par ^= 1;  // the slots' current buffers are desc.f[par]
+      for (auto &sl : b->slots)
+        if (sl.used) sl.steps += 1;
+    }
+  };
+  if (nsteps >= kGraphSteps) {
+    if (b->par == 1) {  // the graph's steps run parity 0, 1, 0, ...
+      direct_step();
+      --nsteps;
+    }
+    if (e == cudaSuccess && (b->graph_dirty || !b->graph))
+      if (int rc = build_graph(b)) return rc;
+  }
+  while (nsteps >= kGraphSteps && e == cudaSuccess) {
+    e = cudaGraphLaunch(b->graph, s);
+    nsteps -= kGraphSteps;
+    for (auto &sl : b->slots)
+      if (sl.used) sl.steps += kGraphSteps;
+  }
+  for (; nsteps > 0 && e == cudaSuccess; --nsteps) direct_step();
+  if (e != cudaSuccess) return cuda_fail(e, "batch step");
+  return 0;
+}
+
+extern "C" int lesbgk_batch_residuals(lesbgk_batch *b, double *h_res, void *stream) {
+  if (!b || !h_res) return fail(LESBGK_EINVAL, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(b->d_res, 0, sizeof(unsigned) * b->capacity, s);
+  for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls) {
+    const int n = b->range[cls][1];
+    if (!n) continue;
+    BatchArgs a = make_args(b, cls);
+    if (cls == 0) k_batch_residual<4><<<n, kBBlock, 0, s>>>(a, b->par, b->d_res);
+    else k_batch_residual<6><<<n, kBBlock, 0, s>>>(a, b->par, b->d_res);
+    e = cudaGetLastError();
+  }
+  std::vector<unsigned> bits(b->capacity);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bits.data(), b->d_res, sizeof(unsigned) * b->capacity, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "batch residuals");
+  for (int i = 0; i < b->capacity; ++i) {
+    auto &sl = b->slots[i];
+    h_res[i] = NAN;
+    if (!sl.used) continue;
+    float r;
+    std::memcpy(&r, &bits[i], sizeof r);
+    if (sl.snap_step >= 0 && sl.steps > sl.snap_step) h_res[i] = r / ((double)(sl.steps - sl.snap_step) * sl.dt);
+    else if (sl.snap_step >= 0) h_res[i] = 0.0;
+    sl.snap_step = sl.steps;
+  }
+  return 0;
+}
+
+extern "C" int lesbgk_batch_moments(lesbgk_batch *b, int32_t slot, float *d_out, double *h_sums, void *stream) {
+  if (!b || slot < 0 || slot >= b->capacity || !b->slots[slot].used) return fail(LESBGK_EINVAL, "no such slot");
+  auto &sl = b->slots[slot];
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = lesbgk_internal::launch_moments(sl.args, sl.nr, sl.desc.f[b->par], d_out, b->d_partial,
+                                                  b->d_sums, s);
+  if (e == cudaSuccess && h_sums) {
+    e = cudaMemcpyAsync(h_sums, b->d_sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "batch moments");
+  if (h_sums)
+    for (int k = 0; k < 4; ++k)
+      if (!std::isfinite(h_sums[k])) return fail(LESBGK_EDIVERGED, "slot %d diverged", slot);
+  return 0;
+}
+
+extern "C" int lesbgk_batch_get_populations(lesbgk_batch *b, int32_t slot, float *d_out, void *stream) {
+  if (!b || !d_out || slot < 0 || slot >= b->capacity || !b->slots[slot].used)
+    return fail(LESBGK_EINVAL, "no such slot");
+  auto &sl = b->slots[slot];
+  cudaError_t e = lesbgk_internal::launch_ungroup(sl.nr, sl.desc.f[b->par], d_out, (long long)sl.p.nx * sl.p.ny,
+                                                  b->sm_count, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? 0 : cuda_fail(e, "batch populations");
+}
+
+extern "C" int lesbgk_batch_get_info(const lesbgk_batch *b, int32_t slot, lesbgk_info *out) {
+  if (!b || !out || slot < 0 || slot >= b->capacity || !b->slots[slot].used) return fail(LESBGK_EINVAL, "no such slot");
+  const auto &sl = b->slots[slot];
+  out->dt = sl.dt;
+  out->dx = sl.dx;
+  out->dy = sl.dy;
+  out->c_max = sl.cmax;
+  out->cfl = sl.cmax * sl.dt / std::fmin(sl.dx, sl.dy);
+  out->tau_ref = sl.tau_ref;
+  out->steps_done = sl.steps;
+  out->q = sl.nr * sl.nr;
+  out->order = sl.order;
+  out->cells_per_thread = 1;
+  out->rows_per_segment = b->rows;
+  return 0;
+}
+
+extern "C" int lesbgk_batch_set_rows(lesbgk_batch *b, int32_t rows, void *stream) {
+  if (!b || rows < 1 || rows > 4096) return fail(LESBGK_EINVAL, "rows must be in [1, 4096]");
+  for (auto &sl : b->slots)
+    if (sl.used && (long long)(sl.p.ny + rows - 1) / rows > (long long)kItemsPerSlot)
+      return fail(LESBGK_EINVAL, "rows %d too short for ny %d", rows, sl.p.ny);
+  b->rows = rows;
+  drop_graph(b);
+  return rebuild_items(b, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int lesbgk_batch_autotune(lesbgk_batch *b, const int32_t *candidates, int32_t n, int32_t *chosen,
+                                     void *stream) {
+  if (!b || !candidates || n < 1) return fail(LESBGK_EINVAL, "bad autotune arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t t0, t1;
+  cudaError_t e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune events");
+  int best = b->rows;
+  float best_ms = 1e30f;
+  for (int c = 0; c < n && e == cudaSuccess; ++c) {
+    if (int rc = lesbgk_batch_set_rows(b, candidates[c], stream)) {
+      cudaEventDestroy(t0);
+      cudaEventDestroy(t1);
+      return rc;
+    }
+    // launches from the current buffers into the spare ones without flipping
+    // the parity: the state is left untouched
+    for (int rep = 0; rep < 13 && e == cudaSuccess; ++rep) {
+      if (rep == 3) e = cudaEventRecord(t0, s);
+      for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls)
+        if (b->range[cls][1]) e = launch_one_step(b, cls, b->par, step_grid(b, b->range[cls][1]), s);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    if (e == cudaSuccess && ms < best_ms) {
+      best_ms = ms;
+      best = candidates[c];
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  if (chosen) *chosen = best;
+  return lesbgk_batch_set_rows(b, best, stream);
+}
+
+extern "C" int lesbgk_batch_pool_free(const lesbgk_batch *b, size_t *largest, size_t *total) {
+  if (!b) return fail(LESBGK_EINVAL, "batch is NULL");
+  if (largest) *largest = b->pool.largest_free();
+  if (total) *total = b->pool.total_free();
+  return 0;
+}
+
+extern "C" int lesbgk_batch_destroy(lesbgk_batch *b) {
+  if (!b) return 0;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  delete b;
+  return 0;
+}

@@ -1,0 +1,324 @@
+// Device code shared by the lattice ES-BGK kernels (single domain and
+// batched): limiter, row mapping, the grouped population layout, the
+// per-node Hermite collision (Sec. 2.2) and the diffuse wall (Sec. 3.2).
+//
+// Functions take their tables through template "accessor" types:
+//   TT: lattice tables  c[i], he[i][m] = He_m(c_i), hw[i][m] = w_i He_m(c_i)/m!
+//   TP: per-solve scalars c_omega, visc_pow, vmode, b, beta, has_force, dtgx, dtgy
+//   TW: wall tables wS[2][Q], wSdev[2][Q], wA[2], wB[2]
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace lesbgk_dev {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float minmod(float a, float b) {
+  // signed smaller magnitude when a and b agree in sign, else 0 (= median(a, b, 0));
+  // equals [f_{i+1}-f_i] Psi(Theta) of Sec. 3.1 with the minmod limiter.
+  return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.0f));
+}
+
+// Hardware approximations (MUFU): relative error ~1 ulp, far below the FP32
+// rounding of the moments they act on.
+__device__ __forceinline__ float fast_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ float fast_sqrt(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ int map_row(int j, int ny, int walls) {
+  if (walls) return j < 0 ? 0 : (j >= ny ? ny - 1 : j);  // ghost rows = wall node
+  int r = j % ny;
+  return r < 0 ? r + ny : r;
+}
+
+// ---------------------------------------------------------------------------
+// Hermite moments a_mk = sum_a df_a He_m(c_ax) He_k(c_ay), m + k <= KM, of one
+// node's deviations F[ix*NR+iy], by sum factorisation over the tensor-product
+// set with the +/- pairing of the roots.
+// ---------------------------------------------------------------------------
+template <int NR, int KM, class TT>
+__device__ __forceinline__ void hermite_moments(const float (&F)[NR * NR], float (&a)[KM + 1][KM + 1],
+                                                const TT &A) {
+  constexpr int H = NR / 2;
+  float s[NR][KM + 1];
+#pragma unroll
+  for (int ix = 0; ix < NR; ++ix) {
+    float ev[H], od[H];
+#pragma unroll
+    for (int p = 0; p < H; ++p) {
+      const float fp = F[ix * NR + H + p], fn = F[ix * NR + H - 1 - p];
+      ev[p] = fp + fn;
+      od[p] = fp - fn;
+    }
+#pragma unroll
+    for (int k = 0; k <= KM; ++k) {
+      float acc;
+      if (k == 0) {
+        acc = ev[0];
+#pragma unroll
+        for (int p = 1; p < H; ++p) acc += ev[p];
+      } else {
+        acc = ((k & 1) ? od[0] : ev[0]) * A.he[H][k];
+#pragma unroll
+        for (int p = 1; p < H; ++p) acc = fmaf((k & 1) ? od[p] : ev[p], A.he[H + p][k], acc);
+      }
+      s[ix][k] = acc;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k <= KM; ++k) {
+    float sp[H], sm[H];
+#pragma unroll
+    for (int p = 0; p < H; ++p) {
+      sp[p] = s[H + p][k] + s[H - 1 - p][k];
+      sm[p] = s[H + p][k] - s[H - 1 - p][k];
+    }
+#pragma unroll
+    for (int m = 0; m + k <= KM; ++m) {
+      float acc;
+      if (m == 0) {
+        acc = sp[0];
+#pragma unroll
+        for (int p = 1; p < H; ++p) acc += sp[p];
+      } else {
+        acc = ((m & 1) ? sm[0] : sp[0]) * A.he[H][m];
+#pragma unroll
+        for (int p = 1; p < H; ++p) acc = fmaf((m & 1) ? sm[p] : sp[p], A.he[H + p][m], acc);
+      }
+      a[m][k] = acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// S_a = w_a sum_{m+k<=N} d_mk He_m(c_ax) He_k(c_ay) / (m! k!), by two 1D
+// passes (x then y) with the +/- pairing.
+// ---------------------------------------------------------------------------
+template <int NR, int N, class TT>
+__device__ __forceinline__ void hermite_evaluate(const float (&d)[N + 1][N + 1], float (&S)[NR * NR],
+                                                 const TT &A) {
+  constexpr int H = NR / 2;
+  float E[NR][N + 1];
+#pragma unroll
+  for (int p = 0; p < H; ++p) {
+    const int P = H + p;
+#pragma unroll
+    for (int k = 0; k <= N; ++k) {
+      float ev = d[0][k] * A.hw[P][0];
+#pragma unroll
+      for (int m = 2; m + k <= N; m += 2) ev = fmaf(d[m][k], A.hw[P][m], ev);
+      float od = 0.0f;
+      if (k + 1 <= N) {
+        od = d[1][k] * A.hw[P][1];
+#pragma unroll
+        for (int m = 3; m + k <= N; m += 2) od = fmaf(d[m][k], A.hw[P][m], od);
+      }
+      E[P][k] = ev + od;
+      E[H - 1 - p][k] = ev - od;
+    }
+  }
+#pragma unroll
+  for (int ix = 0; ix < NR; ++ix) {
+#pragma unroll
+    for (int q = 0; q < H; ++q) {
+      const int P = H + q;
+      float ev = E[ix][0] * A.hw[P][0];
+#pragma unroll
+      for (int k = 2; k <= N; k += 2) ev = fmaf(E[ix][k], A.hw[P][k], ev);
+      float od = E[ix][1] * A.hw[P][1];
+#pragma unroll
+      for (int k = 3; k <= N; k += 2) od = fmaf(E[ix][k], A.hw[P][k], od);
+      S[ix * NR + P] = ev + od;
+      S[ix * NR + H - 1 - q] = ev - od;
+    }
+  }
+}
+
+// Coefficients e_mk = rho E[He_m(X) He_k(Y)], (X,Y) ~ N(u, lambda): the
+// Hermite expansion of the anisotropic Gaussian of Eq. (cfeq) (equal to the
+// a_ES^(n) of Sec. 2.2), from the recursion of its generating function
+// rho exp(u.t + t.(lambda - I).t/2).  Inputs: rho, rho u, and L = lambda - I.
+template <int N>
+__device__ __forceinline__ void gaussian_coeffs(float rho, float ru_x, float ru_y, float ux, float uy,
+                                                float Lxx, float Lxy, float Lyy, float RLxx, float RLxy,
+                                                float RLyy, float (&e)[N + 1][N + 1]) {
+  e[0][0] = rho;
+  e[1][0] = ru_x;
+  e[0][1] = ru_y;
+  e[2][0] = fmaf(ux, ru_x, RLxx);
+  e[1][1] = fmaf(ux, ru_y, RLxy);
+  e[0][2] = fmaf(uy, ru_y, RLyy);
+#pragma unroll
+  for (int n = 3; n <= N; ++n) {
+#pragma unroll
+    for (int m = 0; m <= n; ++m) {
+      const int k = n - m;
+      float v;
+      if (m >= 1) {
+        v = ux * e[m - 1][k];
+        if (m >= 2) v = fmaf((float)(m - 1) * Lxx, e[m - 2][k], v);
+        if (k >= 1) v = fmaf((float)k * Lxy, e[m - 1][k - 1], v);
+      } else {
+        v = uy * e[0][k - 1];
+        if (k >= 2) v = fmaf((float)(k - 1) * Lyy, e[0][k - 2], v);
+      }
+      e[m][k] = v;
+    }
+  }
+}
+
+// One node's collision + force source: S_a = (dt/tau)(f_ES,a - w_a) + dt g_a
+// (deviation form) and omw = 1 - dt/tau.
+template <int NR, int N, class TT, class TP>
+__device__ __forceinline__ void collide(const float (&F)[NR * NR], float (&S)[NR * NR], float &omw,
+                                        const TT &Lt, const TP &P) {
+  constexpr int KM = (N - 1 > 2) ? N - 1 : 2;
+  float a[KM + 1][KM + 1];
+  hermite_moments<NR, KM>(F, a, Lt);
+  const float rho = 1.0f + a[0][0];
+  const float ir = fast_rcp(rho);
+  const float ux = a[1][0] * ir, uy = a[0][1] * ir;
+  // M = P - rho I (pressure tensor minus its rest value), from deviations
+  const float Mxx = fmaf(-a[1][0], ux, a[2][0]);
+  const float Mxy = fmaf(-a[1][0], uy, a[1][1]);
+  const float Myy = fmaf(-a[0][1], uy, a[0][2]);
+  const float trM = Mxx + Myy;
+  const float T = fmaf(0.5f * trM, ir, 1.0f);  // T = tr P / (D rho), D = 2
+  float Tp;
+  if (P.vmode == 1) Tp = fast_sqrt(T);
+  else if (P.vmode == 2) Tp = 1.0f;
+  else Tp = exp2f(P.visc_pow * __log2f(T));
+  const float om = P.c_omega * rho * Tp;  // dt/tau, tau = (Kn/Pr) T^varpi / (rho T)
+  omw = 1.0f - om;
+  // rho (lambda - I) = (1-b) rho (T-1) I + b M,  lambda = (1-b) T I + b P/rho
+  const float RLxx = fmaf(P.beta, trM, P.b * Mxx);
+  const float RLxy = P.b * Mxy;
+  const float RLyy = fmaf(P.beta, trM, P.b * Myy);
+  float e[N + 1][N + 1];
+  gaussian_coeffs<N>(rho, a[1][0], a[0][1], ux, uy, RLxx * ir, RLxy * ir, RLyy * ir, RLxx, RLxy, RLyy, e);
+  float d[N + 1][N + 1];
+#pragma unroll
+  for (int m = 0; m <= N; ++m)
+#pragma unroll
+    for (int k = 0; m + k <= N; ++k) d[m][k] = om * e[m][k];
+  d[0][0] = om * a[0][0];
+  if (P.has_force) {
+    // projected body force: coefficient m g_x a_{m-1,k} + k g_y a_{m,k-1} (a_00 = rho)
+#pragma unroll
+    for (int m = 0; m <= N; ++m)
+#pragma unroll
+      for (int k = 0; m + k <= N; ++k) {
+        if (m + k == 0) continue;
+        float v = d[m][k];
+        if (m >= 1) v = fmaf((float)m * P.dtgx, (m - 1 + k == 0) ? rho : a[m - 1][k], v);
+        if (k >= 1) v = fmaf((float)k * P.dtgy, (m + k - 1 == 0) ? rho : a[m][k - 1], v);
+        d[m][k] = v;
+      }
+  }
+  hermite_evaluate<NR, N>(d, S, Lt);
+}
+
+// Diffuse wall of Sec. 3.2 on one node's updated deviations: rho_W from the
+// incoming half, outgoing half = rho_W S_a(T_w, u_w).  side 0: bottom
+// (outgoing c_y > 0), side 1: top (outgoing c_y < 0).
+template <int NR, class TT, class TW>
+__device__ __forceinline__ void wall_fix(float (&O)[NR * NR], int side, const TT &T, const TW &W) {
+  constexpr int H = NR / 2;
+  float s = 0.0f;
+#pragma unroll
+  for (int ix = 0; ix < NR; ++ix)
+#pragma unroll
+    for (int iy = 0; iy < NR; ++iy) {
+      const bool incoming = side == 0 ? (iy < H) : (iy >= H);
+      if (incoming) s = fmaf(fabsf(T.c[iy]), O[ix * NR + iy], s);
+    }
+  const float rw1 = (s - W.wA[side]) * W.wB[side];  // rho_W - 1
+#pragma unroll
+  for (int ix = 0; ix < NR; ++ix)
+#pragma unroll
+    for (int iy = 0; iy < NR; ++iy) {
+      const bool outgoing = side == 0 ? (iy >= H) : (iy < H);
+      if (outgoing) O[ix * NR + iy] = fmaf(rw1, W.wS[side][ix * NR + iy], W.wSdev[side][ix * NR + iy]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Internal population layout in HBM ("grouped").  The Q populations of a node
+// are put in slot order: first the Q/2 with c_y < 0, then the Q/2 with
+// c_y > 0, each half in (ix, iy) order.  Consecutive slots form groups of V
+// (4 for D2Q16, 2 for D2Q36), and a group is stored as one V-vector per node:
+//   f[((g * ny + j) * nx + i) * V + k]  holds population alpha(g*V + k).
+// All populations of a group share the sign of c_y, so one vector load serves
+// one stencil row; a node's populations move as Q/V vector loads and stores.
+// ---------------------------------------------------------------------------
+template <int NR>
+struct Layout {
+  static constexpr int Q = NR * NR;
+  static constexpr int H = NR / 2;
+  static constexpr int HALF = Q / 2;
+  static constexpr int V = (HALF % 4 == 0) ? 4 : 2;
+  static constexpr int G = Q / V;
+  __host__ __device__ static constexpr int alpha(int s) {
+    return (s % HALF) / H * NR + ((s / HALF) ? H : 0) + (s % HALF) % H;
+  }
+};
+
+template <int V>
+struct VecT;
+template <>
+struct VecT<2> { using T = float2; };
+template <>
+struct VecT<4> { using T = float4; };
+
+// Load group g of one node (p points at the node's row, group 0) into F[alpha].
+template <int NR>
+__device__ __forceinline__ void ld_group(const float *p, long long gstride, int g, float (&F)[NR * NR]) {
+  using L = Layout<NR>;
+  using T = typename VecT<L::V>::T;
+  const T v = __ldg(reinterpret_cast<const T *>(p + g * gstride));
+  const float *e = reinterpret_cast<const float *>(&v);
+#pragma unroll
+  for (int k = 0; k < L::V; ++k) F[L::alpha(g * L::V + k)] = e[k];
+}
+
+template <int NR>
+__device__ __forceinline__ void st_group(float *p, long long gstride, int g, const float (&F)[NR * NR]) {
+  using L = Layout<NR>;
+  using T = typename VecT<L::V>::T;
+  T v;
+  float *e = reinterpret_cast<float *>(&v);
+#pragma unroll
+  for (int k = 0; k < L::V; ++k) e[k] = F[L::alpha(g * L::V + k)];
+  *reinterpret_cast<T *>(p + g * gstride) = v;
+}
+
+// Asynchronous global->shared copy of one V-vector (cp.async; 16-byte copies
+// bypass L1).
+template <int V>
+__device__ __forceinline__ void cp_async_vec(void *smem_dst, const float *gsrc) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  if constexpr (V == 4) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+  }
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+
+
+}  // namespace lesbgk_dev

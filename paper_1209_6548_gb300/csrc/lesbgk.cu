@@ -26,356 +26,19 @@
 #include <new>
 
 #include "lesbgk.h"
-#include "tables.h"
+#include "device.cuh"
+#include "internal.h"
+#include "setup.h"
 
 namespace {
 
-constexpr int kMaxR = 6;
-constexpr int kMaxN = 4;
-constexpr int kMaxQ = kMaxR * kMaxR;
-constexpr unsigned kFull = 0xffffffffu;
+using namespace lesbgk_dev;
+using namespace lesbgk_setup;
+
 constexpr int kBlock = 128;
 constexpr int kMomBlock = 256;
 
-thread_local char g_err[512] = "";
 
-int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
-int fail(int code, const char *fmt, ...) {
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(g_err, sizeof g_err, fmt, ap);
-  va_end(ap);
-  return code;
-}
-
-int cuda_fail(cudaError_t e, const char *where) {
-  return fail(LESBGK_ECUDA, "%s: %s", where, cudaGetErrorString(e));
-}
-
-// Kernel arguments: lattice tables and scalars, passed by value (constant bank).
-struct KArgs {
-  float c[kMaxR];              // 1D abscissae, ascending; c[NR-1-i] = -c[i]
-  float he[kMaxR][kMaxN + 1];  // He_m(c_i)
-  float hw[kMaxR][kMaxN + 1];  // w_i He_m(c_i) / m!
-  float ax[kMaxR], kx[kMaxR];  // c_i dt/dx and (1 - |c_i| dt/dx)/2
-  float ay[kMaxR], ky[kMaxR];  // same along y
-  float wS[2][kMaxQ];          // wall equilibrium S_a(T_w, u_w), [0] bottom, [1] top
-  float wSdev[2][kMaxQ];       // S_a - w_a
-  float wA[2], wB[2];          // sum_out |c_y|(S-w) and 1/sum_out |c_y| S
-  float c_omega;               // dt / (Kn (1-b)):  dt/tau = c_omega rho T^(1-varpi)
-  float visc_pow;              // 1 - varpi
-  float b, beta;               // b and (1-b)/2
-  float dtgx, dtgy;            // dt g
-  int nx, ny, walls, has_force, vmode;  // vmode 1: varpi = 1/2, 2: varpi = 1, 0: general
-  int rows, nstrips, nseg;
-  long long plane;             // nx*ny
-};
-
-__device__ __forceinline__ float minmod(float a, float b) {
-  // signed smaller magnitude when a and b agree in sign, else 0 (= median(a, b, 0));
-  // equals [f_{i+1}-f_i] Psi(Theta) of Sec. 3.1 with the minmod limiter.
-  return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.0f));
-}
-
-// Hardware approximations (MUFU): relative error ~1 ulp, far below the FP32
-// rounding of the moments they act on.
-__device__ __forceinline__ float fast_rcp(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
-__device__ __forceinline__ float fast_sqrt(float x) {
-  float r;
-  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
-__device__ __forceinline__ int map_row(int j, int ny, int walls) {
-  if (walls) return j < 0 ? 0 : (j >= ny ? ny - 1 : j);  // ghost rows = wall node
-  int r = j % ny;
-  return r < 0 ? r + ny : r;
-}
-
-// ---------------------------------------------------------------------------
-// Hermite moments a_mk = sum_a df_a He_m(c_ax) He_k(c_ay), m + k <= KM, of one
-// node's deviations F[ix*NR+iy], by sum factorisation over the tensor-product
-// set with the +/- pairing of the roots.
-// ---------------------------------------------------------------------------
-template <int NR, int KM>
-__device__ __forceinline__ void hermite_moments(const float (&F)[NR * NR], float (&a)[KM + 1][KM + 1],
-                                                const KArgs &A) {
-  constexpr int H = NR / 2;
-  float s[NR][KM + 1];
-#pragma unroll
-  for (int ix = 0; ix < NR; ++ix) {
-    float ev[H], od[H];
-#pragma unroll
-    for (int p = 0; p < H; ++p) {
-      const float fp = F[ix * NR + H + p], fn = F[ix * NR + H - 1 - p];
-      ev[p] = fp + fn;
-      od[p] = fp - fn;
-    }
-#pragma unroll
-    for (int k = 0; k <= KM; ++k) {
-      float acc;
-      if (k == 0) {
-        acc = ev[0];
-#pragma unroll
-        for (int p = 1; p < H; ++p) acc += ev[p];
-      } else {
-        acc = ((k & 1) ? od[0] : ev[0]) * A.he[H][k];
-#pragma unroll
-        for (int p = 1; p < H; ++p) acc = fmaf((k & 1) ? od[p] : ev[p], A.he[H + p][k], acc);
-      }
-      s[ix][k] = acc;
-    }
-  }
-#pragma unroll
-  for (int k = 0; k <= KM; ++k) {
-    float sp[H], sm[H];
-#pragma unroll
-    for (int p = 0; p < H; ++p) {
-      sp[p] = s[H + p][k] + s[H - 1 - p][k];
-      sm[p] = s[H + p][k] - s[H - 1 - p][k];
-    }
-#pragma unroll
-    for (int m = 0; m + k <= KM; ++m) {
-      float acc;
-      if (m == 0) {
-        acc = sp[0];
-#pragma unroll
-        for (int p = 1; p < H; ++p) acc += sp[p];
-      } else {
-        acc = ((m & 1) ? sm[0] : sp[0]) * A.he[H][m];
-#pragma unroll
-        for (int p = 1; p < H; ++p) acc = fmaf((m & 1) ? sm[p] : sp[p], A.he[H + p][m], acc);
-      }
-      a[m][k] = acc;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// S_a = w_a sum_{m+k<=N} d_mk He_m(c_ax) He_k(c_ay) / (m! k!), by two 1D
-// passes (x then y) with the +/- pairing.
-// ---------------------------------------------------------------------------
-template <int NR, int N>
-__device__ __forceinline__ void hermite_evaluate(const float (&d)[N + 1][N + 1], float (&S)[NR * NR],
-                                                 const KArgs &A) {
-  constexpr int H = NR / 2;
-  float E[NR][N + 1];
-#pragma unroll
-  for (int p = 0; p < H; ++p) {
-    const int P = H + p;
-#pragma unroll
-    for (int k = 0; k <= N; ++k) {
-      float ev = d[0][k] * A.hw[P][0];
-#pragma unroll
-      for (int m = 2; m + k <= N; m += 2) ev = fmaf(d[m][k], A.hw[P][m], ev);
-      float od = 0.0f;
-      if (k + 1 <= N) {
-        od = d[1][k] * A.hw[P][1];
-#pragma unroll
-        for (int m = 3; m + k <= N; m += 2) od = fmaf(d[m][k], A.hw[P][m], od);
-      }
-      E[P][k] = ev + od;
-      E[H - 1 - p][k] = ev - od;
-    }
-  }
-#pragma unroll
-  for (int ix = 0; ix < NR; ++ix) {
-#pragma unroll
-    for (int q = 0; q < H; ++q) {
-      const int P = H + q;
-      float ev = E[ix][0] * A.hw[P][0];
-#pragma unroll
-      for (int k = 2; k <= N; k += 2) ev = fmaf(E[ix][k], A.hw[P][k], ev);
-      float od = E[ix][1] * A.hw[P][1];
-#pragma unroll
-      for (int k = 3; k <= N; k += 2) od = fmaf(E[ix][k], A.hw[P][k], od);
-      S[ix * NR + P] = ev + od;
-      S[ix * NR + H - 1 - q] = ev - od;
-    }
-  }
-}
-
-// Coefficients e_mk = rho E[He_m(X) He_k(Y)], (X,Y) ~ N(u, lambda): the
-// Hermite expansion of the anisotropic Gaussian of Eq. (cfeq) (equal to the
-// a_ES^(n) of Sec. 2.2), from the recursion of its generating function
-// rho exp(u.t + t.(lambda - I).t/2).  Inputs: rho, rho u, and L = lambda - I.
-template <int N>
-__device__ __forceinline__ void gaussian_coeffs(float rho, float ru_x, float ru_y, float ux, float uy,
-                                                float Lxx, float Lxy, float Lyy, float RLxx, float RLxy,
-                                                float RLyy, float (&e)[N + 1][N + 1]) {
-  e[0][0] = rho;
-  e[1][0] = ru_x;
-  e[0][1] = ru_y;
-  e[2][0] = fmaf(ux, ru_x, RLxx);
-  e[1][1] = fmaf(ux, ru_y, RLxy);
-  e[0][2] = fmaf(uy, ru_y, RLyy);
-#pragma unroll
-  for (int n = 3; n <= N; ++n) {
-#pragma unroll
-    for (int m = 0; m <= n; ++m) {
-      const int k = n - m;
-      float v;
-      if (m >= 1) {
-        v = ux * e[m - 1][k];
-        if (m >= 2) v = fmaf((float)(m - 1) * Lxx, e[m - 2][k], v);
-        if (k >= 1) v = fmaf((float)k * Lxy, e[m - 1][k - 1], v);
-      } else {
-        v = uy * e[0][k - 1];
-        if (k >= 2) v = fmaf((float)(k - 1) * Lyy, e[0][k - 2], v);
-      }
-      e[m][k] = v;
-    }
-  }
-}
-
-// One node's collision + force source: S_a = (dt/tau)(f_ES,a - w_a) + dt g_a
-// (deviation form) and omw = 1 - dt/tau.
-template <int NR, int N>
-__device__ __forceinline__ void collide(const float (&F)[NR * NR], float (&S)[NR * NR], float &omw,
-                                        const KArgs &A) {
-  constexpr int KM = (N - 1 > 2) ? N - 1 : 2;
-  float a[KM + 1][KM + 1];
-  hermite_moments<NR, KM>(F, a, A);
-  const float rho = 1.0f + a[0][0];
-  const float ir = fast_rcp(rho);
-  const float ux = a[1][0] * ir, uy = a[0][1] * ir;
-  // M = P - rho I (pressure tensor minus its rest value), from deviations
-  const float Mxx = fmaf(-a[1][0], ux, a[2][0]);
-  const float Mxy = fmaf(-a[1][0], uy, a[1][1]);
-  const float Myy = fmaf(-a[0][1], uy, a[0][2]);
-  const float trM = Mxx + Myy;
-  const float T = fmaf(0.5f * trM, ir, 1.0f);  // T = tr P / (D rho), D = 2
-  float Tp;
-  if (A.vmode == 1) Tp = fast_sqrt(T);
-  else if (A.vmode == 2) Tp = 1.0f;
-  else Tp = exp2f(A.visc_pow * __log2f(T));
-  const float om = A.c_omega * rho * Tp;  // dt/tau, tau = (Kn/Pr) T^varpi / (rho T)
-  omw = 1.0f - om;
-  // rho (lambda - I) = (1-b) rho (T-1) I + b M,  lambda = (1-b) T I + b P/rho
-  const float RLxx = fmaf(A.beta, trM, A.b * Mxx);
-  const float RLxy = A.b * Mxy;
-  const float RLyy = fmaf(A.beta, trM, A.b * Myy);
-  float e[N + 1][N + 1];
-  gaussian_coeffs<N>(rho, a[1][0], a[0][1], ux, uy, RLxx * ir, RLxy * ir, RLyy * ir, RLxx, RLxy, RLyy, e);
-  float d[N + 1][N + 1];
-#pragma unroll
-  for (int m = 0; m <= N; ++m)
-#pragma unroll
-    for (int k = 0; m + k <= N; ++k) d[m][k] = om * e[m][k];
-  d[0][0] = om * a[0][0];
-  if (A.has_force) {
-    // projected body force: coefficient m g_x a_{m-1,k} + k g_y a_{m,k-1} (a_00 = rho)
-#pragma unroll
-    for (int m = 0; m <= N; ++m)
-#pragma unroll
-      for (int k = 0; m + k <= N; ++k) {
-        if (m + k == 0) continue;
-        float v = d[m][k];
-        if (m >= 1) v = fmaf((float)m * A.dtgx, (m - 1 + k == 0) ? rho : a[m - 1][k], v);
-        if (k >= 1) v = fmaf((float)k * A.dtgy, (m + k - 1 == 0) ? rho : a[m][k - 1], v);
-        d[m][k] = v;
-      }
-  }
-  hermite_evaluate<NR, N>(d, S, A);
-}
-
-// Diffuse wall of Sec. 3.2 on one node's updated deviations: rho_W from the
-// incoming half, outgoing half = rho_W S_a(T_w, u_w).  side 0: bottom
-// (outgoing c_y > 0), side 1: top (outgoing c_y < 0).
-template <int NR>
-__device__ __forceinline__ void wall_fix(float (&O)[NR * NR], int side, const KArgs &A) {
-  constexpr int H = NR / 2;
-  float s = 0.0f;
-#pragma unroll
-  for (int ix = 0; ix < NR; ++ix)
-#pragma unroll
-    for (int iy = 0; iy < NR; ++iy) {
-      const bool incoming = side == 0 ? (iy < H) : (iy >= H);
-      if (incoming) s = fmaf(fabsf(A.c[iy]), O[ix * NR + iy], s);
-    }
-  const float rw1 = (s - A.wA[side]) * A.wB[side];  // rho_W - 1
-#pragma unroll
-  for (int ix = 0; ix < NR; ++ix)
-#pragma unroll
-    for (int iy = 0; iy < NR; ++iy) {
-      const bool outgoing = side == 0 ? (iy >= H) : (iy < H);
-      if (outgoing) O[ix * NR + iy] = fmaf(rw1, A.wS[side][ix * NR + iy], A.wSdev[side][ix * NR + iy]);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Internal population layout in HBM ("grouped").  The Q populations of a node
-// are put in slot order: first the Q/2 with c_y < 0, then the Q/2 with
-// c_y > 0, each half in (ix, iy) order.  Consecutive slots form groups of V
-// (4 for D2Q16, 2 for D2Q36), and a group is stored as one V-vector per node:
-//   f[((g * ny + j) * nx + i) * V + k]  holds population alpha(g*V + k).
-// All populations of a group share the sign of c_y, so one vector load serves
-// one stencil row; a node's populations move as Q/V vector loads and stores.
-// ---------------------------------------------------------------------------
-template <int NR>
-struct Layout {
-  static constexpr int Q = NR * NR;
-  static constexpr int H = NR / 2;
-  static constexpr int HALF = Q / 2;
-  static constexpr int V = (HALF % 4 == 0) ? 4 : 2;
-  static constexpr int G = Q / V;
-  __host__ __device__ static constexpr int alpha(int s) {
-    return (s % HALF) / H * NR + ((s / HALF) ? H : 0) + (s % HALF) % H;
-  }
-};
-
-template <int V>
-struct VecT;
-template <>
-struct VecT<2> { using T = float2; };
-template <>
-struct VecT<4> { using T = float4; };
-
-// Load group g of one node (p points at the node's row, group 0) into F[alpha].
-template <int NR>
-__device__ __forceinline__ void ld_group(const float *p, long long gstride, int g, float (&F)[NR * NR]) {
-  using L = Layout<NR>;
-  using T = typename VecT<L::V>::T;
-  const T v = __ldg(reinterpret_cast<const T *>(p + g * gstride));
-  const float *e = reinterpret_cast<const float *>(&v);
-#pragma unroll
-  for (int k = 0; k < L::V; ++k) F[L::alpha(g * L::V + k)] = e[k];
-}
-
-template <int NR>
-__device__ __forceinline__ void st_group(float *p, long long gstride, int g, const float (&F)[NR * NR]) {
-  using L = Layout<NR>;
-  using T = typename VecT<L::V>::T;
-  T v;
-  float *e = reinterpret_cast<float *>(&v);
-#pragma unroll
-  for (int k = 0; k < L::V; ++k) e[k] = F[L::alpha(g * L::V + k)];
-  *reinterpret_cast<T *>(p + g * gstride) = v;
-}
-
-// Asynchronous global->shared copy of one V-vector (cp.async; 16-byte copies
-// bypass L1).
-template <int V>
-__device__ __forceinline__ void cp_async_vec(void *smem_dst, const float *gsrc) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
-  if constexpr (V == 4) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
-  } else {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
-  }
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-
-template <int PENDING>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
-}
 
 // ---------------------------------------------------------------------------
 // The fused time step (Sec. 3.1 + Sec. 3.2).
@@ -474,7 +137,7 @@ __global__ void __launch_bounds__(kBlock) k_step(const float *__restrict__ fin, 
 
     float acc[Q];
     float omw;
-    collide<NR, N>(fc, acc, omw, A);
+    collide<NR, N>(fc, acc, omw, A, A);
 
     // y-advection from the carried stencil of f^n; xs = the values the
     // x-fluxes are taken from: f^n_j (update as printed) or the y-swept
@@ -525,7 +188,7 @@ __global__ void __launch_bounds__(kBlock) k_step(const float *__restrict__ fin, 
       acc[a] = fmaf(-ax, diff, acc[a]);
     }
 
-    if (A.walls && (j == 0 || j == ny - 1)) wall_fix<NR>(acc, (j == 0) ? 0 : 1, A);
+    if (A.walls && (j == 0 || j == ny - 1)) wall_fix<NR>(acc, (j == 0) ? 0 : 1, A, A);
 
     if (writer) {
       float *o = fout + (long long)j * rstride + (long long)xw * V;
@@ -564,7 +227,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const double *__restrict__ fiel
     float S[Q];
     hermite_evaluate<NR, N>(e, S, A);
     const int j = (int)(c / A.nx);
-    if (A.walls && (j == 0 || j == A.ny - 1)) wall_fix<NR>(S, j == 0 ? 0 : 1, A);
+    if (A.walls && (j == 0 || j == A.ny - 1)) wall_fix<NR>(S, j == 0 ? 0 : 1, A, A);
 #pragma unroll
     for (int g = 0; g < Lay::G; ++g) st_group<NR>(f + c * Lay::V, gstride, g, S);
   }
@@ -692,7 +355,7 @@ __global__ void k_reduce_partials(const double *__restrict__ partial, int n, dou
   if (lane == 0) sums[q] = t;
 }
 
-constexpr int kMomGrid = 1024;
+constexpr int kMomGrid = lesbgk_internal::kMomentPartials;
 
 }  // namespace
 
@@ -717,32 +380,6 @@ struct lesbgk {
 namespace {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-int check_params(const lesbgk_params *p) {
-  if (!p) return fail(LESBGK_EINVAL, "params is NULL");
-  if (p->struct_size != sizeof(lesbgk_params))
-    return fail(LESBGK_EINVAL, "struct_size %u != %zu", p->struct_size, sizeof(lesbgk_params));
-  if (p->nroots != 4 && p->nroots != 6) return fail(LESBGK_EINVAL, "nroots must be 4 or 6");
-  const int order = p->order ? p->order : (p->nroots == 4 ? 3 : 4);
-  if (order != 3 && order != 4) return fail(LESBGK_EINVAL, "order must be 3 or 4");
-  if (p->nx < 1 || p->ny < 1) return fail(LESBGK_EINVAL, "nx, ny must be >= 1");
-  if ((long long)p->nx * p->ny > (1LL << 31) / 64) return fail(LESBGK_EINVAL, "grid too large");
-  if (p->bc_y != LESBGK_PERIODIC && p->bc_y != LESBGK_DIFFUSE) return fail(LESBGK_EINVAL, "bad bc_y");
-  if (p->bc_y == LESBGK_DIFFUSE && p->ny < 2) return fail(LESBGK_EINVAL, "walls need ny >= 2");
-  if (p->storage != LESBGK_F32) return fail(LESBGK_EINVAL, "storage must be LESBGK_F32");
-  if (p->scheme != LESBGK_UNSPLIT && p->scheme != LESBGK_SPLIT)
-    return fail(LESBGK_EINVAL, "scheme must be LESBGK_UNSPLIT or LESBGK_SPLIT");
-  if (!(p->kn > 0.0) || !std::isfinite(p->kn)) return fail(LESBGK_EINVAL, "Kn must be > 0");
-  if (!(p->b >= -0.5 && p->b < 1.0)) return fail(LESBGK_EINVAL, "b must satisfy -1/2 <= b < 1");
-  if (!(p->visc_exp >= 0.0 && p->visc_exp <= 1.0)) return fail(LESBGK_EINVAL, "visc_exp must be in [0,1]");
-  if (!(p->dt >= 0.0) || !std::isfinite(p->dt)) return fail(LESBGK_EINVAL, "dt must be >= 0");
-  if (p->dt == 0.0 && !(p->cfl > 0.0 && p->cfl <= 1.0)) return fail(LESBGK_EINVAL, "cfl must be in (0,1]");
-  for (int s = 0; s < 2; ++s) {
-    if (!(p->wall_T[s] > 0.0) || !std::isfinite(p->wall_T[s])) return fail(LESBGK_EINVAL, "wall_T must be > 0");
-    if (!std::isfinite(p->wall_ux[s]) || !std::isfinite(p->g[s])) return fail(LESBGK_EINVAL, "non-finite wall_ux/g");
-  }
-  return 0;
-}
 
 size_t buffer_bytes(const lesbgk_params *p) {
   const size_t cells = (size_t)p->nx * p->ny;
@@ -778,105 +415,14 @@ int pick_launch(lesbgk *h) {
 }
 
 int build_tables(lesbgk *h, const double *h_init) {
-  using namespace lesbgk_tables;
-  const lesbgk_params &p = h->p;
-  const int nr = p.nroots, N = h->order;
-  double c[kMaxRoots], w[kMaxRoots];
-  if (gauss_hermite(nr, c, w)) return fail(LESBGK_EINVAL, "quadrature failed");
-  KArgs &A = h->args;
-  std::memset(&A, 0, sizeof A);
-  h->cmax = std::fabs(c[0]);
-  // spacing
-  if (p.bc_y == LESBGK_PERIODIC) {
-    h->dx = 1.0 / p.nx;
-    h->dy = 1.0 / p.ny;
-  } else {
-    h->dy = 1.0 / (p.ny - 1);
-    h->dx = h->dy;
-  }
-  // reference state for tau_ref
-  double tmax = 1.0, rmax = 1.0;
-  if (p.bc_y == LESBGK_DIFFUSE) tmax = std::fmax(tmax, std::fmax(p.wall_T[0], p.wall_T[1]));
-  if (h_init) {
-    const size_t cells = (size_t)p.nx * p.ny;
-    double r0 = h_init[0];
-    for (size_t k = 0; k < cells; ++k) {
-      const double r = h_init[k], T = h_init[3 * cells + k];
-      if (!(r > 0.0) || !(T > 0.0) || !std::isfinite(r) || !std::isfinite(T) ||
-          !std::isfinite(h_init[cells + k]) || !std::isfinite(h_init[2 * cells + k]))
-        return fail(LESBGK_EINVAL, "initial field at node %zu not admissible (rho, T > 0, finite)", k);
-      r0 = std::fmax(r0, r);
-      tmax = std::fmax(tmax, T);
-    }
-    rmax = r0;
-  }
-  const double pr = 1.0 / (1.0 - p.b);
-  h->tau_ref = (p.kn / pr) * std::pow(tmax, p.visc_exp - 1.0) / rmax;
-  const double hmin = std::fmin(h->dx, h->dy);
-  if (p.dt > 0.0) {
-    h->dt = p.dt;
-    if (h->cmax * h->dt / hmin > 1.0) return fail(LESBGK_EUNSTABLE, "CFL %.3f > 1", h->cmax * h->dt / hmin);
-    if (h->dt / h->tau_ref >= 2.0) return fail(LESBGK_EUNSTABLE, "dt/tau_ref = %.3f >= 2", h->dt / h->tau_ref);
-  } else {
-    h->dt = std::fmin(p.cfl * hmin / h->cmax, h->tau_ref);
-  }
-  const double dt = h->dt;
-  double fact[kMaxOrder + 1] = {1, 1, 2, 6, 24};
-  for (int i = 0; i < nr; ++i) {
-    double hv[kMaxOrder + 1];
-    hermite_values(kMaxOrder, c[i], hv);
-    A.c[i] = (float)c[i];
-    for (int m = 0; m <= kMaxOrder; ++m) {
-      A.he[i][m] = (float)hv[m];
-      A.hw[i][m] = (float)(w[i] * hv[m] / fact[m]);
-    }
-    A.ax[i] = (float)(c[i] * dt / h->dx);
-    A.kx[i] = (float)(0.5 * (1.0 - std::fabs(c[i]) * dt / h->dx));
-    A.ay[i] = (float)(c[i] * dt / h->dy);
-    A.ky[i] = (float)(0.5 * (1.0 - std::fabs(c[i]) * dt / h->dy));
-  }
-  // wall equilibria S_a(T_w, u_w) at order N (b = 0 Gaussian projection)
-  for (int s = 0; s < 2; ++s) {
-    double e[kMaxOrder + 1][kMaxOrder + 1];
-    const double th = p.wall_T[s] - 1.0;
-    gaussian_hermite_moments(N, 1.0, p.wall_ux[s], 0.0, th, 0.0, th, e);
-    double A_out = 0.0, Z_out = 0.0;
-    for (int ix = 0; ix < nr; ++ix) {
-      double hx[kMaxOrder + 1];
-      hermite_values(kMaxOrder, c[ix], hx);
-      for (int iy = 0; iy < nr; ++iy) {
-        double hy[kMaxOrder + 1];
-        hermite_values(kMaxOrder, c[iy], hy);
-        double sum = 0.0;
-        for (int m = 0; m <= N; ++m)
-          for (int k = 0; m + k <= N; ++k) sum += e[m][k] * hx[m] * hy[k] / (fact[m] * fact[k]);
-        const double wa = w[ix] * w[iy];
-        const double S = wa * sum;
-        const int a = ix * nr + iy;
-        A.wS[s][a] = (float)S;
-        A.wSdev[s][a] = (float)(S - wa);
-        const bool outgoing = (s == 0) ? (c[iy] > 0.0) : (c[iy] < 0.0);
-        if (outgoing) {
-          A_out += std::fabs(c[iy]) * (S - wa);
-          Z_out += std::fabs(c[iy]) * S;
-        }
-      }
-    }
-    A.wA[s] = (float)A_out;
-    A.wB[s] = (float)(1.0 / Z_out);
-  }
-  A.c_omega = (float)(dt / (p.kn * (1.0 - p.b)));
-  A.visc_pow = (float)(1.0 - p.visc_exp);
-  A.vmode = p.visc_exp == 0.5 ? 1 : (p.visc_exp == 1.0 ? 2 : 0);
-  A.b = (float)p.b;
-  A.beta = (float)(0.5 * (1.0 - p.b));
-  A.dtgx = (float)(dt * p.g[0]);
-  A.dtgy = (float)(dt * p.g[1]);
-  A.has_force = (p.g[0] != 0.0 || p.g[1] != 0.0) ? 1 : 0;
-  A.nx = p.nx;
-  A.ny = p.ny;
-  A.walls = p.bc_y == LESBGK_DIFFUSE ? 1 : 0;
-  A.plane = (long long)p.nx * p.ny;
+  Setup s;
+  if (int rc = build_setup(h->p, h->order, h_init, &s)) return rc;
+  h->args = s.args;
+  h->dt = s.dt;
+  h->dx = s.dx;
+  h->dy = s.dy;
+  h->cmax = s.cmax;
+  h->tau_ref = s.tau_ref;
   return 0;
 }
 
@@ -947,9 +493,42 @@ int launch_moments(lesbgk *h, float *out, cudaStream_t s) {
 
 }  // namespace
 
+namespace lesbgk_internal {
+
+cudaError_t launch_init(const KArgs &A, int nr, int order, const double *fields, float *f, int sm_count,
+                        cudaStream_t s) {
+  long long g = (A.plane + kBlock - 1) / kBlock;
+  if (g > (long long)sm_count * 16) g = (long long)sm_count * 16;
+  const unsigned grid = g < 1 ? 1u : (unsigned)g;
+  if (nr == 4 && order == 3) k_init<4, 3><<<grid, kBlock, 0, s>>>(fields, f, A);
+  else if (nr == 4 && order == 4) k_init<4, 4><<<grid, kBlock, 0, s>>>(fields, f, A);
+  else if (nr == 6 && order == 3) k_init<6, 3><<<grid, kBlock, 0, s>>>(fields, f, A);
+  else k_init<6, 4><<<grid, kBlock, 0, s>>>(fields, f, A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const KArgs &A, int nr, const float *f, float *out, double *partial, double *sums,
+                           cudaStream_t s) {
+  if (nr == 4) k_moments<4><<<kMomGrid, kMomBlock, 0, s>>>(f, out, partial, A);
+  else k_moments<6><<<kMomGrid, kMomBlock, 0, s>>>(f, out, partial, A);
+  k_reduce_partials<<<1, 128, 0, s>>>(partial, kMomGrid, sums);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ungroup(int nr, const float *f, float *out, long long cells, int sm_count, cudaStream_t s) {
+  long long g = (cells + kBlock - 1) / kBlock;
+  if (g > (long long)sm_count * 16) g = (long long)sm_count * 16;
+  const unsigned grid = g < 1 ? 1u : (unsigned)g;
+  if (nr == 4) k_ungroup<4><<<grid, kBlock, 0, s>>>(f, out, cells);
+  else k_ungroup<6><<<grid, kBlock, 0, s>>>(f, out, cells);
+  return cudaGetLastError();
+}
+
+}  // namespace lesbgk_internal
+
 extern "C" int lesbgk_create(const lesbgk_params *p, void *d_workspace, size_t bytes, const double *h_init,
                              void *stream, lesbgk **out) {
-  g_err[0] = 0;
+  clear_error();
   if (int rc = check_params(p)) return rc;
   if (!out) return fail(LESBGK_EINVAL, "out is NULL");
   *out = nullptr;
@@ -961,7 +540,7 @@ extern "C" int lesbgk_create(const lesbgk_params *p, void *d_workspace, size_t b
   if (!h) return fail(LESBGK_EINVAL, "out of host memory");
   h->p = *p;
   h->nr = p->nroots;
-  h->order = p->order ? p->order : (p->nroots == 4 ? 3 : 4);
+  h->order = p->order ? p->order : default_order(p->nroots);
   h->q = h->nr * h->nr;
   h->ws = static_cast<char *>(d_workspace);
   h->ws_bytes = bytes;
@@ -1121,7 +700,6 @@ extern "C" int lesbgk_destroy(lesbgk *h) {
   return 0;
 }
 
-extern "C" const char *lesbgk_last_error(void) { return g_err; }
 
 // ===========================================================================
 // Moments without allocation.
@@ -1259,7 +837,7 @@ extern "C" int lesbgk_moments_noalloc(const lesbgk_params *p, const float *d_pop
   lesbgk tmp{};
   tmp.p = *p;
   tmp.nr = p->nroots;
-  tmp.order = p->order ? p->order : (p->nroots == 4 ? 3 : 4);
+  tmp.order = p->order ? p->order : default_order(p->nroots);
   tmp.q = tmp.nr * tmp.nr;
   if (int rc = build_tables(&tmp, nullptr)) return rc;
   double *scratch = nullptr;

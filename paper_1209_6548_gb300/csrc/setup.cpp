@@ -1,0 +1,166 @@
+// Host-side set-up shared by the solvers (see setup.h).
+#include "setup.h"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "tables.h"
+
+namespace lesbgk_setup {
+
+namespace {
+thread_local char g_err[512] = "";
+}  // namespace
+
+const char *last_error_buffer() { return g_err; }
+
+int fail(int code, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+  return fail(LESBGK_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+void clear_error() { g_err[0] = 0; }
+
+int default_order(int nroots) { return nroots == 4 ? 3 : 4; }
+
+int check_params(const lesbgk_params *p) {
+  if (!p) return fail(LESBGK_EINVAL, "params is NULL");
+  if (p->struct_size != sizeof(lesbgk_params))
+    return fail(LESBGK_EINVAL, "struct_size %u != %zu", p->struct_size, sizeof(lesbgk_params));
+  if (p->nroots != 4 && p->nroots != 6) return fail(LESBGK_EINVAL, "nroots must be 4 or 6");
+  const int order = p->order ? p->order : default_order(p->nroots);
+  if (order != 3 && order != 4) return fail(LESBGK_EINVAL, "order must be 3 or 4");
+  if (p->nx < 1 || p->ny < 1) return fail(LESBGK_EINVAL, "nx, ny must be >= 1");
+  if ((long long)p->nx * p->ny > (1LL << 31) / 64) return fail(LESBGK_EINVAL, "grid too large");
+  if (p->bc_y != LESBGK_PERIODIC && p->bc_y != LESBGK_DIFFUSE) return fail(LESBGK_EINVAL, "bad bc_y");
+  if (p->bc_y == LESBGK_DIFFUSE && p->ny < 2) return fail(LESBGK_EINVAL, "walls need ny >= 2");
+  if (p->storage != LESBGK_F32) return fail(LESBGK_EINVAL, "storage must be LESBGK_F32");
+  if (p->scheme != LESBGK_UNSPLIT && p->scheme != LESBGK_SPLIT)
+    return fail(LESBGK_EINVAL, "scheme must be LESBGK_UNSPLIT or LESBGK_SPLIT");
+  if (!(p->kn > 0.0) || !std::isfinite(p->kn)) return fail(LESBGK_EINVAL, "Kn must be > 0");
+  if (!(p->b >= -0.5 && p->b < 1.0)) return fail(LESBGK_EINVAL, "b must satisfy -1/2 <= b < 1");
+  if (!(p->visc_exp >= 0.0 && p->visc_exp <= 1.0)) return fail(LESBGK_EINVAL, "visc_exp must be in [0,1]");
+  if (!(p->dt >= 0.0) || !std::isfinite(p->dt)) return fail(LESBGK_EINVAL, "dt must be >= 0");
+  if (p->dt == 0.0 && !(p->cfl > 0.0 && p->cfl <= 1.0)) return fail(LESBGK_EINVAL, "cfl must be in (0,1]");
+  for (int s = 0; s < 2; ++s) {
+    if (!(p->wall_T[s] > 0.0) || !std::isfinite(p->wall_T[s])) return fail(LESBGK_EINVAL, "wall_T must be > 0");
+    if (!std::isfinite(p->wall_ux[s]) || !std::isfinite(p->g[s])) return fail(LESBGK_EINVAL, "non-finite wall_ux/g");
+  }
+  return 0;
+}
+
+int build_setup(const lesbgk_params &p, int order, const double *h_init, Setup *out) {
+  using namespace lesbgk_tables;
+  Setup *h = out;
+  const int nr = p.nroots, N = order;
+  double c[kMaxRoots], w[kMaxRoots];
+  if (gauss_hermite(nr, c, w)) return fail(LESBGK_EINVAL, "quadrature failed");
+  KArgs &A = h->args;
+  std::memset(&A, 0, sizeof A);
+  h->cmax = std::fabs(c[0]);
+  // spacing
+  if (p.bc_y == LESBGK_PERIODIC) {
+    h->dx = 1.0 / p.nx;
+    h->dy = 1.0 / p.ny;
+  } else {
+    h->dy = 1.0 / (p.ny - 1);
+    h->dx = h->dy;
+  }
+  // reference state for tau_ref
+  double tmax = 1.0, rmax = 1.0;
+  if (p.bc_y == LESBGK_DIFFUSE) tmax = std::fmax(tmax, std::fmax(p.wall_T[0], p.wall_T[1]));
+  if (h_init) {
+    const size_t cells = (size_t)p.nx * p.ny;
+    double r0 = h_init[0];
+    for (size_t k = 0; k < cells; ++k) {
+      const double r = h_init[k], T = h_init[3 * cells + k];
+      if (!(r > 0.0) || !(T > 0.0) || !std::isfinite(r) || !std::isfinite(T) ||
+          !std::isfinite(h_init[cells + k]) || !std::isfinite(h_init[2 * cells + k]))
+        return fail(LESBGK_EINVAL, "initial field at node %zu not admissible (rho, T > 0, finite)", k);
+      r0 = std::fmax(r0, r);
+      tmax = std::fmax(tmax, T);
+    }
+    rmax = r0;
+  }
+  const double pr = 1.0 / (1.0 - p.b);
+  h->tau_ref = (p.kn / pr) * std::pow(tmax, p.visc_exp - 1.0) / rmax;
+  const double hmin = std::fmin(h->dx, h->dy);
+  if (p.dt > 0.0) {
+    h->dt = p.dt;
+    if (h->cmax * h->dt / hmin > 1.0) return fail(LESBGK_EUNSTABLE, "CFL %.3f > 1", h->cmax * h->dt / hmin);
+    if (h->dt / h->tau_ref >= 2.0) return fail(LESBGK_EUNSTABLE, "dt/tau_ref = %.3f >= 2", h->dt / h->tau_ref);
+  } else {
+    h->dt = std::fmin(p.cfl * hmin / h->cmax, h->tau_ref);
+  }
+  const double dt = h->dt;
+  double fact[kMaxOrder + 1] = {1, 1, 2, 6, 24};
+  for (int i = 0; i < nr; ++i) {
+    double hv[kMaxOrder + 1];
+    hermite_values(kMaxOrder, c[i], hv);
+    A.c[i] = (float)c[i];
+    for (int m = 0; m <= kMaxOrder; ++m) {
+      A.he[i][m] = (float)hv[m];
+      A.hw[i][m] = (float)(w[i] * hv[m] / fact[m]);
+    }
+    A.ax[i] = (float)(c[i] * dt / h->dx);
+    A.kx[i] = (float)(0.5 * (1.0 - std::fabs(c[i]) * dt / h->dx));
+    A.ay[i] = (float)(c[i] * dt / h->dy);
+    A.ky[i] = (float)(0.5 * (1.0 - std::fabs(c[i]) * dt / h->dy));
+  }
+  // wall equilibria S_a(T_w, u_w) at order N (b = 0 Gaussian projection)
+  for (int s = 0; s < 2; ++s) {
+    double e[kMaxOrder + 1][kMaxOrder + 1];
+    const double th = p.wall_T[s] - 1.0;
+    gaussian_hermite_moments(N, 1.0, p.wall_ux[s], 0.0, th, 0.0, th, e);
+    double A_out = 0.0, Z_out = 0.0;
+    for (int ix = 0; ix < nr; ++ix) {
+      double hx[kMaxOrder + 1];
+      hermite_values(kMaxOrder, c[ix], hx);
+      for (int iy = 0; iy < nr; ++iy) {
+        double hy[kMaxOrder + 1];
+        hermite_values(kMaxOrder, c[iy], hy);
+        double sum = 0.0;
+        for (int m = 0; m <= N; ++m)
+          for (int k = 0; m + k <= N; ++k) sum += e[m][k] * hx[m] * hy[k] / (fact[m] * fact[k]);
+        const double wa = w[ix] * w[iy];
+        const double S = wa * sum;
+        const int a = ix * nr + iy;
+        A.wS[s][a] = (float)S;
+        A.wSdev[s][a] = (float)(S - wa);
+        const bool outgoing = (s == 0) ? (c[iy] > 0.0) : (c[iy] < 0.0);
+        if (outgoing) {
+          A_out += std::fabs(c[iy]) * (S - wa);
+          Z_out += std::fabs(c[iy]) * S;
+        }
+      }
+    }
+    A.wA[s] = (float)A_out;
+    A.wB[s] = (float)(1.0 / Z_out);
+  }
+  A.c_omega = (float)(dt / (p.kn * (1.0 - p.b)));
+  A.visc_pow = (float)(1.0 - p.visc_exp);
+  A.vmode = p.visc_exp == 0.5 ? 1 : (p.visc_exp == 1.0 ? 2 : 0);
+  A.b = (float)p.b;
+  A.beta = (float)(0.5 * (1.0 - p.b));
+  A.dtgx = (float)(dt * p.g[0]);
+  A.dtgy = (float)(dt * p.g[1]);
+  A.has_force = (p.g[0] != 0.0 || p.g[1] != 0.0) ? 1 : 0;
+  A.nx = p.nx;
+  A.ny = p.ny;
+  A.walls = p.bc_y == LESBGK_DIFFUSE ? 1 : 0;
+  A.plane = (long long)p.nx * p.ny;
+  return 0;
+}
+
+}  // namespace lesbgk_setup
+
+extern "C" const char *lesbgk_last_error(void) { return lesbgk_setup::last_error_buffer(); }

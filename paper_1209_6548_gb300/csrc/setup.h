@@ -1,0 +1,55 @@
+// Host-side set-up shared by the single-domain solver and the batched
+// solver: argument checks, the FP64 tables of Sec. 2.2 rounded to the kernels'
+// FP32 argument block, the time-step rule, and thread-local error messages.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lesbgk.h"
+
+namespace lesbgk_setup {
+
+constexpr int kMaxR = 6;
+constexpr int kMaxN = 4;
+constexpr int kMaxQ = kMaxR * kMaxR;
+
+// Kernel arguments: lattice tables and scalars, passed by value (constant bank).
+struct KArgs {
+  float c[kMaxR];              // 1D abscissae, ascending; c[NR-1-i] = -c[i]
+  float he[kMaxR][kMaxN + 1];  // He_m(c_i)
+  float hw[kMaxR][kMaxN + 1];  // w_i He_m(c_i) / m!
+  float ax[kMaxR], kx[kMaxR];  // c_i dt/dx and (1 - |c_i| dt/dx)/2
+  float ay[kMaxR], ky[kMaxR];  // same along y
+  float wS[2][kMaxQ];          // wall equilibrium S_a(T_w, u_w), [0] bottom, [1] top
+  float wSdev[2][kMaxQ];       // S_a - w_a
+  float wA[2], wB[2];          // sum_out |c_y|(S-w) and 1/sum_out |c_y| S
+  float c_omega;               // dt / (Kn (1-b)):  dt/tau = c_omega rho T^(1-varpi)
+  float visc_pow;              // 1 - varpi
+  float b, beta;               // b and (1-b)/2
+  float dtgx, dtgy;            // dt g
+  int nx, ny, walls, has_force, vmode;  // vmode 1: varpi = 1/2, 2: varpi = 1, 0: general
+  int rows, nstrips, nseg;
+  long long plane;             // nx*ny
+};
+
+// What one solve's set-up produces.
+struct Setup {
+  KArgs args;                      // tables and per-solve scalars (nx, ny, plane, walls filled)
+  double dt, dx, dy, cmax, tau_ref;
+};
+
+// Record a message for lesbgk_last_error() and return code.
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int cuda_fail(cudaError_t e, const char *where);
+void clear_error();
+const char *last_error_buffer();
+
+int default_order(int nroots);
+int check_params(const lesbgk_params *p);
+
+// Quadrature, Hermite and wall tables in FP64 (rounded to FP32 in args),
+// spacing, tau_ref and dt (Sec. 2.2; the dt rule is the library's reading).
+// h_init (host, double[4][ny][nx], may be NULL) enters tau_ref and is checked.
+int build_setup(const lesbgk_params &p, int order, const double *h_init, Setup *out);
+
+}  // namespace lesbgk_setup

@@ -29,7 +29,11 @@ MOMENT_NAMES = ("rho", "ux", "uy", "T", "sxx", "sxy", "syy", "qx", "qy")
 SYMBOLS = ("lesbgk_workspace_size", "lesbgk_create", "lesbgk_reinit", "lesbgk_step", "lesbgk_moments",
            "lesbgk_moments_host", "lesbgk_get_populations", "lesbgk_set_populations",
            "lesbgk_set_launch", "lesbgk_get_info", "lesbgk_destroy", "lesbgk_moments_noalloc",
-           "lesbgk_last_error")
+           "lesbgk_last_error",
+           "lesbgk_batch_workspace_size", "lesbgk_batch_slot_bytes", "lesbgk_batch_create", "lesbgk_batch_add",
+           "lesbgk_batch_remove", "lesbgk_batch_step", "lesbgk_batch_residuals", "lesbgk_batch_moments",
+           "lesbgk_batch_get_populations", "lesbgk_batch_get_info", "lesbgk_batch_set_rows",
+           "lesbgk_batch_autotune", "lesbgk_batch_pool_free", "lesbgk_batch_destroy")
 
 
 class Params(C.Structure):
@@ -84,6 +88,21 @@ def lib():
             L.lesbgk_get_info.argtypes = [vp, C.POINTER(Info)]
             L.lesbgk_destroy.argtypes = [vp]
             L.lesbgk_moments_noalloc.argtypes = [C.POINTER(Params), vp, vp, vp, vp]
+            sz, i32 = C.c_size_t, C.c_int32
+            L.lesbgk_batch_workspace_size.argtypes = [i32, sz, C.POINTER(sz)]
+            L.lesbgk_batch_slot_bytes.argtypes = [C.POINTER(Params), C.POINTER(sz)]
+            L.lesbgk_batch_create.argtypes = [i32, i32, vp, sz, vp, C.POINTER(vp)]
+            L.lesbgk_batch_add.argtypes = [vp, C.POINTER(Params), vp, vp, C.POINTER(i32)]
+            L.lesbgk_batch_remove.argtypes = [vp, i32, vp]
+            L.lesbgk_batch_step.argtypes = [vp, i64, vp]
+            L.lesbgk_batch_residuals.argtypes = [vp, vp, vp]
+            L.lesbgk_batch_moments.argtypes = [vp, i32, vp, vp, vp]
+            L.lesbgk_batch_get_populations.argtypes = [vp, i32, vp, vp]
+            L.lesbgk_batch_get_info.argtypes = [vp, i32, C.POINTER(Info)]
+            L.lesbgk_batch_set_rows.argtypes = [vp, i32, vp]
+            L.lesbgk_batch_autotune.argtypes = [vp, vp, i32, C.POINTER(i32), vp]
+            L.lesbgk_batch_pool_free.argtypes = [vp, C.POINTER(sz), C.POINTER(sz)]
+            L.lesbgk_batch_destroy.argtypes = [vp]
             L.lesbgk_last_error.restype = C.c_char_p
             L.lesbgk_last_error.argtypes = []
             _lib = L
@@ -255,6 +274,119 @@ class Solver:
     def close(self) -> None:
         if getattr(self, "handle", None):
             destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- batched solver
+def batch_workspace_size(capacity: int, pool_bytes: int) -> int:
+    n = C.c_size_t()
+    _check(lib().lesbgk_batch_workspace_size(C.c_int32(capacity), C.c_size_t(pool_bytes), C.byref(n)))
+    return int(n.value)
+
+
+def batch_slot_bytes(p: Params) -> int:
+    n = C.c_size_t()
+    _check(lib().lesbgk_batch_slot_bytes(C.byref(p), C.byref(n)))
+    return int(n.value)
+
+
+class Batch:
+    """A batch of independent narrow solves (C ABI lesbgk_batch_*) in one
+    torch-allocated workspace: `capacity` slots and a pool of `pool_bytes`."""
+
+    def __init__(self, capacity: int, nx: int, pool_bytes: int, stream=None):
+        import torch
+        self._torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.capacity, self.nx = capacity, nx
+        self.nbytes = batch_workspace_size(capacity, pool_bytes)
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device="cuda")
+        h = C.c_void_p()
+        _check(lib().lesbgk_batch_create(C.c_int32(capacity), C.c_int32(nx), C.c_void_p(self.workspace.data_ptr()),
+                                         C.c_size_t(self.nbytes), C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self.handle = h.value
+        self.params = {}
+
+    @property
+    def _s(self):
+        return C.c_void_p(self.stream.cuda_stream)
+
+    def add(self, p: Params, h_init=None) -> int:
+        ptr = None
+        if h_init is not None:
+            arr = np.ascontiguousarray(h_init, dtype=np.float64)
+            assert arr.shape == (4, p.ny, p.nx)
+            ptr = arr.ctypes.data
+        slot = C.c_int32()
+        _check(lib().lesbgk_batch_add(C.c_void_p(self.handle), C.byref(p), C.c_void_p(ptr), self._s, C.byref(slot)))
+        self.params[slot.value] = p
+        return slot.value
+
+    def try_add(self, p: Params, h_init=None):
+        """add(), or None when the pool or the slots are full."""
+        try:
+            return self.add(p, h_init)
+        except LesbgkError as e:
+            if e.code == ESPACE:
+                return None
+            raise
+
+    def remove(self, slot: int) -> None:
+        _check(lib().lesbgk_batch_remove(C.c_void_p(self.handle), C.c_int32(slot), self._s))
+        self.params.pop(slot, None)
+
+    def step(self, n: int) -> None:
+        _check(lib().lesbgk_batch_step(C.c_void_p(self.handle), C.c_int64(n), self._s))
+
+    def residuals(self) -> np.ndarray:
+        out = np.empty(self.capacity)
+        _check(lib().lesbgk_batch_residuals(C.c_void_p(self.handle), C.c_void_p(out.ctypes.data), self._s))
+        return out
+
+    def moments(self, slot: int, sums: bool = False):
+        p = self.params[slot]
+        out = self._torch.empty((9, p.ny, p.nx), dtype=self._torch.float32, device="cuda")
+        hs = np.zeros(4) if sums else None
+        _check(lib().lesbgk_batch_moments(C.c_void_p(self.handle), C.c_int32(slot), C.c_void_p(out.data_ptr()),
+                                          C.c_void_p(None if hs is None else hs.ctypes.data), self._s))
+        return (out, hs) if sums else out
+
+    def populations(self, slot: int):
+        p = self.params[slot]
+        out = self._torch.empty((p.nroots * p.nroots, p.ny, p.nx), dtype=self._torch.float32, device="cuda")
+        _check(lib().lesbgk_batch_get_populations(C.c_void_p(self.handle), C.c_int32(slot),
+                                                  C.c_void_p(out.data_ptr()), self._s))
+        return out
+
+    def info(self, slot: int) -> Info:
+        out = Info()
+        _check(lib().lesbgk_batch_get_info(C.c_void_p(self.handle), C.c_int32(slot), C.byref(out)))
+        return out
+
+    def set_rows(self, rows: int) -> None:
+        _check(lib().lesbgk_batch_set_rows(C.c_void_p(self.handle), C.c_int32(rows), self._s))
+
+    def autotune(self, candidates=(8, 16, 32, 64, 128)) -> int:
+        arr = (C.c_int32 * len(candidates))(*candidates)
+        chosen = C.c_int32()
+        _check(lib().lesbgk_batch_autotune(C.c_void_p(self.handle), arr, C.c_int32(len(candidates)),
+                                           C.byref(chosen), self._s))
+        return chosen.value
+
+    def pool_free(self):
+        a, t = C.c_size_t(), C.c_size_t()
+        _check(lib().lesbgk_batch_pool_free(C.c_void_p(self.handle), C.byref(a), C.byref(t)))
+        return a.value, t.value
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            lib().lesbgk_batch_destroy(C.c_void_p(self.handle))
             self.handle = None
 
     def __del__(self):

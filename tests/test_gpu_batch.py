@@ -1,0 +1,151 @@
+"""Batched solver (lesbgk_batch_*): each slot gives, bitwise, what the same
+problem gives alone through lesbgk_create/lesbgk_step, whatever else is in
+the batch and whenever slots come and go; and a batch slot matches the FP64
+oracle like the single-domain solver does."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1209_6548_gb300 import build as B
+from paper_1209_6548_gb300 import inputs as I
+from paper_1209_6548_gb300 import lesbgk as L
+from tests.common import field_errors, oracle_params, time_step
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+
+
+def mixed_problems(nx=4, n=10, seed=3, with_q36=True):
+    probs = I.batch_mix(n=n, seed=seed, ny_lo=16, ny_hi=200)
+    out = []
+    for k, p in enumerate(probs):
+        kw = dict(nx=nx)
+        if with_q36 and k % 4 == 3:
+            kw["nroots"] = 6
+        from dataclasses import replace
+        out.append(replace(p, **kw))
+    return out
+
+
+def alone(prob, steps):
+    s = L.Solver(L.params_from_problem(prob))
+    s.step(steps)
+    return s.populations().cpu().numpy(), s.info.dt
+
+
+def pool_for(probs, slack=2.0):
+    return int(sum(L.batch_slot_bytes(L.params_from_problem(p)) for p in probs) * slack) + (1 << 20)
+
+
+def test_batch_equals_alone_bitwise():
+    probs = mixed_problems()
+    bt = L.Batch(capacity=16, nx=4, pool_bytes=pool_for(probs))
+    slots = [bt.add(L.params_from_problem(p)) for p in probs]
+    steps = 64 * 2 + 7  # two graph replays and seven direct steps
+    bt.step(steps)
+    for p, sl in zip(probs, slots):
+        ref, dt = alone(p, steps)
+        got = bt.populations(sl).cpu().numpy()
+        assert bt.info(sl).dt == dt
+        assert bt.info(sl).steps_done == steps
+        assert np.array_equal(got, ref), p.name
+
+
+def test_slots_come_and_go():
+    probs = mixed_problems(n=8, seed=5)
+    bt = L.Batch(capacity=8, nx=4, pool_bytes=pool_for(probs))
+    slots = [bt.add(L.params_from_problem(p)) for p in probs[:6]]
+    bt.step(70)
+    bt.remove(slots[2])
+    bt.remove(slots[4])
+    late = [bt.add(L.params_from_problem(p)) for p in probs[6:8]]
+    bt.step(65)
+    for i in (0, 1, 3, 5):
+        ref, _ = alone(probs[i], 135)
+        assert np.array_equal(bt.populations(slots[i]).cpu().numpy(), ref)
+    for k, sl in enumerate(late):
+        ref, _ = alone(probs[6 + k], 65)
+        assert np.array_equal(bt.populations(sl).cpu().numpy(), ref)
+
+
+def test_autotune_keeps_state_and_rows_do_not_change_bits():
+    probs = mixed_problems(n=6, seed=7)
+    bt = L.Batch(capacity=8, nx=4, pool_bytes=pool_for(probs))
+    slots = [bt.add(L.params_from_problem(p)) for p in probs]
+    bt.step(11)
+    before = [bt.populations(s).cpu().numpy() for s in slots]
+    chosen = bt.autotune((4, 16, 32, 64))
+    assert chosen in (4, 16, 32, 64)
+    for s, b0 in zip(slots, before):
+        assert np.array_equal(bt.populations(s).cpu().numpy(), b0)
+    bt.set_rows(5)
+    bt.step(80)
+    for p, s in zip(probs, slots):
+        ref, _ = alone(p, 91)
+        assert np.array_equal(bt.populations(s).cpu().numpy(), ref)
+
+
+def test_residuals_decay_and_first_call_is_nan():
+    prob = I.Problem(name="c", nx=4, ny=24, kn=0.2, b=-0.5, wall_ux=(-0.05, 0.05))
+    bt = L.Batch(capacity=4, nx=4, pool_bytes=pool_for([prob]))
+    s = bt.add(L.params_from_problem(prob))
+    r0 = bt.residuals()
+    assert np.isnan(r0).all()
+    rs = []
+    for _ in range(5):
+        bt.step(200)
+        rs.append(bt.residuals()[s])
+    assert all(np.isfinite(rs)) and rs[-1] < rs[0] * 0.5
+
+
+def test_pool_exhaustion_and_slot_limit():
+    prob = I.Problem(name="c", nx=4, ny=100, kn=0.1, b=0.0)
+    p = L.params_from_problem(prob)
+    one = L.batch_slot_bytes(p)
+    bt = L.Batch(capacity=8, nx=4, pool_bytes=3 * one + 100)
+    got = [bt.try_add(p) for _ in range(5)]
+    assert got[:3] == [0, 1, 2] and got[3] is None and got[4] is None
+    bt.remove(1)
+    assert bt.try_add(p) == 1
+    small = L.Batch(capacity=2, nx=4, pool_bytes=10 * one)
+    assert [small.try_add(p) for _ in range(3)][2] is None
+
+
+@pytest.mark.parametrize("nx", [1, 2, 8, 32])
+def test_other_widths(nx):
+    probs = mixed_problems(nx=nx, n=5, seed=nx, with_q36=(nx != 32))
+    bt = L.Batch(capacity=8, nx=nx, pool_bytes=pool_for(probs))
+    slots = [bt.add(L.params_from_problem(p)) for p in probs]
+    bt.step(66)
+    for p, s in zip(probs, slots):
+        ref, _ = alone(p, 66)
+        assert np.array_equal(bt.populations(s).cpu().numpy(), ref)
+
+
+def test_batch_slot_matches_oracle():
+    prob = I.Problem(name="p", nx=4, ny=40, kn=0.1, b=0.5, g=(1e-3, 0.0), wall_T=(0.97, 1.02))
+    bt = L.Batch(capacity=4, nx=4, pool_bytes=pool_for([prob]))
+    s = bt.add(L.params_from_problem(prob))
+    bt.step(300)
+    dt = time_step(prob)
+    op = oracle_params(prob, dt)
+    ref, _ = O.moments(op, O.run(op, O.init(op), 300))
+    errs = field_errors(bt.moments(s).cpu().numpy(), ref)
+    assert all(v[0] <= 1e-5 for v in errs.values()), errs
+
+
+def test_mismatched_nx_rejected():
+    bt = L.Batch(capacity=2, nx=4, pool_bytes=1 << 20)
+    with pytest.raises(L.LesbgkError):
+        bt.add(L.make_params(nx=8, ny=16, kn=0.1, b=0.0))
+    with pytest.raises(L.LesbgkError):
+        bt.add(L.make_params(nx=4, ny=16, kn=0.1, b=0.0, nroots=4, order=4))
