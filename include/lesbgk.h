@@ -194,11 +194,13 @@ int lesbgk_batch_slot_bytes(const lesbgk_params *p, size_t *bytes);
 int lesbgk_batch_create(int32_t capacity, int32_t nx, void *d_workspace, size_t bytes, void *stream,
                         lesbgk_batch **out);
 /* Admit a solve: tables, dt and the initial populations exactly as
- * lesbgk_create (h_init: HOST double[4][ny][nx] or NULL); *slot receives its
- * slot index.  Synchronises the stream. */
+ * lesbgk_create (h_init: HOST double[4][ny][nx] or NULL, copied before the
+ * call returns); *slot receives its slot index.  The initialisation is queued
+ * on the stream; the work list is rebuilt at the next step. */
 int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const double *h_init, void *stream,
                      int32_t *slot);
-/* Retire a slot and return its buffers to the pool. */
+/* Retire a slot and return its buffers to the pool (synchronises the stream
+ * first, so no queued step still reads them). */
 int lesbgk_batch_remove(lesbgk_batch *b, int32_t slot, void *stream);
 int lesbgk_batch_step(lesbgk_batch *b, int64_t nsteps, void *stream);
 /* Steady-state residual of every slot since the previous call:

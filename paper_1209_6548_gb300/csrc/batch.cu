@@ -365,6 +365,7 @@ struct lesbgk_batch {
   cudaGraphExec_t graph = nullptr;
   int graph_grid[kNumClasses] = {0, 0};
   bool graph_dirty = true;
+  bool items_dirty = false;  // slots changed since the work list was uploaded
 };
 
 namespace {
@@ -464,12 +465,16 @@ int rebuild_items(lesbgk_batch *b, cudaStream_t s) {
   if (!b->items.empty())
     e = cudaMemcpyAsync(b->d_items, b->items.data(), sizeof(WorkItem) * b->items.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_range, b->range, sizeof(b->range), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host staging vectors are reused
+  // (pageable sources: the copies are staged before cudaMemcpyAsync returns,
+  // so the host vectors may change afterwards)
   if (e != cudaSuccess) return cuda_fail(e, "work list upload");
+  b->items_dirty = false;
   for (int cls = 0; cls < kNumClasses; ++cls)
     if ((int)step_grid(b, b->range[cls][1]) > b->graph_grid[cls]) b->graph_dirty = true;
   return 0;
 }
+
+int ensure_items(lesbgk_batch *b, cudaStream_t s) { return b->items_dirty ? rebuild_items(b, s) : 0; }
 
 void drop_graph(lesbgk_batch *b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
@@ -669,17 +674,20 @@ extern "C" int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const d
     dfields = reinterpret_cast<const double *>(D.f[b->par ^ 1]);
   }
   if (e == cudaSuccess) e = lesbgk_internal::launch_init(A, sl.nr, order, dfields, D.f[b->par], b->sm_count, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host descriptor and h_init are reused
+  if (e == cudaSuccess && h_init) {
+    // a pageable h_init is staged before cudaMemcpyAsync returns; a pinned
+    // one is read asynchronously, so wait for the copy before returning
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, h_init) == cudaSuccess && at.type == cudaMemoryTypeHost)
+      e = cudaStreamSynchronize(s);
+    cudaGetLastError();
+  }
   if (e != cudaSuccess) {
     b->pool.release(off, need);
     return cuda_fail(e, "slot initialisation");
   }
   sl.used = true;
-  if (int rc = rebuild_items(b, s)) {
-    sl.used = false;
-    b->pool.release(off, need);
-    return rc;
-  }
+  b->items_dirty = true;  // the work list is rebuilt before the next step
   *slot_out = slot;
   return 0;
 }
@@ -687,8 +695,12 @@ extern "C" int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const d
 extern "C" int lesbgk_batch_remove(lesbgk_batch *b, int32_t slot, void *stream) {
   if (!b || slot < 0 || slot >= b->capacity || !b->slots[slot].used) return fail(LESBGK_EINVAL, "no such slot");
   auto &sl = b->slots[slot];
+  // the slot's buffers may still be read by queued steps: order the release
+  // after them on the stream, then rebuild the work list
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "slot removal");
   sl.used = false;
-  if (int rc = rebuild_items(b, static_cast<cudaStream_t>(stream))) return rc;
+  b->items_dirty = true;
   b->pool.release(sl.off, sl.bytes);
   return 0;
 }
@@ -697,6 +709,7 @@ extern "C" int lesbgk_batch_step(lesbgk_batch *b, int64_t nsteps, void *stream) 
   if (!b) return fail(LESBGK_EINVAL, "batch is NULL");
   if (nsteps < 0) return fail(LESBGK_EINVAL, "nsteps < 0");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (int rc = ensure_items(b, s)) return rc;
   cudaError_t e = cudaSuccess;
   auto direct_step = [&]() {
     for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls)
@@ -729,6 +742,7 @@ extern "C" int lesbgk_batch_step(lesbgk_batch *b, int64_t nsteps, void *stream) 
 extern "C" int lesbgk_batch_residuals(lesbgk_batch *b, double *h_res, void *stream) {
   if (!b || !h_res) return fail(LESBGK_EINVAL, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (int rc = ensure_items(b, s)) return rc;
   cudaError_t e = cudaMemsetAsync(b->d_res, 0, sizeof(unsigned) * b->capacity, s);
   for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls) {
     const int n = b->range[cls][1];
