@@ -602,3 +602,24 @@ def test_taylor_green_stable_only_split():
     with np.errstate(invalid="ignore"):
         mu, _ = O.moments(pu, fu)
         assert not np.all(np.isfinite(mu)) or np.abs(mu[1]).max() > 0.1
+
+
+def test_fourier_walls_exchange_mass_at_a_constant_rate():
+    """The diffuse-wall rule of Sec. 3.2 as read balances the normal mass flux
+    at the wall node but replaces the node's outgoing half by rho_W S: when the
+    wall temperature differs from the gas next to it, that replacement adds or
+    removes a little mass every step.  In the FP64 oracle the total mass of a
+    Fourier channel changes at a constant rate once the transients have
+    decayed (so its steady state is a constant drift); with the wall at the
+    gas temperature (rest between walls at T_w = 1) mass is exactly conserved
+    (test_rest_between_walls_stays_at_rest)."""
+    prob = Problem(name="f", nroots=4, nx=1, ny=32, bc_y=DIFFUSE, kn=0.1, b=-0.5, wall_T=(0.95, 1.05))
+    p = oracle_params(prob, time_step(prob))
+    f = O.run(p, O.init(p), 3000)
+    masses = []
+    for _ in range(4):
+        masses.append(O.moments(p, f)[1][0])
+        f = O.run(p, f, 500)
+    d = np.diff(masses)
+    assert np.all(d > 0) and np.ptp(d) < 1e-3 * abs(d.mean())
+    assert 1e-5 < d.mean() / masses[0] < 1e-3
