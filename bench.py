@@ -45,9 +45,11 @@ def parse():
     ap.add_argument("--lattice-steps", type=int, default=1000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["tgv", "batch", "serve"], default="tgv",
+    ap.add_argument("--workload", choices=["tgv", "batch", "serve", "precision"], default="tgv",
                     help="tgv: 4096^2 Taylor-Green throughput (default); batch: 512-instance channel mix; "
                          "serve: Poisson arrivals run to steady state with continuous batching")
+    ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
+                    help="population storage for the tgv workload (compute is FP32)")
     ap.add_argument("--requests", type=int, default=400)
     ap.add_argument("--rate", type=float, default=200.0, help="mean arrivals per second")
     ap.add_argument("--pool-mb", type=float, default=64.0, help="device-memory budget of the serving pool")
@@ -90,8 +92,9 @@ def committed_traffic(source_digest: str):
 def source_digest():
     import hashlib
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1209_6548_gb300", "csrc", "lesbgk.cu"), "rb") as fh:
-        h.update(fh.read())
+    for name in ("lesbgk.cu", "device.cuh"):
+        with open(os.path.join(ROOT, "paper_1209_6548_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -357,6 +360,100 @@ def run_serve(args, world, rank, local):
     return 0
 
 
+def run_precision(args, world, rank, local):
+    """Per-field error of FP32, FP16 and BF16 population storage (FP32 compute)
+    against the FP64 oracle: a 256^2 Taylor-Green vortex (split scheme) and the
+    force-driven Poiseuille channel (g = 1e-4, Kn 0.2, b = 0, ny = 1024; the
+    flow does not vary in x, so a 4-node-wide periodic slice computes the same
+    solution as the 512-wide channel), 1000 steps each.  Error per field:
+    e = max|gpu - ref| / max(scale of its quantity, floor) as in the parity
+    tests, and e' = max|gpu - ref| / max|ref - rest| (the perturbation)."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from dataclasses import replace
+    from paper_1209_6548_gb300 import build as B
+    from paper_1209_6548_gb300 import inputs as I
+    from paper_1209_6548_gb300 import lesbgk as L
+
+    torch.cuda.set_device(local)
+    B.build()
+    O.set_threads(len(os.sched_getaffinity(0)))
+    steps = 1000
+    cases = [("tgv256", I.tgv(256, steps=steps)), ("poiseuille_1024", I.poiseuille(nx=4, ny=1024, steps=steps))]
+    groups = {"rho": ["rho"], "T": ["T"], "u": ["ux", "uy"], "sigma": ["sxx", "sxy", "syy"], "q": ["qx", "qy"]}
+    floor = {"rho": 0.0, "T": 0.0, "u": 1e-3, "sigma": 1e-3, "q": 3e-3}
+    names = list(O.MOMENT_NAMES)
+    rest = np.zeros(9)
+    rest[0] = rest[3] = 1.0
+    out = {}
+    t_or = 0.0
+    for cname, prob in cases:
+        fields = I.initial_fields(prob) if prob.init == "tgv" else None
+        # the time step rule of the library, restated (c_max of the 4-point rule)
+        c, _ = O.gauss_hermite_1d(prob.nroots)
+        dx = 1.0 / prob.nx if prob.bc_y == I.PERIODIC else 1.0 / (prob.ny - 1)
+        dy = 1.0 / prob.ny if prob.bc_y == I.PERIODIC else 1.0 / (prob.ny - 1)
+        s0 = L.Solver(L.params_from_problem(prob), h_init=fields)
+        dt = s0.info.dt
+        s0.close()
+        op = O.make_params(nroots=prob.nroots, order=3, nx=prob.nx, ny=prob.ny, bc_y=prob.bc_y, kn=prob.kn,
+                           b=prob.b, visc_exp=prob.visc_exp, dt=dt, dx=dx, dy=dy, wall_T=prob.wall_T,
+                           wall_ux=prob.wall_ux, g=prob.g, scheme=prob.scheme)
+        t0 = time.perf_counter()
+        ref, _ = O.moments(op, O.run(op, O.init(op, fields), steps))
+        t_or += time.perf_counter() - t0
+        for st_name, st in (("f32", L.F32), ("f16", L.F16), ("bf16", L.BF16)):
+            p = L.params_from_problem(prob, dt=dt)
+            p.storage = st
+            s = L.Solver(p, h_init=fields)
+            s.step(steps)
+            g = s.moments().cpu().numpy().astype(np.float64)
+            s.close()
+            row = {}
+            for grp, mem in groups.items():
+                scale = max(max(float(np.max(np.abs(ref[names.index(m)]))) for m in mem), floor[grp])
+                for m in mem:
+                    k = names.index(m)
+                    d = float(np.max(np.abs(g[k] - ref[k])))
+                    pert = float(np.max(np.abs(ref[k] - rest[k])))
+                    row[m] = {"e": d / scale, "e_pert": (d / pert) if pert > 1e-6 else None, "abs": d}
+            out.setdefault(cname, {})[st_name] = row
+    # throughput of 16-bit storage on the 4096^2 case
+    thr = {}
+    n = 4096
+    prob = I.tgv(n)
+    fields = I.initial_fields(prob)
+    stream = torch.cuda.current_stream()
+    for st_name, st in (("f32", L.F32), ("f16", L.F16), ("bf16", L.BF16)):
+        p = L.params_from_problem(prob)
+        p.storage = st
+        s = L.Solver(p, h_init=fields, stream=stream)
+        s.step(20)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(200)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 200
+        bpl = 128 if st == L.F32 else 64
+        thr[st_name] = {"mlups": n * n / (ms / 1e3) / 1e6, "kernel_ms": ms,
+                        "gbs": bpl * n * n / (ms / 1e3) / 1e9, "bytes_per_lup": bpl}
+        s.close()
+    peak, peak_kind = measured_peak()
+    worst = {st: max(max(v["e"] for v in out[c][st].values()) for c in out) for st in ("f32", "f16", "bf16")}
+    line = {"metric": "per-field error vs FP64 oracle by population storage", "value": worst["f16"],
+            "unit": "max relative error (FP16 storage)", "n_gpus": world, "steps": steps, "warmup": 0,
+            "higher_is_better": False, "dtype": "f32 compute", "data": "synthetic",
+            "config": {"workload": "precision_tgv256_poiseuille1024", "lattice_steps": steps,
+                       "cases": [c for c, _ in cases]},
+            "worst_e": worst, "errors": out, "throughput_4096": thr, "peak_gbs": peak,
+            "oracle_seconds": t_or, "cpu_cores": O.get_threads()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
@@ -366,6 +463,8 @@ def main():
         return run_batch(args, world, rank, local)
     if args.workload == "serve":
         return run_serve(args, world, rank, local)
+    if args.workload == "precision":
+        return run_precision(args, world, rank, local)
 
     import numpy as np
     import torch
@@ -398,6 +497,7 @@ def main():
     prob = I.tgv(n, steps=nsteps)
     fields = I.initial_fields(prob)
     params = L.params_from_problem(prob, dt=0.0)
+    params.storage = {"f32": L.F32, "f16": L.F16, "bf16": L.BF16}[args.storage]
     stream = torch.cuda.current_stream()
     d_fields = torch.from_numpy(fields).cuda()
     solver = L.Solver(params, h_init=fields, stream=stream)
@@ -465,7 +565,8 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     peak, peak_kind = measured_peak()
-    achieved = BYTES_PER_LUP * cells / (kernel_ms / 1e3) / 1e9
+    bytes_per_lup = BYTES_PER_LUP if args.storage == "f32" else BYTES_PER_LUP // 2
+    achieved = bytes_per_lup * cells / (kernel_ms / 1e3) / 1e9
     digest = source_digest()
     traffic = committed_traffic(digest)
     base = None
@@ -477,14 +578,15 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"tgv_{n}x{n}_d2q16_fp32", "nx": n, "ny": n, "velocity_set": "D2Q16",
+            "config": {"workload": f"tgv_{n}x{n}_d2q16_{args.storage}", "nx": n, "ny": n, "velocity_set": "D2Q16",
+                       "storage": args.storage,
                        "order": 3, "kn": prob.kn, "b": prob.b, "lattice_steps_per_step": nsteps,
                        "l2": "inputs larger than L2 (two 1.07 GB population buffers)",
                        "parallelism": f"replica x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                         "kernel": f"k_step<4,3,{shape[0]},split> rows={shape[1]}", "kernel_ms": kernel_ms,
-                         "bytes_per_lup": BYTES_PER_LUP, "source_sha256": digest},
+                         "kernel": f"k_step<4,3,split,{args.storage}> rows={shape[1]}", "kernel_ms": kernel_ms,
+                         "bytes_per_lup": bytes_per_lup, "source_sha256": digest},
             "cpu_baseline": base,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,

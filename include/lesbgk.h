@@ -59,7 +59,18 @@ extern "C" {
 #define LESBGK_PERIODIC 0
 #define LESBGK_DIFFUSE 1
 
+/* Population storage (compute is always FP32).  LESBGK_F32 stores the
+ * deviation f_a - w_a; LESBGK_F16 and LESBGK_BF16 store the relative deviation
+ * (f_a - w_a)/w_a (times 2^10 in FP16, to stay in its normal range), halving
+ * the bytes per lattice update.  Each step's stores
+ * round stochastically (8 random bits from a counter-based hash of the step,
+ * the row and the population -- not the column, so a flow uniform in x stays
+ * uniform -- hence reproducible and independent of the launch shape); initial
+ * and set populations round to nearest.  16-bit storage is
+ * built for the default orders (D2Q16 N = 3, D2Q36 N = 4). */
 #define LESBGK_F32 0
+#define LESBGK_F16 1
+#define LESBGK_BF16 2
 
 /* Advection schemes.  LESBGK_UNSPLIT is the update of Sec. 3.1 as printed:
  * both flux differences are taken from f^n.  For flows that vary in both x
@@ -78,7 +89,7 @@ typedef struct lesbgk_params {
   int32_t order;        /* Hermite order N of f_ES (3 or 4); 0 = 3 for D2Q16, 4 for D2Q36 */
   int32_t nx, ny;       /* nodes; nx >= 1; ny >= 1 (>= 2 with walls) */
   int32_t bc_y;         /* LESBGK_PERIODIC or LESBGK_DIFFUSE */
-  int32_t storage;      /* LESBGK_F32 */
+  int32_t storage;      /* LESBGK_F32, LESBGK_F16 or LESBGK_BF16 */
   int32_t scheme;       /* LESBGK_UNSPLIT (default) or LESBGK_SPLIT */
   double kn;            /* Knudsen number of Sec. 2.2, > 0 */
   double b;             /* ES parameter, -1/2 <= b < 1 (b = 1 gives tau = 0) */

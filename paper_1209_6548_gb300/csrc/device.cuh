@@ -8,6 +8,8 @@
 //   TW: wall tables wS[2][Q], wSdev[2][Q], wA[2], wB[2]
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace lesbgk_dev {
@@ -260,13 +262,64 @@ __device__ __forceinline__ void wall_fix(float (&O)[NR * NR], int side, const TT
 // All populations of a group share the sign of c_y, so one vector load serves
 // one stencil row; a node's populations move as Q/V vector loads and stores.
 // ---------------------------------------------------------------------------
-template <int NR>
+// Storage of one population: FP32 holds df itself; the 16-bit types hold the
+// relative deviation s = df / w_a (rounded to nearest), which gives every
+// population the same relative precision whatever its weight.
+template <class S>
+struct Store;
+template <>
+struct Store<float> {
+  static constexpr bool kScaled = false;
+  __device__ static float get(float v, float) { return v; }
+  __device__ static float put(float x, float) { return x; }
+};
+template <>
+struct Store<__half> {
+  static constexpr bool kScaled = true;
+  __device__ static float get(__half v, float w) { return __half2float(v) * w; }
+  __device__ static __half put(float x, float iw) { return __float2half_rn(x * iw); }
+  // stochastic rounding: 8 random bits added just below the 10 kept mantissa
+  // bits, then truncation (FP32 has 13 more mantissa bits than FP16)
+  __device__ static __half put_sr(float x, float iw, unsigned r8) {
+    const unsigned u = __float_as_uint(x * iw) + (r8 << 5);
+    return __float2half_rz(__uint_as_float(u));
+  }
+};
+template <>
+struct Store<__nv_bfloat16> {
+  static constexpr bool kScaled = true;
+  __device__ static float get(__nv_bfloat16 v, float w) { return __bfloat162float(v) * w; }
+  __device__ static __nv_bfloat16 put(float x, float iw) { return __float2bfloat16_rn(x * iw); }
+  // stochastic rounding: 8 random bits just below the 7 kept mantissa bits
+  __device__ static __nv_bfloat16 put_sr(float x, float iw, unsigned r8) {
+    const unsigned u = __float_as_uint(x * iw) + (r8 << 8);
+    return __float2bfloat16_rz(__uint_as_float(u));
+  }
+};
+
+// 32-bit integer mixer (the "lowbias32" finaliser published by C. Wellons):
+// a bijection with good avalanche, used as a counter-based random generator.
+__device__ __forceinline__ unsigned mix32(unsigned x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+__host__ __device__ constexpr int pick_vector(int half, int bytes) {
+  return (half % 8 == 0 && 8 * bytes <= 16) ? 8 : (half % 4 == 0 && 4 * bytes <= 16) ? 4 : (half % 2 == 0) ? 2 : 1;
+}
+
+template <int NR, class S = float>
 struct Layout {
   static constexpr int Q = NR * NR;
   static constexpr int H = NR / 2;
   static constexpr int HALF = Q / 2;
-  static constexpr int V = (HALF % 4 == 0) ? 4 : 2;
-  static constexpr int G = Q / V;
+  static constexpr int V = pick_vector(HALF, (int)sizeof(S));  // populations per vector
+  static constexpr int G = Q / V;                               // vectors (groups) per node
+  static constexpr int VB = V * (int)sizeof(S);                 // bytes per vector
   __host__ __device__ static constexpr int alpha(int s) {
     return (s % HALF) / H * NR + ((s / HALF) ? H : 0) + (s % HALF) % H;
   }
@@ -278,6 +331,15 @@ template <>
 struct VecT<2> { using T = float2; };
 template <>
 struct VecT<4> { using T = float4; };
+
+template <int B>
+struct Raw;
+template <>
+struct Raw<16> { using T = uint4; };
+template <>
+struct Raw<8> { using T = uint2; };
+template <>
+struct Raw<4> { using T = unsigned; };
 
 // Load group g of one node (p points at the node's row, group 0) into F[alpha].
 template <int NR>
@@ -299,6 +361,80 @@ __device__ __forceinline__ void st_group(float *p, long long gstride, int g, con
 #pragma unroll
   for (int k = 0; k < L::V; ++k) e[k] = F[L::alpha(g * L::V + k)];
   *reinterpret_cast<T *>(p + g * gstride) = v;
+}
+
+// The same for any storage type S: one raw vector per group, converted to
+// FP32 deviations (TT provides wq[a] = w_a and iwq[a] = 1/w_a).
+template <int NR, class S, class TT>
+__device__ __forceinline__ void unpack_group(const typename Raw<Layout<NR, S>::VB>::T &raw, int g,
+                                             float (&F)[NR * NR], const TT &Tt) {
+  using L = Layout<NR, S>;
+  const S *e = reinterpret_cast<const S *>(&raw);
+#pragma unroll
+  for (int k = 0; k < L::V; ++k) {
+    const int a = L::alpha(g * L::V + k);
+    F[a] = Store<S>::get(e[k], Store<S>::kScaled ? Tt.wq[a] : 1.0f);
+  }
+}
+
+template <int NR, class S, class TT>
+__device__ __forceinline__ void ld_group_s(const S *p, long long gstride, int g, float (&F)[NR * NR], const TT &Tt) {
+  using R = typename Raw<Layout<NR, S>::VB>::T;
+  const R raw = __ldg(reinterpret_cast<const R *>(p + g * gstride));
+  unpack_group<NR, S>(raw, g, F, Tt);
+}
+
+template <int NR, class S, class TT>
+__device__ __forceinline__ void st_group_s(S *p, long long gstride, int g, const float (&F)[NR * NR],
+                                           const TT &Tt) {
+  using L = Layout<NR, S>;
+  using R = typename Raw<L::VB>::T;
+  R raw;
+  S *e = reinterpret_cast<S *>(&raw);
+#pragma unroll
+  for (int k = 0; k < L::V; ++k) {
+    const int a = L::alpha(g * L::V + k);
+    e[k] = Store<S>::put(F[a], Store<S>::kScaled ? Tt.iwq[a] : 1.0f);
+  }
+  *reinterpret_cast<R *>(p + g * gstride) = raw;
+}
+
+// Store with stochastic rounding for the 16-bit types (FP32 stores as is): the
+// random bits of value k of group g are byte (k % 4) of
+// mix32(key ^ (g * 0x9e3779b9 + k / 4 * 0x85ebca6b)), so results depend only
+// on the key and the population, never on the launch shape.
+template <int NR, class S, class TT>
+__device__ __forceinline__ void st_group_sr(S *p, long long gstride, int g, const float (&F)[NR * NR],
+                                            const TT &Tt, unsigned key) {
+  if constexpr (!Store<S>::kScaled) {
+    st_group_s<NR, S>(p, gstride, g, F, Tt);
+  } else {
+    using L = Layout<NR, S>;
+    using R = typename Raw<L::VB>::T;
+    R raw;
+    S *e = reinterpret_cast<S *>(&raw);
+    unsigned bits = 0;
+#pragma unroll
+    for (int k = 0; k < L::V; ++k) {
+      if (k % 4 == 0) bits = mix32(key ^ ((unsigned)g * 0x9e3779b9u + (unsigned)(k / 4) * 0x85ebca6bu));
+      const int a = L::alpha(g * L::V + k);
+      e[k] = Store<S>::put_sr(F[a], Tt.iwq[a], (bits >> (8 * (k % 4))) & 0xffu);
+    }
+    *reinterpret_cast<R *>(p + g * gstride) = raw;
+  }
+}
+
+// Asynchronous global->shared copy of B bytes (cp.async; 16-byte copies bypass L1).
+template <int B>
+__device__ __forceinline__ void cp_async_raw(void *smem_dst, const void *gsrc) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  if constexpr (B == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+  } else if constexpr (B == 8) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+  }
 }
 
 // Asynchronous global->shared copy of one V-vector (cp.async; 16-byte copies

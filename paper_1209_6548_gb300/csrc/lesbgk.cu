@@ -24,6 +24,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <type_traits>
 
 #include "lesbgk.h"
 #include "device.cuh"
@@ -43,10 +44,10 @@ constexpr int kMomBlock = 256;
 // ---------------------------------------------------------------------------
 // The fused time step (Sec. 3.1 + Sec. 3.2).
 // ---------------------------------------------------------------------------
-template <int NR, int N, bool SPLIT, int RING>
-__global__ void __launch_bounds__(kBlock) k_step(const float *__restrict__ fin, float *__restrict__ fout,
+template <int NR, int N, bool SPLIT, int RING, class S>
+__global__ void __launch_bounds__(kBlock) k_step(const S *__restrict__ fin, S *__restrict__ fout,
                                                  const KArgs A) {
-  using Lay = Layout<NR>;
+  using Lay = Layout<NR, S>;
   constexpr int Q = Lay::Q, H = Lay::H, V = Lay::V, G = Lay::G;
   constexpr int HL = 2;           // halo lanes per side
   constexpr int U = 32 - 2 * HL;  // nodes a strip updates
@@ -62,9 +63,9 @@ __global__ void __launch_bounds__(kBlock) k_step(const float *__restrict__ fin, 
   const bool writer = lane >= HL && lane < 32 - HL && xl < nx;
   const int y0 = seg * A.rows;
   const int y1 = min(y0 + A.rows, ny);
-  const long long gstride = (long long)V * A.plane;  // floats per group plane
-  const long long rstride = (long long)V * nx;       // floats per row
-  const float *fx = fin + (long long)xw * V;
+  const long long gstride = (long long)V * A.plane;  // elements per group plane
+  const long long rstride = (long long)V * nx;       // elements per row
+  const S *fx = fin + (long long)xw * V;
   // Rows are resolved once per row (periodic wrap, or the wall node for ghost
   // rows), never per population.
   auto row_ptr = [&](int j) { return fx + map_row(j, ny, A.walls) * rstride; };
@@ -75,13 +76,13 @@ __global__ void __launch_bounds__(kBlock) k_step(const float *__restrict__ fin, 
   float fc[Q], s0[Q], s1[Q];
   {
     float m2[Q], m1[Q], p1[Q];
-    const float *pm2 = row_ptr(y0 - 2), *pm1 = row_ptr(y0 - 1), *pz = row_ptr(y0), *pp1 = row_ptr(y0 + 1);
+    const S *pm2 = row_ptr(y0 - 2), *pm1 = row_ptr(y0 - 1), *pz = row_ptr(y0), *pp1 = row_ptr(y0 + 1);
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-      ld_group<NR>(pm1, gstride, g, m1);
-      ld_group<NR>(pz, gstride, g, fc);
-      if (g >= G / 2) ld_group<NR>(pm2, gstride, g, m2);
-      else ld_group<NR>(pp1, gstride, g, p1);
+      ld_group_s<NR, S>(pm1, gstride, g, m1, A);
+      ld_group_s<NR, S>(pz, gstride, g, fc, A);
+      if (g >= G / 2) ld_group_s<NR, S>(pm2, gstride, g, m2, A);
+      else ld_group_s<NR, S>(pp1, gstride, g, p1, A);
     }
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
@@ -101,16 +102,16 @@ __global__ void __launch_bounds__(kBlock) k_step(const float *__restrict__ fin, 
   // ring needs no barrier; cp.async.wait_group paces it.  "Row-load k" holds
   // what row y0+k consumes: f_{j+1} for c_y > 0 groups, f_{j+2} for c_y < 0.
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  using T = typename VecT<V>::T;
+  using T = typename Raw<Lay::VB>::T;
   T *ring = reinterpret_cast<T *>(smem_raw) + (size_t)(threadIdx.x >> 5) * RING * G * 32 + lane;
   int r1 = map_row(y0 + 1, ny, A.walls), r2 = map_row(y0 + 2, ny, A.walls);
   const int nrows = y1 - y0;
   auto issue_rowload = [&](int k) {
     if (k < nrows) {
-      const float *q1 = fx + r1 * rstride, *q2 = fx + r2 * rstride;
+      const S *q1 = fx + r1 * rstride, *q2 = fx + r2 * rstride;
       T *slot = ring + (k % RING) * G * 32;
 #pragma unroll
-      for (int g = 0; g < G; ++g) cp_async_vec<V>(slot + g * 32, (g >= G / 2 ? q1 : q2) + g * gstride);
+      for (int g = 0; g < G; ++g) cp_async_raw<Lay::VB>(slot + g * 32, (g >= G / 2 ? q1 : q2) + g * gstride);
       r1 = r2;
       r2 = r2 + 1 < ny ? r2 + 1 : (A.walls ? ny - 1 : 0);
     }
@@ -127,12 +128,7 @@ __global__ void __launch_bounds__(kBlock) k_step(const float *__restrict__ fin, 
     {
       const T *slot = ring + (k % RING) * G * 32;
 #pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const T v = slot[g * 32];
-        const float *e = reinterpret_cast<const float *>(&v);
-#pragma unroll
-        for (int q = 0; q < V; ++q) ld[Lay::alpha(g * V + q)] = e[q];
-      }
+      for (int g = 0; g < G; ++g) unpack_group<NR, S>(slot[g * 32], g, ld, A);
     }
 
     float acc[Q];
@@ -191,9 +187,13 @@ __global__ void __launch_bounds__(kBlock) k_step(const float *__restrict__ fin, 
     if (A.walls && (j == 0 || j == ny - 1)) wall_fix<NR>(acc, (j == 0) ? 0 : 1, A, A);
 
     if (writer) {
-      float *o = fout + (long long)j * rstride + (long long)xw * V;
+      S *o = fout + (long long)j * rstride + (long long)xw * V;
+      // rounding key per step and row (not per column): a flow uniform in x stays
+      // exactly uniform, so rounding noise cannot seed the x-varying modes the
+      // printed unsplit update amplifies
+      const unsigned key = mix32(A.seed ^ mix32((unsigned)j));
 #pragma unroll
-      for (int g = 0; g < G; ++g) st_group<NR>(o, gstride, g, acc);
+      for (int g = 0; g < G; ++g) st_group_sr<NR, S>(o, gstride, g, acc, A, key);
     }
   }
   cp_async_wait<0>();
@@ -204,10 +204,10 @@ __global__ void __launch_bounds__(kBlock) k_step(const float *__restrict__ fin, 
 // expansion of the isotropic Maxwellian), then the wall rule once.
 // fields: double[4][ny][nx] = rho, u_x, u_y, T (or nullptr: rest).
 // ---------------------------------------------------------------------------
-template <int NR, int N>
-__global__ void __launch_bounds__(kBlock) k_init(const double *__restrict__ fields, float *__restrict__ f,
+template <int NR, int N, class S>
+__global__ void __launch_bounds__(kBlock) k_init(const double *__restrict__ fields, S *__restrict__ f,
                                                  const KArgs A) {
-  using Lay = Layout<NR>;
+  using Lay = Layout<NR, S>;
   constexpr int Q = Lay::Q;
   const long long cells = A.plane;
   const long long gstride = (long long)Lay::V * cells;
@@ -224,41 +224,41 @@ __global__ void __launch_bounds__(kBlock) k_init(const double *__restrict__ fiel
     float e[N + 1][N + 1];
     gaussian_coeffs<N>(rho, rho * ux, rho * uy, ux, uy, dT, 0.f, dT, rdT, 0.f, rdT, e);
     e[0][0] = drho;  // deviation from w_a
-    float S[Q];
-    hermite_evaluate<NR, N>(e, S, A);
+    float Sv[Q];
+    hermite_evaluate<NR, N>(e, Sv, A);
     const int j = (int)(c / A.nx);
-    if (A.walls && (j == 0 || j == A.ny - 1)) wall_fix<NR>(S, j == 0 ? 0 : 1, A, A);
+    if (A.walls && (j == 0 || j == A.ny - 1)) wall_fix<NR>(Sv, j == 0 ? 0 : 1, A, A);
 #pragma unroll
-    for (int g = 0; g < Lay::G; ++g) st_group<NR>(f + c * Lay::V, gstride, g, S);
+    for (int g = 0; g < Lay::G; ++g) st_group_s<NR, S>(f + c * Lay::V, gstride, g, Sv, A);
   }
 }
 
 // Populations between the grouped layout and the public [a][j][i] layout.
-template <int NR>
-__global__ void __launch_bounds__(kBlock) k_ungroup(const float *__restrict__ f, float *__restrict__ out,
-                                                    long long cells) {
-  using Lay = Layout<NR>;
+template <int NR, class S>
+__global__ void __launch_bounds__(kBlock) k_ungroup(const S *__restrict__ f, float *__restrict__ out,
+                                                    long long cells, const KArgs A) {
+  using Lay = Layout<NR, S>;
   const long long gstride = (long long)Lay::V * cells;
   for (long long c = blockIdx.x * (long long)kBlock + threadIdx.x; c < cells; c += (long long)gridDim.x * kBlock) {
     float F[Lay::Q];
 #pragma unroll
-    for (int g = 0; g < Lay::G; ++g) ld_group<NR>(f + c * Lay::V, gstride, g, F);
+    for (int g = 0; g < Lay::G; ++g) ld_group_s<NR, S>(f + c * Lay::V, gstride, g, F, A);
 #pragma unroll
     for (int a = 0; a < Lay::Q; ++a) out[a * cells + c] = F[a];
   }
 }
 
-template <int NR>
-__global__ void __launch_bounds__(kBlock) k_group(const float *__restrict__ in, float *__restrict__ f,
-                                                  long long cells) {
-  using Lay = Layout<NR>;
+template <int NR, class S>
+__global__ void __launch_bounds__(kBlock) k_group(const float *__restrict__ in, S *__restrict__ f,
+                                                  long long cells, const KArgs A) {
+  using Lay = Layout<NR, S>;
   const long long gstride = (long long)Lay::V * cells;
   for (long long c = blockIdx.x * (long long)kBlock + threadIdx.x; c < cells; c += (long long)gridDim.x * kBlock) {
     float F[Lay::Q];
 #pragma unroll
     for (int a = 0; a < Lay::Q; ++a) F[a] = __ldg(in + a * cells + c);
 #pragma unroll
-    for (int g = 0; g < Lay::G; ++g) st_group<NR>(f + c * Lay::V, gstride, g, F);
+    for (int g = 0; g < Lay::G; ++g) st_group_s<NR, S>(f + c * Lay::V, gstride, g, F, A);
   }
 }
 
@@ -266,10 +266,10 @@ __global__ void __launch_bounds__(kBlock) k_group(const float *__restrict__ in, 
 // Moments of Eq. (mac) per node, plus FP64 block partial sums of mass,
 // momentum and energy.  out: float[9][ny][nx].
 // ---------------------------------------------------------------------------
-template <int NR>
-__global__ void __launch_bounds__(kMomBlock) k_moments(const float *__restrict__ f, float *__restrict__ out,
+template <int NR, class S>
+__global__ void __launch_bounds__(kMomBlock) k_moments(const S *__restrict__ f, float *__restrict__ out,
                                                        double *__restrict__ partial, const KArgs A) {
-  using Lay = Layout<NR>;
+  using Lay = Layout<NR, S>;
   constexpr int Q = Lay::Q;
   const long long cells = A.plane;
   const long long gstride = (long long)Lay::V * cells;
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kMomBlock) k_moments(const float *__restrict__
        c += (long long)gridDim.x * kMomBlock) {
     float F[Q];
 #pragma unroll
-    for (int g = 0; g < Lay::G; ++g) ld_group<NR>(f + c * Lay::V, gstride, g, F);
+    for (int g = 0; g < Lay::G; ++g) ld_group_s<NR, S>(f + c * Lay::V, gstride, g, F, A);
     float m[4][4];
     hermite_moments<NR, 3>(F, m, A);
     const float rho = 1.0f + m[0][0];
@@ -384,7 +384,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 size_t buffer_bytes(const lesbgk_params *p) {
   const size_t cells = (size_t)p->nx * p->ny;
   const size_t q = (size_t)p->nroots * p->nroots;
-  size_t per = q * sizeof(float);
+  size_t per = q * (p->storage == LESBGK_F32 ? sizeof(float) : 2);
   if (per < 9 * sizeof(float)) per = 9 * sizeof(float);
   if (per < 4 * sizeof(double)) per = 4 * sizeof(double);
   return align_up(cells * per, 256);
@@ -428,43 +428,62 @@ int build_tables(lesbgk *h, const double *h_init) {
 
 constexpr int kRing = 4;
 
-template <int NR>
+template <int NR, class S>
 constexpr size_t step_smem_bytes() {
-  return (size_t)(kBlock / 32) * kRing * Layout<NR>::G * 32 * Layout<NR>::V * sizeof(float);
+  return (size_t)(kBlock / 32) * kRing * Layout<NR, S>::G * 32 * Layout<NR, S>::VB;
 }
 
-template <int NR, int N>
-int launch_step_t(lesbgk *h, const float *fin, float *fout, cudaStream_t s) {
-  const long long warps = (long long)h->args.nstrips * h->args.nseg;
-  const unsigned grid = (unsigned)((warps * 32 + kBlock - 1) / kBlock);
-  constexpr size_t smem = step_smem_bytes<NR>();
-  if (h->p.scheme == LESBGK_SPLIT) k_step<NR, N, true, kRing><<<grid, kBlock, smem, s>>>(fin, fout, h->args);
-  else k_step<NR, N, false, kRing><<<grid, kBlock, smem, s>>>(fin, fout, h->args);
-  return 0;
+// Call fn(NR, N, storage tag) with compile-time constants for the built
+// combinations: every (nroots, order) in FP32, the default orders also in
+// FP16 and BF16.
+template <class Fn>
+void dispatch(int nr, int order, int storage, Fn &&fn) {
+  using R4 = std::integral_constant<int, 4>;
+  using R6 = std::integral_constant<int, 6>;
+  using N3 = std::integral_constant<int, 3>;
+  using N4 = std::integral_constant<int, 4>;
+  if (nr == 4 && order == 3) {
+    if (storage == LESBGK_F16) fn(R4{}, N3{}, __half{});
+    else if (storage == LESBGK_BF16) fn(R4{}, N3{}, __nv_bfloat16{});
+    else fn(R4{}, N3{}, float{});
+  } else if (nr == 6 && order == 4) {
+    if (storage == LESBGK_F16) fn(R6{}, N4{}, __half{});
+    else if (storage == LESBGK_BF16) fn(R6{}, N4{}, __nv_bfloat16{});
+    else fn(R6{}, N4{}, float{});
+  } else if (nr == 4) {
+    fn(R4{}, N4{}, float{});
+  } else {
+    fn(R6{}, N3{}, float{});
+  }
 }
 
 // Opt in to more than 48 KiB of dynamic shared memory where a ring needs it.
-template <int NR, int N>
-cudaError_t allow_smem_t() {
-  constexpr int smem = (int)step_smem_bytes<NR>();
-  cudaError_t e = cudaFuncSetAttribute(k_step<NR, N, true, kRing>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_step<NR, N, false, kRing>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+cudaError_t allow_smem(const lesbgk *h) {
+  cudaError_t e = cudaSuccess;
+  dispatch(h->nr, h->order, h->p.storage, [&](auto r, auto n, auto st) {
+    constexpr int NR = decltype(r)::value, N = decltype(n)::value;
+    using S = decltype(st);
+    constexpr int smem = (int)step_smem_bytes<NR, S>();
+    e = cudaFuncSetAttribute(k_step<NR, N, true, kRing, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_step<NR, N, false, kRing, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  });
   return e;
 }
 
-cudaError_t allow_smem(const lesbgk *h) {
-  if (h->nr == 4 && h->order == 3) return allow_smem_t<4, 3>();
-  if (h->nr == 4 && h->order == 4) return allow_smem_t<4, 4>();
-  if (h->nr == 6 && h->order == 3) return allow_smem_t<6, 3>();
-  return allow_smem_t<6, 4>();
-}
-
-int launch_step(lesbgk *h, const float *fin, float *fout, cudaStream_t s) {
-  if (h->nr == 4 && h->order == 3) return launch_step_t<4, 3>(h, fin, fout, s);
-  if (h->nr == 4 && h->order == 4) return launch_step_t<4, 4>(h, fin, fout, s);
-  if (h->nr == 6 && h->order == 3) return launch_step_t<6, 3>(h, fin, fout, s);
-  return launch_step_t<6, 4>(h, fin, fout, s);
+int launch_step(lesbgk *h, const void *fin, void *fout, cudaStream_t s) {
+  const long long warps = (long long)h->args.nstrips * h->args.nseg;
+  const unsigned grid = (unsigned)((warps * 32 + kBlock - 1) / kBlock);
+  dispatch(h->nr, h->order, h->p.storage, [&](auto r, auto n, auto st) {
+    constexpr int NR = decltype(r)::value, N = decltype(n)::value;
+    using S = decltype(st);
+    constexpr size_t smem = step_smem_bytes<NR, S>();
+    const S *fi = static_cast<const S *>(fin);
+    S *fo = static_cast<S *>(fout);
+    if (h->p.scheme == LESBGK_SPLIT) k_step<NR, N, true, kRing, S><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+    else k_step<NR, N, false, kRing, S><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+  });
+  return 0;
 }
 
 unsigned grid_for(const lesbgk *h, long long cells) {
@@ -474,19 +493,23 @@ unsigned grid_for(const lesbgk *h, long long cells) {
   return g < 1 ? 1u : (unsigned)g;
 }
 
-int launch_init(lesbgk *h, const double *fields, float *f, cudaStream_t s) {
+int launch_init(lesbgk *h, const double *fields, void *f, cudaStream_t s) {
   const unsigned grid = grid_for(h, h->args.plane);
-  if (h->nr == 4 && h->order == 3) k_init<4, 3><<<grid, kBlock, 0, s>>>(fields, f, h->args);
-  else if (h->nr == 4 && h->order == 4) k_init<4, 4><<<grid, kBlock, 0, s>>>(fields, f, h->args);
-  else if (h->nr == 6 && h->order == 3) k_init<6, 3><<<grid, kBlock, 0, s>>>(fields, f, h->args);
-  else k_init<6, 4><<<grid, kBlock, 0, s>>>(fields, f, h->args);
+  dispatch(h->nr, h->order, h->p.storage, [&](auto r, auto n, auto st) {
+    constexpr int NR = decltype(r)::value, N = decltype(n)::value;
+    using S = decltype(st);
+    k_init<NR, N, S><<<grid, kBlock, 0, s>>>(fields, static_cast<S *>(f), h->args);
+  });
   return 0;
 }
 
 int launch_moments(lesbgk *h, float *out, cudaStream_t s) {
-  const float *f = h->buf[h->cur];
-  if (h->nr == 4) k_moments<4><<<kMomGrid, kMomBlock, 0, s>>>(f, out, h->partial, h->args);
-  else k_moments<6><<<kMomGrid, kMomBlock, 0, s>>>(f, out, h->partial, h->args);
+  const void *f = h->buf[h->cur];
+  dispatch(h->nr, h->order, h->p.storage, [&](auto r, auto, auto st) {
+    constexpr int NR = decltype(r)::value;
+    using S = decltype(st);
+    k_moments<NR, S><<<kMomGrid, kMomBlock, 0, s>>>(static_cast<const S *>(f), out, h->partial, h->args);
+  });
   k_reduce_partials<<<1, 128, 0, s>>>(h->partial, kMomGrid, h->sums);
   return 0;
 }
@@ -500,17 +523,16 @@ cudaError_t launch_init(const KArgs &A, int nr, int order, const double *fields,
   long long g = (A.plane + kBlock - 1) / kBlock;
   if (g > (long long)sm_count * 16) g = (long long)sm_count * 16;
   const unsigned grid = g < 1 ? 1u : (unsigned)g;
-  if (nr == 4 && order == 3) k_init<4, 3><<<grid, kBlock, 0, s>>>(fields, f, A);
-  else if (nr == 4 && order == 4) k_init<4, 4><<<grid, kBlock, 0, s>>>(fields, f, A);
-  else if (nr == 6 && order == 3) k_init<6, 3><<<grid, kBlock, 0, s>>>(fields, f, A);
-  else k_init<6, 4><<<grid, kBlock, 0, s>>>(fields, f, A);
+  dispatch(nr, order, LESBGK_F32, [&](auto r, auto n, auto) {
+    k_init<decltype(r)::value, decltype(n)::value, float><<<grid, kBlock, 0, s>>>(fields, f, A);
+  });
   return cudaGetLastError();
 }
 
 cudaError_t launch_moments(const KArgs &A, int nr, const float *f, float *out, double *partial, double *sums,
                            cudaStream_t s) {
-  if (nr == 4) k_moments<4><<<kMomGrid, kMomBlock, 0, s>>>(f, out, partial, A);
-  else k_moments<6><<<kMomGrid, kMomBlock, 0, s>>>(f, out, partial, A);
+  if (nr == 4) k_moments<4, float><<<kMomGrid, kMomBlock, 0, s>>>(f, out, partial, A);
+  else k_moments<6, float><<<kMomGrid, kMomBlock, 0, s>>>(f, out, partial, A);
   k_reduce_partials<<<1, 128, 0, s>>>(partial, kMomGrid, sums);
   return cudaGetLastError();
 }
@@ -519,8 +541,9 @@ cudaError_t launch_ungroup(int nr, const float *f, float *out, long long cells, 
   long long g = (cells + kBlock - 1) / kBlock;
   if (g > (long long)sm_count * 16) g = (long long)sm_count * 16;
   const unsigned grid = g < 1 ? 1u : (unsigned)g;
-  if (nr == 4) k_ungroup<4><<<grid, kBlock, 0, s>>>(f, out, cells);
-  else k_ungroup<6><<<grid, kBlock, 0, s>>>(f, out, cells);
+  const KArgs none{};  // FP32 storage needs no weights
+  if (nr == 4) k_ungroup<4, float><<<grid, kBlock, 0, s>>>(f, out, cells, none);
+  else k_ungroup<6, float><<<grid, kBlock, 0, s>>>(f, out, cells, none);
   return cudaGetLastError();
 }
 
@@ -605,6 +628,7 @@ extern "C" int lesbgk_step(lesbgk *h, int64_t nsteps, void *stream) {
   if (nsteps < 0) return fail(LESBGK_EINVAL, "nsteps < 0");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int64_t k = 0; k < nsteps; ++k) {
+    h->args.seed = (unsigned)(h->steps + k) * 0x9e3779b9u + 0x7f4a7c15u;  // a new rounding key per step
     launch_step(h, h->buf[h->cur], h->buf[h->cur ^ 1], s);
     h->cur ^= 1;
   }
@@ -653,8 +677,12 @@ extern "C" int lesbgk_get_populations(lesbgk *h, float *d_out, void *stream) {
   if (!h || !d_out) return fail(LESBGK_EINVAL, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const long long cells = h->args.plane;
-  if (h->nr == 4) k_ungroup<4><<<grid_for(h, cells), kBlock, 0, s>>>(h->buf[h->cur], d_out, cells);
-  else k_ungroup<6><<<grid_for(h, cells), kBlock, 0, s>>>(h->buf[h->cur], d_out, cells);
+  const void *f = h->buf[h->cur];
+  dispatch(h->nr, h->order, h->p.storage, [&](auto r, auto, auto st) {
+    using S = decltype(st);
+    k_ungroup<decltype(r)::value, S><<<grid_for(h, cells), kBlock, 0, s>>>(static_cast<const S *>(f), d_out, cells,
+                                                                          h->args);
+  });
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? 0 : cuda_fail(e, "get populations");
 }
@@ -663,8 +691,11 @@ extern "C" int lesbgk_set_populations(lesbgk *h, const float *d_in, int64_t step
   if (!h || !d_in) return fail(LESBGK_EINVAL, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const long long cells = h->args.plane;
-  if (h->nr == 4) k_group<4><<<grid_for(h, cells), kBlock, 0, s>>>(d_in, h->buf[h->cur], cells);
-  else k_group<6><<<grid_for(h, cells), kBlock, 0, s>>>(d_in, h->buf[h->cur], cells);
+  void *f = h->buf[h->cur];
+  dispatch(h->nr, h->order, h->p.storage, [&](auto r, auto, auto st) {
+    using S = decltype(st);
+    k_group<decltype(r)::value, S><<<grid_for(h, cells), kBlock, 0, s>>>(d_in, static_cast<S *>(f), cells, h->args);
+  });
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "set populations");
   h->steps = steps_done;

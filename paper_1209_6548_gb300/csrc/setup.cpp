@@ -43,7 +43,10 @@ int check_params(const lesbgk_params *p) {
   if ((long long)p->nx * p->ny > (1LL << 31) / 64) return fail(LESBGK_EINVAL, "grid too large");
   if (p->bc_y != LESBGK_PERIODIC && p->bc_y != LESBGK_DIFFUSE) return fail(LESBGK_EINVAL, "bad bc_y");
   if (p->bc_y == LESBGK_DIFFUSE && p->ny < 2) return fail(LESBGK_EINVAL, "walls need ny >= 2");
-  if (p->storage != LESBGK_F32) return fail(LESBGK_EINVAL, "storage must be LESBGK_F32");
+  if (p->storage != LESBGK_F32 && p->storage != LESBGK_F16 && p->storage != LESBGK_BF16)
+    return fail(LESBGK_EINVAL, "storage must be LESBGK_F32, LESBGK_F16 or LESBGK_BF16");
+  if (p->storage != LESBGK_F32 && order != default_order(p->nroots))
+    return fail(LESBGK_EINVAL, "16-bit storage is built for the default order only");
   if (p->scheme != LESBGK_UNSPLIT && p->scheme != LESBGK_SPLIT)
     return fail(LESBGK_EINVAL, "scheme must be LESBGK_UNSPLIT or LESBGK_SPLIT");
   if (!(p->kn > 0.0) || !std::isfinite(p->kn)) return fail(LESBGK_EINVAL, "Kn must be > 0");
@@ -146,6 +149,14 @@ int build_setup(const lesbgk_params &p, int order, const double *h_init, Setup *
     A.wA[s] = (float)A_out;
     A.wB[s] = (float)(1.0 / Z_out);
   }
+  // FP16 holds 2^10 (f_a - w_a)/w_a: relative deviations down to 6e-8 stay in
+  // its normal range (where stochastic rounding is unbiased) and up to 64 fit
+  const double store_scale = p.storage == LESBGK_F16 ? 1024.0 : 1.0;
+  for (int ix = 0; ix < nr; ++ix)
+    for (int iy = 0; iy < nr; ++iy) {
+      A.wq[ix * nr + iy] = (float)(w[ix] * w[iy] / store_scale);
+      A.iwq[ix * nr + iy] = (float)(store_scale / (w[ix] * w[iy]));
+    }
   A.c_omega = (float)(dt / (p.kn * (1.0 - p.b)));
   A.visc_pow = (float)(1.0 - p.visc_exp);
   A.vmode = p.visc_exp == 0.5 ? 1 : (p.visc_exp == 1.0 ? 2 : 0);

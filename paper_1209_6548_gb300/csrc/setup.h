@@ -23,6 +23,7 @@ struct KArgs {
   float wS[2][kMaxQ];          // wall equilibrium S_a(T_w, u_w), [0] bottom, [1] top
   float wSdev[2][kMaxQ];       // S_a - w_a
   float wA[2], wB[2];          // sum_out |c_y|(S-w) and 1/sum_out |c_y| S
+  float wq[kMaxQ], iwq[kMaxQ]; // 16-bit storage: stored = df * iwq, df = stored * wq
   float c_omega;               // dt / (Kn (1-b)):  dt/tau = c_omega rho T^(1-varpi)
   float visc_pow;              // 1 - varpi
   float b, beta;               // b and (1-b)/2
@@ -30,6 +31,7 @@ struct KArgs {
   int nx, ny, walls, has_force, vmode;  // vmode 1: varpi = 1/2, 2: varpi = 1, 0: general
   int rows, nstrips, nseg;
   long long plane;             // nx*ny
+  unsigned seed;               // per-launch key of the 16-bit stochastic rounding
 };
 
 // What one solve's set-up produces.

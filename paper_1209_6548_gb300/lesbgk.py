@@ -21,7 +21,7 @@ from .build import LIB
 
 OK, EINVAL, EUNSTABLE, ESPACE, ECUDA, EDIVERGED = 0, -1, -2, -3, -4, -5
 PERIODIC, DIFFUSE = 0, 1
-F32 = 0
+F32, F16, BF16 = 0, 1, 2
 UNSPLIT, SPLIT = 0, 1
 MOMENT_NAMES = ("rho", "ux", "uy", "T", "sxx", "sxy", "syy", "qx", "qy")
 
