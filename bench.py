@@ -219,11 +219,32 @@ def run_batch(args, world, rank, local):
     from paper_1209_6548_gb300 import inputs as I
     from paper_1209_6548_gb300 import lesbgk as L
 
+    from paper_1209_6548_gb300 import shard as SH
+
     torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
     B.build()
     nsteps = args.lattice_steps if args.lattice_steps != 1000 else 2000
-    probs = I.batch_mix(n=args.instances, seed=rank, steps=nsteps)
+    # one mix of instances x world solves, split across ranks by cost (LPT)
+    all_probs = I.batch_mix(n=args.instances * world, seed=0, steps=nsteps)
+    _, probs = SH.shard(all_probs, rank, world, steps=nsteps)
     params = [L.params_from_problem(p) for p in probs]
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+
+    def max_over_ranks(x):
+        if pg is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
     pool = int(sum(L.batch_slot_bytes(p) for p in params) * 1.05) + (1 << 20)
     stream = torch.cuda.current_stream()
     bt = L.Batch(capacity=len(params), nx=4, pool_bytes=pool, stream=stream)
@@ -257,14 +278,14 @@ def run_batch(args, world, rank, local):
     torch.cuda.synchronize()
     step_ms = e0.elapsed_time(e1) / 640
     with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
+        barrier()
         w0 = time.perf_counter()
         for _ in range(args.steps):
             one_pass()
-        torch.cuda.synchronize()
-        wsec = time.perf_counter() - w0
+        barrier()
+        wsec = max_over_ranks(time.perf_counter() - w0)
     n = len(params)
-    value = n * args.steps / wsec
+    value = len(all_probs) * args.steps / wsec
     # plain one-at-a-time baseline on a sample
     idx = list(range(0, n, max(1, n // args.plain_sample)))[: args.plain_sample]
     torch.cuda.synchronize()
@@ -286,10 +307,11 @@ def run_batch(args, world, rank, local):
         "metric": "batched solves/s", "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": wsec / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"batch_mix_{n}_nx4_d2q16", "instances": n, "lattice_steps_per_solve": nsteps,
+        "config": {"workload": f"batch_mix_{args.instances}_per_gpu_nx4_d2q16", "instances": len(all_probs),
+                   "instances_this_rank": n, "sharding": "LPT by nodes x steps", "lattice_steps_per_solve": nsteps,
                    "total_nodes": cells, "rows_per_item": rows, "graph_steps": 64,
                    "l2": "working set %.0f MB (L2-resident)" % (2 * 64 * cells / 1e6)},
-        "instance_mlups": sum(lups_per_solve) * args.steps / wsec / 1e6,
+        "instance_mlups": sum(4 * p.ny * nsteps for p in all_probs) * args.steps / wsec / 1e6,
         "plain": {"solves_per_s": plain_solves_s, "sample": f"{len(idx)} of the {n} instances, one at a time",
                   "mlups": 1.0 / plain_sec_per_lup / 1e6,
                   "est_solves_per_s_full_mix": 1.0 / (plain_sec_per_lup * sum(lups_per_solve) / n)},
@@ -302,6 +324,8 @@ def run_batch(args, world, rank, local):
     if rank == 0:
         print(json.dumps(line), flush=True)
     bt.close()
+    if pg is not None:
+        pg.destroy_process_group()
     return 0
 
 
