@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--workload", choices=["tgv", "batch", "serve", "precision"], default="tgv",
                     help="tgv: 4096^2 Taylor-Green throughput (default); batch: 512-instance channel mix; "
                          "serve: Poisson arrivals run to steady state with continuous batching")
+    ap.add_argument("--velocity-set", choices=["d2q16", "d2q36"], default="d2q16",
+                    help="tgv workload lattice: D2Q16 (order 3) or D2Q36 (order 4, the paper's setting)")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
                     help="population storage for the tgv workload (compute is FP32)")
     ap.add_argument("--requests", type=int, default=400)
@@ -57,6 +59,20 @@ def parse():
     ap.add_argument("--instances", type=int, default=512)
     ap.add_argument("--plain-sample", type=int, default=32, help="instances the one-at-a-time baseline runs")
     return ap.parse_args()
+
+
+def tgv_workload_name(n, args):
+    return f"tgv_{n}x{n}_{args.velocity_set}_{args.storage}"
+
+
+def tgv_config(n, args, nsteps):
+    """The config object of the throughput workload (shared by both arms)."""
+    from paper_1209_6548_gb300 import inputs as I
+    nroots = 6 if args.velocity_set == "d2q36" else 4
+    prob = I.tgv(n, steps=nsteps, nroots=nroots)
+    return {"workload": tgv_workload_name(n, args), "nx": n, "ny": n, "velocity_set": args.velocity_set.upper(),
+            "storage": args.storage, "order": 3 if nroots == 4 else 4, "kn": prob.kn, "b": prob.b,
+            "lattice_steps_per_step": nsteps, "scheme": "split"}
 
 
 def measured_peak():
@@ -156,28 +172,29 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline(n: int, rows: int = 1024, steps: int = 48):
+def cpu_baseline(n: int, rows: int = 1024, steps: int = 48, nroots: int = 4):
     """The FP64 oracle, as it stands, on a bounded sample of the workload: the
-    first `rows` rows of the n x n Taylor-Green initial state, periodic, for
-    `steps` time steps, on all host cores the process may use."""
+    first `rows` rows of the n x n Taylor-Green initial state, periodic, split
+    scheme, for `steps` time steps, on all host cores the process may use."""
     import numpy as np
     import oracle as O
     from paper_1209_6548_gb300 import inputs as I
-    prob = I.tgv(n)
+    prob = I.tgv(n, nroots=nroots)
     fields = I.initial_fields(prob)[:, :rows, :].copy()
     cores = len(os.sched_getaffinity(0))
     O.set_threads(cores)
     dx = dy = 1.0 / n
-    c, _ = O.gauss_hermite_1d(4)
+    c, _ = O.gauss_hermite_1d(nroots)
     dt = 0.5 * dx / float(np.abs(c).max())
-    op = O.make_params(nroots=4, order=3, nx=n, ny=rows, bc_y=0, kn=prob.kn, b=prob.b,
-                       visc_exp=prob.visc_exp, dt=dt, dx=dx, dy=dy, scheme=prob.scheme)
+    op = O.make_params(nroots=nroots, order=3 if nroots == 4 else 4, nx=n, ny=rows, bc_y=0, kn=prob.kn,
+                       b=prob.b, visc_exp=prob.visc_exp, dt=dt, dx=dx, dy=dy, scheme=prob.scheme)
     f = O.init(op, fields)
     t0 = time.perf_counter()
     O.run(op, f, steps)
     sec = time.perf_counter() - t0
     return {"value": n * rows * steps / sec / 1e6, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
-            "sample": f"{n}x{rows} periodic rows of the Taylor-Green state, {steps} FP64 oracle steps ({sec:.1f} s)"}
+            "sample": f"{n}x{rows} periodic rows of the Taylor-Green state (D2Q{nroots * nroots}), "
+                      f"{steps} FP64 oracle steps ({sec:.1f} s)"}
 
 
 def run_reference(args, world, rank):
@@ -187,7 +204,7 @@ def run_reference(args, world, rank):
     t_all = time.perf_counter()
     base = None
     for k in range(args.warmup + args.steps):
-        base = cpu_baseline(args.n, rows=32, steps=2)
+        base = cpu_baseline(args.n, rows=256, steps=4, nroots=6 if args.velocity_set == "d2q36" else 4)
         if k >= args.warmup:
             samples.append(base["value"])
     value = statistics.median(samples)
@@ -196,7 +213,7 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"tgv_{args.n}x{args.n}_d2q16", "sample_rows": 32, "lattice_steps": 2},
+        "config": tgv_config(args.n, args, args.lattice_steps),
         "cpu_baseline": base,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": time.perf_counter() - t_all,
@@ -518,7 +535,8 @@ def main():
 
     B.build()
     n, nsteps = args.n, args.lattice_steps
-    prob = I.tgv(n, steps=nsteps)
+    nroots = 6 if args.velocity_set == "d2q36" else 4
+    prob = I.tgv(n, steps=nsteps, nroots=nroots)
     fields = I.initial_fields(prob)
     params = L.params_from_problem(prob, dt=0.0)
     params.storage = {"f32": L.F32, "f16": L.F16, "bf16": L.BF16}[args.storage]
@@ -589,27 +607,31 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     peak, peak_kind = measured_peak()
-    bytes_per_lup = BYTES_PER_LUP if args.storage == "f32" else BYTES_PER_LUP // 2
+    q = nroots * nroots
+    bytes_per_lup = 2 * q * (4 if args.storage == "f32" else 2)
     achieved = bytes_per_lup * cells / (kernel_ms / 1e3) / 1e9
     digest = source_digest()
     traffic = committed_traffic(digest)
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        base = cpu_baseline(n)
+        base = cpu_baseline(n, rows=1024 if nroots == 4 else 256, nroots=nroots)
     if rank == 0:
         clocks = clk.summary()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"tgv_{n}x{n}_d2q16_{args.storage}", "nx": n, "ny": n, "velocity_set": "D2Q16",
-                       "storage": args.storage,
-                       "order": 3, "kn": prob.kn, "b": prob.b, "lattice_steps_per_step": nsteps,
-                       "l2": "inputs larger than L2 (two 1.07 GB population buffers)",
+            "config": {"workload": tgv_workload_name(n, args), "nx": n, "ny": n,
+                       "velocity_set": args.velocity_set.upper(), "storage": args.storage,
+                       "order": 3 if nroots == 4 else 4, "kn": prob.kn, "b": prob.b,
+                       "lattice_steps_per_step": nsteps, "scheme": "split",
+                       "l2": "inputs larger than L2 (two population buffers of %.2f GB)"
+                             % (q * n * n * (4 if args.storage == "f32" else 2) / 1e9),
                        "parallelism": f"replica x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                         "kernel": f"k_step<4,3,split,{args.storage}> rows={shape[1]}", "kernel_ms": kernel_ms,
+                         "kernel": f"k_step<{nroots},{3 if nroots == 4 else 4},split,{args.storage}> rows={shape[1]}",
+                         "kernel_ms": kernel_ms,
                          "bytes_per_lup": bytes_per_lup, "source_sha256": digest},
             "cpu_baseline": base,
             "e2e": e2e,
