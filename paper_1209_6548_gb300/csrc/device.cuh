@@ -17,9 +17,15 @@ namespace lesbgk_dev {
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ float minmod(float a, float b) {
-  // signed smaller magnitude when a and b agree in sign, else 0 (= median(a, b, 0));
-  // equals [f_{i+1}-f_i] Psi(Theta) of Sec. 3.1 with the minmod limiter.
-  return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.0f));
+  // signed smaller magnitude when a and b agree in sign, else 0; equals
+  // [f_{i+1}-f_i] Psi(Theta) of Sec. 3.1 with the minmod limiter.
+  // min.xorsign.abs gives min(|a|,|b|) signed by sign(a) XOR sign(b); clamping
+  // at 0 keeps it only when the signs agree; a's sign is then put back
+  // (three instructions instead of the four of median(a, b, 0)).
+  float t;
+  asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(t) : "f"(a), "f"(b));
+  t = fmaxf(t, 0.0f);
+  return __uint_as_float(__float_as_uint(t) | (__float_as_uint(a) & 0x80000000u));
 }
 
 // Hardware approximations (MUFU): relative error ~1 ulp, far below the FP32
