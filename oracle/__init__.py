@@ -34,6 +34,8 @@ class OrcParams(C.Structure):
         ("kn", C.c_double), ("b", C.c_double), ("visc_exp", C.c_double),
         ("dt", C.c_double), ("dx", C.c_double), ("dy", C.c_double),
         ("wall_T", C.c_double * 2), ("wall_ux", C.c_double * 2), ("g", C.c_double * 2),
+        ("wall_specular", C.c_double), ("wall_T_amp", C.c_double), ("wall_T_freq", C.c_double),
+        ("time", C.c_double),
     ]
 
 
@@ -111,13 +113,15 @@ UNSPLIT, SPLIT = 0, 1
 
 
 def make_params(*, nroots, order, nx, ny, bc_y, kn, b, visc_exp, dt, dx, dy,
-                wall_T=(1.0, 1.0), wall_ux=(0.0, 0.0), g=(0.0, 0.0), scheme=UNSPLIT) -> OrcParams:
+                wall_T=(1.0, 1.0), wall_ux=(0.0, 0.0), g=(0.0, 0.0), scheme=UNSPLIT, wall_specular=0.0,
+                wall_T_amp=0.0, wall_T_freq=0.0, time=0.0) -> OrcParams:
     p = OrcParams()
     p.nroots, p.order, p.nx, p.ny, p.bc_y, p.scheme = nroots, order, nx, ny, bc_y, scheme
     p.kn, p.b, p.visc_exp, p.dt, p.dx, p.dy = kn, b, visc_exp, dt, dx, dy
     p.wall_T[0], p.wall_T[1] = wall_T
     p.wall_ux[0], p.wall_ux[1] = wall_ux
     p.g[0], p.g[1] = g
+    p.wall_specular, p.wall_T_amp, p.wall_T_freq, p.time = wall_specular, wall_T_amp, wall_T_freq, time
     return p
 
 

@@ -65,6 +65,10 @@ typedef struct orc_params {
   double wall_T[2];   /* [0] bottom (j=0), [1] top (j=ny-1) */
   double wall_ux[2];
   double g[2];        /* body force */
+  double wall_specular; /* 1 - gamma of the Maxwell wall model (Sec. 3.2); 0 = fully diffuse */
+  double wall_T_amp;    /* wall temperature T_w(t) = wall_T + amp sin(freq t) (Sec. 4.2) */
+  double wall_T_freq;
+  double time;          /* time of the state handed to orc_init / orc_step / orc_run */
 } orc_params;
 
 static int orc_threads = 1;
@@ -430,14 +434,20 @@ static int row_of(const orc_params *p, int j) {
   return j;
 }
 
-/* Diffuse wall of Sec. 3.2 at wall node (i, j) with inward normal ny_sign:
- * rho_W = sum_{c.n<0} |c.n| f / sum_{c.n>0} |c.n| S ; f_out = rho_W S. */
-static void wall_node(const orc_lattice *L, const orc_params *p, double *f, int i, int j,
-                      int side) {
+/* Wall of Sec. 3.2 at wall node (i, j) at time t: the Maxwell model with
+ * accommodation gamma = 1 - wall_specular.  The diffusely re-emitted part is
+ * rho_W S(T_w(t), u_w) with rho_W = sum_{c.n<0} |c.n| f / sum_{c.n>0} |c.n| S
+ * (zero net normal mass flux); the specular part is the incoming population
+ * with the mirrored normal velocity.  T_w(t) = wall_T + amp sin(freq t), the
+ * heating of Sec. 4.2.  With wall_specular = 0 and amp = 0 this is the fully
+ * diffuse wall the paper implements. */
+static void wall_node(const orc_lattice *L, const orc_params *p, double *f, int i, int j, int side,
+                      double t) {
   double n_y = side == 0 ? 1.0 : -1.0;
   double u[2] = {p->wall_ux[side], 0.0};
+  double Tw = p->wall_T[side] + p->wall_T_amp * sin(p->wall_T_freq * t);
   double S[ORC_MAXQ];
-  for (int a = 0; a < L->Q; ++a) S[a] = feq0_S(p->order, p->wall_T[side], u, L->cx[a], L->cy[a], L->w[a]);
+  for (int a = 0; a < L->Q; ++a) S[a] = feq0_S(p->order, Tw, u, L->cx[a], L->cy[a], L->w[a]);
   double num = 0.0, den = 0.0;
   for (int a = 0; a < L->Q; ++a) {
     double cn = L->cy[a] * n_y;
@@ -445,15 +455,21 @@ static void wall_node(const orc_lattice *L, const orc_params *p, double *f, int 
     if (cn > 0.0) den += fabs(cn) * S[a];
   }
   double rw = num / den;
-  for (int a = 0; a < L->Q; ++a)
-    if (L->cy[a] * n_y > 0.0) f[fidx(p, a, j, i)] = rw * S[a];
+  double spec = p->wall_specular;
+  for (int a = 0; a < L->Q; ++a) {
+    if (L->cy[a] * n_y > 0.0) {
+      int ix = a / L->nroots, iy = a % L->nroots;
+      int mirror = ix * L->nroots + (L->nroots - 1 - iy); /* c_y -> -c_y */
+      f[fidx(p, a, j, i)] = (1.0 - spec) * rw * S[a] + spec * f[fidx(p, mirror, j, i)];
+    }
+  }
 }
 
-static void apply_walls(const orc_lattice *L, const orc_params *p, double *f) {
+static void apply_walls(const orc_lattice *L, const orc_params *p, double *f, double t) {
   if (p->bc_y != 1) return;
   for (int i = 0; i < p->nx; ++i) {
-    wall_node(L, p, f, i, 0, 0);
-    wall_node(L, p, f, i, p->ny - 1, 1);
+    wall_node(L, p, f, i, 0, 0, t);
+    wall_node(L, p, f, i, p->ny - 1, 1, t);
   }
 }
 
@@ -463,6 +479,7 @@ static int check_params(const orc_params *p) {
   if (p->nx < 1 || p->ny < 1) return -1;
   if (p->bc_y == 1 && p->ny < 2) return -1;
   if (p->scheme != 0 && p->scheme != 1) return -1;
+  if (!(p->wall_specular >= 0.0 && p->wall_specular <= 1.0)) return -1;
   return 0;
 }
 
@@ -481,7 +498,7 @@ int orc_init(const orc_params *p, const double *fields, double *f) {
       for (int a = 0; a < L.Q; ++a)
         f[fidx(p, a, j, i)] = rho * feq0_S(p->order, T, u, L.cx[a], L.cy[a], L.w[a]);
     }
-  apply_walls(&L, p, f);
+  apply_walls(&L, p, f, p->time);
   return 0;
 }
 
@@ -542,16 +559,18 @@ int orc_step(const orc_params *p, const double *fin, double *fout) {
     }
   }
   free(fstar);
-  apply_walls(&L, p, fout);
+  apply_walls(&L, p, fout, p->time + p->dt); /* the wall state at the new time */
   return 0;
 }
 
-/* nsteps steps; f is updated in place (work is a scratch array of the same
- * size). */
+/* nsteps steps from time p->time; f is updated in place (work is a scratch
+ * array of the same size). */
 int orc_run(const orc_params *p, double *f, double *work, int64_t nsteps) {
   size_t n = (size_t)p->nroots * p->nroots * p->nx * p->ny;
+  orc_params q = *p;
   for (int64_t s = 0; s < nsteps; ++s) {
-    if (orc_step(p, f, work)) return -1;
+    q.time = p->time + (double)s * p->dt;
+    if (orc_step(&q, f, work)) return -1;
     memcpy(f, work, n * sizeof(double));
   }
   return 0;

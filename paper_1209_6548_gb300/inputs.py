@@ -35,6 +35,8 @@ class Problem:
     g:      body force (g_x, g_y).
     init:   'rest' or 'tgv' (Taylor-Green vortex with density noise).
     scheme: UNSPLIT (both flux differences from f^n, as printed) or SPLIT.
+    wall_specular, wall_T_amp, wall_T_freq: Maxwell walls (fraction re-emitted
+        specularly) and sinusoidal wall heating.
     """
 
     name: str
@@ -57,6 +59,9 @@ class Problem:
     seed: int = 0
     steps: int = 1000
     scheme: int = UNSPLIT
+    wall_specular: float = 0.0  # 1 - accommodation gamma of the Maxwell wall model
+    wall_T_amp: float = 0.0     # wall heating T_w(t) = wall_T + amp sin(freq t)
+    wall_T_freq: float = 0.0
 
     @property
     def cells(self) -> int:
@@ -86,6 +91,14 @@ def fourier(ny: int = 64, kn: float = 0.1, b: float = -0.5) -> Problem:
     """Fourier heat transfer between walls at T = 1 -/+ 0.05."""
     return Problem(name=f"fourier_4x{ny}", nroots=4, nx=4, ny=ny, bc_y=DIFFUSE, kn=kn, b=b,
                    wall_T=(0.95, 1.05))
+
+
+def unsteady_heating(kn: float = 0.1, b: float = -0.5, st: float = 0.5553603672697958, amp: float = 0.002,
+                     ny: int = 64, steps: int = 2000) -> Problem:
+    """Both walls heated as T_w = 1 + amp sin(St t), gas initially at rest at
+    T = 1 (Sec. 4.2; St = pi sqrt(2)/8 by default)."""
+    return Problem(name=f"heating_kn{kn:g}_st{st:.3f}", nroots=4, nx=4, ny=ny, bc_y=DIFFUSE, kn=kn, b=b,
+                   wall_T_amp=amp, wall_T_freq=st, steps=steps)
 
 
 def initial_fields(p: Problem) -> np.ndarray:

@@ -7,8 +7,9 @@ library, so that neither side's input comes from the other.
 Spacing: a periodic axis of n nodes has delta = 1/n; with walls on rows 0 and
 ny-1 the channel width is 1, delta_y = 1/(ny-1) and delta_x = delta_y.
 Time step: dt = min(cfl * min(dx, dy) / c_max, tau_ref) with
-tau_ref = (Kn/Pr) T_max^(varpi-1) / rho_max (forward-Euler relaxation stays
-at dt/tau <= 1 at the reference state).
+tau_ref = (Kn/Pr) T_max^(varpi-1) / rho_max, T_max over the initial fields and
+the walls' peak temperature (forward-Euler relaxation stays at dt/tau <= 1 at
+the reference state).
 """
 from __future__ import annotations
 
@@ -35,7 +36,7 @@ def time_step(p: Problem, fields=None) -> float:
     dx, dy = spacing(p)
     c, _ = O.gauss_hermite_1d(p.nroots)
     dt_cfl = p.cfl * min(dx, dy) / float(np.max(np.abs(c)))
-    tmax = max(p.wall_T) if p.bc_y != PERIODIC else 1.0
+    tmax = max(p.wall_T) + abs(p.wall_T_amp) if p.bc_y != PERIODIC else 1.0
     rmax = 1.0
     if fields is not None:
         tmax = max(tmax, float(fields[3].max()))
@@ -50,7 +51,8 @@ def oracle_params(p: Problem, dt: float, nx=None, ny=None, bc_y=None):
     return O.make_params(nroots=p.nroots, order=order_of(p), nx=nx or p.nx, ny=ny or p.ny,
                          bc_y=p.bc_y if bc_y is None else bc_y, kn=p.kn, b=p.b,
                          visc_exp=p.visc_exp, dt=dt, dx=dx, dy=dy, wall_T=tuple(p.wall_T),
-                         wall_ux=tuple(p.wall_ux), g=tuple(p.g), scheme=p.scheme)
+                         wall_ux=tuple(p.wall_ux), g=tuple(p.g), scheme=p.scheme,
+                         wall_specular=p.wall_specular, wall_T_amp=p.wall_T_amp, wall_T_freq=p.wall_T_freq)
 
 
 GROUPS = {"rho": ("rho",), "T": ("T",), "u": ("ux", "uy"), "sigma": ("sxx", "sxy", "syy"),

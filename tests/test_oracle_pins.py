@@ -623,3 +623,73 @@ def test_fourier_walls_exchange_mass_at_a_constant_rate():
     d = np.diff(masses)
     assert np.all(d > 0) and np.ptp(d) < 1e-3 * abs(d.mean())
     assert 1e-5 < d.mean() / masses[0] < 1e-3
+
+
+# ---------------------------------------------------------------- Maxwell walls, wall heating
+def test_specular_walls_keep_any_rest_state():
+    """Fully specular walls (gamma = 0 in the Maxwell model of Sec. 3.2) impose
+    no wall temperature: a resting gas at T = 1.1 between walls held at 1.0
+    stays exactly as it is (a diffuse wall would heat or cool it).  Like the
+    diffuse rule, the replacement of the wall node's outgoing half is not a
+    conservation law for non-equilibrium states, so only the rest state is
+    pinned here."""
+    prob = Problem(name="s", nroots=4, nx=3, ny=12, bc_y=DIFFUSE, kn=0.1, b=-0.5, wall_T=(1.0, 1.0),
+                   wall_specular=1.0)
+    p = oracle_params(prob, time_step(prob))
+    fields = np.zeros((4, 12, 3))
+    fields[0], fields[3] = 1.0, 1.1
+    f = O.init(p, fields)
+    assert np.max(np.abs(O.run(p, f, 20) - f)) < 1e-15
+    pd = oracle_params(Problem(name="d", nroots=4, nx=3, ny=12, bc_y=DIFFUSE, kn=0.1, b=-0.5), time_step(prob))
+    fd = O.init(pd, fields)
+    assert np.max(np.abs(O.run(pd, fd, 20) - fd)) > 1e-6
+
+
+@pytest.mark.parametrize("spec", [0.0, 0.3, 1.0])
+def test_maxwell_wall_zero_normal_mass_flux(spec):
+    prob = Problem(name="m", nroots=4, nx=4, ny=10, bc_y=DIFFUSE, kn=0.1, b=0.0, wall_ux=(-0.05, 0.05),
+                   wall_T=(0.97, 1.04), wall_specular=spec)
+    from paper_1209_6548_gb300.inputs import random_fields
+    fields = random_fields(prob, seed=9)
+    p = oracle_params(prob, time_step(prob, fields))
+    f = O.init(p, fields)
+    cx, cy, w = O.velocity_set(4)
+    for _ in range(3):
+        f = O.step(p, f)
+        for j in (0, prob.ny - 1):
+            assert np.max(np.abs(np.einsum("a,ai->i", cy, f[:, j, :]))) < 1e-15
+
+
+def test_wall_heating_is_linear_in_the_amplitude_and_zero_amplitude_is_static():
+    """The unsteady heating of Sec. 4.2 (T_w = 1 + A sin(St t)) is a small
+    signal: the gas's temperature perturbation doubles when A doubles (to the
+    order A^2 of the nonlinearity), and A = 0 is the static wall exactly."""
+    from paper_1209_6548_gb300 import inputs as I
+    runs = {}
+    for amp in (0.0, 0.002, 0.004):
+        prob = I.unsteady_heating(kn=0.1, amp=amp, ny=24)
+        p = oracle_params(prob, time_step(I.unsteady_heating(kn=0.1, amp=0.004, ny=24)))
+        runs[amp] = O.moments(p, O.run(p, O.init(p), 600))[0]
+    rest = O.moments(oracle_params(I.unsteady_heating(kn=0.1, amp=0.0, ny=24), 1.0), O.init(oracle_params(
+        I.unsteady_heating(kn=0.1, amp=0.0, ny=24), 1.0)))[0]
+    assert np.max(np.abs(runs[0.0] - rest)) < 1e-15
+    d1 = runs[0.002][3] - 1.0
+    d2 = runs[0.004][3] - 1.0
+    assert np.max(np.abs(d1)) > 1e-4
+    assert np.max(np.abs(d2 - 2.0 * d1)) < 1e-2 * np.max(np.abs(d2))
+    u1, u2 = runs[0.002][2], runs[0.004][2]
+    assert np.max(np.abs(u2 - 2.0 * u1)) < 1e-2 * np.max(np.abs(u2))
+
+
+def test_heated_wall_reemits_the_maxwellian_of_the_new_time():
+    from paper_1209_6548_gb300 import inputs as I
+    prob = I.unsteady_heating(kn=0.1, amp=0.05, ny=12, st=3.0)
+    dt = time_step(prob)
+    p = oracle_params(prob, dt)
+    f = O.run(p, O.init(p), 7)
+    cx, cy, _ = O.velocity_set(4)
+    Tw = 1.0 + 0.05 * np.sin(3.0 * 7 * dt)
+    S = O.feq0(4, 3, Tw, 0.0, 0.0)
+    out = cy > 0
+    r = f[out, 0, 0] / S[out]
+    assert np.allclose(r, r[0], rtol=1e-13)
