@@ -99,6 +99,13 @@ typedef struct lesbgk_params {
   double wall_T[2];     /* wall temperatures, [0] = bottom (j=0), [1] = top */
   double wall_ux[2];    /* wall x-velocities (walls do not move in y) */
   double g[2];          /* body force (g_x, g_y) */
+  double wall_specular; /* Maxwell wall model (Sec. 3.2): fraction 1 - gamma of the outgoing half
+                           re-emitted specularly; 0 = fully diffuse (the paper's runs) */
+  double wall_T_amp;    /* wall heating (Sec. 4.2): T_w(t) = wall_T + wall_T_amp sin(wall_T_freq t) */
+  double wall_T_freq;   /* (St in the units of Sec. 2.2); amp 0 = steady walls.  The wall
+                           tables are rebuilt in FP64 on the host for each step's time.
+                           Specular fractions need FP32 storage; heating takes any storage.
+                           The batched solver takes steady, fully diffuse walls only. */
 } lesbgk_params;
 
 /* Read-only facts about a created solver. */

@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kBBlock) k_batch_step(const BatchArgs B, const
       }
       acc[a] = fmaf(-ax[ix], diff, acc[a]);
     }
-    if (walls && (j == 0 || j == ny - 1)) wall_fix<NR>(acc, (j == 0) ? 0 : 1, B.lat, D);
+    if (walls && (j == 0 || j == ny - 1)) wall_fix<NR, false>(acc, (j == 0) ? 0 : 1, B.lat, D);
     if (k < rows) {
       float *o = fout + (long long)j * rstride + (long long)lx * V;
 #pragma unroll
@@ -598,6 +598,9 @@ extern "C" int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const d
   const int cls = class_of(p->nroots, order);
   if (cls < 0) return fail(LESBGK_EINVAL, "batched instances take D2Q16 (order 3) or D2Q36 (order 4)");
   if (p->nx != b->nx) return fail(LESBGK_EINVAL, "instance nx %d differs from the batch's %d", p->nx, b->nx);
+  if (p->storage != LESBGK_F32) return fail(LESBGK_EINVAL, "batched instances store FP32 populations");
+  if (p->wall_specular != 0.0 || p->wall_T_amp != 0.0)
+    return fail(LESBGK_EINVAL, "batched instances take steady, fully diffuse walls");
   if ((long long)(p->ny + b->rows - 1) / b->rows > (long long)kItemsPerSlot)
     return fail(LESBGK_EINVAL, "ny %d too large for the batch work list", p->ny);
   int slot = -1;

@@ -235,10 +235,15 @@ __device__ __forceinline__ void collide(const float (&F)[NR * NR], float (&S)[NR
   hermite_evaluate<NR, N>(d, S, Lt);
 }
 
-// Diffuse wall of Sec. 3.2 on one node's updated deviations: rho_W from the
-// incoming half, outgoing half = rho_W S_a(T_w, u_w).  side 0: bottom
-// (outgoing c_y > 0), side 1: top (outgoing c_y < 0).
-template <int NR, class TT, class TW>
+// Wall rule of Sec. 3.2 on one node's updated deviations: rho_W from the
+// incoming half (zero net normal mass flux through the wall), outgoing half =
+// rho_W S_a(T_w, u_w), the fully diffuse wall; with SPEC (Maxwell model,
+// accommodation gamma = 1 - W.wspec) the outgoing half is instead
+// gamma rho_W S_a + (1 - gamma) f_a', a' the incoming mirror image (c_y -> -c_y).
+// side 0: bottom (outgoing c_y > 0), side 1: top (outgoing c_y < 0).  The
+// S tables are built on the host in FP64 for the wall temperature of the time
+// the launch writes (a varying one for the heated walls of Sec. 4.2).
+template <int NR, bool SPEC, class TT, class TW>
 __device__ __forceinline__ void wall_fix(float (&O)[NR * NR], int side, const TT &T, const TW &W) {
   constexpr int H = NR / 2;
   float s = 0.0f;
@@ -255,7 +260,11 @@ __device__ __forceinline__ void wall_fix(float (&O)[NR * NR], int side, const TT
 #pragma unroll
     for (int iy = 0; iy < NR; ++iy) {
       const bool outgoing = side == 0 ? (iy >= H) : (iy < H);
-      if (outgoing) O[ix * NR + iy] = fmaf(rw1, W.wS[side][ix * NR + iy], W.wSdev[side][ix * NR + iy]);
+      if (outgoing) {
+        const float diffuse = fmaf(rw1, W.wS[side][ix * NR + iy], W.wSdev[side][ix * NR + iy]);
+        if constexpr (SPEC) O[ix * NR + iy] = fmaf(W.wspec, O[ix * NR + (NR - 1 - iy)] - diffuse, diffuse);
+        else O[ix * NR + iy] = diffuse;
+      }
     }
 }
 

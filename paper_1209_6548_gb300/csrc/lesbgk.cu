@@ -44,7 +44,7 @@ constexpr int kMomBlock = 256;
 // ---------------------------------------------------------------------------
 // The fused time step (Sec. 3.1 + Sec. 3.2).
 // ---------------------------------------------------------------------------
-template <int NR, int N, bool SPLIT, int RING, class S>
+template <int NR, int N, bool SPLIT, int RING, class S, bool SPEC>
 __global__ void __launch_bounds__(kBlock) k_step(const S *__restrict__ fin, S *__restrict__ fout,
                                                  const KArgs A) {
   using Lay = Layout<NR, S>;
@@ -184,7 +184,11 @@ __global__ void __launch_bounds__(kBlock) k_step(const S *__restrict__ fin, S *_
       acc[a] = fmaf(-ax, diff, acc[a]);
     }
 
-    if (A.walls && (j == 0 || j == ny - 1)) wall_fix<NR>(acc, (j == 0) ? 0 : 1, A, A);
+    if (A.walls && (j == 0 || j == ny - 1)) {
+      // the Maxwell wall (specular share) is a separate instantiation so that
+      // the hot loop of everything else keeps its code
+      wall_fix<NR, SPEC>(acc, (j == 0) ? 0 : 1, A, A);
+    }
 
     if (writer) {
       S *o = fout + (long long)j * rstride + (long long)xw * V;
@@ -227,7 +231,10 @@ __global__ void __launch_bounds__(kBlock) k_init(const double *__restrict__ fiel
     float Sv[Q];
     hermite_evaluate<NR, N>(e, Sv, A);
     const int j = (int)(c / A.nx);
-    if (A.walls && (j == 0 || j == A.ny - 1)) wall_fix<NR>(Sv, j == 0 ? 0 : 1, A, A);
+    if (A.walls && (j == 0 || j == A.ny - 1)) {
+      if (A.wspec != 0.0f) wall_fix<NR, true>(Sv, j == 0 ? 0 : 1, A, A);
+      else wall_fix<NR, false>(Sv, j == 0 ? 0 : 1, A, A);
+    }
 #pragma unroll
     for (int g = 0; g < Lay::G; ++g) st_group_s<NR, S>(f + c * Lay::V, gstride, g, Sv, A);
   }
@@ -372,6 +379,7 @@ struct lesbgk {
   size_t buf_bytes;
   double *partial, *sums;
   KArgs args;
+  Setup su;  // FP64 inputs of the wall tables (rebuilt per step for heated walls)
   double dt, dx, dy, cmax, tau_ref;
   int64_t steps;
   int sm_count;
@@ -418,6 +426,7 @@ int build_tables(lesbgk *h, const double *h_init) {
   Setup s;
   if (int rc = build_setup(h->p, h->order, h_init, &s)) return rc;
   h->args = s.args;
+  h->su = s;
   h->dt = s.dt;
   h->dx = s.dx;
   h->dy = s.dy;
@@ -464,9 +473,18 @@ cudaError_t allow_smem(const lesbgk *h) {
     constexpr int NR = decltype(r)::value, N = decltype(n)::value;
     using S = decltype(st);
     constexpr int smem = (int)step_smem_bytes<NR, S>();
-    e = cudaFuncSetAttribute(k_step<NR, N, true, kRing, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(k_step<NR, N, true, kRing, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_step<NR, N, false, kRing, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      e = cudaFuncSetAttribute(k_step<NR, N, false, kRing, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               smem);
+    if constexpr (std::is_same<S, float>::value) {
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_step<NR, N, true, kRing, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_step<NR, N, false, kRing, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem);
+    }
   });
   return e;
 }
@@ -480,8 +498,16 @@ int launch_step(lesbgk *h, const void *fin, void *fout, cudaStream_t s) {
     constexpr size_t smem = step_smem_bytes<NR, S>();
     const S *fi = static_cast<const S *>(fin);
     S *fo = static_cast<S *>(fout);
-    if (h->p.scheme == LESBGK_SPLIT) k_step<NR, N, true, kRing, S><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
-    else k_step<NR, N, false, kRing, S><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+    const bool split = h->p.scheme == LESBGK_SPLIT;
+    if constexpr (std::is_same<S, float>::value) {
+      if (h->args.walls && h->args.wspec != 0.0f) {  // Maxwell walls: FP32 storage only (checked at set-up)
+        if (split) k_step<NR, N, true, kRing, S, true><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+        else k_step<NR, N, false, kRing, S, true><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+        return;
+      }
+    }
+    if (split) k_step<NR, N, true, kRing, S, false><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+    else k_step<NR, N, false, kRing, S, false><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
   });
   return 0;
 }
@@ -618,6 +644,7 @@ extern "C" int lesbgk_reinit(lesbgk *h, const double *d_fields, void *stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   h->cur = 0;
   h->steps = 0;
+  if (heated_walls(h->su)) set_wall_time(h->su, 0.0, &h->args);
   launch_init(h, d_fields, h->buf[0], s);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? 0 : cuda_fail(e, "init kernel");
@@ -629,6 +656,8 @@ extern "C" int lesbgk_step(lesbgk *h, int64_t nsteps, void *stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int64_t k = 0; k < nsteps; ++k) {
     h->args.seed = (unsigned)(h->steps + k) * 0x9e3779b9u + 0x7f4a7c15u;  // a new rounding key per step
+    if (heated_walls(h->su))  // wall tables at the time of the state written
+      set_wall_time(h->su, (double)(h->steps + k + 1) * h->dt, &h->args);
     launch_step(h, h->buf[h->cur], h->buf[h->cur ^ 1], s);
     h->cur ^= 1;
   }

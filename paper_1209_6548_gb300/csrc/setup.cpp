@@ -54,6 +54,14 @@ int check_params(const lesbgk_params *p) {
   if (!(p->visc_exp >= 0.0 && p->visc_exp <= 1.0)) return fail(LESBGK_EINVAL, "visc_exp must be in [0,1]");
   if (!(p->dt >= 0.0) || !std::isfinite(p->dt)) return fail(LESBGK_EINVAL, "dt must be >= 0");
   if (p->dt == 0.0 && !(p->cfl > 0.0 && p->cfl <= 1.0)) return fail(LESBGK_EINVAL, "cfl must be in (0,1]");
+  if (!(p->wall_specular >= 0.0 && p->wall_specular <= 1.0))
+    return fail(LESBGK_EINVAL, "wall_specular must be in [0, 1]");
+  if (!std::isfinite(p->wall_T_amp) || !std::isfinite(p->wall_T_freq))
+    return fail(LESBGK_EINVAL, "non-finite wall heating parameters");
+  if (!(std::fabs(p->wall_T_amp) < std::fmin(p->wall_T[0], p->wall_T[1])))
+    return fail(LESBGK_EINVAL, "|wall_T_amp| must stay below the wall temperatures");
+  if (p->wall_specular != 0.0 && p->storage != LESBGK_F32)
+    return fail(LESBGK_EINVAL, "Maxwell walls (wall_specular > 0) are built for FP32 storage");
   for (int s = 0; s < 2; ++s) {
     if (!(p->wall_T[s] > 0.0) || !std::isfinite(p->wall_T[s])) return fail(LESBGK_EINVAL, "wall_T must be > 0");
     if (!std::isfinite(p->wall_ux[s]) || !std::isfinite(p->g[s])) return fail(LESBGK_EINVAL, "non-finite wall_ux/g");
@@ -80,7 +88,8 @@ int build_setup(const lesbgk_params &p, int order, const double *h_init, Setup *
   }
   // reference state for tau_ref
   double tmax = 1.0, rmax = 1.0;
-  if (p.bc_y == LESBGK_DIFFUSE) tmax = std::fmax(tmax, std::fmax(p.wall_T[0], p.wall_T[1]));
+  if (p.bc_y == LESBGK_DIFFUSE)
+    tmax = std::fmax(tmax, std::fmax(p.wall_T[0], p.wall_T[1]) + std::fabs(p.wall_T_amp));
   if (h_init) {
     const size_t cells = (size_t)p.nx * p.ny;
     double r0 = h_init[0];
@@ -119,11 +128,55 @@ int build_setup(const lesbgk_params &p, int order, const double *h_init, Setup *
     A.ay[i] = (float)(c[i] * dt / h->dy);
     A.ky[i] = (float)(0.5 * (1.0 - std::fabs(c[i]) * dt / h->dy));
   }
+  // FP16 holds 2^10 (f_a - w_a)/w_a: relative deviations down to 6e-8 stay in
+  // its normal range (where stochastic rounding is unbiased) and up to 64 fit
+  const double store_scale = p.storage == LESBGK_F16 ? 1024.0 : 1.0;
+  for (int ix = 0; ix < nr; ++ix)
+    for (int iy = 0; iy < nr; ++iy) {
+      A.wq[ix * nr + iy] = (float)(w[ix] * w[iy] / store_scale);
+      A.iwq[ix * nr + iy] = (float)(store_scale / (w[ix] * w[iy]));
+    }
+  A.c_omega = (float)(dt / (p.kn * (1.0 - p.b)));
+  A.visc_pow = (float)(1.0 - p.visc_exp);
+  A.vmode = p.visc_exp == 0.5 ? 1 : (p.visc_exp == 1.0 ? 2 : 0);
+  A.b = (float)p.b;
+  A.beta = (float)(0.5 * (1.0 - p.b));
+  A.dtgx = (float)(dt * p.g[0]);
+  A.dtgy = (float)(dt * p.g[1]);
+  A.has_force = (p.g[0] != 0.0 || p.g[1] != 0.0) ? 1 : 0;
+  A.nx = p.nx;
+  A.ny = p.ny;
+  A.walls = p.bc_y == LESBGK_DIFFUSE ? 1 : 0;
+  A.wspec = (float)p.wall_specular;
+  A.plane = (long long)p.nx * p.ny;
+  h->nroots = nr;
+  h->order = N;
+  for (int i = 0; i < nr; ++i) {
+    h->c[i] = c[i];
+    h->w[i] = w[i];
+  }
+  for (int s = 0; s < 2; ++s) {
+    h->wall_T[s] = p.wall_T[s];
+    h->wall_ux[s] = p.wall_ux[s];
+  }
+  h->wall_T_amp = p.wall_T_amp;
+  h->wall_T_freq = p.wall_T_freq;
+  set_wall_time(*h, 0.0, &h->args);
+  return 0;
+}
+
+void set_wall_time(const Setup &h, double t, KArgs *out) {
+  using namespace lesbgk_tables;
+  KArgs &A = *out;
+  const int nr = h.nroots, N = h.order;
+  const double *c = h.c, *w = h.w;
+  const double fact[kMaxOrder + 1] = {1, 1, 2, 6, 24};
+  const double heat = h.wall_T_amp != 0.0 ? h.wall_T_amp * std::sin(h.wall_T_freq * t) : 0.0;
   // wall equilibria S_a(T_w, u_w) at order N (b = 0 Gaussian projection)
   for (int s = 0; s < 2; ++s) {
     double e[kMaxOrder + 1][kMaxOrder + 1];
-    const double th = p.wall_T[s] - 1.0;
-    gaussian_hermite_moments(N, 1.0, p.wall_ux[s], 0.0, th, 0.0, th, e);
+    const double th = h.wall_T[s] + heat - 1.0;
+    gaussian_hermite_moments(N, 1.0, h.wall_ux[s], 0.0, th, 0.0, th, e);
     double A_out = 0.0, Z_out = 0.0;
     for (int ix = 0; ix < nr; ++ix) {
       double hx[kMaxOrder + 1];
@@ -149,27 +202,6 @@ int build_setup(const lesbgk_params &p, int order, const double *h_init, Setup *
     A.wA[s] = (float)A_out;
     A.wB[s] = (float)(1.0 / Z_out);
   }
-  // FP16 holds 2^10 (f_a - w_a)/w_a: relative deviations down to 6e-8 stay in
-  // its normal range (where stochastic rounding is unbiased) and up to 64 fit
-  const double store_scale = p.storage == LESBGK_F16 ? 1024.0 : 1.0;
-  for (int ix = 0; ix < nr; ++ix)
-    for (int iy = 0; iy < nr; ++iy) {
-      A.wq[ix * nr + iy] = (float)(w[ix] * w[iy] / store_scale);
-      A.iwq[ix * nr + iy] = (float)(store_scale / (w[ix] * w[iy]));
-    }
-  A.c_omega = (float)(dt / (p.kn * (1.0 - p.b)));
-  A.visc_pow = (float)(1.0 - p.visc_exp);
-  A.vmode = p.visc_exp == 0.5 ? 1 : (p.visc_exp == 1.0 ? 2 : 0);
-  A.b = (float)p.b;
-  A.beta = (float)(0.5 * (1.0 - p.b));
-  A.dtgx = (float)(dt * p.g[0]);
-  A.dtgy = (float)(dt * p.g[1]);
-  A.has_force = (p.g[0] != 0.0 || p.g[1] != 0.0) ? 1 : 0;
-  A.nx = p.nx;
-  A.ny = p.ny;
-  A.walls = p.bc_y == LESBGK_DIFFUSE ? 1 : 0;
-  A.plane = (long long)p.nx * p.ny;
-  return 0;
 }
 
 }  // namespace lesbgk_setup

@@ -32,12 +32,18 @@ struct KArgs {
   int rows, nstrips, nseg;
   long long plane;             // nx*ny
   unsigned seed;               // per-launch key of the 16-bit stochastic rounding
+  float wspec;                 // specular fraction 1 - gamma of the Maxwell wall (0: fully diffuse)
 };
 
 // What one solve's set-up produces.
 struct Setup {
   KArgs args;                      // tables and per-solve scalars (nx, ny, plane, walls filled)
   double dt, dx, dy, cmax, tau_ref;
+  // what the wall tables are built from (Sec. 3.2; heating of Sec. 4.2)
+  int nroots, order;
+  double c[kMaxR], w[kMaxR];       // FP64 quadrature
+  double wall_T[2], wall_ux[2];    // steady wall temperature and velocity
+  double wall_T_amp, wall_T_freq;  // T_w(t) = wall_T + wall_T_amp sin(wall_T_freq t)
 };
 
 // Record a message for lesbgk_last_error() and return code.
@@ -53,5 +59,12 @@ int check_params(const lesbgk_params *p);
 // spacing, tau_ref and dt (Sec. 2.2; the dt rule is the library's reading).
 // h_init (host, double[4][ny][nx], may be NULL) enters tau_ref and is checked.
 int build_setup(const lesbgk_params &p, int order, const double *h_init, Setup *out);
+
+// Build the wall tables (wS, wSdev, wA, wB) of *A in FP64 for the wall
+// temperature at time t; build_setup calls it for args with t = 0.
+void set_wall_time(const Setup &h, double t, KArgs *A);
+
+// Whether the wall temperature varies in time (the tables then change per step).
+inline bool heated_walls(const Setup &h) { return h.args.walls && h.wall_T_amp != 0.0; }
 
 }  // namespace lesbgk_setup

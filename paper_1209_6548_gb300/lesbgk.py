@@ -44,6 +44,7 @@ class Params(C.Structure):
         ("kn", C.c_double), ("b", C.c_double), ("visc_exp", C.c_double),
         ("cfl", C.c_double), ("dt", C.c_double),
         ("wall_T", C.c_double * 2), ("wall_ux", C.c_double * 2), ("g", C.c_double * 2),
+        ("wall_specular", C.c_double), ("wall_T_amp", C.c_double), ("wall_T_freq", C.c_double),
     ]
 
 
@@ -119,7 +120,8 @@ def _check(rc: int) -> None:
 
 
 def make_params(*, nroots=4, order=0, nx, ny, bc_y=DIFFUSE, kn, b, visc_exp=0.5, cfl=0.5, dt=0.0,
-                wall_T=(1.0, 1.0), wall_ux=(0.0, 0.0), g=(0.0, 0.0), storage=F32, scheme=UNSPLIT) -> Params:
+                wall_T=(1.0, 1.0), wall_ux=(0.0, 0.0), g=(0.0, 0.0), storage=F32, scheme=UNSPLIT,
+                wall_specular=0.0, wall_T_amp=0.0, wall_T_freq=0.0) -> Params:
     p = Params()
     p.struct_size = C.sizeof(Params)
     p.nroots, p.order, p.nx, p.ny, p.bc_y, p.storage = nroots, order, nx, ny, bc_y, storage
@@ -128,6 +130,7 @@ def make_params(*, nroots=4, order=0, nx, ny, bc_y=DIFFUSE, kn, b, visc_exp=0.5,
     p.wall_T[0], p.wall_T[1] = wall_T
     p.wall_ux[0], p.wall_ux[1] = wall_ux
     p.g[0], p.g[1] = g
+    p.wall_specular, p.wall_T_amp, p.wall_T_freq = wall_specular, wall_T_amp, wall_T_freq
     return p
 
 
@@ -135,7 +138,8 @@ def params_from_problem(prob, dt: float = 0.0) -> Params:
     return make_params(nroots=prob.nroots, order=prob.order, nx=prob.nx, ny=prob.ny, bc_y=prob.bc_y,
                        kn=prob.kn, b=prob.b, visc_exp=prob.visc_exp, cfl=prob.cfl, dt=dt,
                        wall_T=tuple(prob.wall_T), wall_ux=tuple(prob.wall_ux), g=tuple(prob.g),
-                       scheme=prob.scheme)
+                       scheme=prob.scheme, wall_specular=prob.wall_specular, wall_T_amp=prob.wall_T_amp,
+                       wall_T_freq=prob.wall_T_freq)
 
 
 def workspace_size(p: Params) -> int:

@@ -54,6 +54,11 @@ def test_struct_sizes_match_header(lib):
     (dict(cfl=1.5), L.EINVAL),
     (dict(visc_exp=1.5), L.EINVAL),
     (dict(storage=7), L.EINVAL),
+    (dict(wall_specular=1.5), L.EINVAL),
+    (dict(wall_specular=-0.1), L.EINVAL),
+    (dict(wall_specular=0.5, storage=L.F16), L.EINVAL),  # Maxwell walls: FP32 storage only
+    (dict(wall_T_amp=1.0), L.EINVAL),                     # T_w would reach 0
+    (dict(wall_T_amp=float("nan")), L.EINVAL),
 ])
 def test_invalid_arguments_rejected(lib, kw, code):
     base = dict(nx=4, ny=8, kn=0.1, b=0.0, bc_y=L.DIFFUSE)
@@ -61,6 +66,12 @@ def test_invalid_arguments_rejected(lib, kw, code):
     with pytest.raises(L.LesbgkError) as e:
         L.workspace_size(L.make_params(**base))
     assert e.value.code == code
+
+
+def test_wall_models_accepted(lib):
+    for kw in (dict(wall_specular=1.0), dict(wall_T_amp=0.02, wall_T_freq=0.5),
+               dict(wall_T_amp=0.02, wall_T_freq=0.5, storage=L.BF16)):
+        assert L.workspace_size(L.make_params(nx=4, ny=8, kn=0.1, b=0.0, bc_y=L.DIFFUSE, **kw)) > 0
 
 
 def test_workspace_size_formula(lib):

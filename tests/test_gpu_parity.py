@@ -50,6 +50,7 @@ def run_pair(prob, fields, checkpoints, dt=None):
     done = 0
     out = []
     for n in checkpoints:
+        op.time = done * dt  # the oracle's clock follows the steps taken (time-dependent walls)
         f = O.run(op, f, n - done)
         s.step(n - done)
         done = n
@@ -310,3 +311,29 @@ def test_d2q36_order3():
     res, *_ = run_pair(prob, None, [1, 100])
     for n, g, r, *_ in res:
         assert_fields_close(g, r, what=f"d2q36 N=3 step {n}")
+
+
+# ---------------------------------------------------------------- wall models
+@pytest.mark.parametrize("spec", [0.3, 1.0])
+def test_maxwell_walls(spec):
+    """Maxwell walls with accommodation 1 - spec (Sec. 3.2's model), moving and
+    at two temperatures, rough interior."""
+    prob = I.Problem(name="mw", nx=32, ny=30, bc_y=I.DIFFUSE, kn=0.1, b=-0.5, wall_ux=(-0.05, 0.05),
+                     wall_T=(0.97, 1.04), wall_specular=spec)
+    fields = I.random_fields(prob, seed=12, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
+    res, *_ = run_pair(prob, fields, [1, 10])
+    for n, g, r, *_ in res:
+        assert_fields_close(g, r, what=f"spec {spec} step {n}")
+
+
+@pytest.mark.parametrize("kn,st", [(0.1, 0.5553603672697958), (0.5, 1.1107207345395915)])
+def test_unsteady_wall_heating(kn, st):
+    """Both walls heated as T_w = 1 + A sin(St t) (Sec. 4.2), A = 0.02 for a
+    clear signal, gas at rest at T = 1 initially; up to t ~ 3 pi / 2 / St."""
+    prob = I.unsteady_heating(kn=kn, st=st, amp=0.02, ny=40)
+    dt = time_step(prob)
+    n_end = int(round(3 * np.pi / 2 / st / dt / 10)) * 10
+    res, *_ = run_pair(prob, None, [1, 50, n_end], dt=dt)
+    for n, g, r, *_ in res:
+        assert_fields_close(g, r, what=f"heating step {n}")
+    assert np.max(np.abs(res[-1][2][3] - 1.0)) > 1e-3  # the walls did heat the gas
