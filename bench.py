@@ -84,10 +84,11 @@ def measured_peak():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-def committed_traffic(source_digest: str):
-    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_step_tgv4096_d2q16.md")
+def committed_traffic(source_digest: str, velocity_set: str = "d2q16", storage: str = "f32"):
+    """Per-launch DRAM bytes of the step kernel on this velocity set and
+    storage from the committed ncu summary, if it was taken on the current
+    kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"k_step_tgv4096_{velocity_set}.md")
     try:
         lines = open(path).read().splitlines()
     except OSError:
@@ -100,7 +101,7 @@ def committed_traffic(source_digest: str):
     if vals.get("kernel source sha256") != source_digest:
         return None
     try:
-        return float(vals["dram bytes per launch (scaled to 4096^2)"])
+        return float(vals[f"dram bytes per launch (scaled to 4096^2, {storage} storage)"])
     except (KeyError, ValueError):
         return None
 
@@ -611,7 +612,7 @@ def main():
     bytes_per_lup = 2 * q * (4 if args.storage == "f32" else 2)
     achieved = bytes_per_lup * cells / (kernel_ms / 1e3) / 1e9
     digest = source_digest()
-    traffic = committed_traffic(digest)
+    traffic = committed_traffic(digest, args.velocity_set, args.storage)
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(n, rows=1024 if nroots == 4 else 256, nroots=nroots)

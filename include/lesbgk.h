@@ -157,7 +157,8 @@ int lesbgk_step(lesbgk *h, int64_t nsteps, void *stream);
  * (sigma trace-free, q_i = 1/2 sum f C_i C^2, D = 2).
  * If h_sums is not NULL it receives, in HOST memory, double[4]: total mass,
  * x- and y-momentum and energy (sum over nodes of sum_a f_a {1, c_x, c_y,
- * c^2/2}), accumulated in FP64 in a fixed order (bitwise reproducible); this
+ * c^2/2}): per-node sums in FP32, summed in FP32 over runs of 16 nodes, the
+ * runs in FP64, in a fixed order (bitwise reproducible); this
  * synchronises the stream, and returns LESBGK_EDIVERGED if any is not
  * finite. */
 int lesbgk_moments(lesbgk *h, float *d_out, double *h_sums, void *stream);

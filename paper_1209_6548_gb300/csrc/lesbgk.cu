@@ -270,9 +270,97 @@ __global__ void __launch_bounds__(kBlock) k_group(const float *__restrict__ in, 
 }
 
 // ---------------------------------------------------------------------------
-// Moments of Eq. (mac) per node, plus FP64 block partial sums of mass,
-// momentum and energy.  out: float[9][ny][nx].
+// Moments of Eq. (mac) of one node from its deviations F = f - w, written to
+// out[k * cells + c] (k = rho, u_x, u_y, T, sigma_xx, sigma_xy, sigma_yy, q_x,
+// q_y) when out is set; returns in d the node's deviations of the conserved
+// sums sum_a df_a {1, c_x, c_y, c^2}: with the Hermite moments m_pq =
+// sum df He_p(c_x) He_q(c_y) these are m00, m10, m01 and m20 + m02 + 2 m00.
 // ---------------------------------------------------------------------------
+template <int NR>
+__device__ __forceinline__ void node_moments(const float (&F)[NR * NR], float *__restrict__ out, long long cells,
+                                             long long c, const KArgs &A, float (&d)[4]) {
+  float m[4][4];
+  hermite_moments<NR, 3>(F, m, A);
+  const float rho = 1.0f + m[0][0];
+  const float ir = __frcp_rn(rho);
+  const float ux = m[1][0] * ir, uy = m[0][1] * ir;
+  const float Mxx = fmaf(-m[1][0], ux, m[2][0]);
+  const float Mxy = fmaf(-m[1][0], uy, m[1][1]);
+  const float Myy = fmaf(-m[0][1], uy, m[0][2]);
+  const float trM = Mxx + Myy;
+  const float T = fmaf(0.5f * trM, ir, 1.0f);
+  const float u2 = ux * ux + uy * uy;
+  // sum f C_i C^2 = sum df c_i (c^2 - D - 2) - 2 M_ij u_j - u_i tr M - rho u_i u^2
+  const float hx = m[3][0] + m[1][2], hy = m[0][3] + m[2][1];
+  const float qx = 0.5f * (hx - 2.0f * (Mxx * ux + Mxy * uy) - ux * trM - rho * ux * u2);
+  const float qy = 0.5f * (hy - 2.0f * (Mxy * ux + Myy * uy) - uy * trM - rho * uy * u2);
+  if (out) {
+    out[c] = rho;
+    out[cells + c] = ux;
+    out[2 * cells + c] = uy;
+    out[3 * cells + c] = T;
+    out[4 * cells + c] = 0.5f * (Mxx - Myy);
+    out[5 * cells + c] = Mxy;
+    out[6 * cells + c] = 0.5f * (Myy - Mxx);
+    out[7 * cells + c] = qx;
+    out[8 * cells + c] = qy;
+  }
+  d[0] = m[0][0];
+  d[1] = m[1][0];
+  d[2] = m[0][1];
+  d[3] = fmaf(2.0f, m[0][0], m[2][0] + m[0][2]);
+}
+
+// Conservation totals: per-node sums in FP32 (above), summed in FP32 over
+// runs of kSumRun nodes, the runs in FP64 (GB300 issues about two FP64
+// operations per SM and clock, so one FP64 add per node and quantity would
+// cost as much as reading the populations).  Fixed order: reproducible.
+constexpr int kSumRun = 16;
+
+struct ConsSums {
+  float run[4] = {0.f, 0.f, 0.f, 0.f};
+  double tot[4] = {0.0, 0.0, 0.0, 0.0};
+  int n = 0;          // nodes in the current run
+  long long nodes = 0;
+  __device__ __forceinline__ void add(const float (&d)[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) run[k] += d[k];
+    if (++n == kSumRun) flush();
+  }
+  __device__ __forceinline__ void flush() {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      tot[k] += (double)run[k];
+      run[k] = 0.f;
+    }
+    nodes += n;
+    n = 0;
+  }
+  // Block totals of mass, x/y momentum and energy (sum f {1, c_x, c_y, c^2/2},
+  // f = w + df, sum_a w_a = 1, sum_a w_a c_a^2 = D = 2) into partial[4 * block].
+  __device__ __forceinline__ void write_block(double *__restrict__ partial) {
+    flush();
+    double v[4] = {(double)nodes + tot[0], tot[1], tot[2], (double)nodes + 0.5 * tot[3]};
+    __shared__ double red[4][kMomBlock / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] += __shfl_down_sync(kFull, v[k], o);
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) red[k][w] = v[k];
+    __syncthreads();
+    if (threadIdx.x < 4) {  // every block writes all four of its slots: no zeroing needed
+      double t = 0.0;
+      for (int k = 0; k < kMomBlock / 32; ++k) t += red[threadIdx.x][k];
+      partial[blockIdx.x * 4 + threadIdx.x] = t;
+    }
+  }
+};
+
+// Moments per node of the grouped layout, plus the block partial sums.
+// out: float[9][ny][nx] or nullptr.
 template <int NR, class S>
 __global__ void __launch_bounds__(kMomBlock) k_moments(const S *__restrict__ f, float *__restrict__ out,
                                                        double *__restrict__ partial, const KArgs A) {
@@ -280,75 +368,17 @@ __global__ void __launch_bounds__(kMomBlock) k_moments(const S *__restrict__ f, 
   constexpr int Q = Lay::Q;
   const long long cells = A.plane;
   const long long gstride = (long long)Lay::V * cells;
-  double sm = 0.0, sx = 0.0, sy = 0.0, se = 0.0;
+  ConsSums cs;
   for (long long c = blockIdx.x * (long long)kMomBlock + threadIdx.x; c < cells;
        c += (long long)gridDim.x * kMomBlock) {
     float F[Q];
 #pragma unroll
     for (int g = 0; g < Lay::G; ++g) ld_group_s<NR, S>(f + c * Lay::V, gstride, g, F, A);
-    float m[4][4];
-    hermite_moments<NR, 3>(F, m, A);
-    const float rho = 1.0f + m[0][0];
-    const float ir = __frcp_rn(rho);
-    const float ux = m[1][0] * ir, uy = m[0][1] * ir;
-    const float Mxx = fmaf(-m[1][0], ux, m[2][0]);
-    const float Mxy = fmaf(-m[1][0], uy, m[1][1]);
-    const float Myy = fmaf(-m[0][1], uy, m[0][2]);
-    const float trM = Mxx + Myy;
-    const float T = fmaf(0.5f * trM, ir, 1.0f);
-    const float u2 = ux * ux + uy * uy;
-    // sum f C_i C^2 = sum df c_i (c^2 - D - 2) - 2 M_ij u_j - u_i tr M - rho u_i u^2
-    const float hx = m[3][0] + m[1][2], hy = m[0][3] + m[2][1];
-    const float qx = 0.5f * (hx - 2.0f * (Mxx * ux + Mxy * uy) - ux * trM - rho * ux * u2);
-    const float qy = 0.5f * (hy - 2.0f * (Mxy * ux + Myy * uy) - uy * trM - rho * uy * u2);
-    if (out) {
-      out[c] = rho;
-      out[cells + c] = ux;
-      out[2 * cells + c] = uy;
-      out[3 * cells + c] = T;
-      out[4 * cells + c] = 0.5f * (Mxx - Myy);
-      out[5 * cells + c] = Mxy;
-      out[6 * cells + c] = 0.5f * (Myy - Mxx);
-      out[7 * cells + c] = qx;
-      out[8 * cells + c] = qy;
-    }
-    // FP64 conservation sums: sum_a f_a {1, c_x, c_y, c^2/2}, f_a = w_a + df_a
-    double dm = 0.0, dx = 0.0, dy = 0.0, de = 0.0;
-#pragma unroll
-    for (int a = 0; a < Q; ++a) {
-      const double cx = A.c[a / NR], cy = A.c[a % NR];
-      const double v = F[a];
-      dm += v;
-      dx += v * cx;
-      dy += v * cy;
-      de += v * (cx * cx + cy * cy);
-    }
-    sm += 1.0 + dm;
-    sx += dx;
-    sy += dy;
-    se += 0.5 * (2.0 + de);  // sum_a w_a c_a^2 = D = 2
+    float d[4];
+    node_moments<NR>(F, out, cells, c, A, d);
+    cs.add(d);
   }
-  __shared__ double red[4][kMomBlock / 32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    sm += __shfl_down_sync(kFull, sm, o);
-    sx += __shfl_down_sync(kFull, sx, o);
-    sy += __shfl_down_sync(kFull, sy, o);
-    se += __shfl_down_sync(kFull, se, o);
-  }
-  if (lane == 0) {
-    red[0][w] = sm;
-    red[1][w] = sx;
-    red[2][w] = sy;
-    red[3][w] = se;
-  }
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    double t = 0.0;
-    for (int k = 0; k < kMomBlock / 32; ++k) t += red[threadIdx.x][k];
-    partial[blockIdx.x * 4 + threadIdx.x] = t;
-  }
+  cs.write_block(partial);
 }
 
 __global__ void k_reduce_partials(const double *__restrict__ partial, int n, double *__restrict__ sums) {
@@ -791,7 +821,7 @@ __global__ void __launch_bounds__(kMomBlock) k_moments_public(const float *__res
                                                               double *__restrict__ partial, const KArgs A) {
   constexpr int Q = NR * NR;
   const long long cells = A.plane;
-  double sm = 0.0, sx = 0.0, sy = 0.0, se = 0.0;
+  ConsSums cs;
   const long long c0 = blockIdx.x * kNoAllocNodesPerBlock;
   for (int t = 0; t < kNoAllocNodesPerThread; ++t) {
     const long long c = c0 + (long long)t * kMomBlock + threadIdx.x;
@@ -799,67 +829,11 @@ __global__ void __launch_bounds__(kMomBlock) k_moments_public(const float *__res
     float F[Q];
 #pragma unroll
     for (int a = 0; a < Q; ++a) F[a] = __ldg(f + a * cells + c);
-    float m[4][4];
-    hermite_moments<NR, 3>(F, m, A);
-    const float rho = 1.0f + m[0][0];
-    const float ir = __frcp_rn(rho);
-    const float ux = m[1][0] * ir, uy = m[0][1] * ir;
-    const float Mxx = fmaf(-m[1][0], ux, m[2][0]);
-    const float Mxy = fmaf(-m[1][0], uy, m[1][1]);
-    const float Myy = fmaf(-m[0][1], uy, m[0][2]);
-    const float trM = Mxx + Myy;
-    const float T = fmaf(0.5f * trM, ir, 1.0f);
-    const float u2 = ux * ux + uy * uy;
-    const float hx = m[3][0] + m[1][2], hy = m[0][3] + m[2][1];
-    const float qx = 0.5f * (hx - 2.0f * (Mxx * ux + Mxy * uy) - ux * trM - rho * ux * u2);
-    const float qy = 0.5f * (hy - 2.0f * (Mxy * ux + Myy * uy) - uy * trM - rho * uy * u2);
-    if (out) {
-      out[c] = rho;
-      out[cells + c] = ux;
-      out[2 * cells + c] = uy;
-      out[3 * cells + c] = T;
-      out[4 * cells + c] = 0.5f * (Mxx - Myy);
-      out[5 * cells + c] = Mxy;
-      out[6 * cells + c] = 0.5f * (Myy - Mxx);
-      out[7 * cells + c] = qx;
-      out[8 * cells + c] = qy;
-    }
-    double dm = 0.0, dx = 0.0, dy = 0.0, de = 0.0;
-#pragma unroll
-    for (int a = 0; a < Q; ++a) {
-      const double cx = A.c[a / NR], cy = A.c[a % NR];
-      const double v = F[a];
-      dm += v;
-      dx += v * cx;
-      dy += v * cy;
-      de += v * (cx * cx + cy * cy);
-    }
-    sm += 1.0 + dm;
-    sx += dx;
-    sy += dy;
-    se += 0.5 * (2.0 + de);
+    float d[4];
+    node_moments<NR>(F, out, cells, c, A, d);
+    cs.add(d);
   }
-  __shared__ double red[4][kMomBlock / 32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    sm += __shfl_down_sync(kFull, sm, o);
-    sx += __shfl_down_sync(kFull, sx, o);
-    sy += __shfl_down_sync(kFull, sy, o);
-    se += __shfl_down_sync(kFull, se, o);
-  }
-  if (lane == 0) {
-    red[0][w] = sm;
-    red[1][w] = sx;
-    red[2][w] = sy;
-    red[3][w] = se;
-  }
-  __syncthreads();
-  if (threadIdx.x < 4) {  // every block writes all four of its slots: no zeroing needed
-    double t = 0.0;
-    for (int k = 0; k < kMomBlock / 32; ++k) t += red[threadIdx.x][k];
-    partial[blockIdx.x * 4 + threadIdx.x] = t;
-  }
+  cs.write_block(partial);
 }
 
 // Device address of g_noalloc_scratch per device, looked up once per device

@@ -272,6 +272,27 @@ def test_conservation_periodic_gpu():
     assert abs(s1[3] - s0[3]) < 1e-9 * cells
 
 
+@pytest.mark.parametrize("nroots", [4, 6])
+def test_conservation_sums_match_populations(nroots):
+    """The FP64 totals of lesbgk_moments (per-node sums in FP32, the nodes'
+    runs accumulated in FP64) agree with FP64 sums of the stored populations
+    sum f {1, c_x, c_y, c^2/2}, within FP32 rounding of the per-node terms."""
+    prob = I.Problem(name="cs", nroots=nroots, nx=70, ny=37, bc_y=I.DIFFUSE, kn=0.1, b=-0.5,
+                     wall_ux=(-0.05, 0.05), wall_T=(0.97, 1.03), g=(1e-3, 0.0))
+    fields = I.random_fields(prob, seed=21, amp_u=0.05, amp_T=0.05, amp_rho=0.05)
+    s = gpu_solver(prob, time_step(prob, fields), fields)
+    s.step(13)
+    _, sums = s.moments(sums=True)
+    df = s.populations().cpu().numpy().astype(np.float64)  # f - w, [a][j][i]
+    cx, cy, w = O.velocity_set(nroots)
+    phis = [np.ones_like(cx), cx, cy, 0.5 * (cx * cx + cy * cy)]
+    cells = prob.cells
+    for k, phi in enumerate(phis):
+        ref = float(np.sum(w * phi) * cells + np.einsum("a,aji->", phi, df))
+        scale = float(np.einsum("a,aji->", np.abs(phi), np.abs(df))) + cells * 1e-3
+        assert abs(sums[k] - ref) <= 1e-6 * scale, (k, sums[k], ref)
+
+
 # ---------------------------------------------------------------- other lattices
 @pytest.mark.parametrize("scheme", [I.UNSPLIT, I.SPLIT])
 def test_d2q36_rough_periodic(scheme):

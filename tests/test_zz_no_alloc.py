@@ -49,7 +49,10 @@ def test_noalloc_moments_match_workspace_moments(prob):
         errs = field_errors(out.cpu().numpy(), ref.astype(np.float64))
         bad = {k: v for k, v in errs.items() if not v[0] <= 1e-5}
         assert not bad, bad
-        assert np.allclose(sums, ref_sums, rtol=1e-12, atol=1e-9)
+        # both sum per-node FP32 terms in FP32 runs accumulated in FP64; the
+        # runs group nodes differently, so the totals agree to FP32 rounding
+        # of the per-node terms (well inside 1e-9 per node)
+        assert np.allclose(sums, ref_sums, rtol=0.0, atol=1e-9 * prob.cells)
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch():
