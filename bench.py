@@ -107,11 +107,21 @@ def committed_traffic(source_digest: str, velocity_set: str = "d2q16", storage: 
 
 
 def source_digest():
+    """sha256 (16 hex digits) of the step kernel's source: device.cuh, the
+    k_step section of lesbgk.cu, its launch set-up (pick_launch .. launch_step)
+    and its block size; other kernels in the file do not change it."""
     import hashlib
+    csrc = os.path.join(ROOT, "paper_1209_6548_gb300", "csrc")
     h = hashlib.sha256()
-    for name in ("lesbgk.cu", "device.cuh"):
-        with open(os.path.join(ROOT, "paper_1209_6548_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(csrc, "device.cuh"), "rb") as fh:
+        h.update(fh.read())
+    with open(os.path.join(csrc, "lesbgk.cu")) as fh:
+        text = fh.read()
+    a = text.index("// The fused time step")
+    h.update(text[a:text.index("// Initial populations", a)].encode())
+    a = text.index("int pick_launch(")
+    h.update(text[a:text.index("unsigned grid_for(", a)].encode())
+    h.update("".join(ln for ln in text.splitlines(True) if ln.startswith("constexpr int kBlock ")).encode())
     return h.hexdigest()[:16]
 
 
