@@ -30,7 +30,7 @@ _lib = None
 class OrcParams(C.Structure):
     _fields_ = [
         ("nroots", C.c_int32), ("order", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32),
-        ("bc_y", C.c_int32), ("scheme", C.c_int32),
+        ("bc_y", C.c_int32), ("scheme", C.c_int32), ("dim", C.c_int32),
         ("kn", C.c_double), ("b", C.c_double), ("visc_exp", C.c_double),
         ("dt", C.c_double), ("dx", C.c_double), ("dy", C.c_double),
         ("wall_T", C.c_double * 2), ("wall_ux", C.c_double * 2), ("g", C.c_double * 2),
@@ -86,7 +86,12 @@ def gauss_hermite_1d(n: int):
     return c, w
 
 
+def nvel(nroots: int, dim: int = 2) -> int:
+    return nroots ** dim
+
+
 def velocity_set(nroots: int):
+    """D = 2 set: (c_x, c_y, w), alpha = ix*nroots + iy."""
     q = nroots * nroots
     cx, cy, w = np.zeros(q), np.zeros(q), np.zeros(q)
     if lib().orc_velocity_set(int(nroots), _dp(cx), _dp(cy), _dp(w)):
@@ -94,19 +99,42 @@ def velocity_set(nroots: int):
     return cx, cy, w
 
 
+def velocity_set_d(nroots: int, dim: int):
+    """(c_x, c_y, c_z, w) of the D-dimensional set (c_z = 0 for D = 2);
+    alpha = (ix*nroots + iy)*nroots + iz for D = 3."""
+    q = nvel(nroots, dim)
+    cx, cy, cz, w = np.zeros(q), np.zeros(q), np.zeros(q), np.zeros(q)
+    if lib().orc_velocity_set_d(int(nroots), int(dim), _dp(cx), _dp(cy), _dp(cz), _dp(w)):
+        raise ValueError("bad nroots or dim")
+    return cx, cy, cz, w
+
+
 def chi(n: int, c) -> np.ndarray:
-    out = np.zeros(1 << n)
+    """chi^(n)(c) as a (D,)*n array, D = len(c)."""
     cc = np.ascontiguousarray(c, dtype=np.float64)
-    lib().orc_chi(int(n), _dp(cc), _dp(out))
-    return out.reshape((2,) * n) if n else out
+    d = cc.size
+    out = np.zeros(d ** n)
+    lib().orc_chi_d(int(n), int(d), _dp(cc), _dp(out))
+    return out.reshape((d,) * n) if n else out
 
 
 def a_es(n: int, rho: float, u, lam) -> np.ndarray:
-    out = np.zeros(1 << n)
+    """The printed a_ES^(n) as a (D,)*n array, D = len(u)."""
     uu = np.ascontiguousarray(u, dtype=np.float64)
-    ll = np.ascontiguousarray(lam, dtype=np.float64).reshape(4)
-    lib().orc_a_es(int(n), C.c_double(rho), _dp(uu), _dp(ll), _dp(out))
-    return out.reshape((2,) * n) if n else out
+    d = uu.size
+    out = np.zeros(d ** n)
+    ll = np.ascontiguousarray(lam, dtype=np.float64).reshape(d * d)
+    lib().orc_a_es_d(int(n), int(d), C.c_double(rho), _dp(uu), _dp(ll), _dp(out))
+    return out.reshape((d,) * n) if n else out
+
+
+def cell_moments(nroots: int, dim: int, f):
+    """One cell's moments: (the nine fields of moments(), P (D, D), u (D,))."""
+    ff = np.ascontiguousarray(f, dtype=np.float64)
+    out, P, u = np.zeros(9), np.zeros(dim * dim), np.zeros(dim)
+    if lib().orc_cell_moments(int(nroots), int(dim), _dp(ff), _dp(out), _dp(P), _dp(u)):
+        raise ValueError("bad nroots or dim")
+    return out, P.reshape(dim, dim), u
 
 
 UNSPLIT, SPLIT = 0, 1
@@ -114,9 +142,10 @@ UNSPLIT, SPLIT = 0, 1
 
 def make_params(*, nroots, order, nx, ny, bc_y, kn, b, visc_exp, dt, dx, dy,
                 wall_T=(1.0, 1.0), wall_ux=(0.0, 0.0), g=(0.0, 0.0), scheme=UNSPLIT, wall_specular=0.0,
-                wall_T_amp=0.0, wall_T_freq=0.0, time=0.0) -> OrcParams:
+                wall_T_amp=0.0, wall_T_freq=0.0, time=0.0, dim=2) -> OrcParams:
     p = OrcParams()
     p.nroots, p.order, p.nx, p.ny, p.bc_y, p.scheme = nroots, order, nx, ny, bc_y, scheme
+    p.dim = dim
     p.kn, p.b, p.visc_exp, p.dt, p.dx, p.dy = kn, b, visc_exp, dt, dx, dy
     p.wall_T[0], p.wall_T[1] = wall_T
     p.wall_ux[0], p.wall_ux[1] = wall_ux
@@ -125,8 +154,12 @@ def make_params(*, nroots, order, nx, ny, bc_y, kn, b, visc_exp, dt, dx, dy,
     return p
 
 
+def _q(p: OrcParams) -> int:
+    return nvel(p.nroots, p.dim or 2)
+
+
 def cell_terms(p: OrcParams, f):
-    q = p.nroots * p.nroots
+    q = _q(p)
     ff = np.ascontiguousarray(f, dtype=np.float64)
     fes, gf, tau = np.zeros(q), np.zeros(q), C.c_double()
     if lib().orc_cell_terms(C.byref(p), _dp(ff), _dp(fes), _dp(gf), C.byref(tau)):
@@ -134,9 +167,10 @@ def cell_terms(p: OrcParams, f):
     return fes, gf, tau.value
 
 
-def feq0(nroots: int, order: int, T: float, ux: float, uy: float) -> np.ndarray:
-    out = np.zeros(nroots * nroots)
-    if lib().orc_feq0(int(nroots), int(order), C.c_double(T), C.c_double(ux), C.c_double(uy), _dp(out)):
+def feq0(nroots: int, order: int, T: float, ux: float, uy: float, dim: int = 2) -> np.ndarray:
+    out = np.zeros(nvel(nroots, dim))
+    if lib().orc_feq0_d(int(nroots), int(dim), int(order), C.c_double(T), C.c_double(ux), C.c_double(uy),
+                        _dp(out)):
         raise ValueError("bad nroots")
     return out
 
@@ -149,7 +183,7 @@ def advect_1d(c: float, nu: float, f) -> np.ndarray:
 
 
 def init(p: OrcParams, fields=None) -> np.ndarray:
-    q = p.nroots * p.nroots
+    q = _q(p)
     f = np.zeros((q, p.ny, p.nx))
     if fields is None:
         rc = lib().orc_init(C.byref(p), None, _dp(f))

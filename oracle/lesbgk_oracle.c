@@ -11,10 +11,11 @@
  * for thermal non-equilibrium flows", arXiv 1209.6548):
  *
  *   - 1D Gauss-Hermite abscissae = roots of He_n, weights by Eq. (weight)
- *     w = n!/[n He_{n-1}(c)]^2, and the 2D tensor-product set (Sec. 2.2).
+ *     w = n!/[n He_{n-1}(c)]^2, and the D-dimensional tensor-product set
+ *     (Sec. 2.2), D = 2 or 3.
  *   - Tensor Hermite polynomials chi^(n)_{i1..in}, n <= 4, in full index form
- *     (the basis of Eq. approxf; Grad's definitions).
- *   - Moments rho, u, P_ij, T, sigma_ij, q_i of Eq. (mac) with D = 2.
+ *     (the basis of Eq. approxf; Grad's definitions), indices 0..D-1.
+ *   - Moments rho, u, P_ij, T, sigma_ij, q_i of Eq. (mac) in D dimensions.
  *   - tau = (Kn/Pr) mu/p, mu = T^varpi, p = rho T, Pr = 1/(1-b) (Sec. 2.1-2.2).
  *   - lambda_ij = T delta_ij + b sigma_ij / rho (Eq. cfeq).
  *   - a_ES^(0..4) as printed in Sec. 2.2 and f_ES,a = w_a sum_n a:chi/n!.
@@ -27,7 +28,10 @@
  *     Sec. 3.2 (outgoing half = rho_W S, ghosts = wall node).
  *
  * Readings where the paper is silent (each restated where it is used):
- *   D = 2 (the lattice dimension) in T, Eq. (feq0) and chi traces;
+ *   D is the dimension of the velocity set, used in T, Eq. (feq0) and the chi
+ *   traces (the paper's runs take D = 3 without naming their set; the 2D sets
+ *   give D = 2); the grid is two-dimensional whatever D is: populations are
+ *   advected along x and y only (nothing varies in z);
  *   for c < 0 the flux is the mirror image of the printed c > 0 formula;
  *   Psi(Theta)*(f_{i+1}-f_i) is 0 when f_{i+1} = f_i (Psi is bounded);
  *   walls sit on nodes j = 0 and j = ny-1; the wall node is first updated like
@@ -45,10 +49,11 @@
 #include <omp.h>
 #endif
 
-#define ORC_D 2          /* lattice dimension (reading: D = 2) */
+#define ORC_MAXD 3       /* largest velocity-set dimension */
 #define ORC_MAXR 64      /* largest 1D rule the root finder is asked for */
-#define ORC_MAXQ 64      /* largest 2D velocity set the step handles (8x8) */
+#define ORC_MAXQ 216     /* largest velocity set the step handles (6^3) */
 #define ORC_MAXN 4       /* highest Hermite order */
+#define ORC_MAXT 81      /* components of a rank-4 tensor in D = 3 */
 
 typedef struct orc_params {
   int32_t nroots;   /* roots of He_nroots per axis: Q = nroots^2 */
@@ -58,13 +63,15 @@ typedef struct orc_params {
   int32_t scheme;   /* 0 = the update of Sec. 3.1 as printed (both flux
                        differences from f^n); 1 = split: a y-sweep, then an
                        x-sweep of the y-swept values (reading for 2D flows) */
+  int32_t dim;      /* velocity-set dimension D: 2 (Q = nroots^2) or 3
+                       (Q = nroots^3); 0 means 2 */
   double kn;        /* Kn of Sec. 2.2 */
   double b;         /* ES parameter, Pr = 1/(1-b) */
   double visc_exp;  /* varpi in mu = T^varpi */
   double dt, dx, dy;
   double wall_T[2];   /* [0] bottom (j=0), [1] top (j=ny-1) */
   double wall_ux[2];
-  double g[2];        /* body force */
+  double g[2];        /* body force (g_x, g_y); g_z = 0 */
   double wall_specular; /* 1 - gamma of the Maxwell wall model (Sec. 3.2); 0 = fully diffuse */
   double wall_T_amp;    /* wall temperature T_w(t) = wall_T + amp sin(freq t) (Sec. 4.2) */
   double wall_T_freq;
@@ -130,24 +137,33 @@ int orc_gauss_hermite_1d(int n, double *c, double *w) {
   return 0;
 }
 
-/* 2D tensor-product ("production") set, Sec. 2.2: alpha = ix*nroots + iy,
- * c_alpha = (c_ix, c_iy), w_alpha = w_ix w_iy. */
-int orc_velocity_set(int nroots, double *cx, double *cy, double *w) {
+/* D-dimensional tensor-product ("production") set, Sec. 2.2:
+ *   D = 2: alpha = ix*nroots + iy,            c = (c_ix, c_iy)
+ *   D = 3: alpha = (ix*nroots + iy)*nroots + iz, c = (c_ix, c_iy, c_iz)
+ * w_alpha = product of the 1D weights.  cz may be NULL for D = 2. */
+int orc_velocity_set_d(int nroots, int D, double *cx, double *cy, double *cz, double *w) {
   double c1[ORC_MAXR], w1[ORC_MAXR];
-  if (orc_gauss_hermite_1d(nroots, c1, w1)) return -1;
+  if ((D != 2 && D != 3) || orc_gauss_hermite_1d(nroots, c1, w1)) return -1;
+  int nz = D == 3 ? nroots : 1;
   for (int ix = 0; ix < nroots; ++ix)
-    for (int iy = 0; iy < nroots; ++iy) {
-      int a = ix * nroots + iy;
-      cx[a] = c1[ix];
-      cy[a] = c1[iy];
-      w[a] = w1[ix] * w1[iy];
-    }
+    for (int iy = 0; iy < nroots; ++iy)
+      for (int iz = 0; iz < nz; ++iz) {
+        int a = (ix * nroots + iy) * nz + iz;
+        cx[a] = c1[ix];
+        cy[a] = c1[iy];
+        if (cz) cz[a] = D == 3 ? c1[iz] : 0.0;
+        w[a] = w1[ix] * w1[iy] * (D == 3 ? w1[iz] : 1.0);
+      }
   return 0;
 }
 
+int orc_velocity_set(int nroots, double *cx, double *cy, double *w) {
+  return orc_velocity_set_d(nroots, 2, cx, cy, NULL, w);
+}
+
 /* ------------------------------------------------------------------ */
-/* Tensor Hermite polynomials in D = 2, full index form.               */
-/* A rank-n tensor is stored flat with index sum_k i_k 2^(n-1-k).       */
+/* Tensor Hermite polynomials in D dimensions, full index form.        */
+/* A rank-n tensor is stored flat with index sum_k i_k D^(n-1-k).       */
 /*   chi0 = 1                                                           */
 /*   chi1_i = c_i                                                       */
 /*   chi2_ij = c_i c_j - d_ij                                           */
@@ -156,17 +172,24 @@ int orc_velocity_set(int nroots, double *cx, double *cy, double *w) {
 /* ------------------------------------------------------------------ */
 static double dl(int i, int j) { return i == j ? 1.0 : 0.0; }
 
-static int rank_size(int n) { return 1 << n; }
-
-static void idx_of(int n, int flat, int *ix) {
-  for (int k = 0; k < n; ++k) ix[k] = (flat >> (n - 1 - k)) & 1;
+static int rank_size(int D, int n) {
+  int r = 1;
+  for (int k = 0; k < n; ++k) r *= D;
+  return r;
 }
 
-void orc_chi(int n, const double *c, double *out) {
-  int sz = rank_size(n);
+static void idx_of(int D, int n, int flat, int *ix) {
+  for (int k = n - 1; k >= 0; --k) {
+    ix[k] = flat % D;
+    flat /= D;
+  }
+}
+
+void orc_chi_d(int n, int D, const double *c, double *out) {
+  int sz = rank_size(D, n);
   for (int f = 0; f < sz; ++f) {
     int I[4];
-    idx_of(n, f, I);
+    idx_of(D, n, f, I);
     double v = 0.0;
     if (n == 0) {
       v = 1.0;
@@ -188,17 +211,19 @@ void orc_chi(int n, const double *c, double *out) {
   }
 }
 
+void orc_chi(int n, const double *c, double *out) { orc_chi_d(n, 2, c, out); }
+
 /* ------------------------------------------------------------------ */
-/* a_ES^(n), Sec. 2.2, exactly as printed (D = 2 index loops).         */
-/* lam is the 2x2 ES tensor, row-major.                                */
+/* a_ES^(n), Sec. 2.2, exactly as printed (index loops over 0..D-1).   */
+/* lam is the D x D ES tensor, row-major.                              */
 /* ------------------------------------------------------------------ */
-void orc_a_es(int n, double rho, const double *u, const double *lam, double *out) {
-  int sz = rank_size(n);
-#define L(p, q) (lam[(p) * 2 + (q)])
+void orc_a_es_d(int n, int D, double rho, const double *u, const double *lam, double *out) {
+  int sz = rank_size(D, n);
+#define L(p, q) (lam[(p) * D + (q)])
 #define LM(p, q) (L(p, q) - dl(p, q))
   for (int f = 0; f < sz; ++f) {
     int I[4];
-    idx_of(n, f, I);
+    idx_of(D, n, f, I);
     double v = 0.0;
     if (n == 0) {
       v = rho;
@@ -224,6 +249,10 @@ void orc_a_es(int n, double rho, const double *u, const double *lam, double *out
 #undef LM
 }
 
+void orc_a_es(int n, double rho, const double *u, const double *lam, double *out) {
+  orc_a_es_d(n, 2, rho, u, lam, out);
+}
+
 static double factorial(int n) {
   double r = 1.0;
   for (int k = 2; k <= n; ++k) r *= (double)k;
@@ -231,61 +260,93 @@ static double factorial(int n) {
 }
 
 /* Full contraction a:chi of two rank-n tensors. */
-static double contract(int n, const double *a, const double *chi) {
+static double contract(int D, int n, const double *a, const double *chi) {
   double s = 0.0;
-  for (int f = 0; f < rank_size(n); ++f) s += a[f] * chi[f];
+  for (int f = 0; f < rank_size(D, n); ++f) s += a[f] * chi[f];
   return s;
 }
 
 /* Velocity-set tables shared by one call: c, w and chi^(n)(c_alpha). */
 typedef struct orc_lattice {
-  int Q, nroots;
-  double cx[ORC_MAXQ], cy[ORC_MAXQ], w[ORC_MAXQ];
-  double chi[ORC_MAXN + 1][ORC_MAXQ][16];
+  int Q, nroots, D;
+  double c[ORC_MAXQ][ORC_MAXD];  /* c[alpha][i], i < D; components i >= D are 0 */
+  double w[ORC_MAXQ];
+  double chi[ORC_MAXN + 1][ORC_MAXQ][ORC_MAXT];
 } orc_lattice;
 
-static int lattice_init(orc_lattice *L, int nroots) {
-  if (nroots < 1 || nroots * nroots > ORC_MAXQ) return -1;
+static int dim_of(const orc_params *p) { return p->dim == 0 ? 2 : p->dim; }
+
+/* Heap-allocated (the chi tables take 0.7 MB for D3Q216); free() it. */
+static orc_lattice *lattice_new(int nroots, int D) {
+  if (nroots < 1 || (D != 2 && D != 3)) return NULL;
+  int Q = D == 3 ? nroots * nroots * nroots : nroots * nroots;
+  if (Q > ORC_MAXQ) return NULL;
+  orc_lattice *L = (orc_lattice *)calloc(1, sizeof(orc_lattice));
+  if (!L) return NULL;
   L->nroots = nroots;
-  L->Q = nroots * nroots;
-  if (orc_velocity_set(nroots, L->cx, L->cy, L->w)) return -1;
-  for (int a = 0; a < L->Q; ++a) {
-    double c[2] = {L->cx[a], L->cy[a]};
-    for (int n = 0; n <= ORC_MAXN; ++n) orc_chi(n, c, L->chi[n][a]);
+  L->D = D;
+  L->Q = Q;
+  double cx[ORC_MAXQ], cy[ORC_MAXQ], cz[ORC_MAXQ];
+  if (orc_velocity_set_d(nroots, D, cx, cy, cz, L->w)) {
+    free(L);
+    return NULL;
   }
-  return 0;
+  for (int a = 0; a < Q; ++a) {
+    L->c[a][0] = cx[a];
+    L->c[a][1] = cy[a];
+    L->c[a][2] = cz[a];
+    for (int n = 0; n <= ORC_MAXN; ++n) orc_chi_d(n, D, L->c[a], L->chi[n][a]);
+  }
+  return L;
+}
+
+/* alpha with c_y -> -c_y (the specular image across a wall normal to y) */
+static int mirror_y(const orc_lattice *L, int a) {
+  int nr = L->nroots, nz = L->D == 3 ? nr : 1;
+  int iz = a % nz, iy = (a / nz) % nr, ix = a / (nz * nr);
+  return (ix * nr + (nr - 1 - iy)) * nz + iz;
 }
 
 /* ------------------------------------------------------------------ */
-/* Moments of Eq. (mac), D = 2.                                        */
+/* Moments of Eq. (mac) in D dimensions.                               */
 /* out: rho, ux, uy, T, sxx, sxy, syy, qx, qy                           */
 /* P_ij = sum f C_i C_j;  T = P_ii/(D rho);  sigma = P - delta P_ii/D;  */
-/* q_i = 1/2 sum f C_i C^2.                                             */
+/* q_i = 1/2 sum f C_i C^2 (C^2 over all D components).  For D = 3 the  */
+/* z components (u_z, sigma_iz, q_z) are left out of out; Pout gets     */
+/* the whole D x D tensor and uout (if set) the D velocity components.  */
 /* ------------------------------------------------------------------ */
-static void cell_moments(const orc_lattice *L, const double *f, double *out, double P[4]) {
-  double rho = 0.0, mx = 0.0, my = 0.0;
+static void cell_moments(const orc_lattice *L, const double *f, double *out, double *Pout, double *uout) {
+  const int D = L->D;
+  double rho = 0.0, m[ORC_MAXD] = {0.0, 0.0, 0.0};
   for (int a = 0; a < L->Q; ++a) {
     rho += f[a];
-    mx += f[a] * L->cx[a];
-    my += f[a] * L->cy[a];
+    for (int i = 0; i < D; ++i) m[i] += f[a] * L->c[a][i];
   }
-  double ux = mx / rho, uy = my / rho;
-  double pxx = 0, pxy = 0, pyy = 0, qx = 0, qy = 0;
+  double u[ORC_MAXD] = {0.0, 0.0, 0.0};
+  for (int i = 0; i < D; ++i) u[i] = m[i] / rho;
+  double P[ORC_MAXD * ORC_MAXD] = {0.0}, q[ORC_MAXD] = {0.0, 0.0, 0.0};
   for (int a = 0; a < L->Q; ++a) {
-    double Cx = L->cx[a] - ux, Cy = L->cy[a] - uy;
-    double C2 = Cx * Cx + Cy * Cy;
-    pxx += f[a] * Cx * Cx;
-    pxy += f[a] * Cx * Cy;
-    pyy += f[a] * Cy * Cy;
-    qx += 0.5 * f[a] * Cx * C2;
-    qy += 0.5 * f[a] * Cy * C2;
+    double C[ORC_MAXD], C2 = 0.0;
+    for (int i = 0; i < D; ++i) {
+      C[i] = L->c[a][i] - u[i];
+      C2 += C[i] * C[i];
+    }
+    for (int i = 0; i < D; ++i) {
+      for (int j = 0; j < D; ++j) P[i * D + j] += f[a] * C[i] * C[j];
+      q[i] += 0.5 * f[a] * C[i] * C2;
+    }
   }
-  double T = (pxx + pyy) / (ORC_D * rho);
-  double tr = (pxx + pyy) / ORC_D;
-  out[0] = rho; out[1] = ux; out[2] = uy; out[3] = T;
-  out[4] = pxx - tr; out[5] = pxy; out[6] = pyy - tr;
-  out[7] = qx; out[8] = qy;
-  if (P) { P[0] = pxx; P[1] = pxy; P[2] = pxy; P[3] = pyy; }
+  double trP = 0.0;
+  for (int i = 0; i < D; ++i) trP += P[i * D + i];
+  double T = trP / (D * rho);
+  double tr = trP / D;
+  out[0] = rho; out[1] = u[0]; out[2] = u[1]; out[3] = T;
+  out[4] = P[0] - tr; out[5] = P[1]; out[6] = P[D + 1] - tr;
+  out[7] = q[0]; out[8] = q[1];
+  if (Pout)
+    for (int k = 0; k < D * D; ++k) Pout[k] = P[k];
+  if (uout)
+    for (int i = 0; i < D; ++i) uout[i] = u[i];
 }
 
 /* ------------------------------------------------------------------ */
@@ -296,37 +357,43 @@ static void cell_moments(const orc_lattice *L, const double *f, double *out, dou
 /* ------------------------------------------------------------------ */
 static void cell_collision(const orc_lattice *L, const orc_params *p, const double *f,
                            double *fes, double *gf, double *tau_out) {
-  double m[9], P[4];
-  cell_moments(L, f, m, P);
-  double rho = m[0], u[2] = {m[1], m[2]}, T = m[3];
-  /* lambda = T delta + b sigma / rho, sigma trace-free (Eq. cfeq, Eq. mac) */
-  double sig[4] = {m[4], m[5], m[5], m[6]};
-  double lam[4];
-  for (int i = 0; i < 2; ++i)
-    for (int j = 0; j < 2; ++j) lam[i * 2 + j] = T * dl(i, j) + p->b * sig[i * 2 + j] / rho;
+  const int D = L->D;
+  double m[9], P[ORC_MAXD * ORC_MAXD], u[ORC_MAXD];
+  cell_moments(L, f, m, P, u);
+  double rho = m[0], T = m[3];
+  /* lambda = T delta + b sigma / rho, sigma = P - delta tr(P)/D (Eq. cfeq, Eq. mac) */
+  double trP = 0.0;
+  for (int i = 0; i < D; ++i) trP += P[i * D + i];
+  double lam[ORC_MAXD * ORC_MAXD];
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) {
+      double sig = P[i * D + j] - dl(i, j) * trP / D;
+      lam[i * D + j] = T * dl(i, j) + p->b * sig / rho;
+    }
   int N = p->order;
-  double aes[ORC_MAXN + 1][16];
-  for (int n = 0; n <= N; ++n) orc_a_es(n, rho, u, lam, aes[n]);
+  double aes[ORC_MAXN + 1][ORC_MAXT];
+  for (int n = 0; n <= N; ++n) orc_a_es_d(n, D, rho, u, lam, aes[n]);
   /* the distribution's own Hermite moments a^(k) = sum_b f_b chi^(k)(c_b) */
-  double af[ORC_MAXN + 1][16];
+  double af[ORC_MAXN + 1][ORC_MAXT];
   for (int n = 0; n < N; ++n) {
-    for (int k = 0; k < rank_size(n); ++k) {
+    for (int k = 0; k < rank_size(D, n); ++k) {
       double s = 0.0;
       for (int b = 0; b < L->Q; ++b) s += f[b] * L->chi[n][b][k];
       af[n][k] = s;
     }
   }
+  double g[ORC_MAXD] = {p->g[0], p->g[1], 0.0};
   for (int a = 0; a < L->Q; ++a) {
     double s = 0.0;
-    for (int n = 0; n <= N; ++n) s += contract(n, aes[n], L->chi[n][a]) / factorial(n);
+    for (int n = 0; n <= N; ++n) s += contract(D, n, aes[n], L->chi[n][a]) / factorial(n);
     fes[a] = L->w[a] * s;
     double gs = 0.0;
     for (int n = 1; n <= N; ++n) {
       /* g_{i1} a^(n-1)_{i2..in} chi^(n)_{i1 i2..in} */
       double t = 0.0;
-      int szm = rank_size(n - 1);
-      for (int i1 = 0; i1 < 2; ++i1)
-        for (int r = 0; r < szm; ++r) t += p->g[i1] * af[n - 1][r] * L->chi[n][a][(i1 << (n - 1)) | r];
+      int szm = rank_size(D, n - 1);
+      for (int i1 = 0; i1 < D; ++i1)
+        for (int r = 0; r < szm; ++r) t += g[i1] * af[n - 1][r] * L->chi[n][a][i1 * szm + r];
       gs += t / factorial(n - 1);
     }
     gf[a] = L->w[a] * gs;
@@ -339,21 +406,35 @@ static void cell_collision(const orc_lattice *L, const orc_params *p, const doub
 
 /* Exported for the tests: f_ES, g_a and tau of one cell. */
 int orc_cell_terms(const orc_params *p, const double *f, double *fes, double *gf, double *tau) {
-  orc_lattice L;
-  if (lattice_init(&L, p->nroots)) return -1;
-  cell_collision(&L, p, f, fes, gf, tau);
+  orc_lattice *L = lattice_new(p->nroots, dim_of(p));
+  if (!L) return -1;
+  cell_collision(L, p, f, fes, gf, tau);
+  free(L);
+  return 0;
+}
+
+/* Exported for the tests: the moments of one cell in D dimensions:
+ * out9 as in orc_moments, P (D x D), u (D). */
+int orc_cell_moments(int nroots, int D, const double *f, double *out9, double *P, double *u) {
+  orc_lattice *L = lattice_new(nroots, D);
+  if (!L) return -1;
+  cell_moments(L, f, out9, P, u);
+  free(L);
   return 0;
 }
 
 /* ------------------------------------------------------------------ */
-/* Truncated Maxwellian S(T,u), Eq. (feq0), carried to order N <= 4.   */
+/* Truncated Maxwellian S(T,u), Eq. (feq0), carried to order N <= 4,   */
+/* in D dimensions (c.u, u.u and c.c over all D components).           */
 /* Lines of Eq. (feq0): orders 0,1,2 | order 3 | order 4 (three lines). */
 /* ------------------------------------------------------------------ */
-static double feq0_S(int N, double T, const double *u, double cx, double cy, double w) {
-  const double D = ORC_D;
-  double cu = cx * u[0] + cy * u[1];
-  double uu = u[0] * u[0] + u[1] * u[1];
-  double cc = cx * cx + cy * cy;
+static double feq0_S(int N, int D, double T, const double *u, const double *c, double w) {
+  double cu = 0.0, uu = 0.0, cc = 0.0;
+  for (int i = 0; i < D; ++i) {
+    cu += c[i] * u[i];
+    uu += u[i] * u[i];
+    cc += c[i] * c[i];
+  }
   double th = T - 1.0;
   double s = 1.0;
   if (N >= 1) s += cu;
@@ -367,12 +448,17 @@ static double feq0_S(int N, double T, const double *u, double cx, double cy, dou
   return w * s;
 }
 
-int orc_feq0(int nroots, int N, double T, double ux, double uy, double *out) {
-  orc_lattice L;
-  if (lattice_init(&L, nroots)) return -1;
-  double u[2] = {ux, uy};
-  for (int a = 0; a < L.Q; ++a) out[a] = feq0_S(N, T, u, L.cx[a], L.cy[a], L.w[a]);
+int orc_feq0_d(int nroots, int D, int N, double T, double ux, double uy, double *out) {
+  orc_lattice *L = lattice_new(nroots, D);
+  if (!L) return -1;
+  double u[ORC_MAXD] = {ux, uy, 0.0};
+  for (int a = 0; a < L->Q; ++a) out[a] = feq0_S(N, D, T, u, L->c[a], L->w[a]);
+  free(L);
   return 0;
+}
+
+int orc_feq0(int nroots, int N, double T, double ux, double uy, double *out) {
+  return orc_feq0_d(nroots, 2, N, T, ux, uy, out);
 }
 
 /* ------------------------------------------------------------------ */
@@ -444,22 +530,21 @@ static int row_of(const orc_params *p, int j) {
 static void wall_node(const orc_lattice *L, const orc_params *p, double *f, int i, int j, int side,
                       double t) {
   double n_y = side == 0 ? 1.0 : -1.0;
-  double u[2] = {p->wall_ux[side], 0.0};
+  double u[ORC_MAXD] = {p->wall_ux[side], 0.0, 0.0};
   double Tw = p->wall_T[side] + p->wall_T_amp * sin(p->wall_T_freq * t);
   double S[ORC_MAXQ];
-  for (int a = 0; a < L->Q; ++a) S[a] = feq0_S(p->order, Tw, u, L->cx[a], L->cy[a], L->w[a]);
+  for (int a = 0; a < L->Q; ++a) S[a] = feq0_S(p->order, L->D, Tw, u, L->c[a], L->w[a]);
   double num = 0.0, den = 0.0;
   for (int a = 0; a < L->Q; ++a) {
-    double cn = L->cy[a] * n_y;
+    double cn = L->c[a][1] * n_y;
     if (cn < 0.0) num += fabs(cn) * f[fidx(p, a, j, i)];
     if (cn > 0.0) den += fabs(cn) * S[a];
   }
   double rw = num / den;
   double spec = p->wall_specular;
   for (int a = 0; a < L->Q; ++a) {
-    if (L->cy[a] * n_y > 0.0) {
-      int ix = a / L->nroots, iy = a % L->nroots;
-      int mirror = ix * L->nroots + (L->nroots - 1 - iy); /* c_y -> -c_y */
+    if (L->c[a][1] * n_y > 0.0) {
+      int mirror = mirror_y(L, a); /* c_y -> -c_y */
       f[fidx(p, a, j, i)] = (1.0 - spec) * rw * S[a] + spec * f[fidx(p, mirror, j, i)];
     }
   }
@@ -474,7 +559,9 @@ static void apply_walls(const orc_lattice *L, const orc_params *p, double *f, do
 }
 
 static int check_params(const orc_params *p) {
-  if (p->nroots < 2 || p->nroots * p->nroots > ORC_MAXQ) return -1;
+  int D = dim_of(p);
+  if (D != 2 && D != 3) return -1;
+  if (p->nroots < 2 || (D == 3 ? p->nroots * p->nroots * p->nroots : p->nroots * p->nroots) > ORC_MAXQ) return -1;
   if (p->order < 0 || p->order > ORC_MAXN) return -1;
   if (p->nx < 1 || p->ny < 1) return -1;
   if (p->bc_y == 1 && p->ny < 2) return -1;
@@ -486,19 +573,21 @@ static int check_params(const orc_params *p) {
 /* Initial state: f = rho S(T,u) from fields[4][ny][nx] = rho, ux, uy, T;
  * then the wall rule once so the state satisfies the boundary condition. */
 int orc_init(const orc_params *p, const double *fields, double *f) {
-  orc_lattice L;
-  if (check_params(p) || lattice_init(&L, p->nroots)) return -1;
+  if (check_params(p)) return -1;
+  orc_lattice *L = lattice_new(p->nroots, dim_of(p));
+  if (!L) return -1;
   size_t cells = (size_t)p->nx * p->ny;
   for (int j = 0; j < p->ny; ++j)
     for (int i = 0; i < p->nx; ++i) {
       size_t c = (size_t)j * p->nx + i;
       double rho = fields ? fields[c] : 1.0;
-      double u[2] = {fields ? fields[cells + c] : 0.0, fields ? fields[2 * cells + c] : 0.0};
+      double u[ORC_MAXD] = {fields ? fields[cells + c] : 0.0, fields ? fields[2 * cells + c] : 0.0, 0.0};
       double T = fields ? fields[3 * cells + c] : 1.0;
-      for (int a = 0; a < L.Q; ++a)
-        f[fidx(p, a, j, i)] = rho * feq0_S(p->order, T, u, L.cx[a], L.cy[a], L.w[a]);
+      for (int a = 0; a < L->Q; ++a)
+        f[fidx(p, a, j, i)] = rho * feq0_S(p->order, L->D, T, u, L->c[a], L->w[a]);
     }
-  apply_walls(&L, p, f, p->time);
+  apply_walls(L, p, f, p->time);
+  free(L);
   return 0;
 }
 
@@ -512,19 +601,24 @@ int orc_init(const orc_params *p, const double *fields, double *f) {
  * the x-sweep of f*; collision and force are evaluated from f^n as printed.
  * For fields that do not vary in x both schemes give the same update. */
 int orc_step(const orc_params *p, const double *fin, double *fout) {
-  orc_lattice L;
-  if (check_params(p) || lattice_init(&L, p->nroots)) return -1;
-  const int Q = L.Q;
+  if (check_params(p)) return -1;
+  orc_lattice *Lp = lattice_new(p->nroots, dim_of(p));
+  if (!Lp) return -1;
+  const orc_lattice *L = Lp;
+  const int Q = L->Q;
   const size_t n = (size_t)Q * p->nx * p->ny;
   double *fstar = NULL;
   if (p->scheme == 1) {
     fstar = (double *)malloc(n * sizeof(double));
-    if (!fstar) return -1;
+    if (!fstar) {
+      free(Lp);
+      return -1;
+    }
 #pragma omp parallel for schedule(static) num_threads(orc_threads)
     for (int j = 0; j < p->ny; ++j)
       for (int i = 0; i < p->nx; ++i)
         for (int a = 0; a < Q; ++a) {
-          double cy = L.cy[a], fy[5];
+          double cy = L->c[a][1], fy[5];
           for (int k = -2; k <= 2; ++k) fy[k + 2] = fin[fidx(p, a, row_of(p, j + k), i)];
           double nuy = fabs(cy) * p->dt / p->dy;
           double dFy = flux_difference(cy, nuy, fy[0], fy[1], fy[2], fy[3], fy[4]);
@@ -536,9 +630,9 @@ int orc_step(const orc_params *p, const double *fin, double *fout) {
     double f[ORC_MAXQ], fes[ORC_MAXQ], gf[ORC_MAXQ], tau;
     for (int i = 0; i < p->nx; ++i) {
       for (int a = 0; a < Q; ++a) f[a] = fin[fidx(p, a, j, i)];
-      cell_collision(&L, p, f, fes, gf, &tau);
+      cell_collision(L, p, f, fes, gf, &tau);
       for (int a = 0; a < Q; ++a) {
-        double cx = L.cx[a], cy = L.cy[a];
+        double cx = L->c[a][0], cy = L->c[a][1]; /* c_z is not advected: the grid is 2D */
         double nux = fabs(cx) * p->dt / p->dx, nuy = fabs(cy) * p->dt / p->dy;
         double fx[5], fy[5];
         double coll = p->dt / tau * (fes[a] - f[a]) + gf[a] * p->dt;
@@ -559,14 +653,16 @@ int orc_step(const orc_params *p, const double *fin, double *fout) {
     }
   }
   free(fstar);
-  apply_walls(&L, p, fout, p->time + p->dt); /* the wall state at the new time */
+  apply_walls(L, p, fout, p->time + p->dt); /* the wall state at the new time */
+  free(Lp);
   return 0;
 }
 
 /* nsteps steps from time p->time; f is updated in place (work is a scratch
  * array of the same size). */
 int orc_run(const orc_params *p, double *f, double *work, int64_t nsteps) {
-  size_t n = (size_t)p->nroots * p->nroots * p->nx * p->ny;
+  size_t nq = (size_t)p->nroots * p->nroots * (dim_of(p) == 3 ? p->nroots : 1);
+  size_t n = nq * p->nx * p->ny;
   orc_params q = *p;
   for (int64_t s = 0; s < nsteps; ++s) {
     q.time = p->time + (double)s * p->dt;
@@ -577,27 +673,31 @@ int orc_run(const orc_params *p, double *f, double *work, int64_t nsteps) {
 }
 
 /* Moments of every node: out[9][ny][nx]; sums = {mass, x-mom, y-mom, energy}
- * with energy = sum_cells 1/2 sum_a f_a c_a^2. */
+ * with energy = sum_cells 1/2 sum_a f_a c_a^2 (c^2 over all D components). */
 int orc_moments(const orc_params *p, const double *f, double *out, double *sums) {
-  orc_lattice L;
-  if (check_params(p) || lattice_init(&L, p->nroots)) return -1;
+  if (check_params(p)) return -1;
+  orc_lattice *L = lattice_new(p->nroots, dim_of(p));
+  if (!L) return -1;
   size_t cells = (size_t)p->nx * p->ny;
   double s[4] = {0, 0, 0, 0};
   for (int j = 0; j < p->ny; ++j)
     for (int i = 0; i < p->nx; ++i) {
       double fc[ORC_MAXQ], m[9];
-      for (int a = 0; a < L.Q; ++a) fc[a] = f[fidx(p, a, j, i)];
-      cell_moments(&L, fc, m, NULL);
+      for (int a = 0; a < L->Q; ++a) fc[a] = f[fidx(p, a, j, i)];
+      cell_moments(L, fc, m, NULL, NULL);
       size_t c = (size_t)j * p->nx + i;
       if (out)
         for (int k = 0; k < 9; ++k) out[k * cells + c] = m[k];
-      for (int a = 0; a < L.Q; ++a) {
+      for (int a = 0; a < L->Q; ++a) {
+        double c2 = 0.0;
+        for (int d = 0; d < L->D; ++d) c2 += L->c[a][d] * L->c[a][d];
         s[0] += fc[a];
-        s[1] += fc[a] * L.cx[a];
-        s[2] += fc[a] * L.cy[a];
-        s[3] += 0.5 * fc[a] * (L.cx[a] * L.cx[a] + L.cy[a] * L.cy[a]);
+        s[1] += fc[a] * L->c[a][0];
+        s[2] += fc[a] * L->c[a][1];
+        s[3] += 0.5 * fc[a] * c2;
       }
     }
+  free(L);
   if (sums)
     for (int k = 0; k < 4; ++k) sums[k] = s[k];
   return 0;

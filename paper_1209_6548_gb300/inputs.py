@@ -26,7 +26,10 @@ SPLIT = 1    # y-sweep then x-sweep (for flows varying in x and y)
 class Problem:
     """One solve: lattice, grid, gas and boundary parameters.
 
-    nroots: Gauss-Hermite roots per axis (4 -> D2Q16, 6 -> D2Q36).
+    nroots: Gauss-Hermite roots per axis (4 -> D2Q16, 6 -> D2Q36; with dim 3,
+            4 -> D3Q64).
+    dim:    dimension D of the velocity set (2, or 3 for the paper's D = 3
+            thermodynamics on the same two-dimensional grid).
     order:  Hermite truncation order N of f_ES (0 selects the default).
     bc_y:   PERIODIC or DIFFUSE (walls on rows j=0 and j=ny-1).
     kn, b, visc_exp: Knudsen number, ES parameter b, viscosity exponent.
@@ -42,6 +45,7 @@ class Problem:
     name: str
     nroots: int = 4
     order: int = 0
+    dim: int = 2
     nx: int = 4
     ny: int = 64
     bc_y: int = DIFFUSE

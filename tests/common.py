@@ -52,7 +52,8 @@ def oracle_params(p: Problem, dt: float, nx=None, ny=None, bc_y=None):
                          bc_y=p.bc_y if bc_y is None else bc_y, kn=p.kn, b=p.b,
                          visc_exp=p.visc_exp, dt=dt, dx=dx, dy=dy, wall_T=tuple(p.wall_T),
                          wall_ux=tuple(p.wall_ux), g=tuple(p.g), scheme=p.scheme,
-                         wall_specular=p.wall_specular, wall_T_amp=p.wall_T_amp, wall_T_freq=p.wall_T_freq)
+                         wall_specular=p.wall_specular, wall_T_amp=p.wall_T_amp, wall_T_freq=p.wall_T_freq,
+                         dim=p.dim)
 
 
 GROUPS = {"rho": ("rho",), "T": ("T",), "u": ("ux", "uy"), "sigma": ("sxx", "sxy", "syy"),
