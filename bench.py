@@ -48,8 +48,9 @@ def parse():
     ap.add_argument("--workload", choices=["tgv", "batch", "serve", "precision"], default="tgv",
                     help="tgv: 4096^2 Taylor-Green throughput (default); batch: 512-instance channel mix; "
                          "serve: Poisson arrivals run to steady state with continuous batching")
-    ap.add_argument("--velocity-set", choices=["d2q16", "d2q36"], default="d2q16",
-                    help="tgv workload lattice: D2Q16 (order 3) or D2Q36 (order 4, the paper's setting)")
+    ap.add_argument("--velocity-set", choices=["d2q16", "d2q36", "d3q64"], default="d2q16",
+                    help="tgv workload lattice: D2Q16 (order 3), D2Q36 (order 4, the paper's setting) or "
+                         "D3Q64 (order 3, D = 3: the paper's C_p = 5/2; stored by its z-even half)")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
                     help="population storage for the tgv workload (compute is FP32)")
     ap.add_argument("--requests", type=int, default=400)
@@ -65,13 +66,25 @@ def tgv_workload_name(n, args):
     return f"tgv_{n}x{n}_{args.velocity_set}_{args.storage}"
 
 
+LATTICES = {  # velocity set -> (nroots, dim, order, values stored per node)
+    "d2q16": (4, 2, 3, 16),
+    "d2q36": (6, 2, 4, 36),
+    "d3q64": (4, 3, 3, 32),
+}
+
+
+def tgv_problem(n, args, nsteps):
+    from dataclasses import replace
+    from paper_1209_6548_gb300 import inputs as I
+    nroots, dim, _, _ = LATTICES[args.velocity_set]
+    return replace(I.tgv(n, steps=nsteps, nroots=nroots), dim=dim)
+
+
 def tgv_config(n, args, nsteps):
     """The config object of the throughput workload (shared by both arms)."""
-    from paper_1209_6548_gb300 import inputs as I
-    nroots = 6 if args.velocity_set == "d2q36" else 4
-    prob = I.tgv(n, steps=nsteps, nroots=nroots)
+    prob = tgv_problem(n, args, nsteps)
     return {"workload": tgv_workload_name(n, args), "nx": n, "ny": n, "velocity_set": args.velocity_set.upper(),
-            "storage": args.storage, "order": 3 if nroots == 4 else 4, "kn": prob.kn, "b": prob.b,
+            "storage": args.storage, "order": LATTICES[args.velocity_set][2], "kn": prob.kn, "b": prob.b,
             "lattice_steps_per_step": nsteps, "scheme": "split"}
 
 
@@ -183,13 +196,14 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline(n: int, rows: int = 1024, steps: int = 48, nroots: int = 4):
+def cpu_baseline(n: int, rows: int = 1024, steps: int = 48, velocity_set: str = "d2q16"):
     """The FP64 oracle, as it stands, on a bounded sample of the workload: the
     first `rows` rows of the n x n Taylor-Green initial state, periodic, split
     scheme, for `steps` time steps, on all host cores the process may use."""
     import numpy as np
     import oracle as O
     from paper_1209_6548_gb300 import inputs as I
+    nroots, dim, order, _ = LATTICES[velocity_set]
     prob = I.tgv(n, nroots=nroots)
     fields = I.initial_fields(prob)[:, :rows, :].copy()
     cores = len(os.sched_getaffinity(0))
@@ -197,14 +211,14 @@ def cpu_baseline(n: int, rows: int = 1024, steps: int = 48, nroots: int = 4):
     dx = dy = 1.0 / n
     c, _ = O.gauss_hermite_1d(nroots)
     dt = 0.5 * dx / float(np.abs(c).max())
-    op = O.make_params(nroots=nroots, order=3 if nroots == 4 else 4, nx=n, ny=rows, bc_y=0, kn=prob.kn,
-                       b=prob.b, visc_exp=prob.visc_exp, dt=dt, dx=dx, dy=dy, scheme=prob.scheme)
+    op = O.make_params(nroots=nroots, order=order, nx=n, ny=rows, bc_y=0, kn=prob.kn, b=prob.b,
+                       visc_exp=prob.visc_exp, dt=dt, dx=dx, dy=dy, scheme=prob.scheme, dim=dim)
     f = O.init(op, fields)
     t0 = time.perf_counter()
     O.run(op, f, steps)
     sec = time.perf_counter() - t0
     return {"value": n * rows * steps / sec / 1e6, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
-            "sample": f"{n}x{rows} periodic rows of the Taylor-Green state (D2Q{nroots * nroots}), "
+            "sample": f"{n}x{rows} periodic rows of the Taylor-Green state ({velocity_set.upper()}), "
                       f"{steps} FP64 oracle steps ({sec:.1f} s)"}
 
 
@@ -215,7 +229,7 @@ def run_reference(args, world, rank):
     t_all = time.perf_counter()
     base = None
     for k in range(args.warmup + args.steps):
-        base = cpu_baseline(args.n, rows=256, steps=4, nroots=6 if args.velocity_set == "d2q36" else 4)
+        base = cpu_baseline(args.n, rows=256, steps=4, velocity_set=args.velocity_set)
         if k >= args.warmup:
             samples.append(base["value"])
     value = statistics.median(samples)
@@ -546,8 +560,8 @@ def main():
 
     B.build()
     n, nsteps = args.n, args.lattice_steps
-    nroots = 6 if args.velocity_set == "d2q36" else 4
-    prob = I.tgv(n, steps=nsteps, nroots=nroots)
+    nroots, dim, order, q = LATTICES[args.velocity_set]
+    prob = tgv_problem(n, args, nsteps)
     fields = I.initial_fields(prob)
     params = L.params_from_problem(prob, dt=0.0)
     params.storage = {"f32": L.F32, "f16": L.F16, "bf16": L.BF16}[args.storage]
@@ -618,14 +632,14 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     peak, peak_kind = measured_peak()
-    q = nroots * nroots
-    bytes_per_lup = 2 * q * (4 if args.storage == "f32" else 2)
+    bytes_per_lup = 2 * q * (4 if args.storage == "f32" else 2)  # q: values stored per node
     achieved = bytes_per_lup * cells / (kernel_ms / 1e3) / 1e9
     digest = source_digest()
     traffic = committed_traffic(digest, args.velocity_set, args.storage)
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        base = cpu_baseline(n, rows=1024 if nroots == 4 else 256, nroots=nroots)
+        base = cpu_baseline(n, rows={"d2q16": 1024, "d2q36": 256, "d3q64": 256}[args.velocity_set],
+                            velocity_set=args.velocity_set)
     if rank == 0:
         clocks = clk.summary()
         line = {
@@ -634,14 +648,15 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": tgv_workload_name(n, args), "nx": n, "ny": n,
                        "velocity_set": args.velocity_set.upper(), "storage": args.storage,
-                       "order": 3 if nroots == 4 else 4, "kn": prob.kn, "b": prob.b,
+                       "order": order, "kn": prob.kn, "b": prob.b,
                        "lattice_steps_per_step": nsteps, "scheme": "split",
                        "l2": "inputs larger than L2 (two population buffers of %.2f GB)"
                              % (q * n * n * (4 if args.storage == "f32" else 2) / 1e9),
                        "parallelism": f"replica x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                         "kernel": f"k_step<{nroots},{3 if nroots == 4 else 4},split,{args.storage}> rows={shape[1]}",
+                         "kernel": f"k_step<{nroots},{order},split,{args.storage},nz={q // (nroots * nroots)}> "
+                                   f"rows={shape[1]}",
                          "kernel_ms": kernel_ms,
                          "bytes_per_lup": bytes_per_lup, "source_sha256": digest},
             "cpu_baseline": base,

@@ -106,6 +106,14 @@ typedef struct lesbgk_params {
                            tables are rebuilt in FP64 on the host for each step's time.
                            Specular fractions need FP32 storage; heating takes any storage.
                            The batched solver takes steady, fully diffuse walls only. */
+  int32_t dim;          /* dimension D of the velocity set: 0 or 2 = the 2D sets above;
+                           3 = D3Q64 (nroots 4, order 3, FP32 storage) on the same 2D grid,
+                           the paper's D = 3 thermodynamics (C_p = 5/2; Sec. 2.1, Sec. 4).
+                           Nothing varies in z and walls and forces have no z part, so the
+                           state stays even in c_z: the library stores the c_z > 0 half
+                           (Q = 32 values per node, population a = iz*16 + ix*4 + iy,
+                           c_z = c[2 + iz]), each value standing for +c_z and -c_z.
+                           T = tr P/(3 rho) and sigma is trace-free in 3D in the moments. */
 } lesbgk_params;
 
 /* Read-only facts about a created solver. */
@@ -115,7 +123,7 @@ typedef struct lesbgk_info {
   double cfl;         /* effective Courant number c_max dt / min(dx,dy) */
   double tau_ref;     /* (Kn/Pr) T_max^(varpi-1) / rho_max at set-up */
   int64_t steps_done; /* time steps taken since create */
-  int32_t q, order;   /* number of velocities, Hermite order in use */
+  int32_t q, order;   /* values stored per node (velocities; 32 for D3Q64), Hermite order */
   int32_t cells_per_thread, rows_per_segment; /* launch shape of the step kernel */
 } lesbgk_info;
 

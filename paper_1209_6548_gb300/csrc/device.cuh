@@ -2,6 +2,14 @@
 // batched): limiter, row mapping, the grouped population layout, the
 // per-node Hermite collision (Sec. 2.2) and the diffuse wall (Sec. 3.2).
 //
+// Velocity sets: the D = 2 tensor-product sets (Q = NR^2, population
+// alpha = ix*NR + iy) and the D = 3 set with NR^3 velocities on the same
+// two-dimensional grid, stored by its z-even half: nothing varies in z and
+// the walls and forces have no z component, so a state even in c_z stays
+// even; populations (ix, iy, +c_z) and (ix, iy, -c_z) are equal and one value
+// (alpha = iz*NR^2 + ix*NR + iy, c_z = c[NR/2 + iz] > 0) stands for both.
+// NZ = the number of stored z-levels (1 for D = 2, NR/2 for D = 3).
+//
 // Functions take their tables through template "accessor" types:
 //   TT: lattice tables  c[i], he[i][m] = He_m(c_i), hw[i][m] = w_i He_m(c_i)/m!
 //   TP: per-solve scalars c_omega, visc_pow, vmode, b, beta, has_force, dtgx, dtgy
@@ -235,6 +243,144 @@ __device__ __forceinline__ void collide(const float (&F)[NR * NR], float (&S)[NR
   hermite_evaluate<NR, N>(d, S, Lt);
 }
 
+// ---------------------------------------------------------------------------
+// D = 3 set, z-even storage (NZ = NR/2 stored z-levels).  Hermite
+// coefficients carry a third index l (He_l(c_z)); odd l vanish by the
+// symmetry, so each node holds the in-plane arrays for l = 0, 2, 4.
+// ---------------------------------------------------------------------------
+
+// Moments b[l/2][m][k] = sum over all NR^3 velocities of df He_m(c_x) He_k(c_y)
+// He_l(c_z), l even, m + k <= KM - l: per stored level the in-plane sums,
+// weighted by 2 He_l(c_z) (the stored value stands for c_z and -c_z).
+template <int NR, int KM, int Q, class TT>
+__device__ __forceinline__ void hermite_moments3(const float (&F)[Q], float (&b)[3][KM + 1][KM + 1], const TT &A) {
+  constexpr int H = NR / 2, Q2 = NR * NR, NZ = Q / Q2;
+  static_assert(NZ == H, "the D = 3 set stores NR/2 z-levels");
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+#pragma unroll
+    for (int m = 0; m <= KM; ++m)
+#pragma unroll
+      for (int k = 0; k <= KM; ++k) b[l][m][k] = 0.0f;
+#pragma unroll
+  for (int iz = 0; iz < NZ; ++iz) {
+    float Fs[Q2];
+#pragma unroll
+    for (int a = 0; a < Q2; ++a) Fs[a] = F[iz * Q2 + a];
+    float a2[KM + 1][KM + 1];
+    hermite_moments<NR, KM>(Fs, a2, A);
+#pragma unroll
+    for (int l = 0; l <= 4 && l <= KM; l += 2) {
+      const float hz = 2.0f * A.he[H + iz][l];
+#pragma unroll
+      for (int m = 0; m + l <= KM; ++m)
+#pragma unroll
+        for (int k = 0; m + k + l <= KM; ++k) b[l / 2][m][k] = fmaf(hz, a2[m][k], b[l / 2][m][k]);
+    }
+  }
+}
+
+// S_a = w_a sum_{m+k+l<=N, l even} d[l/2][m][k] He_m He_k He_l(c_z)/(m! k! l!)
+// over the stored populations: per level the in-plane evaluation of
+// d'_mk = sum_l d[l/2][m][k] w_z He_l(c_z)/l!.
+template <int NR, int N, int Q, class TT>
+__device__ __forceinline__ void hermite_evaluate3(const float (&d)[3][N + 1][N + 1], float (&S)[Q], const TT &A) {
+  constexpr int H = NR / 2, Q2 = NR * NR, NZ = Q / Q2;
+#pragma unroll
+  for (int iz = 0; iz < NZ; ++iz) {
+    float dz[N + 1][N + 1];
+#pragma unroll
+    for (int m = 0; m <= N; ++m)
+#pragma unroll
+      for (int k = 0; m + k <= N; ++k) {
+        float v = d[0][m][k] * A.hw[H + iz][0];
+        if (m + k + 2 <= N) v = fmaf(d[1][m][k], A.hw[H + iz][2], v);
+        if (m + k + 4 <= N) v = fmaf(d[2][m][k], A.hw[H + iz][4], v);
+        dz[m][k] = v;
+      }
+    float Ss[Q2];
+    hermite_evaluate<NR, N>(dz, Ss, A);
+#pragma unroll
+    for (int a = 0; a < Q2; ++a) S[iz * Q2 + a] = Ss[a];
+  }
+}
+
+// In-plane Gaussian coefficients e (from gaussian_coeffs) times the z-factor
+// E[He_l(Z)], Z ~ N(0, 1 + Lzz): 1, Lzz, 3 Lzz^2 for l = 0, 2, 4 (lambda has no
+// xz or yz part and u_z = 0, so the generating function factorises).
+template <int N>
+__device__ __forceinline__ void z_factor(const float (&e)[N + 1][N + 1], float Lzz, float scale,
+                                         float (&d)[3][N + 1][N + 1]) {
+  const float z2 = Lzz * scale, z4 = 3.0f * Lzz * Lzz * scale;
+#pragma unroll
+  for (int m = 0; m <= N; ++m)
+#pragma unroll
+    for (int k = 0; m + k <= N; ++k) {
+      d[0][m][k] = scale * e[m][k];
+      d[1][m][k] = (m + k + 2 <= N) ? z2 * e[m][k] : 0.0f;
+      d[2][m][k] = (m + k + 4 <= N) ? z4 * e[m][k] : 0.0f;
+    }
+}
+
+// The collision + force source of collide() for the D = 3 set (T = tr P/(3 rho),
+// lambda 3x3 with lambda_zz = (1-b) T + b P_zz/rho).
+template <int NR, int N, int Q, class TT, class TP>
+__device__ __forceinline__ void collide3(const float (&F)[Q], float (&S)[Q], float &omw, const TT &Lt,
+                                         const TP &P) {
+  constexpr int KM = (N - 1 > 2) ? N - 1 : 2;
+  float b[3][KM + 1][KM + 1];
+  hermite_moments3<NR, KM>(F, b, Lt);
+  const float rho = 1.0f + b[0][0][0];
+  const float ir = fast_rcp(rho);
+  const float ux = b[0][1][0] * ir, uy = b[0][0][1] * ir;
+  const float Mxx = fmaf(-b[0][1][0], ux, b[0][2][0]);
+  const float Mxy = fmaf(-b[0][1][0], uy, b[0][1][1]);
+  const float Myy = fmaf(-b[0][0][1], uy, b[0][0][2]);
+  const float Mzz = b[1][0][0];  // sum df He_2(c_z); u_z = 0
+  const float trM = Mxx + Myy + Mzz;
+  const float T = fmaf((1.0f / 3.0f) * trM, ir, 1.0f);  // T = tr P / (D rho), D = 3
+  float Tp;
+  if (P.vmode == 1) Tp = fast_sqrt(T);
+  else if (P.vmode == 2) Tp = 1.0f;
+  else Tp = exp2f(P.visc_pow * __log2f(T));
+  const float om = P.c_omega * rho * Tp;
+  omw = 1.0f - om;
+  // rho (lambda - I) = (1-b) rho (T-1) I + b M, with beta = (1-b)/3
+  const float RLxx = fmaf(P.beta, trM, P.b * Mxx);
+  const float RLxy = P.b * Mxy;
+  const float RLyy = fmaf(P.beta, trM, P.b * Myy);
+  const float RLzz = fmaf(P.beta, trM, P.b * Mzz);
+  float e[N + 1][N + 1];
+  gaussian_coeffs<N>(rho, b[0][1][0], b[0][0][1], ux, uy, RLxx * ir, RLxy * ir, RLyy * ir, RLxx, RLxy, RLyy, e);
+  float d[3][N + 1][N + 1];
+  z_factor<N>(e, RLzz * ir, om, d);
+  d[0][0][0] = om * b[0][0][0];
+  if (P.has_force) {
+    // m g_x a_{m-1,k,l} + k g_y a_{m,k-1,l} (a_000 = rho; g_z = 0)
+#pragma unroll
+    for (int l = 0; l <= 2 && l <= N; l += 2)
+#pragma unroll
+      for (int m = 0; m + l <= N; ++m)
+#pragma unroll
+        for (int k = 0; m + k + l <= N; ++k) {
+          if (m + k == 0) continue;
+          float v = d[l / 2][m][k];
+          if (m >= 1) v = fmaf((float)m * P.dtgx, (m - 1 + k + l == 0) ? rho : b[l / 2][m - 1][k], v);
+          if (k >= 1) v = fmaf((float)k * P.dtgy, (m + k - 1 + l == 0) ? rho : b[l / 2][m][k - 1], v);
+          d[l / 2][m][k] = v;
+        }
+  }
+  hermite_evaluate3<NR, N>(d, S, Lt);
+}
+
+// One node's source for either kind of set: collide() for D = 2, collide3() for D = 3.
+template <int NR, int N, int Q, class TT, class TP>
+__device__ __forceinline__ void collide_any(const float (&F)[Q], float (&S)[Q], float &omw, const TT &Lt,
+                                            const TP &P) {
+  if constexpr (Q == NR * NR) collide<NR, N>(F, S, omw, Lt, P);
+  else collide3<NR, N>(F, S, omw, Lt, P);
+}
+
 // Wall rule of Sec. 3.2 on one node's updated deviations: rho_W from the
 // incoming half (zero net normal mass flux through the wall), outgoing half =
 // rho_W S_a(T_w, u_w), the fully diffuse wall; with SPEC (Maxwell model,
@@ -243,29 +389,27 @@ __device__ __forceinline__ void collide(const float (&F)[NR * NR], float (&S)[NR
 // side 0: bottom (outgoing c_y > 0), side 1: top (outgoing c_y < 0).  The
 // S tables are built on the host in FP64 for the wall temperature of the time
 // the launch writes (a varying one for the heated walls of Sec. 4.2).
-template <int NR, bool SPEC, class TT, class TW>
-__device__ __forceinline__ void wall_fix(float (&O)[NR * NR], int side, const TT &T, const TW &W) {
+template <int NR, bool SPEC, int Q, class TT, class TW>
+__device__ __forceinline__ void wall_fix(float (&O)[Q], int side, const TT &T, const TW &W) {
   constexpr int H = NR / 2;
   float s = 0.0f;
 #pragma unroll
-  for (int ix = 0; ix < NR; ++ix)
-#pragma unroll
-    for (int iy = 0; iy < NR; ++iy) {
-      const bool incoming = side == 0 ? (iy < H) : (iy >= H);
-      if (incoming) s = fmaf(fabsf(T.c[iy]), O[ix * NR + iy], s);
-    }
+  for (int a = 0; a < Q; ++a) {
+    const int iy = a % NR;
+    const bool incoming = side == 0 ? (iy < H) : (iy >= H);
+    if (incoming) s = fmaf(fabsf(T.c[iy]), O[a], s);
+  }
   const float rw1 = (s - W.wA[side]) * W.wB[side];  // rho_W - 1
 #pragma unroll
-  for (int ix = 0; ix < NR; ++ix)
-#pragma unroll
-    for (int iy = 0; iy < NR; ++iy) {
-      const bool outgoing = side == 0 ? (iy >= H) : (iy < H);
-      if (outgoing) {
-        const float diffuse = fmaf(rw1, W.wS[side][ix * NR + iy], W.wSdev[side][ix * NR + iy]);
-        if constexpr (SPEC) O[ix * NR + iy] = fmaf(W.wspec, O[ix * NR + (NR - 1 - iy)] - diffuse, diffuse);
-        else O[ix * NR + iy] = diffuse;
-      }
+  for (int a = 0; a < Q; ++a) {
+    const int iy = a % NR;
+    const bool outgoing = side == 0 ? (iy >= H) : (iy < H);
+    if (outgoing) {
+      const float diffuse = fmaf(rw1, W.wS[side][a], W.wSdev[side][a]);
+      if constexpr (SPEC) O[a] = fmaf(W.wspec, O[a + (NR - 1 - 2 * iy)] - diffuse, diffuse);
+      else O[a] = diffuse;
     }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -327,18 +471,24 @@ __host__ __device__ constexpr int pick_vector(int half, int bytes) {
   return (half % 8 == 0 && 8 * bytes <= 16) ? 8 : (half % 4 == 0 && 4 * bytes <= 16) ? 4 : (half % 2 == 0) ? 2 : 1;
 }
 
-template <int NR, class S = float>
+template <int NR, class S = float, int NZ = 1>
 struct Layout {
-  static constexpr int Q = NR * NR;
+  static constexpr int Q = NZ * NR * NR;
   static constexpr int H = NR / 2;
   static constexpr int HALF = Q / 2;
   static constexpr int V = pick_vector(HALF, (int)sizeof(S));  // populations per vector
   static constexpr int G = Q / V;                               // vectors (groups) per node
   static constexpr int VB = V * (int)sizeof(S);                 // bytes per vector
+  // slot s -> population alpha = iz*NR^2 + ix*NR + iy: the first half of the
+  // slots holds c_y < 0 (iy < H), the second c_y > 0, each in (iz, ix, iy) order
   __host__ __device__ static constexpr int alpha(int s) {
-    return (s % HALF) / H * NR + ((s / HALF) ? H : 0) + (s % HALF) % H;
+    return (s % HALF) / (NR * H) * NR * NR + (s % HALF) % (NR * H) / H * NR + ((s / HALF) ? H : 0) +
+           (s % HALF) % H;
   }
 };
+
+template <int NR, class S, int Q>
+using LayoutQ = Layout<NR, S, Q / (NR * NR)>;
 
 template <int V>
 struct VecT;
@@ -357,9 +507,9 @@ template <>
 struct Raw<4> { using T = unsigned; };
 
 // Load group g of one node (p points at the node's row, group 0) into F[alpha].
-template <int NR>
-__device__ __forceinline__ void ld_group(const float *p, long long gstride, int g, float (&F)[NR * NR]) {
-  using L = Layout<NR>;
+template <int NR, int Q>
+__device__ __forceinline__ void ld_group(const float *p, long long gstride, int g, float (&F)[Q]) {
+  using L = LayoutQ<NR, float, Q>;
   using T = typename VecT<L::V>::T;
   const T v = __ldg(reinterpret_cast<const T *>(p + g * gstride));
   const float *e = reinterpret_cast<const float *>(&v);
@@ -367,9 +517,9 @@ __device__ __forceinline__ void ld_group(const float *p, long long gstride, int 
   for (int k = 0; k < L::V; ++k) F[L::alpha(g * L::V + k)] = e[k];
 }
 
-template <int NR>
-__device__ __forceinline__ void st_group(float *p, long long gstride, int g, const float (&F)[NR * NR]) {
-  using L = Layout<NR>;
+template <int NR, int Q>
+__device__ __forceinline__ void st_group(float *p, long long gstride, int g, const float (&F)[Q]) {
+  using L = LayoutQ<NR, float, Q>;
   using T = typename VecT<L::V>::T;
   T v;
   float *e = reinterpret_cast<float *>(&v);
@@ -380,10 +530,10 @@ __device__ __forceinline__ void st_group(float *p, long long gstride, int g, con
 
 // The same for any storage type S: one raw vector per group, converted to
 // FP32 deviations (TT provides wq[a] = w_a and iwq[a] = 1/w_a).
-template <int NR, class S, class TT>
-__device__ __forceinline__ void unpack_group(const typename Raw<Layout<NR, S>::VB>::T &raw, int g,
-                                             float (&F)[NR * NR], const TT &Tt) {
-  using L = Layout<NR, S>;
+template <int NR, class S, int Q, class TT>
+__device__ __forceinline__ void unpack_group(const typename Raw<LayoutQ<NR, S, Q>::VB>::T &raw, int g,
+                                             float (&F)[Q], const TT &Tt) {
+  using L = LayoutQ<NR, S, Q>;
   const S *e = reinterpret_cast<const S *>(&raw);
 #pragma unroll
   for (int k = 0; k < L::V; ++k) {
@@ -392,17 +542,17 @@ __device__ __forceinline__ void unpack_group(const typename Raw<Layout<NR, S>::V
   }
 }
 
-template <int NR, class S, class TT>
-__device__ __forceinline__ void ld_group_s(const S *p, long long gstride, int g, float (&F)[NR * NR], const TT &Tt) {
-  using R = typename Raw<Layout<NR, S>::VB>::T;
+template <int NR, class S, int Q, class TT>
+__device__ __forceinline__ void ld_group_s(const S *p, long long gstride, int g, float (&F)[Q], const TT &Tt) {
+  using R = typename Raw<LayoutQ<NR, S, Q>::VB>::T;
   const R raw = __ldg(reinterpret_cast<const R *>(p + g * gstride));
   unpack_group<NR, S>(raw, g, F, Tt);
 }
 
-template <int NR, class S, class TT>
-__device__ __forceinline__ void st_group_s(S *p, long long gstride, int g, const float (&F)[NR * NR],
+template <int NR, class S, int Q, class TT>
+__device__ __forceinline__ void st_group_s(S *p, long long gstride, int g, const float (&F)[Q],
                                            const TT &Tt) {
-  using L = Layout<NR, S>;
+  using L = LayoutQ<NR, S, Q>;
   using R = typename Raw<L::VB>::T;
   R raw;
   S *e = reinterpret_cast<S *>(&raw);
@@ -418,13 +568,13 @@ __device__ __forceinline__ void st_group_s(S *p, long long gstride, int g, const
 // random bits of value k of group g are byte (k % 4) of
 // mix32(key ^ (g * 0x9e3779b9 + k / 4 * 0x85ebca6b)), so results depend only
 // on the key and the population, never on the launch shape.
-template <int NR, class S, class TT>
-__device__ __forceinline__ void st_group_sr(S *p, long long gstride, int g, const float (&F)[NR * NR],
+template <int NR, class S, int Q, class TT>
+__device__ __forceinline__ void st_group_sr(S *p, long long gstride, int g, const float (&F)[Q],
                                             const TT &Tt, unsigned key) {
   if constexpr (!Store<S>::kScaled) {
     st_group_s<NR, S>(p, gstride, g, F, Tt);
   } else {
-    using L = Layout<NR, S>;
+    using L = LayoutQ<NR, S, Q>;
     using R = typename Raw<L::VB>::T;
     R raw;
     S *e = reinterpret_cast<S *>(&raw);

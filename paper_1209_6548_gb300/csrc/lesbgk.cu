@@ -44,10 +44,10 @@ constexpr int kMomBlock = 256;
 // ---------------------------------------------------------------------------
 // The fused time step (Sec. 3.1 + Sec. 3.2).
 // ---------------------------------------------------------------------------
-template <int NR, int N, bool SPLIT, int RING, class S, bool SPEC>
+template <int NR, int N, bool SPLIT, int RING, class S, bool SPEC, int NZ = 1>
 __global__ void __launch_bounds__(kBlock) k_step(const S *__restrict__ fin, S *__restrict__ fout,
                                                  const KArgs A) {
-  using Lay = Layout<NR, S>;
+  using Lay = Layout<NR, S, NZ>;
   constexpr int Q = Lay::Q, H = Lay::H, V = Lay::V, G = Lay::G;
   constexpr int HL = 2;           // halo lanes per side
   constexpr int U = 32 - 2 * HL;  // nodes a strip updates
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kBlock) k_step(const S *__restrict__ fin, S *_
 
     float acc[Q];
     float omw;
-    collide<NR, N>(fc, acc, omw, A, A);
+    collide_any<NR, N>(fc, acc, omw, A, A);
 
     // y-advection from the carried stencil of f^n; xs = the values the
     // x-fluxes are taken from: f^n_j (update as printed) or the y-swept
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kBlock) k_step(const S *__restrict__ fin, S *_
     // x-advection: neighbours from adjacent lanes
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-      const int ix = a / NR;
+      const int ix = (a / NR) % NR;
       const float ax = A.ax[ix], kx = A.kx[ix];
       const float left = __shfl_up_sync(kFull, xs[a], 1);
       const float dl = xs[a] - left;                       // f_i - f_{i-1}
@@ -208,10 +208,10 @@ __global__ void __launch_bounds__(kBlock) k_step(const S *__restrict__ fin, S *_
 // expansion of the isotropic Maxwellian), then the wall rule once.
 // fields: double[4][ny][nx] = rho, u_x, u_y, T (or nullptr: rest).
 // ---------------------------------------------------------------------------
-template <int NR, int N, class S>
+template <int NR, int N, class S, int NZ = 1>
 __global__ void __launch_bounds__(kBlock) k_init(const double *__restrict__ fields, S *__restrict__ f,
                                                  const KArgs A) {
-  using Lay = Layout<NR, S>;
+  using Lay = Layout<NR, S, NZ>;
   constexpr int Q = Lay::Q;
   const long long cells = A.plane;
   const long long gstride = (long long)Lay::V * cells;
@@ -227,9 +227,16 @@ __global__ void __launch_bounds__(kBlock) k_init(const double *__restrict__ fiel
     const float rdT = rho * dT;
     float e[N + 1][N + 1];
     gaussian_coeffs<N>(rho, rho * ux, rho * uy, ux, uy, dT, 0.f, dT, rdT, 0.f, rdT, e);
-    e[0][0] = drho;  // deviation from w_a
     float Sv[Q];
-    hermite_evaluate<NR, N>(e, Sv, A);
+    if constexpr (NZ == 1) {
+      e[0][0] = drho;  // deviation from w_a
+      hermite_evaluate<NR, N>(e, Sv, A);
+    } else {  // D = 3: isotropic, so lambda_zz - 1 = T - 1 as in-plane
+      float d[3][N + 1][N + 1];
+      z_factor<N>(e, dT, 1.0f, d);
+      d[0][0][0] = drho;
+      hermite_evaluate3<NR, N>(d, Sv, A);
+    }
     const int j = (int)(c / A.nx);
     if (A.walls && (j == 0 || j == A.ny - 1)) {
       if (A.wspec != 0.0f) wall_fix<NR, true>(Sv, j == 0 ? 0 : 1, A, A);
@@ -241,10 +248,10 @@ __global__ void __launch_bounds__(kBlock) k_init(const double *__restrict__ fiel
 }
 
 // Populations between the grouped layout and the public [a][j][i] layout.
-template <int NR, class S>
+template <int NR, class S, int NZ = 1>
 __global__ void __launch_bounds__(kBlock) k_ungroup(const S *__restrict__ f, float *__restrict__ out,
                                                     long long cells, const KArgs A) {
-  using Lay = Layout<NR, S>;
+  using Lay = Layout<NR, S, NZ>;
   const long long gstride = (long long)Lay::V * cells;
   for (long long c = blockIdx.x * (long long)kBlock + threadIdx.x; c < cells; c += (long long)gridDim.x * kBlock) {
     float F[Lay::Q];
@@ -255,10 +262,10 @@ __global__ void __launch_bounds__(kBlock) k_ungroup(const S *__restrict__ f, flo
   }
 }
 
-template <int NR, class S>
+template <int NR, class S, int NZ = 1>
 __global__ void __launch_bounds__(kBlock) k_group(const float *__restrict__ in, S *__restrict__ f,
                                                   long long cells, const KArgs A) {
-  using Lay = Layout<NR, S>;
+  using Lay = Layout<NR, S, NZ>;
   const long long gstride = (long long)Lay::V * cells;
   for (long long c = blockIdx.x * (long long)kBlock + threadIdx.x; c < cells; c += (long long)gridDim.x * kBlock) {
     float F[Lay::Q];
@@ -273,25 +280,42 @@ __global__ void __launch_bounds__(kBlock) k_group(const float *__restrict__ in, 
 // Moments of Eq. (mac) of one node from its deviations F = f - w, written to
 // out[k * cells + c] (k = rho, u_x, u_y, T, sigma_xx, sigma_xy, sigma_yy, q_x,
 // q_y) when out is set; returns in d the node's deviations of the conserved
-// sums sum_a df_a {1, c_x, c_y, c^2}: with the Hermite moments m_pq =
-// sum df He_p(c_x) He_q(c_y) these are m00, m10, m01 and m20 + m02 + 2 m00.
+// sums sum_a df_a {1, c_x, c_y, c^2}: with the Hermite moments m_pql =
+// sum df He_p(c_x) He_q(c_y) He_l(c_z) these are m000, m100, m010 and
+// m200 + m020 (+ m002) + D m000.  D = 2 for the 2D sets; D = 3 (Q = NR^3/2
+// stored, z-even) adds the c_z terms: T = tr P/(3 rho), sigma trace-free in
+// 3D (sigma_zz = -sigma_xx - sigma_yy is not written), q with c_z^2 in C^2.
 // ---------------------------------------------------------------------------
-template <int NR>
-__device__ __forceinline__ void node_moments(const float (&F)[NR * NR], float *__restrict__ out, long long cells,
+template <int NR, int Q>
+__device__ __forceinline__ void node_moments(const float (&F)[Q], float *__restrict__ out, long long cells,
                                              long long c, const KArgs &A, float (&d)[4]) {
+  constexpr bool D3 = Q != NR * NR;
   float m[4][4];
-  hermite_moments<NR, 3>(F, m, A);
+  float mzz = 0.0f, mzx = 0.0f, mzy = 0.0f;  // m002, m102, m012 (D = 3)
+  if constexpr (!D3) {
+    hermite_moments<NR, 3>(F, m, A);
+  } else {
+    float b[3][4][4];
+    hermite_moments3<NR, 3>(F, b, A);
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; p + q < 4; ++q) m[p][q] = b[0][p][q];
+    mzz = b[1][0][0];
+    mzx = b[1][1][0];
+    mzy = b[1][0][1];
+  }
   const float rho = 1.0f + m[0][0];
   const float ir = __frcp_rn(rho);
   const float ux = m[1][0] * ir, uy = m[0][1] * ir;
   const float Mxx = fmaf(-m[1][0], ux, m[2][0]);
   const float Mxy = fmaf(-m[1][0], uy, m[1][1]);
   const float Myy = fmaf(-m[0][1], uy, m[0][2]);
-  const float trM = Mxx + Myy;
-  const float T = fmaf(0.5f * trM, ir, 1.0f);
+  const float trM = Mxx + Myy + mzz;  // M_zz = m002 (u_z = 0)
+  const float T = fmaf((D3 ? 1.0f / 3.0f : 0.5f) * trM, ir, 1.0f);
   const float u2 = ux * ux + uy * uy;
   // sum f C_i C^2 = sum df c_i (c^2 - D - 2) - 2 M_ij u_j - u_i tr M - rho u_i u^2
-  const float hx = m[3][0] + m[1][2], hy = m[0][3] + m[2][1];
+  const float hx = m[3][0] + m[1][2] + mzx, hy = m[0][3] + m[2][1] + mzy;
   const float qx = 0.5f * (hx - 2.0f * (Mxx * ux + Mxy * uy) - ux * trM - rho * ux * u2);
   const float qy = 0.5f * (hy - 2.0f * (Mxy * ux + Myy * uy) - uy * trM - rho * uy * u2);
   if (out) {
@@ -299,16 +323,21 @@ __device__ __forceinline__ void node_moments(const float (&F)[NR * NR], float *_
     out[cells + c] = ux;
     out[2 * cells + c] = uy;
     out[3 * cells + c] = T;
-    out[4 * cells + c] = 0.5f * (Mxx - Myy);
+    if constexpr (!D3) {
+      out[4 * cells + c] = 0.5f * (Mxx - Myy);
+      out[6 * cells + c] = 0.5f * (Myy - Mxx);
+    } else {
+      out[4 * cells + c] = fmaf(-1.0f / 3.0f, trM, Mxx);
+      out[6 * cells + c] = fmaf(-1.0f / 3.0f, trM, Myy);
+    }
     out[5 * cells + c] = Mxy;
-    out[6 * cells + c] = 0.5f * (Myy - Mxx);
     out[7 * cells + c] = qx;
     out[8 * cells + c] = qy;
   }
   d[0] = m[0][0];
   d[1] = m[1][0];
   d[2] = m[0][1];
-  d[3] = fmaf(2.0f, m[0][0], m[2][0] + m[0][2]);
+  d[3] = fmaf(D3 ? 3.0f : 2.0f, m[0][0], m[2][0] + m[0][2] + mzz);
 }
 
 // Conservation totals: per-node sums in FP32 (above), summed in FP32 over
@@ -337,10 +366,10 @@ struct ConsSums {
     n = 0;
   }
   // Block totals of mass, x/y momentum and energy (sum f {1, c_x, c_y, c^2/2},
-  // f = w + df, sum_a w_a = 1, sum_a w_a c_a^2 = D = 2) into partial[4 * block].
-  __device__ __forceinline__ void write_block(double *__restrict__ partial) {
+  // f = w + df, sum_a w_a = 1, sum_a w_a c_a^2 = D) into partial[4 * block].
+  __device__ __forceinline__ void write_block(double *__restrict__ partial, int D) {
     flush();
-    double v[4] = {(double)nodes + tot[0], tot[1], tot[2], (double)nodes + 0.5 * tot[3]};
+    double v[4] = {(double)nodes + tot[0], tot[1], tot[2], 0.5 * ((double)D * (double)nodes + tot[3])};
     __shared__ double red[4][kMomBlock / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -361,10 +390,10 @@ struct ConsSums {
 
 // Moments per node of the grouped layout, plus the block partial sums.
 // out: float[9][ny][nx] or nullptr.
-template <int NR, class S>
+template <int NR, class S, int NZ = 1>
 __global__ void __launch_bounds__(kMomBlock) k_moments(const S *__restrict__ f, float *__restrict__ out,
                                                        double *__restrict__ partial, const KArgs A) {
-  using Lay = Layout<NR, S>;
+  using Lay = Layout<NR, S, NZ>;
   constexpr int Q = Lay::Q;
   const long long cells = A.plane;
   const long long gstride = (long long)Lay::V * cells;
@@ -378,7 +407,7 @@ __global__ void __launch_bounds__(kMomBlock) k_moments(const S *__restrict__ f, 
     node_moments<NR>(F, out, cells, c, A, d);
     cs.add(d);
   }
-  cs.write_block(partial);
+  cs.write_block(partial, NZ == 1 ? 2 : 3);
 }
 
 __global__ void k_reduce_partials(const double *__restrict__ partial, int n, double *__restrict__ sums) {
@@ -421,7 +450,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 size_t buffer_bytes(const lesbgk_params *p) {
   const size_t cells = (size_t)p->nx * p->ny;
-  const size_t q = (size_t)p->nroots * p->nroots;
+  const size_t q = (size_t)p->nroots * p->nroots * (p->dim == 3 ? p->nroots / 2 : 1);  // values per node
   size_t per = q * (p->storage == LESBGK_F32 ? sizeof(float) : 2);
   if (per < 9 * sizeof(float)) per = 9 * sizeof(float);
   if (per < 4 * sizeof(double)) per = 4 * sizeof(double);
@@ -467,53 +496,59 @@ int build_tables(lesbgk *h, const double *h_init) {
 
 constexpr int kRing = 4;
 
-template <int NR, class S>
+template <int NR, class S, int NZ>
 constexpr size_t step_smem_bytes() {
-  return (size_t)(kBlock / 32) * kRing * Layout<NR, S>::G * 32 * Layout<NR, S>::VB;
+  return (size_t)(kBlock / 32) * kRing * Layout<NR, S, NZ>::G * 32 * Layout<NR, S, NZ>::VB;
 }
 
-// Call fn(NR, N, storage tag) with compile-time constants for the built
-// combinations: every (nroots, order) in FP32, the default orders also in
-// FP16 and BF16.
+// Call fn(NR, N, storage tag, NZ) with compile-time constants for the built
+// combinations: every (nroots, order) of the 2D sets in FP32, the default
+// orders also in FP16 and BF16; the D = 3 set as D3Q64, N = 3, FP32 (NZ = 2
+// stored z-levels; NZ = 1 for the 2D sets).
 template <class Fn>
-void dispatch(int nr, int order, int storage, Fn &&fn) {
+void dispatch(int nr, int order, int storage, int dim, Fn &&fn) {
   using R4 = std::integral_constant<int, 4>;
   using R6 = std::integral_constant<int, 6>;
   using N3 = std::integral_constant<int, 3>;
   using N4 = std::integral_constant<int, 4>;
-  if (nr == 4 && order == 3) {
-    if (storage == LESBGK_F16) fn(R4{}, N3{}, __half{});
-    else if (storage == LESBGK_BF16) fn(R4{}, N3{}, __nv_bfloat16{});
-    else fn(R4{}, N3{}, float{});
+  using Z1 = std::integral_constant<int, 1>;
+  using Z2 = std::integral_constant<int, 2>;
+  if (dim == 3) {
+    fn(R4{}, N3{}, float{}, Z2{});
+  } else if (nr == 4 && order == 3) {
+    if (storage == LESBGK_F16) fn(R4{}, N3{}, __half{}, Z1{});
+    else if (storage == LESBGK_BF16) fn(R4{}, N3{}, __nv_bfloat16{}, Z1{});
+    else fn(R4{}, N3{}, float{}, Z1{});
   } else if (nr == 6 && order == 4) {
-    if (storage == LESBGK_F16) fn(R6{}, N4{}, __half{});
-    else if (storage == LESBGK_BF16) fn(R6{}, N4{}, __nv_bfloat16{});
-    else fn(R6{}, N4{}, float{});
+    if (storage == LESBGK_F16) fn(R6{}, N4{}, __half{}, Z1{});
+    else if (storage == LESBGK_BF16) fn(R6{}, N4{}, __nv_bfloat16{}, Z1{});
+    else fn(R6{}, N4{}, float{}, Z1{});
   } else if (nr == 4) {
-    fn(R4{}, N4{}, float{});
+    fn(R4{}, N4{}, float{}, Z1{});
   } else {
-    fn(R6{}, N3{}, float{});
+    fn(R6{}, N3{}, float{}, Z1{});
   }
 }
 
 // Opt in to more than 48 KiB of dynamic shared memory where a ring needs it.
 cudaError_t allow_smem(const lesbgk *h) {
   cudaError_t e = cudaSuccess;
-  dispatch(h->nr, h->order, h->p.storage, [&](auto r, auto n, auto st) {
-    constexpr int NR = decltype(r)::value, N = decltype(n)::value;
+  dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto n, auto st, auto z) {
+    constexpr int NR = decltype(r)::value, N = decltype(n)::value, NZ = decltype(z)::value;
     using S = decltype(st);
-    constexpr int smem = (int)step_smem_bytes<NR, S>();
-    e = cudaFuncSetAttribute(k_step<NR, N, true, kRing, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    constexpr int smem = (int)step_smem_bytes<NR, S, NZ>();
+    e = cudaFuncSetAttribute(k_step<NR, N, true, kRing, S, false, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_step<NR, N, false, kRing, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               smem);
+      e = cudaFuncSetAttribute(k_step<NR, N, false, kRing, S, false, NZ>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if constexpr (std::is_same<S, float>::value) {
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_step<NR, N, true, kRing, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smem);
+        e = cudaFuncSetAttribute(k_step<NR, N, true, kRing, S, true, NZ>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_step<NR, N, false, kRing, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smem);
+        e = cudaFuncSetAttribute(k_step<NR, N, false, kRing, S, true, NZ>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     }
   });
   return e;
@@ -522,22 +557,22 @@ cudaError_t allow_smem(const lesbgk *h) {
 int launch_step(lesbgk *h, const void *fin, void *fout, cudaStream_t s) {
   const long long warps = (long long)h->args.nstrips * h->args.nseg;
   const unsigned grid = (unsigned)((warps * 32 + kBlock - 1) / kBlock);
-  dispatch(h->nr, h->order, h->p.storage, [&](auto r, auto n, auto st) {
-    constexpr int NR = decltype(r)::value, N = decltype(n)::value;
+  dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto n, auto st, auto z) {
+    constexpr int NR = decltype(r)::value, N = decltype(n)::value, NZ = decltype(z)::value;
     using S = decltype(st);
-    constexpr size_t smem = step_smem_bytes<NR, S>();
+    constexpr size_t smem = step_smem_bytes<NR, S, NZ>();
     const S *fi = static_cast<const S *>(fin);
     S *fo = static_cast<S *>(fout);
     const bool split = h->p.scheme == LESBGK_SPLIT;
     if constexpr (std::is_same<S, float>::value) {
       if (h->args.walls && h->args.wspec != 0.0f) {  // Maxwell walls: FP32 storage only (checked at set-up)
-        if (split) k_step<NR, N, true, kRing, S, true><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
-        else k_step<NR, N, false, kRing, S, true><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+        if (split) k_step<NR, N, true, kRing, S, true, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+        else k_step<NR, N, false, kRing, S, true, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
         return;
       }
     }
-    if (split) k_step<NR, N, true, kRing, S, false><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
-    else k_step<NR, N, false, kRing, S, false><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+    if (split) k_step<NR, N, true, kRing, S, false, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+    else k_step<NR, N, false, kRing, S, false, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
   });
   return 0;
 }
@@ -551,20 +586,20 @@ unsigned grid_for(const lesbgk *h, long long cells) {
 
 int launch_init(lesbgk *h, const double *fields, void *f, cudaStream_t s) {
   const unsigned grid = grid_for(h, h->args.plane);
-  dispatch(h->nr, h->order, h->p.storage, [&](auto r, auto n, auto st) {
-    constexpr int NR = decltype(r)::value, N = decltype(n)::value;
+  dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto n, auto st, auto z) {
+    constexpr int NR = decltype(r)::value, N = decltype(n)::value, NZ = decltype(z)::value;
     using S = decltype(st);
-    k_init<NR, N, S><<<grid, kBlock, 0, s>>>(fields, static_cast<S *>(f), h->args);
+    k_init<NR, N, S, NZ><<<grid, kBlock, 0, s>>>(fields, static_cast<S *>(f), h->args);
   });
   return 0;
 }
 
 int launch_moments(lesbgk *h, float *out, cudaStream_t s) {
   const void *f = h->buf[h->cur];
-  dispatch(h->nr, h->order, h->p.storage, [&](auto r, auto, auto st) {
-    constexpr int NR = decltype(r)::value;
+  dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto, auto st, auto z) {
+    constexpr int NR = decltype(r)::value, NZ = decltype(z)::value;
     using S = decltype(st);
-    k_moments<NR, S><<<kMomGrid, kMomBlock, 0, s>>>(static_cast<const S *>(f), out, h->partial, h->args);
+    k_moments<NR, S, NZ><<<kMomGrid, kMomBlock, 0, s>>>(static_cast<const S *>(f), out, h->partial, h->args);
   });
   k_reduce_partials<<<1, 128, 0, s>>>(h->partial, kMomGrid, h->sums);
   return 0;
@@ -579,7 +614,7 @@ cudaError_t launch_init(const KArgs &A, int nr, int order, const double *fields,
   long long g = (A.plane + kBlock - 1) / kBlock;
   if (g > (long long)sm_count * 16) g = (long long)sm_count * 16;
   const unsigned grid = g < 1 ? 1u : (unsigned)g;
-  dispatch(nr, order, LESBGK_F32, [&](auto r, auto n, auto) {
+  dispatch(nr, order, LESBGK_F32, 2, [&](auto r, auto n, auto, auto) {
     k_init<decltype(r)::value, decltype(n)::value, float><<<grid, kBlock, 0, s>>>(fields, f, A);
   });
   return cudaGetLastError();
@@ -620,7 +655,7 @@ extern "C" int lesbgk_create(const lesbgk_params *p, void *d_workspace, size_t b
   h->p = *p;
   h->nr = p->nroots;
   h->order = p->order ? p->order : default_order(p->nroots);
-  h->q = h->nr * h->nr;
+  h->q = h->nr * h->nr * (p->dim == 3 ? h->nr / 2 : 1);
   h->ws = static_cast<char *>(d_workspace);
   h->ws_bytes = bytes;
   h->buf_bytes = buffer_bytes(p);
@@ -737,10 +772,10 @@ extern "C" int lesbgk_get_populations(lesbgk *h, float *d_out, void *stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const long long cells = h->args.plane;
   const void *f = h->buf[h->cur];
-  dispatch(h->nr, h->order, h->p.storage, [&](auto r, auto, auto st) {
+  dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto, auto st, auto z) {
     using S = decltype(st);
-    k_ungroup<decltype(r)::value, S><<<grid_for(h, cells), kBlock, 0, s>>>(static_cast<const S *>(f), d_out, cells,
-                                                                          h->args);
+    k_ungroup<decltype(r)::value, S, decltype(z)::value>
+        <<<grid_for(h, cells), kBlock, 0, s>>>(static_cast<const S *>(f), d_out, cells, h->args);
   });
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? 0 : cuda_fail(e, "get populations");
@@ -751,9 +786,10 @@ extern "C" int lesbgk_set_populations(lesbgk *h, const float *d_in, int64_t step
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const long long cells = h->args.plane;
   void *f = h->buf[h->cur];
-  dispatch(h->nr, h->order, h->p.storage, [&](auto r, auto, auto st) {
+  dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto, auto st, auto z) {
     using S = decltype(st);
-    k_group<decltype(r)::value, S><<<grid_for(h, cells), kBlock, 0, s>>>(d_in, static_cast<S *>(f), cells, h->args);
+    k_group<decltype(r)::value, S, decltype(z)::value>
+        <<<grid_for(h, cells), kBlock, 0, s>>>(d_in, static_cast<S *>(f), cells, h->args);
   });
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "set populations");
@@ -816,10 +852,10 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocBlocks * 4 + 4
 
 // One block per kNoAllocNodesPerBlock nodes of the public layout
 // f[a][j][i] (deviations f_a - w_a); per-node arithmetic as in k_moments.
-template <int NR>
+template <int NR, int NZ = 1>
 __global__ void __launch_bounds__(kMomBlock) k_moments_public(const float *__restrict__ f, float *__restrict__ out,
                                                               double *__restrict__ partial, const KArgs A) {
-  constexpr int Q = NR * NR;
+  constexpr int Q = NZ * NR * NR;
   const long long cells = A.plane;
   ConsSums cs;
   const long long c0 = blockIdx.x * kNoAllocNodesPerBlock;
@@ -833,7 +869,7 @@ __global__ void __launch_bounds__(kMomBlock) k_moments_public(const float *__res
     node_moments<NR>(F, out, cells, c, A, d);
     cs.add(d);
   }
-  cs.write_block(partial);
+  cs.write_block(partial, NZ == 1 ? 2 : 3);
 }
 
 // Device address of g_noalloc_scratch per device, looked up once per device
@@ -872,14 +908,15 @@ extern "C" int lesbgk_moments_noalloc(const lesbgk_params *p, const float *d_pop
   tmp.p = *p;
   tmp.nr = p->nroots;
   tmp.order = p->order ? p->order : default_order(p->nroots);
-  tmp.q = tmp.nr * tmp.nr;
+  tmp.q = tmp.nr * tmp.nr * (p->dim == 3 ? tmp.nr / 2 : 1);
   if (int rc = build_tables(&tmp, nullptr)) return rc;
   double *scratch = nullptr;
   if (int rc = noalloc_scratch(&scratch)) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int blocks = (int)((cells + kNoAllocNodesPerBlock - 1) / kNoAllocNodesPerBlock);
   double *sums = scratch + (size_t)kNoAllocBlocks * 4;
-  if (p->nroots == 4) k_moments_public<4><<<blocks, kMomBlock, 0, s>>>(d_populations, d_out, scratch, tmp.args);
+  if (p->dim == 3) k_moments_public<4, 2><<<blocks, kMomBlock, 0, s>>>(d_populations, d_out, scratch, tmp.args);
+  else if (p->nroots == 4) k_moments_public<4><<<blocks, kMomBlock, 0, s>>>(d_populations, d_out, scratch, tmp.args);
   else k_moments_public<6><<<blocks, kMomBlock, 0, s>>>(d_populations, d_out, scratch, tmp.args);
   k_reduce_partials<<<1, 128, 0, s>>>(scratch, blocks, sums);
   cudaError_t e = cudaGetLastError();

@@ -41,6 +41,9 @@ int check_params(const lesbgk_params *p) {
   if (order != 3 && order != 4) return fail(LESBGK_EINVAL, "order must be 3 or 4");
   if (p->nx < 1 || p->ny < 1) return fail(LESBGK_EINVAL, "nx, ny must be >= 1");
   if ((long long)p->nx * p->ny > (1LL << 31) / 64) return fail(LESBGK_EINVAL, "grid too large");
+  if (p->dim != 0 && p->dim != 2 && p->dim != 3) return fail(LESBGK_EINVAL, "dim must be 2 or 3");
+  if (p->dim == 3 && (p->nroots != 4 || order != 3 || p->storage != LESBGK_F32))
+    return fail(LESBGK_EINVAL, "D = 3 is built as D3Q64 (nroots 4, order 3) with FP32 storage");
   if (p->bc_y != LESBGK_PERIODIC && p->bc_y != LESBGK_DIFFUSE) return fail(LESBGK_EINVAL, "bad bc_y");
   if (p->bc_y == LESBGK_DIFFUSE && p->ny < 2) return fail(LESBGK_EINVAL, "walls need ny >= 2");
   if (p->storage != LESBGK_F32 && p->storage != LESBGK_F16 && p->storage != LESBGK_BF16)
@@ -139,8 +142,9 @@ int build_setup(const lesbgk_params &p, int order, const double *h_init, Setup *
   A.c_omega = (float)(dt / (p.kn * (1.0 - p.b)));
   A.visc_pow = (float)(1.0 - p.visc_exp);
   A.vmode = p.visc_exp == 0.5 ? 1 : (p.visc_exp == 1.0 ? 2 : 0);
+  const int D = p.dim == 3 ? 3 : 2;
   A.b = (float)p.b;
-  A.beta = (float)(0.5 * (1.0 - p.b));
+  A.beta = (float)((1.0 - p.b) / D);  // rho (lambda - I) = (1-b) tr M / D + b M
   A.dtgx = (float)(dt * p.g[0]);
   A.dtgy = (float)(dt * p.g[1]);
   A.has_force = (p.g[0] != 0.0 || p.g[1] != 0.0) ? 1 : 0;
@@ -151,6 +155,7 @@ int build_setup(const lesbgk_params &p, int order, const double *h_init, Setup *
   A.plane = (long long)p.nx * p.ny;
   h->nroots = nr;
   h->order = N;
+  h->dim = D;
   for (int i = 0; i < nr; ++i) {
     h->c[i] = c[i];
     h->w[i] = w[i];
@@ -172,24 +177,38 @@ void set_wall_time(const Setup &h, double t, KArgs *out) {
   const double *c = h.c, *w = h.w;
   const double fact[kMaxOrder + 1] = {1, 1, 2, 6, 24};
   const double heat = h.wall_T_amp != 0.0 ? h.wall_T_amp * std::sin(h.wall_T_freq * t) : 0.0;
-  // wall equilibria S_a(T_w, u_w) at order N (b = 0 Gaussian projection)
+  // D = 3 stores the z-even half: levels c_z = c[nr/2 + iz] > 0
+  const int nz = h.dim == 3 ? nr / 2 : 1;
+  // wall equilibria S_a(T_w, u_w) at order N (b = 0 Gaussian projection); in
+  // D = 3 the z-factor of the isotropic Gaussian's coefficients is
+  // E[He_l(Z)] = 1, th, 3 th^2 for l = 0, 2, 4 (Z ~ N(0, T_w), u_z = 0)
   for (int s = 0; s < 2; ++s) {
     double e[kMaxOrder + 1][kMaxOrder + 1];
     const double th = h.wall_T[s] + heat - 1.0;
     gaussian_hermite_moments(N, 1.0, h.wall_ux[s], 0.0, th, 0.0, th, e);
+    const double zf[kMaxOrder + 1] = {1.0, 0.0, th, 0.0, 3.0 * th * th};
     double A_out = 0.0, Z_out = 0.0;
+    for (int iz = 0; iz < nz; ++iz)
     for (int ix = 0; ix < nr; ++ix) {
-      double hx[kMaxOrder + 1];
+      double hx[kMaxOrder + 1], hz[kMaxOrder + 1];
       hermite_values(kMaxOrder, c[ix], hx);
+      hermite_values(kMaxOrder, h.dim == 3 ? c[nr / 2 + iz] : 0.0, hz);
       for (int iy = 0; iy < nr; ++iy) {
         double hy[kMaxOrder + 1];
         hermite_values(kMaxOrder, c[iy], hy);
         double sum = 0.0;
         for (int m = 0; m <= N; ++m)
-          for (int k = 0; m + k <= N; ++k) sum += e[m][k] * hx[m] * hy[k] / (fact[m] * fact[k]);
-        const double wa = w[ix] * w[iy];
+          for (int k = 0; m + k <= N; ++k) {
+            if (h.dim != 3) {
+              sum += e[m][k] * hx[m] * hy[k] / (fact[m] * fact[k]);
+              continue;
+            }
+            for (int l = 0; m + k + l <= N; l += 2)
+              sum += e[m][k] * zf[l] * hx[m] * hy[k] * hz[l] / (fact[m] * fact[k] * fact[l]);
+          }
+        const double wa = w[ix] * w[iy] * (h.dim == 3 ? w[nr / 2 + iz] : 1.0);
         const double S = wa * sum;
-        const int a = ix * nr + iy;
+        const int a = (iz * nr + ix) * nr + iy;
         A.wS[s][a] = (float)S;
         A.wSdev[s][a] = (float)(S - wa);
         const bool outgoing = (s == 0) ? (c[iy] > 0.0) : (c[iy] < 0.0);

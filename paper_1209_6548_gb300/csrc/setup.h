@@ -20,13 +20,13 @@ struct KArgs {
   float hw[kMaxR][kMaxN + 1];  // w_i He_m(c_i) / m!
   float ax[kMaxR], kx[kMaxR];  // c_i dt/dx and (1 - |c_i| dt/dx)/2
   float ay[kMaxR], ky[kMaxR];  // same along y
-  float wS[2][kMaxQ];          // wall equilibrium S_a(T_w, u_w), [0] bottom, [1] top
+  float wS[2][kMaxQ];          // wall equilibrium S_a(T_w, u_w) per stored population, [0] bottom, [1] top
   float wSdev[2][kMaxQ];       // S_a - w_a
   float wA[2], wB[2];          // sum_out |c_y|(S-w) and 1/sum_out |c_y| S
   float wq[kMaxQ], iwq[kMaxQ]; // 16-bit storage: stored = df * iwq, df = stored * wq
   float c_omega;               // dt / (Kn (1-b)):  dt/tau = c_omega rho T^(1-varpi)
   float visc_pow;              // 1 - varpi
-  float b, beta;               // b and (1-b)/2
+  float b, beta;               // b and (1-b)/D
   float dtgx, dtgy;            // dt g
   int nx, ny, walls, has_force, vmode;  // vmode 1: varpi = 1/2, 2: varpi = 1, 0: general
   int rows, nstrips, nseg;
@@ -40,7 +40,7 @@ struct Setup {
   KArgs args;                      // tables and per-solve scalars (nx, ny, plane, walls filled)
   double dt, dx, dy, cmax, tau_ref;
   // what the wall tables are built from (Sec. 3.2; heating of Sec. 4.2)
-  int nroots, order;
+  int nroots, order, dim;          // dim: velocity-set dimension D (2 or 3)
   double c[kMaxR], w[kMaxR];       // FP64 quadrature
   double wall_T[2], wall_ux[2];    // steady wall temperature and velocity
   double wall_T_amp, wall_T_freq;  // T_w(t) = wall_T + wall_T_amp sin(wall_T_freq t)

@@ -45,6 +45,7 @@ class Params(C.Structure):
         ("cfl", C.c_double), ("dt", C.c_double),
         ("wall_T", C.c_double * 2), ("wall_ux", C.c_double * 2), ("g", C.c_double * 2),
         ("wall_specular", C.c_double), ("wall_T_amp", C.c_double), ("wall_T_freq", C.c_double),
+        ("dim", C.c_int32),
     ]
 
 
@@ -121,7 +122,7 @@ def _check(rc: int) -> None:
 
 def make_params(*, nroots=4, order=0, nx, ny, bc_y=DIFFUSE, kn, b, visc_exp=0.5, cfl=0.5, dt=0.0,
                 wall_T=(1.0, 1.0), wall_ux=(0.0, 0.0), g=(0.0, 0.0), storage=F32, scheme=UNSPLIT,
-                wall_specular=0.0, wall_T_amp=0.0, wall_T_freq=0.0) -> Params:
+                wall_specular=0.0, wall_T_amp=0.0, wall_T_freq=0.0, dim=2) -> Params:
     p = Params()
     p.struct_size = C.sizeof(Params)
     p.nroots, p.order, p.nx, p.ny, p.bc_y, p.storage = nroots, order, nx, ny, bc_y, storage
@@ -131,7 +132,14 @@ def make_params(*, nroots=4, order=0, nx, ny, bc_y=DIFFUSE, kn, b, visc_exp=0.5,
     p.wall_ux[0], p.wall_ux[1] = wall_ux
     p.g[0], p.g[1] = g
     p.wall_specular, p.wall_T_amp, p.wall_T_freq = wall_specular, wall_T_amp, wall_T_freq
+    p.dim = dim
     return p
+
+
+def stored_q(p: Params) -> int:
+    """Values stored per node: nroots^2 for the 2D sets, nroots^3 / 2 for the
+    D = 3 set (its z-even half)."""
+    return p.nroots * p.nroots * (p.nroots // 2 if p.dim == 3 else 1)
 
 
 def params_from_problem(prob, dt: float = 0.0) -> Params:
@@ -139,7 +147,7 @@ def params_from_problem(prob, dt: float = 0.0) -> Params:
                        kn=prob.kn, b=prob.b, visc_exp=prob.visc_exp, cfl=prob.cfl, dt=dt,
                        wall_T=tuple(prob.wall_T), wall_ux=tuple(prob.wall_ux), g=tuple(prob.g),
                        scheme=prob.scheme, wall_specular=prob.wall_specular, wall_T_amp=prob.wall_T_amp,
-                       wall_T_freq=prob.wall_T_freq)
+                       wall_T_freq=prob.wall_T_freq, dim=getattr(prob, "dim", 2))
 
 
 def workspace_size(p: Params) -> int:
@@ -232,7 +240,7 @@ class Solver:
 
     @property
     def q(self) -> int:
-        return self.params.nroots * self.params.nroots
+        return stored_q(self.params)
 
     def reinit(self, d_fields=None) -> None:
         """Re-initialise from a (4, ny, nx) float64 CUDA tensor (or rest)."""
@@ -363,7 +371,7 @@ class Batch:
 
     def populations(self, slot: int):
         p = self.params[slot]
-        out = self._torch.empty((p.nroots * p.nroots, p.ny, p.nx), dtype=self._torch.float32, device="cuda")
+        out = self._torch.empty((stored_q(p), p.ny, p.nx), dtype=self._torch.float32, device="cuda")
         _check(lib().lesbgk_batch_get_populations(C.c_void_p(self.handle), C.c_int32(slot),
                                                   C.c_void_p(out.data_ptr()), self._s))
         return out

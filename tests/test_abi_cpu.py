@@ -59,6 +59,10 @@ def test_struct_sizes_match_header(lib):
     (dict(wall_specular=0.5, storage=L.F16), L.EINVAL),  # Maxwell walls: FP32 storage only
     (dict(wall_T_amp=1.0), L.EINVAL),                     # T_w would reach 0
     (dict(wall_T_amp=float("nan")), L.EINVAL),
+    (dict(dim=4), L.EINVAL),
+    (dict(dim=3, nroots=6), L.EINVAL),                    # D = 3 is built as D3Q64
+    (dict(dim=3, order=4), L.EINVAL),
+    (dict(dim=3, storage=L.F16), L.EINVAL),
 ])
 def test_invalid_arguments_rejected(lib, kw, code):
     base = dict(nx=4, ny=8, kn=0.1, b=0.0, bc_y=L.DIFFUSE)
@@ -72,6 +76,14 @@ def test_wall_models_accepted(lib):
     for kw in (dict(wall_specular=1.0), dict(wall_T_amp=0.02, wall_T_freq=0.5),
                dict(wall_T_amp=0.02, wall_T_freq=0.5, storage=L.BF16)):
         assert L.workspace_size(L.make_params(nx=4, ny=8, kn=0.1, b=0.0, bc_y=L.DIFFUSE, **kw)) > 0
+
+
+def test_d3_workspace_holds_the_z_even_half(lib):
+    """D3Q64 stores 32 values per node (its z-even half): two FP32 buffers."""
+    p = L.make_params(nx=64, ny=32, kn=0.1, b=0.0, bc_y=L.DIFFUSE, dim=3)
+    assert L.stored_q(p) == 32
+    n = L.workspace_size(p)
+    assert 2 * 32 * 64 * 32 * 4 <= n < 2 * 33 * 64 * 32 * 4 + (1 << 16)
 
 
 def test_workspace_size_formula(lib):

@@ -358,3 +358,84 @@ def test_unsteady_wall_heating(kn, st):
     for n, g, r, *_ in res:
         assert_fields_close(g, r, what=f"heating step {n}")
     assert np.max(np.abs(res[-1][2][3] - 1.0)) > 1e-3  # the walls did heat the gas
+
+
+# ---------------------------------------------------------------- D = 3 set
+# D3Q64 (N = 3) on the 2D grid: the library stores the z-even half (32 values
+# per node); the oracle runs all 64 velocities.
+def d3(prob):
+    from dataclasses import replace
+    return replace(prob, dim=3, nroots=4, order=0, name=prob.name + "_d3q64")
+
+
+def z_even_half(fp):
+    """Oracle populations (64, ny, nx) -> deviations at the 32 stored
+    velocities (iz, ix, iy), c_z = c[2 + iz] > 0."""
+    *_, w = O.velocity_set_d(4, 3)
+    idx = [(ix * 4 + iy) * 4 + 2 + iz for iz in range(2) for ix in range(4) for iy in range(4)]
+    return (fp - w[:, None, None])[idx]
+
+
+def assert_d3_populations(gp, fp, what):
+    dev = z_even_half(fp)
+    err = np.max(np.abs(gp - dev))
+    assert err <= 2e-6 * np.max(np.abs(dev)), f"{what} populations: {err:.3e} vs {np.max(np.abs(dev)):.3e}"
+
+
+def test_d3_couette_2000_steps():
+    """Couette 4x64 with the D = 3 set (the paper's C_p = 5/2 gas)."""
+    prob = d3(I.couette_4x64())
+    res, s, _ = run_pair(prob, None, [1, 10, 100, 2000])
+    for n, g, r, gp, fp in res:
+        assert_fields_close(g, r, what=f"d3 couette step {n}")
+        assert_d3_populations(gp, fp, f"d3 couette step {n}")
+    assert s.info.q == 32
+
+
+@pytest.mark.parametrize("scheme", [I.UNSPLIT, I.SPLIT])
+@pytest.mark.parametrize("nx,ny", [(70, 37), (5, 66), (1, 1)])
+def test_d3_rough_periodic_fields(nx, ny, scheme):
+    prob = d3(I.Problem(name="rough", nx=nx, ny=ny, bc_y=I.PERIODIC, kn=0.05, b=-0.5, scheme=scheme))
+    fields = I.random_fields(prob, seed=nx * 100 + ny + 7)
+    res, *_ = run_pair(prob, fields, [1, 6])
+    for n, g, r, gp, fp in res:
+        assert_fields_close(g, r, what=f"d3 {nx}x{ny} step {n}")
+        assert_d3_populations(gp, fp, f"d3 {nx}x{ny} step {n}")
+
+
+@pytest.mark.parametrize("b", [-0.5, 0.5])
+def test_d3_walls_force_rough(b):
+    """Moving walls at two temperatures, body force, rough interior."""
+    prob = d3(I.Problem(name="wf", nx=60, ny=45, bc_y=I.DIFFUSE, kn=0.1, b=b, wall_ux=(-0.05, 0.05),
+                        wall_T=(0.97, 1.03), g=(1e-3, 2e-4)))
+    fields = I.random_fields(prob, seed=31, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
+    res, *_ = run_pair(prob, fields, [1, 10])
+    for n, g, r, gp, fp in res:
+        assert_fields_close(g, r, what=f"d3 walls b={b} step {n}")
+        assert_d3_populations(gp, fp, f"d3 walls b={b} step {n}")
+
+
+def test_d3_maxwell_walls_and_heating():
+    """Specular share 0.3 and heated walls (Sec. 3.2, Sec. 4.2) with D = 3."""
+    prob = d3(I.Problem(name="mh", nx=8, ny=40, bc_y=I.DIFFUSE, kn=0.2, b=-0.5, wall_specular=0.3,
+                        wall_T_amp=0.02, wall_T_freq=0.5553603672697958))
+    res, *_ = run_pair(prob, None, [1, 50, 300])
+    for n, g, r, *_ in res:
+        assert_fields_close(g, r, what=f"d3 maxwell+heating step {n}")
+
+
+def test_d3_conservation_and_totals():
+    """Periodic D = 3: the FP64 totals match the oracle's (energy counts
+    c_z^2: 3/2 rho T per node at rest) and are conserved over 200 steps."""
+    prob = d3(I.tgv(128, steps=200))
+    fields = I.initial_fields(prob)
+    dt = time_step(prob, fields)
+    s = gpu_solver(prob, dt, fields)
+    op = oracle_params(prob, dt)
+    _, ref = O.moments(op, O.init(op, fields))
+    _, s0 = s.moments(sums=True)
+    cells = prob.cells
+    assert np.allclose(s0, ref, rtol=0, atol=1e-9 * cells), (s0, ref)
+    s.step(200)
+    _, s1 = s.moments(sums=True)
+    assert np.allclose(s1, s0, rtol=0, atol=1e-9 * cells)

@@ -31,8 +31,10 @@ def _built():
 
 @pytest.mark.parametrize("prob", [I.tgv(512, steps=20), I.poiseuille(64, 300, steps=20),
                                   I.Problem(name="d2q36", nroots=6, nx=45, ny=33, bc_y=I.DIFFUSE, kn=0.1,
-                                            b=-0.5, wall_ux=(-0.05, 0.05))],
-                         ids=["tgv512", "poiseuille64x300", "d2q36"])
+                                            b=-0.5, wall_ux=(-0.05, 0.05)),
+                                  I.Problem(name="d3q64", nroots=4, dim=3, nx=45, ny=33, bc_y=I.DIFFUSE, kn=0.1,
+                                            b=0.5, wall_ux=(-0.05, 0.05), g=(1e-3, 0.0))],
+                         ids=["tgv512", "poiseuille64x300", "d2q36", "d3q64"])
 def test_noalloc_moments_match_workspace_moments(prob):
     import torch
     fields = I.initial_fields(prob) if prob.init == "tgv" else None
