@@ -105,6 +105,34 @@ def unsteady_heating(kn: float = 0.1, b: float = -0.5, st: float = 0.55536036726
                    wall_T_amp=amp, wall_T_freq=st, steps=steps)
 
 
+def kn_of_kd(kd: float) -> float:
+    """Kn of Sec. 2.2 from the K_D = sqrt(pi/2) Kn that labels the paper's results."""
+    return kd / np.sqrt(np.pi / 2.0)
+
+
+# The high-Mach-number workloads of Sec. 4 (the paper runs them with its
+# "11th-order" set, D2Q36 here, or the D = 3 set for its C_p = 5/2 gas).
+def couette_high_ma(kd: float = 0.05, nroots: int = 6, dim: int = 2, b: float = -0.5, ny: int = 64,
+                    steps: int = 4000) -> Problem:
+    """Couette flow with walls at -/+0.2 (viscous heating), T_w = 1."""
+    return Problem(name=f"couette_ma_kd{kd:g}", nroots=nroots, dim=dim, nx=4, ny=ny, bc_y=DIFFUSE,
+                   kn=kn_of_kd(kd), b=b, wall_ux=(-0.2, 0.2), steps=steps)
+
+
+def poiseuille_high_force(kd: float = 0.1, nroots: int = 6, dim: int = 2, b: float = -0.5, ny: int = 64,
+                          steps: int = 2000) -> Problem:
+    """Force-driven Poiseuille flow, g = 0.22 along x, walls at rest, T_w = 1."""
+    return Problem(name=f"poiseuille_g0.22_kd{kd:g}", nroots=nroots, dim=dim, nx=4, ny=ny, bc_y=DIFFUSE,
+                   kn=kn_of_kd(kd), b=b, g=(0.22, 0.0), steps=steps)
+
+
+def couette_fourier(kd: float = 0.1, nroots: int = 6, dim: int = 2, b: float = -0.5, ny: int = 64,
+                    steps: int = 4000) -> Problem:
+    """Combined Couette-Fourier flow: walls at -/+0.2 and T_w = 1 -/+ 0.15."""
+    return Problem(name=f"couette_fourier_kd{kd:g}", nroots=nroots, dim=dim, nx=4, ny=ny, bc_y=DIFFUSE,
+                   kn=kn_of_kd(kd), b=b, wall_ux=(-0.2, 0.2), wall_T=(0.85, 1.15), steps=steps)
+
+
 def initial_fields(p: Problem) -> np.ndarray:
     """(4, ny, nx) float64: rho, u_x, u_y, T at the nodes.
 

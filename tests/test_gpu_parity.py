@@ -439,3 +439,19 @@ def test_d3_conservation_and_totals():
     s.step(200)
     _, s1 = s.moments(sums=True)
     assert np.allclose(s1, s0, rtol=0, atol=1e-9 * cells)
+
+
+# ---------------------------------------------------------------- high Mach number (Sec. 4)
+@pytest.mark.parametrize("kind", ["couette", "poiseuille", "couette_fourier"])
+@pytest.mark.parametrize("nroots,dim", [(6, 2), (4, 3)])
+def test_high_mach_workloads(kind, nroots, dim):
+    """The paper's nonlinear workloads: Couette at -/+0.2, force-driven
+    Poiseuille with g = 0.22, Couette-Fourier with T_w = 1 -/+ 0.15, at
+    K_D = 0.1, on D2Q36 (N = 4) and D3Q64 (N = 3)."""
+    gen = {"couette": I.couette_high_ma, "poiseuille": I.poiseuille_high_force,
+           "couette_fourier": I.couette_fourier}[kind]
+    prob = gen(kd=0.1, nroots=nroots, dim=dim, ny=40)
+    res, *_ = run_pair(prob, None, [1, 100, 1000])
+    for n, g, r, *_ in res:
+        assert_fields_close(g, r, what=f"{prob.name} D={dim} step {n}")
+    assert np.max(np.abs(res[-1][2][1])) > 0.1  # a high-speed flow did develop
