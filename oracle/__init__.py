@@ -30,12 +30,12 @@ _lib = None
 class OrcParams(C.Structure):
     _fields_ = [
         ("nroots", C.c_int32), ("order", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32),
-        ("bc_y", C.c_int32), ("scheme", C.c_int32), ("dim", C.c_int32),
+        ("bc_y", C.c_int32), ("scheme", C.c_int32), ("dim", C.c_int32), ("bc_x", C.c_int32),
         ("kn", C.c_double), ("b", C.c_double), ("visc_exp", C.c_double),
         ("dt", C.c_double), ("dx", C.c_double), ("dy", C.c_double),
         ("wall_T", C.c_double * 2), ("wall_ux", C.c_double * 2), ("g", C.c_double * 2),
         ("wall_specular", C.c_double), ("wall_T_amp", C.c_double), ("wall_T_freq", C.c_double),
-        ("time", C.c_double),
+        ("time", C.c_double), ("wall_Tx", C.c_double * 2),
     ]
 
 
@@ -142,10 +142,11 @@ UNSPLIT, SPLIT = 0, 1
 
 def make_params(*, nroots, order, nx, ny, bc_y, kn, b, visc_exp, dt, dx, dy,
                 wall_T=(1.0, 1.0), wall_ux=(0.0, 0.0), g=(0.0, 0.0), scheme=UNSPLIT, wall_specular=0.0,
-                wall_T_amp=0.0, wall_T_freq=0.0, time=0.0, dim=2) -> OrcParams:
+                wall_T_amp=0.0, wall_T_freq=0.0, time=0.0, dim=2, bc_x=0, wall_Tx=(1.0, 1.0)) -> OrcParams:
     p = OrcParams()
     p.nroots, p.order, p.nx, p.ny, p.bc_y, p.scheme = nroots, order, nx, ny, bc_y, scheme
-    p.dim = dim
+    p.dim, p.bc_x = dim, bc_x
+    p.wall_Tx[0], p.wall_Tx[1] = wall_Tx
     p.kn, p.b, p.visc_exp, p.dt, p.dx, p.dy = kn, b, visc_exp, dt, dx, dy
     p.wall_T[0], p.wall_T[1] = wall_T
     p.wall_ux[0], p.wall_ux[1] = wall_ux

@@ -27,6 +27,11 @@
  *   - Truncated Maxwellian S(T,u), Eq. (feq0), and the diffuse wall of
  *     Sec. 3.2 (outgoing half = rho_W S, ghosts = wall node).
  *
+ * Walls in x (a cavity; not in the paper, whose flows are all uniform in x):
+ * fully diffuse walls at rest on columns i = 0 and nx-1, treated like the
+ * y-walls; a node on both a y-wall and an x-wall (a corner) follows the
+ * corner rule of wall_corner().
+ *
  * Readings where the paper is silent (each restated where it is used):
  *   D is the dimension of the velocity set, used in T, Eq. (feq0) and the chi
  *   traces (the paper's runs take D = 3 without naming their set; the 2D sets
@@ -65,6 +70,7 @@ typedef struct orc_params {
                        x-sweep of the y-swept values (reading for 2D flows) */
   int32_t dim;      /* velocity-set dimension D: 2 (Q = nroots^2) or 3
                        (Q = nroots^3); 0 means 2 */
+  int32_t bc_x;     /* 0 = periodic in x, 1 = diffuse walls at rest on i=0, i=nx-1 */
   double kn;        /* Kn of Sec. 2.2 */
   double b;         /* ES parameter, Pr = 1/(1-b) */
   double visc_exp;  /* varpi in mu = T^varpi */
@@ -76,6 +82,7 @@ typedef struct orc_params {
   double wall_T_amp;    /* wall temperature T_w(t) = wall_T + amp sin(freq t) (Sec. 4.2) */
   double wall_T_freq;
   double time;          /* time of the state handed to orc_init / orc_step / orc_run */
+  double wall_Tx[2];    /* x-wall temperatures, [0] left (i=0), [1] right (i=nx-1) */
 } orc_params;
 
 static int orc_threads = 1;
@@ -512,6 +519,14 @@ static size_t fidx(const orc_params *p, int a, int j, int i) {
 
 static int wrap(int i, int n) { return ((i % n) + n) % n; }
 
+/* Column index of neighbour i+di: periodic wrap, or ghosts = wall node. */
+static int col_of(const orc_params *p, int i) {
+  if (p->bc_x == 0) return wrap(i, p->nx);
+  if (i < 0) return 0;
+  if (i >= p->nx) return p->nx - 1;
+  return i;
+}
+
 /* Row index of neighbour j+dj: periodic wrap, or ghosts = wall node. */
 static int row_of(const orc_params *p, int j) {
   if (p->bc_y == 0) return wrap(j, p->ny);
@@ -550,11 +565,72 @@ static void wall_node(const orc_lattice *L, const orc_params *p, double *f, int 
   }
 }
 
+/* Diffuse wall at rest normal to x at node (i, j): side 0 = left wall
+ * (i = 0, normal +x), side 1 = right wall (i = nx-1, normal -x); the rule of
+ * wall_node with c_x in place of c_y and S(T_wx, u = 0). */
+static void wall_node_x(const orc_lattice *L, const orc_params *p, double *f, int i, int j, int side) {
+  double n_x = side == 0 ? 1.0 : -1.0;
+  double u[ORC_MAXD] = {0.0, 0.0, 0.0};
+  double S[ORC_MAXQ];
+  for (int a = 0; a < L->Q; ++a) S[a] = feq0_S(p->order, L->D, p->wall_Tx[side], u, L->c[a], L->w[a]);
+  double num = 0.0, den = 0.0;
+  for (int a = 0; a < L->Q; ++a) {
+    double cn = L->c[a][0] * n_x;
+    if (cn < 0.0) num += fabs(cn) * f[fidx(p, a, j, i)];
+    if (cn > 0.0) den += fabs(cn) * S[a];
+  }
+  double rw = num / den;
+  for (int a = 0; a < L->Q; ++a)
+    if (L->c[a][0] * n_x > 0.0) f[fidx(p, a, j, i)] = rw * S[a];
+}
+
+/* Corner node (i, j) on the x-wall `xside` and the y-wall `yside` (a reading;
+ * the paper has no corners).  The node belongs to both walls: populations
+ * moving away from either wall (c.n_x > 0 or c.n_y > 0, n_x and n_y the
+ * inward normals) are re-emitted as rho_W S(T_wx, u = 0) -- the side wall's,
+ * so a moving lid stops short of the corners -- and the others, arriving
+ * from the interior towards both walls, are kept.  rho_W makes the net mass
+ * flux along n = n_x + n_y zero; with the wall at rest sum_a (c.n) S_a = 0,
+ * so rho_W = sum_in |c.n| f / sum_in |c.n| S over the kept populations. */
+static void wall_corner(const orc_lattice *L, const orc_params *p, double *f, int i, int j, int xside,
+                        int yside) {
+  double n_x = xside == 0 ? 1.0 : -1.0, n_y = yside == 0 ? 1.0 : -1.0;
+  double u[ORC_MAXD] = {0.0, 0.0, 0.0};
+  double S[ORC_MAXQ];
+  for (int a = 0; a < L->Q; ++a) S[a] = feq0_S(p->order, L->D, p->wall_Tx[xside], u, L->c[a], L->w[a]);
+  double num = 0.0, den = 0.0;
+  for (int a = 0; a < L->Q; ++a) {
+    int kept = L->c[a][0] * n_x < 0.0 && L->c[a][1] * n_y < 0.0;
+    double cn = fabs(L->c[a][0] * n_x + L->c[a][1] * n_y);
+    if (kept) {
+      num += cn * f[fidx(p, a, j, i)];
+      den += cn * S[a];
+    }
+  }
+  double rw = num / den;
+  for (int a = 0; a < L->Q; ++a) {
+    int kept = L->c[a][0] * n_x < 0.0 && L->c[a][1] * n_y < 0.0;
+    if (!kept) f[fidx(p, a, j, i)] = rw * S[a];
+  }
+}
+
 static void apply_walls(const orc_lattice *L, const orc_params *p, double *f, double t) {
-  if (p->bc_y != 1) return;
-  for (int i = 0; i < p->nx; ++i) {
-    wall_node(L, p, f, i, 0, 0, t);
-    wall_node(L, p, f, i, p->ny - 1, 1, t);
+  int xw = p->bc_x == 1, yw = p->bc_y == 1;
+  if (yw)
+    for (int i = xw ? 1 : 0; i < p->nx - (xw ? 1 : 0); ++i) {
+      wall_node(L, p, f, i, 0, 0, t);
+      wall_node(L, p, f, i, p->ny - 1, 1, t);
+    }
+  if (xw)
+    for (int j = yw ? 1 : 0; j < p->ny - (yw ? 1 : 0); ++j) {
+      wall_node_x(L, p, f, 0, j, 0);
+      wall_node_x(L, p, f, p->nx - 1, j, 1);
+    }
+  if (xw && yw) {
+    wall_corner(L, p, f, 0, 0, 0, 0);
+    wall_corner(L, p, f, p->nx - 1, 0, 1, 0);
+    wall_corner(L, p, f, 0, p->ny - 1, 0, 1);
+    wall_corner(L, p, f, p->nx - 1, p->ny - 1, 1, 1);
   }
 }
 
@@ -565,6 +641,8 @@ static int check_params(const orc_params *p) {
   if (p->order < 0 || p->order > ORC_MAXN) return -1;
   if (p->nx < 1 || p->ny < 1) return -1;
   if (p->bc_y == 1 && p->ny < 2) return -1;
+  if (p->bc_x != 0 && p->bc_x != 1) return -1;
+  if (p->bc_x == 1 && p->nx < 2) return -1;
   if (p->scheme != 0 && p->scheme != 1) return -1;
   if (!(p->wall_specular >= 0.0 && p->wall_specular <= 1.0)) return -1;
   return 0;
@@ -637,12 +715,12 @@ int orc_step(const orc_params *p, const double *fin, double *fout) {
         double fx[5], fy[5];
         double coll = p->dt / tau * (fes[a] - f[a]) + gf[a] * p->dt;
         if (p->scheme == 1) {
-          for (int k = -2; k <= 2; ++k) fx[k + 2] = fstar[fidx(p, a, j, wrap(i + k, p->nx))];
+          for (int k = -2; k <= 2; ++k) fx[k + 2] = fstar[fidx(p, a, j, col_of(p, i + k))];
           double dFx = flux_difference(cx, nux, fx[0], fx[1], fx[2], fx[3], fx[4]);
           fout[fidx(p, a, j, i)] = fx[2] - cx * p->dt / p->dx * dFx + coll;
         } else {
           for (int k = -2; k <= 2; ++k) {
-            fx[k + 2] = fin[fidx(p, a, j, wrap(i + k, p->nx))];
+            fx[k + 2] = fin[fidx(p, a, j, col_of(p, i + k))];
             fy[k + 2] = fin[fidx(p, a, row_of(p, j + k), i)];
           }
           double dFx = flux_difference(cx, nux, fx[0], fx[1], fx[2], fx[3], fx[4]);

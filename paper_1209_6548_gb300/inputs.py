@@ -32,6 +32,9 @@ class Problem:
             thermodynamics on the same two-dimensional grid).
     order:  Hermite truncation order N of f_ES (0 selects the default).
     bc_y:   PERIODIC or DIFFUSE (walls on rows j=0 and j=ny-1).
+    bc_x:   PERIODIC or DIFFUSE (walls at rest on columns i=0 and i=nx-1, at
+            temperatures wall_Tx; with walls on both axes: a cavity whose lid
+            is the top wall, moving at wall_ux[1]).
     kn, b, visc_exp: Knudsen number, ES parameter b, viscosity exponent.
     cfl:    Courant number used when no explicit dt is given.
     wall_T, wall_ux: (bottom, top) wall temperature and x-velocity.
@@ -66,6 +69,8 @@ class Problem:
     wall_specular: float = 0.0  # 1 - accommodation gamma of the Maxwell wall model
     wall_T_amp: float = 0.0     # wall heating T_w(t) = wall_T + amp sin(freq t)
     wall_T_freq: float = 0.0
+    bc_x: int = PERIODIC
+    wall_Tx: tuple = (1.0, 1.0)
 
     @property
     def cells(self) -> int:
@@ -131,6 +136,15 @@ def couette_fourier(kd: float = 0.1, nroots: int = 6, dim: int = 2, b: float = -
     """Combined Couette-Fourier flow: walls at -/+0.2 and T_w = 1 -/+ 0.15."""
     return Problem(name=f"couette_fourier_kd{kd:g}", nroots=nroots, dim=dim, nx=4, ny=ny, bc_y=DIFFUSE,
                    kn=kn_of_kd(kd), b=b, wall_ux=(-0.2, 0.2), wall_T=(0.85, 1.15), steps=steps)
+
+
+def lid_driven_cavity(n: int = 256, u_lid: float = 0.05, kn: float = 0.1, b: float = -0.5, nroots: int = 4,
+                      steps: int = 4000) -> Problem:
+    """2D lid-driven cavity on the unit square: n x n nodes, walls on all four
+    sides at T_w = 1, the top wall moving at u_lid in x (not in the paper:
+    its flows are uniform in x; a standard 2D test of the wall rule)."""
+    return Problem(name=f"cavity_{n}_kn{kn:g}", nroots=nroots, nx=n, ny=n, bc_y=DIFFUSE, bc_x=DIFFUSE, kn=kn, b=b,
+                   wall_ux=(0.0, u_lid), scheme=SPLIT, steps=steps)
 
 
 def initial_fields(p: Problem) -> np.ndarray:

@@ -5,7 +5,9 @@ problem statement, and passed explicitly to both the oracle and the CUDA
 library, so that neither side's input comes from the other.
 
 Spacing: a periodic axis of n nodes has delta = 1/n; with walls on rows 0 and
-ny-1 the channel width is 1, delta_y = 1/(ny-1) and delta_x = delta_y.
+ny-1 the channel width is 1, delta_y = 1/(ny-1) and delta_x = delta_y (and
+the same with the axes exchanged); with walls on both axes the box is the
+unit square, delta_x = 1/(nx-1), delta_y = 1/(ny-1).
 Time step: dt = min(cfl * min(dx, dy) / c_max, tau_ref) with
 tau_ref = (Kn/Pr) T_max^(varpi-1) / rho_max, T_max over the initial fields and
 the walls' peak temperature (forward-Euler relaxation stays at dt/tau <= 1 at
@@ -26,10 +28,16 @@ def order_of(p: Problem) -> int:
 
 
 def spacing(p: Problem):
-    if p.bc_y == PERIODIC:
+    bc_x = getattr(p, "bc_x", PERIODIC)
+    if p.bc_y == PERIODIC and bc_x == PERIODIC:
         return 1.0 / p.nx, 1.0 / p.ny
-    d = 1.0 / (p.ny - 1)
-    return d, d
+    if bc_x == PERIODIC:  # walls in y: channel of width 1, square cells
+        d = 1.0 / (p.ny - 1)
+        return d, d
+    if p.bc_y == PERIODIC:  # walls in x only
+        d = 1.0 / (p.nx - 1)
+        return d, d
+    return 1.0 / (p.nx - 1), 1.0 / (p.ny - 1)  # walls on both axes: the unit square
 
 
 def time_step(p: Problem, fields=None) -> float:
@@ -37,6 +45,8 @@ def time_step(p: Problem, fields=None) -> float:
     c, _ = O.gauss_hermite_1d(p.nroots)
     dt_cfl = p.cfl * min(dx, dy) / float(np.max(np.abs(c)))
     tmax = max(p.wall_T) + abs(p.wall_T_amp) if p.bc_y != PERIODIC else 1.0
+    if getattr(p, "bc_x", PERIODIC) != PERIODIC:
+        tmax = max(tmax, max(p.wall_Tx))
     rmax = 1.0
     if fields is not None:
         tmax = max(tmax, float(fields[3].max()))
@@ -53,7 +63,7 @@ def oracle_params(p: Problem, dt: float, nx=None, ny=None, bc_y=None):
                          visc_exp=p.visc_exp, dt=dt, dx=dx, dy=dy, wall_T=tuple(p.wall_T),
                          wall_ux=tuple(p.wall_ux), g=tuple(p.g), scheme=p.scheme,
                          wall_specular=p.wall_specular, wall_T_amp=p.wall_T_amp, wall_T_freq=p.wall_T_freq,
-                         dim=p.dim)
+                         dim=p.dim, bc_x=p.bc_x, wall_Tx=tuple(p.wall_Tx))
 
 
 GROUPS = {"rho": ("rho",), "T": ("T",), "u": ("ux", "uy"), "sigma": ("sxx", "sxy", "syy"),
