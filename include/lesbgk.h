@@ -88,7 +88,7 @@ typedef struct lesbgk_params {
   int32_t nroots;       /* Gauss-Hermite roots per axis: 4 (D2Q16) or 6 (D2Q36) */
   int32_t order;        /* Hermite order N of f_ES (3 or 4); 0 = 3 for D2Q16, 4 for D2Q36 */
   int32_t nx, ny;       /* nodes; nx >= 1; ny >= 1 (>= 2 with walls) */
-  int32_t bc_y;         /* LESBGK_PERIODIC or LESBGK_DIFFUSE */
+  int32_t bc_y;         /* LESBGK_PERIODIC or LESBGK_DIFFUSE (walls on rows j = 0 and ny-1) */
   int32_t storage;      /* LESBGK_F32, LESBGK_F16 or LESBGK_BF16 */
   int32_t scheme;       /* LESBGK_UNSPLIT (default) or LESBGK_SPLIT */
   double kn;            /* Knudsen number of Sec. 2.2, > 0 */
@@ -114,6 +114,16 @@ typedef struct lesbgk_params {
                            (Q = 32 values per node, population a = iz*16 + ix*4 + iy,
                            c_z = c[2 + iz]), each value standing for +c_z and -c_z.
                            T = tr P/(3 rho) and sigma is trace-free in 3D in the moments. */
+  int32_t bc_x;         /* LESBGK_PERIODIC (default) or LESBGK_DIFFUSE: fully diffuse walls at rest
+                           on columns i = 0 and nx-1 (not in the paper, whose flows are uniform
+                           in x), at temperatures wall_Tx; ghost columns hold the wall node.
+                           With walls in y as well the domain is a cavity (the unit square,
+                           dx = 1/(nx-1), dy = 1/(ny-1)) whose lid is the top wall (wall_ux[1]);
+                           a corner node belongs to both walls: the populations arriving
+                           towards both walls are kept, the others re-emitted as rho_W S(T_wx,
+                           u = 0) with zero net mass flux along n_x + n_y.  With walls in x only,
+                           dy = dx = 1/(nx-1).  FP32 storage, fully diffuse y-walls. */
+  double wall_Tx[2];    /* x-wall temperatures, [0] = left (i = 0), [1] = right (i = nx-1) */
 } lesbgk_params;
 
 /* Read-only facts about a created solver. */

@@ -602,6 +602,7 @@ extern "C" int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const d
   if (p->wall_specular != 0.0 || p->wall_T_amp != 0.0)
     return fail(LESBGK_EINVAL, "batched instances take steady, fully diffuse walls");
   if (p->dim == 3) return fail(LESBGK_EINVAL, "batched instances take the 2D velocity sets");
+  if (p->bc_x != LESBGK_PERIODIC) return fail(LESBGK_EINVAL, "batched instances are periodic in x");
   if ((long long)(p->ny + b->rows - 1) / b->rows > (long long)kItemsPerSlot)
     return fail(LESBGK_EINVAL, "ny %d too large for the batch work list", p->ny);
   int slot = -1;

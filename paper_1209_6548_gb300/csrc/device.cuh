@@ -412,6 +412,69 @@ __device__ __forceinline__ void wall_fix(float (&O)[Q], int side, const TT &T, c
   }
 }
 
+// Diffuse wall at rest normal to x (columns i = 0 and nx-1; side 0 = left,
+// inward normal +x): the rule of wall_fix with c_x in place of c_y, tables
+// wSx, wSxdev, wAx, wBx of S(T_wx, u = 0).
+template <int NR, int Q, class TT, class TW>
+__device__ __forceinline__ void wall_fix_x(float (&O)[Q], int side, const TT &T, const TW &W) {
+  constexpr int H = NR / 2;
+  float s = 0.0f;
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const int ix = (a / NR) % NR;
+    const bool incoming = side == 0 ? (ix < H) : (ix >= H);
+    if (incoming) s = fmaf(fabsf(T.c[ix]), O[a], s);
+  }
+  const float rw1 = (s - W.wAx[side]) * W.wBx[side];  // rho_W - 1
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const int ix = (a / NR) % NR;
+    const bool outgoing = side == 0 ? (ix >= H) : (ix < H);
+    if (outgoing) O[a] = fmaf(rw1, W.wSx[side][a], W.wSxdev[side][a]);
+  }
+}
+
+// Corner node on the x-wall xside and the y-wall yside (a reading: the paper
+// has no corners).  Kept: the populations arriving towards both walls
+// (c.n_x < 0 and c.n_y < 0, inward normals); all others are re-emitted as
+// rho_W S(T_wx, u = 0) of the side wall, with rho_W from zero net mass flux
+// along n = n_x + n_y: rho_W - 1 = (sum_kept |c.n| df - wAc) wBc.
+template <int NR, int Q, class TT, class TW>
+__device__ __forceinline__ void wall_corner(float (&O)[Q], int xside, int yside, const TT &T, const TW &W) {
+  constexpr int H = NR / 2;
+  const int k = yside * 2 + xside;
+  const float nx = xside == 0 ? 1.0f : -1.0f, ny = yside == 0 ? 1.0f : -1.0f;
+  float s = 0.0f;
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const int ix = (a / NR) % NR, iy = a % NR;
+    const bool kept = (xside == 0 ? ix < H : ix >= H) && (yside == 0 ? iy < H : iy >= H);
+    if (kept) s = fmaf(fabsf(fmaf(T.c[ix], nx, T.c[iy] * ny)), O[a], s);
+  }
+  const float rw1 = (s - W.wAc[k]) * W.wBc[k];
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const int ix = (a / NR) % NR, iy = a % NR;
+    const bool kept = (xside == 0 ? ix < H : ix >= H) && (yside == 0 ? iy < H : iy >= H);
+    if (!kept) O[a] = fmaf(rw1, W.wSx[xside][a], W.wSxdev[xside][a]);
+  }
+}
+
+// The walls of one node.  WM = 0: y-walls (fully diffuse) if any; 1: y-walls
+// with a specular share; 2: walls in x as well (cavity; y-walls diffuse).
+template <int NR, int WM, int Q, class TA>
+__device__ __forceinline__ void apply_walls_node(float (&O)[Q], int i, int j, const TA &A) {
+  const bool yw = A.walls && (j == 0 || j == A.ny - 1);
+  if constexpr (WM == 2) {
+    const bool xw = i == 0 || i == A.nx - 1;
+    if (xw && yw) wall_corner<NR>(O, i == 0 ? 0 : 1, j == 0 ? 0 : 1, A, A);
+    else if (xw) wall_fix_x<NR>(O, i == 0 ? 0 : 1, A, A);
+    else if (yw) wall_fix<NR, false>(O, j == 0 ? 0 : 1, A, A);
+  } else {
+    if (yw) wall_fix<NR, WM == 1>(O, j == 0 ? 0 : 1, A, A);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Internal population layout in HBM ("grouped").  The Q populations of a node
 // are put in slot order: first the Q/2 with c_y < 0, then the Q/2 with

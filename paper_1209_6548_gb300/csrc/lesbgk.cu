@@ -44,7 +44,7 @@ constexpr int kMomBlock = 256;
 // ---------------------------------------------------------------------------
 // The fused time step (Sec. 3.1 + Sec. 3.2).
 // ---------------------------------------------------------------------------
-template <int NR, int N, bool SPLIT, int RING, class S, bool SPEC, int NZ = 1>
+template <int NR, int N, bool SPLIT, int RING, class S, int WM, int NZ = 1>
 __global__ void __launch_bounds__(kBlock) k_step(const S *__restrict__ fin, S *__restrict__ fout,
                                                  const KArgs A) {
   using Lay = Layout<NR, S, NZ>;
@@ -58,8 +58,13 @@ __global__ void __launch_bounds__(kBlock) k_step(const S *__restrict__ fin, S *_
   if (seg >= A.nseg) return;  // uniform over the warp
   const int nx = A.nx, ny = A.ny;
   const int xl = strip * U - HL + lane;  // this lane's node, unwrapped
-  int xw = xl % nx;
-  if (xw < 0) xw += nx;
+  int xw;
+  if constexpr (WM == 2) {
+    xw = min(max(xl, 0), nx - 1);  // walls in x: ghost columns hold the wall node
+  } else {
+    xw = xl % nx;
+    if (xw < 0) xw += nx;
+  }
   const bool writer = lane >= HL && lane < 32 - HL && xl < nx;
   const int y0 = seg * A.rows;
   const int y1 = min(y0 + A.rows, ny);
@@ -184,11 +189,9 @@ __global__ void __launch_bounds__(kBlock) k_step(const S *__restrict__ fin, S *_
       acc[a] = fmaf(-ax, diff, acc[a]);
     }
 
-    if (A.walls && (j == 0 || j == ny - 1)) {
-      // the Maxwell wall (specular share) is a separate instantiation so that
-      // the hot loop of everything else keeps its code
-      wall_fix<NR, SPEC>(acc, (j == 0) ? 0 : 1, A, A);
-    }
+    // the Maxwell wall (specular share) and walls in x are separate
+    // instantiations so that the hot loop of everything else keeps its code
+    apply_walls_node<NR, WM>(acc, xw, j, A);
 
     if (writer) {
       S *o = fout + (long long)j * rstride + (long long)xw * V;
@@ -237,11 +240,10 @@ __global__ void __launch_bounds__(kBlock) k_init(const double *__restrict__ fiel
       d[0][0][0] = drho;
       hermite_evaluate3<NR, N>(d, Sv, A);
     }
-    const int j = (int)(c / A.nx);
-    if (A.walls && (j == 0 || j == A.ny - 1)) {
-      if (A.wspec != 0.0f) wall_fix<NR, true>(Sv, j == 0 ? 0 : 1, A, A);
-      else wall_fix<NR, false>(Sv, j == 0 ? 0 : 1, A, A);
-    }
+    const int j = (int)(c / A.nx), i = (int)(c - (long long)j * A.nx);
+    if (A.xwalls) apply_walls_node<NR, 2>(Sv, i, j, A);
+    else if (A.wspec != 0.0f) apply_walls_node<NR, 1>(Sv, i, j, A);
+    else apply_walls_node<NR, 0>(Sv, i, j, A);
 #pragma unroll
     for (int g = 0; g < Lay::G; ++g) st_group_s<NR, S>(f + c * Lay::V, gstride, g, Sv, A);
   }
@@ -537,18 +539,16 @@ cudaError_t allow_smem(const lesbgk *h) {
     constexpr int NR = decltype(r)::value, N = decltype(n)::value, NZ = decltype(z)::value;
     using S = decltype(st);
     constexpr int smem = (int)step_smem_bytes<NR, S, NZ>();
-    e = cudaFuncSetAttribute(k_step<NR, N, true, kRing, S, false, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_step<NR, N, false, kRing, S, false, NZ>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    auto allow = [&](auto kernel) {
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    };
+    allow(k_step<NR, N, true, kRing, S, 0, NZ>);
+    allow(k_step<NR, N, false, kRing, S, 0, NZ>);
     if constexpr (std::is_same<S, float>::value) {
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_step<NR, N, true, kRing, S, true, NZ>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_step<NR, N, false, kRing, S, true, NZ>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      allow(k_step<NR, N, true, kRing, S, 1, NZ>);
+      allow(k_step<NR, N, false, kRing, S, 1, NZ>);
+      allow(k_step<NR, N, true, kRing, S, 2, NZ>);
+      allow(k_step<NR, N, false, kRing, S, 2, NZ>);
     }
   });
   return e;
@@ -564,15 +564,20 @@ int launch_step(lesbgk *h, const void *fin, void *fout, cudaStream_t s) {
     const S *fi = static_cast<const S *>(fin);
     S *fo = static_cast<S *>(fout);
     const bool split = h->p.scheme == LESBGK_SPLIT;
-    if constexpr (std::is_same<S, float>::value) {
-      if (h->args.walls && h->args.wspec != 0.0f) {  // Maxwell walls: FP32 storage only (checked at set-up)
-        if (split) k_step<NR, N, true, kRing, S, true, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
-        else k_step<NR, N, false, kRing, S, true, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+    if constexpr (std::is_same<S, float>::value) {  // FP32 storage only (checked at set-up)
+      if (h->args.xwalls) {  // walls in x (cavity)
+        if (split) k_step<NR, N, true, kRing, S, 2, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+        else k_step<NR, N, false, kRing, S, 2, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+        return;
+      }
+      if (h->args.walls && h->args.wspec != 0.0f) {  // Maxwell walls
+        if (split) k_step<NR, N, true, kRing, S, 1, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+        else k_step<NR, N, false, kRing, S, 1, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
         return;
       }
     }
-    if (split) k_step<NR, N, true, kRing, S, false, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
-    else k_step<NR, N, false, kRing, S, false, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+    if (split) k_step<NR, N, true, kRing, S, 0, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+    else k_step<NR, N, false, kRing, S, 0, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
   });
   return 0;
 }

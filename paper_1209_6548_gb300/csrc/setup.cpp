@@ -45,6 +45,14 @@ int check_params(const lesbgk_params *p) {
   if (p->dim == 3 && (p->nroots != 4 || order != 3 || p->storage != LESBGK_F32))
     return fail(LESBGK_EINVAL, "D = 3 is built as D3Q64 (nroots 4, order 3) with FP32 storage");
   if (p->bc_y != LESBGK_PERIODIC && p->bc_y != LESBGK_DIFFUSE) return fail(LESBGK_EINVAL, "bad bc_y");
+  if (p->bc_x != LESBGK_PERIODIC && p->bc_x != LESBGK_DIFFUSE) return fail(LESBGK_EINVAL, "bad bc_x");
+  if (p->bc_x == LESBGK_DIFFUSE) {
+    if (p->nx < 2) return fail(LESBGK_EINVAL, "walls in x need nx >= 2");
+    if (p->storage != LESBGK_F32) return fail(LESBGK_EINVAL, "walls in x are built for FP32 storage");
+    if (p->wall_specular != 0.0) return fail(LESBGK_EINVAL, "walls in x are built with fully diffuse y-walls");
+    for (int s = 0; s < 2; ++s)
+      if (!(p->wall_Tx[s] > 0.0) || !std::isfinite(p->wall_Tx[s])) return fail(LESBGK_EINVAL, "wall_Tx must be > 0");
+  }
   if (p->bc_y == LESBGK_DIFFUSE && p->ny < 2) return fail(LESBGK_EINVAL, "walls need ny >= 2");
   if (p->storage != LESBGK_F32 && p->storage != LESBGK_F16 && p->storage != LESBGK_BF16)
     return fail(LESBGK_EINVAL, "storage must be LESBGK_F32, LESBGK_F16 or LESBGK_BF16");
@@ -81,18 +89,28 @@ int build_setup(const lesbgk_params &p, int order, const double *h_init, Setup *
   KArgs &A = h->args;
   std::memset(&A, 0, sizeof A);
   h->cmax = std::fabs(c[0]);
-  // spacing
-  if (p.bc_y == LESBGK_PERIODIC) {
+  // spacing: a walled axis spans [0, 1] with walls on its end nodes; a
+  // periodic axis of n nodes has 1/n, or the walled axis's spacing when only
+  // one axis has walls (square cells)
+  const bool xw = p.bc_x == LESBGK_DIFFUSE, yw = p.bc_y == LESBGK_DIFFUSE;
+  if (!xw && !yw) {
     h->dx = 1.0 / p.nx;
     h->dy = 1.0 / p.ny;
-  } else {
+  } else if (!xw) {
     h->dy = 1.0 / (p.ny - 1);
     h->dx = h->dy;
+  } else if (!yw) {
+    h->dx = 1.0 / (p.nx - 1);
+    h->dy = h->dx;
+  } else {
+    h->dx = 1.0 / (p.nx - 1);
+    h->dy = 1.0 / (p.ny - 1);
   }
   // reference state for tau_ref
   double tmax = 1.0, rmax = 1.0;
   if (p.bc_y == LESBGK_DIFFUSE)
     tmax = std::fmax(tmax, std::fmax(p.wall_T[0], p.wall_T[1]) + std::fabs(p.wall_T_amp));
+  if (p.bc_x == LESBGK_DIFFUSE) tmax = std::fmax(tmax, std::fmax(p.wall_Tx[0], p.wall_Tx[1]));
   if (h_init) {
     const size_t cells = (size_t)p.nx * p.ny;
     double r0 = h_init[0];
@@ -166,8 +184,73 @@ int build_setup(const lesbgk_params &p, int order, const double *h_init, Setup *
   }
   h->wall_T_amp = p.wall_T_amp;
   h->wall_T_freq = p.wall_T_freq;
+  h->wall_Tx[0] = p.wall_Tx[0];
+  h->wall_Tx[1] = p.wall_Tx[1];
   set_wall_time(*h, 0.0, &h->args);
+  A.xwalls = xw ? 1 : 0;
+  if (xw) x_wall_tables(*h, &h->args);
   return 0;
+}
+
+// Walls at rest normal to x and the cavity corners: S(T_wx, u = 0) per stored
+// population in FP64, the x-wall constants (|c_x| over the outgoing half) and
+// the corner constants (|c.n_x + c.n_y| over the kept populations).
+void x_wall_tables(const Setup &h, KArgs *out) {
+  using namespace lesbgk_tables;
+  KArgs &A = *out;
+  const int nr = h.nroots, N = h.order, H = nr / 2;
+  const double *c = h.c, *w = h.w;
+  const double fact[kMaxOrder + 1] = {1, 1, 2, 6, 24};
+  const int nz = h.dim == 3 ? H : 1;
+  for (int s = 0; s < 2; ++s) {
+    double e[kMaxOrder + 1][kMaxOrder + 1];
+    const double th = h.wall_Tx[s] - 1.0;
+    gaussian_hermite_moments(N, 1.0, 0.0, 0.0, th, 0.0, th, e);
+    const double zf[kMaxOrder + 1] = {1.0, 0.0, th, 0.0, 3.0 * th * th};
+    double S[kMaxQ];
+    double A_out = 0.0, Z_out = 0.0;
+    for (int iz = 0; iz < nz; ++iz)
+      for (int ix = 0; ix < nr; ++ix)
+        for (int iy = 0; iy < nr; ++iy) {
+          double hx[kMaxOrder + 1], hy[kMaxOrder + 1], hz[kMaxOrder + 1];
+          hermite_values(kMaxOrder, c[ix], hx);
+          hermite_values(kMaxOrder, c[iy], hy);
+          hermite_values(kMaxOrder, h.dim == 3 ? c[H + iz] : 0.0, hz);
+          double sum = 0.0;
+          for (int m = 0; m <= N; ++m)
+            for (int k = 0; m + k <= N; ++k)
+              for (int l = 0; m + k + l <= N && (l == 0 || h.dim == 3); l += 2)
+                sum += e[m][k] * zf[l] * hx[m] * hy[k] * hz[l] / (fact[m] * fact[k] * fact[l]);
+          const double wa = w[ix] * w[iy] * (h.dim == 3 ? w[H + iz] : 1.0);
+          const int a = (iz * nr + ix) * nr + iy;
+          S[a] = wa * sum;
+          A.wSx[s][a] = (float)S[a];
+          A.wSxdev[s][a] = (float)(S[a] - wa);
+          const bool outgoing = s == 0 ? (c[ix] > 0.0) : (c[ix] < 0.0);
+          if (outgoing) {
+            A_out += std::fabs(c[ix]) * (S[a] - wa);
+            Z_out += std::fabs(c[ix]) * S[a];
+          }
+        }
+    A.wAx[s] = (float)A_out;
+    A.wBx[s] = (float)(1.0 / Z_out);
+    for (int ys = 0; ys < 2; ++ys) {  // the two corners on this x-wall
+      const double nx = s == 0 ? 1.0 : -1.0, ny = ys == 0 ? 1.0 : -1.0;
+      double Ac = 0.0, Zc = 0.0;
+      for (int iz = 0; iz < nz; ++iz)
+        for (int ix = 0; ix < nr; ++ix)
+          for (int iy = 0; iy < nr; ++iy) {
+            if (!(c[ix] * nx < 0.0 && c[iy] * ny < 0.0)) continue;
+            const int a = (iz * nr + ix) * nr + iy;
+            const double wa = w[ix] * w[iy] * (h.dim == 3 ? w[H + iz] : 1.0);
+            const double cn = std::fabs(c[ix] * nx + c[iy] * ny);
+            Ac += cn * (S[a] - wa);
+            Zc += cn * S[a];
+          }
+      A.wAc[ys * 2 + s] = (float)Ac;
+      A.wBc[ys * 2 + s] = (float)(1.0 / Zc);
+    }
+  }
 }
 
 void set_wall_time(const Setup &h, double t, KArgs *out) {

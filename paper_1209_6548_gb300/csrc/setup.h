@@ -33,6 +33,11 @@ struct KArgs {
   long long plane;             // nx*ny
   unsigned seed;               // per-launch key of the 16-bit stochastic rounding
   float wspec;                 // specular fraction 1 - gamma of the Maxwell wall (0: fully diffuse)
+  int xwalls;                  // diffuse walls at rest on columns 0 and nx-1
+  float wSx[2][kMaxQ];         // x-wall equilibrium S(T_wx, 0), [0] left, [1] right
+  float wSxdev[2][kMaxQ];      // S - w
+  float wAx[2], wBx[2];        // as wA, wB with |c_x| over the outgoing half
+  float wAc[4], wBc[4];        // corners [yside * 2 + xside]: sum_kept |c.n|(S-w), 1/sum_kept |c.n| S
 };
 
 // What one solve's set-up produces.
@@ -44,6 +49,7 @@ struct Setup {
   double c[kMaxR], w[kMaxR];       // FP64 quadrature
   double wall_T[2], wall_ux[2];    // steady wall temperature and velocity
   double wall_T_amp, wall_T_freq;  // T_w(t) = wall_T + wall_T_amp sin(wall_T_freq t)
+  double wall_Tx[2];               // x-wall temperatures (walls in x are steady and at rest)
 };
 
 // Record a message for lesbgk_last_error() and return code.
@@ -63,6 +69,10 @@ int build_setup(const lesbgk_params &p, int order, const double *h_init, Setup *
 // Build the wall tables (wS, wSdev, wA, wB) of *A in FP64 for the wall
 // temperature at time t; build_setup calls it for args with t = 0.
 void set_wall_time(const Setup &h, double t, KArgs *A);
+
+// Tables of the walls normal to x and of the corners (steady; build_setup
+// calls it when bc_x has walls).
+void x_wall_tables(const Setup &h, KArgs *A);
 
 // Whether the wall temperature varies in time (the tables then change per step).
 inline bool heated_walls(const Setup &h) { return h.args.walls && h.wall_T_amp != 0.0; }

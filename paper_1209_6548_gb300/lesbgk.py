@@ -45,7 +45,7 @@ class Params(C.Structure):
         ("cfl", C.c_double), ("dt", C.c_double),
         ("wall_T", C.c_double * 2), ("wall_ux", C.c_double * 2), ("g", C.c_double * 2),
         ("wall_specular", C.c_double), ("wall_T_amp", C.c_double), ("wall_T_freq", C.c_double),
-        ("dim", C.c_int32),
+        ("dim", C.c_int32), ("bc_x", C.c_int32), ("wall_Tx", C.c_double * 2),
     ]
 
 
@@ -122,7 +122,8 @@ def _check(rc: int) -> None:
 
 def make_params(*, nroots=4, order=0, nx, ny, bc_y=DIFFUSE, kn, b, visc_exp=0.5, cfl=0.5, dt=0.0,
                 wall_T=(1.0, 1.0), wall_ux=(0.0, 0.0), g=(0.0, 0.0), storage=F32, scheme=UNSPLIT,
-                wall_specular=0.0, wall_T_amp=0.0, wall_T_freq=0.0, dim=2) -> Params:
+                wall_specular=0.0, wall_T_amp=0.0, wall_T_freq=0.0, dim=2, bc_x=PERIODIC,
+                wall_Tx=(1.0, 1.0)) -> Params:
     p = Params()
     p.struct_size = C.sizeof(Params)
     p.nroots, p.order, p.nx, p.ny, p.bc_y, p.storage = nroots, order, nx, ny, bc_y, storage
@@ -133,6 +134,8 @@ def make_params(*, nroots=4, order=0, nx, ny, bc_y=DIFFUSE, kn, b, visc_exp=0.5,
     p.g[0], p.g[1] = g
     p.wall_specular, p.wall_T_amp, p.wall_T_freq = wall_specular, wall_T_amp, wall_T_freq
     p.dim = dim
+    p.bc_x = bc_x
+    p.wall_Tx[0], p.wall_Tx[1] = wall_Tx
     return p
 
 
@@ -147,7 +150,8 @@ def params_from_problem(prob, dt: float = 0.0) -> Params:
                        kn=prob.kn, b=prob.b, visc_exp=prob.visc_exp, cfl=prob.cfl, dt=dt,
                        wall_T=tuple(prob.wall_T), wall_ux=tuple(prob.wall_ux), g=tuple(prob.g),
                        scheme=prob.scheme, wall_specular=prob.wall_specular, wall_T_amp=prob.wall_T_amp,
-                       wall_T_freq=prob.wall_T_freq, dim=getattr(prob, "dim", 2))
+                       wall_T_freq=prob.wall_T_freq, dim=getattr(prob, "dim", 2),
+                       bc_x=getattr(prob, "bc_x", PERIODIC), wall_Tx=tuple(getattr(prob, "wall_Tx", (1.0, 1.0))))
 
 
 def workspace_size(p: Params) -> int:

@@ -63,6 +63,11 @@ def test_struct_sizes_match_header(lib):
     (dict(dim=3, nroots=6), L.EINVAL),                    # D = 3 is built as D3Q64
     (dict(dim=3, order=4), L.EINVAL),
     (dict(dim=3, storage=L.F16), L.EINVAL),
+    (dict(bc_x=2), L.EINVAL),
+    (dict(bc_x=L.DIFFUSE, nx=1), L.EINVAL),              # walls in x need two columns
+    (dict(bc_x=L.DIFFUSE, storage=L.BF16), L.EINVAL),
+    (dict(bc_x=L.DIFFUSE, wall_specular=0.2), L.EINVAL),
+    (dict(bc_x=L.DIFFUSE, wall_Tx=(1.0, 0.0)), L.EINVAL),
 ])
 def test_invalid_arguments_rejected(lib, kw, code):
     base = dict(nx=4, ny=8, kn=0.1, b=0.0, bc_y=L.DIFFUSE)

@@ -455,3 +455,42 @@ def test_high_mach_workloads(kind, nroots, dim):
     for n, g, r, *_ in res:
         assert_fields_close(g, r, what=f"{prob.name} D={dim} step {n}")
     assert np.max(np.abs(res[-1][2][1])) > 0.1  # a high-speed flow did develop
+
+
+# ---------------------------------------------------------------- walls in x (cavity)
+@pytest.mark.parametrize("nroots,dim", [(4, 2), (6, 2), (4, 3)])
+def test_lid_driven_cavity(nroots, dim):
+    """Lid-driven cavity (walls on all sides, corners, lid at 0.05), split
+    scheme, on a grid that spans two warp strips with a ragged tail."""
+    from dataclasses import replace
+    prob = replace(I.lid_driven_cavity(n=45, u_lid=0.05, kn=0.1), nroots=nroots, dim=dim, ny=37)
+    res, *_ = run_pair(prob, None, [1, 10, 200])
+    for n, g, r, *_ in res:
+        assert_fields_close(g, r, what=f"cavity nroots={nroots} D={dim} step {n}")
+    assert np.max(np.abs(res[-1][2][2])) > 1e-3  # the lid set up a vortex
+
+
+@pytest.mark.parametrize("scheme", [I.UNSPLIT, I.SPLIT])
+def test_walls_in_x_rough(scheme):
+    """Rough fields in a box with heated walls on all sides and a lid, and in
+    a channel walled in x only (periodic y); populations element by element."""
+    for prob in (I.Problem(name="box", nx=60, ny=33, bc_y=I.DIFFUSE, bc_x=I.DIFFUSE, kn=0.1, b=0.5,
+                           wall_ux=(0.0, 0.05), wall_T=(0.98, 1.02), wall_Tx=(1.03, 0.97), scheme=scheme),
+                 I.Problem(name="xchan", nx=29, ny=30, bc_y=I.PERIODIC, bc_x=I.DIFFUSE, kn=0.05, b=-0.5,
+                           wall_Tx=(0.97, 1.04), g=(0.0, 1e-3), scheme=scheme)):
+        fields = I.random_fields(prob, seed=prob.nx + 3, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
+        res, *_ = run_pair(prob, fields, [1, 10])
+        for n, g, r, gp, fp in res:
+            assert_fields_close(g, r, what=f"{prob.name} step {n}")
+            w = O.velocity_set(4)[2][:, None, None]
+            err = np.max(np.abs(gp - (fp - w)))
+            assert err <= 2e-6 * np.max(np.abs(fp - w)), f"{prob.name} populations {err:.3e}"
+
+
+def test_cavity_of_two_by_two_is_all_corners():
+    prob = I.Problem(name="tiny", nx=2, ny=2, bc_y=I.DIFFUSE, bc_x=I.DIFFUSE, kn=0.1, b=0.0,
+                     wall_T=(1.0, 1.0), wall_Tx=(1.02, 0.99))
+    fields = I.random_fields(prob, seed=2, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
+    res, *_ = run_pair(prob, fields, [1, 5])
+    for n, g, r, *_ in res:
+        assert_fields_close(g, r, what=f"2x2 step {n}")
