@@ -473,10 +473,13 @@ namespace {
 int pick_launch(lesbgk *h) {
   const int nx = h->p.nx, ny = h->p.ny;
   // one node per lane, 28 nodes per strip (two halo lanes per side); default
-  // 32-row segments (measured best on the 4096^2 periodic case)
+  // segments of 32 rows (D2Q16, D3Q64) or 128 rows (D2Q36): measured best on
+  // the 4096^2 periodic case (D2Q36: 961 us per step at 128 rows, 988 us at
+  // 32, where the three prologue rows per segment weigh more)
   h->cpt = 1;
   const int nstrips = (nx + 27) / 28;
-  if (h->rows <= 0) h->rows = ny < 32 ? ny : 32;
+  const int rows_default = h->q == 36 ? 128 : 32;
+  if (h->rows <= 0) h->rows = ny < rows_default ? ny : rows_default;
   h->args.rows = h->rows;
   h->args.nstrips = nstrips;
   h->args.nseg = (ny + h->rows - 1) / h->rows;
