@@ -18,6 +18,13 @@ gas next to them, the diffuse-wall rule exchanges a small, constant amount of
 mass per step (the FP64 oracle shows the same), so such solves approach a
 constant drift rather than a fixed point.
 
+Solves that the batch cannot hold (another width, walls in x such as the
+lid-driven cavities of the mix, the D = 3 set, Maxwell or heated walls) go
+to a wide lane: each runs as a single-domain solver on its own CUDA stream,
+so they advance concurrently with the batch; the lane admits them in arrival
+order while its own device-memory budget has room, and checks them with the
+same residual and criterion (computed from lesbgk_moments fields).
+
 Everything on the device runs in the library's kernels; this module is the
 scheduler (host bookkeeping only).
 """
@@ -76,36 +83,117 @@ def poisson_trace(n: int, rate: float, problems, seed: int = 0):
     return [Request(rid=k, arrival=float(t[k]), problem=problems[k % len(problems)]) for k in range(n)]
 
 
-def serving_mix(n: int, seed: int = 0, q36_share: float = 0.2, ny_hi: int = 512):
+def serving_mix(n: int, seed: int = 0, q36_share: float = 0.2, ny_hi: int = 512, cavity_share: float = 0.0,
+                cavity_n: int = 256):
     """The channel mix of the batched benchmark (nx = 4, Couette / Fourier /
     Poiseuille, Kn log-uniform 0.01-0.5, b in {-1/2, 0, 1/2}) with ny
-    log-uniform 16..ny_hi, and a share of the requests on D2Q36 (order 4)."""
+    log-uniform 16..ny_hi, a share of the requests on D2Q36 (order 4), and a
+    share of lid-driven cavities (cavity_n^2, lid 0.05, Kn log-uniform
+    0.05-0.5, D2Q16, split scheme)."""
     from dataclasses import replace
     probs = I.batch_mix(n=n, seed=seed, ny_hi=ny_hi)
     rng = np.random.default_rng(seed + 1)
     pick = rng.random(n) < q36_share
-    return [replace(p, nroots=6) if q else p for p, q in zip(probs, pick)]
+    out = [replace(p, nroots=6) if q else p for p, q in zip(probs, pick)]
+    rng2 = np.random.default_rng(seed + 2)
+    cav = rng2.random(n) < cavity_share
+    kn = np.exp(rng2.uniform(np.log(0.05), np.log(0.5), size=n))
+    for k in np.flatnonzero(cav):
+        out[k] = replace(I.lid_driven_cavity(n=cavity_n, u_lid=0.05, kn=float(kn[k]), b=out[k].b),
+                         name=f"cavity{k}")
+    return out
+
+
+def fits_batch(prob, nx: int) -> bool:
+    """Whether the batched solver takes this problem (the library's own
+    admission checks say the same)."""
+    return (prob.nx == nx and getattr(prob, "bc_x", I.PERIODIC) == I.PERIODIC and getattr(prob, "dim", 2) == 2
+            and prob.wall_specular == 0.0 and prob.wall_T_amp == 0.0)
+
+
+class WideLane:
+    """Single-domain solvers, one CUDA stream each, for the solves the batch
+    cannot hold; admission while the summed workspaces fit budget_bytes."""
+
+    def __init__(self, budget_bytes: int, max_solvers: int = 16):
+        import torch
+        self._torch = torch
+        self.budget = budget_bytes
+        self.max_solvers = max_solvers
+        self.used = 0
+        self.active = {}  # key -> (request, solver, stream, previous fields, residual history)
+        self._next = 0
+
+    def try_admit(self, req) -> bool:
+        p = L.params_from_problem(req.problem)
+        need = L.workspace_size(p)
+        if self.used + need > self.budget or len(self.active) >= self.max_solvers:
+            return False
+        st = self._torch.cuda.Stream()
+        with self._torch.cuda.stream(st):  # the solver's allocations belong to its stream
+            s = L.Solver(p, stream=st)
+            prev = s.moments()[[0, 1, 2, 3]].clone()
+        self.used += need
+        self.active[self._next] = (req, s, st, prev, [])
+        self._next += 1
+        return True
+
+    def step(self, n: int) -> None:
+        for _, s, _, _, _ in self.active.values():
+            s.step(n)  # asynchronous on the solver's own stream
+
+    def residuals(self, n: int):
+        """key -> residual over the last n steps (max over nodes of
+        |d rho| + |d u| + |d T|, per unit time), as lesbgk_batch_residuals."""
+        out = {}
+        for key, (req, s, st, prev, hist) in self.active.items():
+            with self._torch.cuda.stream(st):
+                cur = s.moments()[[0, 1, 2, 3]]
+                r = float((cur - prev).abs().sum(dim=0).max().item()) / (n * s.info.dt)
+                prev.copy_(cur)
+            hist.append(r)
+            out[key] = r
+        return out
+
+    def retire(self, key, keep_moments: bool) -> None:
+        req, s, st, prev, _ = self.active.pop(key)
+        if keep_moments:
+            with self._torch.cuda.stream(st):
+                req.moments = s.moments()
+        st.synchronize()  # nothing of this solve in flight before its memory is released
+        self.used -= s.nbytes
+        s.close()
 
 
 class ServingLoop:
     def __init__(self, capacity: int, pool_bytes: int, nx: int = 4, check_every: int = 256,
-                 conv: Convergence | None = None, keep_moments: bool = False, stream=None):
+                 conv: Convergence | None = None, keep_moments: bool = False, stream=None,
+                 wide_bytes: int | None = None, wide_solvers: int = 16):
+        self.nx = nx
         self.batch = L.Batch(capacity=capacity, nx=nx, pool_bytes=pool_bytes, stream=stream)
+        self.wide = WideLane(pool_bytes if wide_bytes is None else wide_bytes, wide_solvers)
         self.check_every = check_every
         self.conv = conv or Convergence()
         self.keep_moments = keep_moments
 
     def run(self, requests, clock=time.perf_counter):
-        bt = self.batch
+        bt, wide = self.batch, self.wide
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
-        waiting = collections.deque()
+        waiting = collections.deque()       # for the batch
+        waiting_wide = collections.deque()  # for the wide lane
         active = {}  # slot -> (request, residual history)
         t0 = clock()
         done = []
-        while pending or waiting or active:
+
+        def finish(req, v, r, now):
+            req.status, req.residual, req.completed = v, r, now
+            done.append(req)
+
+        while pending or waiting or waiting_wide or active or wide.active:
             now = clock() - t0
             while pending and pending[0].arrival <= now:
-                waiting.append(pending.popleft())
+                req = pending.popleft()
+                (waiting if fits_batch(req.problem, self.nx) else waiting_wide).append(req)
             while waiting:  # FIFO admission while the pool has room
                 req = waiting[0]
                 slot = bt.try_add(L.params_from_problem(req.problem))
@@ -115,26 +203,43 @@ class ServingLoop:
                 req.admitted = clock() - t0
                 req.status = "running"
                 active[slot] = (req, [])
-            if not active:
+            while waiting_wide and wide.try_admit(waiting_wide[0]):
+                req = waiting_wide.popleft()
+                req.admitted = clock() - t0
+                req.status = "running"
+            if not active and not wide.active:
                 if pending:
                     time.sleep(max(0.0, min(pending[0].arrival - (clock() - t0), 0.01)))
                 continue
-            bt.step(self.check_every)
-            res = bt.residuals()
-            now = clock() - t0
-            for slot in list(active):
-                req, hist = active[slot]
-                req.steps = bt.info(slot).steps_done
-                hist.append(float(res[slot]))
-                v = self.conv.verdict([h for h in hist if np.isfinite(h)], req.steps)
-                if v is None:
-                    continue
-                req.status, req.residual, req.completed = v, hist[-1], now
-                if self.keep_moments:
-                    req.moments = bt.moments(slot)
-                bt.remove(slot)
-                del active[slot]
-                done.append(req)
+            if wide.active:
+                wide.step(self.check_every)  # their own streams: they run beside the batch
+            if active:
+                bt.step(self.check_every)
+                res = bt.residuals()
+                now = clock() - t0
+                for slot in list(active):
+                    req, hist = active[slot]
+                    req.steps = bt.info(slot).steps_done
+                    hist.append(float(res[slot]))
+                    v = self.conv.verdict([h for h in hist if np.isfinite(h)], req.steps)
+                    if v is None:
+                        continue
+                    if self.keep_moments:
+                        req.moments = bt.moments(slot)
+                    bt.remove(slot)
+                    del active[slot]
+                    finish(req, v, hist[-1], now)
+            if wide.active:
+                res = wide.residuals(self.check_every)
+                now = clock() - t0
+                for key in list(wide.active):
+                    req, s, _, _, hist = wide.active[key]
+                    req.steps = s.info.steps_done
+                    v = self.conv.verdict([h for h in hist if np.isfinite(h)], req.steps)
+                    if v is None:
+                        continue
+                    wide.retire(key, self.keep_moments)
+                    finish(req, v, res[key], now)
         return done
 
 

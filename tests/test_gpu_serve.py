@@ -41,3 +41,27 @@ def test_continuous_batching_small_trace():
         s.step(r.steps)
         alone = s.moments().cpu().numpy()
         assert np.array_equal(r.moments.cpu().numpy(), alone), r.rid
+
+
+def test_cavities_run_in_the_wide_lane_beside_the_batch():
+    """Lid-driven cavities (walls in x: not batchable) are served by the wide
+    lane concurrently with batched channels; each result equals the same
+    solve run alone for the same number of steps."""
+    probs = S.serving_mix(24, seed=5, ny_hi=64, cavity_share=0.25, cavity_n=40)
+    assert sum(not S.fits_batch(p, 4) for p in probs) >= 3
+    reqs = S.poisson_trace(24, 400.0, probs, seed=5)
+    one = max(L.batch_slot_bytes(L.params_from_problem(p)) for p in probs if S.fits_batch(p, 4))
+    wide_one = max(L.workspace_size(L.params_from_problem(p)) for p in probs if not S.fits_batch(p, 4))
+    loop = S.ServingLoop(capacity=8, pool_bytes=6 * one, check_every=128, keep_moments=True,
+                         conv=S.Convergence(rtol=1e-6, max_steps=60_000), wide_bytes=2 * wide_one)
+    done = loop.run(reqs)
+    assert len(done) == 24
+    assert all(r.status in ("converged", "plateau") for r in done), [r.status for r in done]
+    cav = [r for r in done if not S.fits_batch(r.problem, 4)]
+    for r in cav:
+        s = L.Solver(L.params_from_problem(r.problem))
+        s.step(r.steps)
+        assert np.array_equal(r.moments.cpu().numpy(), s.moments().cpu().numpy()), r.rid
+    # at most two cavities at a time (the lane's budget): some cavity waited for another to finish
+    first_done = min(r.completed for r in cav)
+    assert len(cav) <= 2 or any(r.admitted >= first_done for r in cav)

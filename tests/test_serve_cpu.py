@@ -31,3 +31,12 @@ def test_serving_mix_share():
     share = np.mean([p.nroots == 6 for p in probs])
     assert 0.15 < share < 0.25
     assert all(p.nx == 4 and 16 <= p.ny <= 512 for p in probs)
+
+
+def test_serving_mix_cavities_go_to_the_wide_lane():
+    probs = S.serving_mix(1000, seed=0, q36_share=0.2, cavity_share=0.1, cavity_n=256)
+    cav = [p for p in probs if p.bc_x == 1]
+    assert 70 <= len(cav) <= 130
+    assert all(p.nx == p.ny == 256 and p.wall_ux == (0.0, 0.05) and 0.05 <= p.kn <= 0.5 for p in cav)
+    assert all(not S.fits_batch(p, 4) for p in cav)
+    assert all(S.fits_batch(p, 4) for p in probs if p.bc_x == 0)
