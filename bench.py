@@ -375,7 +375,7 @@ def run_serve(args, world, rank, local):
     """Serving: a seeded Poisson stream (args.rate per second) of channel solves
     (the batched mix with ny 16-512 and 20% on D2Q36) and 10% lid-driven
     256^2 cavities (served beside the batch by the wide lane), each run to steady state
-    (residual below 1e-6, or a residual that has stopped changing); admission
+    (residual below 1e-8, or a residual that has stopped changing); admission
     by a fixed device-memory pool.  Reports p50/p99 latency (completion minus
     arrival), solves/s and offered vs achieved load, against the plain solver
     serving the same trace one request at a time (FIFO)."""
@@ -414,7 +414,7 @@ def run_serve(args, world, rank, local):
                    "rate_per_s": args.rate, "pool_mb": args.pool_mb, "check_every": loop.check_every,
                    "mix": "nx 4, ny 16-512, Couette/Fourier/Poiseuille, Kn 0.01-0.5, 20% D2Q36; "
                           "10% lid-driven cavities 256^2 (lid 0.05, Kn 0.05-0.5) in the wide lane",
-                   "convergence": "r < 1e-6 or r flat within 2% over 4 checks (cap 400k steps)"},
+                   "convergence": "r < 1e-8 or r flat within 2% over 4 checks (cap 400k steps)"},
         "latency": {"p50_s": served.get("p50_s"), "p99_s": served.get("p99_s"), "mean_s": served.get("mean_s")},
         "offered_per_s": args.rate, "achieved_per_s": served.get("solves_per_s"), "status": served.get("status"),
         "wall_s": wall,

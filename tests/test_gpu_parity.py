@@ -494,3 +494,23 @@ def test_cavity_of_two_by_two_is_all_corners():
     res, *_ = run_pair(prob, fields, [1, 5])
     for n, g, r, *_ in res:
         assert_fields_close(g, r, what=f"2x2 step {n}")
+
+
+# ---------------------------------------------------------------- failure path
+def test_diverged_solve_is_reported():
+    """The printed (unsplit) update is unstable for flows varying in x and y
+    (the oracle pins it); the Taylor-Green vortex then blows up in FP32 too,
+    and lesbgk_moments with totals reports LESBGK_EDIVERGED instead of
+    returning non-finite sums.  (A data failure, not a GPU fault.)"""
+    prob = I.Problem(name="tgv_unsplit", nx=64, ny=64, bc_y=I.PERIODIC, kn=0.05, b=-0.5, init="tgv", scheme=I.UNSPLIT)
+    s = gpu_solver(prob, time_step(prob, I.initial_fields(prob)), I.initial_fields(prob))
+    for _ in range(200):
+        s.step(100)
+        m = s.moments()
+        if not bool(m.isfinite().all()):
+            break
+    else:
+        pytest.fail("the unsplit 2D update did not diverge")
+    with pytest.raises(L.LesbgkError) as e:
+        s.moments(sums=True)
+    assert e.value.code == L.EDIVERGED
