@@ -62,11 +62,12 @@ extern "C" {
 /* Population storage (compute is always FP32).  LESBGK_F32 stores the
  * deviation f_a - w_a; LESBGK_F16 and LESBGK_BF16 store the relative deviation
  * (f_a - w_a)/w_a (times 2^10 in FP16, to stay in its normal range), halving
- * the bytes per lattice update.  Each step's stores
- * round stochastically (8 random bits from a counter-based hash of the step,
- * the row and the population -- not the column, so a flow uniform in x stays
- * uniform -- hence reproducible and independent of the launch shape); initial
- * and set populations round to nearest.  16-bit storage is
+ * the bytes per lattice update.  Each step's stores round stochastically
+ * (the hardware's unbiased stochastic rounding, fed random words from a
+ * counter-based hash of the step, the row and the population group -- not the
+ * column, so a flow uniform in x stays uniform -- hence reproducible and
+ * independent of the launch shape); initial and set populations round to
+ * nearest.  16-bit storage is
  * built for the default orders (D2Q16 N = 3, D2Q36 N = 4). */
 #define LESBGK_F32 0
 #define LESBGK_F16 1

@@ -500,11 +500,12 @@ struct Store<__half> {
   static constexpr bool kScaled = true;
   __device__ static float get(__half v, float w) { return __half2float(v) * w; }
   __device__ static __half put(float x, float iw) { return __float2half_rn(x * iw); }
-  // stochastic rounding: 8 random bits added just below the 10 kept mantissa
-  // bits, then truncation (FP32 has 13 more mantissa bits than FP16)
-  __device__ static __half put_sr(float x, float iw, unsigned r8) {
-    const unsigned u = __float_as_uint(x * iw) + (r8 << 5);
-    return __float2half_rz(__uint_as_float(u));
+  // two values packed (x0 low, x1 high), stochastically rounded by the
+  // hardware (cvt.rs): rbits supplies the random bits of both
+  __device__ static unsigned put_sr2(float x0, float x1, unsigned rbits) {
+    unsigned d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(x1), "f"(x0), "r"(rbits));
+    return d;
   }
 };
 template <>
@@ -512,10 +513,10 @@ struct Store<__nv_bfloat16> {
   static constexpr bool kScaled = true;
   __device__ static float get(__nv_bfloat16 v, float w) { return __bfloat162float(v) * w; }
   __device__ static __nv_bfloat16 put(float x, float iw) { return __float2bfloat16_rn(x * iw); }
-  // stochastic rounding: 8 random bits just below the 7 kept mantissa bits
-  __device__ static __nv_bfloat16 put_sr(float x, float iw, unsigned r8) {
-    const unsigned u = __float_as_uint(x * iw) + (r8 << 8);
-    return __float2bfloat16_rz(__uint_as_float(u));
+  __device__ static unsigned put_sr2(float x0, float x1, unsigned rbits) {
+    unsigned d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(x1), "f"(x0), "r"(rbits));
+    return d;
   }
 };
 
@@ -627,10 +628,12 @@ __device__ __forceinline__ void st_group_s(S *p, long long gstride, int g, const
   *reinterpret_cast<R *>(p + g * gstride) = raw;
 }
 
-// Store with stochastic rounding for the 16-bit types (FP32 stores as is): the
-// random bits of value k of group g are byte (k % 4) of
-// mix32(key ^ (g * 0x9e3779b9 + k / 4 * 0x85ebca6b)), so results depend only
-// on the key and the population, never on the launch shape.
+// Store with stochastic rounding for the 16-bit types (FP32 stores as is):
+// pairs of values go through the hardware's stochastic rounding (cvt.rs,
+// unbiased for both halves), fed one 32-bit random word per pair: the first
+// is mix32(key ^ g * 0x9e3779b9), each next one a multiply-add of the last
+// (each word is a bijection of a uniform seed, hence uniform).  Results depend
+// only on the key and the population, never on the launch shape.
 template <int NR, class S, int Q, class TT>
 __device__ __forceinline__ void st_group_sr(S *p, long long gstride, int g, const float (&F)[Q],
                                             const TT &Tt, unsigned key) {
@@ -638,15 +641,16 @@ __device__ __forceinline__ void st_group_sr(S *p, long long gstride, int g, cons
     st_group_s<NR, S>(p, gstride, g, F, Tt);
   } else {
     using L = LayoutQ<NR, S, Q>;
+    static_assert(L::V % 2 == 0, "16-bit groups hold pairs");
     using R = typename Raw<L::VB>::T;
     R raw;
-    S *e = reinterpret_cast<S *>(&raw);
-    unsigned bits = 0;
+    unsigned *w = reinterpret_cast<unsigned *>(&raw);
+    unsigned bits = mix32(key ^ ((unsigned)g * 0x9e3779b9u));
 #pragma unroll
-    for (int k = 0; k < L::V; ++k) {
-      if (k % 4 == 0) bits = mix32(key ^ ((unsigned)g * 0x9e3779b9u + (unsigned)(k / 4) * 0x85ebca6bu));
-      const int a = L::alpha(g * L::V + k);
-      e[k] = Store<S>::put_sr(F[a], Tt.iwq[a], (bits >> (8 * (k % 4))) & 0xffu);
+    for (int k = 0; k < L::V; k += 2) {
+      const int a0 = L::alpha(g * L::V + k), a1 = L::alpha(g * L::V + k + 1);
+      w[k / 2] = Store<S>::put_sr2(F[a0] * Tt.iwq[a0], F[a1] * Tt.iwq[a1], bits);
+      bits = bits * 0x9e3779b5u + 0x7f4a7c15u;
     }
     *reinterpret_cast<R *>(p + g * gstride) = raw;
   }
