@@ -119,10 +119,26 @@ def committed_traffic(source_digest: str, velocity_set: str = "d2q16", storage: 
         return None
 
 
+def _function_text(text: str, head: str) -> str:
+    """The source of the function whose definition starts with head (up to
+    its matching closing brace)."""
+    a = text.index(head)
+    depth, k = 0, text.index("{", a)
+    while True:
+        if text[k] == "{":
+            depth += 1
+        elif text[k] == "}":
+            depth -= 1
+            if depth == 0:
+                return text[a:k + 1]
+        k += 1
+
+
 def source_digest():
     """sha256 (16 hex digits) of the step kernel's source: device.cuh, the
-    k_step section of lesbgk.cu, its launch set-up (pick_launch .. launch_step)
-    and its block size; other kernels in the file do not change it."""
+    k_step section of lesbgk.cu, the functions that pick its launch shape and
+    launch it, and its block size and ring depth; other code in the file does
+    not change it."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1209_6548_gb300", "csrc")
     h = hashlib.sha256()
@@ -132,9 +148,10 @@ def source_digest():
         text = fh.read()
     a = text.index("// The fused time step")
     h.update(text[a:text.index("// Initial populations", a)].encode())
-    a = text.index("int pick_launch(")
-    h.update(text[a:text.index("unsigned grid_for(", a)].encode())
-    h.update("".join(ln for ln in text.splitlines(True) if ln.startswith("constexpr int kBlock ")).encode())
+    for head in ("int pick_launch(", "int launch_step("):
+        h.update(_function_text(text, head).encode())
+    h.update("".join(ln for ln in text.splitlines(True)
+                     if ln.startswith(("constexpr int kBlock ", "constexpr int kRing "))).encode())
     return h.hexdigest()[:16]
 
 

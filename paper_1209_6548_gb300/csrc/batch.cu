@@ -613,7 +613,9 @@ extern "C" int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const d
     }
   if (slot < 0) return fail(LESBGK_ESPACE, "all %d slots are in use", b->capacity);
   Setup su;
-  if (int rc = build_setup(*p, order, h_init, &su)) return rc;
+  FieldStats stats{1.0, 1.0, -1};
+  if (h_init) stats = field_stats_host(h_init, (size_t)p->nx * p->ny);  // small instances: a host loop
+  if (int rc = build_setup(*p, order, h_init ? &stats : nullptr, &su)) return rc;
   size_t off = 0;
   const size_t need = slot_bytes(*p);
   if (!b->pool.alloc(need, &off))

@@ -249,6 +249,36 @@ __global__ void __launch_bounds__(kBlock) k_init(const double *__restrict__ fiel
   }
 }
 
+// Largest density and temperature of initial fields double[4][cells] and the
+// first node that is not admissible (rho, T > 0, all four finite):
+// st[0], st[1] = bits of the maxima (non-negative doubles order like their
+// bits), st[2] = the node index (or all ones).  st set to {0, 0, ~0} before.
+__global__ void __launch_bounds__(kBlock) k_field_stats(const double *__restrict__ f, long long cells,
+                                                        unsigned long long *__restrict__ st) {
+  double rmax = 0.0, tmax = 0.0;
+  unsigned long long bad = ~0ull;
+  for (long long c = blockIdx.x * (long long)kBlock + threadIdx.x; c < cells; c += (long long)gridDim.x * kBlock) {
+    const double r = f[c], ux = f[cells + c], uy = f[2 * cells + c], T = f[3 * cells + c];
+    if (!(r > 0.0) || !(T > 0.0) || !isfinite(r) || !isfinite(T) || !isfinite(ux) || !isfinite(uy)) {
+      bad = min(bad, (unsigned long long)c);
+    } else {
+      rmax = fmax(rmax, r);
+      tmax = fmax(tmax, T);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rmax = fmax(rmax, __shfl_xor_sync(kFull, rmax, o));
+    tmax = fmax(tmax, __shfl_xor_sync(kFull, tmax, o));
+    bad = min(bad, __shfl_xor_sync(kFull, bad, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&st[0], (unsigned long long)__double_as_longlong(rmax));
+    atomicMax(&st[1], (unsigned long long)__double_as_longlong(tmax));
+    if (bad != ~0ull) atomicMin(&st[2], bad);
+  }
+}
+
 // Populations between the grouped layout and the public [a][j][i] layout.
 template <int NR, class S, int NZ = 1>
 __global__ void __launch_bounds__(kBlock) k_ungroup(const S *__restrict__ f, float *__restrict__ out,
@@ -486,9 +516,9 @@ int pick_launch(lesbgk *h) {
   return 0;
 }
 
-int build_tables(lesbgk *h, const double *h_init) {
+int build_tables(lesbgk *h, const FieldStats *stats) {
   Setup s;
-  if (int rc = build_setup(h->p, h->order, h_init, &s)) return rc;
+  if (int rc = build_setup(h->p, h->order, stats, &s)) return rc;
   h->args = s.args;
   h->su = s;
   h->dt = s.dt;
@@ -680,7 +710,36 @@ extern "C" int lesbgk_create(const lesbgk_params *p, void *d_workspace, size_t b
     delete h;
     return cuda_fail(e, "device query");
   }
-  if (int rc = build_tables(h, h_init)) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const double *dfields = nullptr;
+  FieldStats stats{1.0, 1.0, -1};
+  if (h_init) {
+    // fields to the device, then their check and maxima there (a host loop
+    // over 4 nx ny values would cost more than the copy)
+    const long long cells = (long long)p->nx * p->ny;
+    const size_t fb = (size_t)4 * cells * sizeof(double);
+    unsigned long long *st = reinterpret_cast<unsigned long long *>(h->sums);
+    unsigned long long hs[3] = {0, 0, 0};
+    e = cudaMemcpyAsync(h->buf[1], h_init, fb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, 2 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(st + 2, 0xff, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+      dfields = reinterpret_cast<const double *>(h->buf[1]);
+      k_field_stats<<<grid_for(h, cells), kBlock, 0, s>>>(dfields, cells, st);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs, st, sizeof hs, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // also: h_init may be freed after return
+    if (e != cudaSuccess) {
+      delete h;
+      return cuda_fail(e, "copy and check of initial fields");
+    }
+    double r, t;
+    std::memcpy(&r, &hs[0], sizeof r);
+    std::memcpy(&t, &hs[1], sizeof t);
+    stats = FieldStats{r, t, hs[2] == ~0ull ? -1 : (long long)hs[2]};
+  }
+  if (int rc = build_tables(h, h_init ? &stats : nullptr)) {
     delete h;
     return rc;
   }
@@ -690,20 +749,8 @@ extern "C" int lesbgk_create(const lesbgk_params *p, void *d_workspace, size_t b
     delete h;
     return cuda_fail(e, "step kernel shared-memory opt-in");
   }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const double *dfields = nullptr;
-  if (h_init) {
-    const size_t fb = (size_t)4 * p->nx * p->ny * sizeof(double);
-    e = cudaMemcpyAsync(h->buf[1], h_init, fb, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) {
-      delete h;
-      return cuda_fail(e, "copy of initial fields");
-    }
-    dfields = reinterpret_cast<const double *>(h->buf[1]);
-  }
-  launch_init(h, dfields, h->buf[0], s);
+  launch_init(h, dfields, h->buf[0], s);  // reads the device copy: no wait for the host
   e = cudaGetLastError();
-  if (e == cudaSuccess && h_init) e = cudaStreamSynchronize(s);  // h_init may be freed after return
   if (e != cudaSuccess) {
     delete h;
     return cuda_fail(e, "init kernel");

@@ -80,7 +80,22 @@ int check_params(const lesbgk_params *p) {
   return 0;
 }
 
-int build_setup(const lesbgk_params &p, int order, const double *h_init, Setup *out) {
+FieldStats field_stats_host(const double *h_init, size_t cells) {
+  FieldStats st{h_init[0], 0.0, -1};
+  for (size_t k = 0; k < cells; ++k) {
+    const double r = h_init[k], T = h_init[3 * cells + k];
+    if (!(r > 0.0) || !(T > 0.0) || !std::isfinite(r) || !std::isfinite(T) || !std::isfinite(h_init[cells + k]) ||
+        !std::isfinite(h_init[2 * cells + k])) {
+      st.bad_node = (long long)k;
+      return st;
+    }
+    st.rho_max = std::fmax(st.rho_max, r);
+    st.T_max = std::fmax(st.T_max, T);
+  }
+  return st;
+}
+
+int build_setup(const lesbgk_params &p, int order, const FieldStats *stats, Setup *out) {
   using namespace lesbgk_tables;
   Setup *h = out;
   const int nr = p.nroots, N = order;
@@ -111,18 +126,11 @@ int build_setup(const lesbgk_params &p, int order, const double *h_init, Setup *
   if (p.bc_y == LESBGK_DIFFUSE)
     tmax = std::fmax(tmax, std::fmax(p.wall_T[0], p.wall_T[1]) + std::fabs(p.wall_T_amp));
   if (p.bc_x == LESBGK_DIFFUSE) tmax = std::fmax(tmax, std::fmax(p.wall_Tx[0], p.wall_Tx[1]));
-  if (h_init) {
-    const size_t cells = (size_t)p.nx * p.ny;
-    double r0 = h_init[0];
-    for (size_t k = 0; k < cells; ++k) {
-      const double r = h_init[k], T = h_init[3 * cells + k];
-      if (!(r > 0.0) || !(T > 0.0) || !std::isfinite(r) || !std::isfinite(T) ||
-          !std::isfinite(h_init[cells + k]) || !std::isfinite(h_init[2 * cells + k]))
-        return fail(LESBGK_EINVAL, "initial field at node %zu not admissible (rho, T > 0, finite)", k);
-      r0 = std::fmax(r0, r);
-      tmax = std::fmax(tmax, T);
-    }
-    rmax = r0;
+  if (stats) {
+    if (stats->bad_node >= 0)
+      return fail(LESBGK_EINVAL, "initial field at node %lld not admissible (rho, T > 0, finite)", stats->bad_node);
+    rmax = stats->rho_max;
+    tmax = std::fmax(tmax, stats->T_max);
   }
   const double pr = 1.0 / (1.0 - p.b);
   h->tau_ref = (p.kn / pr) * std::pow(tmax, p.visc_exp - 1.0) / rmax;

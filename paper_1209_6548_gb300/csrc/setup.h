@@ -61,10 +61,21 @@ const char *last_error_buffer();
 int default_order(int nroots);
 int check_params(const lesbgk_params *p);
 
+// What the initial fields contribute to the set-up: their largest density and
+// temperature (tau_ref), and the first node that is not admissible (rho > 0,
+// T > 0, all four fields finite), or -1.
+struct FieldStats {
+  double rho_max, T_max;
+  long long bad_node;
+};
+
+// The same from host fields double[4][cells] (a plain loop).
+FieldStats field_stats_host(const double *h_init, size_t cells);
+
 // Quadrature, Hermite and wall tables in FP64 (rounded to FP32 in args),
 // spacing, tau_ref and dt (Sec. 2.2; the dt rule is the library's reading).
-// h_init (host, double[4][ny][nx], may be NULL) enters tau_ref and is checked.
-int build_setup(const lesbgk_params &p, int order, const double *h_init, Setup *out);
+// stats (may be NULL: rest initial state) enters tau_ref and is checked.
+int build_setup(const lesbgk_params &p, int order, const FieldStats *stats, Setup *out);
 
 // Build the wall tables (wS, wSdev, wA, wB) of *A in FP64 for the wall
 // temperature at time t; build_setup calls it for args with t = 0.

@@ -514,3 +514,24 @@ def test_diverged_solve_is_reported():
     with pytest.raises(L.LesbgkError) as e:
         s.moments(sums=True)
     assert e.value.code == L.EDIVERGED
+
+
+# ---------------------------------------------------------------- initial fields
+def test_initial_fields_checked_and_maxima_on_the_device():
+    """lesbgk_create checks the initial fields and takes their largest rho and
+    T (for tau_ref) on the device: tau_ref equals the host formula, and a
+    non-finite or non-positive value is refused with the first bad node."""
+    prob = I.Problem(name="f", nx=300, ny=70, bc_y=I.DIFFUSE, kn=0.07, b=0.5, visc_exp=0.7, wall_T=(1.01, 1.05))
+    fields = I.random_fields(prob, seed=4, amp_u=0.02, amp_T=0.2, amp_rho=0.2)
+    s = L.Solver(L.params_from_problem(prob), h_init=fields)
+    tmax = max(1.0, 1.05, float(fields[3].max()))
+    ref = (0.07 * (1 - 0.5)) * tmax ** (0.7 - 1.0) / float(fields[0].max())
+    assert s.info.tau_ref == pytest.approx(ref, rel=1e-15)
+    s.close()
+    for field, node, value in ((2, 1234, np.nan), (0, 20000, 0.0), (3, 7, -1.0), (1, 5000, np.inf)):
+        bad = fields.copy()
+        bad[field].reshape(-1)[node] = value
+        bad[field].reshape(-1)[node + 3] = value  # the first one is reported
+        with pytest.raises(L.LesbgkError) as e:
+            L.Solver(L.params_from_problem(prob), h_init=bad)
+        assert e.value.code == L.EINVAL and f"node {node} " in L.last_error(), L.last_error()
