@@ -13,7 +13,9 @@
 // Functions take their tables through template "accessor" types:
 //   TT: lattice tables  c[i], he[i][m] = He_m(c_i), hw[i][m] = w_i He_m(c_i)/m!
 //   TP: per-solve scalars c_omega, visc_pow, vmode, b, beta, has_force, dtgx, dtgy
-//   TW: wall tables wS[2][Q], wSdev[2][Q], wA[2], wB[2]
+//   TW: wall tables wS[2][Q], wSdev[2][Q], wA[2], wB[2] (walls normal to y);
+//       wSx[2][Q], wSxdev[2][Q], wAx[2], wBx[2], wAc[4], wBc[4] (walls normal
+//       to x and the corners); wspec (specular share)
 #pragma once
 
 #include <cuda_bf16.h>
