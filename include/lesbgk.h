@@ -88,7 +88,7 @@ typedef struct lesbgk_params {
   uint32_t struct_size; /* sizeof(lesbgk_params), checked */
   int32_t nroots;       /* Gauss-Hermite roots per axis: 4 (D2Q16) or 6 (D2Q36) */
   int32_t order;        /* Hermite order N of f_ES (3 or 4); 0 = 3 for D2Q16, 4 for D2Q36 */
-  int32_t nx, ny;       /* nodes; nx >= 1; ny >= 1 (>= 2 with walls) */
+  int32_t nx, ny;       /* nodes; nx >= 1; ny >= 1 (>= 2 with walls); nx ny < 2^31 */
   int32_t bc_y;         /* LESBGK_PERIODIC or LESBGK_DIFFUSE (walls on rows j = 0 and ny-1) */
   int32_t storage;      /* LESBGK_F32, LESBGK_F16 or LESBGK_BF16 */
   int32_t scheme;       /* LESBGK_UNSPLIT (default) or LESBGK_SPLIT */

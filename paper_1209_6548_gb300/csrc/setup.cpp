@@ -40,7 +40,9 @@ int check_params(const lesbgk_params *p) {
   const int order = p->order ? p->order : default_order(p->nroots);
   if (order != 3 && order != 4) return fail(LESBGK_EINVAL, "order must be 3 or 4");
   if (p->nx < 1 || p->ny < 1) return fail(LESBGK_EINVAL, "nx, ny must be >= 1");
-  if ((long long)p->nx * p->ny > (1LL << 31) / 64) return fail(LESBGK_EINVAL, "grid too large");
+  // node indices stay below 2^31 (each thread's warp index and the row/column
+  // products in the kernels are 64-bit or bounded by it)
+  if ((long long)p->nx * p->ny > (1LL << 31) - 1) return fail(LESBGK_EINVAL, "grid too large (nx ny >= 2^31)");
   if (p->dim != 0 && p->dim != 2 && p->dim != 3) return fail(LESBGK_EINVAL, "dim must be 2 or 3");
   if (p->dim == 3 && (p->nroots != 4 || order != 3 || p->storage != LESBGK_F32))
     return fail(LESBGK_EINVAL, "D = 3 is built as D3Q64 (nroots 4, order 3) with FP32 storage");

@@ -64,6 +64,7 @@ def test_struct_sizes_match_header(lib):
     (dict(dim=3, order=4), L.EINVAL),
     (dict(dim=3, storage=L.F16), L.EINVAL),
     (dict(bc_x=2), L.EINVAL),
+    (dict(nx=65536, ny=32768, bc_y=L.PERIODIC), L.EINVAL),  # 2^31 nodes
     (dict(bc_x=L.DIFFUSE, nx=1), L.EINVAL),              # walls in x need two columns
     (dict(bc_x=L.DIFFUSE, storage=L.BF16), L.EINVAL),
     (dict(bc_x=L.DIFFUSE, wall_specular=0.2), L.EINVAL),
@@ -81,6 +82,13 @@ def test_wall_models_accepted(lib):
     for kw in (dict(wall_specular=1.0), dict(wall_T_amp=0.02, wall_T_freq=0.5),
                dict(wall_T_amp=0.02, wall_T_freq=0.5, storage=L.BF16)):
         assert L.workspace_size(L.make_params(nx=4, ny=8, kn=0.1, b=0.0, bc_y=L.DIFFUSE, **kw)) > 0
+
+
+def test_large_grids_accepted(lib):
+    """Grids up to 2^31 - 1 nodes are admissible (a 16384^2 D2Q16 solve needs 34 GB)."""
+    p = L.make_params(nx=16384, ny=16384, kn=0.05, b=-0.5, bc_y=L.PERIODIC)
+    assert L.workspace_size(p) >= 2 * 16 * 16384 * 16384 * 4
+    assert L.workspace_size(L.make_params(nx=65535, ny=32768, kn=0.05, b=0.0, bc_y=L.PERIODIC)) > 0
 
 
 def test_d3_workspace_holds_the_z_even_half(lib):

@@ -133,14 +133,15 @@ def _sampled_oracle(prob, fields, dt, k, cells):
     return np.array(out).T  # (9, ncells)
 
 
-@pytest.mark.parametrize("which", ["tgv4096", "poiseuille512x1024", "tgv4096_d2q36", "tgv4096_d3q64"])
+@pytest.mark.parametrize("which", ["tgv4096", "poiseuille512x1024", "tgv4096_d2q36", "tgv4096_d3q64", "tgv16384"])
 def test_full_size_sampled(which):
     """At the full benchmark sizes and the default launch shape: moments after
     3 steps at 24 seeded nodes against the oracle run node by node."""
     from dataclasses import replace
     prob = {"tgv4096": lambda: I.tgv(4096), "poiseuille512x1024": lambda: I.poiseuille(512, 1024),
             "tgv4096_d2q36": lambda: I.tgv(4096, nroots=6),
-            "tgv4096_d3q64": lambda: replace(I.tgv(4096), dim=3)}[which]()
+            "tgv4096_d3q64": lambda: replace(I.tgv(4096), dim=3),
+            "tgv16384": lambda: I.tgv(16384)}[which]()  # 268M nodes: 34 GB of populations
     fields = I.initial_fields(prob)
     dt = time_step(prob, fields)
     s = gpu_solver(prob, dt, fields)
