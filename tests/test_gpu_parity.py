@@ -539,3 +539,19 @@ def test_initial_fields_checked_and_maxima_on_the_device():
         with pytest.raises(L.LesbgkError) as e:
             L.Solver(L.params_from_problem(prob), h_init=bad)
         assert e.value.code == L.EINVAL and f"node {node} " in L.last_error(), L.last_error()
+
+
+# ---------------------------------------------------------------- degenerate cases
+def test_collisionless_limit_and_zero_steps():
+    """Kn -> infinity (dt/tau ~ 1e-8): pure TVD transport with walls, against
+    the oracle; and a zero-step call leaves the state and the clock alone."""
+    prob = I.Problem(name="free", nx=61, ny=40, bc_y=I.DIFFUSE, kn=1e6, b=0.0, wall_ux=(-0.05, 0.05),
+                     wall_T=(0.97, 1.03), scheme=I.SPLIT)
+    fields = I.random_fields(prob, seed=8, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
+    res, s, _ = run_pair(prob, fields, [1, 30])
+    for n, g, r, *_ in res:
+        assert_fields_close(g, r, what=f"collisionless step {n}")
+    before = s.populations().cpu().numpy()
+    s.step(0)
+    assert s.info.steps_done == 30
+    assert np.array_equal(s.populations().cpu().numpy(), before)
