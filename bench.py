@@ -48,9 +48,10 @@ def parse():
     ap.add_argument("--workload", choices=["tgv", "batch", "serve", "precision"], default="tgv",
                     help="tgv: 4096^2 Taylor-Green throughput (default); batch: 512-instance channel mix; "
                          "serve: Poisson arrivals run to steady state with continuous batching")
-    ap.add_argument("--velocity-set", choices=["d2q16", "d2q36", "d3q64"], default="d2q16",
-                    help="tgv workload lattice: D2Q16 (order 3), D2Q36 (order 4, the paper's setting) or "
-                         "D3Q64 (order 3, D = 3: the paper's C_p = 5/2; stored by its z-even half)")
+    ap.add_argument("--velocity-set", choices=["d2q16", "d2q36", "d3q64", "d3q216"], default="d2q16",
+                    help="tgv workload lattice: D2Q16 (order 3), D2Q36 (order 4), D3Q64 (order 3, D = 3: the "
+                         "paper's C_p = 5/2) or D3Q216 (order 4, D = 3: the paper's set); the D = 3 sets are "
+                         "stored by their z-even half")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
                     help="population storage for the tgv workload (compute is FP32)")
     ap.add_argument("--requests", type=int, default=400)
@@ -72,6 +73,7 @@ LATTICES = {  # velocity set -> (nroots, dim, order, values stored per node)
     "d2q16": (4, 2, 3, 16),
     "d2q36": (6, 2, 4, 36),
     "d3q64": (4, 3, 3, 32),
+    "d3q216": (6, 3, 4, 108),
 }
 
 
@@ -686,7 +688,7 @@ def main():
     traffic = committed_traffic(digest, args.velocity_set, args.storage)
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        base = cpu_baseline(n, rows={"d2q16": 1024, "d2q36": 256, "d3q64": 256}[args.velocity_set],
+        base = cpu_baseline(n, rows={"d2q16": 1024, "d2q36": 256, "d3q64": 256, "d3q216": 32}[args.velocity_set],
                             velocity_set=args.velocity_set)
     if rank == 0:
         clocks = clk.summary()
@@ -703,8 +705,9 @@ def main():
                        "parallelism": f"replica x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                         "kernel": f"k_step<{nroots},{order},split,{args.storage},nz={q // (nroots * nroots)}> "
-                                   f"rows={shape[1]}",
+                         "kernel": (f"k_step<{nroots},{order},split,{args.storage},nz={q // (nroots * nroots)}> "
+                                    if q // (nroots * nroots) < 3 else "k_step_z<split> (one warp per z-level) ")
+                                   + f"rows={shape[1]}",
                          "kernel_ms": kernel_ms,
                          "bytes_per_lup": bytes_per_lup, "source_sha256": digest},
             "cpu_baseline": base,

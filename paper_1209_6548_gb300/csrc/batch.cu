@@ -661,8 +661,10 @@ extern "C" int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const d
   std::memcpy(D.kx, A.kx, sizeof D.kx);
   std::memcpy(D.ay, A.ay, sizeof D.ay);
   std::memcpy(D.ky, A.ky, sizeof D.ky);
-  std::memcpy(D.wS, A.wS, sizeof D.wS);
-  std::memcpy(D.wSdev, A.wSdev, sizeof D.wSdev);
+  for (int side = 0; side < 2; ++side) {  // the batch's rows are shorter (2D sets only)
+    std::memcpy(D.wS[side], A.wS[side], sizeof D.wS[side]);
+    std::memcpy(D.wSdev[side], A.wSdev[side], sizeof D.wSdev[side]);
+  }
   std::memcpy(D.wA, A.wA, sizeof D.wA);
   std::memcpy(D.wB, A.wB, sizeof D.wB);
   if (!b->lat_ready[cls]) {

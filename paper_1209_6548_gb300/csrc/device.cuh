@@ -324,14 +324,12 @@ __device__ __forceinline__ void z_factor(const float (&e)[N + 1][N + 1], float L
     }
 }
 
-// The collision + force source of collide() for the D = 3 set (T = tr P/(3 rho),
-// lambda 3x3 with lambda_zz = (1-b) T + b P_zz/rho).
-template <int NR, int N, int Q, class TT, class TP>
-__device__ __forceinline__ void collide3(const float (&F)[Q], float (&S)[Q], float &omw, const TT &Lt,
-                                         const TP &P) {
-  constexpr int KM = (N - 1 > 2) ? N - 1 : 2;
-  float b[3][KM + 1][KM + 1];
-  hermite_moments3<NR, KM>(F, b, Lt);
+// Coefficients d[l/2][m][k] of the D = 3 collision + force source from the
+// moments b of hermite_moments3 (T = tr P/(3 rho), lambda 3x3 with
+// lambda_zz = (1-b) T + b P_zz/rho), and omw = 1 - dt/tau.
+template <int NR, int N, int KM, class TP>
+__device__ __forceinline__ void es_coefficients3(const float (&b)[3][KM + 1][KM + 1], float (&d)[3][N + 1][N + 1],
+                                                 float &omw, const TP &P) {
   const float rho = 1.0f + b[0][0][0];
   const float ir = fast_rcp(rho);
   const float ux = b[0][1][0] * ir, uy = b[0][0][1] * ir;
@@ -354,7 +352,6 @@ __device__ __forceinline__ void collide3(const float (&F)[Q], float (&S)[Q], flo
   const float RLzz = fmaf(P.beta, trM, P.b * Mzz);
   float e[N + 1][N + 1];
   gaussian_coeffs<N>(rho, b[0][1][0], b[0][0][1], ux, uy, RLxx * ir, RLxy * ir, RLyy * ir, RLxx, RLxy, RLyy, e);
-  float d[3][N + 1][N + 1];
   z_factor<N>(e, RLzz * ir, om, d);
   d[0][0][0] = om * b[0][0][0];
   if (P.has_force) {
@@ -372,7 +369,38 @@ __device__ __forceinline__ void collide3(const float (&F)[Q], float (&S)[Q], flo
           d[l / 2][m][k] = v;
         }
   }
+}
+
+// The collision + force source of collide() for the D = 3 set, all stored
+// levels in one thread.
+template <int NR, int N, int Q, class TT, class TP>
+__device__ __forceinline__ void collide3(const float (&F)[Q], float (&S)[Q], float &omw, const TT &Lt,
+                                         const TP &P) {
+  constexpr int KM = (N - 1 > 2) ? N - 1 : 2;
+  float b[3][KM + 1][KM + 1];
+  hermite_moments3<NR, KM>(F, b, Lt);
+  float d[3][N + 1][N + 1];
+  es_coefficients3<NR, N, KM>(b, d, omw, P);
   hermite_evaluate3<NR, N>(d, S, Lt);
+}
+
+// The source at one stored z-level iz (c_z = c[NR/2 + iz]) only: the in-plane
+// evaluation of d'_mk = sum_l d[l/2][m][k] w_z He_l(c_z)/l!.
+template <int NR, int N, class TT>
+__device__ __forceinline__ void hermite_evaluate_level(const float (&d)[3][N + 1][N + 1], int iz,
+                                                       float (&S)[NR * NR], const TT &A) {
+  constexpr int H = NR / 2;
+  float dz[N + 1][N + 1];
+#pragma unroll
+  for (int m = 0; m <= N; ++m)
+#pragma unroll
+    for (int k = 0; m + k <= N; ++k) {
+      float v = d[0][m][k] * A.hw[H + iz][0];
+      if (m + k + 2 <= N) v = fmaf(d[1][m][k], A.hw[H + iz][2], v);
+      if (m + k + 4 <= N) v = fmaf(d[2][m][k], A.hw[H + iz][4], v);
+      dz[m][k] = v;
+    }
+  hermite_evaluate<NR, N>(dz, S, A);
 }
 
 // One node's source for either kind of set: collide() for D = 2, collide3() for D = 3.

@@ -207,6 +207,228 @@ __global__ void __launch_bounds__(kBlock) k_step(const S *__restrict__ fin, S *_
 }
 
 // ---------------------------------------------------------------------------
+// The fused time step for D3Q216 (N = 4): 108 stored values per node (the
+// z-even half), too many for one thread.  A block of three warps shares one
+// strip of nodes, warp iz holding z-level iz (c_z = c[3 + iz]) -- 36 values
+// laid out like D2Q36 -- and running the step of k_step on them.  The levels
+// meet in the collision, whose moments are sums over all levels (each warp
+// adds its in-plane Hermite moments weighted by 2 He_l(c_z) into shared
+// memory, one barrier per row, every warp sums the three in the same order),
+// and in the wall rule's incoming flux (one more barrier on wall rows).
+// ---------------------------------------------------------------------------
+constexpr int kBlockZ = 96;  // three warps: one per stored z-level
+constexpr int kXch = 13;     // moments a level contributes: l = 0, m + k <= 3 (10); l = 2, m + k <= 1 (3)
+
+template <int RING>
+constexpr size_t stepz_smem_bytes() {
+  return (size_t)3 * RING * 18 * 32 * 8 + (size_t)2 * 3 * kXch * 32 * sizeof(float) + 3 * 32 * sizeof(float);
+}
+
+template <bool SPLIT, int RING, bool SPEC>
+__global__ void __launch_bounds__(kBlockZ) k_step_z(const float *__restrict__ fin, float *__restrict__ fout,
+                                                    const KArgs A) {
+  constexpr int NR = 6, N = 4, H = 3, Q = 36, V = 2, GL = 18, KM = 3;
+  constexpr int HL = 2, U = 32 - 2 * HL;
+  const int lane = threadIdx.x & 31;
+  const int iz = threadIdx.x >> 5;  // stored z-level of this warp
+  const int strip = blockIdx.x % A.nstrips;
+  const int seg = blockIdx.x / A.nstrips;
+  if (seg >= A.nseg) return;  // uniform over the block
+  const int nx = A.nx, ny = A.ny;
+  const int xl = strip * U - HL + lane;
+  int xw = xl % nx;
+  if (xw < 0) xw += nx;
+  const bool writer = lane >= HL && lane < 32 - HL && xl < nx;
+  const int y0 = seg * A.rows;
+  const int y1 = min(y0 + A.rows, ny);
+  const long long gstride = (long long)V * A.plane;
+  const long long rstride = (long long)V * nx;
+  // level iz's 18 group planes: c_y < 0 groups at 9 iz + gl (gl < 9), c_y > 0
+  // groups at 27 + 9 iz + (gl - 9); ld_group_s reads plane base + gl gstride
+  const long long lo = (long long)(9 * iz) * gstride, hi = (long long)(18 + 9 * iz) * gstride;
+  const float *fx = fin + (long long)xw * V;
+  auto row_ptr = [&](int j) { return fx + map_row(j, ny, A.walls) * rstride; };
+
+  float fc[Q], s0[Q], s1[Q];
+  {
+    float m2[Q], m1[Q], p1[Q];
+    const float *pm2 = row_ptr(y0 - 2), *pm1 = row_ptr(y0 - 1), *pz = row_ptr(y0), *pp1 = row_ptr(y0 + 1);
+#pragma unroll
+    for (int g = 0; g < GL; ++g) {
+      const long long off = g < GL / 2 ? lo : hi;
+      ld_group_s<NR, float>(pm1 + off, gstride, g, m1, A);
+      ld_group_s<NR, float>(pz + off, gstride, g, fc, A);
+      if (g >= GL / 2) ld_group_s<NR, float>(pm2 + off, gstride, g, m2, A);
+      else ld_group_s<NR, float>(pp1 + off, gstride, g, p1, A);
+    }
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      if (a % NR >= H) {
+        s0[a] = fc[a] - m1[a];
+        s1[a] = minmod(m1[a] - m2[a], fc[a] - m1[a]);
+      } else {
+        s0[a] = p1[a];
+        s1[a] = minmod(fc[a] - m1[a], p1[a] - fc[a]);
+      }
+    }
+  }
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using T = uint2;
+  T *ring = reinterpret_cast<T *>(smem_raw) + (size_t)iz * RING * GL * 32 + lane;
+  float *xch = reinterpret_cast<float *>(smem_raw + (size_t)3 * RING * GL * 32 * sizeof(T));
+  float *wsum = xch + 2 * 3 * kXch * 32;
+  int r1 = map_row(y0 + 1, ny, A.walls), r2 = map_row(y0 + 2, ny, A.walls);
+  const int nrows = y1 - y0;
+  auto issue_rowload = [&](int k) {
+    if (k < nrows) {
+      const float *q1 = fx + r1 * rstride, *q2 = fx + r2 * rstride;
+      T *slot = ring + (k % RING) * GL * 32;
+#pragma unroll
+      for (int g = 0; g < GL; ++g)
+        cp_async_raw<8>(slot + g * 32, (g >= GL / 2 ? q1 + hi : q2 + lo) + g * gstride);
+      r1 = r2;
+      r2 = r2 + 1 < ny ? r2 + 1 : (A.walls ? ny - 1 : 0);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int k = 0; k < RING - 1; ++k) issue_rowload(k);
+
+  for (int j = y0; j < y1; ++j) {
+    const int k = j - y0;
+    issue_rowload(k + RING - 1);
+    cp_async_wait<RING - 1>();
+    float ld[Q];
+    {
+      const T *slot = ring + (k % RING) * GL * 32;
+#pragma unroll
+      for (int g = 0; g < GL; ++g) unpack_group<NR, float>(slot[g * 32], g, ld, A);
+    }
+
+    // moments over all levels: this level's share into shared memory, then the sum
+    float acc[Q];
+    float omw;
+    {
+      float a2[KM + 1][KM + 1];
+      hermite_moments<NR, KM>(fc, a2, A);
+      float *x = xch + ((k & 1) * 3 + iz) * kXch * 32 + lane;
+      const float h0 = 2.0f, h2 = 2.0f * A.he[H + iz][2];
+      int v = 0;
+#pragma unroll
+      for (int m = 0; m <= KM; ++m)
+#pragma unroll
+        for (int q = 0; m + q <= KM; ++q) x[(v++) * 32] = h0 * a2[m][q];
+#pragma unroll
+      for (int m = 0; m <= KM - 2; ++m)
+#pragma unroll
+        for (int q = 0; m + q <= KM - 2; ++q) x[(v++) * 32] = h2 * a2[m][q];
+      __syncthreads();
+      float b[3][KM + 1][KM + 1];
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int m = 0; m <= KM; ++m)
+#pragma unroll
+          for (int q = 0; q <= KM; ++q) b[l][m][q] = 0.0f;
+      const float *x0 = xch + (k & 1) * 3 * kXch * 32 + lane;
+      v = 0;
+#pragma unroll
+      for (int m = 0; m <= KM; ++m)
+#pragma unroll
+        for (int q = 0; m + q <= KM; ++q, ++v)
+          b[0][m][q] = (x0[v * 32] + x0[(kXch + v) * 32]) + x0[(2 * kXch + v) * 32];
+#pragma unroll
+      for (int m = 0; m <= KM - 2; ++m)
+#pragma unroll
+        for (int q = 0; m + q <= KM - 2; ++q, ++v)
+          b[1][m][q] = (x0[v * 32] + x0[(kXch + v) * 32]) + x0[(2 * kXch + v) * 32];
+      float d[3][N + 1][N + 1];
+      es_coefficients3<NR, N, KM>(b, d, omw, A);
+      hermite_evaluate_level<NR, N>(d, iz, acc, A);
+    }
+
+    float xs[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      const int iy = a % NR;
+      const float ay = A.ay[iy], ky = A.ky[iy];
+      float diff;
+      const float f0 = fc[a];
+      if (iy >= H) {
+        const float dn = ld[a] - f0;
+        const float sg = minmod(s0[a], dn);
+        diff = fmaf(ky, sg - s1[a], s0[a]);
+        s0[a] = dn;
+        s1[a] = sg;
+        fc[a] = ld[a];
+      } else {
+        const float d1 = s0[a] - f0;
+        const float sg = minmod(d1, ld[a] - s0[a]);
+        diff = fmaf(-ky, sg - s1[a], d1);
+        s1[a] = sg;
+        fc[a] = s0[a];
+        s0[a] = ld[a];
+      }
+      acc[a] = fmaf(omw, f0, fmaf(-ay, diff, acc[a]));
+      xs[a] = SPLIT ? fmaf(-ay, diff, f0) : f0;
+    }
+
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      const int ix = a / NR;
+      const float ax = A.ax[ix], kx = A.kx[ix];
+      const float left = __shfl_up_sync(kFull, xs[a], 1);
+      const float dl = xs[a] - left;
+      const float dr = __shfl_down_sync(kFull, dl, 1);
+      const float sg = minmod(dl, dr);
+      float diff;
+      if (ix >= H) {
+        const float sprev = __shfl_up_sync(kFull, sg, 1);
+        diff = fmaf(kx, sg - sprev, dl);
+      } else {
+        const float snext = __shfl_down_sync(kFull, sg, 1);
+        diff = fmaf(-kx, snext - sg, dr);
+      }
+      acc[a] = fmaf(-ax, diff, acc[a]);
+    }
+
+    if (A.walls && (j == 0 || j == ny - 1)) {  // uniform over the block
+      // the wall rule of wall_fix with the incoming flux summed over the levels
+      const int side = j == 0 ? 0 : 1;
+      float sl = 0.0f;
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const int iy = a % NR;
+        const bool incoming = side == 0 ? (iy < H) : (iy >= H);
+        if (incoming) sl = fmaf(fabsf(A.c[iy]), acc[a], sl);
+      }
+      wsum[iz * 32 + lane] = sl;
+      __syncthreads();
+      const float s = (wsum[lane] + wsum[32 + lane]) + wsum[64 + lane];
+      const float rw1 = (s - A.wA[side]) * A.wB[side];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const int iy = a % NR;
+        const bool outgoing = side == 0 ? (iy >= H) : (iy < H);
+        if (outgoing) {
+          const int ag = iz * Q + a;
+          const float diffuse = fmaf(rw1, A.wS[side][ag], A.wSdev[side][ag]);
+          if constexpr (SPEC) acc[a] = fmaf(A.wspec, acc[a + (NR - 1 - 2 * iy)] - diffuse, diffuse);
+          else acc[a] = diffuse;
+        }
+      }
+    }
+
+    if (writer) {
+      float *o = fout + (long long)j * rstride + (long long)xw * V;
+#pragma unroll
+      for (int g = 0; g < GL; ++g) st_group_s<NR, float>(o + (g < GL / 2 ? lo : hi), gstride, g, acc, A);
+    }
+  }
+  cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
 // Initial populations f = rho S(T,u) (Eq. feq0 to order N: the Hermite
 // expansion of the isotropic Maxwellian), then the wall rule once.
 // fields: double[4][ny][nx] = rho, u_x, u_y, T (or nullptr: rest).
@@ -508,7 +730,7 @@ int pick_launch(lesbgk *h) {
   // 32, where the three prologue rows per segment weigh more)
   h->cpt = 1;
   const int nstrips = (nx + 27) / 28;
-  const int rows_default = h->q == 36 ? 128 : 32;
+  const int rows_default = h->q >= 36 ? 128 : 32;
   if (h->rows <= 0) h->rows = ny < rows_default ? ny : rows_default;
   h->args.rows = h->rows;
   h->args.nstrips = nstrips;
@@ -548,7 +770,10 @@ void dispatch(int nr, int order, int storage, int dim, Fn &&fn) {
   using N4 = std::integral_constant<int, 4>;
   using Z1 = std::integral_constant<int, 1>;
   using Z2 = std::integral_constant<int, 2>;
-  if (dim == 3) {
+  using Z3 = std::integral_constant<int, 3>;
+  if (dim == 3 && nr == 6) {
+    fn(R6{}, N4{}, float{}, Z3{});
+  } else if (dim == 3) {
     fn(R4{}, N3{}, float{}, Z2{});
   } else if (nr == 4 && order == 3) {
     if (storage == LESBGK_F16) fn(R4{}, N3{}, __half{}, Z1{});
@@ -571,17 +796,25 @@ cudaError_t allow_smem(const lesbgk *h) {
   dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto n, auto st, auto z) {
     constexpr int NR = decltype(r)::value, N = decltype(n)::value, NZ = decltype(z)::value;
     using S = decltype(st);
-    constexpr int smem = (int)step_smem_bytes<NR, S, NZ>();
-    auto allow = [&](auto kernel) {
+    auto allow = [&](auto kernel, int smem) {
       if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     };
-    allow(k_step<NR, N, true, kRing, S, 0, NZ>);
-    allow(k_step<NR, N, false, kRing, S, 0, NZ>);
-    if constexpr (std::is_same<S, float>::value) {
-      allow(k_step<NR, N, true, kRing, S, 1, NZ>);
-      allow(k_step<NR, N, false, kRing, S, 1, NZ>);
-      allow(k_step<NR, N, true, kRing, S, 2, NZ>);
-      allow(k_step<NR, N, false, kRing, S, 2, NZ>);
+    if constexpr (NZ == 3) {  // D3Q216: one warp per stored z-level
+      constexpr int smem = (int)stepz_smem_bytes<kRing>();
+      allow(k_step_z<true, kRing, false>, smem);
+      allow(k_step_z<false, kRing, false>, smem);
+      allow(k_step_z<true, kRing, true>, smem);
+      allow(k_step_z<false, kRing, true>, smem);
+    } else {
+      constexpr int smem = (int)step_smem_bytes<NR, S, NZ>();
+      allow(k_step<NR, N, true, kRing, S, 0, NZ>, smem);
+      allow(k_step<NR, N, false, kRing, S, 0, NZ>, smem);
+      if constexpr (std::is_same<S, float>::value) {
+        allow(k_step<NR, N, true, kRing, S, 1, NZ>, smem);
+        allow(k_step<NR, N, false, kRing, S, 1, NZ>, smem);
+        allow(k_step<NR, N, true, kRing, S, 2, NZ>, smem);
+        allow(k_step<NR, N, false, kRing, S, 2, NZ>, smem);
+      }
     }
   });
   return e;
@@ -593,24 +826,38 @@ int launch_step(lesbgk *h, const void *fin, void *fout, cudaStream_t s) {
   dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto n, auto st, auto z) {
     constexpr int NR = decltype(r)::value, N = decltype(n)::value, NZ = decltype(z)::value;
     using S = decltype(st);
-    constexpr size_t smem = step_smem_bytes<NR, S, NZ>();
     const S *fi = static_cast<const S *>(fin);
     S *fo = static_cast<S *>(fout);
     const bool split = h->p.scheme == LESBGK_SPLIT;
-    if constexpr (std::is_same<S, float>::value) {  // FP32 storage only (checked at set-up)
-      if (h->args.xwalls) {  // walls in x (cavity)
-        if (split) k_step<NR, N, true, kRing, S, 2, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
-        else k_step<NR, N, false, kRing, S, 2, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
-        return;
+    if constexpr (NZ == 3) {  // D3Q216: a block of three warps per strip and segment
+      constexpr size_t smem = stepz_smem_bytes<kRing>();
+      const unsigned gz = (unsigned)warps;
+      const bool spec = h->args.walls && h->args.wspec != 0.0f;
+      if (split) {
+        if (spec) k_step_z<true, kRing, true><<<gz, kBlockZ, smem, s>>>(fi, fo, h->args);
+        else k_step_z<true, kRing, false><<<gz, kBlockZ, smem, s>>>(fi, fo, h->args);
+      } else {
+        if (spec) k_step_z<false, kRing, true><<<gz, kBlockZ, smem, s>>>(fi, fo, h->args);
+        else k_step_z<false, kRing, false><<<gz, kBlockZ, smem, s>>>(fi, fo, h->args);
       }
-      if (h->args.walls && h->args.wspec != 0.0f) {  // Maxwell walls
-        if (split) k_step<NR, N, true, kRing, S, 1, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
-        else k_step<NR, N, false, kRing, S, 1, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
-        return;
+      return;
+    } else {
+      constexpr size_t smem = step_smem_bytes<NR, S, NZ>();
+      if constexpr (std::is_same<S, float>::value) {  // FP32 storage only (checked at set-up)
+        if (h->args.xwalls) {  // walls in x (cavity)
+          if (split) k_step<NR, N, true, kRing, S, 2, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+          else k_step<NR, N, false, kRing, S, 2, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+          return;
+        }
+        if (h->args.walls && h->args.wspec != 0.0f) {  // Maxwell walls
+          if (split) k_step<NR, N, true, kRing, S, 1, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+          else k_step<NR, N, false, kRing, S, 1, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+          return;
+        }
       }
+      if (split) k_step<NR, N, true, kRing, S, 0, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+      else k_step<NR, N, false, kRing, S, 0, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
     }
-    if (split) k_step<NR, N, true, kRing, S, 0, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
-    else k_step<NR, N, false, kRing, S, 0, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
   });
   return 0;
 }
@@ -970,7 +1217,9 @@ extern "C" int lesbgk_moments_noalloc(const lesbgk_params *p, const float *d_pop
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int blocks = (int)((cells + kNoAllocNodesPerBlock - 1) / kNoAllocNodesPerBlock);
   double *sums = scratch + (size_t)kNoAllocBlocks * 4;
-  if (p->dim == 3) k_moments_public<4, 2><<<blocks, kMomBlock, 0, s>>>(d_populations, d_out, scratch, tmp.args);
+  if (p->dim == 3 && p->nroots == 6)
+    k_moments_public<6, 3><<<blocks, kMomBlock, 0, s>>>(d_populations, d_out, scratch, tmp.args);
+  else if (p->dim == 3) k_moments_public<4, 2><<<blocks, kMomBlock, 0, s>>>(d_populations, d_out, scratch, tmp.args);
   else if (p->nroots == 4) k_moments_public<4><<<blocks, kMomBlock, 0, s>>>(d_populations, d_out, scratch, tmp.args);
   else k_moments_public<6><<<blocks, kMomBlock, 0, s>>>(d_populations, d_out, scratch, tmp.args);
   k_reduce_partials<<<1, 128, 0, s>>>(scratch, blocks, sums);

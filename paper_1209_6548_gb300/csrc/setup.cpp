@@ -44,8 +44,11 @@ int check_params(const lesbgk_params *p) {
   // products in the kernels are 64-bit or bounded by it)
   if ((long long)p->nx * p->ny > (1LL << 31) - 1) return fail(LESBGK_EINVAL, "grid too large (nx ny >= 2^31)");
   if (p->dim != 0 && p->dim != 2 && p->dim != 3) return fail(LESBGK_EINVAL, "dim must be 2 or 3");
-  if (p->dim == 3 && (p->nroots != 4 || order != 3 || p->storage != LESBGK_F32))
-    return fail(LESBGK_EINVAL, "D = 3 is built as D3Q64 (nroots 4, order 3) with FP32 storage");
+  if (p->dim == 3 && !((p->nroots == 4 && order == 3) || (p->nroots == 6 && order == 4)))
+    return fail(LESBGK_EINVAL, "D = 3 is built as D3Q64 (nroots 4, order 3) and D3Q216 (nroots 6, order 4)");
+  if (p->dim == 3 && p->storage != LESBGK_F32) return fail(LESBGK_EINVAL, "D = 3 is built for FP32 storage");
+  if (p->dim == 3 && p->nroots == 6 && p->bc_x != LESBGK_PERIODIC)
+    return fail(LESBGK_EINVAL, "walls in x are not built for D3Q216");
   if (p->bc_y != LESBGK_PERIODIC && p->bc_y != LESBGK_DIFFUSE) return fail(LESBGK_EINVAL, "bad bc_y");
   if (p->bc_x != LESBGK_PERIODIC && p->bc_x != LESBGK_DIFFUSE) return fail(LESBGK_EINVAL, "bad bc_x");
   if (p->bc_x == LESBGK_DIFFUSE) {
@@ -212,6 +215,7 @@ void x_wall_tables(const Setup &h, KArgs *out) {
   const double *c = h.c, *w = h.w;
   const double fact[kMaxOrder + 1] = {1, 1, 2, 6, 24};
   const int nz = h.dim == 3 ? H : 1;
+  if (nz * nr * nr > kMaxQ) return;  // (walls in x are refused for such sets by check_params)
   for (int s = 0; s < 2; ++s) {
     double e[kMaxOrder + 1][kMaxOrder + 1];
     const double th = h.wall_Tx[s] - 1.0;

@@ -11,7 +11,8 @@ namespace lesbgk_setup {
 
 constexpr int kMaxR = 6;
 constexpr int kMaxN = 4;
-constexpr int kMaxQ = kMaxR * kMaxR;
+constexpr int kMaxQ = kMaxR * kMaxR;             // values per node of the 2D sets, D3Q64's 32
+constexpr int kMaxWQ = kMaxR * kMaxR * kMaxR / 2;  // values per node of D3Q216 (its z-even half)
 
 // Kernel arguments: lattice tables and scalars, passed by value (constant bank).
 struct KArgs {
@@ -20,8 +21,8 @@ struct KArgs {
   float hw[kMaxR][kMaxN + 1];  // w_i He_m(c_i) / m!
   float ax[kMaxR], kx[kMaxR];  // c_i dt/dx and (1 - |c_i| dt/dx)/2
   float ay[kMaxR], ky[kMaxR];  // same along y
-  float wS[2][kMaxQ];          // wall equilibrium S_a(T_w, u_w) per stored population, [0] bottom, [1] top
-  float wSdev[2][kMaxQ];       // S_a - w_a
+  float wS[2][kMaxWQ];         // wall equilibrium S_a(T_w, u_w) per stored population, [0] bottom, [1] top
+  float wSdev[2][kMaxWQ];      // S_a - w_a
   float wA[2], wB[2];          // sum_out |c_y|(S-w) and 1/sum_out |c_y| S
   float wq[kMaxQ], iwq[kMaxQ]; // 16-bit storage: stored = df * iwq, df = stored * wq
   float c_omega;               // dt / (Kn (1-b)):  dt/tau = c_omega rho T^(1-varpi)

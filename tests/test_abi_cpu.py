@@ -60,7 +60,8 @@ def test_struct_sizes_match_header(lib):
     (dict(wall_T_amp=1.0), L.EINVAL),                     # T_w would reach 0
     (dict(wall_T_amp=float("nan")), L.EINVAL),
     (dict(dim=4), L.EINVAL),
-    (dict(dim=3, nroots=6), L.EINVAL),                    # D = 3 is built as D3Q64
+    (dict(dim=3, nroots=6, order=3), L.EINVAL),           # D = 3: D3Q64 N = 3, D3Q216 N = 4
+    (dict(dim=3, nroots=6, bc_x=L.DIFFUSE), L.EINVAL),    # no walls in x on D3Q216
     (dict(dim=3, order=4), L.EINVAL),
     (dict(dim=3, storage=L.F16), L.EINVAL),
     (dict(bc_x=2), L.EINVAL),
@@ -92,11 +93,12 @@ def test_large_grids_accepted(lib):
 
 
 def test_d3_workspace_holds_the_z_even_half(lib):
-    """D3Q64 stores 32 values per node (its z-even half): two FP32 buffers."""
-    p = L.make_params(nx=64, ny=32, kn=0.1, b=0.0, bc_y=L.DIFFUSE, dim=3)
-    assert L.stored_q(p) == 32
-    n = L.workspace_size(p)
-    assert 2 * 32 * 64 * 32 * 4 <= n < 2 * 33 * 64 * 32 * 4 + (1 << 16)
+    """D3Q64 and D3Q216 store 32 and 108 values per node (their z-even halves)."""
+    for nroots, q in ((4, 32), (6, 108)):
+        p = L.make_params(nroots=nroots, nx=64, ny=32, kn=0.1, b=0.0, bc_y=L.DIFFUSE, dim=3)
+        assert L.stored_q(p) == q
+        n = L.workspace_size(p)
+        assert 2 * q * 64 * 32 * 4 <= n < 2 * (q + 1) * 64 * 32 * 4 + (1 << 16)
 
 
 def test_workspace_size_formula(lib):

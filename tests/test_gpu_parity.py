@@ -133,7 +133,8 @@ def _sampled_oracle(prob, fields, dt, k, cells):
     return np.array(out).T  # (9, ncells)
 
 
-@pytest.mark.parametrize("which", ["tgv4096", "poiseuille512x1024", "tgv4096_d2q36", "tgv4096_d3q64", "tgv16384"])
+@pytest.mark.parametrize("which", ["tgv4096", "poiseuille512x1024", "tgv4096_d2q36", "tgv4096_d3q64", "tgv4096_d3q216",
+                                   "tgv16384"])
 def test_full_size_sampled(which):
     """At the full benchmark sizes and the default launch shape: moments after
     3 steps at 24 seeded nodes against the oracle run node by node."""
@@ -141,6 +142,7 @@ def test_full_size_sampled(which):
     prob = {"tgv4096": lambda: I.tgv(4096), "poiseuille512x1024": lambda: I.poiseuille(512, 1024),
             "tgv4096_d2q36": lambda: I.tgv(4096, nroots=6),
             "tgv4096_d3q64": lambda: replace(I.tgv(4096), dim=3),
+            "tgv4096_d3q216": lambda: replace(I.tgv(4096, nroots=6), dim=3),
             "tgv16384": lambda: I.tgv(16384)}[which]()  # 268M nodes: 34 GB of populations
     fields = I.initial_fields(prob)
     dt = time_step(prob, fields)
@@ -364,74 +366,80 @@ def test_unsteady_wall_heating(kn, st):
     assert np.max(np.abs(res[-1][2][3] - 1.0)) > 1e-3  # the walls did heat the gas
 
 
-# ---------------------------------------------------------------- D = 3 set
-# D3Q64 (N = 3) on the 2D grid: the library stores the z-even half (32 values
-# per node); the oracle runs all 64 velocities.
-def d3(prob):
+# ---------------------------------------------------------------- D = 3 sets
+# D3Q64 (N = 3) and D3Q216 (N = 4) on the 2D grid: the library stores the
+# z-even half (32 or 108 values per node); the oracle runs all 64 or 216.
+def d3(prob, nroots=4):
     from dataclasses import replace
-    return replace(prob, dim=3, nroots=4, order=0, name=prob.name + "_d3q64")
+    return replace(prob, dim=3, nroots=nroots, order=0, name=prob.name + f"_d3q{nroots ** 3}")
 
 
-def z_even_half(fp):
-    """Oracle populations (64, ny, nx) -> deviations at the 32 stored
-    velocities (iz, ix, iy), c_z = c[2 + iz] > 0."""
-    *_, w = O.velocity_set_d(4, 3)
-    idx = [(ix * 4 + iy) * 4 + 2 + iz for iz in range(2) for ix in range(4) for iy in range(4)]
+def z_even_half(fp, nroots=4):
+    """Oracle populations (nroots^3, ny, nx) -> deviations at the stored
+    velocities (iz, ix, iy), c_z = c[nroots/2 + iz] > 0."""
+    *_, w = O.velocity_set_d(nroots, 3)
+    h = nroots // 2
+    idx = [(ix * nroots + iy) * nroots + h + iz for iz in range(h) for ix in range(nroots) for iy in range(nroots)]
     return (fp - w[:, None, None])[idx]
 
 
-def assert_d3_populations(gp, fp, what):
-    dev = z_even_half(fp)
+def assert_d3_populations(gp, fp, what, nroots=4):
+    dev = z_even_half(fp, nroots)
     err = np.max(np.abs(gp - dev))
     assert err <= 2e-6 * np.max(np.abs(dev)), f"{what} populations: {err:.3e} vs {np.max(np.abs(dev)):.3e}"
 
 
-def test_d3_couette_2000_steps():
-    """Couette 4x64 with the D = 3 set (the paper's C_p = 5/2 gas)."""
-    prob = d3(I.couette_4x64())
-    res, s, _ = run_pair(prob, None, [1, 10, 100, 2000])
+@pytest.mark.parametrize("nroots", [4, 6])
+def test_d3_couette(nroots):
+    """Couette 4x64 with the D = 3 sets (the paper's C_p = 5/2 gas)."""
+    prob = d3(I.couette_4x64(), nroots)
+    res, s, _ = run_pair(prob, None, [1, 10, 100, 2000] if nroots == 4 else [1, 10, 300])
     for n, g, r, gp, fp in res:
-        assert_fields_close(g, r, what=f"d3 couette step {n}")
-        assert_d3_populations(gp, fp, f"d3 couette step {n}")
-    assert s.info.q == 32
+        assert_fields_close(g, r, what=f"d3q{nroots ** 3} couette step {n}")
+        assert_d3_populations(gp, fp, f"d3q{nroots ** 3} couette step {n}", nroots)
+    assert s.info.q == nroots ** 3 // 2
 
 
+@pytest.mark.parametrize("nroots", [4, 6])
 @pytest.mark.parametrize("scheme", [I.UNSPLIT, I.SPLIT])
 @pytest.mark.parametrize("nx,ny", [(70, 37), (5, 66), (1, 1)])
-def test_d3_rough_periodic_fields(nx, ny, scheme):
-    prob = d3(I.Problem(name="rough", nx=nx, ny=ny, bc_y=I.PERIODIC, kn=0.05, b=-0.5, scheme=scheme))
+def test_d3_rough_periodic_fields(nx, ny, scheme, nroots):
+    prob = d3(I.Problem(name="rough", nx=nx, ny=ny, bc_y=I.PERIODIC, kn=0.05, b=-0.5, scheme=scheme), nroots)
     fields = I.random_fields(prob, seed=nx * 100 + ny + 7)
     res, *_ = run_pair(prob, fields, [1, 6])
     for n, g, r, gp, fp in res:
-        assert_fields_close(g, r, what=f"d3 {nx}x{ny} step {n}")
-        assert_d3_populations(gp, fp, f"d3 {nx}x{ny} step {n}")
+        assert_fields_close(g, r, what=f"d3q{nroots ** 3} {nx}x{ny} step {n}")
+        assert_d3_populations(gp, fp, f"d3q{nroots ** 3} {nx}x{ny} step {n}", nroots)
 
 
+@pytest.mark.parametrize("nroots", [4, 6])
 @pytest.mark.parametrize("b", [-0.5, 0.5])
-def test_d3_walls_force_rough(b):
+def test_d3_walls_force_rough(b, nroots):
     """Moving walls at two temperatures, body force, rough interior."""
     prob = d3(I.Problem(name="wf", nx=60, ny=45, bc_y=I.DIFFUSE, kn=0.1, b=b, wall_ux=(-0.05, 0.05),
-                        wall_T=(0.97, 1.03), g=(1e-3, 2e-4)))
+                        wall_T=(0.97, 1.03), g=(1e-3, 2e-4)), nroots)
     fields = I.random_fields(prob, seed=31, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
     res, *_ = run_pair(prob, fields, [1, 10])
     for n, g, r, gp, fp in res:
-        assert_fields_close(g, r, what=f"d3 walls b={b} step {n}")
-        assert_d3_populations(gp, fp, f"d3 walls b={b} step {n}")
+        assert_fields_close(g, r, what=f"d3q{nroots ** 3} walls b={b} step {n}")
+        assert_d3_populations(gp, fp, f"d3q{nroots ** 3} walls b={b} step {n}", nroots)
 
 
-def test_d3_maxwell_walls_and_heating():
+@pytest.mark.parametrize("nroots", [4, 6])
+def test_d3_maxwell_walls_and_heating(nroots):
     """Specular share 0.3 and heated walls (Sec. 3.2, Sec. 4.2) with D = 3."""
     prob = d3(I.Problem(name="mh", nx=8, ny=40, bc_y=I.DIFFUSE, kn=0.2, b=-0.5, wall_specular=0.3,
-                        wall_T_amp=0.02, wall_T_freq=0.5553603672697958))
+                        wall_T_amp=0.02, wall_T_freq=0.5553603672697958), nroots)
     res, *_ = run_pair(prob, None, [1, 50, 300])
     for n, g, r, *_ in res:
-        assert_fields_close(g, r, what=f"d3 maxwell+heating step {n}")
+        assert_fields_close(g, r, what=f"d3q{nroots ** 3} maxwell+heating step {n}")
 
 
-def test_d3_conservation_and_totals():
+@pytest.mark.parametrize("nroots", [4, 6])
+def test_d3_conservation_and_totals(nroots):
     """Periodic D = 3: the FP64 totals match the oracle's (energy counts
     c_z^2: 3/2 rho T per node at rest) and are conserved over 200 steps."""
-    prob = d3(I.tgv(128, steps=200))
+    prob = d3(I.tgv(128, steps=200), nroots)
     fields = I.initial_fields(prob)
     dt = time_step(prob, fields)
     s = gpu_solver(prob, dt, fields)
