@@ -384,25 +384,6 @@ __device__ __forceinline__ void collide3(const float (&F)[Q], float (&S)[Q], flo
   hermite_evaluate3<NR, N>(d, S, Lt);
 }
 
-// The source at one stored z-level iz (c_z = c[NR/2 + iz]) only: the in-plane
-// evaluation of d'_mk = sum_l d[l/2][m][k] w_z He_l(c_z)/l!.
-template <int NR, int N, class TT>
-__device__ __forceinline__ void hermite_evaluate_level(const float (&d)[3][N + 1][N + 1], int iz,
-                                                       float (&S)[NR * NR], const TT &A) {
-  constexpr int H = NR / 2;
-  float dz[N + 1][N + 1];
-#pragma unroll
-  for (int m = 0; m <= N; ++m)
-#pragma unroll
-    for (int k = 0; m + k <= N; ++k) {
-      float v = d[0][m][k] * A.hw[H + iz][0];
-      if (m + k + 2 <= N) v = fmaf(d[1][m][k], A.hw[H + iz][2], v);
-      if (m + k + 4 <= N) v = fmaf(d[2][m][k], A.hw[H + iz][4], v);
-      dz[m][k] = v;
-    }
-  hermite_evaluate<NR, N>(dz, S, A);
-}
-
 // One node's source for either kind of set: collide() for D = 2, collide3() for D = 3.
 template <int NR, int N, int Q, class TT, class TP>
 __device__ __forceinline__ void collide_any(const float (&F)[Q], float (&S)[Q], float &omw, const TT &Lt,

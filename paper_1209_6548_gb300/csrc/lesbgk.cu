@@ -218,10 +218,11 @@ __global__ void __launch_bounds__(kBlock) k_step(const S *__restrict__ fin, S *_
 // ---------------------------------------------------------------------------
 constexpr int kBlockZ = 96;  // three warps: one per stored z-level
 constexpr int kXch = 13;     // moments a level contributes: l = 0, m + k <= 3 (10); l = 2, m + k <= 1 (3)
+constexpr int kXch4 = 4;     // ... held as four float4 per thread (16 slots)
 
 template <int RING>
 constexpr size_t stepz_smem_bytes() {
-  return (size_t)3 * RING * 18 * 32 * 8 + (size_t)2 * 3 * kXch * 32 * sizeof(float) + 3 * 32 * sizeof(float);
+  return (size_t)3 * RING * 18 * 32 * 8 + (size_t)2 * 3 * kXch4 * 32 * sizeof(float4) + 3 * 32 * sizeof(float);
 }
 
 template <bool SPLIT, int RING, bool SPEC>
@@ -275,8 +276,13 @@ __global__ void __launch_bounds__(kBlockZ) k_step_z(const float *__restrict__ fi
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using T = uint2;
   T *ring = reinterpret_cast<T *>(smem_raw) + (size_t)iz * RING * GL * 32 + lane;
-  float *xch = reinterpret_cast<float *>(smem_raw + (size_t)3 * RING * GL * 32 * sizeof(T));
-  float *wsum = xch + 2 * 3 * kXch * 32;
+  // exchange buffer [row parity][level][float4 k][lane]: consecutive lanes read
+  // consecutive 16-byte words (no bank conflicts)
+  float4 *xch = reinterpret_cast<float4 *>(smem_raw + (size_t)3 * RING * GL * 32 * sizeof(T));
+  float *wsum = reinterpret_cast<float *>(xch + 2 * 3 * kXch4 * 32);
+  // this level's z-weights, read once: 2 He_2(c_z) and w_z He_l(c_z)/l!, l = 0, 2, 4
+  const float he2 = 2.0f * A.he[H + iz][2];
+  const float hz[3] = {A.hw[H + iz][0], A.hw[H + iz][2], A.hw[H + iz][4]};
   int r1 = map_row(y0 + 1, ny, A.walls), r2 = map_row(y0 + 2, ny, A.walls);
   const int nrows = y1 - y0;
   auto issue_rowload = [&](int k) {
@@ -311,18 +317,33 @@ __global__ void __launch_bounds__(kBlockZ) k_step_z(const float *__restrict__ fi
     {
       float a2[KM + 1][KM + 1];
       hermite_moments<NR, KM>(fc, a2, A);
-      float *x = xch + ((k & 1) * 3 + iz) * kXch * 32 + lane;
-      const float h0 = 2.0f, h2 = 2.0f * A.he[H + iz][2];
+      float part[4 * kXch4];
       int v = 0;
 #pragma unroll
       for (int m = 0; m <= KM; ++m)
 #pragma unroll
-        for (int q = 0; m + q <= KM; ++q) x[(v++) * 32] = h0 * a2[m][q];
+        for (int q = 0; m + q <= KM; ++q) part[v++] = 2.0f * a2[m][q];
 #pragma unroll
       for (int m = 0; m <= KM - 2; ++m)
 #pragma unroll
-        for (int q = 0; m + q <= KM - 2; ++q) x[(v++) * 32] = h2 * a2[m][q];
+        for (int q = 0; m + q <= KM - 2; ++q) part[v++] = he2 * a2[m][q];
+#pragma unroll
+      for (; v < 4 * kXch4; ++v) part[v] = 0.0f;
+      float4 *x = xch + ((k & 1) * 3 + iz) * kXch4 * 32 + lane;
+#pragma unroll
+      for (int q = 0; q < kXch4; ++q)
+        x[q * 32] = make_float4(part[4 * q], part[4 * q + 1], part[4 * q + 2], part[4 * q + 3]);
       __syncthreads();
+      float tot[4 * kXch4];
+      const float4 *x0 = xch + (k & 1) * 3 * kXch4 * 32 + lane;
+#pragma unroll
+      for (int q = 0; q < kXch4; ++q) {
+        const float4 p0 = x0[q * 32], p1 = x0[(kXch4 + q) * 32], p2 = x0[(2 * kXch4 + q) * 32];
+        tot[4 * q] = (p0.x + p1.x) + p2.x;  // the levels in a fixed order
+        tot[4 * q + 1] = (p0.y + p1.y) + p2.y;
+        tot[4 * q + 2] = (p0.z + p1.z) + p2.z;
+        tot[4 * q + 3] = (p0.w + p1.w) + p2.w;
+      }
       float b[3][KM + 1][KM + 1];
 #pragma unroll
       for (int l = 0; l < 3; ++l)
@@ -330,21 +351,28 @@ __global__ void __launch_bounds__(kBlockZ) k_step_z(const float *__restrict__ fi
         for (int m = 0; m <= KM; ++m)
 #pragma unroll
           for (int q = 0; q <= KM; ++q) b[l][m][q] = 0.0f;
-      const float *x0 = xch + (k & 1) * 3 * kXch * 32 + lane;
       v = 0;
 #pragma unroll
       for (int m = 0; m <= KM; ++m)
 #pragma unroll
-        for (int q = 0; m + q <= KM; ++q, ++v)
-          b[0][m][q] = (x0[v * 32] + x0[(kXch + v) * 32]) + x0[(2 * kXch + v) * 32];
+        for (int q = 0; m + q <= KM; ++q) b[0][m][q] = tot[v++];
 #pragma unroll
       for (int m = 0; m <= KM - 2; ++m)
 #pragma unroll
-        for (int q = 0; m + q <= KM - 2; ++q, ++v)
-          b[1][m][q] = (x0[v * 32] + x0[(kXch + v) * 32]) + x0[(2 * kXch + v) * 32];
+        for (int q = 0; m + q <= KM - 2; ++q) b[1][m][q] = tot[v++];
       float d[3][N + 1][N + 1];
       es_coefficients3<NR, N, KM>(b, d, omw, A);
-      hermite_evaluate_level<NR, N>(d, iz, acc, A);
+      float dz[N + 1][N + 1];  // the in-plane coefficients at this level
+#pragma unroll
+      for (int m = 0; m <= N; ++m)
+#pragma unroll
+        for (int q = 0; m + q <= N; ++q) {
+          float t = d[0][m][q] * hz[0];
+          if (m + q + 2 <= N) t = fmaf(d[1][m][q], hz[1], t);
+          if (m + q + 4 <= N) t = fmaf(d[2][m][q], hz[2], t);
+          dz[m][q] = t;
+        }
+      hermite_evaluate<NR, N>(dz, acc, A);
     }
 
     float xs[Q];
