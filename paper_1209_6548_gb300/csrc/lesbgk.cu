@@ -214,7 +214,11 @@ __global__ void __launch_bounds__(kBlock) k_step(const S *__restrict__ fin, S *_
 // meet in the collision, whose moments are sums over all levels (each warp
 // adds its in-plane Hermite moments weighted by 2 He_l(c_z) into shared
 // memory, one barrier per row, every warp sums the three in the same order),
-// and in the wall rule's incoming flux (one more barrier on wall rows).
+// and in the wall rule's incoming flux (one more barrier on wall rows).  The
+// advection does not depend on the collision, so a warp publishes its share,
+// advects, and only then waits for the others: the barrier no longer lines
+// the three warps up for the shuffle-heavy x-sweep (5.41 -> 3.98 ms per
+// 4096^2 step).
 // ---------------------------------------------------------------------------
 constexpr int kBlockZ = 96;  // three warps: one per stored z-level
 constexpr int kXch = 13;     // moments a level contributes: l = 0, m + k <= 3 (10); l = 2, m + k <= 1 (3)
@@ -311,9 +315,8 @@ __global__ void __launch_bounds__(kBlockZ) k_step_z(const float *__restrict__ fi
       for (int g = 0; g < GL; ++g) unpack_group<NR, float>(slot[g * 32], g, ld, A);
     }
 
-    // moments over all levels: this level's share into shared memory, then the sum
-    float acc[Q];
-    float omw;
+    // this level's share of the moments into shared memory; the barrier and
+    // the sum come after the advection, which does not depend on them
     {
       float a2[KM + 1][KM + 1];
       hermite_moments<NR, KM>(fc, a2, A);
@@ -333,6 +336,58 @@ __global__ void __launch_bounds__(kBlockZ) k_step_z(const float *__restrict__ fi
 #pragma unroll
       for (int q = 0; q < kXch4; ++q)
         x[q * 32] = make_float4(part[4 * q], part[4 * q + 1], part[4 * q + 2], part[4 * q + 3]);
+    }
+
+    float f0v[Q], acc[Q];  // f^n_j and the advective change
+    {
+      float xs[Q];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const int iy = a % NR;
+        const float ay = A.ay[iy], ky = A.ky[iy];
+        float diff;
+        const float f0 = fc[a];
+        if (iy >= H) {
+          const float dn = ld[a] - f0;
+          const float sg = minmod(s0[a], dn);
+          diff = fmaf(ky, sg - s1[a], s0[a]);
+          s0[a] = dn;
+          s1[a] = sg;
+          fc[a] = ld[a];
+        } else {
+          const float d1 = s0[a] - f0;
+          const float sg = minmod(d1, ld[a] - s0[a]);
+          diff = fmaf(-ky, sg - s1[a], d1);
+          s1[a] = sg;
+          fc[a] = s0[a];
+          s0[a] = ld[a];
+        }
+        f0v[a] = f0;
+        acc[a] = -ay * diff;
+        xs[a] = SPLIT ? fmaf(-ay, diff, f0) : f0;
+      }
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const int ix = a / NR;
+        const float ax = A.ax[ix], kx = A.kx[ix];
+        const float left = __shfl_up_sync(kFull, xs[a], 1);
+        const float dl = xs[a] - left;
+        const float dr = __shfl_down_sync(kFull, dl, 1);
+        const float sg = minmod(dl, dr);
+        float diff;
+        if (ix >= H) {
+          const float sprev = __shfl_up_sync(kFull, sg, 1);
+          diff = fmaf(kx, sg - sprev, dl);
+        } else {
+          const float snext = __shfl_down_sync(kFull, sg, 1);
+          diff = fmaf(-kx, snext - sg, dr);
+        }
+        acc[a] = fmaf(-ax, diff, acc[a]);
+      }
+    }
+
+    // the moments summed over the levels, then collision and force
+    {
       __syncthreads();
       float tot[4 * kXch4];
       const float4 *x0 = xch + (k & 1) * 3 * kXch4 * 32 + lane;
@@ -351,7 +406,7 @@ __global__ void __launch_bounds__(kBlockZ) k_step_z(const float *__restrict__ fi
         for (int m = 0; m <= KM; ++m)
 #pragma unroll
           for (int q = 0; q <= KM; ++q) b[l][m][q] = 0.0f;
-      v = 0;
+      int v = 0;
 #pragma unroll
       for (int m = 0; m <= KM; ++m)
 #pragma unroll
@@ -361,8 +416,9 @@ __global__ void __launch_bounds__(kBlockZ) k_step_z(const float *__restrict__ fi
 #pragma unroll
         for (int q = 0; m + q <= KM - 2; ++q) b[1][m][q] = tot[v++];
       float d[3][N + 1][N + 1];
+      float omw;
       es_coefficients3<NR, N, KM>(b, d, omw, A);
-      float dz[N + 1][N + 1];  // the in-plane coefficients at this level
+      float dz[N + 1][N + 1];
 #pragma unroll
       for (int m = 0; m <= N; ++m)
 #pragma unroll
@@ -372,52 +428,10 @@ __global__ void __launch_bounds__(kBlockZ) k_step_z(const float *__restrict__ fi
           if (m + q + 4 <= N) t = fmaf(d[2][m][q], hz[2], t);
           dz[m][q] = t;
         }
-      hermite_evaluate<NR, N>(dz, acc, A);
-    }
-
-    float xs[Q];
+      float src[Q];
+      hermite_evaluate<NR, N>(dz, src, A);
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
-      const int iy = a % NR;
-      const float ay = A.ay[iy], ky = A.ky[iy];
-      float diff;
-      const float f0 = fc[a];
-      if (iy >= H) {
-        const float dn = ld[a] - f0;
-        const float sg = minmod(s0[a], dn);
-        diff = fmaf(ky, sg - s1[a], s0[a]);
-        s0[a] = dn;
-        s1[a] = sg;
-        fc[a] = ld[a];
-      } else {
-        const float d1 = s0[a] - f0;
-        const float sg = minmod(d1, ld[a] - s0[a]);
-        diff = fmaf(-ky, sg - s1[a], d1);
-        s1[a] = sg;
-        fc[a] = s0[a];
-        s0[a] = ld[a];
-      }
-      acc[a] = fmaf(omw, f0, fmaf(-ay, diff, acc[a]));
-      xs[a] = SPLIT ? fmaf(-ay, diff, f0) : f0;
-    }
-
-#pragma unroll
-    for (int a = 0; a < Q; ++a) {
-      const int ix = a / NR;
-      const float ax = A.ax[ix], kx = A.kx[ix];
-      const float left = __shfl_up_sync(kFull, xs[a], 1);
-      const float dl = xs[a] - left;
-      const float dr = __shfl_down_sync(kFull, dl, 1);
-      const float sg = minmod(dl, dr);
-      float diff;
-      if (ix >= H) {
-        const float sprev = __shfl_up_sync(kFull, sg, 1);
-        diff = fmaf(kx, sg - sprev, dl);
-      } else {
-        const float snext = __shfl_down_sync(kFull, sg, 1);
-        diff = fmaf(-kx, snext - sg, dr);
-      }
-      acc[a] = fmaf(-ax, diff, acc[a]);
+      for (int a = 0; a < Q; ++a) acc[a] = fmaf(omw, f0v[a], acc[a] + src[a]);
     }
 
     if (A.walls && (j == 0 || j == ny - 1)) {  // uniform over the block
