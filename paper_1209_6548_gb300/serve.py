@@ -51,7 +51,8 @@ class Request:
     completed: float = float("nan")
     steps: int = 0
     residual: float = float("nan")
-    status: str = "pending"  # pending, running, converged, plateau, max_steps
+    status: str = "pending"  # pending, running, converged, plateau, max_steps, rejected
+    error: str = ""          # why a request was rejected (the library's message)
     moments: object = None   # (9, ny, nx) float32 device tensor when kept
 
 
@@ -127,6 +128,8 @@ class WideLane:
         self._next = 0
 
     def try_admit(self, req) -> bool:
+        """Admit when the budget has room; raises LesbgkError for a problem
+        the library refuses."""
         p = L.params_from_problem(req.problem)
         need = L.workspace_size(p)
         if self.used + need > self.budget or len(self.active) >= self.max_solvers:
@@ -191,6 +194,11 @@ class ServingLoop:
             req.status, req.residual, req.completed = v, r, now
             done.append(req)
 
+        def reject(req, err):  # a problem the library refuses ends alone; the others go on
+            req.error = str(err)
+            req.admitted = clock() - t0
+            finish(req, "rejected", float("nan"), req.admitted)
+
         while pending or waiting or waiting_wide or active or wide.active:
             now = clock() - t0
             while pending and pending[0].arrival <= now:
@@ -198,14 +206,24 @@ class ServingLoop:
                 (waiting if fits_batch(req.problem, self.nx) else waiting_wide).append(req)
             while waiting:  # FIFO admission while the pool has room
                 req = waiting[0]
-                slot = bt.try_add(L.params_from_problem(req.problem))
+                try:
+                    slot = bt.try_add(L.params_from_problem(req.problem))
+                except L.LesbgkError as err:
+                    reject(waiting.popleft(), err)
+                    continue
                 if slot is None:
                     break
                 waiting.popleft()
                 req.admitted = clock() - t0
                 req.status = "running"
                 active[slot] = (req, [])
-            while waiting_wide and wide.try_admit(waiting_wide[0]):
+            while waiting_wide:
+                try:
+                    if not wide.try_admit(waiting_wide[0]):
+                        break
+                except L.LesbgkError as err:
+                    reject(waiting_wide.popleft(), err)
+                    continue
                 req = waiting_wide.popleft()
                 req.admitted = clock() - t0
                 req.status = "running"
@@ -282,11 +300,14 @@ def run_plain_fifo(requests, check_every: int = 256, conv: Convergence | None = 
 
 
 def latency_summary(done):
-    lat = np.array([r.completed - r.arrival for r in done])
+    """Latency percentiles and throughput over the solved requests (rejected
+    ones are counted apart)."""
+    solved = [r for r in done if r.status != "rejected"]
+    lat = np.array([r.completed - r.arrival for r in solved])
     if not len(lat):
-        return {}
-    first = min(r.arrival for r in done)
-    last = max(r.completed for r in done)
-    return {"completed": len(done), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "mean_s": float(lat.mean()), "solves_per_s": len(done) / max(last - first, 1e-9),
-            "status": dict(collections.Counter(r.status for r in done))}
+        return {"completed": 0, "rejected": len(done)}
+    first = min(r.arrival for r in solved)
+    last = max(r.completed for r in solved)
+    return {"completed": len(solved), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "solves_per_s": len(solved) / max(last - first, 1e-9),
+            "status": dict(collections.Counter(r.status for r in done)), "rejected": len(done) - len(solved)}

@@ -65,3 +65,26 @@ def test_cavities_run_in_the_wide_lane_beside_the_batch():
     # at most two cavities at a time (the lane's budget): some cavity waited for another to finish
     first_done = min(r.completed for r in cav)
     assert len(cav) <= 2 or any(r.admitted >= first_done for r in cav)
+
+
+def test_invalid_requests_are_rejected_alone():
+    """A request the library refuses (b out of range for the batch, Kn <= 0 for
+    the wide lane) ends as 'rejected' with the library's message; the other
+    requests are served as usual."""
+    from dataclasses import replace
+    probs = S.serving_mix(12, seed=9, ny_hi=48, cavity_share=0.3, cavity_n=24)
+    batch_k = next(k for k, p in enumerate(probs) if S.fits_batch(p, 4))
+    wide_k = next(k for k, p in enumerate(probs) if not S.fits_batch(p, 4))
+    probs[batch_k] = replace(probs[batch_k], b=1.5)
+    probs[wide_k] = replace(probs[wide_k], kn=0.0)
+    reqs = S.poisson_trace(12, 400.0, probs, seed=9)
+    loop = S.ServingLoop(capacity=8, pool_bytes=64 << 20, check_every=128,
+                         conv=S.Convergence(rtol=1e-6, max_steps=60_000))
+    done = loop.run(reqs)
+    assert len(done) == 12
+    bad = {r.rid for r in done if r.status == "rejected"}
+    assert bad == {batch_k, wide_k}, [(r.rid, r.status) for r in done]
+    assert all(r.error for r in done if r.status == "rejected")
+    assert all(r.status in ("converged", "plateau") for r in done if r.rid not in bad)
+    summary = S.latency_summary(done)
+    assert summary["rejected"] == 2 and summary["completed"] == 10
