@@ -12,7 +12,7 @@ as float64 arrays of shape (4, ny, nx) holding rho, u_x, u_y, T.
 """
 from __future__ import annotations
 
-from dataclasses import dataclass, field, replace
+from dataclasses import dataclass, replace
 
 import numpy as np
 

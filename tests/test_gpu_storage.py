@@ -8,7 +8,6 @@ force-driven channel; BF16 3.3e-2 and 3.4e-4).
 """
 from __future__ import annotations
 
-import numpy as np
 import pytest
 
 import oracle as O
