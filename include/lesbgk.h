@@ -186,6 +186,20 @@ int lesbgk_moments(lesbgk *h, float *d_out, double *h_sums, void *stream);
  * moments are staged in the workspace and copied back before returning. */
 int lesbgk_moments_host(lesbgk *h, float *h_out, double *h_sums, void *stream);
 
+/* Steady-state residual of the solve since a snapshot (not in the paper; the
+ * test a serving loop applies):
+ *   r = max over nodes of (|d rho| + |d u_x| + |d u_y| + |d T|) / (steps dt),
+ * d the change of the node's fields since the snapshot, steps the time steps
+ * taken since it.
+ *   d_snap:  DEVICE float[4][ny][nx] (rho, u_x, u_y, T), caller-owned; read as
+ *            the previous snapshot and overwritten with the current fields.
+ *   steps:   time steps since the snapshot; <= 0 only takes the snapshot and
+ *            returns r = NaN.
+ *   h_r:     HOST double, receives r.
+ * Synchronises the stream.  Errors: LESBGK_EINVAL (NULL arguments),
+ * LESBGK_ECUDA. */
+int lesbgk_residual(lesbgk *h, float *d_snap, int64_t steps, double *h_r, void *stream);
+
 /* Copy the current populations (deviations f_a - w_a, float[Q][ny][nx]) into
  * DEVICE memory d_out; with lesbgk_set_populations this is a checkpoint. */
 int lesbgk_get_populations(lesbgk *h, float *d_out, void *stream);

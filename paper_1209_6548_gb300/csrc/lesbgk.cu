@@ -706,6 +706,53 @@ __global__ void __launch_bounds__(kMomBlock) k_moments(const S *__restrict__ f, 
   cs.write_block(partial, NZ == 1 ? 2 : 3);
 }
 
+// Fields rho, u_x, u_y, T of each node against a snapshot: r_max (bits of a
+// non-negative float in *rbits, atomic max) of |d rho| + |d u| + |d T|, and the
+// snapshot overwritten with the current fields (residual of lesbgk_residual).
+template <int NR, class S, int NZ = 1>
+__global__ void __launch_bounds__(kMomBlock) k_residual(const S *__restrict__ f, float *__restrict__ snap,
+                                                        int update_only, unsigned *__restrict__ rbits,
+                                                        const KArgs A) {
+  using Lay = Layout<NR, S, NZ>;
+  constexpr int Q = Lay::Q;
+  const long long cells = A.plane;
+  const long long gstride = (long long)Lay::V * cells;
+  float rmax = 0.0f;
+  for (long long c = blockIdx.x * (long long)kMomBlock + threadIdx.x; c < cells;
+       c += (long long)gridDim.x * kMomBlock) {
+    float F[Q];
+#pragma unroll
+    for (int g = 0; g < Lay::G; ++g) ld_group_s<NR, S>(f + c * Lay::V, gstride, g, F, A);
+    float m[3][3], mzz = 0.0f;
+    if constexpr (NZ == 1) {
+      hermite_moments<NR, 2>(F, m, A);
+    } else {
+      float b[3][3][3];
+      hermite_moments3<NR, 2>(F, b, A);
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = 0; p + q < 3; ++q) m[p][q] = b[0][p][q];
+      mzz = b[1][0][0];
+    }
+    const float rho = 1.0f + m[0][0];
+    const float ir = __frcp_rn(rho);
+    const float ux = m[1][0] * ir, uy = m[0][1] * ir;
+    const float trM = fmaf(-m[1][0], ux, m[2][0]) + fmaf(-m[0][1], uy, m[0][2]) + mzz;
+    const float T = fmaf((NZ == 1 ? 0.5f : 1.0f / 3.0f) * trM, ir, 1.0f);
+    const float d = fabsf(rho - snap[c]) + fabsf(ux - snap[cells + c]) + fabsf(uy - snap[2 * cells + c]) +
+                    fabsf(T - snap[3 * cells + c]);
+    rmax = update_only ? 0.0f : fmaxf(rmax, d != d ? __int_as_float(0x7f800000) : d);  // NaN counts as Inf
+    snap[c] = rho;
+    snap[cells + c] = ux;
+    snap[2 * cells + c] = uy;
+    snap[3 * cells + c] = T;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(kFull, rmax, o));
+  if ((threadIdx.x & 31) == 0 && rmax > 0.0f) atomicMax(rbits, __float_as_uint(rmax));
+}
+
 __global__ void k_reduce_partials(const double *__restrict__ partial, int n, double *__restrict__ sums) {
   // one warp per quantity, fixed order: bitwise reproducible
   const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1109,6 +1156,30 @@ extern "C" int lesbgk_moments_host(lesbgk *h, float *h_out, double *h_sums, void
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "moments to host");
   return finish_sums(h, h_sums, s);
+}
+
+extern "C" int lesbgk_residual(lesbgk *h, float *d_snap, int64_t steps, double *h_r, void *stream) {
+  if (!h || !d_snap || !h_r) return fail(LESBGK_EINVAL, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned *rbits = reinterpret_cast<unsigned *>(h->partial);  // scratch: no moments call runs meanwhile
+  cudaError_t e = cudaMemsetAsync(rbits, 0, sizeof(unsigned), s);
+  const void *f = h->buf[h->cur];
+  if (e == cudaSuccess) {
+    dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto, auto st, auto z) {
+      using S = decltype(st);
+      k_residual<decltype(r)::value, S, decltype(z)::value><<<kMomGrid, kMomBlock, 0, s>>>(
+          static_cast<const S *>(f), d_snap, steps <= 0 ? 1 : 0, rbits, h->args);
+    });
+    e = cudaGetLastError();
+  }
+  unsigned hb = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, rbits, sizeof hb, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "residual");
+  float rmax;
+  std::memcpy(&rmax, &hb, sizeof rmax);
+  *h_r = steps <= 0 ? std::nan("") : (double)rmax / ((double)steps * h->dt);
+  return 0;
 }
 
 extern "C" int lesbgk_get_populations(lesbgk *h, float *d_out, void *stream) {

@@ -29,7 +29,7 @@ MOMENT_NAMES = ("rho", "ux", "uy", "T", "sxx", "sxy", "syy", "qx", "qy")
 SYMBOLS = ("lesbgk_workspace_size", "lesbgk_create", "lesbgk_reinit", "lesbgk_step", "lesbgk_moments",
            "lesbgk_moments_host", "lesbgk_get_populations", "lesbgk_set_populations",
            "lesbgk_set_launch", "lesbgk_get_info", "lesbgk_destroy", "lesbgk_moments_noalloc",
-           "lesbgk_last_error",
+           "lesbgk_last_error", "lesbgk_residual",
            "lesbgk_batch_workspace_size", "lesbgk_batch_slot_bytes", "lesbgk_batch_create", "lesbgk_batch_add",
            "lesbgk_batch_remove", "lesbgk_batch_step", "lesbgk_batch_residuals", "lesbgk_batch_moments",
            "lesbgk_batch_get_populations", "lesbgk_batch_get_info", "lesbgk_batch_set_rows",
@@ -270,6 +270,17 @@ class Solver:
         hs = np.zeros(4)
         moments_host(self.handle, out, hs, self.stream.cuda_stream)
         return out, hs
+
+    def residual(self, snap, steps: int) -> float:
+        """lesbgk_residual: r over the last `steps` steps against `snap`, a
+        (4, ny, nx) float32 CUDA tensor that is overwritten with the current
+        fields (steps <= 0 only takes the snapshot and returns NaN)."""
+        assert snap.is_cuda and snap.dtype == self._torch.float32 and snap.is_contiguous()
+        assert tuple(snap.shape) == (4, self.params.ny, self.params.nx)
+        r = C.c_double()
+        _check(lib().lesbgk_residual(C.c_void_p(self.handle), C.c_void_p(snap.data_ptr()), C.c_int64(int(steps)),
+                                     C.byref(r), C.c_void_p(self.stream.cuda_stream)))
+        return r.value
 
     def populations(self):
         out = self._torch.empty((self.q, self.params.ny, self.params.nx), dtype=self._torch.float32, device="cuda")

@@ -25,7 +25,7 @@ lid-driven cavities of the mix, the D = 3 set, Maxwell or heated walls) go
 to a wide lane: each runs as a single-domain solver on its own CUDA stream,
 so they advance concurrently with the batch; the lane admits them in arrival
 order while its own device-memory budget has room, and checks them with the
-same residual and criterion (computed from lesbgk_moments fields).
+same residual and criterion (lesbgk_residual, one kernel per check).
 
 Everything on the device runs in the library's kernels; this module is the
 scheduler (host bookkeeping only).
@@ -137,7 +137,8 @@ class WideLane:
         st = self._torch.cuda.Stream()
         with self._torch.cuda.stream(st):  # the solver's allocations belong to its stream
             s = L.Solver(p, stream=st)
-            prev = s.moments()[[0, 1, 2, 3]].clone()
+            prev = self._torch.empty((4, p.ny, p.nx), dtype=self._torch.float32, device="cuda")
+        s.residual(prev, 0)  # the first snapshot
         self.used += need
         self.active[self._next] = (req, s, st, prev, [])
         self._next += 1
@@ -149,13 +150,11 @@ class WideLane:
 
     def residuals(self, n: int):
         """key -> residual over the last n steps (max over nodes of
-        |d rho| + |d u| + |d T|, per unit time), as lesbgk_batch_residuals."""
+        |d rho| + |d u| + |d T|, per unit time; lesbgk_residual, the same
+        quantity as lesbgk_batch_residuals)."""
         out = {}
         for key, (req, s, st, prev, hist) in self.active.items():
-            with self._torch.cuda.stream(st):
-                cur = s.moments()[[0, 1, 2, 3]]
-                r = float((cur - prev).abs().sum(dim=0).max().item()) / (n * s.info.dt)
-                prev.copy_(cur)
+            r = s.residual(prev, n)
             hist.append(r)
             out[key] = r
         return out
@@ -266,8 +265,8 @@ class ServingLoop:
 def run_plain_fifo(requests, check_every: int = 256, conv: Convergence | None = None, stream=None,
                    time_budget: float | None = None, clock=time.perf_counter):
     """The baseline: the plain single-domain solver, one request at a time in
-    arrival order, with the same residual and convergence test (the residual
-    from lesbgk_moments fields of consecutive checks)."""
+    arrival order, with the same residual (lesbgk_residual) and convergence
+    test."""
     import torch
     conv = conv or Convergence()
     done = []
@@ -280,14 +279,12 @@ def run_plain_fifo(requests, check_every: int = 256, conv: Convergence | None = 
             break
         req.admitted = clock() - t0
         s = L.Solver(L.params_from_problem(req.problem), stream=stream)
-        dt = s.info.dt
-        prev = s.moments()[[0, 1, 2, 3]].clone()
+        prev = torch.empty((4, req.problem.ny, req.problem.nx), dtype=torch.float32, device="cuda")
+        s.residual(prev, 0)
         hist = []
         while True:
             s.step(check_every)
-            cur = s.moments()[[0, 1, 2, 3]]
-            r = float((cur - prev).abs().sum(dim=0).max().item()) / (check_every * dt)
-            prev = cur.clone()
+            r = s.residual(prev, check_every)
             hist.append(r)
             v = conv.verdict(hist, s.info.steps_done)
             if v is not None:

@@ -563,3 +563,25 @@ def test_collisionless_limit_and_zero_steps():
     s.step(0)
     assert s.info.steps_done == 30
     assert np.array_equal(s.populations().cpu().numpy(), before)
+
+
+# ---------------------------------------------------------------- residual
+@pytest.mark.parametrize("nroots,dim", [(4, 2), (6, 2), (4, 3), (6, 3)])
+def test_residual_against_the_moment_fields(nroots, dim):
+    """lesbgk_residual equals max over nodes of |d rho| + |d u| + |d T| of the
+    moment fields, per unit time; the first call only takes the snapshot."""
+    import torch
+    from dataclasses import replace
+    prob = replace(I.Problem(name="res", nx=45, ny=38, bc_y=I.DIFFUSE, kn=0.1, b=0.5, wall_ux=(-0.05, 0.05),
+                             wall_T=(0.98, 1.03)), nroots=nroots, dim=dim)
+    s = gpu_solver(prob, time_step(prob), None)
+    snap = torch.empty((4, prob.ny, prob.nx), dtype=torch.float32, device="cuda")
+    assert np.isnan(s.residual(snap, 0))
+    m0 = s.moments()[[0, 1, 2, 3]].cpu().numpy().astype(np.float64)
+    assert np.allclose(snap.cpu().numpy(), m0, rtol=0, atol=1e-6)
+    s.step(37)
+    r = s.residual(snap, 37)
+    m1 = s.moments()[[0, 1, 2, 3]].cpu().numpy().astype(np.float64)
+    ref = np.abs(m1 - m0).sum(axis=0).max() / (37 * s.info.dt)
+    assert r == pytest.approx(ref, rel=1e-4, abs=1e-6 / (37 * s.info.dt))
+    assert np.allclose(snap.cpu().numpy(), m1, rtol=0, atol=1e-6)
