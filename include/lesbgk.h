@@ -86,7 +86,7 @@ extern "C" {
 
 typedef struct lesbgk_params {
   uint32_t struct_size; /* sizeof(lesbgk_params), checked */
-  int32_t nroots;       /* Gauss-Hermite roots per axis: 4 (D2Q16) or 6 (D2Q36) */
+  int32_t nroots;       /* Gauss-Hermite roots per axis: 4 (D2Q16, D3Q64) or 6 (D2Q36, D3Q216) */
   int32_t order;        /* Hermite order N of f_ES (3 or 4); 0 = 3 for D2Q16, 4 for D2Q36 */
   int32_t nx, ny;       /* nodes; nx >= 1; ny >= 1 (>= 2 with walls); nx ny < 2^31 */
   int32_t bc_y;         /* LESBGK_PERIODIC or LESBGK_DIFFUSE (walls on rows j = 0 and ny-1) */
@@ -108,13 +108,15 @@ typedef struct lesbgk_params {
                            Specular fractions need FP32 storage; heating takes any storage.
                            The batched solver takes steady, fully diffuse walls only. */
   int32_t dim;          /* dimension D of the velocity set: 0 or 2 = the 2D sets above;
-                           3 = D3Q64 (nroots 4, order 3, FP32 storage) on the same 2D grid,
-                           the paper's D = 3 thermodynamics (C_p = 5/2; Sec. 2.1, Sec. 4).
+                           3 = D3Q64 (nroots 4, order 3) or D3Q216 (nroots 6, order 4, the
+                           paper's 11th-order set), FP32 storage, on the same 2D grid: the
+                           paper's D = 3 thermodynamics (C_p = 5/2; Sec. 2.1, Sec. 4).
                            Nothing varies in z and walls and forces have no z part, so the
                            state stays even in c_z: the library stores the c_z > 0 half
-                           (Q = 32 values per node, population a = iz*16 + ix*4 + iy,
-                           c_z = c[2 + iz]), each value standing for +c_z and -c_z.
-                           T = tr P/(3 rho) and sigma is trace-free in 3D in the moments. */
+                           (Q = nroots^3/2 values per node, population
+                           a = (iz*nroots + ix)*nroots + iy, c_z = c[nroots/2 + iz]), each
+                           value standing for +c_z and -c_z.  T = tr P/(3 rho) and sigma is
+                           trace-free in 3D in the moments.  No walls in x for D3Q216. */
   int32_t bc_x;         /* LESBGK_PERIODIC (default) or LESBGK_DIFFUSE: fully diffuse walls at rest
                            on columns i = 0 and nx-1 (not in the paper, whose flows are uniform
                            in x), at temperatures wall_Tx; ghost columns hold the wall node.

@@ -1,20 +1,23 @@
 // liblesbgk: GB300 (sm_103a) lattice ES-BGK solver behind the C ABI of
 // include/lesbgk.h.  Method: Meng, Zhang, Hadjiconstantinou, Radtke & Shan,
 // arXiv 1209.6548 (Sec. 2.2 lattice ES-BGK equation, Sec. 3.1 scheme,
-// Sec. 3.2 diffuse walls).
+// Sec. 3.2 walls, Sec. 4.2 heated walls).
 //
-// Data layout in HBM: populations as deviations df_a = f_a - w_a, float32, in
-// the grouped layout of Layout<NR> below (vectors of 4 (D2Q16) or 2 (D2Q36)
-// populations of one node that share the sign of c_y), two ping-pong buffers
-// in the caller's workspace.  One time step = one launch of k_step.
+// Data layout in HBM: populations as deviations df_a = f_a - w_a (FP32, or
+// 16-bit relative deviations), in the grouped layout of Layout<NR, S, NZ>
+// (device.cuh: vectors of 2, 4 or 8 populations of one node that share the
+// sign of c_y), two ping-pong buffers in the caller's workspace.  The D = 3
+// sets store their z-even half.  One time step = one launch of k_step (or
+// k_step_z for D3Q216).
 //
 // k_step mapping: a warp owns a strip of 32 consecutive x-nodes (the two
 // outer lanes on each side are halo lanes that load but do not store) and
 // marches up a segment of rows.  x-neighbours come from warp shuffles, the
 // y-stencil is carried in registers from row to row, so each population is
 // read from HBM once and written once per step (plus halo strips/rows that
-// hit in L2).  Per node, all Q populations live in one thread: moments,
-// collision, Hermite evaluation and the wall reduction are in-thread.
+// hit in L2).  Per node, all stored values live in one thread: moments,
+// collision, Hermite evaluation and the wall reduction are in-thread.  The
+// D3Q216 step spreads a node's three stored z-levels over three warps.
 #include <cuda_runtime.h>
 
 #include <cmath>
