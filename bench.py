@@ -673,13 +673,16 @@ def main():
         for _ in range(max(1, args.warmup // 2)):
             e2e_solve()
         barrier()
-        w0 = time.perf_counter()
-        for _ in range(args.steps):
-            e2e_solve()
-        barrier()
-        wsec = max_over_ranks(time.perf_counter() - w0)
+        with ClockSampler(local) as eclk:
+            w0 = time.perf_counter()
+            for _ in range(args.steps):
+                e2e_solve()
+            barrier()
+            wsec = max_over_ranks(time.perf_counter() - w0)
+        ec = eclk.summary()
         e2e = {"value": cells * nsteps * args.steps * world / wsec / 1e6, "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "clocks": {"sm_mhz": ec["sm_mhz"], "reasons": ec["reasons"]}}
 
     peak, peak_kind = measured_peak()
     bytes_per_lup = 2 * q * (4 if args.storage == "f32" else 2)  # q: values stored per node
