@@ -68,7 +68,7 @@ extern "C" {
  * column, so a flow uniform in x stays uniform -- hence reproducible and
  * independent of the launch shape); initial and set populations round to
  * nearest.  16-bit storage is
- * built for the default orders (D2Q16 N = 3, D2Q36 N = 4). */
+ * built for the default orders (D2Q16 N = 3, D2Q36 N = 4) and D3Q64. */
 #define LESBGK_F32 0
 #define LESBGK_F16 1
 #define LESBGK_BF16 2
@@ -108,8 +108,8 @@ typedef struct lesbgk_params {
                            Specular fractions need FP32 storage; heating takes any storage.
                            The batched solver takes steady, fully diffuse walls only. */
   int32_t dim;          /* dimension D of the velocity set: 0 or 2 = the 2D sets above;
-                           3 = D3Q64 (nroots 4, order 3) or D3Q216 (nroots 6, order 4, the
-                           paper's 11th-order set), FP32 storage, on the same 2D grid: the
+                           3 = D3Q64 (nroots 4, order 3; any storage) or D3Q216 (nroots 6,
+                           order 4, the paper's 11th-order set; FP32), on the same 2D grid: the
                            paper's D = 3 thermodynamics (C_p = 5/2; Sec. 2.1, Sec. 4).
                            Nothing varies in z and walls and forces have no z part, so the
                            state stays even in c_z: the library stores the c_z > 0 half

@@ -866,7 +866,9 @@ void dispatch(int nr, int order, int storage, int dim, Fn &&fn) {
   if (dim == 3 && nr == 6) {
     fn(R6{}, N4{}, float{}, Z3{});
   } else if (dim == 3) {
-    fn(R4{}, N3{}, float{}, Z2{});
+    if (storage == LESBGK_F16) fn(R4{}, N3{}, __half{}, Z2{});
+    else if (storage == LESBGK_BF16) fn(R4{}, N3{}, __nv_bfloat16{}, Z2{});
+    else fn(R4{}, N3{}, float{}, Z2{});
   } else if (nr == 4 && order == 3) {
     if (storage == LESBGK_F16) fn(R4{}, N3{}, __half{}, Z1{});
     else if (storage == LESBGK_BF16) fn(R4{}, N3{}, __nv_bfloat16{}, Z1{});

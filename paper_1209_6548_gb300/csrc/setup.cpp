@@ -46,7 +46,8 @@ int check_params(const lesbgk_params *p) {
   if (p->dim != 0 && p->dim != 2 && p->dim != 3) return fail(LESBGK_EINVAL, "dim must be 2 or 3");
   if (p->dim == 3 && !((p->nroots == 4 && order == 3) || (p->nroots == 6 && order == 4)))
     return fail(LESBGK_EINVAL, "D = 3 is built as D3Q64 (nroots 4, order 3) and D3Q216 (nroots 6, order 4)");
-  if (p->dim == 3 && p->storage != LESBGK_F32) return fail(LESBGK_EINVAL, "D = 3 is built for FP32 storage");
+  if (p->dim == 3 && p->nroots == 6 && p->storage != LESBGK_F32)
+    return fail(LESBGK_EINVAL, "D3Q216 is built for FP32 storage");
   if (p->dim == 3 && p->nroots == 6 && p->bc_x != LESBGK_PERIODIC)
     return fail(LESBGK_EINVAL, "walls in x are not built for D3Q216");
   if (p->bc_y != LESBGK_PERIODIC && p->bc_y != LESBGK_DIFFUSE) return fail(LESBGK_EINVAL, "bad bc_y");
@@ -165,11 +166,14 @@ int build_setup(const lesbgk_params &p, int order, const FieldStats *stats, Setu
   // FP16 holds 2^10 (f_a - w_a)/w_a: relative deviations down to 6e-8 stay in
   // its normal range (where stochastic rounding is unbiased) and up to 64 fit
   const double store_scale = p.storage == LESBGK_F16 ? 1024.0 : 1.0;
-  for (int ix = 0; ix < nr; ++ix)
-    for (int iy = 0; iy < nr; ++iy) {
-      A.wq[ix * nr + iy] = (float)(w[ix] * w[iy] / store_scale);
-      A.iwq[ix * nr + iy] = (float)(store_scale / (w[ix] * w[iy]));
-    }
+  const int nzw = (p.dim == 3 && nr * nr * (nr / 2) <= kMaxQ) ? nr / 2 : 1;  // D3Q64: stored z-levels
+  for (int iz = 0; iz < nzw; ++iz)
+    for (int ix = 0; ix < nr; ++ix)
+      for (int iy = 0; iy < nr; ++iy) {
+        const double wa = w[ix] * w[iy] * (p.dim == 3 ? w[nr / 2 + iz] : 1.0);
+        A.wq[(iz * nr + ix) * nr + iy] = (float)(wa / store_scale);
+        A.iwq[(iz * nr + ix) * nr + iy] = (float)(store_scale / wa);
+      }
   A.c_omega = (float)(dt / (p.kn * (1.0 - p.b)));
   A.visc_pow = (float)(1.0 - p.visc_exp);
   A.vmode = p.visc_exp == 0.5 ? 1 : (p.visc_exp == 1.0 ? 2 : 0);

@@ -106,3 +106,28 @@ def test_wall_heating_16bit(storage):
     ref, _ = O.moments(op, O.run(op, O.init(op), 600))
     errs = field_errors(s.moments().cpu().numpy(), ref)
     assert max(v[2] for v in errs.values()) <= BOUND[storage] * 0.02, f"{errs}"
+
+
+@pytest.mark.parametrize("storage", [L.F16, L.BF16])
+def test_d3q64_16bit(storage):
+    """16-bit storage of the D3Q64 set (its z-even half, 3D weights in the
+    scale tables): Couette and rough periodic fields against the 64-velocity
+    oracle within the storage's bound."""
+    from dataclasses import replace
+    prob = replace(I.couette_4x64(), dim=3)
+    dt = time_step(prob)
+    s = solver(prob, storage, dt=dt)
+    s.step(1000)
+    op = oracle_params(prob, dt)
+    ref, _ = O.moments(op, O.run(op, O.init(op), 1000))
+    errs = field_errors(s.moments().cpu().numpy(), ref)
+    assert max(v[0] for v in errs.values()) <= BOUND[storage], errs
+    prob = I.Problem(name="r", nroots=4, dim=3, nx=60, ny=33, bc_y=I.PERIODIC, kn=0.05, b=-0.5, scheme=I.SPLIT)
+    fields = I.random_fields(prob, seed=3, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
+    dt = time_step(prob, fields)
+    s = solver(prob, storage, fields, dt)
+    s.step(5)
+    op = oracle_params(prob, dt)
+    ref, _ = O.moments(op, O.run(op, O.init(op, fields), 5))
+    errs = field_errors(s.moments().cpu().numpy(), ref)
+    assert max(v[0] for v in errs.values()) <= BOUND[storage], errs
