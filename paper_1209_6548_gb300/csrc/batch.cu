@@ -76,6 +76,13 @@ constexpr size_t batch_smem_bytes() {
   return (size_t)(kBBlock / 32) * kBRing * Layout<NR>::G * 32 * Layout<NR>::V * sizeof(float);
 }
 
+// neighbour lanes inside a lane group of W lanes (periodic in x)
+struct GroupLanes {
+  int srcL, srcR;
+  __device__ __forceinline__ float left(float v) const { return __shfl_sync(kFull, v, srcL); }
+  __device__ __forceinline__ float right(float v) const { return __shfl_sync(kFull, v, srcR); }
+};
+
 // One time step of every work item of a lattice class.
 template <int NR, int N, int W>
 __global__ void __launch_bounds__(kBBlock) k_batch_step(const BatchArgs B, const int par) {
@@ -178,45 +185,45 @@ __global__ void __launch_bounds__(kBBlock) k_batch_step(const BatchArgs B, const
     float omw;
     collide<NR, N>(fc, acc, omw, B.lat, P);
     float xs[Q];
+    const GroupLanes nb{srcL, srcR};
+    if constexpr (NR == 4) {  // packed pairs a, a+1 (same ix, c_y of one sign)
+      const float2 omw2 = make_float2(omw, omw);
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
-      const int iy = a % NR;
-      float diff;
-      const float f0 = fc[a];
-      if (iy >= H) {
-        const float dn = ld[a] - f0;
-        const float sg = minmod(s0[a], dn);
-        diff = fmaf(ky[iy], sg - s1[a], s0[a]);
-        s0[a] = dn;
-        s1[a] = sg;
-        fc[a] = ld[a];
-      } else {
-        const float d1 = s0[a] - f0;
-        const float sg = minmod(d1, ld[a] - s0[a]);
-        diff = fmaf(-ky[iy], sg - s1[a], d1);
-        s1[a] = sg;
-        fc[a] = s0[a];
-        s0[a] = ld[a];
+      for (int a = 0; a < Q; a += 2) {
+        const int iy = a % NR;
+        const float2 nay = make_float2(-ay[iy], -ay[iy + 1]);
+        float2 f0;
+        const float2 diff = yflux2(iy >= H, a, fc, s0, s1, ld, make_float2(ky[iy], ky[iy + 1]), f0);
+        const float2 ac = fma2(omw2, f0, fma2(nay, diff, make_float2(acc[a], acc[a + 1])));
+        const float2 x2 = split ? fma2(nay, diff, f0) : f0;
+        acc[a] = ac.x;
+        acc[a + 1] = ac.y;
+        xs[a] = x2.x;
+        xs[a + 1] = x2.y;
       }
-      acc[a] = fmaf(omw, f0, fmaf(-ay[iy], diff, acc[a]));
-      xs[a] = split ? fmaf(-ay[iy], diff, f0) : f0;
-    }
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
-      const int ix = a / NR;
-      const float left = __shfl_sync(kFull, xs[a], srcL);
-      const float dl = xs[a] - left;
-      const float dr = __shfl_sync(kFull, dl, srcR);
-      const float sg = minmod(dl, dr);
-      float diff;
-      if (ix >= H) {
-        const float sprev = __shfl_sync(kFull, sg, srcL);
-        diff = fmaf(kx[ix], sg - sprev, dl);
-      } else {
-        const float snext = __shfl_sync(kFull, sg, srcR);
-        diff = fmaf(-kx[ix], snext - sg, dr);
+      for (int a = 0; a < Q; a += 2) {
+        const int ix = a / NR;
+        const float2 nax = make_float2(-ax[ix], -ax[ix]);
+        const float2 diff = xflux2(ix >= H, make_float2(xs[a], xs[a + 1]), make_float2(kx[ix], kx[ix]), nb);
+        const float2 ac = fma2(nax, diff, make_float2(acc[a], acc[a + 1]));
+        acc[a] = ac.x;
+        acc[a + 1] = ac.y;
       }
-      acc[a] = fmaf(-ax[ix], diff, acc[a]);
+    } else {  // D2Q36: one population at a time (the pair constants would spill)
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const int iy = a % NR;
+        float f0;
+        const float diff = yflux(iy >= H, a, fc, s0, s1, ld, ky[iy], f0);
+        acc[a] = fmaf(omw, f0, fmaf(-ay[iy], diff, acc[a]));
+        xs[a] = split ? fmaf(-ay[iy], diff, f0) : f0;
+      }
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const int ix = a / NR;
+        acc[a] = fmaf(-ax[ix], xflux(ix >= H, xs[a], kx[ix], nb), acc[a]);
+      }
     }
     if (walls && (j == 0 || j == ny - 1)) wall_fix<NR, false>(acc, (j == 0) ? 0 : 1, B.lat, D);
     if (k < rows) {

@@ -38,6 +38,18 @@ __device__ __forceinline__ float minmod(float a, float b) {
   return __uint_as_float(__float_as_uint(t) | (__float_as_uint(a) & 0x80000000u));
 }
 
+// Packed FP32 pairs (sm_100 family): one instruction, two independently
+// rounded results, each bitwise equal to the scalar operation.  The pair
+// travels as one 64-bit register; the subtraction has no intrinsic.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  float2 r;
+  asm("{\n.reg .b64 ra, rb, rr;\nmov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\n"
+      "sub.rn.f32x2 rr, ra, rb;\nmov.b64 {%0, %1}, rr;\n}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 // Hardware approximations (MUFU): relative error ~1 ulp, far below the FP32
 // rounding of the moments they act on.
 __device__ __forceinline__ float fast_rcp(float x) {
@@ -51,6 +63,108 @@ __device__ __forceinline__ float fast_sqrt(float x) {
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+
+// ---------------------------------------------------------------------------
+// Second-order TVD advection with the minmod limiter (Sec. 3.1), per
+// population, in units of the Courant number: the update is
+// f -= (c dt/dh) diff with diff = F_{i+1/2} - F_{i-1/2} divided by c, where
+// F_{i+1/2} = f_i + k sigma_i for c > 0 and f_{i+1} - k sigma_{i+1} for c < 0,
+// k = (1 - |c| dt/dh)/2 and sigma_i = minmod(f_i - f_{i-1}, f_{i+1} - f_i).
+//
+// The y-sweep marches up the rows and carries a stencil per population:
+//   c_y > 0: s0 = f_j - f_{j-1}, s1 = sigma_{j-1}, fc = f_j
+//   c_y < 0: s0 = f_{j+1},       s1 = sigma_j,     fc = f_j
+// ld holds the row entering the stencil: f_{j+1} (c_y > 0) or f_{j+2}
+// (c_y < 0).  yflux returns diff at row j, sets f0 = f_j and moves the
+// stencil on by one row.  The packed forms treat populations a and a+1 (the
+// same ix, neighbouring iy, so c_y of one sign when the caller pairs them) as
+// one f32x2 pair; each of their operations is the scalar one, term for term.
+// ---------------------------------------------------------------------------
+template <int Q>
+__device__ __forceinline__ float yflux(bool up, int a, float (&fc)[Q], float (&s0)[Q], float (&s1)[Q],
+                                       const float (&ld)[Q], float ky, float &f0) {
+  f0 = fc[a];
+  float diff;
+  if (up) {  // c_y > 0
+    const float dn = ld[a] - f0;
+    const float sg = minmod(s0[a], dn);
+    diff = fmaf(ky, sg - s1[a], s0[a]);
+    s0[a] = dn;
+    s1[a] = sg;
+    fc[a] = ld[a];
+  } else {  // c_y < 0
+    const float d1 = s0[a] - f0;
+    const float sg = minmod(d1, ld[a] - s0[a]);
+    diff = fmaf(-ky, sg - s1[a], d1);
+    s1[a] = sg;
+    fc[a] = s0[a];
+    s0[a] = ld[a];
+  }
+  return diff;
+}
+
+template <int Q>
+__device__ __forceinline__ float2 yflux2(bool up, int a, float (&fc)[Q], float (&s0)[Q], float (&s1)[Q],
+                                         const float (&ld)[Q], float2 ky, float2 &f0) {
+  f0 = make_float2(fc[a], fc[a + 1]);
+  const float2 l2 = make_float2(ld[a], ld[a + 1]);
+  const float2 S0 = make_float2(s0[a], s0[a + 1]);
+  const float2 S1 = make_float2(s1[a], s1[a + 1]);
+  float2 diff, sg;
+  if (up) {
+    const float2 dn = sub2(l2, f0);
+    sg = make_float2(minmod(S0.x, dn.x), minmod(S0.y, dn.y));
+    diff = fma2(ky, sub2(sg, S1), S0);
+    s0[a] = dn.x;
+    s0[a + 1] = dn.y;
+    fc[a] = l2.x;
+    fc[a + 1] = l2.y;
+  } else {
+    const float2 d1 = sub2(S0, f0);
+    const float2 dr = sub2(l2, S0);
+    sg = make_float2(minmod(d1.x, dr.x), minmod(d1.y, dr.y));
+    diff = fma2(ky, sub2(S1, sg), d1);  // (-k)(sg - s1) = k (s1 - sg), exactly
+    fc[a] = S0.x;
+    fc[a + 1] = S0.y;
+    s0[a] = l2.x;
+    s0[a + 1] = l2.y;
+  }
+  s1[a] = sg.x;
+  s1[a + 1] = sg.y;
+  return diff;
+}
+
+// x-sweep of f_i (xflux) or of a pair x2 = (f_i of population a, of a+1)
+// with c_x of one sign (right: c_x > 0).  The neighbours f_{i-1}, f_{i+1}
+// and the slopes of the adjacent nodes come from the adjacent lanes:
+// nb.left(v) / nb.right(v) return v of the lane holding node i-1 / i+1.
+template <class NB>
+__device__ __forceinline__ float2 xflux2(bool right, float2 x2, float2 kx, const NB &nb) {
+  const float2 dl = sub2(x2, make_float2(nb.left(x2.x), nb.left(x2.y)));  // f_i - f_{i-1}
+  const float2 dr = make_float2(nb.right(dl.x), nb.right(dl.y));           // f_{i+1} - f_i
+  const float2 sg = make_float2(minmod(dl.x, dr.x), minmod(dl.y, dr.y));   // sigma_i
+  if (right) {
+    const float2 sp = make_float2(nb.left(sg.x), nb.left(sg.y));
+    return fma2(kx, sub2(sg, sp), dl);
+  }
+  const float2 sn = make_float2(nb.right(sg.x), nb.right(sg.y));
+  return fma2(kx, sub2(sg, sn), dr);  // (-k)(sigma_{i+1} - sigma_i) = k (sigma_i - sigma_{i+1})
+}
+
+template <class NB>
+__device__ __forceinline__ float xflux(bool right, float x, float kx, const NB &nb) {
+  const float dl = x - nb.left(x);
+  const float dr = nb.right(dl);
+  const float sg = minmod(dl, dr);
+  if (right) return fmaf(kx, sg - nb.left(sg), dl);
+  return fmaf(-kx, nb.right(sg) - sg, dr);
+}
+
+// neighbour lanes of a warp-wide strip
+struct StripLanes {
+  __device__ __forceinline__ float left(float v) const { return __shfl_up_sync(kFull, v, 1); }
+  __device__ __forceinline__ float right(float v) const { return __shfl_down_sync(kFull, v, 1); }
+};
 
 __device__ __forceinline__ int map_row(int j, int ny, int walls) {
   if (walls) return j < 0 ? 0 : (j >= ny ? ny - 1 : j);  // ghost rows = wall node

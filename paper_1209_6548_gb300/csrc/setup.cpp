@@ -162,6 +162,9 @@ int build_setup(const lesbgk_params &p, int order, const FieldStats *stats, Setu
     A.kx[i] = (float)(0.5 * (1.0 - std::fabs(c[i]) * dt / h->dx));
     A.ay[i] = (float)(c[i] * dt / h->dy);
     A.ky[i] = (float)(0.5 * (1.0 - std::fabs(c[i]) * dt / h->dy));
+    A.nay[i] = -A.ay[i];
+    A.kx2[i][0] = A.kx2[i][1] = A.kx[i];
+    A.nax2[i][0] = A.nax2[i][1] = -A.ax[i];
   }
   // FP16 holds 2^10 (f_a - w_a)/w_a: relative deviations down to 6e-8 stay in
   // its normal range (where stochastic rounding is unbiased) and up to 64 fit

@@ -20,7 +20,13 @@ struct KArgs {
   float he[kMaxR][kMaxN + 1];  // He_m(c_i)
   float hw[kMaxR][kMaxN + 1];  // w_i He_m(c_i) / m!
   float ax[kMaxR], kx[kMaxR];  // c_i dt/dx and (1 - |c_i| dt/dx)/2
-  float ay[kMaxR], ky[kMaxR];  // same along y
+  alignas(8) float ay[kMaxR];  // same along y
+  alignas(8) float ky[kMaxR];
+  // pair operands of the packed (f32x2) advection, whose pairs are the
+  // populations a, a+1 (the same ix, neighbouring iy)
+  alignas(8) float nay[kMaxR];      // -ay
+  alignas(8) float kx2[kMaxR][2];   // {kx, kx}
+  alignas(8) float nax2[kMaxR][2];  // {-ax, -ax}
   float wS[2][kMaxWQ];         // wall equilibrium S_a(T_w, u_w) per stored population, [0] bottom, [1] top
   float wSdev[2][kMaxWQ];      // S_a - w_a
   float wA[2], wB[2];          // sum_out |c_y|(S-w) and 1/sum_out |c_y| S
