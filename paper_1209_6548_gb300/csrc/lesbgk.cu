@@ -849,8 +849,8 @@ constexpr size_t step_smem_bytes() {
 
 // Call fn(NR, N, storage tag, NZ) with compile-time constants for the built
 // combinations: every (nroots, order) of the 2D sets in FP32, the default
-// orders also in FP16 and BF16; the D = 3 set as D3Q64, N = 3, FP32 (NZ = 2
-// stored z-levels; NZ = 1 for the 2D sets).
+// orders also in FP16 and BF16 (NZ = 1); D3Q64, N = 3, in FP32, FP16 and BF16
+// (NZ = 2 stored z-levels); D3Q216, N = 4, in FP32 (NZ = 3).
 template <class Fn>
 void dispatch(int nr, int order, int storage, int dim, Fn &&fn) {
   using R4 = std::integral_constant<int, 4>;
