@@ -341,16 +341,18 @@ def test_d2q36_order3():
 
 
 # ---------------------------------------------------------------- wall models
+@pytest.mark.parametrize("scheme", [I.UNSPLIT, I.SPLIT])
 @pytest.mark.parametrize("spec", [0.3, 1.0])
-def test_maxwell_walls(spec):
+def test_maxwell_walls(spec, scheme):
     """Maxwell walls with accommodation 1 - spec (Sec. 3.2's model), moving and
-    at two temperatures, rough interior."""
+    at two temperatures, rough interior; both update schemes (each its own
+    kernel instantiation)."""
     prob = I.Problem(name="mw", nx=32, ny=30, bc_y=I.DIFFUSE, kn=0.1, b=-0.5, wall_ux=(-0.05, 0.05),
-                     wall_T=(0.97, 1.04), wall_specular=spec)
+                     wall_T=(0.97, 1.04), wall_specular=spec, scheme=scheme)
     fields = I.random_fields(prob, seed=12, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
     res, *_ = run_pair(prob, fields, [1, 10])
     for n, g, r, *_ in res:
-        assert_fields_close(g, r, what=f"spec {spec} step {n}")
+        assert_fields_close(g, r, what=f"spec {spec} scheme {scheme} step {n}")
 
 
 @pytest.mark.parametrize("kn,st", [(0.1, 0.5553603672697958), (0.5, 1.1107207345395915)])
@@ -426,13 +428,15 @@ def test_d3_walls_force_rough(b, nroots):
 
 
 @pytest.mark.parametrize("nroots", [4, 6])
-def test_d3_maxwell_walls_and_heating(nroots):
-    """Specular share 0.3 and heated walls (Sec. 3.2, Sec. 4.2) with D = 3."""
+@pytest.mark.parametrize("scheme", [I.UNSPLIT, I.SPLIT])
+def test_d3_maxwell_walls_and_heating(scheme, nroots):
+    """Specular share 0.3 and heated walls (Sec. 3.2, Sec. 4.2) with D = 3,
+    both update schemes."""
     prob = d3(I.Problem(name="mh", nx=8, ny=40, bc_y=I.DIFFUSE, kn=0.2, b=-0.5, wall_specular=0.3,
-                        wall_T_amp=0.02, wall_T_freq=0.5553603672697958), nroots)
+                        wall_T_amp=0.02, wall_T_freq=0.5553603672697958, scheme=scheme), nroots)
     res, *_ = run_pair(prob, None, [1, 50, 300])
     for n, g, r, *_ in res:
-        assert_fields_close(g, r, what=f"d3q{nroots ** 3} maxwell+heating step {n}")
+        assert_fields_close(g, r, what=f"d3q{nroots ** 3} maxwell+heating scheme {scheme} step {n}")
 
 
 @pytest.mark.parametrize("nroots", [4, 6])
@@ -482,21 +486,28 @@ def test_lid_driven_cavity(nroots, dim):
     assert np.max(np.abs(res[-1][2][2])) > 1e-3  # the lid set up a vortex
 
 
+@pytest.mark.parametrize("nroots,dim", [(4, 2), (6, 2), (4, 3)])
 @pytest.mark.parametrize("scheme", [I.UNSPLIT, I.SPLIT])
-def test_walls_in_x_rough(scheme):
+def test_walls_in_x_rough(scheme, nroots, dim):
     """Rough fields in a box with heated walls on all sides and a lid, and in
-    a channel walled in x only (periodic y); populations element by element."""
-    for prob in (I.Problem(name="box", nx=60, ny=33, bc_y=I.DIFFUSE, bc_x=I.DIFFUSE, kn=0.1, b=0.5,
-                           wall_ux=(0.0, 0.05), wall_T=(0.98, 1.02), wall_Tx=(1.03, 0.97), scheme=scheme),
-                 I.Problem(name="xchan", nx=29, ny=30, bc_y=I.PERIODIC, bc_x=I.DIFFUSE, kn=0.05, b=-0.5,
-                           wall_Tx=(0.97, 1.04), g=(0.0, 1e-3), scheme=scheme)):
+    a channel walled in x only (periodic y); populations element by element,
+    on every set with walls in x and in both update schemes."""
+    for prob in (I.Problem(name="box", nroots=nroots, dim=dim, nx=60, ny=33, bc_y=I.DIFFUSE, bc_x=I.DIFFUSE,
+                           kn=0.1, b=0.5, wall_ux=(0.0, 0.05), wall_T=(0.98, 1.02), wall_Tx=(1.03, 0.97),
+                           scheme=scheme),
+                 I.Problem(name="xchan", nroots=nroots, dim=dim, nx=29, ny=30, bc_y=I.PERIODIC, bc_x=I.DIFFUSE,
+                           kn=0.05, b=-0.5, wall_Tx=(0.97, 1.04), g=(0.0, 1e-3), scheme=scheme)):
         fields = I.random_fields(prob, seed=prob.nx + 3, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
         res, *_ = run_pair(prob, fields, [1, 10])
         for n, g, r, gp, fp in res:
-            assert_fields_close(g, r, what=f"{prob.name} step {n}")
-            w = O.velocity_set(4)[2][:, None, None]
-            err = np.max(np.abs(gp - (fp - w)))
-            assert err <= 2e-6 * np.max(np.abs(fp - w)), f"{prob.name} populations {err:.3e}"
+            what = f"{prob.name} nroots={nroots} D={dim} step {n}"
+            assert_fields_close(g, r, what=what)
+            if dim == 3:
+                assert_d3_populations(gp, fp, what, nroots)
+            else:
+                w = O.velocity_set(nroots)[2][:, None, None]
+                err = np.max(np.abs(gp - (fp - w)))
+                assert err <= 2e-6 * np.max(np.abs(fp - w)), f"{what} populations {err:.3e}"
 
 
 def test_cavity_of_two_by_two_is_all_corners():
