@@ -322,37 +322,40 @@ def test_d2q36_couette_walls_force():
         assert_fields_close(g, r, what=f"d2q36 couette step {n}")
 
 
-def test_d2q16_order4():
+@pytest.mark.parametrize("scheme", [I.UNSPLIT, I.SPLIT])
+def test_d2q16_order4(scheme):
     """N = 4 on D2Q16 (projection not exact, still conservative)."""
     prob = I.Problem(name="q16n4", nroots=4, order=4, nx=30, ny=25, bc_y=I.DIFFUSE, kn=0.1, b=0.5,
-                     wall_ux=(0.0, 0.05), g=(0.0, -1e-3))
+                     wall_ux=(0.0, 0.05), g=(0.0, -1e-3), scheme=scheme)
     fields = I.random_fields(prob, seed=4, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
     res, *_ = run_pair(prob, fields, [1, 10])
     for n, g, r, *_ in res:
         assert_fields_close(g, r, what=f"d2q16 N=4 step {n}")
 
 
-def test_d2q36_order3():
+@pytest.mark.parametrize("scheme", [I.UNSPLIT, I.SPLIT])
+def test_d2q36_order3(scheme):
     prob = I.Problem(name="q36n3", nroots=6, order=3, nx=12, ny=20, bc_y=I.DIFFUSE, kn=0.2, b=0.0,
-                     wall_T=(0.95, 1.05))
+                     wall_T=(0.95, 1.05), scheme=scheme)
     res, *_ = run_pair(prob, None, [1, 100])
     for n, g, r, *_ in res:
         assert_fields_close(g, r, what=f"d2q36 N=3 step {n}")
 
 
 # ---------------------------------------------------------------- wall models
+@pytest.mark.parametrize("nroots", [4, 6])
 @pytest.mark.parametrize("scheme", [I.UNSPLIT, I.SPLIT])
 @pytest.mark.parametrize("spec", [0.3, 1.0])
-def test_maxwell_walls(spec, scheme):
+def test_maxwell_walls(spec, scheme, nroots):
     """Maxwell walls with accommodation 1 - spec (Sec. 3.2's model), moving and
     at two temperatures, rough interior; both update schemes (each its own
     kernel instantiation)."""
-    prob = I.Problem(name="mw", nx=32, ny=30, bc_y=I.DIFFUSE, kn=0.1, b=-0.5, wall_ux=(-0.05, 0.05),
-                     wall_T=(0.97, 1.04), wall_specular=spec, scheme=scheme)
+    prob = I.Problem(name="mw", nroots=nroots, nx=32, ny=30, bc_y=I.DIFFUSE, kn=0.1, b=-0.5,
+                     wall_ux=(-0.05, 0.05), wall_T=(0.97, 1.04), wall_specular=spec, scheme=scheme)
     fields = I.random_fields(prob, seed=12, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
     res, *_ = run_pair(prob, fields, [1, 10])
     for n, g, r, *_ in res:
-        assert_fields_close(g, r, what=f"spec {spec} scheme {scheme} step {n}")
+        assert_fields_close(g, r, what=f"nroots {nroots} spec {spec} scheme {scheme} step {n}")
 
 
 @pytest.mark.parametrize("kn,st", [(0.1, 0.5553603672697958), (0.5, 1.1107207345395915)])

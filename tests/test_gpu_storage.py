@@ -50,8 +50,9 @@ def test_couette_against_oracle(storage):
 
 @pytest.mark.parametrize("storage", [L.F16, L.BF16])
 @pytest.mark.parametrize("nroots", [4, 6])
-def test_rough_fields_short_run(storage, nroots):
-    prob = I.Problem(name="r", nroots=nroots, nx=60, ny=33, bc_y=I.PERIODIC, kn=0.05, b=-0.5, scheme=I.SPLIT)
+@pytest.mark.parametrize("scheme", [I.UNSPLIT, I.SPLIT])
+def test_rough_fields_short_run(storage, nroots, scheme):
+    prob = I.Problem(name="r", nroots=nroots, nx=60, ny=33, bc_y=I.PERIODIC, kn=0.05, b=-0.5, scheme=scheme)
     fields = I.random_fields(prob, seed=nroots, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
     dt = time_step(prob, fields)
     s = solver(prob, storage, fields, dt)
