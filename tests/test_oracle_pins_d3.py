@@ -178,29 +178,31 @@ def test_d3_oracle_moments_match_numpy():
     assert np.allclose(P, Pn, atol=1e-15) and np.allclose(u, un, atol=1e-16)
 
 
+@pytest.mark.parametrize("nroots,order", [(4, 3), (6, 4)])
 @pytest.mark.parametrize("b", [-0.5, 0.0, 0.5])
-def test_d3_b_zero_is_bgk_and_tau(b):
+def test_d3_b_zero_is_bgk_and_tau(b, nroots, order):
     """tau = (Kn/Pr) T^varpi/(rho T) with the D = 3 temperature; at b = 0,
     f_ES is rho S(T, u) of Eq. (feq0) with D = 3."""
-    p = params3(4, 3, b, kn=0.2, visc=0.7)
-    cx, cy, cz, _ = O.velocity_set_d(4, 3)
-    f = noneq3(4, 3, 11)
-    f = 0.5 * (f + f[mirror_z(4)])  # even in c_z: u_z = 0
+    p = params3(nroots, order, b, kn=0.2, visc=0.7)
+    cx, cy, cz, _ = O.velocity_set_d(nroots, 3)
+    f = noneq3(nroots, order, 11)
+    f = 0.5 * (f + f[mirror_z(nroots)])  # even in c_z: u_z = 0
     fes, _, tau = O.cell_terms(p, f)
     rho, u, _, T, _ = moments3(f, cx, cy, cz)
     assert abs(tau - 0.2 * (1 - b) * T ** 0.7 / (rho * T)) < 1e-15
     if b == 0.0:
         assert abs(u[2]) < 1e-16
-        assert np.allclose(fes, rho * O.feq0(4, 3, T, u[0], u[1], dim=3), atol=1e-15)
+        assert np.allclose(fes, rho * O.feq0(nroots, order, T, u[0], u[1], dim=3), atol=1e-15)
 
 
+@pytest.mark.parametrize("nroots,order", [(4, 3), (6, 4)])
 @pytest.mark.parametrize("b", [-0.5, 0.5])
-def test_d3_prandtl_number_from_relaxation(b):
+def test_d3_prandtl_number_from_relaxation(b, nroots, order):
     """One homogeneous step at u = 0: (1 - r_q)/(1 - r_sigma) = 1/(1 - b)."""
     dt = 2e-3
-    p = params3(4, 3, b, kn=0.1, dt=dt)
-    cx, cy, cz, w = O.velocity_set_d(4, 3)
-    f = O.feq0(4, 3, 1.0, 0.0, 0.0, dim=3)
+    p = params3(nroots, order, b, kn=0.1, dt=dt)
+    cx, cy, cz, w = O.velocity_set_d(nroots, 3)
+    f = O.feq0(nroots, order, 1.0, 0.0, 0.0, dim=3)
     pert = w * (0.01 * cx * cy + 0.01 * cx * (cx * cx + cy * cy + cz * cz - 5.0))
     f = f + pert - w * np.sum(pert * cx) / np.sum(w * cx * cx) * cx
     _, u0, P0, _, q0 = moments3(f, cx, cy, cz)
@@ -210,13 +212,14 @@ def test_d3_prandtl_number_from_relaxation(b):
     assert abs((1 - q1[0] / q0[0]) / (1 - P1[0, 1] / P0[0, 1]) - 1.0 / (1.0 - b)) < 1e-9
 
 
-def test_d3_force_moments():
+@pytest.mark.parametrize("nroots,order", [(4, 3), (6, 4)])
+def test_d3_force_moments(nroots, order):
     """Projected force with g_z = 0: sum g_a = 0, sum g_a c = rho g (no z
     component), sum g_a c^2 = 2 rho u.g."""
     g = (3e-3, -1e-3)
-    p = params3(4, 3, 0.0, g=g)
-    cx, cy, cz, _ = O.velocity_set_d(4, 3)
-    f = noneq3(4, 3, 4)
+    p = params3(nroots, order, 0.0, g=g)
+    cx, cy, cz, _ = O.velocity_set_d(nroots, 3)
+    f = noneq3(nroots, order, 4)
     _, gf, _ = O.cell_terms(p, f)
     rho, u, *_ = moments3(f, cx, cy, cz)
     assert abs(gf.sum()) < 1e-16
@@ -226,11 +229,12 @@ def test_d3_force_moments():
 
 
 # ---------------------------------------------------------------- whole steps
-def test_d3_uniform_equilibrium_fixed_point_and_conservation():
+@pytest.mark.parametrize("nroots", [4, 6])
+def test_d3_uniform_equilibrium_fixed_point_and_conservation(nroots):
     """A uniform rho S(T, u) is a fixed point; rough periodic fields keep mass,
     x/y momentum and energy (1/2 sum f c^2 with c_z^2) to rounding; the energy
     at rest equilibrium is (D/2) rho T per node with D = 3."""
-    prob = Problem(name="t", nroots=4, dim=3, nx=6, ny=5, bc_y=PERIODIC, kn=0.05, b=-0.5)
+    prob = Problem(name="t", nroots=nroots, dim=3, nx=6, ny=5, bc_y=PERIODIC, kn=0.05, b=-0.5)
     fields = np.zeros((4, 5, 6))
     fields[0], fields[1], fields[2], fields[3] = 1.2, 0.05, -0.03, 1.04
     p = oracle_params(prob, 2e-3)
@@ -246,25 +250,26 @@ def test_d3_uniform_equilibrium_fixed_point_and_conservation():
     assert np.allclose(s1, s0, rtol=0, atol=1e-12)
 
 
-def test_d3_cz_is_not_advected_and_symmetry_in_cz_is_kept():
+@pytest.mark.parametrize("nroots", [4, 6])
+def test_d3_cz_is_not_advected_and_symmetry_in_cz_is_kept(nroots):
     """The grid is two-dimensional: populations that differ only in c_z have
     the same x/y transport, and a state even in c_z (u_z = 0, g_z = 0, walls
     at rest in z) stays even through steps with walls, force, Maxwell walls
     and heating (to rounding).  Catches c_z entering the advection or a wall
     mirror that also flips c_z."""
-    prob = Problem(name="t", nroots=4, dim=3, nx=8, ny=12, bc_y=DIFFUSE, kn=0.1, b=-0.5, wall_ux=(-0.05, 0.05),
+    prob = Problem(name="t", nroots=nroots, dim=3, nx=8, ny=12, bc_y=DIFFUSE, kn=0.1, b=-0.5, wall_ux=(-0.05, 0.05),
                    wall_T=(0.97, 1.04), g=(1e-3, 2e-4), wall_specular=0.3, wall_T_amp=0.01, wall_T_freq=0.7)
     fields = random_fields(prob, seed=8, amp_u=0.03, amp_T=0.03, amp_rho=0.03)
     p = oracle_params(prob, time_step(prob, fields))
     f = O.init(p, fields)
-    mz = mirror_z(4)
+    mz = mirror_z(nroots)
     assert np.max(np.abs(f - f[mz])) < 1e-16
     f = O.run(p, f, 20)
     assert np.max(np.abs(f - f[mz])) < 1e-14
     # zero z-momentum and zero normal mass flux at the walls
-    *_, cz, _ = O.velocity_set_d(4, 3)
+    *_, cz, _ = O.velocity_set_d(nroots, 3)
     assert np.abs(np.einsum("a,aji->ji", cz, f)).max() < 1e-14
-    _, cy, _, _ = O.velocity_set_d(4, 3)
+    _, cy, _, _ = O.velocity_set_d(nroots, 3)
     for j in (0, prob.ny - 1):
         assert np.abs(np.einsum("a,ai->i", cy, f[:, j, :])).max() < 1e-15
 
