@@ -19,7 +19,7 @@ from numpy.polynomial import hermite_e as HE
 
 import oracle as O
 from paper_1209_6548_gb300.inputs import PERIODIC, DIFFUSE, Problem
-from tests.common import oracle_params, time_step
+from tests.common import DEFAULT_ORDER, oracle_params, time_step
 
 
 def he(m, x):
@@ -226,19 +226,21 @@ def _moments_np(f, cx, cy):
     return {"rho": rho, "u": u, "T": T, "q": q}, P
 
 
+@pytest.mark.parametrize("nroots", [4, 6])
 @pytest.mark.parametrize("b", [-0.5, 0.0, 0.5])
-def test_b_zero_and_tau(b):
+def test_b_zero_and_tau(b, nroots):
     """tau = (Kn/Pr) T^varpi/(rho T), Pr = 1/(1-b); at b = 0 f_ES is the
     truncated Maxwellian Eq. (feq0) of f's rho, u, T (BGK special case)."""
-    p = _params(4, 3, b, kn=0.2, visc=0.7)
-    cx, cy, _ = O.velocity_set(4)
-    f = _noneq_f(4, 3, 11)
+    order = DEFAULT_ORDER[nroots]
+    p = _params(nroots, order, b, kn=0.2, visc=0.7)
+    cx, cy, _ = O.velocity_set(nroots)
+    f = _noneq_f(nroots, order, 11)
     fes, _, tau = O.cell_terms(p, f)
     m, _ = _moments_np(f, cx, cy)
     pr = 1.0 / (1.0 - b)
     assert abs(tau - (0.2 / pr) * m["T"] ** 0.7 / (m["rho"] * m["T"])) < 1e-15
     if b == 0.0:
-        ref = m["rho"] * O.feq0(4, 3, m["T"], *m["u"])
+        ref = m["rho"] * O.feq0(nroots, order, m["T"], *m["u"])
         assert np.allclose(fes, ref, atol=1e-15)
 
 
@@ -370,9 +372,10 @@ def test_tvd_zero_denominator():
 
 
 # ---------------------------------------------------------------- whole step
-def test_uniform_equilibrium_is_a_fixed_point():
+@pytest.mark.parametrize("nroots", [4, 6])
+def test_uniform_equilibrium_is_a_fixed_point(nroots):
     """A uniform rho S(T,u) on a periodic grid is unchanged by a step."""
-    p = _params(4, 3, -0.5, nx=6, ny=5, dt=2e-3, dx=0.1, dy=0.1)
+    p = _params(nroots, DEFAULT_ORDER[nroots], -0.5, nx=6, ny=5, dt=2e-3, dx=0.1, dy=0.1)
     fields = np.zeros((4, 5, 6))
     fields[0], fields[1], fields[2], fields[3] = 1.2, 0.05, -0.03, 1.04
     f = O.init(p, fields)
@@ -394,10 +397,11 @@ def test_global_conservation_periodic(nroots):
     assert np.allclose(s1, s0, rtol=0, atol=1e-12)
 
 
-def test_force_momentum_budget():
+@pytest.mark.parametrize("nroots", [4, 6])
+def test_force_momentum_budget(nroots):
     """Periodic with g: total momentum grows by dt g sum(rho) per step and
     energy by dt sum(rho u).g."""
-    prob = Problem(name="t", nroots=4, nx=8, ny=8, bc_y=PERIODIC, kn=0.05, b=0.0, g=(2e-3, -1e-3))
+    prob = Problem(name="t", nroots=nroots, nx=8, ny=8, bc_y=PERIODIC, kn=0.05, b=0.0, g=(2e-3, -1e-3))
     from paper_1209_6548_gb300.inputs import random_fields
     fields = random_fields(prob, seed=5)
     dt = time_step(prob, fields)
@@ -411,22 +415,23 @@ def test_force_momentum_budget():
     assert abs(s1[3] - s0[3] - dt * (2e-3 * s0[1] - 1e-3 * s0[2])) < 1e-13
 
 
-def test_collision_free_advection_moves_mass_at_c():
+@pytest.mark.parametrize("nroots", [4, 6])
+def test_collision_free_advection_moves_mass_at_c(nroots):
     """With collisions switched off (Kn huge), each population is transported
     at its own velocity: the centre of mass of a smooth bump in population a
     moves by c_a dt per step (pins the sign and axes of the update)."""
     n = 64
-    prob = Problem(name="t", nroots=4, nx=n, ny=n, bc_y=PERIODIC, kn=1e30, b=0.0)
-    dt = 0.5 / n / 2.334414218338977
+    prob = Problem(name="t", nroots=nroots, nx=n, ny=n, bc_y=PERIODIC, kn=1e30, b=0.0)
+    cx, cy, w = O.velocity_set(nroots)
+    dt = 0.5 / n / np.max(np.abs(cx))
     p = oracle_params(prob, dt)
-    cx, cy, w = O.velocity_set(4)
     x = np.arange(n) / n
     X, Y = np.meshgrid(x, x)
     bump = np.exp(-((X - 0.5) ** 2 + (Y - 0.5) ** 2) / 0.01)
     f = w[:, None, None] * (1.0 + 0.1 * bump[None])
     steps = 10
     g = O.run(p, f, steps)
-    for a in range(16):
+    for a in range(nroots * nroots):
         d0 = f[a] - w[a]
         d1 = g[a] - w[a]
         mx0, mx1 = np.sum(d0 * X) / d0.sum(), np.sum(d1 * X) / d1.sum()
@@ -435,16 +440,17 @@ def test_collision_free_advection_moves_mass_at_c():
         assert abs((my1 - my0) - cy[a] * dt * steps) < 0.02 * abs(cy[a] * dt * steps)
 
 
-def test_wall_zero_normal_mass_flux():
+@pytest.mark.parametrize("nroots", [4, 6])
+def test_wall_zero_normal_mass_flux(nroots):
     """After the diffuse-wall rule, the wall node's net normal mass flux
     sum_a c_ay f_a is zero (the definition of rho_W, Sec. 3.2)."""
-    prob = Problem(name="t", nroots=4, nx=4, ny=12, bc_y=DIFFUSE, kn=0.1, b=-0.5,
+    prob = Problem(name="t", nroots=nroots, nx=4, ny=12, bc_y=DIFFUSE, kn=0.1, b=-0.5,
                    wall_ux=(-0.05, 0.05), wall_T=(0.97, 1.04))
     from paper_1209_6548_gb300.inputs import random_fields
     fields = random_fields(prob, seed=6)
     p = oracle_params(prob, time_step(prob, fields))
     f = O.init(p, fields)
-    cx, cy, w = O.velocity_set(4)
+    cx, cy, w = O.velocity_set(nroots)
     for _ in range(3):
         for j in (0, prob.ny - 1):
             flux = np.einsum("a,ai->i", cy, f[:, j, :])
@@ -452,15 +458,16 @@ def test_wall_zero_normal_mass_flux():
         f = O.step(p, f)
 
 
-def test_wall_outgoing_half_is_wall_maxwellian():
+@pytest.mark.parametrize("nroots", [4, 6])
+def test_wall_outgoing_half_is_wall_maxwellian(nroots):
     """Outgoing populations at the bottom wall are proportional to S(T_w, u_w)."""
-    prob = Problem(name="t", nroots=4, nx=4, ny=10, bc_y=DIFFUSE, kn=0.1, b=-0.5,
+    prob = Problem(name="t", nroots=nroots, nx=4, ny=10, bc_y=DIFFUSE, kn=0.1, b=-0.5,
                    wall_ux=(-0.05, 0.05), wall_T=(0.97, 1.04))
     p = oracle_params(prob, time_step(prob))
     f = O.step(p, O.init(p))
-    cx, cy, _ = O.velocity_set(4)
-    S0 = O.feq0(4, 3, 0.97, -0.05, 0.0)
-    S1 = O.feq0(4, 3, 1.04, 0.05, 0.0)
+    cx, cy, _ = O.velocity_set(nroots)
+    S0 = O.feq0(nroots, DEFAULT_ORDER[nroots], 0.97, -0.05, 0.0)
+    S1 = O.feq0(nroots, DEFAULT_ORDER[nroots], 1.04, 0.05, 0.0)
     out0 = cy > 0
     r0 = f[out0, 0, 0] / S0[out0]
     assert np.allclose(r0, r0[0], rtol=1e-14)
@@ -469,20 +476,22 @@ def test_wall_outgoing_half_is_wall_maxwellian():
     assert np.allclose(r1, r1[0], rtol=1e-14)
 
 
-def test_rest_between_walls_stays_at_rest():
+@pytest.mark.parametrize("nroots", [4, 6])
+def test_rest_between_walls_stays_at_rest(nroots):
     """Resting gas between stationary walls at T_w = 1 is a fixed point."""
-    prob = Problem(name="t", nroots=4, nx=4, ny=9, bc_y=DIFFUSE, kn=0.1, b=-0.5)
+    prob = Problem(name="t", nroots=nroots, nx=4, ny=9, bc_y=DIFFUSE, kn=0.1, b=-0.5)
     p = oracle_params(prob, time_step(prob))
     f = O.init(p)
     f1 = O.run(p, f, 5)
     assert np.max(np.abs(f1 - f)) < 1e-15
 
 
-def test_couette_antisymmetry_and_uniform_shear():
+@pytest.mark.parametrize("nroots", [4, 6])
+def test_couette_antisymmetry_and_uniform_shear(nroots):
     """Couette walls at -/+u: u_x is odd about the centre line, sigma_xy is
     even, and at steady state the shear stress is uniform across the channel
     (momentum balance); it has the sign that opposes the shear."""
-    prob = Problem(name="t", nroots=4, nx=1, ny=16, bc_y=DIFFUSE, kn=0.1, b=-0.5,
+    prob = Problem(name="t", nroots=nroots, nx=1, ny=16, bc_y=DIFFUSE, kn=0.1, b=-0.5,
                    wall_ux=(-0.05, 0.05))
     p = oracle_params(prob, time_step(prob))
     f = O.run(p, O.init(p), 4000)
@@ -626,34 +635,37 @@ def test_fourier_walls_exchange_mass_at_a_constant_rate():
 
 
 # ---------------------------------------------------------------- Maxwell walls, wall heating
-def test_specular_walls_keep_any_rest_state():
+@pytest.mark.parametrize("nroots", [4, 6])
+def test_specular_walls_keep_any_rest_state(nroots):
     """Fully specular walls (gamma = 0 in the Maxwell model of Sec. 3.2) impose
     no wall temperature: a resting gas at T = 1.1 between walls held at 1.0
     stays exactly as it is (a diffuse wall would heat or cool it).  Like the
     diffuse rule, the replacement of the wall node's outgoing half is not a
     conservation law for non-equilibrium states, so only the rest state is
     pinned here."""
-    prob = Problem(name="s", nroots=4, nx=3, ny=12, bc_y=DIFFUSE, kn=0.1, b=-0.5, wall_T=(1.0, 1.0),
+    prob = Problem(name="s", nroots=nroots, nx=3, ny=12, bc_y=DIFFUSE, kn=0.1, b=-0.5, wall_T=(1.0, 1.0),
                    wall_specular=1.0)
     p = oracle_params(prob, time_step(prob))
     fields = np.zeros((4, 12, 3))
     fields[0], fields[3] = 1.0, 1.1
     f = O.init(p, fields)
     assert np.max(np.abs(O.run(p, f, 20) - f)) < 1e-15
-    pd = oracle_params(Problem(name="d", nroots=4, nx=3, ny=12, bc_y=DIFFUSE, kn=0.1, b=-0.5), time_step(prob))
+    pd = oracle_params(Problem(name="d", nroots=nroots, nx=3, ny=12, bc_y=DIFFUSE, kn=0.1, b=-0.5),
+                       time_step(prob))
     fd = O.init(pd, fields)
     assert np.max(np.abs(O.run(pd, fd, 20) - fd)) > 1e-6
 
 
+@pytest.mark.parametrize("nroots", [4, 6])
 @pytest.mark.parametrize("spec", [0.0, 0.3, 1.0])
-def test_maxwell_wall_zero_normal_mass_flux(spec):
-    prob = Problem(name="m", nroots=4, nx=4, ny=10, bc_y=DIFFUSE, kn=0.1, b=0.0, wall_ux=(-0.05, 0.05),
+def test_maxwell_wall_zero_normal_mass_flux(spec, nroots):
+    prob = Problem(name="m", nroots=nroots, nx=4, ny=10, bc_y=DIFFUSE, kn=0.1, b=0.0, wall_ux=(-0.05, 0.05),
                    wall_T=(0.97, 1.04), wall_specular=spec)
     from paper_1209_6548_gb300.inputs import random_fields
     fields = random_fields(prob, seed=9)
     p = oracle_params(prob, time_step(prob, fields))
     f = O.init(p, fields)
-    cx, cy, w = O.velocity_set(4)
+    cx, cy, w = O.velocity_set(nroots)
     for _ in range(3):
         f = O.step(p, f)
         for j in (0, prob.ny - 1):
@@ -681,15 +693,17 @@ def test_wall_heating_is_linear_in_the_amplitude_and_zero_amplitude_is_static():
     assert np.max(np.abs(u2 - 2.0 * u1)) < 1e-2 * np.max(np.abs(u2))
 
 
-def test_heated_wall_reemits_the_maxwellian_of_the_new_time():
+@pytest.mark.parametrize("nroots", [4, 6])
+def test_heated_wall_reemits_the_maxwellian_of_the_new_time(nroots):
+    from dataclasses import replace
     from paper_1209_6548_gb300 import inputs as I
-    prob = I.unsteady_heating(kn=0.1, amp=0.05, ny=12, st=3.0)
+    prob = replace(I.unsteady_heating(kn=0.1, amp=0.05, ny=12, st=3.0), nroots=nroots, order=0)
     dt = time_step(prob)
     p = oracle_params(prob, dt)
     f = O.run(p, O.init(p), 7)
-    cx, cy, _ = O.velocity_set(4)
+    cx, cy, _ = O.velocity_set(nroots)
     Tw = 1.0 + 0.05 * np.sin(3.0 * 7 * dt)
-    S = O.feq0(4, 3, Tw, 0.0, 0.0)
+    S = O.feq0(nroots, DEFAULT_ORDER[nroots], Tw, 0.0, 0.0)
     out = cy > 0
     r = f[out, 0, 0] / S[out]
     assert np.allclose(r, r[0], rtol=1e-13)
