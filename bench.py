@@ -124,6 +124,39 @@ def committed_traffic(source_digest: str, velocity_set: str = "d2q16", storage: 
         return None
 
 
+def committed_instructions(source_digest: str, velocity_set: str = "d2q16", storage: str = "f32"):
+    """Thread-instructions per lattice update of the step kernel from the
+    committed ncu summary (same digest rule as committed_traffic), or None."""
+    path = os.path.join(ROOT, "profiles", f"k_step_tgv4096_{velocity_set}.md")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    vals = {}
+    for ln in lines:
+        if ln.startswith("- ") and ":" in ln:
+            k, v = ln[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel source sha256") != source_digest:
+        return None
+    try:
+        return float(vals[f"thread-instructions per lattice update ({storage} storage)"])
+    except (KeyError, ValueError):
+        return None
+
+
+def issue_view(instr_per_update, cells, kernel_ms, sm_count, sm_mhz):
+    """The step as instruction issue: warp-instructions issued per second
+    (instructions per update from ncu, updates per second from the CUDA-event
+    kernel time) against SMs x 4 schedulers x the sampled SM clock."""
+    if not instr_per_update or not sm_mhz:
+        return None
+    achieved = instr_per_update / 32.0 * cells / (kernel_ms / 1e3)
+    peak = sm_count * 4 * sm_mhz * 1e6
+    return {"achieved": achieved, "peak": peak, "unit": "warp-instructions/s", "frac": achieved / peak,
+            "instr_per_update": instr_per_update, "sm_mhz": sm_mhz}
+
+
 def _function_text(text: str, head: str) -> str:
     """The source of the function whose definition starts with head (up to
     its matching closing brace)."""
@@ -218,10 +251,12 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline(n: int, rows: int = 1024, steps: int = 48, velocity_set: str = "d2q16"):
+def cpu_baseline(n: int, rows: int = 1024, steps: int = 48, velocity_set: str = "d2q16",
+                 single_thread: bool = True):
     """The FP64 oracle, as it stands, on a bounded sample of the workload: the
     first `rows` rows of the n x n Taylor-Green initial state, periodic, split
-    scheme, for `steps` time steps, on all host cores the process may use."""
+    scheme, for `steps` time steps, on all host cores the process may use; and
+    (single_thread) on one core, on a sixteenth of the rows for half the steps."""
     import numpy as np
     import oracle as O
     from paper_1209_6548_gb300 import inputs as I
@@ -239,9 +274,22 @@ def cpu_baseline(n: int, rows: int = 1024, steps: int = 48, velocity_set: str = 
     t0 = time.perf_counter()
     O.run(op, f, steps)
     sec = time.perf_counter() - t0
-    return {"value": n * rows * steps / sec / 1e6, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
-            "sample": f"{n}x{rows} periodic rows of the Taylor-Green state ({velocity_set.upper()}), "
-                      f"{steps} FP64 oracle steps ({sec:.1f} s)"}
+    out = {"value": n * rows * steps / sec / 1e6, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
+           "sample": f"{n}x{rows} periodic rows of the Taylor-Green state ({velocity_set.upper()}), "
+                     f"{steps} FP64 oracle steps ({sec:.1f} s)"}
+    if single_thread:
+        r1, s1 = max(1, rows // 16), max(1, steps // 2)
+        op1 = O.make_params(nroots=nroots, order=order, nx=n, ny=r1, bc_y=0, kn=prob.kn, b=prob.b,
+                            visc_exp=prob.visc_exp, dt=dt, dx=dx, dy=dy, scheme=prob.scheme, dim=dim)
+        f1 = O.init(op1, fields[:, :r1, :].copy())
+        O.set_threads(1)
+        t0 = time.perf_counter()
+        O.run(op1, f1, s1)
+        sec1 = time.perf_counter() - t0
+        O.set_threads(cores)
+        out["single_thread"] = {"value": n * r1 * s1 / sec1 / 1e6, "unit": UNIT, "cores": 1,
+                                "sample": f"{n}x{r1} rows, {s1} steps ({sec1:.1f} s)"}
+    return out
 
 
 def run_reference(args, world, rank):
@@ -251,7 +299,7 @@ def run_reference(args, world, rank):
     t_all = time.perf_counter()
     base = None
     for k in range(args.warmup + args.steps):
-        base = cpu_baseline(args.n, rows=256, steps=4, velocity_set=args.velocity_set)
+        base = cpu_baseline(args.n, rows=256, steps=4, velocity_set=args.velocity_set, single_thread=False)
         if k >= args.warmup:
             samples.append(base["value"])
     value = statistics.median(samples)
@@ -725,7 +773,11 @@ def main():
                                     if q // (nroots * nroots) < 3 else "k_step_z<split> (one warp per z-level) ")
                                    + f"rows={shape[1]}",
                          "kernel_ms": kernel_ms,
-                         "bytes_per_lup": bytes_per_lup, "source_sha256": digest},
+                         "bytes_per_lup": bytes_per_lup, "source_sha256": digest,
+                         "of_nominal_hbm": achieved / 7900.0,
+                         "issue": issue_view(committed_instructions(digest, args.velocity_set, args.storage), cells,
+                                             kernel_ms, torch.cuda.get_device_properties(local).multi_processor_count,
+                                             clocks["sm_mhz"])},
             "cpu_baseline": base,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,

@@ -59,3 +59,24 @@ def test_digest_ignores_code_outside_the_step_kernels(tmp_path, monkeypatch):
     a = text.index("// The fused time step")
     (csrc / "lesbgk.cu").write_text(text[:a] + text[a:].replace("const int lane", "const int lane ", 1))
     assert bench.source_digest() != d0
+
+
+INSTR_CASES = [("d2q16", "f32"), ("d2q16", "f16"), ("d2q16", "bf16"), ("d2q36", "f32"), ("d2q36", "f16"),
+               ("d3q64", "f32"), ("d3q64", "f16"), ("d3q64", "bf16"), ("d3q216", "f32")]
+
+
+@pytest.mark.parametrize("velocity_set,storage", INSTR_CASES)
+def test_instruction_counts_were_taken_on_the_current_kernel_source(velocity_set, storage):
+    n = bench.committed_instructions(bench.source_digest(), velocity_set, storage)
+    assert n is not None and 500 < n < 6000
+
+
+def test_issue_view_arithmetic():
+    """674.2 instructions per update over 4096^2 updates in 356.3 us is
+    674.2/32 * 4096^2 / 356.3e-6 warp-instructions/s; the issue peak of 152
+    SMs at 2070 MHz is 152 * 4 * 2.07e9."""
+    v = bench.issue_view(674.2, 4096 * 4096, 0.3563, 152, 2070.0)
+    assert abs(v["achieved"] - 674.2 / 32 * 4096 ** 2 / 356.3e-6) < 1e-3 * v["achieved"]
+    assert v["peak"] == 152 * 4 * 2070e6
+    assert abs(v["frac"] - v["achieved"] / v["peak"]) < 1e-15
+    assert bench.issue_view(None, 1, 1.0, 152, 2070.0) is None
