@@ -463,7 +463,9 @@ def run_batch(args, world, rank, local):
                      "kernel_ms": step_ms,
                      "note": "algorithmic bytes of one batch step over its time; the working set is served "
                              "partly from L2 (about 40% of the reads in the ncu capture)"},
-        "gpu_launches": (n + nsteps // 64 * 1 + nsteps % 64 + 2 * n) * args.steps,
+        # per pass: one init per admitted slot, one step kernel per step (64 of them in each
+        # replayed graph; the mix has one lattice class), moments and reduction per slot
+        "gpu_launches": (n + nsteps + 2 * n) * args.steps,
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
         "steady": steady,
     }
