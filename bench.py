@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--rate", type=float, default=200.0, help="mean arrivals per second")
     ap.add_argument("--pool-mb", type=float, default=64.0, help="device-memory budget of the serving pool")
     ap.add_argument("--plain-budget", type=float, default=60.0, help="seconds the FIFO baseline may run")
+    ap.add_argument("--tgv-n", type=int, default=256,
+                    help="precision workload: Taylor-Green grid (4096 = the throughput workload; the FP64 "
+                         "oracle then needs about half an hour on 16 cores)")
     ap.add_argument("--instances", type=int, default=512)
     ap.add_argument("--plain-sample", type=int, default=32, help="instances the one-at-a-time baseline runs")
     ap.add_argument("--no-steady", action="store_true",
@@ -535,7 +538,8 @@ def run_serve(args, world, rank, local):
 
 def run_precision(args, world, rank, local):
     """Per-field error of FP32, FP16 and BF16 population storage (FP32 compute)
-    against the FP64 oracle: a 256^2 Taylor-Green vortex (split scheme) and the
+    against the FP64 oracle: an n^2 Taylor-Green vortex (split scheme; n = --tgv-n,
+    256 by default, 4096 for the throughput workload itself) and the
     force-driven Poiseuille channel (g = 1e-4, Kn 0.2, b = 0, ny = 1024; the
     flow does not vary in x, so a 4-node-wide periodic slice computes the same
     solution as the 512-wide channel), 1000 steps each.  Error per field:
@@ -553,7 +557,8 @@ def run_precision(args, world, rank, local):
     B.build()
     O.set_threads(len(os.sched_getaffinity(0)))
     steps = 1000
-    cases = [("tgv256", I.tgv(256, steps=steps)), ("poiseuille_1024", I.poiseuille(nx=4, ny=1024, steps=steps))]
+    cases = [(f"tgv{args.tgv_n}", I.tgv(args.tgv_n, steps=steps)),
+             ("poiseuille_1024", I.poiseuille(nx=4, ny=1024, steps=steps))]
     groups = {"rho": ["rho"], "T": ["T"], "u": ["ux", "uy"], "sigma": ["sxx", "sxy", "syy"], "q": ["qx", "qy"]}
     floor = {"rho": 0.0, "T": 0.0, "u": 1e-3, "sigma": 1e-3, "q": 3e-3}
     names = list(O.MOMENT_NAMES)
@@ -618,7 +623,7 @@ def run_precision(args, world, rank, local):
     line = {"metric": "per-field error vs FP64 oracle by population storage", "value": worst["f16"],
             "unit": "max relative error (FP16 storage)", "n_gpus": world, "steps": steps, "warmup": 0,
             "higher_is_better": False, "dtype": "f32 compute", "data": "synthetic",
-            "config": {"workload": "precision_tgv256_poiseuille1024", "lattice_steps": steps,
+            "config": {"workload": f"precision_tgv{args.tgv_n}_poiseuille1024", "lattice_steps": steps,
                        "cases": [c for c, _ in cases]},
             "worst_e": worst, "errors": out, "throughput_4096": thr, "peak_gbs": peak,
             "oracle_seconds": t_or, "cpu_cores": O.get_threads()}
