@@ -127,6 +127,15 @@ typedef struct lesbgk_params {
                            u = 0) with zero net mass flux along n_x + n_y.  With walls in x only,
                            dy = dx = 1/(nx-1).  FP32 storage, fully diffuse y-walls. */
   double wall_Tx[2];    /* x-wall temperatures, [0] = left (i = 0), [1] = right (i = nx-1) */
+  double dx, dy;        /* grid spacing; 0, 0 = derived from the grid and walls as described above.
+                           Explicit values (both > 0) serve a y-slab of a larger domain, which
+                           runs as a solver of its own on the slab's rows plus halo rows and
+                           keeps the whole domain's spacing (pass the whole domain's dt too). */
+  int32_t row_offset;   /* global index of this grid's row 0 (a y-slab's place in the whole
+                           domain, negative where its halo wraps around a periodic domain; 0
+                           otherwise): the 16-bit stochastic rounding is keyed by the global
+                           row, so a slab rounds exactly as the whole domain does */
+  int32_t reserved;     /* must be 0 */
 } lesbgk_params;
 
 /* Read-only facts about a created solver. */
@@ -192,15 +201,20 @@ int lesbgk_moments_host(lesbgk *h, float *h_out, double *h_sums, void *stream);
  * test a serving loop applies):
  *   r = max over nodes of (|d rho| + |d u_x| + |d u_y| + |d T|) / (steps dt),
  * d the change of the node's fields since the snapshot, steps the time steps
- * taken since it.
+ * taken since it; a node whose change is not finite makes r = +Inf.
  *   d_snap:  DEVICE float[4][ny][nx] (rho, u_x, u_y, T), caller-owned; read as
  *            the previous snapshot and overwritten with the current fields.
  *   steps:   time steps since the snapshot; <= 0 only takes the snapshot and
  *            returns r = NaN.
  *   h_r:     HOST double, receives r.
+ *   h_mass:  HOST double receiving the total mass sum over nodes of rho (the
+ *            per-node values in FP32, summed in FP64 in a fixed order), or
+ *            NULL.  With diffuse walls at a temperature other than the gas's
+ *            the wall rule exchanges a constant amount of mass per step, and
+ *            the mass history tells that drift apart from a transient.
  * Synchronises the stream.  Errors: LESBGK_EINVAL (NULL arguments),
  * LESBGK_ECUDA. */
-int lesbgk_residual(lesbgk *h, float *d_snap, int64_t steps, double *h_r, void *stream);
+int lesbgk_residual(lesbgk *h, float *d_snap, int64_t steps, double *h_r, double *h_mass, void *stream);
 
 /* Copy the current populations (deviations f_a - w_a, float[Q][ny][nx]) into
  * DEVICE memory d_out; with lesbgk_set_populations this is a checkpoint. */
@@ -209,6 +223,28 @@ int lesbgk_get_populations(lesbgk *h, float *d_out, void *stream);
 /* Overwrite the current populations from DEVICE memory d_in (same layout);
  * the step counter is set to steps_done. */
 int lesbgk_set_populations(lesbgk *h, const float *d_in, int64_t steps_done, void *stream);
+
+/* Rows of the populations in the library's internal grouped layout, for the
+ * halo exchange of a y-slab decomposition (not in the paper: one large solve
+ * split over several solvers, each holding a slab of rows plus halo rows that
+ * its neighbours refill; the TVD stencil of Sec. 3.1 reaches two rows, so a
+ * halo of 2k rows carries k steps).
+ *   lesbgk_rows_bytes: bytes of nrows packed rows.
+ *   lesbgk_get_rows:   copy rows [j0, j0 + nrows) of the current populations
+ *                      into DEVICE d_out (packed: for each population group,
+ *                      its nrows x nx vectors; the stored type, any storage).
+ *   lesbgk_set_rows:   overwrite rows [j0, j0 + nrows) from DEVICE d_in in the
+ *                      same packing.
+ * Both are one asynchronous 2D copy on the stream.  Errors: LESBGK_EINVAL for
+ * rows outside [0, ny) or NULL pointers. */
+int lesbgk_rows_bytes(const lesbgk *h, int32_t nrows, size_t *bytes);
+int lesbgk_get_rows(lesbgk *h, int32_t j0, int32_t nrows, void *d_out, void *stream);
+int lesbgk_set_rows(lesbgk *h, int32_t j0, int32_t nrows, const void *d_in, void *stream);
+
+/* As lesbgk_moments, over rows [j0, j0 + nrows) only (a slab's own rows,
+ * without its halo): d_out (DEVICE, or NULL) is float[9][nrows][nx], h_sums
+ * (HOST, or NULL) the FP64 totals of those rows. */
+int lesbgk_moments_rows(lesbgk *h, int32_t j0, int32_t nrows, float *d_out, double *h_sums, void *stream);
 
 /* Choose the launch shape of the step kernel: cells_per_thread (1 or 2
  * consecutive x-nodes per lane; 2 needs nx even and nroots = 4) and
@@ -259,9 +295,11 @@ int lesbgk_batch_remove(lesbgk_batch *b, int32_t slot, void *stream);
 int lesbgk_batch_step(lesbgk_batch *b, int64_t nsteps, void *stream);
 /* Steady-state residual of every slot since the previous call:
  * r = max over nodes of (|d rho| + |d u_x| + |d u_y| + |d T|) / (steps * dt),
- * into HOST double[capacity]; NaN for empty slots and for a slot's first call.
- * Synchronises the stream. */
-int lesbgk_batch_residuals(lesbgk_batch *b, double *h_res, void *stream);
+ * into HOST double[capacity]; NaN for empty slots and for a slot's first call,
+ * +Inf for a slot with a non-finite change (a diverged solve).  h_mass, if not
+ * NULL, receives HOST double[capacity]: each slot's total mass (as
+ * lesbgk_residual; NaN for empty slots).  Synchronises the stream. */
+int lesbgk_batch_residuals(lesbgk_batch *b, double *h_res, double *h_mass, void *stream);
 /* As lesbgk_moments / lesbgk_get_populations / lesbgk_get_info, per slot. */
 int lesbgk_batch_moments(lesbgk_batch *b, int32_t slot, float *d_out, double *h_sums, void *stream);
 int lesbgk_batch_get_populations(lesbgk_batch *b, int32_t slot, float *d_out, void *stream);
@@ -291,13 +329,16 @@ int lesbgk_batch_destroy(lesbgk_batch *b);
  *                  stream is synchronised).
  * Limit: nx*ny <= 2^24 nodes (4096 x 4096); larger grids return LESBGK_EINVAL.
  * Its scratch is a fixed 256 KiB + 32 B array inside the library that every GPU which
- * loads the library keeps until the process exits.  The first call on a
- * device looks up that array's device address (a one-time set-up per device,
- * done with that device current); make that first call before any stream
- * capture.  All calls share the array: each call writes every scratch slot it
- * reads, so nothing carries over, but calls that overlap on the GPU (other
- * streams, other host threads) race on it and must be serialised by the
- * caller. */
+ * loads the library keeps until the process exits.  The first call in a CUDA
+ * context looks up that array's device address in the current context (the
+ * device's primary context unless the caller made another one current) and
+ * remembers it for that context's unique ID; make that first call before any
+ * stream capture.  The address belongs to the context: after a device reset,
+ * or in a context of the caller's own, the next call looks it up again (it is
+ * then again a first call).  All calls share the array: each call writes
+ * every scratch slot it reads, so nothing carries over, but calls that
+ * overlap on the GPU (other streams, other host threads) race on it and must
+ * be serialised by the caller. */
 int lesbgk_moments_noalloc(const lesbgk_params *p, const float *d_populations, float *d_out, double *h_sums,
                            void *stream);
 

@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kBlock) k_step(const S *__restrict__ fin, S *_
       // rounding key per step and row (not per column): a flow uniform in x stays
       // exactly uniform, so rounding noise cannot seed the x-varying modes the
       // printed unsplit update amplifies
-      const unsigned key = mix32(A.seed ^ mix32((unsigned)j));
+      const unsigned key = mix32(A.seed ^ mix32((unsigned)j + A.row_key));
 #pragma unroll
       for (int g = 0; g < G; ++g) st_group_sr<NR, S>(o, gstride, g, acc, A, key);
     }
@@ -684,15 +684,16 @@ struct ConsSums {
   }
 };
 
-// Moments per node of the grouped layout, plus the block partial sums.
-// out: float[9][ny][nx] or nullptr.
+// Moments per node of the grouped layout, plus the block partial sums, over
+// `cells` consecutive nodes from f (a whole grid, or a range of its rows);
+// gstride: elements between group planes (V nx ny).  out: float[9][cells] or
+// nullptr.
 template <int NR, class S, int NZ = 1>
 __global__ void __launch_bounds__(kMomBlock) k_moments(const S *__restrict__ f, float *__restrict__ out,
-                                                       double *__restrict__ partial, const KArgs A) {
+                                                       double *__restrict__ partial, long long cells,
+                                                       long long gstride, const KArgs A) {
   using Lay = Layout<NR, S, NZ>;
   constexpr int Q = Lay::Q;
-  const long long cells = A.plane;
-  const long long gstride = (long long)Lay::V * cells;
   ConsSums cs;
   for (long long c = blockIdx.x * (long long)kMomBlock + threadIdx.x; c < cells;
        c += (long long)gridDim.x * kMomBlock) {
@@ -707,17 +708,19 @@ __global__ void __launch_bounds__(kMomBlock) k_moments(const S *__restrict__ f, 
 }
 
 // Fields rho, u_x, u_y, T of each node against a snapshot: r_max (bits of a
-// non-negative float in *rbits, atomic max) of |d rho| + |d u| + |d T|, and the
-// snapshot overwritten with the current fields (residual of lesbgk_residual).
+// non-negative float in *rbits, atomic max) of |d rho| + |d u| + |d T| (a
+// non-finite change counts as +Inf), and the snapshot overwritten with the
+// current fields (residual of lesbgk_residual); mpart[block] receives the
+// block's sum of rho - 1 (FP32 per thread, FP64 across the block).
 template <int NR, class S, int NZ = 1>
 __global__ void __launch_bounds__(kMomBlock) k_residual(const S *__restrict__ f, float *__restrict__ snap,
                                                         int update_only, unsigned *__restrict__ rbits,
-                                                        const KArgs A) {
+                                                        double *__restrict__ mpart, const KArgs A) {
   using Lay = Layout<NR, S, NZ>;
   constexpr int Q = Lay::Q;
   const long long cells = A.plane;
   const long long gstride = (long long)Lay::V * cells;
-  float rmax = 0.0f;
+  float rmax = 0.0f, dm = 0.0f;
   for (long long c = blockIdx.x * (long long)kMomBlock + threadIdx.x; c < cells;
        c += (long long)gridDim.x * kMomBlock) {
     float F[Q];
@@ -743,14 +746,40 @@ __global__ void __launch_bounds__(kMomBlock) k_residual(const S *__restrict__ f,
     const float d = fabsf(rho - snap[c]) + fabsf(ux - snap[cells + c]) + fabsf(uy - snap[2 * cells + c]) +
                     fabsf(T - snap[3 * cells + c]);
     rmax = update_only ? 0.0f : fmaxf(rmax, d != d ? __int_as_float(0x7f800000) : d);  // NaN counts as Inf
+    dm += m[0][0];
     snap[c] = rho;
     snap[cells + c] = ux;
     snap[2 * cells + c] = uy;
     snap[3 * cells + c] = T;
   }
+  double dmd = (double)dm;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(kFull, rmax, o));
-  if ((threadIdx.x & 31) == 0 && rmax > 0.0f) atomicMax(rbits, __float_as_uint(rmax));
+  for (int o = 16; o > 0; o >>= 1) {
+    rmax = fmaxf(rmax, __shfl_xor_sync(kFull, rmax, o));
+    dmd += __shfl_down_sync(kFull, dmd, o);
+  }
+  __shared__ double wsum[kMomBlock / 32];
+  if ((threadIdx.x & 31) == 0) {
+    if (rmax > 0.0f) atomicMax(rbits, __float_as_uint(rmax));
+    wsum[threadIdx.x >> 5] = dmd;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kMomBlock / 32; ++w) t += wsum[w];  // fixed order
+    mpart[blockIdx.x] = t;
+  }
+}
+
+// Sum of n doubles in a fixed order (one warp): bitwise reproducible.
+__global__ void k_reduce_one(const double *__restrict__ part, int n, double *__restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x >= 32) return;
+  double t = 0.0;
+  for (int k = lane; k < n; k += 32) t += part[k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(kFull, t, o);
+  if (lane == 0) *out = t;
 }
 
 __global__ void k_reduce_partials(const double *__restrict__ partial, int n, double *__restrict__ sums) {
@@ -975,7 +1004,8 @@ int launch_moments(lesbgk *h, float *out, cudaStream_t s) {
   dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto, auto st, auto z) {
     constexpr int NR = decltype(r)::value, NZ = decltype(z)::value;
     using S = decltype(st);
-    k_moments<NR, S, NZ><<<kMomGrid, kMomBlock, 0, s>>>(static_cast<const S *>(f), out, h->partial, h->args);
+    k_moments<NR, S, NZ><<<kMomGrid, kMomBlock, 0, s>>>(static_cast<const S *>(f), out, h->partial, h->args.plane,
+                                                        (long long)Layout<NR, S, NZ>::V * h->args.plane, h->args);
   });
   k_reduce_partials<<<1, 128, 0, s>>>(h->partial, kMomGrid, h->sums);
   return 0;
@@ -998,8 +1028,8 @@ cudaError_t launch_init(const KArgs &A, int nr, int order, const double *fields,
 
 cudaError_t launch_moments(const KArgs &A, int nr, const float *f, float *out, double *partial, double *sums,
                            cudaStream_t s) {
-  if (nr == 4) k_moments<4, float><<<kMomGrid, kMomBlock, 0, s>>>(f, out, partial, A);
-  else k_moments<6, float><<<kMomGrid, kMomBlock, 0, s>>>(f, out, partial, A);
+  if (nr == 4) k_moments<4, float><<<kMomGrid, kMomBlock, 0, s>>>(f, out, partial, A.plane, 4 * A.plane, A);
+  else k_moments<6, float><<<kMomGrid, kMomBlock, 0, s>>>(f, out, partial, A.plane, 2 * A.plane, A);
   k_reduce_partials<<<1, 128, 0, s>>>(partial, kMomGrid, sums);
   return cudaGetLastError();
 }
@@ -1160,27 +1190,35 @@ extern "C" int lesbgk_moments_host(lesbgk *h, float *h_out, double *h_sums, void
   return finish_sums(h, h_sums, s);
 }
 
-extern "C" int lesbgk_residual(lesbgk *h, float *d_snap, int64_t steps, double *h_r, void *stream) {
+extern "C" int lesbgk_residual(lesbgk *h, float *d_snap, int64_t steps, double *h_r, double *h_mass,
+                               void *stream) {
   if (!h || !d_snap || !h_r) return fail(LESBGK_EINVAL, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  unsigned *rbits = reinterpret_cast<unsigned *>(h->partial);  // scratch: no moments call runs meanwhile
+  // scratch in the handle's reduction area (no moments call runs meanwhile):
+  // the residual's bits in sums[0], the mass in sums[1], block partials in partial
+  unsigned *rbits = reinterpret_cast<unsigned *>(h->sums);
   cudaError_t e = cudaMemsetAsync(rbits, 0, sizeof(unsigned), s);
   const void *f = h->buf[h->cur];
   if (e == cudaSuccess) {
     dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto, auto st, auto z) {
       using S = decltype(st);
       k_residual<decltype(r)::value, S, decltype(z)::value><<<kMomGrid, kMomBlock, 0, s>>>(
-          static_cast<const S *>(f), d_snap, steps <= 0 ? 1 : 0, rbits, h->args);
+          static_cast<const S *>(f), d_snap, steps <= 0 ? 1 : 0, rbits, h->partial, h->args);
     });
     e = cudaGetLastError();
   }
-  unsigned hb = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, rbits, sizeof hb, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) {
+    k_reduce_one<<<1, 32, 0, s>>>(h->partial, kMomGrid, h->sums + 1);
+    e = cudaGetLastError();
+  }
+  double hb[2] = {0.0, 0.0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hb, h->sums, sizeof hb, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "residual");
   float rmax;
-  std::memcpy(&rmax, &hb, sizeof rmax);
+  std::memcpy(&rmax, &hb[0], sizeof rmax);
   *h_r = steps <= 0 ? std::nan("") : (double)rmax / ((double)steps * h->dt);
+  if (h_mass) *h_mass = (double)h->args.plane + hb[1];
   return 0;
 }
 
@@ -1212,6 +1250,77 @@ extern "C" int lesbgk_set_populations(lesbgk *h, const float *d_in, int64_t step
   if (e != cudaSuccess) return cuda_fail(e, "set populations");
   h->steps = steps_done;
   return 0;
+}
+
+namespace {
+// Bytes of one stored vector and the number of group planes of the solver's layout.
+void row_geometry(const lesbgk *h, int *vb, int *groups) {
+  dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto, auto st, auto z) {
+    using Lay = Layout<decltype(r)::value, decltype(st), decltype(z)::value>;
+    *vb = Lay::VB;
+    *groups = Lay::G;
+  });
+}
+
+int check_rows(const lesbgk *h, int32_t j0, int32_t nrows) {
+  if (!h) return fail(LESBGK_EINVAL, "handle is NULL");
+  if (nrows < 0 || j0 < 0 || (long long)j0 + nrows > h->p.ny)
+    return fail(LESBGK_EINVAL, "rows [%d, %d) outside [0, %d)", j0, j0 + nrows, h->p.ny);
+  return 0;
+}
+
+// One 2D copy: G planes of nrows x nx vectors, between the current buffer and
+// a packed array.
+int copy_rows(lesbgk *h, int32_t j0, int32_t nrows, void *packed, bool to_packed, cudaStream_t s) {
+  int vb = 0, groups = 0;
+  row_geometry(h, &vb, &groups);
+  const size_t width = (size_t)nrows * h->p.nx * vb, pitch = (size_t)h->args.plane * vb;
+  char *base = reinterpret_cast<char *>(h->buf[h->cur]) + (size_t)j0 * h->p.nx * vb;
+  if (!width) return 0;
+  cudaError_t e = to_packed ? cudaMemcpy2DAsync(packed, width, base, pitch, width, groups, cudaMemcpyDeviceToDevice, s)
+                            : cudaMemcpy2DAsync(base, pitch, packed, width, width, groups, cudaMemcpyDeviceToDevice, s);
+  return e == cudaSuccess ? 0 : cuda_fail(e, "row copy");
+}
+}  // namespace
+
+extern "C" int lesbgk_rows_bytes(const lesbgk *h, int32_t nrows, size_t *bytes) {
+  if (!h || !bytes || nrows < 0) return fail(LESBGK_EINVAL, "bad argument");
+  int vb = 0, groups = 0;
+  row_geometry(h, &vb, &groups);
+  *bytes = (size_t)groups * nrows * h->p.nx * vb;
+  return 0;
+}
+
+extern "C" int lesbgk_get_rows(lesbgk *h, int32_t j0, int32_t nrows, void *d_out, void *stream) {
+  if (int rc = check_rows(h, j0, nrows)) return rc;
+  if (!d_out) return fail(LESBGK_EINVAL, "d_out is NULL");
+  return copy_rows(h, j0, nrows, d_out, true, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int lesbgk_set_rows(lesbgk *h, int32_t j0, int32_t nrows, const void *d_in, void *stream) {
+  if (int rc = check_rows(h, j0, nrows)) return rc;
+  if (!d_in) return fail(LESBGK_EINVAL, "d_in is NULL");
+  return copy_rows(h, j0, nrows, const_cast<void *>(d_in), false, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int lesbgk_moments_rows(lesbgk *h, int32_t j0, int32_t nrows, float *d_out, double *h_sums,
+                                   void *stream) {
+  if (int rc = check_rows(h, j0, nrows)) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const void *f = h->buf[h->cur];
+  const long long cells = (long long)nrows * h->p.nx;
+  dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto, auto st, auto z) {
+    constexpr int NR = decltype(r)::value, NZ = decltype(z)::value;
+    using S = decltype(st);
+    using Lay = Layout<NR, S, NZ>;
+    const S *fr = static_cast<const S *>(f) + (long long)j0 * h->p.nx * Lay::V;
+    k_moments<NR, S, NZ><<<kMomGrid, kMomBlock, 0, s>>>(fr, d_out, h->partial, cells,
+                                                        (long long)Lay::V * h->args.plane, h->args);
+  });
+  k_reduce_partials<<<1, 128, 0, s>>>(h->partial, kMomGrid, h->sums);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "moments of rows");
+  return finish_sums(h, h_sums, s);
 }
 
 extern "C" int lesbgk_set_launch(lesbgk *h, int32_t cells_per_thread, int32_t rows_per_segment) {
@@ -1289,25 +1398,67 @@ __global__ void __launch_bounds__(kMomBlock) k_moments_public(const float *__res
   cs.write_block(partial, NZ == 1 ? 2 : 3);
 }
 
-// Device address of g_noalloc_scratch per device, looked up once per device
-// with that device current (in host code the symbol is only a stand-in).
-constexpr int kMaxDevices = 64;
+// Device address of g_noalloc_scratch (in host code the symbol is only a
+// stand-in).  An address belongs to one CUDA context, not to a device: a
+// device reset, or a caller that runs its own context on the same device,
+// loads the module again at another address.  So the cache is keyed by the
+// current context's process-unique ID (cuCtxGetId, reached through the
+// runtime's driver entry points, so that the library does not link libcuda),
+// and each new context gets its own cudaGetSymbolAddress.  If those driver
+// entry points are unavailable the address is looked up on every call.
+using CtxGetCurrentFn = int (*)(void **);
+using CtxGetIdFn = int (*)(void *, unsigned long long *);
+constexpr int kNoAllocCache = 64;  // contexts remembered (oldest replaced first)
 std::mutex g_noalloc_mutex;
-double *g_noalloc_ptr[kMaxDevices] = {};
+struct NoAllocEntry {
+  unsigned long long ctx_id;
+  double *ptr;
+};
+NoAllocEntry g_noalloc_cache[kNoAllocCache] = {};
+int g_noalloc_next = 0;
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+bool g_ctx_fns_looked_up = false;
+
+// The current context's unique ID; false if there is none (or no way to ask).
+bool current_context_id(unsigned long long *id) {
+  if (!g_ctx_fns_looked_up) {
+    g_ctx_fns_looked_up = true;
+    void *f = nullptr, *g = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f);
+      g_ctx_id = reinterpret_cast<CtxGetIdFn>(g);
+    }
+    cudaGetLastError();  // a failed query leaves no sticky error
+  }
+  if (!g_ctx_current || !g_ctx_id) return false;
+  void *ctx = nullptr;
+  if (g_ctx_current(&ctx) != 0 || !ctx) return false;
+  return g_ctx_id(ctx, id) == 0;
+}
 
 int noalloc_scratch(double **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices) return fail(LESBGK_EINVAL, "device index %d beyond %d", dev, kMaxDevices);
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static moment scratch");
-    g_noalloc_ptr[dev] = static_cast<double *>(p);
+  unsigned long long id = 0;
+  bool have = current_context_id(&id);
+  if (have)
+    for (const NoAllocEntry &e : g_noalloc_cache)
+      if (e.ptr && e.ctx_id == id) {
+        *out = e.ptr;
+        return 0;
+      }
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static moment scratch");
+  if (!have) have = current_context_id(&id);  // the lookup made the device's primary context current
+  if (have) {
+    g_noalloc_cache[g_noalloc_next] = NoAllocEntry{id, static_cast<double *>(p)};
+    g_noalloc_next = (g_noalloc_next + 1) % kNoAllocCache;
   }
-  *out = g_noalloc_ptr[dev];
+  *out = static_cast<double *>(p);
   return 0;
 }
 
