@@ -39,7 +39,8 @@ class Problem:
     cfl:    Courant number used when no explicit dt is given.
     wall_T, wall_ux: (bottom, top) wall temperature and x-velocity.
     g:      body force (g_x, g_y).
-    init:   'rest' or 'tgv' (Taylor-Green vortex with density noise).
+    init:   'rest', 'tgv' (Taylor-Green vortex with density noise) or 'shear'
+            (a shear and temperature wave along y with density noise).
     scheme: UNSPLIT (both flux differences from f^n, as printed) or SPLIT.
     wall_specular, wall_T_amp, wall_T_freq: Maxwell walls (fraction re-emitted
         specularly) and sinusoidal wall heating.
@@ -88,6 +89,17 @@ def tgv(n: int = 4096, steps: int = 1000, nroots: int = 4) -> Problem:
     The flow varies in x and y, so it runs with the split scheme."""
     return Problem(name=f"tgv_{n}x{n}_d2q{nroots * nroots}", nroots=nroots, nx=n, ny=n,
                    bc_y=PERIODIC, kn=0.05, b=-0.5, init="tgv", steps=steps, scheme=SPLIT)
+
+
+def shear_strip(ny: int = 4096, nx: int = 4, kn: float = 0.05, steps: int = 1000, nroots: int = 4,
+                dim: int = 2) -> Problem:
+    """A periodic strip nx x ny holding a shear wave and a temperature wave
+    along y (Taylor-Green amplitudes: u_x = 0.05 sin 2 pi y, T = 1 + 0.01
+    cos 2 pi y, density noise 1e-4), Kn 0.05, b = -1/2, split scheme.  With
+    ny = 4096 its y-spacing, time step and tau are those of the 4096^2
+    Taylor-Green solve (dt/tau ~ 7e-4), on 4 ny nodes instead of ny^2."""
+    return Problem(name=f"shear_{nx}x{ny}", nroots=nroots, dim=dim, nx=nx, ny=ny, bc_y=PERIODIC, kn=kn, b=-0.5,
+                   init="shear", steps=steps, scheme=SPLIT)
 
 
 def poiseuille(nx: int = 512, ny: int = 1024, steps: int = 1000) -> Problem:
@@ -154,11 +166,21 @@ def initial_fields(p: Problem) -> np.ndarray:
     y = j/(ny-1).  'tgv': u_x = A sin(2 pi x) cos(2 pi y),
     u_y = -A cos(2 pi x) sin(2 pi y), T = 1 + dT sin(2 pi x) sin(2 pi y),
     rho = 1 + U(-noise, noise) i.i.d. per node (numpy default_rng(seed)).
+    'shear' (periodic in y, node j at y = j/ny): u_x = A sin(2 pi y), u_y = 0,
+    T = 1 + dT cos(2 pi y), rho = 1 + U(-noise, noise) i.i.d. per node.
     """
     out = np.zeros((4, p.ny, p.nx))
     out[0] = 1.0
     out[3] = 1.0
     if p.init == "rest":
+        return out
+    if p.init == "shear":
+        y = np.arange(p.ny) / p.ny
+        tp = 2.0 * np.pi
+        out[1] = p.tgv_amp * np.sin(tp * y)[:, None]
+        out[3] = 1.0 + p.tgv_dT * np.cos(tp * y)[:, None]
+        rng = np.random.default_rng(p.seed)
+        out[0] = 1.0 + rng.uniform(-p.rho_noise, p.rho_noise, size=(p.ny, p.nx))
         return out
     if p.init != "tgv":
         raise ValueError(p.init)
