@@ -237,11 +237,15 @@ __global__ void __launch_bounds__(kBBlock) k_batch_step(const BatchArgs B, const
 
 // Residual of every work item: max over its nodes of
 // |d rho| + |d u_x| + |d u_y| + |d T| since the snapshot, folded into
-// res_bits[instance] (non-negative floats order like their bit patterns);
-// the snapshot is refreshed.  One block per item.
+// res_bits[instance] (non-negative floats order like their bit patterns; a
+// node whose change is not finite counts as +Inf, so a diverged slot reports
+// r = Inf); the snapshot is refreshed.  mass[item] receives the item's sum of
+// rho - 1 over its nodes (FP32 per thread, FP64 across the block).  One block
+// per item.
 template <int NR>
 __global__ void __launch_bounds__(kBBlock) k_batch_residual(const BatchArgs B, const int par,
-                                                            unsigned *__restrict__ res_bits) {
+                                                            unsigned *__restrict__ res_bits,
+                                                            double *__restrict__ mass) {
   using Lay = Layout<NR>;
   constexpr int Q = Lay::Q;
   const int first = B.range[0], count = B.range[1];
@@ -252,7 +256,7 @@ __global__ void __launch_bounds__(kBBlock) k_batch_residual(const BatchArgs B, c
   const long long cells = (long long)nx * ny;
   const long long gstride = (long long)Lay::V * cells;
   const float *f = D.f[par];
-  float r = 0.0f;
+  float r = 0.0f, dm = 0.0f;
   for (int t = threadIdx.x; t < wi.rows * nx; t += kBBlock) {
     const long long c = (long long)wi.y0 * nx + t;
     float F[Q];
@@ -266,15 +270,31 @@ __global__ void __launch_bounds__(kBBlock) k_batch_residual(const BatchArgs B, c
     const float trM = fmaf(-m[1][0], ux, m[2][0]) + fmaf(-m[0][1], uy, m[0][2]);
     const float T = fmaf(0.5f * trM, ir, 1.0f);
     float *s = D.snap + 4 * c;
-    r = fmaxf(r, fabsf(rho - s[0]) + fabsf(ux - s[1]) + fabsf(uy - s[2]) + fabsf(T - s[3]));
+    const float d = fabsf(rho - s[0]) + fabsf(ux - s[1]) + fabsf(uy - s[2]) + fabsf(T - s[3]);
+    r = fmaxf(r, d != d ? __int_as_float(0x7f800000) : d);  // NaN counts as Inf
+    dm += m[0][0];
     s[0] = rho;
     s[1] = ux;
     s[2] = uy;
     s[3] = T;
   }
+  double dmd = (double)dm;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(kFull, r, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(res_bits + wi.inst, __float_as_uint(r));
+  for (int o = 16; o > 0; o >>= 1) {
+    r = fmaxf(r, __shfl_xor_sync(kFull, r, o));
+    dmd += __shfl_down_sync(kFull, dmd, o);
+  }
+  __shared__ double wsum[kBBlock / 32];
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(res_bits + wi.inst, __float_as_uint(r));
+    wsum[threadIdx.x >> 5] = dmd;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kBBlock / 32; ++w) t += wsum[w];  // fixed order
+    mass[first + blockIdx.x] = t;
+  }
 }
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -356,6 +376,7 @@ struct lesbgk_batch {
   WorkItem *d_items = nullptr;
   int *d_range = nullptr;
   unsigned *d_res = nullptr;
+  double *d_mass = nullptr;
   double *d_partial = nullptr, *d_sums = nullptr;
   char *pool_base = nullptr;
   size_t pool_bytes = 0;
@@ -380,7 +401,7 @@ namespace {
 constexpr size_t kItemsPerSlot = 1024;  // work-list room: items per slot (rows/8 for ny <= 8192)
 
 struct Layout0 {
-  size_t desc, items, range, res, partial, sums, pool;
+  size_t desc, items, mass, range, res, partial, sums, pool;
 };
 
 Layout0 fixed_layout(int capacity) {
@@ -390,6 +411,8 @@ Layout0 fixed_layout(int capacity) {
   o = align_up(o + sizeof(InstDesc) * (size_t)capacity, 256);
   L.items = o;
   o = align_up(o + sizeof(WorkItem) * (size_t)capacity * kItemsPerSlot, 256);
+  L.mass = o;  // per-item mass partial of the residual pass
+  o = align_up(o + sizeof(double) * (size_t)capacity * kItemsPerSlot, 256);
   L.range = o;
   o = align_up(o + sizeof(int) * 2 * kNumClasses, 256);
   L.res = o;
@@ -570,6 +593,7 @@ extern "C" int lesbgk_batch_create(int32_t capacity, int32_t nx, void *d_workspa
   b->d_items = reinterpret_cast<WorkItem *>(b->ws + L.items);
   b->d_range = reinterpret_cast<int *>(b->ws + L.range);
   b->d_res = reinterpret_cast<unsigned *>(b->ws + L.res);
+  b->d_mass = reinterpret_cast<double *>(b->ws + L.mass);
   b->d_partial = reinterpret_cast<double *>(b->ws + L.partial);
   b->d_sums = reinterpret_cast<double *>(b->ws + L.sums);
   b->pool_base = b->ws + L.pool;
@@ -755,7 +779,7 @@ extern "C" int lesbgk_batch_step(lesbgk_batch *b, int64_t nsteps, void *stream) 
   return 0;
 }
 
-extern "C" int lesbgk_batch_residuals(lesbgk_batch *b, double *h_res, void *stream) {
+extern "C" int lesbgk_batch_residuals(lesbgk_batch *b, double *h_res, double *h_mass, void *stream) {
   if (!b || !h_res) return fail(LESBGK_EINVAL, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (int rc = ensure_items(b, s)) return rc;
@@ -764,24 +788,31 @@ extern "C" int lesbgk_batch_residuals(lesbgk_batch *b, double *h_res, void *stre
     const int n = b->range[cls][1];
     if (!n) continue;
     BatchArgs a = make_args(b, cls);
-    if (cls == 0) k_batch_residual<4><<<n, kBBlock, 0, s>>>(a, b->par, b->d_res);
-    else k_batch_residual<6><<<n, kBBlock, 0, s>>>(a, b->par, b->d_res);
+    if (cls == 0) k_batch_residual<4><<<n, kBBlock, 0, s>>>(a, b->par, b->d_res, b->d_mass);
+    else k_batch_residual<6><<<n, kBBlock, 0, s>>>(a, b->par, b->d_res, b->d_mass);
     e = cudaGetLastError();
   }
   std::vector<unsigned> bits(b->capacity);
+  std::vector<double> part(h_mass ? b->items.size() : 0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(bits.data(), b->d_res, sizeof(unsigned) * b->capacity, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && !part.empty())
+    e = cudaMemcpyAsync(part.data(), b->d_mass, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "batch residuals");
   for (int i = 0; i < b->capacity; ++i) {
     auto &sl = b->slots[i];
     h_res[i] = NAN;
+    if (h_mass) h_mass[i] = NAN;
     if (!sl.used) continue;
     float r;
     std::memcpy(&r, &bits[i], sizeof r);
     if (sl.snap_step >= 0 && sl.steps > sl.snap_step) h_res[i] = r / ((double)(sl.steps - sl.snap_step) * sl.dt);
     else if (sl.snap_step >= 0) h_res[i] = 0.0;
     sl.snap_step = sl.steps;
+    if (h_mass) h_mass[i] = (double)sl.p.nx * sl.p.ny;
   }
+  if (h_mass)  // the items' partials in work-list order: reproducible
+    for (size_t k = 0; k < part.size(); ++k) h_mass[b->items[k].inst] += part[k];
   return 0;
 }
 

@@ -29,7 +29,8 @@ MOMENT_NAMES = ("rho", "ux", "uy", "T", "sxx", "sxy", "syy", "qx", "qy")
 SYMBOLS = ("lesbgk_workspace_size", "lesbgk_create", "lesbgk_reinit", "lesbgk_step", "lesbgk_moments",
            "lesbgk_moments_host", "lesbgk_get_populations", "lesbgk_set_populations",
            "lesbgk_set_launch", "lesbgk_get_info", "lesbgk_destroy", "lesbgk_moments_noalloc",
-           "lesbgk_last_error", "lesbgk_residual",
+           "lesbgk_last_error", "lesbgk_residual", "lesbgk_rows_bytes", "lesbgk_get_rows", "lesbgk_set_rows",
+           "lesbgk_moments_rows",
            "lesbgk_batch_workspace_size", "lesbgk_batch_slot_bytes", "lesbgk_batch_create", "lesbgk_batch_add",
            "lesbgk_batch_remove", "lesbgk_batch_step", "lesbgk_batch_residuals", "lesbgk_batch_moments",
            "lesbgk_batch_get_populations", "lesbgk_batch_get_info", "lesbgk_batch_set_rows",
@@ -46,6 +47,7 @@ class Params(C.Structure):
         ("wall_T", C.c_double * 2), ("wall_ux", C.c_double * 2), ("g", C.c_double * 2),
         ("wall_specular", C.c_double), ("wall_T_amp", C.c_double), ("wall_T_freq", C.c_double),
         ("dim", C.c_int32), ("bc_x", C.c_int32), ("wall_Tx", C.c_double * 2),
+        ("dx", C.c_double), ("dy", C.c_double), ("row_offset", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
@@ -90,6 +92,10 @@ def lib():
             L.lesbgk_get_info.argtypes = [vp, C.POINTER(Info)]
             L.lesbgk_destroy.argtypes = [vp]
             L.lesbgk_moments_noalloc.argtypes = [C.POINTER(Params), vp, vp, vp, vp]
+            L.lesbgk_rows_bytes.argtypes = [vp, C.c_int32, C.POINTER(C.c_size_t)]
+            L.lesbgk_get_rows.argtypes = [vp, C.c_int32, C.c_int32, vp, vp]
+            L.lesbgk_set_rows.argtypes = [vp, C.c_int32, C.c_int32, vp, vp]
+            L.lesbgk_moments_rows.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp]
             sz, i32 = C.c_size_t, C.c_int32
             L.lesbgk_batch_workspace_size.argtypes = [i32, sz, C.POINTER(sz)]
             L.lesbgk_batch_slot_bytes.argtypes = [C.POINTER(Params), C.POINTER(sz)]
@@ -97,7 +103,8 @@ def lib():
             L.lesbgk_batch_add.argtypes = [vp, C.POINTER(Params), vp, vp, C.POINTER(i32)]
             L.lesbgk_batch_remove.argtypes = [vp, i32, vp]
             L.lesbgk_batch_step.argtypes = [vp, i64, vp]
-            L.lesbgk_batch_residuals.argtypes = [vp, vp, vp]
+            L.lesbgk_batch_residuals.argtypes = [vp, vp, vp, vp]
+            L.lesbgk_residual.argtypes = [vp, vp, i64, vp, vp, vp]
             L.lesbgk_batch_moments.argtypes = [vp, i32, vp, vp, vp]
             L.lesbgk_batch_get_populations.argtypes = [vp, i32, vp, vp]
             L.lesbgk_batch_get_info.argtypes = [vp, i32, C.POINTER(Info)]
@@ -123,7 +130,7 @@ def _check(rc: int) -> None:
 def make_params(*, nroots=4, order=0, nx, ny, bc_y=DIFFUSE, kn, b, visc_exp=0.5, cfl=0.5, dt=0.0,
                 wall_T=(1.0, 1.0), wall_ux=(0.0, 0.0), g=(0.0, 0.0), storage=F32, scheme=UNSPLIT,
                 wall_specular=0.0, wall_T_amp=0.0, wall_T_freq=0.0, dim=2, bc_x=PERIODIC,
-                wall_Tx=(1.0, 1.0)) -> Params:
+                wall_Tx=(1.0, 1.0), dx=0.0, dy=0.0, row_offset=0) -> Params:
     p = Params()
     p.struct_size = C.sizeof(Params)
     p.nroots, p.order, p.nx, p.ny, p.bc_y, p.storage = nroots, order, nx, ny, bc_y, storage
@@ -136,6 +143,7 @@ def make_params(*, nroots=4, order=0, nx, ny, bc_y=DIFFUSE, kn, b, visc_exp=0.5,
     p.dim = dim
     p.bc_x = bc_x
     p.wall_Tx[0], p.wall_Tx[1] = wall_Tx
+    p.dx, p.dy, p.row_offset, p.reserved = dx, dy, row_offset, 0
     return p
 
 
@@ -271,16 +279,17 @@ class Solver:
         moments_host(self.handle, out, hs, self.stream.cuda_stream)
         return out, hs
 
-    def residual(self, snap, steps: int) -> float:
+    def residual(self, snap, steps: int, mass: bool = False):
         """lesbgk_residual: r over the last `steps` steps against `snap`, a
         (4, ny, nx) float32 CUDA tensor that is overwritten with the current
-        fields (steps <= 0 only takes the snapshot and returns NaN)."""
+        fields (steps <= 0 only takes the snapshot and returns NaN); with
+        mass=True returns (r, total mass)."""
         assert snap.is_cuda and snap.dtype == self._torch.float32 and snap.is_contiguous()
         assert tuple(snap.shape) == (4, self.params.ny, self.params.nx)
-        r = C.c_double()
+        r, m = C.c_double(), C.c_double()
         _check(lib().lesbgk_residual(C.c_void_p(self.handle), C.c_void_p(snap.data_ptr()), C.c_int64(int(steps)),
-                                     C.byref(r), C.c_void_p(self.stream.cuda_stream)))
-        return r.value
+                                     C.byref(r), C.byref(m) if mass else None, C.c_void_p(self.stream.cuda_stream)))
+        return (r.value, m.value) if mass else r.value
 
     def populations(self):
         out = self._torch.empty((self.q, self.params.ny, self.params.nx), dtype=self._torch.float32, device="cuda")
@@ -371,10 +380,14 @@ class Batch:
     def step(self, n: int) -> None:
         _check(lib().lesbgk_batch_step(C.c_void_p(self.handle), C.c_int64(n), self._s))
 
-    def residuals(self) -> np.ndarray:
+    def residuals(self, mass: bool = False):
+        """Per-slot residuals (NaN: empty slot or first call; Inf: diverged);
+        with mass=True also the per-slot total mass."""
         out = np.empty(self.capacity)
-        _check(lib().lesbgk_batch_residuals(C.c_void_p(self.handle), C.c_void_p(out.ctypes.data), self._s))
-        return out
+        m = np.empty(self.capacity) if mass else None
+        _check(lib().lesbgk_batch_residuals(C.c_void_p(self.handle), C.c_void_p(out.ctypes.data),
+                                            C.c_void_p(None if m is None else m.ctypes.data), self._s))
+        return (out, m) if mass else out
 
     def moments(self, slot: int, sums: bool = False):
         p = self.params[slot]

@@ -9,16 +9,28 @@ per-slot residuals, and retires converged solves -- reading their moments and
 returning their memory to the pool -- so that solves arriving while others
 are on the GPU join them as slots free up.
 
-Convergence: with r the residual of lesbgk_batch_residuals (max over nodes of
-|d rho| + |d u| + |d T| per unit time since the previous check), a solve is
-done when r < rtol (1e-8; measured in FP32, force-driven channels between
-isothermal walls at rest reach r = 0 to 2e-11, so the bar is not a rounding
-floor), or when r has stopped changing (the last `plateau_checks`
-values within `plateau_rel` of each other) -- the state then changes only at a
-constant rate.  That second case is real: with walls hotter or colder than the
-gas next to them, the diffuse-wall rule exchanges a small, constant amount of
-mass per step (the FP64 oracle shows the same), so such solves approach a
-constant drift rather than a fixed point.
+Convergence (Convergence.verdict), with r the residual of
+lesbgk_batch_residuals (max over nodes of |d rho| + |d u| + |d T| per unit
+time since the previous check) and m the solve's total mass at each check:
+  - converged: r < rtol (1e-8; measured in FP32, force-driven channels
+    between isothermal walls at rest reach r = 0 to 2e-11, so the bar is not
+    a rounding floor);
+  - steady_drift: r has settled on a floor that the wall rule's constant mass
+    exchange sets.  With walls hotter or colder than the gas next to them the
+    diffuse-wall rule adds or removes a small, constant amount of mass per
+    step (the FP64 oracle shows the same), so such solves approach a state
+    that drifts at a constant rate, never a fixed point, and r cannot fall
+    below 1e-8 in any precision.  Two conditions, over three checks r0, r1, r2
+    equally spaced across the latter half of the run so far (so the spacing
+    grows with the run): the part of r still decaying,
+    estimated by Aitken's delta-squared extrapolation of the three,
+    (r2 - r1)^2 / |(r2 - r1) - (r1 - r0)|, is below rtol (a slow exponential
+    approach keeps this large until it has run its course); and the mass
+    changes linearly in time over the same checks, the drift's signature;
+  - diverged: r is infinite (a non-finite node) or not a number after the
+    first check -- the slot is freed at once and the request ends with an
+    error;
+  - max_steps: the cap.
 
 Solves that the batch cannot hold (another width, walls in x such as the
 lid-driven cavities of the mix, the D = 3 set, Maxwell or heated walls) go
@@ -51,31 +63,55 @@ class Request:
     completed: float = float("nan")
     steps: int = 0
     residual: float = float("nan")
-    status: str = "pending"  # pending, running, converged, plateau, max_steps, rejected
-    error: str = ""          # why a request was rejected (the library's message)
+    status: str = "pending"  # pending, running, converged, steady_drift, max_steps, diverged, rejected
+    error: str = ""          # why a request was rejected or diverged
     moments: object = None   # (9, ny, nx) float32 device tensor when kept
+
+
+SOLVED = ("converged", "steady_drift")
 
 
 @dataclass
 class Convergence:
-    rtol: float = 1e-8  # the FP32 floor is far below it (force-driven channels reach r = 0)
-    plateau_rel: float = 0.02
-    plateau_checks: int = 4
+    rtol: float = 1e-8          # the FP32 floor is far below it (force-driven channels reach r = 0)
+    min_checks: int = 9         # the drift test's lag is at least 2 check intervals
+    mass_linear: float = 0.05   # |m2 - 2 m1 + m0| <= mass_linear |m2 - m1| (+ rounding of m)
+    mass_eps: float = 1e-6      # rounding allowance of the mass per node (FP32 per-node values)
     max_steps: int = 400_000
 
-    def verdict(self, hist, steps):
+    def verdict(self, hist, steps, mass=None, nodes: int = 1):
+        """hist: r at each check (the first is NaN: no previous snapshot);
+        mass: the total mass at the same checks (or None: no drift test);
+        nodes: the solve's node count (scales the mass rounding allowance)."""
         if not hist:
             return None
         r = hist[-1]
+        if np.isinf(r) or (np.isnan(r) and len(hist) > 1):
+            return "diverged"
         if np.isfinite(r) and r < self.rtol:
             return "converged"
-        if len(hist) >= self.plateau_checks:
-            tail = np.array(hist[-self.plateau_checks:])
-            if np.all(np.isfinite(tail)) and np.ptp(tail) <= self.plateau_rel * np.max(tail):
-                return "plateau"
+        if mass is not None and len(hist) >= self.min_checks and self._drift(hist, mass, nodes):
+            return "steady_drift"
         if steps >= self.max_steps:
             return "max_steps"
         return None
+
+    def _drift(self, hist, mass, nodes):
+        k = (len(hist) - 1) // 4  # lag: r0, r1, r2 span the latter half of the checks so far
+        r0, r1, r2 = hist[-1 - 2 * k], hist[-1 - k], hist[-1]
+        m0, m1, m2 = mass[-1 - 2 * k], mass[-1 - k], mass[-1]
+        if not all(np.isfinite(v) for v in (r0, r1, r2, m0, m1, m2)):
+            return False
+        d1, d2 = r1 - r0, r2 - r1
+        if abs(d2) > abs(d1):  # not contracting
+            return False
+        den = abs(d2 - d1)
+        transient = 0.0 if d2 == 0.0 else (d2 * d2 / den if den > 0.0 else np.inf)
+        if not transient < self.rtol:
+            return False
+        eps = self.mass_eps * nodes
+        dm = m2 - m1
+        return abs(dm) > eps and abs(m2 - 2.0 * m1 + m0) <= self.mass_linear * abs(dm) + eps
 
 
 def poisson_trace(n: int, rate: float, problems, seed: int = 0):
@@ -138,9 +174,9 @@ class WideLane:
         with self._torch.cuda.stream(st):  # the solver's allocations belong to its stream
             s = L.Solver(p, stream=st)
             prev = self._torch.empty((4, p.ny, p.nx), dtype=self._torch.float32, device="cuda")
-        s.residual(prev, 0)  # the first snapshot
+        r, m = s.residual(prev, 0, mass=True)  # the first snapshot
         self.used += need
-        self.active[self._next] = (req, s, st, prev, [])
+        self.active[self._next] = (req, s, st, prev, ([r], [m]))
         self._next += 1
         return True
 
@@ -153,9 +189,10 @@ class WideLane:
         |d rho| + |d u| + |d T|, per unit time; lesbgk_residual, the same
         quantity as lesbgk_batch_residuals)."""
         out = {}
-        for key, (req, s, st, prev, hist) in self.active.items():
-            r = s.residual(prev, n)
+        for key, (req, s, st, prev, (hist, mass)) in self.active.items():
+            r, m = s.residual(prev, n, mass=True)
             hist.append(r)
+            mass.append(m)
             out[key] = r
         return out
 
@@ -170,12 +207,17 @@ class WideLane:
 
 
 class ServingLoop:
+    """batch / wide: an L.Batch and a WideLane to serve with (created from
+    capacity, pool_bytes, wide_bytes when not given)."""
+
     def __init__(self, capacity: int, pool_bytes: int, nx: int = 4, check_every: int = 256,
                  conv: Convergence | None = None, keep_moments: bool = False, stream=None,
-                 wide_bytes: int | None = None, wide_solvers: int = 16):
+                 wide_bytes: int | None = None, wide_solvers: int = 16, batch=None, wide=None):
         self.nx = nx
-        self.batch = L.Batch(capacity=capacity, nx=nx, pool_bytes=pool_bytes, stream=stream)
-        self.wide = WideLane(pool_bytes if wide_bytes is None else wide_bytes, wide_solvers)
+        self.batch = batch if batch is not None else L.Batch(capacity=capacity, nx=nx, pool_bytes=pool_bytes,
+                                                             stream=stream)
+        self.wide = wide if wide is not None else WideLane(pool_bytes if wide_bytes is None else wide_bytes,
+                                                           wide_solvers)
         self.check_every = check_every
         self.conv = conv or Convergence()
         self.keep_moments = keep_moments
@@ -185,7 +227,7 @@ class ServingLoop:
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting = collections.deque()       # for the batch
         waiting_wide = collections.deque()  # for the wide lane
-        active = {}  # slot -> (request, residual history)
+        active = {}  # slot -> (request, residual history, mass history)
         t0 = clock()
         done = []
 
@@ -215,7 +257,7 @@ class ServingLoop:
                 waiting.popleft()
                 req.admitted = clock() - t0
                 req.status = "running"
-                active[slot] = (req, [])
+                active[slot] = (req, [], [])
             while waiting_wide:
                 try:
                     if not wide.try_admit(waiting_wide[0]):
@@ -234,30 +276,35 @@ class ServingLoop:
                 wide.step(self.check_every)  # their own streams: they run beside the batch
             if active:
                 bt.step(self.check_every)
-                res = bt.residuals()
+                res, mass = bt.residuals(mass=True)
                 now = clock() - t0
                 for slot in list(active):
-                    req, hist = active[slot]
+                    req, hist, mhist = active[slot]
                     req.steps = bt.info(slot).steps_done
                     hist.append(float(res[slot]))
-                    v = self.conv.verdict([h for h in hist if np.isfinite(h)], req.steps)
+                    mhist.append(float(mass[slot]))
+                    v = self.conv.verdict(hist, req.steps, mhist, req.problem.cells)
                     if v is None:
                         continue
-                    if self.keep_moments:
+                    if self.keep_moments and v != "diverged":
                         req.moments = bt.moments(slot)
-                    bt.remove(slot)
+                    if v == "diverged":
+                        req.error = "non-finite residual: the solve diverged"
+                    bt.remove(slot)  # a diverged slot frees its memory at once
                     del active[slot]
                     finish(req, v, hist[-1], now)
             if wide.active:
                 res = wide.residuals(self.check_every)
                 now = clock() - t0
                 for key in list(wide.active):
-                    req, s, _, _, hist = wide.active[key]
+                    req, s, _, _, (hist, mhist) = wide.active[key]
                     req.steps = s.info.steps_done
-                    v = self.conv.verdict([h for h in hist if np.isfinite(h)], req.steps)
+                    v = self.conv.verdict(hist, req.steps, mhist, req.problem.cells)
                     if v is None:
                         continue
-                    wide.retire(key, self.keep_moments)
+                    if v == "diverged":
+                        req.error = "non-finite residual: the solve diverged"
+                    wide.retire(key, self.keep_moments and v != "diverged")
                     finish(req, v, res[key], now)
         return done
 
@@ -280,13 +327,14 @@ def run_plain_fifo(requests, check_every: int = 256, conv: Convergence | None = 
         req.admitted = clock() - t0
         s = L.Solver(L.params_from_problem(req.problem), stream=stream)
         prev = torch.empty((4, req.problem.ny, req.problem.nx), dtype=torch.float32, device="cuda")
-        s.residual(prev, 0)
-        hist = []
+        r, m = s.residual(prev, 0, mass=True)
+        hist, mhist = [r], [m]
         while True:
             s.step(check_every)
-            r = s.residual(prev, check_every)
+            r, m = s.residual(prev, check_every, mass=True)
             hist.append(r)
-            v = conv.verdict(hist, s.info.steps_done)
+            mhist.append(m)
+            v = conv.verdict(hist, s.info.steps_done, mhist, req.problem.cells)
             if v is not None:
                 break
         req.status, req.residual, req.steps = v, hist[-1], s.info.steps_done
@@ -297,14 +345,16 @@ def run_plain_fifo(requests, check_every: int = 256, conv: Convergence | None = 
 
 
 def latency_summary(done):
-    """Latency percentiles and throughput over the solved requests (rejected
-    ones are counted apart)."""
-    solved = [r for r in done if r.status != "rejected"]
+    """Latency percentiles and throughput over the solved requests (converged,
+    or settled on the wall-mass drift); every other ending (max_steps,
+    diverged, rejected) is counted in `status` and not as a solve."""
+    solved = [r for r in done if r.status in SOLVED]
+    status = dict(collections.Counter(r.status for r in done))
     lat = np.array([r.completed - r.arrival for r in solved])
     if not len(lat):
-        return {"completed": 0, "rejected": len(done)}
+        return {"completed": 0, "status": status}
     first = min(r.arrival for r in solved)
     last = max(r.completed for r in solved)
     return {"completed": len(solved), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "mean_s": float(lat.mean()), "solves_per_s": len(solved) / max(last - first, 1e-9),
-            "status": dict(collections.Counter(r.status for r in done)), "rejected": len(done) - len(solved)}
+            "status": status, "not_solved": len(done) - len(solved)}

@@ -1,19 +1,132 @@
-"""Host-side logic of the serving loop (no GPU): the convergence verdict and
-the seeded arrival trace."""
+"""Host-side logic of the serving loop (no GPU): the convergence verdict, the
+eviction of diverged solves (driven through a fake batch), and the seeded
+arrival trace."""
 from __future__ import annotations
 
 import numpy as np
 
+from paper_1209_6548_gb300 import inputs as I
 from paper_1209_6548_gb300 import serve as S
 
 
-def test_verdict_threshold_plateau_and_cap():
-    c = S.Convergence(rtol=1e-6, plateau_rel=0.02, plateau_checks=4, max_steps=1000)
+def test_verdict_threshold_diverged_and_cap():
+    c = S.Convergence(rtol=1e-6, max_steps=1000)
     assert c.verdict([], 0) is None
-    assert c.verdict([1e-3, 1e-5, 5e-7], 100) == "converged"
-    assert c.verdict([1e-3, 5e-4, 2e-4], 100) is None
-    assert c.verdict([3e-5, 1.31e-5, 1.32e-5, 1.315e-5, 1.32e-5], 100) == "plateau"
-    assert c.verdict([1e-3, 5e-4, 2e-4, 1e-4], 1000) == "max_steps"
+    assert c.verdict([np.nan], 0) is None  # the first check has no residual yet
+    assert c.verdict([np.nan, 1e-3, 1e-5, 5e-7], 100) == "converged"
+    assert c.verdict([np.nan, 1e-3, 5e-4, 2e-4], 100) is None
+    assert c.verdict([np.nan, 1e-3, 5e-4, 2e-4, 1e-4], 1000) == "max_steps"
+    assert c.verdict([np.nan, 1e-3, np.inf], 100) == "diverged"
+    assert c.verdict([np.nan, 1e-3, np.nan], 100) == "diverged"
+
+
+def _drifting(t, floor=1.3e-5, amp=1e-3, tau=2000.0, rate=2e-7):
+    """A residual decaying exponentially (time constant tau) onto a floor, and
+    a mass growing by a transient plus a constant drift."""
+    r = floor + amp * np.exp(-t / tau)
+    m = 4096.0 + rate * t - 0.05 * np.exp(-t / tau)
+    return r, m
+
+
+def test_steady_drift_needs_the_transient_gone_and_a_linear_mass():
+    c = S.Convergence(rtol=1e-8)
+    t = np.arange(0, 200_001, 256.0)
+    r, m = _drifting(t)
+    r[0] = np.nan
+    found = None
+    for k in range(2, len(t)):
+        v = c.verdict(list(r[:k]), int(t[k - 1]), list(m[:k]), nodes=4096)
+        if v is not None:
+            found = (v, t[k - 1])
+            break
+    assert found is not None and found[0] == "steady_drift"
+    # declared only once the decaying part amp exp(-t/tau) is below 1e-8
+    assert 1e-3 * np.exp(-found[1] / 2000.0) < 1e-8
+    # the same residual floor without the drift signature -- a constant mass,
+    # or one whose rate keeps changing (quadratic) -- gets no verdict
+    for m_other in (np.full_like(t, 4096.0), 4096.0 + 1e-9 * t * t):
+        assert all(c.verdict(list(r[:k]), int(t[k - 1]), list(m_other[:k]), nodes=4096) is None
+                   for k in range(2, len(t)))
+
+
+def test_slow_exponential_approach_is_not_a_plateau():
+    """A residual still decaying with a time constant far beyond the checks
+    (the case a fixed-ratio plateau test passed after a few checks) is not
+    declared steady: Aitken's estimate of its transient stays large."""
+    c = S.Convergence(rtol=1e-8, max_steps=10**9)
+    t = np.arange(0, 40_001, 256.0)
+    r, m = _drifting(t, floor=1e-6, amp=1e-4, tau=50_000.0)
+    r[0] = np.nan
+    assert all(c.verdict(list(r[:k]), int(t[k - 1]), list(m[:k]), nodes=4096) is None for k in range(2, len(t)))
+
+
+class FakeBatch:
+    """Stands in for L.Batch: per-problem residual and mass trajectories,
+    `capacity` slots."""
+
+    def __init__(self, capacity, traj):
+        self.capacity, self.traj = capacity, traj
+        self.slots = {}   # slot -> [problem name, steps done, checks]
+        self.removed = []
+
+    def try_add(self, p):
+        for k in range(self.capacity):
+            if k not in self.slots:
+                self.slots[k] = [self._names.pop(0), 0, 0]
+                return k
+        return None
+
+    def step(self, n):
+        for v in self.slots.values():
+            v[1] += n
+
+    def residuals(self, mass=False):
+        res, ms = np.full(self.capacity, np.nan), np.full(self.capacity, np.nan)
+        for k, (name, steps, checks) in self.slots.items():
+            res[k], ms[k] = self.traj[name](steps, checks)
+            self.slots[k][2] += 1
+        return (res, ms) if mass else res
+
+    def info(self, slot):
+        return type("Info", (), {"steps_done": self.slots[slot][1]})
+
+    def moments(self, slot):
+        return None
+
+    def remove(self, slot):
+        self.removed.append((self.slots[slot][0], self.slots[slot][1]))
+        del self.slots[slot]
+
+
+class NoWide:
+    active = {}
+
+    def try_admit(self, req):
+        raise AssertionError("every problem here fits the batch")
+
+
+def test_diverged_solve_is_evicted_at_once_and_frees_its_slot():
+    probs = [I.Problem(name=n, nx=4, ny=32) for n in ("ok0", "boom", "ok1", "ok2")]
+    reqs = [S.Request(rid=k, arrival=0.0, problem=p) for k, p in enumerate(probs)]
+
+    def converging(steps, checks):
+        return (np.nan if checks == 0 else 1e-3 * np.exp(-steps / 300.0)), 128.0
+
+    def diverging(steps, checks):
+        return (np.nan if checks == 0 else (1e-3 if checks < 3 else np.inf)), 128.0
+
+    fb = FakeBatch(2, {"ok0": converging, "ok1": converging, "ok2": converging, "boom": diverging})
+    fb._names = [p.name for p in probs]
+    loop = S.ServingLoop(capacity=2, pool_bytes=0, check_every=128, batch=fb, wide=NoWide(),
+                         conv=S.Convergence(rtol=1e-8, max_steps=100_000))
+    done = loop.run(reqs, clock=lambda: 0.0)
+    status = {r.problem.name: r.status for r in done}
+    assert status == {"ok0": "converged", "boom": "diverged", "ok1": "converged", "ok2": "converged"}
+    boom = next(r for r in done if r.problem.name == "boom")
+    assert boom.error and boom.steps == 4 * 128  # evicted at the first non-finite residual (4th check)
+    assert ("boom", 4 * 128) in fb.removed
+    summary = S.latency_summary(done)
+    assert summary["completed"] == 3 and summary["status"]["diverged"] == 1
 
 
 def test_poisson_trace_is_seeded_and_ordered():
