@@ -60,6 +60,10 @@ int check_params(const lesbgk_params *p) {
       if (!(p->wall_Tx[s] > 0.0) || !std::isfinite(p->wall_Tx[s])) return fail(LESBGK_EINVAL, "wall_Tx must be > 0");
   }
   if (p->bc_y == LESBGK_DIFFUSE && p->ny < 2) return fail(LESBGK_EINVAL, "walls need ny >= 2");
+  if (!(p->dx >= 0.0 && p->dy >= 0.0) || !std::isfinite(p->dx) || !std::isfinite(p->dy) ||
+      ((p->dx > 0.0) != (p->dy > 0.0)))
+    return fail(LESBGK_EINVAL, "dx and dy must both be 0 (derived) or both > 0");
+  if (p->reserved != 0) return fail(LESBGK_EINVAL, "reserved must be 0");
   if (p->storage != LESBGK_F32 && p->storage != LESBGK_F16 && p->storage != LESBGK_BF16)
     return fail(LESBGK_EINVAL, "storage must be LESBGK_F32, LESBGK_F16 or LESBGK_BF16");
   if (p->storage != LESBGK_F32 && order != default_order(p->nroots))
@@ -127,6 +131,10 @@ int build_setup(const lesbgk_params &p, int order, const FieldStats *stats, Setu
     h->dx = 1.0 / (p.nx - 1);
     h->dy = 1.0 / (p.ny - 1);
   }
+  if (p.dx > 0.0) {  // explicit spacing (a y-slab keeps the whole domain's)
+    h->dx = p.dx;
+    h->dy = p.dy;
+  }
   // reference state for tau_ref
   double tmax = 1.0, rmax = 1.0;
   if (p.bc_y == LESBGK_DIFFUSE)
@@ -191,6 +199,7 @@ int build_setup(const lesbgk_params &p, int order, const FieldStats *stats, Setu
   A.walls = p.bc_y == LESBGK_DIFFUSE ? 1 : 0;
   A.wspec = (float)p.wall_specular;
   A.plane = (long long)p.nx * p.ny;
+  A.row_key = (unsigned)p.row_offset;
   h->nroots = nr;
   h->order = N;
   h->dim = D;

@@ -71,3 +71,17 @@ def test_two_ranks_gloo():
     assert not set(parts[0]) & set(parts[1])
     assert parts == SH.lpt_partition([SH.instance_cost(p, 2000) for p in I.batch_mix(n=200, seed=1)], 2)
     assert slowest == 2.0
+
+
+def test_costs_count_stored_values_and_steady_state_work():
+    """D = 3 instances cost their stored half (nroots^3/2 values per node);
+    run-to-steady costs grow with ny and with 1/Kn, as the diffusion time
+    over the time step does."""
+    from dataclasses import replace
+    p = I.Problem(name="c", nx=4, ny=65, kn=0.1, b=0.0)
+    assert SH.instance_cost(replace(p, dim=3), 100) == 2 * SH.instance_cost(p, 100)
+    assert SH.instance_cost(replace(p, nroots=6, dim=3), 100) == 108 / 16 * SH.instance_cost(p, 100)
+    base = SH.instance_cost(p, to_steady=True)
+    assert SH.instance_cost(replace(p, kn=0.01), to_steady=True) == 10 * base
+    assert SH.instance_cost(replace(p, ny=129), to_steady=True) == pytest.approx(base * 129 * 128 / (65 * 64))
+    assert SH.instance_cost(replace(p, b=0.5), to_steady=True) == 2 * base  # slower heat diffusion
