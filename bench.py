@@ -46,6 +46,19 @@ def parse():
     ap.add_argument("--lattice-steps", type=int, default=1000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="default workload: leave out the batched-solves object")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="default workload: leave out the serving object")
+    ap.add_argument("--decomp", choices=["slab", "replica"], default="slab",
+                    help="with several ranks: split the one domain into y-slabs (strong scaling), or run "
+                         "an independent replica per rank (weak scaling)")
+    ap.add_argument("--halo-steps", type=int, default=8,
+                    help="y-slabs: time steps per halo exchange (halo of 2k rows)")
+    ap.add_argument("--serve-requests", type=int, default=100,
+                    help="requests of the default line's serving object")
+    ap.add_argument("--serve-plain-budget", type=float, default=20.0,
+                    help="seconds the default line's FIFO serving baseline may run")
     ap.add_argument("--workload", choices=["tgv", "batch", "serve", "precision"], default="tgv",
                     help="tgv: 4096^2 Taylor-Green throughput (default); batch: 512-instance channel mix; "
                          "serve: Poisson arrivals run to steady state with continuous batching")
@@ -320,6 +333,118 @@ def run_reference(args, world, rank):
     return 0
 
 
+def measure_batch_fixed(params, nsteps, passes, warmup, stream, local, plain_sample, barrier=None,
+                        max_over_ranks=None):
+    """Batched solves of fixed length: one pass = L2 flush, admit every
+    instance, nsteps steps for all, the nine moment fields of every instance;
+    `passes` timed passes after `warmup`.  Also times one batch step (CUDA
+    events) and the plain solver on `plain_sample` of the instances one at a
+    time.  Returns (dict, batch step ms, rows per item)."""
+    import torch
+    from paper_1209_6548_gb300 import lesbgk as L
+
+    barrier = barrier or torch.cuda.synchronize
+    max_over_ranks = max_over_ranks or (lambda x: x)
+    pool = int(sum(L.batch_slot_bytes(p) for p in params) * 1.05) + (1 << 20)
+    bt = L.Batch(capacity=len(params), nx=4, pool_bytes=pool, stream=stream)
+    outs = [torch.empty((9, p.ny, p.nx), dtype=torch.float32, device="cuda") for p in params]
+
+    def admit_all():
+        for s in list(bt.params):
+            bt.remove(s)
+        return [bt.add(p) for p in params]
+
+    admit_all()
+    rows = bt.autotune((8, 16, 32, 64, 128))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # larger than the 129 MB L2
+
+    def one_pass():
+        flush.fill_(1)  # L2 flushed between timed passes (inside a pass the steps reuse it)
+        sl = admit_all()
+        bt.step(nsteps)
+        for s, o in zip(sl, outs):
+            L.lib().lesbgk_batch_moments(L.C.c_void_p(bt.handle), L.C.c_int32(s), L.C.c_void_p(o.data_ptr()),
+                                         None, L.C.c_void_p(stream.cuda_stream))
+
+    for _ in range(warmup):
+        one_pass()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    admit_all()
+    e0.record(stream)
+    bt.step(640)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / 640
+    with ClockSampler(local) as clk:
+        barrier()
+        w0 = time.perf_counter()
+        for _ in range(passes):
+            one_pass()
+        barrier()
+        wsec = max_over_ranks(time.perf_counter() - w0)
+    bt.close()
+    n = len(params)
+    idx = list(range(0, n, max(1, n // plain_sample)))[:plain_sample]
+    lups = [p.nx * p.ny * nsteps for p in params]
+    torch.cuda.synchronize()
+    p0 = time.perf_counter()
+    for i in idx:
+        s = L.Solver(params[i], stream=stream)
+        s.step(nsteps)
+        L.moments(s.handle, outs[i].data_ptr(), None, stream.cuda_stream)
+        s.close()
+    torch.cuda.synchronize()
+    psec = time.perf_counter() - p0
+    plain_sec_per_lup = psec / sum(lups[i] for i in idx)
+    clocks = clk.summary()
+    out = {"solves_per_s_this_rank": n * passes / wsec, "wall_s": wsec, "passes": passes,
+           "instance_mlups_this_rank": sum(lups) * passes / wsec / 1e6,
+           "step_ms": step_ms, "rows_per_item": rows,
+           "plain": {"solves_per_s": len(idx) / psec, "sample": f"{len(idx)} of the {n} instances, one at a time",
+                     "mlups": 1.0 / plain_sec_per_lup / 1e6,
+                     "est_solves_per_s_full_mix": 1.0 / (plain_sec_per_lup * sum(lups) / n)},
+           "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]}}
+    return out, step_ms, rows, pool
+
+
+def measure_serve(requests, rate, pool_mb, plain_budget, stream, local, seed=0, cavity_share=0.1):
+    """Serving: a seeded Poisson stream of `requests` solves at `rate` per
+    second (the serving mix, run to steady state), the continuous-batching loop
+    against the plain solver serving the same trace one request at a time
+    (FIFO, within plain_budget seconds).  Returns a dict."""
+    from paper_1209_6548_gb300 import serve as S
+
+    probs = S.serving_mix(requests, seed=seed, cavity_share=cavity_share)
+    conv = S.Convergence()
+    warm = S.ServingLoop(capacity=8, pool_bytes=int(pool_mb * 2**20), stream=stream, conv=conv)
+    warm.run(S.poisson_trace(8, rate, probs[:8], seed=99))  # kernel loading, graph build
+    warm.batch.close()
+    loop = S.ServingLoop(capacity=1024, pool_bytes=int(pool_mb * 2**20), stream=stream, conv=conv)
+    reqs = S.poisson_trace(requests, rate, probs, seed=seed)
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        done = loop.run(reqs)
+        wall = time.perf_counter() - t0
+    loop.batch.close()
+    served = S.latency_summary(done)
+    plain_reqs = S.poisson_trace(requests, rate, probs, seed=seed)
+    p0 = time.perf_counter()
+    plain_done = S.run_plain_fifo(plain_reqs, conv=conv, stream=stream, time_budget=plain_budget)
+    plain_wall = time.perf_counter() - p0
+    plain = S.latency_summary(plain_done)
+    clocks = clk.summary()
+    return {"requests": requests, "rate_per_s": rate, "pool_mb": pool_mb, "check_every": loop.check_every,
+            "solves_per_s": served.get("solves_per_s"), "completed": served.get("completed"),
+            "latency": {"p50_s": served.get("p50_s"), "p99_s": served.get("p99_s"), "mean_s": served.get("mean_s")},
+            "status": served.get("status"), "wall_s": wall,
+            "convergence": "r < 1e-8, or steady_drift: Aitken transient of r < 1e-8 with the total mass drifting "
+                           "linearly (the wall rule's mass exchange); cap 400k steps",
+            "plain_fifo": {**plain, "wall_s": plain_wall, "budget_s": plain_budget,
+                           "note": "the same trace, one request at a time, within the budget"},
+            "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]}}
+
+
 def run_batch(args, world, rank, local):
     """Batched solves: the seeded mix of independent channel flows (nx = 4, ny
     log-uniform 16-1024, Couette / Fourier / Poiseuille, Kn log-uniform
@@ -328,9 +453,10 @@ def run_batch(args, world, rank, local):
     moment fields of every instance.  value = solves/s.  The plain solver runs a
     sample of the same instances one at a time (lesbgk_create, lesbgk_step,
     lesbgk_moments) for the baseline.  Second mode (unless --no-steady): the
-    same instances run to steady state (r < 1e-8 or a plateau, as in the
-    serving loop) in one batch, all admitted at once, against the plain solver
-    running them to steady state one at a time within --plain-budget."""
+    same instances run to steady state (r < 1e-8, or settled on the wall-mass
+    drift, as in the serving loop) in one batch, all admitted at once, against
+    the plain solver running them to steady state one at a time within
+    --plain-budget; solves/s counts solved instances only."""
     import collections
     import numpy as np
     import torch
@@ -365,68 +491,17 @@ def run_batch(args, world, rank, local):
         t = torch.tensor([x], dtype=torch.float64, device="cuda")
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         return float(t.item())
-    pool = int(sum(L.batch_slot_bytes(p) for p in params) * 1.05) + (1 << 20)
     stream = torch.cuda.current_stream()
-    bt = L.Batch(capacity=len(params), nx=4, pool_bytes=pool, stream=stream)
-    outs = [torch.empty((9, p.ny, p.nx), dtype=torch.float32, device="cuda") for p in params]
-
-    def admit_all():
-        for s in list(bt.params):
-            bt.remove(s)
-        return [bt.add(p) for p in params]
-
-    slots = admit_all()
-    rows = bt.autotune((8, 16, 32, 64, 128))
-    lups_per_solve = [4 * p.ny * nsteps for p in params]
-
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # larger than the 129 MB L2
-
-    def one_pass():
-        flush.fill_(1)  # L2 flushed between timed passes (inside a pass the steps reuse it)
-        sl = admit_all()
-        bt.step(nsteps)
-        for s, o in zip(sl, outs):
-            L.lib().lesbgk_batch_moments(L.C.c_void_p(bt.handle), L.C.c_int32(s), L.C.c_void_p(o.data_ptr()),
-                                         None, L.C.c_void_p(stream.cuda_stream))
-
-    for _ in range(args.warmup):
-        one_pass()
-    torch.cuda.synchronize()
-    # kernel-only timing of one batch step (all instances), graph replays
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    admit_all()
-    e0.record(stream)
-    bt.step(640)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    step_ms = e0.elapsed_time(e1) / 640
-    with ClockSampler(local) as clk:
-        barrier()
-        w0 = time.perf_counter()
-        for _ in range(args.steps):
-            one_pass()
-        barrier()
-        wsec = max_over_ranks(time.perf_counter() - w0)
+    fixed, step_ms, rows, pool = measure_batch_fixed(params, nsteps, args.steps, args.warmup, stream, local,
+                                                     args.plain_sample, barrier, max_over_ranks)
     n = len(params)
+    wsec = fixed["wall_s"]
     value = len(all_probs) * args.steps / wsec
-    # plain one-at-a-time baseline on a sample
     idx = list(range(0, n, max(1, n // args.plain_sample)))[: args.plain_sample]
-    torch.cuda.synchronize()
-    p0 = time.perf_counter()
-    for i in idx:
-        s = L.Solver(params[i], stream=stream)
-        s.step(nsteps)
-        L.moments(s.handle, outs[i].data_ptr(), None, stream.cuda_stream)
-        s.close()
-    torch.cuda.synchronize()
-    psec = time.perf_counter() - p0
-    plain_solves_s = len(idx) / psec
-    plain_sec_per_lup = psec / sum(lups_per_solve[i] for i in idx)
     cells = sum(4 * p.ny for p in params)
     peak, peak_kind = measured_peak()
     eff = 2 * 16 * 4 * cells / (step_ms / 1e3) / 1e9
-    clocks = clk.summary()
-    bt.close()
+    clocks = fixed["clocks"]
     steady = None
     if not args.no_steady:
         reqs = [S.Request(rid=k, arrival=0.0, problem=p) for k, p in enumerate(probs)]
@@ -441,11 +516,15 @@ def run_batch(args, world, rank, local):
         plain_reqs = [S.Request(rid=k, arrival=0.0, problem=probs[i]) for k, i in enumerate(idx)]
         pdone = S.run_plain_fifo(plain_reqs, stream=stream, time_budget=args.plain_budget)
         pwall = sum(r.completed - r.admitted for r in pdone)
-        steady = {"solves_per_s": len(all_probs) / ssec, "wall_s": ssec, "solved": len(done),
+        solved = [r for r in done if r.status in S.SOLVED]
+        psolved = [r for r in pdone if r.status in S.SOLVED]
+        steady = {"solves_per_s": len(solved) * world / ssec, "wall_s": ssec, "solved": len(solved),
                   "status": dict(collections.Counter(r.status for r in done)),
                   "steps_median": float(np.median(steps)), "steps_max": int(steps.max()),
-                  "criterion": "r < 1e-8, or r flat within 2% over 4 checks 256 steps apart",
-                  "plain": {"solved": len(pdone), "solves_per_s": len(pdone) / max(pwall, 1e-9),
+                  "criterion": "r < 1e-8, or steady_drift: Aitken transient of r < 1e-8 with the total mass "
+                               "drifting linearly (the wall rule's mass exchange); cap 400k steps",
+                  "plain": {"solved": len(psolved), "solves_per_s": len(psolved) / max(pwall, 1e-9),
+                            "status": dict(collections.Counter(r.status for r in pdone)),
                             "sample": f"the first {len(pdone)} of {len(idx)} sampled instances within "
                                       f"{args.plain_budget:g} s, one at a time"}}
     line = {
@@ -458,9 +537,7 @@ def run_batch(args, world, rank, local):
                    "l2": "L2 flushed between timed passes (256 MB write); within a pass the %.0f MB working "
                          "set is partly L2-resident" % (2 * 64 * cells / 1e6)},
         "instance_mlups": sum(4 * p.ny * nsteps for p in all_probs) * args.steps / wsec / 1e6,
-        "plain": {"solves_per_s": plain_solves_s, "sample": f"{len(idx)} of the {n} instances, one at a time",
-                  "mlups": 1.0 / plain_sec_per_lup / 1e6,
-                  "est_solves_per_s_full_mix": 1.0 / (plain_sec_per_lup * sum(lups_per_solve) / n)},
+        "plain": fixed["plain"],
         "roofline": {"bound": "hbm", "achieved": eff, "peak": peak, "unit": "GB/s", "frac": eff / peak,
                      "traffic": None, "peak_source": peak_kind, "kernel": "k_batch_step<4,3,4>",
                      "kernel_ms": step_ms,
@@ -495,44 +572,121 @@ def run_serve(args, world, rank, local):
     torch.cuda.set_device(local)
     B.build()
     stream = torch.cuda.current_stream()
-    probs = S.serving_mix(args.requests, seed=rank, cavity_share=0.1)
-    conv = S.Convergence()
-    # warm-up: a few solves through a small loop (kernel loading, graph build)
-    warm = S.ServingLoop(capacity=8, pool_bytes=int(args.pool_mb * 2**20), stream=stream, conv=conv)
-    warm.run(S.poisson_trace(8, args.rate, probs[:8], seed=99))
-    warm.batch.close()
-    loop = S.ServingLoop(capacity=1024, pool_bytes=int(args.pool_mb * 2**20), stream=stream, conv=conv)
-    reqs = S.poisson_trace(args.requests, args.rate, probs, seed=rank)
-    with ClockSampler(local) as clk:
-        t0 = time.perf_counter()
-        done = loop.run(reqs)
-        wall = time.perf_counter() - t0
-    served = S.latency_summary(done)
-    plain_reqs = S.poisson_trace(args.requests, args.rate, probs, seed=rank)
-    p0 = time.perf_counter()
-    plain_done = S.run_plain_fifo(plain_reqs, conv=conv, stream=stream, time_budget=args.plain_budget)
-    plain_wall = time.perf_counter() - p0
-    plain = S.latency_summary(plain_done)
-    clocks = clk.summary()
+    sv = measure_serve(args.requests, args.rate, args.pool_mb, args.plain_budget, stream, local, seed=rank)
     line = {
-        "metric": "served solves/s (p50/p99 latency)", "value": served.get("solves_per_s"), "unit": "solves/s",
-        "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": wall * 1e3, "higher_is_better": True,
+        "metric": "served solves/s (p50/p99 latency)", "value": sv["solves_per_s"], "unit": "solves/s",
+        "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": sv["wall_s"] * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"serve_{args.requests}_poisson{args.rate:g}", "requests": args.requests,
-                   "rate_per_s": args.rate, "pool_mb": args.pool_mb, "check_every": loop.check_every,
+                   "rate_per_s": args.rate, "pool_mb": args.pool_mb, "check_every": sv["check_every"],
                    "mix": "nx 4, ny 16-512, Couette/Fourier/Poiseuille, Kn 0.01-0.5, 20% D2Q36; "
                           "10% lid-driven cavities 256^2 (lid 0.05, Kn 0.05-0.5) in the wide lane",
-                   "convergence": "r < 1e-8 or r flat within 2% over 4 checks (cap 400k steps)"},
-        "latency": {"p50_s": served.get("p50_s"), "p99_s": served.get("p99_s"), "mean_s": served.get("mean_s")},
-        "offered_per_s": args.rate, "achieved_per_s": served.get("solves_per_s"), "status": served.get("status"),
-        "wall_s": wall,
-        "plain_fifo": {**plain, "wall_s": plain_wall, "budget_s": args.plain_budget,
-                       "note": "requests completed within the budget, one at a time"},
-        "gpu_launches": None,
-        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
+                   "convergence": sv["convergence"]},
+        "latency": sv["latency"], "offered_per_s": args.rate, "achieved_per_s": sv["solves_per_s"],
+        "status": sv["status"], "wall_s": sv["wall_s"], "plain_fifo": sv["plain_fifo"],
+        "gpu_launches": None, "clocks": sv["clocks"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_slab(args, world, rank, local):
+    """One 4096^2 solve split over the ranks in y-slabs (slab.py): each rank's
+    solver holds its slab plus a halo of 2k rows, exchanged with its
+    neighbours over NCCL every k steps (k = --halo-steps); the conservation
+    totals are one FP64 allreduce.  value = the whole domain's lattice
+    updates per second (strong scaling: the work is fixed as N grows)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1209_6548_gb300 import build as B
+    from paper_1209_6548_gb300 import inputs as I
+    from paper_1209_6548_gb300 import lesbgk as L
+    from paper_1209_6548_gb300 import slab as SL
+
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    n, nsteps, k = args.n, args.lattice_steps, args.halo_steps
+    nroots, dim, order, q = LATTICES[args.velocity_set]
+    prob = tgv_problem(n, args, nsteps)
+    fields = I.initial_fields(prob)
+    storage = {"f32": L.F32, "f16": L.F16, "bf16": L.BF16}[args.storage]
+    stream = torch.cuda.current_stream()
+    # the whole domain's time step (tau_ref depends on its fields) and spacing, as the library sets them
+    whole = L.Solver(L.params_from_problem(prob), h_init=fields, stream=stream)
+    dt, dx, dy = whole.info.dt, whole.info.dx, whole.info.dy
+    whole.close()
+    del whole
+    torch.cuda.empty_cache()
+    slab = SL.partition(n, world, 2 * k, True)[rank]
+    st = SL.GpuSlab(prob, slab, fields, dt, dx, dy, storage, stream=stream)
+    d_fields = torch.from_numpy(SL.slab_fields(fields, slab)).cuda()
+    mom = torch.empty((9, slab.rows, n), dtype=torch.float32, device="cuda")
+
+    def one_solve(ev=None):
+        st.solver.reinit(d_fields)
+        SL.exchange_dist(st, slab, dist)
+        if ev is not None:
+            ev[0].record(stream)
+        done = 0
+        while done < nsteps:
+            m = min(k, nsteps - done)
+            st.step(m)
+            done += m
+            if m == k and done < nsteps:
+                SL.exchange_dist(st, slab, dist)
+        if ev is not None:
+            ev[1].record(stream)
+        hs = np.zeros(4)
+        L._check(L.lib().lesbgk_moments_rows(L.C.c_void_p(st.solver.handle), slab.lo, slab.rows,
+                                            L.C.c_void_p(mom.data_ptr()), L.C.c_void_p(hs.ctypes.data),
+                                            L.C.c_void_p(stream.cuda_stream)))
+        tot = torch.tensor(hs, dtype=torch.float64, device="cuda")
+        dist.all_reduce(tot)  # the decomposition's one FP64 reduction
+        return tot
+
+    for _ in range(args.warmup):
+        one_solve()
+    torch.cuda.synchronize()
+    dist.barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        dist.barrier()
+        w0 = time.perf_counter()
+        for i in range(args.steps):
+            tot = one_solve(evs[i])
+        torch.cuda.synchronize()
+        dist.barrier()
+        wall = time.perf_counter() - w0
+    t = torch.tensor([wall], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    wall = float(t.item())
+    step_ms = sum(a.elapsed_time(b) for a, b in evs) / (args.steps * nsteps)
+    clocks = clk.summary()
+    lups = n * n * nsteps * args.steps
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": lups / wall / 1e6, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+            "config": {"workload": tgv_workload_name(n, args), "nx": n, "ny": n,
+                       "velocity_set": args.velocity_set.upper(), "storage": args.storage, "order": order,
+                       "lattice_steps_per_step": nsteps, "scheme": "split",
+                       "parallelism": f"y-slabs x{world}: {slab.rows} or so rows per rank, halo {2 * k} rows "
+                                      f"exchanged over NCCL every {k} steps",
+                       "l2": "inputs larger than L2"},
+            "slab_ms_per_lattice_step_rank0": step_ms,
+            "totals": tot.cpu().numpy().tolist(),
+            "e2e": None,
+            "gpu_launches": (1 + nsteps + 2) * args.steps,
+            "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
+        }
+        print(json.dumps(line), flush=True)
+    st.close()
+    dist.destroy_process_group()
     return 0
 
 
@@ -643,6 +797,8 @@ def main():
         return run_serve(args, world, rank, local)
     if args.workload == "precision":
         return run_precision(args, world, rank, local)
+    if world > 1 and args.decomp == "slab":
+        return run_slab(args, world, rank, local)
 
     import numpy as np
     import torch
@@ -749,6 +905,24 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "solve_ms": solve_ms,
                "clocks": {"sm_mhz": ec["sm_mhz"], "reasons": ec["reasons"]}}
 
+    # the batched and served forms of the metric, each with its own timed
+    # region, on one GPU (the config-4 and config-5 workloads at bench size)
+    batch_obj = serve_obj = None
+    if world == 1 and not args.no_batch:
+        bprobs = I.batch_mix(n=args.instances, seed=0, steps=2000)
+        bfixed, bstep_ms, brows, _ = measure_batch_fixed([L.params_from_problem(p) for p in bprobs], 2000,
+                                                         args.steps, args.warmup, stream, local, args.plain_sample)
+        batch_obj = {"workload": f"batch_mix_{args.instances}_nx4_d2q16", "instances": args.instances,
+                     "lattice_steps_per_solve": 2000, "solves_per_s": bfixed["solves_per_s_this_rank"],
+                     "vs_plain": bfixed["solves_per_s_this_rank"] / bfixed["plain"]["est_solves_per_s_full_mix"],
+                     **{k: v for k, v in bfixed.items() if k != "solves_per_s_this_rank"},
+                     "l2": "L2 flushed between timed passes"}
+    if world == 1 and not args.no_serve:
+        serve_obj = measure_serve(args.serve_requests, args.rate, args.pool_mb, args.serve_plain_budget, stream,
+                                  local, seed=0)
+        serve_obj["vs_plain_solves_per_s"] = ((serve_obj["solves_per_s"] or 0.0) /
+                                              max(serve_obj["plain_fifo"].get("solves_per_s") or 1e-9, 1e-9))
+
     peak, peak_kind = measured_peak()
     bytes_per_lup = 2 * q * (4 if args.storage == "f32" else 2)  # q: values stored per node
     achieved = bytes_per_lup * cells / (kernel_ms / 1e3) / 1e9
@@ -787,6 +961,8 @@ def main():
                                              clocks["sm_mhz"])},
             "cpu_baseline": base,
             "e2e": e2e,
+            "batch": batch_obj,
+            "serve": serve_obj,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                        "reasons": clocks["reasons"]},
