@@ -36,6 +36,9 @@ METRIC = "ES-BGK MLUPS"
 UNIT = "MLUPS"
 
 
+STORE_BYTES = {"f32": 4, "f16": 2, "bf16": 2, "f32c": 6}  # bytes per stored value (f32c: FP32 hi + FP16 lo)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -50,6 +53,10 @@ def parse():
                     help="default workload: leave out the batched-solves object")
     ap.add_argument("--no-serve", action="store_true",
                     help="default workload: leave out the serving object")
+    ap.add_argument("--save-moments", default=None,
+                    help="precision workload: run the GPU leg only and save its sampled moments here")
+    ap.add_argument("--compare-moments", default=None,
+                    help="precision workload: run the oracle leg only, against moments saved by --save-moments")
     ap.add_argument("--decomp", choices=["slab", "replica"], default="slab",
                     help="with several ranks: split the one domain into y-slabs (strong scaling), or run "
                          "an independent replica per rank (weak scaling)")
@@ -66,7 +73,7 @@ def parse():
                     help="tgv workload lattice: D2Q16 (order 3), D2Q36 (order 4), D3Q64 (order 3, D = 3: the "
                          "paper's C_p = 5/2) or D3Q216 (order 4, D = 3: the paper's set); the D = 3 sets are "
                          "stored by their z-even half")
-    ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
+    ap.add_argument("--storage", choices=["f32", "f16", "bf16", "f32c"], default="f32",
                     help="population storage for the tgv workload (compute is FP32)")
     ap.add_argument("--requests", type=int, default=400)
     ap.add_argument("--rate", type=float, default=200.0, help="mean arrivals per second")
@@ -352,7 +359,7 @@ def measure_batch_fixed(params, nsteps, passes, warmup, stream, local, plain_sam
     def admit_all():
         for s in list(bt.params):
             bt.remove(s)
-        return [bt.add(p) for p in params]
+        return bt.add_many(params)  # one descriptor copy, one init launch
 
     admit_all()
     rows = bt.autotune((8, 16, 32, 64, 128))
@@ -362,9 +369,7 @@ def measure_batch_fixed(params, nsteps, passes, warmup, stream, local, plain_sam
         flush.fill_(1)  # L2 flushed between timed passes (inside a pass the steps reuse it)
         sl = admit_all()
         bt.step(nsteps)
-        for s, o in zip(sl, outs):
-            L.lib().lesbgk_batch_moments(L.C.c_void_p(bt.handle), L.C.c_int32(s), L.C.c_void_p(o.data_ptr()),
-                                         None, L.C.c_void_p(stream.cuda_stream))
+        bt.moments_many(sl, outs)  # every instance's nine fields in one launch
 
     for _ in range(warmup):
         one_pass()
@@ -612,7 +617,7 @@ def run_slab(args, world, rank, local):
     nroots, dim, order, q = LATTICES[args.velocity_set]
     prob = tgv_problem(n, args, nsteps)
     fields = I.initial_fields(prob)
-    storage = {"f32": L.F32, "f16": L.F16, "bf16": L.BF16}[args.storage]
+    storage = {"f32": L.F32, "f16": L.F16, "bf16": L.BF16, "f32c": L.F32C}[args.storage]
     stream = torch.cuda.current_stream()
     # the whole domain's time step (tau_ref depends on its fields) and spacing, as the library sets them
     whole = L.Solver(L.params_from_problem(prob), h_init=fields, stream=stream)
@@ -691,95 +696,129 @@ def run_slab(args, world, rank, local):
 
 
 def run_precision(args, world, rank, local):
-    """Per-field error of FP32, FP16 and BF16 population storage (FP32 compute)
-    against the FP64 oracle: an n^2 Taylor-Green vortex (split scheme; n = --tgv-n,
-    256 by default, 4096 for the throughput workload itself) and the
+    """Per-field error of FP32, FP16, BF16 and compensated FP32 population
+    storage (FP32 compute) against the FP64 oracle: an n^2 Taylor-Green vortex
+    (split scheme; n = --tgv-n, 256 by default, 4096 for the throughput
+    workload itself, compared at every 8th node in x and y there) and the
     force-driven Poiseuille channel (g = 1e-4, Kn 0.2, b = 0, ny = 1024; the
     flow does not vary in x, so a 4-node-wide periodic slice computes the same
-    solution as the 512-wide channel), 1000 steps each.  Error per field:
-    e = max|gpu - ref| / max(scale of its quantity, floor) as in the parity
-    tests, and e' = max|gpu - ref| / max|ref - rest| (the perturbation)."""
+    solution as the 512-wide channel), 1000 steps each.  Errors per field as
+    in the parity tests: e = max|gpu - ref| / (largest magnitude of the
+    field's quantity), e_own = ... / max|ref field|, e_pert = ... /
+    max|ref - rest value|.
+    --save-moments DIR: the GPU leg only, writing its sampled moments to DIR;
+    --compare-moments DIR: the oracle leg only, against moments so saved (the
+    4096^2 oracle run takes hours: it may run on other host cores than the GPU
+    box's)."""
     import numpy as np
-    import torch
     import oracle as O
     from dataclasses import replace
-    from paper_1209_6548_gb300 import build as B
     from paper_1209_6548_gb300 import inputs as I
-    from paper_1209_6548_gb300 import lesbgk as L
 
-    torch.cuda.set_device(local)
-    B.build()
-    O.set_threads(len(os.sched_getaffinity(0)))
     steps = 1000
     cases = [(f"tgv{args.tgv_n}", I.tgv(args.tgv_n, steps=steps)),
              ("poiseuille_1024", I.poiseuille(nx=4, ny=1024, steps=steps))]
+    stores = ("f32", "f16", "bf16", "f32c")
     groups = {"rho": ["rho"], "T": ["T"], "u": ["ux", "uy"], "sigma": ["sxx", "sxy", "syy"], "q": ["qx", "qy"]}
-    floor = {"rho": 0.0, "T": 0.0, "u": 1e-3, "sigma": 1e-3, "q": 3e-3}
     names = list(O.MOMENT_NAMES)
     rest = np.zeros(9)
     rest[0] = rest[3] = 1.0
+
+    def stride(prob):
+        return 8 if prob.nx >= 2048 else 1
+
+    def time_step_of(prob, fields):
+        # the time step the library takes (its rule, restated on the test side)
+        from tests.common import time_step
+        return time_step(prob, fields)
+
+    gpu = {}
+    thr = {}
+    if not args.compare_moments:
+        import torch
+        from paper_1209_6548_gb300 import build as B
+        from paper_1209_6548_gb300 import lesbgk as L
+        torch.cuda.set_device(local)
+        B.build()
+        code = {"f32": L.F32, "f16": L.F16, "bf16": L.BF16, "f32c": L.F32C}
+        for cname, prob in cases:
+            fields = I.initial_fields(prob) if prob.init == "tgv" else None
+            dt = time_step_of(prob, fields)
+            k = stride(prob)
+            for st in stores:
+                p = L.params_from_problem(prob, dt=dt)
+                p.storage = code[st]
+                sv = L.Solver(p, h_init=fields)
+                sv.step(steps)
+                gpu[(cname, st)] = sv.moments()[:, ::k, ::k].cpu().numpy().astype(np.float64)
+                sv.close()
+        if args.save_moments:
+            os.makedirs(args.save_moments, exist_ok=True)
+            np.savez(os.path.join(args.save_moments, f"gpu_moments_tgv{args.tgv_n}.npz"),
+                     **{f"{c}|{st}": v for (c, st), v in gpu.items()})
+        # throughput of each storage on the 4096^2 case
+        n = 4096
+        prob = I.tgv(n)
+        fields = I.initial_fields(prob)
+        stream = torch.cuda.current_stream()
+        for st in stores:
+            p = L.params_from_problem(prob)
+            p.storage = code[st]
+            sv = L.Solver(p, h_init=fields, stream=stream)
+            sv.step(20)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sv.step(200)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 200
+            bpl = 2 * 16 * STORE_BYTES[st]
+            thr[st] = {"mlups": n * n / (ms / 1e3) / 1e6, "kernel_ms": ms,
+                       "gbs": bpl * n * n / (ms / 1e3) / 1e9, "bytes_per_lup": bpl}
+            sv.close()
+        if args.save_moments:
+            line = {"metric": "GPU moments saved for the precision comparison", "dir": args.save_moments,
+                    "throughput_4096": thr, "source_sha256": source_digest()}
+            if rank == 0:
+                print(json.dumps(line), flush=True)
+            return 0
+    else:
+        z = np.load(os.path.join(args.compare_moments, f"gpu_moments_tgv{args.tgv_n}.npz"))
+        gpu = {tuple(key.split("|")): z[key] for key in z.files}
+
+    O.set_threads(len(os.sched_getaffinity(0)))
     out = {}
     t_or = 0.0
+    from tests.common import oracle_params
     for cname, prob in cases:
         fields = I.initial_fields(prob) if prob.init == "tgv" else None
-        # the time step rule of the library, restated (c_max of the 4-point rule)
-        c, _ = O.gauss_hermite_1d(prob.nroots)
-        dx = 1.0 / prob.nx if prob.bc_y == I.PERIODIC else 1.0 / (prob.ny - 1)
-        dy = 1.0 / prob.ny if prob.bc_y == I.PERIODIC else 1.0 / (prob.ny - 1)
-        s0 = L.Solver(L.params_from_problem(prob), h_init=fields)
-        dt = s0.info.dt
-        s0.close()
-        op = O.make_params(nroots=prob.nroots, order=3, nx=prob.nx, ny=prob.ny, bc_y=prob.bc_y, kn=prob.kn,
-                           b=prob.b, visc_exp=prob.visc_exp, dt=dt, dx=dx, dy=dy, wall_T=prob.wall_T,
-                           wall_ux=prob.wall_ux, g=prob.g, scheme=prob.scheme)
+        dt = time_step_of(prob, fields)
+        op = oracle_params(prob, dt)
         t0 = time.perf_counter()
         ref, _ = O.moments(op, O.run(op, O.init(op, fields), steps))
         t_or += time.perf_counter() - t0
-        for st_name, st in (("f32", L.F32), ("f16", L.F16), ("bf16", L.BF16)):
-            p = L.params_from_problem(prob, dt=dt)
-            p.storage = st
-            s = L.Solver(p, h_init=fields)
-            s.step(steps)
-            g = s.moments().cpu().numpy().astype(np.float64)
-            s.close()
+        k = stride(prob)
+        ref = ref[:, ::k, ::k]
+        for st in stores:
+            g = gpu[(cname, st)]
             row = {}
             for grp, mem in groups.items():
-                scale = max(max(float(np.max(np.abs(ref[names.index(m)]))) for m in mem), floor[grp])
+                scale = max(float(np.max(np.abs(ref[names.index(m)]))) for m in mem)
                 for m in mem:
-                    k = names.index(m)
-                    d = float(np.max(np.abs(g[k] - ref[k])))
-                    pert = float(np.max(np.abs(ref[k] - rest[k])))
-                    row[m] = {"e": d / scale, "e_pert": (d / pert) if pert > 1e-6 else None, "abs": d}
-            out.setdefault(cname, {})[st_name] = row
-    # throughput of 16-bit storage on the 4096^2 case
-    thr = {}
-    n = 4096
-    prob = I.tgv(n)
-    fields = I.initial_fields(prob)
-    stream = torch.cuda.current_stream()
-    for st_name, st in (("f32", L.F32), ("f16", L.F16), ("bf16", L.BF16)):
-        p = L.params_from_problem(prob)
-        p.storage = st
-        s = L.Solver(p, h_init=fields, stream=stream)
-        s.step(20)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s.step(200)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / 200
-        bpl = 128 if st == L.F32 else 64
-        thr[st_name] = {"mlups": n * n / (ms / 1e3) / 1e6, "kernel_ms": ms,
-                        "gbs": bpl * n * n / (ms / 1e3) / 1e9, "bytes_per_lup": bpl}
-        s.close()
-    peak, peak_kind = measured_peak()
-    worst = {st: max(max(v["e"] for v in out[c][st].values()) for c in out) for st in ("f32", "f16", "bf16")}
-    line = {"metric": "per-field error vs FP64 oracle by population storage", "value": worst["f16"],
-            "unit": "max relative error (FP16 storage)", "n_gpus": world, "steps": steps, "warmup": 0,
+                    i = names.index(m)
+                    d = float(np.max(np.abs(g[i] - ref[i])))
+                    own = float(np.max(np.abs(ref[i])))
+                    pert = float(np.max(np.abs(ref[i] - rest[i])))
+                    row[m] = {"e": d / scale, "e_own": d / own if own > 0 else None,
+                              "e_pert": (d / pert) if pert > 1e-6 else None, "abs": d}
+            out.setdefault(cname, {})[st] = row
+    worst = {st: max(max(v["e"] for v in out[c][st].values()) for c in out) for st in stores}
+    line = {"metric": "per-field error vs FP64 oracle by population storage", "value": worst["f32"],
+            "unit": "max relative error (FP32 storage)", "n_gpus": world, "steps": steps, "warmup": 0,
             "higher_is_better": False, "dtype": "f32 compute", "data": "synthetic",
             "config": {"workload": f"precision_tgv{args.tgv_n}_poiseuille1024", "lattice_steps": steps,
-                       "cases": [c for c, _ in cases]},
-            "worst_e": worst, "errors": out, "throughput_4096": thr, "peak_gbs": peak,
+                       "cases": [c for c, _ in cases], "sampled_every": {c: stride(p) for c, p in cases}},
+            "worst_e": worst, "errors": out, "throughput_4096": thr or None,
             "oracle_seconds": t_or, "cpu_cores": O.get_threads()}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -832,7 +871,7 @@ def main():
     prob = tgv_problem(n, args, nsteps)
     fields = I.initial_fields(prob)
     params = L.params_from_problem(prob, dt=0.0)
-    params.storage = {"f32": L.F32, "f16": L.F16, "bf16": L.BF16}[args.storage]
+    params.storage = {"f32": L.F32, "f16": L.F16, "bf16": L.BF16, "f32c": L.F32C}[args.storage]
     stream = torch.cuda.current_stream()
     d_fields = torch.from_numpy(fields).cuda()
     solver = L.Solver(params, h_init=fields, stream=stream)
@@ -924,7 +963,7 @@ def main():
                                               max(serve_obj["plain_fifo"].get("solves_per_s") or 1e-9, 1e-9))
 
     peak, peak_kind = measured_peak()
-    bytes_per_lup = 2 * q * (4 if args.storage == "f32" else 2)  # q: values stored per node
+    bytes_per_lup = 2 * q * STORE_BYTES[args.storage]  # q: values stored per node
     achieved = bytes_per_lup * cells / (kernel_ms / 1e3) / 1e9
     digest = source_digest()
     traffic = committed_traffic(digest, args.velocity_set, args.storage)
@@ -944,9 +983,9 @@ def main():
                        "order": order, "kn": prob.kn, "b": prob.b,
                        "lattice_steps_per_step": nsteps, "scheme": "split",
                        "l2": ("inputs larger than L2 (two population buffers of %.2f GB)"
-                              if q * n * n * (4 if args.storage == "f32" else 2) > L2_BYTES else
+                              if q * n * n * STORE_BYTES[args.storage] > L2_BYTES else
                               "a small case: the two population buffers of %.2f GB fit in L2")
-                             % (q * n * n * (4 if args.storage == "f32" else 2) / 1e9),
+                             % (q * n * n * STORE_BYTES[args.storage] / 1e9),
                        "parallelism": f"replica x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,

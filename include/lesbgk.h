@@ -72,6 +72,17 @@ extern "C" {
 #define LESBGK_F32 0
 #define LESBGK_F16 1
 #define LESBGK_BF16 2
+/* Compensated FP32 storage (not in the paper; FP32 compute): each deviation
+ * f_a - w_a is held as hi + lo, hi in FP32 and lo, the remainder FP32 cannot
+ * hold, in FP16 (stored as lo 2^24 / w_a), 6 bytes per value.  Every step
+ * adds its increment to hi + lo exactly (an error-free two-sum) and the TVD
+ * differences take both parts, so the storage rounding per step falls from
+ * half an FP32 ulp to 2^-11 of it: a solve of many small steps (dt/tau ~ 1e-3,
+ * where the relaxation barely damps accumulated rounding) keeps its stress
+ * and heat flux to the precision FP32 arithmetic gives one step.  1.5 times
+ * the bytes of FP32 storage.  Built for D2Q16 and D3Q64 (order 3) with
+ * periodic or fully diffuse steady or heated y-walls. */
+#define LESBGK_F32C 3
 
 /* Advection schemes.  LESBGK_UNSPLIT is the update of Sec. 3.1 as printed:
  * both flux differences are taken from f^n.  For flows that vary in both x
@@ -90,7 +101,7 @@ typedef struct lesbgk_params {
   int32_t order;        /* Hermite order N of f_ES (3 or 4); 0 = 3 for D2Q16, 4 for D2Q36 */
   int32_t nx, ny;       /* nodes; nx >= 1; ny >= 1 (>= 2 with walls); nx ny < 2^31 */
   int32_t bc_y;         /* LESBGK_PERIODIC or LESBGK_DIFFUSE (walls on rows j = 0 and ny-1) */
-  int32_t storage;      /* LESBGK_F32, LESBGK_F16 or LESBGK_BF16 */
+  int32_t storage;      /* LESBGK_F32, LESBGK_F16, LESBGK_BF16 or LESBGK_F32C */
   int32_t scheme;       /* LESBGK_UNSPLIT (default) or LESBGK_SPLIT */
   double kn;            /* Knudsen number of Sec. 2.2, > 0 */
   double b;             /* ES parameter, -1/2 <= b < 1 (b = 1 gives tau = 0) */
@@ -133,9 +144,11 @@ typedef struct lesbgk_params {
                            keeps the whole domain's spacing (pass the whole domain's dt too). */
   int32_t row_offset;   /* global index of this grid's row 0 (a y-slab's place in the whole
                            domain, negative where its halo wraps around a periodic domain; 0
-                           otherwise): the 16-bit stochastic rounding is keyed by the global
-                           row, so a slab rounds exactly as the whole domain does */
-  int32_t reserved;     /* must be 0 */
+                           otherwise) */
+  int32_t row_period;   /* the whole domain's ny where it is periodic in y, else 0: the 16-bit
+                           stochastic rounding is keyed by the global row, (row + row_offset)
+                           mod row_period, so a slab -- halo rows that wrap around included --
+                           rounds exactly as the whole domain does */
 } lesbgk_params;
 
 /* Read-only facts about a created solver. */
@@ -289,6 +302,16 @@ int lesbgk_batch_create(int32_t capacity, int32_t nx, void *d_workspace, size_t 
  * on the stream; the work list is rebuilt at the next step. */
 int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const double *h_init, void *stream,
                      int32_t *slot);
+/* Admit n solves at once (ps[i], h_inits[i] as in lesbgk_batch_add; h_inits
+ * may be NULL for all at rest, or hold NULL entries): their descriptors go to
+ * the device in one copy and their initial populations are written by one
+ * launch per velocity set, with the arithmetic of lesbgk_batch_add (bitwise
+ * the same populations).  slots_out (HOST int32[n]) receives the slots.  All
+ * or nothing: if one solve cannot be admitted (LESBGK_ESPACE when the pool or
+ * the slots run out), none is, and the error is returned.  Synchronises the
+ * stream. */
+int lesbgk_batch_add_many(lesbgk_batch *b, int32_t n, const lesbgk_params *ps, const double *const *h_inits,
+                          void *stream, int32_t *slots_out);
 /* Retire a slot and return its buffers to the pool (synchronises the stream
  * first, so no queued step still reads them). */
 int lesbgk_batch_remove(lesbgk_batch *b, int32_t slot, void *stream);
@@ -303,6 +326,13 @@ int lesbgk_batch_residuals(lesbgk_batch *b, double *h_res, double *h_mass, void 
 /* As lesbgk_moments / lesbgk_get_populations / lesbgk_get_info, per slot. */
 int lesbgk_batch_moments(lesbgk_batch *b, int32_t slot, float *d_out, double *h_sums, void *stream);
 int lesbgk_batch_get_populations(lesbgk_batch *b, int32_t slot, float *d_out, void *stream);
+/* The moment fields of n slots in one launch per velocity set: d_outs (HOST
+ * array of n DEVICE pointers) receives slot slots[i]'s float[9][ny][nx], with
+ * the per-node arithmetic of lesbgk_batch_moments (bitwise the same fields;
+ * no totals).  The pointer list is staged in the batch's workspace: calls on
+ * one batch must not overlap on the GPU. */
+int lesbgk_batch_moments_many(lesbgk_batch *b, int32_t n, const int32_t *slots, float *const *d_outs,
+                              void *stream);
 int lesbgk_batch_get_info(const lesbgk_batch *b, int32_t slot, lesbgk_info *out);
 /* Rows per work item (default 32); results do not depend on it. */
 int lesbgk_batch_set_rows(lesbgk_batch *b, int32_t rows, void *stream);

@@ -297,6 +297,66 @@ __global__ void __launch_bounds__(kBBlock) k_batch_residual(const BatchArgs B, c
   }
 }
 
+// Initial populations of newly admitted slots, one block per slot of the
+// list: f = rho S(T,u) (Eq. feq0 to order N) from the slot's fields (device
+// double[4][ny][nx] in its spare buffer when list entry bit 30 is set, else
+// rest), then the wall rule -- the arithmetic of the single-domain k_init.
+template <int NR, int N>
+__global__ void __launch_bounds__(kBBlock) k_batch_init(const BatchArgs B, const int *__restrict__ list, int n,
+                                                        const int par) {
+  if ((int)blockIdx.x >= n) return;
+  const int entry = list[blockIdx.x];
+  const InstDesc &D = B.desc[entry & 0x3fffffff];
+  const bool has_fields = (entry >> 30) & 1;
+  const int nx = D.nx, ny = D.ny;
+  const long long cells = (long long)nx * ny;
+  const double *fields = has_fields ? reinterpret_cast<const double *>(D.f[par ^ 1]) : nullptr;
+  float *f = D.f[par];
+  for (long long c = threadIdx.x; c < cells; c += kBBlock) {
+    float drho = 0.f, ux = 0.f, uy = 0.f, dT = 0.f;
+    if (fields) {
+      drho = (float)(fields[c] - 1.0);
+      ux = (float)fields[cells + c];
+      uy = (float)fields[2 * cells + c];
+      dT = (float)(fields[3 * cells + c] - 1.0);
+    }
+    const float rho = 1.0f + drho;
+    const float rdT = rho * dT;
+    float e[N + 1][N + 1];
+    gaussian_coeffs<N>(rho, rho * ux, rho * uy, ux, uy, dT, 0.f, dT, rdT, 0.f, rdT, e);
+    e[0][0] = drho;
+    float Sv[NR * NR];
+    hermite_evaluate<NR, N>(e, Sv, B.lat);
+    const int j = (int)(c / nx);
+    if (D.walls && (j == 0 || j == ny - 1)) wall_fix<NR, false>(Sv, j == 0 ? 0 : 1, B.lat, D);
+    st_node<NR, float, 1>(f, c, cells, Sv, B.lat);
+  }
+}
+
+// Moments (Eq. mac) of every node of every work item whose slot has an output
+// in outs[slot] (DEVICE float[9][ny][nx] each, or null): the per-node
+// arithmetic of lesbgk_moments, one block per item.
+template <int NR>
+__global__ void __launch_bounds__(kBBlock) k_batch_moments(const BatchArgs B, const int par,
+                                                           float *const *__restrict__ outs) {
+  const int first = B.range[0], count = B.range[1];
+  if ((int)blockIdx.x >= count) return;
+  const WorkItem wi = B.items[first + blockIdx.x];
+  float *out = outs[wi.inst];
+  if (!out) return;
+  const InstDesc &D = B.desc[wi.inst];
+  const int nx = D.nx;
+  const long long cells = (long long)nx * D.ny;
+  const float *f = D.f[par];
+  for (int t = threadIdx.x; t < wi.rows * nx; t += kBBlock) {
+    const long long c = (long long)wi.y0 * nx + t;
+    float F[NR * NR];
+    ld_node<NR, float, 1>(f, c, cells, F, B.lat);
+    float d[4];
+    node_moments<NR>(F, out, cells, c, B.lat, d);
+  }
+}
+
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // First-fit allocator over [0, cap) in 256-byte units, coalescing on release.
@@ -377,6 +437,8 @@ struct lesbgk_batch {
   int *d_range = nullptr;
   unsigned *d_res = nullptr;
   double *d_mass = nullptr;
+  int *d_list = nullptr;
+  float **d_outs = nullptr;
   double *d_partial = nullptr, *d_sums = nullptr;
   char *pool_base = nullptr;
   size_t pool_bytes = 0;
@@ -401,7 +463,7 @@ namespace {
 constexpr size_t kItemsPerSlot = 1024;  // work-list room: items per slot (rows/8 for ny <= 8192)
 
 struct Layout0 {
-  size_t desc, items, mass, range, res, partial, sums, pool;
+  size_t desc, items, mass, range, res, partial, sums, list, outs, pool;
 };
 
 Layout0 fixed_layout(int capacity) {
@@ -421,6 +483,10 @@ Layout0 fixed_layout(int capacity) {
   o = align_up(o + sizeof(double) * 4 * lesbgk_internal::kMomentPartials, 256);
   L.sums = o;
   o = align_up(o + sizeof(double) * 4, 256);
+  L.list = o;  // slots to initialise (lesbgk_batch_add_many)
+  o = align_up(o + sizeof(int) * (size_t)capacity, 256);
+  L.outs = o;  // per-slot moment outputs (lesbgk_batch_moments_many)
+  o = align_up(o + sizeof(float *) * (size_t)capacity, 256);
   L.pool = o;
   return L;
 }
@@ -594,6 +660,8 @@ extern "C" int lesbgk_batch_create(int32_t capacity, int32_t nx, void *d_workspa
   b->d_range = reinterpret_cast<int *>(b->ws + L.range);
   b->d_res = reinterpret_cast<unsigned *>(b->ws + L.res);
   b->d_mass = reinterpret_cast<double *>(b->ws + L.mass);
+  b->d_list = reinterpret_cast<int *>(b->ws + L.list);
+  b->d_outs = reinterpret_cast<float **>(b->ws + L.outs);
   b->d_partial = reinterpret_cast<double *>(b->ws + L.partial);
   b->d_sums = reinterpret_cast<double *>(b->ws + L.sums);
   b->pool_base = b->ws + L.pool;
@@ -621,9 +689,11 @@ extern "C" int lesbgk_batch_create(int32_t capacity, int32_t nx, void *d_workspa
   return 0;
 }
 
-extern "C" int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const double *h_init, void *stream,
-                                int32_t *slot_out) {
-  if (!b || !slot_out) return fail(LESBGK_EINVAL, "NULL argument");
+namespace {
+
+// Validate p, build its tables and take a slot and pool memory for it; the
+// slot's descriptor is filled on the host (sl.desc), not yet on the device.
+int prepare_slot(lesbgk_batch *b, const lesbgk_params *p, const double *h_init, int *slot_out) {
   if (int rc = check_params(p)) return rc;
   const int order = p->order ? p->order : default_order(p->nroots);
   const int cls = class_of(p->nroots, order);
@@ -706,6 +776,37 @@ extern "C" int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const d
     b->lat_ready[cls] = true;
     drop_graph(b);
   }
+  *slot_out = slot;
+  return 0;
+}
+
+// Wait for the copy of a pinned h_init before returning (a pageable one is
+// staged before cudaMemcpyAsync returns).
+cudaError_t settle_host_copy(const double *h_init, cudaStream_t s) {
+  cudaPointerAttributes at{};
+  cudaError_t e = cudaSuccess;
+  if (cudaPointerGetAttributes(&at, h_init) == cudaSuccess && at.type == cudaMemoryTypeHost)
+    e = cudaStreamSynchronize(s);
+  cudaGetLastError();
+  return e;
+}
+
+void release_slot(lesbgk_batch *b, int slot) {
+  auto &sl = b->slots[slot];
+  b->pool.release(sl.off, sl.bytes);
+  sl = lesbgk_batch::Slot();
+}
+
+}  // namespace
+
+extern "C" int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const double *h_init, void *stream,
+                                int32_t *slot_out) {
+  if (!b || !slot_out) return fail(LESBGK_EINVAL, "NULL argument");
+  int slot = -1;
+  if (int rc = prepare_slot(b, p, h_init, &slot)) return rc;
+  auto &sl = b->slots[slot];
+  const InstDesc &D = sl.desc;
+  const size_t cells = (size_t)p->nx * p->ny;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemcpyAsync(b->d_desc + slot, &D, sizeof D, cudaMemcpyHostToDevice, s);
   const double *dfields = nullptr;
@@ -713,22 +814,78 @@ extern "C" int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const d
     e = cudaMemcpyAsync(D.f[b->par ^ 1], h_init, 4 * cells * sizeof(double), cudaMemcpyHostToDevice, s);
     dfields = reinterpret_cast<const double *>(D.f[b->par ^ 1]);
   }
-  if (e == cudaSuccess) e = lesbgk_internal::launch_init(A, sl.nr, order, dfields, D.f[b->par], b->sm_count, s);
-  if (e == cudaSuccess && h_init) {
-    // a pageable h_init is staged before cudaMemcpyAsync returns; a pinned
-    // one is read asynchronously, so wait for the copy before returning
-    cudaPointerAttributes at{};
-    if (cudaPointerGetAttributes(&at, h_init) == cudaSuccess && at.type == cudaMemoryTypeHost)
-      e = cudaStreamSynchronize(s);
-    cudaGetLastError();
-  }
+  if (e == cudaSuccess)
+    e = lesbgk_internal::launch_init(sl.args, sl.nr, sl.order, dfields, D.f[b->par], b->sm_count, s);
+  if (e == cudaSuccess && h_init) e = settle_host_copy(h_init, s);
   if (e != cudaSuccess) {
-    b->pool.release(off, need);
+    release_slot(b, slot);
     return cuda_fail(e, "slot initialisation");
   }
   sl.used = true;
   b->items_dirty = true;  // the work list is rebuilt before the next step
   *slot_out = slot;
+  return 0;
+}
+
+extern "C" int lesbgk_batch_add_many(lesbgk_batch *b, int32_t n, const lesbgk_params *ps,
+                                     const double *const *h_inits, void *stream, int32_t *slots_out) {
+  if (!b || n < 0 || (n && (!ps || !slots_out))) return fail(LESBGK_EINVAL, "NULL argument");
+  std::vector<int> taken;
+  taken.reserve(n);
+  int rc = 0;
+  for (int i = 0; i < n && !rc; ++i) {
+    int slot = -1;
+    rc = prepare_slot(b, &ps[i], h_inits ? h_inits[i] : nullptr, &slot);
+    if (!rc) {
+      b->slots[slot].used = true;  // taken for the rest of this call
+      taken.push_back(slot);
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (!rc && n) {
+    // the descriptors of the touched range in one copy, the fields one by one,
+    // then one init launch per lattice class over the new slots
+    const int lo = *std::min_element(taken.begin(), taken.end());
+    const int hi = *std::max_element(taken.begin(), taken.end());
+    std::vector<InstDesc> desc(hi - lo + 1);
+    for (int i = lo; i <= hi; ++i)
+      if (b->slots[i].used) desc[i - lo] = b->slots[i].desc;
+    // (slots in the range not taken here keep their device descriptors: copy
+    // them back unchanged from the host mirror, which is the same data)
+    e = cudaMemcpyAsync(b->d_desc + lo, desc.data(), sizeof(InstDesc) * desc.size(), cudaMemcpyHostToDevice, s);
+    std::vector<int> list[kNumClasses];
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+      const auto &sl = b->slots[taken[i]];
+      const double *hi_init = h_inits ? h_inits[i] : nullptr;
+      if (hi_init)
+        e = cudaMemcpyAsync(sl.desc.f[b->par ^ 1], hi_init, 4 * (size_t)sl.p.nx * sl.p.ny * sizeof(double),
+                            cudaMemcpyHostToDevice, s);
+      list[sl.cls].push_back(taken[i] | (hi_init ? (1 << 30) : 0));
+    }
+    int at = 0;
+    for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls) {
+      const int m = (int)list[cls].size();
+      if (!m) continue;
+      e = cudaMemcpyAsync(b->d_list + at, list[cls].data(), sizeof(int) * m, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) break;
+      BatchArgs a = make_args(b, cls);
+      if (cls == 0) k_batch_init<4, 3><<<m, kBBlock, 0, s>>>(a, b->d_list + at, m, b->par);
+      else k_batch_init<6, 4><<<m, kBBlock, 0, s>>>(a, b->d_list + at, m, b->par);
+      e = cudaGetLastError();
+      at += m;
+    }
+    // host arrays above are pageable (staged at once); pinned fields are waited for
+    for (int i = 0; i < n && e == cudaSuccess && h_inits; ++i)
+      if (h_inits[i]) e = settle_host_copy(h_inits[i], s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the list and descriptor staging buffers
+  }
+  if (rc || e != cudaSuccess) {
+    for (int slot : taken) release_slot(b, slot);
+    return rc ? rc : cuda_fail(e, "batched slot initialisation");
+  }
+  for (int i = 0; i < n; ++i) slots_out[i] = taken[i];
+  b->items_dirty = true;
   return 0;
 }
 
@@ -830,6 +987,31 @@ extern "C" int lesbgk_batch_moments(lesbgk_batch *b, int32_t slot, float *d_out,
   if (h_sums)
     for (int k = 0; k < 4; ++k)
       if (!std::isfinite(h_sums[k])) return fail(LESBGK_EDIVERGED, "slot %d diverged", slot);
+  return 0;
+}
+
+extern "C" int lesbgk_batch_moments_many(lesbgk_batch *b, int32_t n, const int32_t *slots, float *const *d_outs,
+                                         void *stream) {
+  if (!b || n < 0 || (n && (!slots || !d_outs))) return fail(LESBGK_EINVAL, "NULL argument");
+  std::vector<float *> outs(b->capacity, nullptr);
+  for (int i = 0; i < n; ++i) {
+    const int sl = slots[i];
+    if (sl < 0 || sl >= b->capacity || !b->slots[sl].used) return fail(LESBGK_EINVAL, "no such slot %d", sl);
+    if (!d_outs[i]) return fail(LESBGK_EINVAL, "output %d is NULL", i);
+    outs[sl] = d_outs[i];
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (int rc = ensure_items(b, s)) return rc;
+  cudaError_t e = cudaMemcpyAsync(b->d_outs, outs.data(), sizeof(float *) * outs.size(), cudaMemcpyHostToDevice, s);
+  for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls) {
+    const int m = b->range[cls][1];
+    if (!m) continue;
+    BatchArgs a = make_args(b, cls);
+    if (cls == 0) k_batch_moments<4><<<m, kBBlock, 0, s>>>(a, b->par, b->d_outs);
+    else k_batch_moments<6><<<m, kBBlock, 0, s>>>(a, b->par, b->d_outs);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "batched moments");
   return 0;
 }
 

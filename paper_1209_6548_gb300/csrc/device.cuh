@@ -22,6 +22,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace lesbgk_dev {
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -312,7 +314,7 @@ __device__ __forceinline__ void gaussian_coeffs(float rho, float ru_x, float ru_
 // (deviation form) and omw = 1 - dt/tau.
 template <int NR, int N, class TT, class TP>
 __device__ __forceinline__ void collide(const float (&F)[NR * NR], float (&S)[NR * NR], float &omw,
-                                        const TT &Lt, const TP &P) {
+                                        const TT &Lt, const TP &P, float *om_out = nullptr) {
   constexpr int KM = (N - 1 > 2) ? N - 1 : 2;
   float a[KM + 1][KM + 1];
   hermite_moments<NR, KM>(F, a, Lt);
@@ -331,6 +333,7 @@ __device__ __forceinline__ void collide(const float (&F)[NR * NR], float (&S)[NR
   else Tp = exp2f(P.visc_pow * __log2f(T));
   const float om = P.c_omega * rho * Tp;  // dt/tau, tau = (Kn/Pr) T^varpi / (rho T)
   omw = 1.0f - om;
+  if (om_out) *om_out = om;
   // rho (lambda - I) = (1-b) rho (T-1) I + b M,  lambda = (1-b) T I + b P/rho
   const float RLxx = fmaf(P.beta, trM, P.b * Mxx);
   const float RLxy = P.b * Mxy;
@@ -443,7 +446,7 @@ __device__ __forceinline__ void z_factor(const float (&e)[N + 1][N + 1], float L
 // lambda_zz = (1-b) T + b P_zz/rho), and omw = 1 - dt/tau.
 template <int NR, int N, int KM, class TP>
 __device__ __forceinline__ void es_coefficients3(const float (&b)[3][KM + 1][KM + 1], float (&d)[3][N + 1][N + 1],
-                                                 float &omw, const TP &P) {
+                                                 float &omw, const TP &P, float *om_out = nullptr) {
   const float rho = 1.0f + b[0][0][0];
   const float ir = fast_rcp(rho);
   const float ux = b[0][1][0] * ir, uy = b[0][0][1] * ir;
@@ -459,6 +462,7 @@ __device__ __forceinline__ void es_coefficients3(const float (&b)[3][KM + 1][KM 
   else Tp = exp2f(P.visc_pow * __log2f(T));
   const float om = P.c_omega * rho * Tp;
   omw = 1.0f - om;
+  if (om_out) *om_out = om;
   // rho (lambda - I) = (1-b) rho (T-1) I + b M, with beta = (1-b)/3
   const float RLxx = fmaf(P.beta, trM, P.b * Mxx);
   const float RLxy = P.b * Mxy;
@@ -489,12 +493,12 @@ __device__ __forceinline__ void es_coefficients3(const float (&b)[3][KM + 1][KM 
 // levels in one thread.
 template <int NR, int N, int Q, class TT, class TP>
 __device__ __forceinline__ void collide3(const float (&F)[Q], float (&S)[Q], float &omw, const TT &Lt,
-                                         const TP &P) {
+                                         const TP &P, float *om_out = nullptr) {
   constexpr int KM = (N - 1 > 2) ? N - 1 : 2;
   float b[3][KM + 1][KM + 1];
   hermite_moments3<NR, KM>(F, b, Lt);
   float d[3][N + 1][N + 1];
-  es_coefficients3<NR, N, KM>(b, d, omw, P);
+  es_coefficients3<NR, N, KM>(b, d, omw, P, om_out);
   hermite_evaluate3<NR, N>(d, S, Lt);
 }
 
@@ -504,6 +508,82 @@ __device__ __forceinline__ void collide_any(const float (&F)[Q], float (&S)[Q], 
                                             const TP &P) {
   if constexpr (Q == NR * NR) collide<NR, N>(F, S, omw, Lt, P);
   else collide3<NR, N>(F, S, omw, Lt, P);
+}
+
+// The same, returning dt/tau itself (om) rather than 1 - dt/tau: the
+// compensated update adds -om f to the remainder, where 1 - (1 - om) would
+// carry the rounding of 1 - om (2^-24 absolute, a 1e-4 relative error of om
+// at dt/tau ~ 1e-3).
+template <int NR, int N, int Q, class TT, class TP>
+__device__ __forceinline__ void collide_om(const float (&F)[Q], float (&S)[Q], float &om, const TT &Lt,
+                                           const TP &P) {
+  float omw;
+  if constexpr (Q == NR * NR) collide<NR, N>(F, S, omw, Lt, P, &om);
+  else collide3<NR, N>(F, S, omw, Lt, P, &om);
+}
+
+// ---------------------------------------------------------------------------
+// Moments of Eq. (mac) of one node from its deviations F = f - w, written to
+// out[k * cells + c] (k = rho, u_x, u_y, T, sigma_xx, sigma_xy, sigma_yy, q_x,
+// q_y) when out is set; returns in d the node's deviations of the conserved
+// sums sum_a df_a {1, c_x, c_y, c^2}: with the Hermite moments m_pql =
+// sum df He_p(c_x) He_q(c_y) He_l(c_z) these are m000, m100, m010 and
+// m200 + m020 (+ m002) + D m000.  D = 2 for the 2D sets; D = 3 (Q = NR^3/2
+// stored, z-even) adds the c_z terms: T = tr P/(3 rho), sigma trace-free in
+// 3D (sigma_zz = -sigma_xx - sigma_yy is not written), q with c_z^2 in C^2.
+// ---------------------------------------------------------------------------
+template <int NR, int Q, class TT>
+__device__ __forceinline__ void node_moments(const float (&F)[Q], float *__restrict__ out, long long cells,
+                                             long long c, const TT &A, float (&d)[4]) {
+  constexpr bool D3 = Q != NR * NR;
+  float m[4][4];
+  float mzz = 0.0f, mzx = 0.0f, mzy = 0.0f;  // m002, m102, m012 (D = 3)
+  if constexpr (!D3) {
+    hermite_moments<NR, 3>(F, m, A);
+  } else {
+    float b[3][4][4];
+    hermite_moments3<NR, 3>(F, b, A);
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; p + q < 4; ++q) m[p][q] = b[0][p][q];
+    mzz = b[1][0][0];
+    mzx = b[1][1][0];
+    mzy = b[1][0][1];
+  }
+  const float rho = 1.0f + m[0][0];
+  const float ir = __frcp_rn(rho);
+  const float ux = m[1][0] * ir, uy = m[0][1] * ir;
+  const float Mxx = fmaf(-m[1][0], ux, m[2][0]);
+  const float Mxy = fmaf(-m[1][0], uy, m[1][1]);
+  const float Myy = fmaf(-m[0][1], uy, m[0][2]);
+  const float trM = Mxx + Myy + mzz;  // M_zz = m002 (u_z = 0)
+  const float T = fmaf((D3 ? 1.0f / 3.0f : 0.5f) * trM, ir, 1.0f);
+  const float u2 = ux * ux + uy * uy;
+  // sum f C_i C^2 = sum df c_i (c^2 - D - 2) - 2 M_ij u_j - u_i tr M - rho u_i u^2
+  const float hx = m[3][0] + m[1][2] + mzx, hy = m[0][3] + m[2][1] + mzy;
+  const float qx = 0.5f * (hx - 2.0f * (Mxx * ux + Mxy * uy) - ux * trM - rho * ux * u2);
+  const float qy = 0.5f * (hy - 2.0f * (Mxy * ux + Myy * uy) - uy * trM - rho * uy * u2);
+  if (out) {
+    out[c] = rho;
+    out[cells + c] = ux;
+    out[2 * cells + c] = uy;
+    out[3 * cells + c] = T;
+    if constexpr (!D3) {
+      out[4 * cells + c] = 0.5f * (Mxx - Myy);
+      out[6 * cells + c] = 0.5f * (Myy - Mxx);
+    } else {
+      out[4 * cells + c] = fmaf(-1.0f / 3.0f, trM, Mxx);
+      out[6 * cells + c] = fmaf(-1.0f / 3.0f, trM, Myy);
+    }
+    out[5 * cells + c] = Mxy;
+    out[7 * cells + c] = qx;
+    out[8 * cells + c] = qy;
+  }
+  d[0] = m[0][0];
+  d[1] = m[1][0];
+  d[2] = m[0][1];
+  d[3] = fmaf(D3 ? 3.0f : 2.0f, m[0][0], m[2][0] + m[0][2] + mzz);
 }
 
 // Wall rule of Sec. 3.2 on one node's updated deviations: rho_W from the
@@ -623,7 +703,10 @@ struct Store<float> {
 template <>
 struct Store<__half> {
   static constexpr bool kScaled = true;
-  __device__ static float get(__half v, float w) { return __half2float(v) * w; }
+  // a rounded product (__fmul_rn is never contracted into the subtraction
+  // that follows): a loaded value is then one number whether a segment's
+  // prologue or the ring brought it, so results do not depend on the launch shape
+  __device__ static float get(__half v, float w) { return __fmul_rn(__half2float(v), w); }
   __device__ static __half put(float x, float iw) { return __float2half_rn(x * iw); }
   // two values packed (x0 low, x1 high), stochastically rounded by the
   // hardware (cvt.rs): rbits supplies the random bits of both
@@ -636,7 +719,7 @@ struct Store<__half> {
 template <>
 struct Store<__nv_bfloat16> {
   static constexpr bool kScaled = true;
-  __device__ static float get(__nv_bfloat16 v, float w) { return __bfloat162float(v) * w; }
+  __device__ static float get(__nv_bfloat16 v, float w) { return __fmul_rn(__bfloat162float(v), w); }
   __device__ static __nv_bfloat16 put(float x, float iw) { return __float2bfloat16_rn(x * iw); }
   __device__ static unsigned put_sr2(float x0, float x1, unsigned rbits) {
     unsigned d;
@@ -778,6 +861,95 @@ __device__ __forceinline__ void st_group_sr(S *p, long long gstride, int g, cons
       bits = bits * 0x9e3779b5u + 0x7f4a7c15u;
     }
     *reinterpret_cast<R *>(p + g * gstride) = raw;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Compensated FP32 storage (tag Comp): each stored deviation is hi + lo, hi an
+// FP32 value in the grouped layout above and lo its rounding remainder, held
+// in FP16 as lo * 2^24 / w_a (TT's wq[a] = w_a 2^-24 converts back) in a
+// second plane of the same 16-byte vectors right after the hi plane (its
+// groups hold twice as many values, so a row of either plane is nx 16-byte
+// vectors per group and one byte offset serves both).  Built for the sets
+// whose hi vectors hold 4 values (D2Q16, D3Q64).
+// ---------------------------------------------------------------------------
+struct Comp {};
+
+template <class S>
+struct Elem { using T = S; };
+template <>
+struct Elem<Comp> { using T = float; };
+
+template <class S>
+constexpr bool kIsComp = false;
+template <>
+constexpr bool kIsComp<Comp> = true;
+
+// The lo plane of the populations whose hi plane starts at f (or at a row of
+// it: the byte offset is the same in both planes); plane = nx ny of the grid.
+template <int Q>
+__device__ __forceinline__ const __half *lo_plane(const float *f, long long plane) {
+  return reinterpret_cast<const __half *>(reinterpret_cast<const char *>(f) + (size_t)Q * plane * sizeof(float));
+}
+template <int Q>
+__device__ __forceinline__ __half *lo_plane(float *f, long long plane) {
+  return reinterpret_cast<__half *>(reinterpret_cast<char *>(f) + (size_t)Q * plane * sizeof(float));
+}
+
+// All stored values of node c as FP32 deviations (for Comp, hi + lo rounded
+// once); f at the grid's (or a row's) start, plane = nx ny.
+template <int NR, class S, int NZ, class TT>
+__device__ __forceinline__ void ld_node(const typename Elem<S>::T *f, long long c, long long plane,
+                                        float (&F)[NZ * NR * NR], const TT &Tt) {
+  if constexpr (kIsComp<S>) {
+    using LH = Layout<NR, float, NZ>;
+    using LL = Layout<NR, __half, NZ>;
+    static_assert(LL::V == 2 * LH::V, "hi and lo vectors of 16 bytes");
+#pragma unroll
+    for (int g = 0; g < LH::G; ++g) ld_group<NR>(f + c * LH::V, (long long)LH::V * plane, g, F);
+    const __half *lo = lo_plane<LH::Q>(f, plane) + c * LL::V;
+#pragma unroll
+    for (int g = 0; g < LL::G; ++g) {
+      const uint4 raw = __ldg(reinterpret_cast<const uint4 *>(lo + (long long)g * LL::V * plane));
+      const __half *e = reinterpret_cast<const __half *>(&raw);
+#pragma unroll
+      for (int k = 0; k < LL::V; ++k) {
+        const int a = LL::alpha(g * LL::V + k);
+        F[a] = fmaf(__half2float(e[k]), Tt.wq[a], F[a]);
+      }
+    }
+  } else if constexpr (std::is_same<S, float>::value) {  // (no scale tables needed)
+    using L = Layout<NR, float, NZ>;
+#pragma unroll
+    for (int g = 0; g < L::G; ++g) ld_group<NR>(f + c * L::V, (long long)L::V * plane, g, F);
+  } else {
+    using L = Layout<NR, S, NZ>;
+#pragma unroll
+    for (int g = 0; g < L::G; ++g) ld_group_s<NR, S>(f + c * L::V, (long long)L::V * plane, g, F, Tt);
+  }
+}
+
+// Store node c's values F (round to nearest; for Comp, hi = F and lo = 0).
+template <int NR, class S, int NZ, class TT>
+__device__ __forceinline__ void st_node(typename Elem<S>::T *f, long long c, long long plane,
+                                        const float (&F)[NZ * NR * NR], const TT &Tt) {
+  if constexpr (kIsComp<S>) {
+    using LH = Layout<NR, float, NZ>;
+    using LL = Layout<NR, __half, NZ>;
+#pragma unroll
+    for (int g = 0; g < LH::G; ++g) st_group<NR>(f + c * LH::V, (long long)LH::V * plane, g, F);
+    __half *lo = lo_plane<LH::Q>(f, plane) + c * LL::V;
+#pragma unroll
+    for (int g = 0; g < LL::G; ++g)
+      *reinterpret_cast<uint4 *>(lo + (long long)g * LL::V * plane) = make_uint4(0u, 0u, 0u, 0u);
+  } else if constexpr (std::is_same<S, float>::value) {
+    using L = Layout<NR, float, NZ>;
+#pragma unroll
+    for (int g = 0; g < L::G; ++g) st_group<NR>(f + c * L::V, (long long)L::V * plane, g, F);
+  } else {
+    using L = Layout<NR, S, NZ>;
+#pragma unroll
+    for (int g = 0; g < L::G; ++g) st_group_s<NR, S>(f + c * L::V, (long long)L::V * plane, g, F, Tt);
   }
 }
 

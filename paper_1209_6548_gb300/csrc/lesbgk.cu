@@ -199,7 +199,12 @@ __global__ void __launch_bounds__(kBlock) k_step(const S *__restrict__ fin, S *_
       // rounding key per step and row (not per column): a flow uniform in x stays
       // exactly uniform, so rounding noise cannot seed the x-varying modes the
       // printed unsplit update amplifies
-      const unsigned key = mix32(A.seed ^ mix32((unsigned)j + A.row_key));
+      int gr = j + A.row_key;  // the global row (a y-slab's halo rows may wrap around)
+      if (A.row_period) {
+        gr %= A.row_period;
+        if (gr < 0) gr += A.row_period;
+      }
+      const unsigned key = mix32(A.seed ^ mix32((unsigned)gr));
 #pragma unroll
       for (int g = 0; g < G; ++g) st_group_sr<NR, S>(o, gstride, g, acc, A, key);
     }
@@ -471,17 +476,241 @@ __global__ void __launch_bounds__(kBlockZ) k_step_z(const float *__restrict__ fi
 }
 
 // ---------------------------------------------------------------------------
+// The fused time step with compensated FP32 storage (tag Comp: D2Q16 and
+// D3Q64, N = 3, periodic or fully diffuse walls).  The mapping of k_step
+// (32-node strips, a segment of rows per warp, a per-lane cp.async ring of
+// look-ahead rows), with every stored value carried as hi + lo:
+//   - differences of stored values, the TVD slopes and fluxes of Sec. 3.1,
+//     take (hi_1 - hi_0) + (lo_1 - lo_0), which keeps the stored precision;
+//   - the collision and force source of Sec. 2.2 read hi alone (the source
+//     is dt/tau times the non-equilibrium part, so leaving lo out costs that
+//     fraction of one FP32 rounding);
+//   - the update adds the step's increment t to hi + lo with an error-free
+//     two-sum: s = hi + (lo + t), e = (hi - s) + (lo + t); hi = s, lo = e.
+// A step's storage error is then the FP16 rounding of the remainder, 2^-11
+// of at most half an FP32 ulp, instead of half an FP32 ulp.  The x-advection
+// of each population follows its y-advection at once (it needs only that
+// population's neighbours), so the per-population temporaries stay short.
+// ---------------------------------------------------------------------------
+template <bool SPLIT, int RING, int NZ>
+__global__ void __launch_bounds__(kBlock) k_step_c(const float *__restrict__ fin, float *__restrict__ fout,
+                                                   const KArgs A) {
+  constexpr int NR = 4, N = 3;
+  using LH = Layout<NR, float, NZ>;   // hi plane: 4 FP32 per 16-byte vector
+  using LL = Layout<NR, __half, NZ>;  // lo plane: 8 FP16 per 16-byte vector
+  constexpr int Q = LH::Q, H = LH::H, GH = LH::G, GL = LL::G, VH = LH::V, VL = LL::V, G = GH + GL;
+  static_assert(VL == 2 * VH, "hi and lo vectors of 16 bytes");
+  constexpr int HL = 2;
+  constexpr int U = 32 - 2 * HL;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int strip = warp % A.nstrips;
+  const int seg = warp / A.nstrips;
+  if (seg >= A.nseg) return;  // uniform over the warp
+  const int nx = A.nx, ny = A.ny;
+  const int xl = strip * U - HL + lane;
+  int xw = xl % nx;
+  if (xw < 0) xw += nx;
+  const bool writer = lane >= HL && lane < 32 - HL && xl < nx;
+  const int y0 = seg * A.rows;
+  const int y1 = min(y0 + A.rows, ny);
+  // both planes as 16-byte vectors: vector g < GH of a node is hi group g,
+  // vector GH + g lo group g; each group plane holds nx ny vectors
+  const long long plane = A.plane;
+  const uint4 *vx = reinterpret_cast<const uint4 *>(fin) + xw;
+  auto up_group = [](int g) { return g < GH ? g >= GH / 2 : (g - GH) >= GL / 2; };  // c_y > 0
+  auto unpack = [&](const uint4 (&v)[G], float (&hi)[Q], float (&lo)[Q]) {
+#pragma unroll
+    for (int g = 0; g < GH; ++g) {
+      const float *e = reinterpret_cast<const float *>(&v[g]);
+#pragma unroll
+      for (int k = 0; k < VH; ++k) hi[LH::alpha(g * VH + k)] = e[k];
+    }
+#pragma unroll
+    for (int g = 0; g < GL; ++g) {
+      const __half *e = reinterpret_cast<const __half *>(&v[GH + g]);
+#pragma unroll
+      for (int k = 0; k < VL; ++k) {
+        const int a = LL::alpha(g * VL + k);
+        // a rounded product (never contracted into a later subtraction): a
+        // row's lo values are then the same numbers whether a segment's
+        // prologue loads the row or the ring brings it, whatever the segment
+        // boundaries -- slabs and launch shapes give bitwise the same result
+        lo[a] = __fmul_rn(__half2float(e[k]), A.wq[a]);
+      }
+    }
+  };
+  auto load_row = [&](int j, float (&hi)[Q], float (&lo)[Q]) {
+    const uint4 *p = vx + (long long)map_row(j, ny, A.walls) * nx;
+    uint4 v[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) v[g] = __ldg(p + g * plane);
+    unpack(v, hi, lo);
+  };
+
+  // y-stencil per population, as in k_step, with hi and lo parts of values:
+  //   c_y > 0: s0 = f_j - f_{j-1} (a difference), s1 = sigma_{j-1}; fc = f_j
+  //   c_y < 0: s0 = f_{j+1} (s0h + s0l),        s1 = sigma_j;     fc = f_j
+  float fch[Q], fcl[Q], s0h[Q], s0l[Q], s1[Q];
+  {
+    float m2h[Q], m2l[Q], m1h[Q], m1l[Q], p1h[Q], p1l[Q];
+    load_row(y0 - 2, m2h, m2l);
+    load_row(y0 - 1, m1h, m1l);
+    load_row(y0, fch, fcl);
+    load_row(y0 + 1, p1h, p1l);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      const float d0 = (fch[a] - m1h[a]) + (fcl[a] - m1l[a]);  // f_j - f_{j-1}
+      if (a % NR >= H) {
+        s0h[a] = d0;
+        s0l[a] = 0.0f;
+        s1[a] = minmod((m1h[a] - m2h[a]) + (m1l[a] - m2l[a]), d0);
+      } else {
+        s0h[a] = p1h[a];
+        s0l[a] = p1l[a];
+        s1[a] = minmod(d0, (p1h[a] - fch[a]) + (p1l[a] - fcl[a]));
+      }
+    }
+  }
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint4 *ring = reinterpret_cast<uint4 *>(smem_raw) + (size_t)(threadIdx.x >> 5) * RING * G * 32 + lane;
+  int r1 = map_row(y0 + 1, ny, A.walls), r2 = map_row(y0 + 2, ny, A.walls);
+  const int nrows = y1 - y0;
+  auto issue_rowload = [&](int k) {
+    if (k < nrows) {
+      uint4 *slot = ring + (k % RING) * G * 32;
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        cp_async_raw<16>(slot + g * 32, vx + (long long)(up_group(g) ? r1 : r2) * nx + g * plane);
+      r1 = r2;
+      r2 = r2 + 1 < ny ? r2 + 1 : (A.walls ? ny - 1 : 0);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int k = 0; k < RING - 1; ++k) issue_rowload(k);
+
+  for (int j = y0; j < y1; ++j) {
+    const int k = j - y0;
+    issue_rowload(k + RING - 1);
+    cp_async_wait<RING - 1>();
+    float ldh[Q], ldl[Q];
+    {
+      uint4 v[G];
+      const uint4 *slot = ring + (k % RING) * G * 32;
+#pragma unroll
+      for (int g = 0; g < G; ++g) v[g] = slot[g * 32];
+      unpack(v, ldh, ldl);
+    }
+    float src[Q], om;
+    collide_om<NR, N>(fch, src, om, A, A);
+
+    float nh[Q], nl[Q];  // f^{n+1} as hi + lo
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      const int iy = a % NR, ix = (a / NR) % NR;
+      const float f0h = fch[a], f0l = fcl[a];
+      float diff;
+      if (iy >= H) {  // c_y > 0
+        const float dn = (ldh[a] - f0h) + (ldl[a] - f0l);
+        const float sg = minmod(s0h[a], dn);
+        diff = fmaf(A.ky[iy], sg - s1[a], s0h[a]);
+        s0h[a] = dn;
+        s1[a] = sg;
+        fch[a] = ldh[a];
+        fcl[a] = ldl[a];
+      } else {  // c_y < 0
+        const float d1 = (s0h[a] - f0h) + (s0l[a] - f0l);
+        const float sg = minmod(d1, (ldh[a] - s0h[a]) + (ldl[a] - s0l[a]));
+        diff = fmaf(-A.ky[iy], sg - s1[a], d1);
+        s1[a] = sg;
+        fch[a] = s0h[a];
+        fcl[a] = s0l[a];
+        s0h[a] = ldh[a];
+        s0l[a] = ldl[a];
+      }
+      const float ady = A.ay[iy] * diff;  // (c_y dt/dy)(F_{j+1/2} - F_{j-1/2})
+      float inc = fmaf(-om, f0h, src[a]) - ady;
+      // x-fluxes of f^n (printed update) or of f* = f^n - ady (split), whose
+      // hi part is f0h and whose change goes to the lo part
+      const float xl_ = SPLIT ? f0l - ady : f0l;
+      const float dl = (f0h - __shfl_up_sync(kFull, f0h, 1)) + (xl_ - __shfl_up_sync(kFull, xl_, 1));
+      const float dr = __shfl_down_sync(kFull, dl, 1);
+      const float sg = minmod(dl, dr);
+      float dxf;
+      if (ix >= H) dxf = fmaf(A.kx[ix], sg - __shfl_up_sync(kFull, sg, 1), dl);
+      else dxf = fmaf(-A.kx[ix], __shfl_down_sync(kFull, sg, 1) - sg, dr);
+      inc = fmaf(-A.ax[ix], dxf, inc);
+      // error-free update of hi + lo
+      const float t = f0l + inc;
+      const float sh = f0h + t;
+      nh[a] = sh;
+      nl[a] = (f0h - sh) + t;
+    }
+
+    if (A.walls && (j == 0 || j == ny - 1)) {
+      // the wall rule of wall_fix on hi + lo: rho_W from the incoming half
+      // (two sums), the outgoing half rho_W S as hi with its FMA remainder as lo
+      const int side = j == 0 ? 0 : 1;
+      float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const int iy = a % NR;
+        if (side == 0 ? (iy < H) : (iy >= H)) {
+          sh = fmaf(fabsf(A.c[iy]), nh[a], sh);
+          sl = fmaf(fabsf(A.c[iy]), nl[a], sl);
+        }
+      }
+      const float rw1 = ((sh - A.wA[side]) + sl) * A.wB[side];  // rho_W - 1
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const int iy = a % NR;
+        if (side == 0 ? (iy >= H) : (iy < H)) {
+          const float h = fmaf(rw1, A.wS[side][a], A.wSdev[side][a]);
+          nl[a] = fmaf(rw1, A.wS[side][a], A.wSdev[side][a] - h);
+          nh[a] = h;
+        }
+      }
+    }
+
+    if (writer) {
+      uint4 *o = reinterpret_cast<uint4 *>(fout) + (long long)j * nx + xw;
+#pragma unroll
+      for (int g = 0; g < GH; ++g) {
+        float4 v;
+        v.x = nh[LH::alpha(g * VH)];
+        v.y = nh[LH::alpha(g * VH + 1)];
+        v.z = nh[LH::alpha(g * VH + 2)];
+        v.w = nh[LH::alpha(g * VH + 3)];
+        *reinterpret_cast<float4 *>(o + g * plane) = v;
+      }
+#pragma unroll
+      for (int g = 0; g < GL; ++g) {
+        uint4 raw;
+        unsigned *w = reinterpret_cast<unsigned *>(&raw);
+#pragma unroll
+        for (int k2 = 0; k2 < VL; k2 += 2) {
+          const int a0 = LL::alpha(g * VL + k2), a1 = LL::alpha(g * VL + k2 + 1);
+          const __half2 h2 = __floats2half2_rn(nl[a0] * A.iwq[a0], nl[a1] * A.iwq[a1]);
+          w[k2 / 2] = *reinterpret_cast<const unsigned *>(&h2);
+        }
+        o[(GH + g) * plane] = raw;
+      }
+    }
+  }
+  cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
 // Initial populations f = rho S(T,u) (Eq. feq0 to order N: the Hermite
 // expansion of the isotropic Maxwellian), then the wall rule once.
 // fields: double[4][ny][nx] = rho, u_x, u_y, T (or nullptr: rest).
 // ---------------------------------------------------------------------------
 template <int NR, int N, class S, int NZ = 1>
-__global__ void __launch_bounds__(kBlock) k_init(const double *__restrict__ fields, S *__restrict__ f,
-                                                 const KArgs A) {
-  using Lay = Layout<NR, S, NZ>;
-  constexpr int Q = Lay::Q;
+__global__ void __launch_bounds__(kBlock) k_init(const double *__restrict__ fields,
+                                                 typename Elem<S>::T *__restrict__ f, const KArgs A) {
+  constexpr int Q = NZ * NR * NR;
   const long long cells = A.plane;
-  const long long gstride = (long long)Lay::V * cells;
   for (long long c = blockIdx.x * (long long)kBlock + threadIdx.x; c < cells; c += (long long)gridDim.x * kBlock) {
     float drho = 0.f, ux = 0.f, uy = 0.f, dT = 0.f;
     if (fields) {
@@ -508,8 +737,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const double *__restrict__ fiel
     if (A.xwalls) apply_walls_node<NR, 2>(Sv, i, j, A);
     else if (A.wspec != 0.0f) apply_walls_node<NR, 1>(Sv, i, j, A);
     else apply_walls_node<NR, 0>(Sv, i, j, A);
-#pragma unroll
-    for (int g = 0; g < Lay::G; ++g) st_group_s<NR, S>(f + c * Lay::V, gstride, g, Sv, A);
+    st_node<NR, S, NZ>(f, c, cells, Sv, A);
   }
 }
 
@@ -545,95 +773,27 @@ __global__ void __launch_bounds__(kBlock) k_field_stats(const double *__restrict
 
 // Populations between the grouped layout and the public [a][j][i] layout.
 template <int NR, class S, int NZ = 1>
-__global__ void __launch_bounds__(kBlock) k_ungroup(const S *__restrict__ f, float *__restrict__ out,
-                                                    long long cells, const KArgs A) {
-  using Lay = Layout<NR, S, NZ>;
-  const long long gstride = (long long)Lay::V * cells;
+__global__ void __launch_bounds__(kBlock) k_ungroup(const typename Elem<S>::T *__restrict__ f,
+                                                    float *__restrict__ out, long long cells, const KArgs A) {
+  constexpr int Q = NZ * NR * NR;
   for (long long c = blockIdx.x * (long long)kBlock + threadIdx.x; c < cells; c += (long long)gridDim.x * kBlock) {
-    float F[Lay::Q];
+    float F[Q];
+    ld_node<NR, S, NZ>(f, c, cells, F, A);
 #pragma unroll
-    for (int g = 0; g < Lay::G; ++g) ld_group_s<NR, S>(f + c * Lay::V, gstride, g, F, A);
-#pragma unroll
-    for (int a = 0; a < Lay::Q; ++a) out[a * cells + c] = F[a];
+    for (int a = 0; a < Q; ++a) out[a * cells + c] = F[a];
   }
 }
 
 template <int NR, class S, int NZ = 1>
-__global__ void __launch_bounds__(kBlock) k_group(const float *__restrict__ in, S *__restrict__ f,
+__global__ void __launch_bounds__(kBlock) k_group(const float *__restrict__ in, typename Elem<S>::T *__restrict__ f,
                                                   long long cells, const KArgs A) {
-  using Lay = Layout<NR, S, NZ>;
-  const long long gstride = (long long)Lay::V * cells;
+  constexpr int Q = NZ * NR * NR;
   for (long long c = blockIdx.x * (long long)kBlock + threadIdx.x; c < cells; c += (long long)gridDim.x * kBlock) {
-    float F[Lay::Q];
+    float F[Q];
 #pragma unroll
-    for (int a = 0; a < Lay::Q; ++a) F[a] = __ldg(in + a * cells + c);
-#pragma unroll
-    for (int g = 0; g < Lay::G; ++g) st_group_s<NR, S>(f + c * Lay::V, gstride, g, F, A);
+    for (int a = 0; a < Q; ++a) F[a] = __ldg(in + a * cells + c);
+    st_node<NR, S, NZ>(f, c, cells, F, A);
   }
-}
-
-// ---------------------------------------------------------------------------
-// Moments of Eq. (mac) of one node from its deviations F = f - w, written to
-// out[k * cells + c] (k = rho, u_x, u_y, T, sigma_xx, sigma_xy, sigma_yy, q_x,
-// q_y) when out is set; returns in d the node's deviations of the conserved
-// sums sum_a df_a {1, c_x, c_y, c^2}: with the Hermite moments m_pql =
-// sum df He_p(c_x) He_q(c_y) He_l(c_z) these are m000, m100, m010 and
-// m200 + m020 (+ m002) + D m000.  D = 2 for the 2D sets; D = 3 (Q = NR^3/2
-// stored, z-even) adds the c_z terms: T = tr P/(3 rho), sigma trace-free in
-// 3D (sigma_zz = -sigma_xx - sigma_yy is not written), q with c_z^2 in C^2.
-// ---------------------------------------------------------------------------
-template <int NR, int Q>
-__device__ __forceinline__ void node_moments(const float (&F)[Q], float *__restrict__ out, long long cells,
-                                             long long c, const KArgs &A, float (&d)[4]) {
-  constexpr bool D3 = Q != NR * NR;
-  float m[4][4];
-  float mzz = 0.0f, mzx = 0.0f, mzy = 0.0f;  // m002, m102, m012 (D = 3)
-  if constexpr (!D3) {
-    hermite_moments<NR, 3>(F, m, A);
-  } else {
-    float b[3][4][4];
-    hermite_moments3<NR, 3>(F, b, A);
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-      for (int q = 0; p + q < 4; ++q) m[p][q] = b[0][p][q];
-    mzz = b[1][0][0];
-    mzx = b[1][1][0];
-    mzy = b[1][0][1];
-  }
-  const float rho = 1.0f + m[0][0];
-  const float ir = __frcp_rn(rho);
-  const float ux = m[1][0] * ir, uy = m[0][1] * ir;
-  const float Mxx = fmaf(-m[1][0], ux, m[2][0]);
-  const float Mxy = fmaf(-m[1][0], uy, m[1][1]);
-  const float Myy = fmaf(-m[0][1], uy, m[0][2]);
-  const float trM = Mxx + Myy + mzz;  // M_zz = m002 (u_z = 0)
-  const float T = fmaf((D3 ? 1.0f / 3.0f : 0.5f) * trM, ir, 1.0f);
-  const float u2 = ux * ux + uy * uy;
-  // sum f C_i C^2 = sum df c_i (c^2 - D - 2) - 2 M_ij u_j - u_i tr M - rho u_i u^2
-  const float hx = m[3][0] + m[1][2] + mzx, hy = m[0][3] + m[2][1] + mzy;
-  const float qx = 0.5f * (hx - 2.0f * (Mxx * ux + Mxy * uy) - ux * trM - rho * ux * u2);
-  const float qy = 0.5f * (hy - 2.0f * (Mxy * ux + Myy * uy) - uy * trM - rho * uy * u2);
-  if (out) {
-    out[c] = rho;
-    out[cells + c] = ux;
-    out[2 * cells + c] = uy;
-    out[3 * cells + c] = T;
-    if constexpr (!D3) {
-      out[4 * cells + c] = 0.5f * (Mxx - Myy);
-      out[6 * cells + c] = 0.5f * (Myy - Mxx);
-    } else {
-      out[4 * cells + c] = fmaf(-1.0f / 3.0f, trM, Mxx);
-      out[6 * cells + c] = fmaf(-1.0f / 3.0f, trM, Myy);
-    }
-    out[5 * cells + c] = Mxy;
-    out[7 * cells + c] = qx;
-    out[8 * cells + c] = qy;
-  }
-  d[0] = m[0][0];
-  d[1] = m[1][0];
-  d[2] = m[0][1];
-  d[3] = fmaf(D3 ? 3.0f : 2.0f, m[0][0], m[2][0] + m[0][2] + mzz);
 }
 
 // Conservation totals: per-node sums in FP32 (above), summed in FP32 over
@@ -686,20 +846,18 @@ struct ConsSums {
 
 // Moments per node of the grouped layout, plus the block partial sums, over
 // `cells` consecutive nodes from f (a whole grid, or a range of its rows);
-// gstride: elements between group planes (V nx ny).  out: float[9][cells] or
-// nullptr.
+// plane: nodes of the whole grid (nx ny, the distance between group planes in
+// vectors).  out: float[9][cells] or nullptr.
 template <int NR, class S, int NZ = 1>
-__global__ void __launch_bounds__(kMomBlock) k_moments(const S *__restrict__ f, float *__restrict__ out,
-                                                       double *__restrict__ partial, long long cells,
-                                                       long long gstride, const KArgs A) {
-  using Lay = Layout<NR, S, NZ>;
-  constexpr int Q = Lay::Q;
+__global__ void __launch_bounds__(kMomBlock) k_moments(const typename Elem<S>::T *__restrict__ f,
+                                                       float *__restrict__ out, double *__restrict__ partial,
+                                                       long long cells, long long plane, const KArgs A) {
+  constexpr int Q = NZ * NR * NR;
   ConsSums cs;
   for (long long c = blockIdx.x * (long long)kMomBlock + threadIdx.x; c < cells;
        c += (long long)gridDim.x * kMomBlock) {
     float F[Q];
-#pragma unroll
-    for (int g = 0; g < Lay::G; ++g) ld_group_s<NR, S>(f + c * Lay::V, gstride, g, F, A);
+    ld_node<NR, S, NZ>(f, c, plane, F, A);
     float d[4];
     node_moments<NR>(F, out, cells, c, A, d);
     cs.add(d);
@@ -713,19 +871,17 @@ __global__ void __launch_bounds__(kMomBlock) k_moments(const S *__restrict__ f, 
 // current fields (residual of lesbgk_residual); mpart[block] receives the
 // block's sum of rho - 1 (FP32 per thread, FP64 across the block).
 template <int NR, class S, int NZ = 1>
-__global__ void __launch_bounds__(kMomBlock) k_residual(const S *__restrict__ f, float *__restrict__ snap,
-                                                        int update_only, unsigned *__restrict__ rbits,
-                                                        double *__restrict__ mpart, const KArgs A) {
-  using Lay = Layout<NR, S, NZ>;
-  constexpr int Q = Lay::Q;
+__global__ void __launch_bounds__(kMomBlock) k_residual(const typename Elem<S>::T *__restrict__ f,
+                                                        float *__restrict__ snap, int update_only,
+                                                        unsigned *__restrict__ rbits, double *__restrict__ mpart,
+                                                        const KArgs A) {
+  constexpr int Q = NZ * NR * NR;
   const long long cells = A.plane;
-  const long long gstride = (long long)Lay::V * cells;
   float rmax = 0.0f, dm = 0.0f;
   for (long long c = blockIdx.x * (long long)kMomBlock + threadIdx.x; c < cells;
        c += (long long)gridDim.x * kMomBlock) {
     float F[Q];
-#pragma unroll
-    for (int g = 0; g < Lay::G; ++g) ld_group_s<NR, S>(f + c * Lay::V, gstride, g, F, A);
+    ld_node<NR, S, NZ>(f, c, cells, F, A);
     float m[3][3], mzz = 0.0f;
     if constexpr (NZ == 1) {
       hermite_moments<NR, 2>(F, m, A);
@@ -823,7 +979,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 size_t buffer_bytes(const lesbgk_params *p) {
   const size_t cells = (size_t)p->nx * p->ny;
   const size_t q = (size_t)p->nroots * p->nroots * (p->dim == 3 ? p->nroots / 2 : 1);  // values per node
-  size_t per = q * (p->storage == LESBGK_F32 ? sizeof(float) : 2);
+  size_t per = q * (p->storage == LESBGK_F32 ? sizeof(float) : p->storage == LESBGK_F32C ? 6 : 2);
   if (per < 9 * sizeof(float)) per = 9 * sizeof(float);
   if (per < 4 * sizeof(double)) per = 4 * sizeof(double);
   return align_up(cells * per, 256);
@@ -873,13 +1029,17 @@ constexpr int kRing = 4;
 
 template <int NR, class S, int NZ>
 constexpr size_t step_smem_bytes() {
-  return (size_t)(kBlock / 32) * kRing * Layout<NR, S, NZ>::G * 32 * Layout<NR, S, NZ>::VB;
+  if constexpr (kIsComp<S>)  // both planes' 16-byte vectors
+    return (size_t)(kBlock / 32) * kRing * (Layout<NR, float, NZ>::G + Layout<NR, __half, NZ>::G) * 32 * 16;
+  else
+    return (size_t)(kBlock / 32) * kRing * Layout<NR, S, NZ>::G * 32 * Layout<NR, S, NZ>::VB;
 }
 
 // Call fn(NR, N, storage tag, NZ) with compile-time constants for the built
 // combinations: every (nroots, order) of the 2D sets in FP32, the default
-// orders also in FP16 and BF16 (NZ = 1); D3Q64, N = 3, in FP32, FP16 and BF16
-// (NZ = 2 stored z-levels); D3Q216, N = 4, in FP32 (NZ = 3).
+// orders also in FP16 and BF16 (NZ = 1), D2Q16 also compensated (Comp);
+// D3Q64, N = 3, in FP32, FP16, BF16 and compensated (NZ = 2 stored z-levels);
+// D3Q216, N = 4, in FP32 (NZ = 3).
 template <class Fn>
 void dispatch(int nr, int order, int storage, int dim, Fn &&fn) {
   using R4 = std::integral_constant<int, 4>;
@@ -892,11 +1052,13 @@ void dispatch(int nr, int order, int storage, int dim, Fn &&fn) {
   if (dim == 3 && nr == 6) {
     fn(R6{}, N4{}, float{}, Z3{});
   } else if (dim == 3) {
-    if (storage == LESBGK_F16) fn(R4{}, N3{}, __half{}, Z2{});
+    if (storage == LESBGK_F32C) fn(R4{}, N3{}, Comp{}, Z2{});
+    else if (storage == LESBGK_F16) fn(R4{}, N3{}, __half{}, Z2{});
     else if (storage == LESBGK_BF16) fn(R4{}, N3{}, __nv_bfloat16{}, Z2{});
     else fn(R4{}, N3{}, float{}, Z2{});
   } else if (nr == 4 && order == 3) {
-    if (storage == LESBGK_F16) fn(R4{}, N3{}, __half{}, Z1{});
+    if (storage == LESBGK_F32C) fn(R4{}, N3{}, Comp{}, Z1{});
+    else if (storage == LESBGK_F16) fn(R4{}, N3{}, __half{}, Z1{});
     else if (storage == LESBGK_BF16) fn(R4{}, N3{}, __nv_bfloat16{}, Z1{});
     else fn(R4{}, N3{}, float{}, Z1{});
   } else if (nr == 6 && order == 4) {
@@ -919,7 +1081,11 @@ cudaError_t allow_smem(const lesbgk *h) {
     auto allow = [&](auto kernel, int smem) {
       if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     };
-    if constexpr (NZ == 3) {  // D3Q216: one warp per stored z-level
+    if constexpr (kIsComp<S>) {
+      constexpr int smem = (int)step_smem_bytes<NR, S, NZ>();
+      allow(k_step_c<true, kRing, NZ>, smem);
+      allow(k_step_c<false, kRing, NZ>, smem);
+    } else if constexpr (NZ == 3) {  // D3Q216: one warp per stored z-level
       constexpr int smem = (int)stepz_smem_bytes<kRing>();
       allow(k_step_z<true, kRing, false>, smem);
       allow(k_step_z<false, kRing, false>, smem);
@@ -946,10 +1112,16 @@ int launch_step(lesbgk *h, const void *fin, void *fout, cudaStream_t s) {
   dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto n, auto st, auto z) {
     constexpr int NR = decltype(r)::value, N = decltype(n)::value, NZ = decltype(z)::value;
     using S = decltype(st);
-    const S *fi = static_cast<const S *>(fin);
-    S *fo = static_cast<S *>(fout);
+    using E = typename Elem<S>::T;
+    const E *fi = static_cast<const E *>(fin);
+    E *fo = static_cast<E *>(fout);
     const bool split = h->p.scheme == LESBGK_SPLIT;
-    if constexpr (NZ == 3) {  // D3Q216: a block of three warps per strip and segment
+    if constexpr (kIsComp<S>) {  // compensated storage: hi + lo planes
+      constexpr size_t smem = step_smem_bytes<NR, S, NZ>();
+      if (split) k_step_c<true, kRing, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+      else k_step_c<false, kRing, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+      return;
+    } else if constexpr (NZ == 3) {  // D3Q216: a block of three warps per strip and segment
       constexpr size_t smem = stepz_smem_bytes<kRing>();
       const unsigned gz = (unsigned)warps;
       const bool spec = h->args.walls && h->args.wspec != 0.0f;
@@ -994,7 +1166,7 @@ int launch_init(lesbgk *h, const double *fields, void *f, cudaStream_t s) {
   dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto n, auto st, auto z) {
     constexpr int NR = decltype(r)::value, N = decltype(n)::value, NZ = decltype(z)::value;
     using S = decltype(st);
-    k_init<NR, N, S, NZ><<<grid, kBlock, 0, s>>>(fields, static_cast<S *>(f), h->args);
+    k_init<NR, N, S, NZ><<<grid, kBlock, 0, s>>>(fields, static_cast<typename Elem<S>::T *>(f), h->args);
   });
   return 0;
 }
@@ -1004,8 +1176,8 @@ int launch_moments(lesbgk *h, float *out, cudaStream_t s) {
   dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto, auto st, auto z) {
     constexpr int NR = decltype(r)::value, NZ = decltype(z)::value;
     using S = decltype(st);
-    k_moments<NR, S, NZ><<<kMomGrid, kMomBlock, 0, s>>>(static_cast<const S *>(f), out, h->partial, h->args.plane,
-                                                        (long long)Layout<NR, S, NZ>::V * h->args.plane, h->args);
+    k_moments<NR, S, NZ><<<kMomGrid, kMomBlock, 0, s>>>(static_cast<const typename Elem<S>::T *>(f), out,
+                                                        h->partial, h->args.plane, h->args.plane, h->args);
   });
   k_reduce_partials<<<1, 128, 0, s>>>(h->partial, kMomGrid, h->sums);
   return 0;
@@ -1028,8 +1200,8 @@ cudaError_t launch_init(const KArgs &A, int nr, int order, const double *fields,
 
 cudaError_t launch_moments(const KArgs &A, int nr, const float *f, float *out, double *partial, double *sums,
                            cudaStream_t s) {
-  if (nr == 4) k_moments<4, float><<<kMomGrid, kMomBlock, 0, s>>>(f, out, partial, A.plane, 4 * A.plane, A);
-  else k_moments<6, float><<<kMomGrid, kMomBlock, 0, s>>>(f, out, partial, A.plane, 2 * A.plane, A);
+  if (nr == 4) k_moments<4, float><<<kMomGrid, kMomBlock, 0, s>>>(f, out, partial, A.plane, A.plane, A);
+  else k_moments<6, float><<<kMomGrid, kMomBlock, 0, s>>>(f, out, partial, A.plane, A.plane, A);
   k_reduce_partials<<<1, 128, 0, s>>>(partial, kMomGrid, sums);
   return cudaGetLastError();
 }
@@ -1203,7 +1375,7 @@ extern "C" int lesbgk_residual(lesbgk *h, float *d_snap, int64_t steps, double *
     dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto, auto st, auto z) {
       using S = decltype(st);
       k_residual<decltype(r)::value, S, decltype(z)::value><<<kMomGrid, kMomBlock, 0, s>>>(
-          static_cast<const S *>(f), d_snap, steps <= 0 ? 1 : 0, rbits, h->partial, h->args);
+          static_cast<const typename Elem<S>::T *>(f), d_snap, steps <= 0 ? 1 : 0, rbits, h->partial, h->args);
     });
     e = cudaGetLastError();
   }
@@ -1230,7 +1402,7 @@ extern "C" int lesbgk_get_populations(lesbgk *h, float *d_out, void *stream) {
   dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto, auto st, auto z) {
     using S = decltype(st);
     k_ungroup<decltype(r)::value, S, decltype(z)::value>
-        <<<grid_for(h, cells), kBlock, 0, s>>>(static_cast<const S *>(f), d_out, cells, h->args);
+        <<<grid_for(h, cells), kBlock, 0, s>>>(static_cast<const typename Elem<S>::T *>(f), d_out, cells, h->args);
   });
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? 0 : cuda_fail(e, "get populations");
@@ -1244,7 +1416,7 @@ extern "C" int lesbgk_set_populations(lesbgk *h, const float *d_in, int64_t step
   dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto, auto st, auto z) {
     using S = decltype(st);
     k_group<decltype(r)::value, S, decltype(z)::value>
-        <<<grid_for(h, cells), kBlock, 0, s>>>(d_in, static_cast<S *>(f), cells, h->args);
+        <<<grid_for(h, cells), kBlock, 0, s>>>(d_in, static_cast<typename Elem<S>::T *>(f), cells, h->args);
   });
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "set populations");
@@ -1256,9 +1428,15 @@ namespace {
 // Bytes of one stored vector and the number of group planes of the solver's layout.
 void row_geometry(const lesbgk *h, int *vb, int *groups) {
   dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto, auto st, auto z) {
-    using Lay = Layout<decltype(r)::value, decltype(st), decltype(z)::value>;
-    *vb = Lay::VB;
-    *groups = Lay::G;
+    using S = decltype(st);
+    constexpr int NR = decltype(r)::value, NZ = decltype(z)::value;
+    if constexpr (kIsComp<S>) {  // the lo plane's groups follow the hi plane's, 16-byte vectors in both
+      *vb = 16;
+      *groups = Layout<NR, float, NZ>::G + Layout<NR, __half, NZ>::G;
+    } else {
+      *vb = Layout<NR, S, NZ>::VB;
+      *groups = Layout<NR, S, NZ>::G;
+    }
   });
 }
 
@@ -1312,10 +1490,10 @@ extern "C" int lesbgk_moments_rows(lesbgk *h, int32_t j0, int32_t nrows, float *
   dispatch(h->nr, h->order, h->p.storage, h->p.dim, [&](auto r, auto, auto st, auto z) {
     constexpr int NR = decltype(r)::value, NZ = decltype(z)::value;
     using S = decltype(st);
-    using Lay = Layout<NR, S, NZ>;
-    const S *fr = static_cast<const S *>(f) + (long long)j0 * h->p.nx * Lay::V;
-    k_moments<NR, S, NZ><<<kMomGrid, kMomBlock, 0, s>>>(fr, d_out, h->partial, cells,
-                                                        (long long)Lay::V * h->args.plane, h->args);
+    using E = typename Elem<S>::T;
+    constexpr int V = Layout<NR, E, NZ>::V;  // (for Comp the hi plane's; the lo plane shares its byte offsets)
+    const E *fr = static_cast<const E *>(f) + (long long)j0 * h->p.nx * V;
+    k_moments<NR, S, NZ><<<kMomGrid, kMomBlock, 0, s>>>(fr, d_out, h->partial, cells, h->args.plane, h->args);
   });
   k_reduce_partials<<<1, 128, 0, s>>>(h->partial, kMomGrid, h->sums);
   cudaError_t e = cudaGetLastError();

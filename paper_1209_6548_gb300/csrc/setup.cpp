@@ -63,9 +63,14 @@ int check_params(const lesbgk_params *p) {
   if (!(p->dx >= 0.0 && p->dy >= 0.0) || !std::isfinite(p->dx) || !std::isfinite(p->dy) ||
       ((p->dx > 0.0) != (p->dy > 0.0)))
     return fail(LESBGK_EINVAL, "dx and dy must both be 0 (derived) or both > 0");
-  if (p->reserved != 0) return fail(LESBGK_EINVAL, "reserved must be 0");
-  if (p->storage != LESBGK_F32 && p->storage != LESBGK_F16 && p->storage != LESBGK_BF16)
-    return fail(LESBGK_EINVAL, "storage must be LESBGK_F32, LESBGK_F16 or LESBGK_BF16");
+  if (p->row_period < 0) return fail(LESBGK_EINVAL, "row_period must be >= 0");
+  if (p->storage != LESBGK_F32 && p->storage != LESBGK_F16 && p->storage != LESBGK_BF16 &&
+      p->storage != LESBGK_F32C)
+    return fail(LESBGK_EINVAL, "storage must be LESBGK_F32, LESBGK_F16, LESBGK_BF16 or LESBGK_F32C");
+  if (p->storage == LESBGK_F32C &&
+      (p->nroots != 4 || order != 3 || p->bc_x != LESBGK_PERIODIC || p->wall_specular != 0.0))
+    return fail(LESBGK_EINVAL, "compensated storage is built for D2Q16 and D3Q64 (order 3), periodic in x, "
+                "without a specular share");
   if (p->storage != LESBGK_F32 && order != default_order(p->nroots))
     return fail(LESBGK_EINVAL, "16-bit storage is built for the default order only");
   if (p->scheme != LESBGK_UNSPLIT && p->scheme != LESBGK_SPLIT)
@@ -175,8 +180,10 @@ int build_setup(const lesbgk_params &p, int order, const FieldStats *stats, Setu
     A.nax2[i][0] = A.nax2[i][1] = -A.ax[i];
   }
   // FP16 holds 2^10 (f_a - w_a)/w_a: relative deviations down to 6e-8 stay in
-  // its normal range (where stochastic rounding is unbiased) and up to 64 fit
-  const double store_scale = p.storage == LESBGK_F16 ? 1024.0 : 1.0;
+  // its normal range (where stochastic rounding is unbiased) and up to 64 fit;
+  // the compensated storage's FP16 remainder holds lo 2^24 / w_a (|lo| is at
+  // most half an FP32 ulp of the deviation: 2^-24 of it)
+  const double store_scale = p.storage == LESBGK_F16 ? 1024.0 : (p.storage == LESBGK_F32C ? 16777216.0 : 1.0);
   const int nzw = (p.dim == 3 && nr * nr * (nr / 2) <= kMaxQ) ? nr / 2 : 1;  // D3Q64: stored z-levels
   for (int iz = 0; iz < nzw; ++iz)
     for (int ix = 0; ix < nr; ++ix)
@@ -199,7 +206,8 @@ int build_setup(const lesbgk_params &p, int order, const FieldStats *stats, Setu
   A.walls = p.bc_y == LESBGK_DIFFUSE ? 1 : 0;
   A.wspec = (float)p.wall_specular;
   A.plane = (long long)p.nx * p.ny;
-  A.row_key = (unsigned)p.row_offset;
+  A.row_key = p.row_offset;
+  A.row_period = p.row_period;
   h->nroots = nr;
   h->order = N;
   h->dim = D;

@@ -39,7 +39,8 @@ struct KArgs {
   int rows, nstrips, nseg;
   long long plane;             // nx*ny
   unsigned seed;               // per-launch key of the 16-bit stochastic rounding
-  unsigned row_key;            // global index of row 0 (the rounding is keyed by global row)
+  int row_key;                 // global index of row 0 (the rounding is keyed by global row)
+  int row_period;              // wrap of the global row (the whole domain's ny if periodic), or 0
   float wspec;                 // specular fraction 1 - gamma of the Maxwell wall (0: fully diffuse)
   int xwalls;                  // diffuse walls at rest on columns 0 and nx-1
   float wSx[2][kMaxQ];         // x-wall equilibrium S(T_wx, 0), [0] left, [1] right

@@ -21,7 +21,7 @@ from .build import LIB
 
 OK, EINVAL, EUNSTABLE, ESPACE, ECUDA, EDIVERGED = 0, -1, -2, -3, -4, -5
 PERIODIC, DIFFUSE = 0, 1
-F32, F16, BF16 = 0, 1, 2
+F32, F16, BF16, F32C = 0, 1, 2, 3
 UNSPLIT, SPLIT = 0, 1
 MOMENT_NAMES = ("rho", "ux", "uy", "T", "sxx", "sxy", "syy", "qx", "qy")
 
@@ -34,7 +34,8 @@ SYMBOLS = ("lesbgk_workspace_size", "lesbgk_create", "lesbgk_reinit", "lesbgk_st
            "lesbgk_batch_workspace_size", "lesbgk_batch_slot_bytes", "lesbgk_batch_create", "lesbgk_batch_add",
            "lesbgk_batch_remove", "lesbgk_batch_step", "lesbgk_batch_residuals", "lesbgk_batch_moments",
            "lesbgk_batch_get_populations", "lesbgk_batch_get_info", "lesbgk_batch_set_rows",
-           "lesbgk_batch_autotune", "lesbgk_batch_pool_free", "lesbgk_batch_destroy")
+           "lesbgk_batch_autotune", "lesbgk_batch_pool_free", "lesbgk_batch_destroy", "lesbgk_batch_add_many",
+           "lesbgk_batch_moments_many")
 
 
 class Params(C.Structure):
@@ -47,7 +48,7 @@ class Params(C.Structure):
         ("wall_T", C.c_double * 2), ("wall_ux", C.c_double * 2), ("g", C.c_double * 2),
         ("wall_specular", C.c_double), ("wall_T_amp", C.c_double), ("wall_T_freq", C.c_double),
         ("dim", C.c_int32), ("bc_x", C.c_int32), ("wall_Tx", C.c_double * 2),
-        ("dx", C.c_double), ("dy", C.c_double), ("row_offset", C.c_int32), ("reserved", C.c_int32),
+        ("dx", C.c_double), ("dy", C.c_double), ("row_offset", C.c_int32), ("row_period", C.c_int32),
     ]
 
 
@@ -102,6 +103,8 @@ def lib():
             L.lesbgk_batch_create.argtypes = [i32, i32, vp, sz, vp, C.POINTER(vp)]
             L.lesbgk_batch_add.argtypes = [vp, C.POINTER(Params), vp, vp, C.POINTER(i32)]
             L.lesbgk_batch_remove.argtypes = [vp, i32, vp]
+            L.lesbgk_batch_add_many.argtypes = [vp, i32, C.POINTER(Params), vp, vp, vp]
+            L.lesbgk_batch_moments_many.argtypes = [vp, i32, vp, vp, vp]
             L.lesbgk_batch_step.argtypes = [vp, i64, vp]
             L.lesbgk_batch_residuals.argtypes = [vp, vp, vp, vp]
             L.lesbgk_residual.argtypes = [vp, vp, i64, vp, vp, vp]
@@ -143,7 +146,7 @@ def make_params(*, nroots=4, order=0, nx, ny, bc_y=DIFFUSE, kn, b, visc_exp=0.5,
     p.dim = dim
     p.bc_x = bc_x
     p.wall_Tx[0], p.wall_Tx[1] = wall_Tx
-    p.dx, p.dy, p.row_offset, p.reserved = dx, dy, row_offset, 0
+    p.dx, p.dy, p.row_offset, p.row_period = dx, dy, row_offset, 0
     return p
 
 
@@ -363,6 +366,37 @@ class Batch:
         _check(lib().lesbgk_batch_add(C.c_void_p(self.handle), C.byref(p), C.c_void_p(ptr), self._s, C.byref(slot)))
         self.params[slot.value] = p
         return slot.value
+
+    def add_many(self, params, h_inits=None):
+        """lesbgk_batch_add_many: admit every problem of `params` at once
+        (all or nothing); h_inits: None or a list of (4, ny, nx) arrays / None."""
+        n = len(params)
+        arr = (Params * n)(*params)
+        keep, ptrs = [], None
+        if h_inits is not None:
+            ptrs = (C.c_void_p * n)()
+            for i, h in enumerate(h_inits):
+                if h is not None:
+                    a = np.ascontiguousarray(h, dtype=np.float64)
+                    keep.append(a)
+                    ptrs[i] = a.ctypes.data
+        slots = (C.c_int32 * n)()
+        _check(lib().lesbgk_batch_add_many(C.c_void_p(self.handle), C.c_int32(n), arr,
+                                           None if ptrs is None else C.cast(ptrs, C.c_void_p), self._s,
+                                           C.cast(slots, C.c_void_p)))
+        out = list(slots)
+        for sl, p in zip(out, params):
+            self.params[sl] = p
+        return out
+
+    def moments_many(self, slots, outs) -> None:
+        """lesbgk_batch_moments_many: slot slots[i]'s moment fields into the
+        (9, ny, nx) float32 CUDA tensor outs[i], one launch for all."""
+        n = len(slots)
+        sl = (C.c_int32 * n)(*slots)
+        ptrs = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+        _check(lib().lesbgk_batch_moments_many(C.c_void_p(self.handle), C.c_int32(n), C.cast(sl, C.c_void_p),
+                                               C.cast(ptrs, C.c_void_p), self._s))
 
     def try_add(self, p: Params, h_init=None):
         """add(), or None when the pool or the slots are full."""

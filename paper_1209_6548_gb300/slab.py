@@ -192,6 +192,7 @@ class GpuSlab:
         if slab.world > 1:
             p.dx, p.dy = dx, dy
             p.row_offset = slab.y0 - slab.lo
+            p.row_period = slab.ny if slab.periodic else 0
         self.solver = L.Solver(p, h_init=None if fields is None else slab_fields(fields, slab), stream=stream)
 
     @property

@@ -78,7 +78,11 @@ REST = {"rho": 1.0, "T": 1.0}  # rest-state value of each field (0 for the other
 #   (three FMAs): 2 * 2^-24 covers them.
 #   FP16 / BF16, stochastic rounding of df/w: std <= ulp/2 <= 2^-11 (FP16) and
 #   2^-8 (BF16) times |df|, plus the same FP32 arithmetic.
-EPS_STEP = {"f32": 2.0 * 2.0 ** -24, "f16": 2.0 ** -11 + 2.0 * 2.0 ** -24,
+#   Compensated FP32 (f32c): the stored remainder makes the storage error
+#   2^-11 of half an ulp, but the increment is still formed in FP32, whose
+#   rounding is at most that of FP32 storage where the increment is as large
+#   as the value (rough data, dt/tau ~ 1): bounded as FP32.
+EPS_STEP = {"f32": 2.0 * 2.0 ** -24, "f32c": 2.0 * 2.0 ** -24, "f16": 2.0 ** -11 + 2.0 * 2.0 ** -24,
             "bf16": 2.0 ** -8 + 2.0 * 2.0 ** -24}
 
 
@@ -186,13 +190,13 @@ def rounding_bound(states, nroots: int, dim: int, steps: int, storage: str = "f3
     out = np.zeros(9)
     for k, name in enumerate(names):
         rate = relaxing.get(name, 0.0) * omega_min if np.isfinite(omega_min) else 0.0
-        if storage == "f32" and name in relaxing:  # biased: linear, damped
+        if storage in ("f32", "f32c") and name in relaxing:  # biased: linear, damped
             walk = min(n, 1.0 / rate) if rate > 0.0 else n
             per_step = walk * eps * Rmax[k]
         else:  # unbiased: random walk, damped where the field relaxes
             walk = min(n, 1.0 / (2.0 * rate)) if rate > 0.0 else n
             per_step = z * np.sqrt(max(walk, 1.0)) * eps * Rmax[k]
-        store = 0.0 if storage == "f32" else eps - 2.0 * 2.0 ** -24
+        store = 0.0 if storage in ("f32", "f32c") else eps - 2.0 * 2.0 ** -24
         out[k] = per_step + (4.0 * 2.0 ** -24 + store) * Amax[k]
     return out
 

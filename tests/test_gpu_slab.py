@@ -60,7 +60,7 @@ def test_walls_force_rough(nslabs, k, scheme):
     compare(prob, I.random_fields(prob, seed=9, amp_u=0.03, amp_T=0.03, amp_rho=0.03), nslabs, k, 13)
 
 
-@pytest.mark.parametrize("storage", [L.F16, L.BF16])
+@pytest.mark.parametrize("storage", [L.F16, L.BF16, L.F32C])
 def test_16bit_storage_rounds_by_global_row(storage):
     """Stochastic rounding is keyed by the global row (row_offset), so the
     16-bit slabs are bitwise the single domain too."""
