@@ -14,8 +14,8 @@ import bench
 
 N = 4096
 STORED = {"d2q16": 16, "d2q36": 36, "d3q64": 32, "d3q216": 108}  # values stored per node
-CASES = [("d2q16", "f32"), ("d2q16", "f16"), ("d2q16", "bf16"), ("d2q36", "f32"), ("d3q64", "f32"),
-         ("d3q216", "f32")]
+CASES = [("d2q16", "f32"), ("d2q16", "f16"), ("d2q16", "bf16"), ("d2q16", "f32c"), ("d2q36", "f32"),
+         ("d3q64", "f32"), ("d3q216", "f32")]
 
 
 @pytest.mark.parametrize("velocity_set,storage", CASES)
@@ -29,7 +29,7 @@ def test_committed_traffic_is_near_the_algorithmic_bytes(velocity_set, storage):
     lattice update; halo re-reads and data still in L2 at the end of a launch
     keep the measured traffic within a few per cent to ~15% of it."""
     traffic = bench.committed_traffic(bench.source_digest(), velocity_set, storage)
-    algorithmic = 2 * STORED[velocity_set] * (4 if storage == "f32" else 2) * N * N
+    algorithmic = 2 * STORED[velocity_set] * bench.STORE_BYTES[storage] * N * N
     assert 0.8 < traffic / algorithmic < 1.1
 
 
@@ -61,7 +61,8 @@ def test_digest_ignores_code_outside_the_step_kernels(tmp_path, monkeypatch):
     assert bench.source_digest() != d0
 
 
-INSTR_CASES = [("d2q16", "f32"), ("d2q16", "f16"), ("d2q16", "bf16"), ("d2q36", "f32"), ("d2q36", "f16"),
+INSTR_CASES = [("d2q16", "f32"), ("d2q16", "f16"), ("d2q16", "bf16"), ("d2q16", "f32c"), ("d2q36", "f32"),
+               ("d2q36", "f16"),
                ("d3q64", "f32"), ("d3q64", "f16"), ("d3q64", "bf16"), ("d3q216", "f32")]
 
 
