@@ -362,7 +362,7 @@ def measure_batch_fixed(params, nsteps, passes, warmup, stream, local, plain_sam
         return bt.add_many(params)  # one descriptor copy, one init launch
 
     admit_all()
-    rows = bt.autotune((8, 16, 32, 64, 128))
+    rows = bt.autotune((2, 4, 8, 16, 32, 64))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # larger than the 129 MB L2
 
     def one_pass():
@@ -374,13 +374,25 @@ def measure_batch_fixed(params, nsteps, passes, warmup, stream, local, plain_sam
     for _ in range(warmup):
         one_pass()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    admit_all()
-    e0.record(stream)
-    bt.step(640)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    step_ms = e0.elapsed_time(e1) / 640
+    launch = bt.launch()  # the autotuner's choice
+
+    def time_steps():
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        admit_all()
+        e0.record(stream)
+        bt.step(640)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 640
+
+    # one batch step of all instances, per launch mode (the chosen one last)
+    modes = {}
+    for name, on, k, lim in (("per_step_only", False, 64, 128), ("resident_k64_ny64", True, 64, 64),
+                             ("resident_k64_ny128", True, 64, 128), ("resident_k64_all", True, 64, 1 << 20)):
+        bt.set_resident(on, k, lim)
+        modes[name] = time_steps()
+    bt.set_resident(launch["resident"], launch["steps_per_launch"], launch["resident_max_ny"])
+    step_ms = time_steps()
     with ClockSampler(local) as clk:
         barrier()
         w0 = time.perf_counter()
@@ -405,7 +417,7 @@ def measure_batch_fixed(params, nsteps, passes, warmup, stream, local, plain_sam
     clocks = clk.summary()
     out = {"solves_per_s_this_rank": n * passes / wsec, "wall_s": wsec, "passes": passes,
            "instance_mlups_this_rank": sum(lups) * passes / wsec / 1e6,
-           "step_ms": step_ms, "rows_per_item": rows,
+           "step_ms": step_ms, "rows_per_item": rows, "launch": launch, "step_ms_by_mode": modes,
            "plain": {"solves_per_s": len(idx) / psec, "sample": f"{len(idx)} of the {n} instances, one at a time",
                      "mlups": 1.0 / plain_sec_per_lup / 1e6,
                      "est_solves_per_s_full_mix": 1.0 / (plain_sec_per_lup * sum(lups) / n)},
@@ -542,6 +554,7 @@ def run_batch(args, world, rank, local):
                    "l2": "L2 flushed between timed passes (256 MB write); within a pass the %.0f MB working "
                          "set is partly L2-resident" % (2 * 64 * cells / 1e6)},
         "instance_mlups": sum(4 * p.ny * nsteps for p in all_probs) * args.steps / wsec / 1e6,
+        "launch": fixed["launch"], "step_ms_by_mode": fixed["step_ms_by_mode"],
         "plain": fixed["plain"],
         "roofline": {"bound": "hbm", "achieved": eff, "peak": peak, "unit": "GB/s", "frac": eff / peak,
                      "traffic": None, "peak_source": peak_kind, "kernel": "k_batch_step<4,3,4>",

@@ -336,8 +336,25 @@ int lesbgk_batch_moments_many(lesbgk_batch *b, int32_t n, const int32_t *slots, 
 int lesbgk_batch_get_info(const lesbgk_batch *b, int32_t slot, lesbgk_info *out);
 /* Rows per work item (default 32); results do not depend on it. */
 int lesbgk_batch_set_rows(lesbgk_batch *b, int32_t rows, void *stream);
-/* Time one step for each candidate rows-per-item on the current slots (the
- * state is left unchanged) and keep the fastest; *chosen receives it. */
+/* Resident kernel (on by default): D2Q16 instances of at most max_ny rows
+ * (0 keeps the current limit, 128 by default) whose two population buffers
+ * fit in one block's shared memory (454 rows at nx = 4 on GB300) are each held
+ * by one block for steps_per_launch time steps (an even divisor of 64; 0
+ * keeps the current, 64 by default), reading and writing device memory once
+ * per launch, while the other instances take one launch per step; in the
+ * 64-step graphs the two run side by side.  A resident instance is one
+ * block's serial work, so tall ones are better left to the per-step kernel.
+ * Results do not depend on the choice (bitwise). */
+int lesbgk_batch_set_resident(lesbgk_batch *b, int32_t on, int32_t steps_per_launch, int32_t max_ny, void *stream);
+/* The launch configuration in use (any pointer may be NULL). */
+int lesbgk_batch_get_launch(const lesbgk_batch *b, int32_t *rows, int32_t *resident, int32_t *steps_per_launch,
+                            int32_t *resident_max_ny);
+/* Autotuner: time a 64-step chunk of the current slots for each candidate
+ * rows per work item, each with the resident kernel off, and on at 16 and 64
+ * steps per launch for instances of at most 64, 128, 256 rows or as many as
+ * fit (the state is left unchanged: every timed launch writes the spare
+ * buffers), and keep the fastest; *chosen receives its rows per item
+ * (lesbgk_batch_get_launch gives the rest). */
 int lesbgk_batch_autotune(lesbgk_batch *b, const int32_t *candidates, int32_t n, int32_t *chosen, void *stream);
 /* Largest free block and total free bytes of the pool. */
 int lesbgk_batch_pool_free(const lesbgk_batch *b, size_t *largest, size_t *total);

@@ -36,6 +36,7 @@ constexpr int kBBlock = 128;
 constexpr int kBRing = 4;
 constexpr int kNumClasses = 2;  // class 0: D2Q16 order 3, class 1: D2Q36 order 4
 constexpr int kGraphSteps = 64;
+constexpr int kBuckets = 6;  // resident instances by height: ny <= 16, 32, ..., 512 (smem permitting)
 
 // Per-instance descriptor (device memory).
 struct InstDesc {
@@ -233,6 +234,127 @@ __global__ void __launch_bounds__(kBBlock) k_batch_step(const BatchArgs B, const
     }
   }
   cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// Resident batched step (D2Q16, order 3): one block holds one whole instance
+// in shared memory -- two buffers of Q planes of ny x W values -- and takes K
+// time steps there, reading the instance from device memory once and writing
+// it once per launch.  Per step every thread updates the nodes of its row
+// (its lane's column) pass after pass, 128/W rows at a time, then one barrier
+// swaps the buffers.  Each thread rebuilds, from the five rows j-2..j+2 of its
+// column, the y-stencil state that k_batch_step carries from row to row (fc,
+// s0, s1 and the incoming row, each by the same floating-point operations) and
+// runs the same yflux2 / xflux2 / collide / wall_fix: the result is bitwise
+// that of the per-step kernel, so a solve's answer does not depend on which
+// path stepped it.  rlist: the instances, one per block; smem holds the
+// largest of them.  Reads buffer p_in, writes buffer p_out (p_in ^ (K & 1)
+// when stepping; the spare buffer when the autotuner times it).
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void __launch_bounds__(kBBlock) k_batch_resident(const BatchArgs B, const int *__restrict__ rlist,
+                                                            const int *__restrict__ rrange, int K, int p_in,
+                                                            int p_out) {
+  constexpr int NR = 4, N = 3, Q = 16, H = 2;
+  constexpr int R = kBBlock / W;  // rows per pass
+  if ((int)blockIdx.x >= rrange[1]) return;  // the bucket's count, read from device memory
+  const int inst = rlist[rrange[0] + blockIdx.x];
+  const InstDesc &D = B.desc[inst];
+  const int ny = D.ny, walls = D.walls;
+  const bool split = D.split != 0;
+  const long long cells = (long long)W * ny;
+  InstRegs P{D.c_omega, D.visc_pow, D.b, D.beta, D.dtgx, D.dtgy, D.vmode, D.has_force};
+  float ax[NR], kx[NR], ay[NR], ky[NR];
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    ax[i] = D.ax[i];
+    kx[i] = D.kx[i];
+    ay[i] = D.ay[i];
+    ky[i] = D.ky[i];
+  }
+  extern __shared__ __align__(16) float sm[];
+  float *buf[2] = {sm, sm + (size_t)Q * cells};  // [a][j][i] planes
+  // the instance into buffer 0
+  for (long long c = threadIdx.x; c < cells; c += kBBlock) {
+    float F[Q];
+    ld_node<NR, float, 1>(D.f[p_in], c, cells, F, B.lat);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) buf[0][a * cells + c] = F[a];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int lx = threadIdx.x % W;
+  const int gi = lane / W;  // group of W lanes within the warp
+  const GroupLanes nb{gi * W + ((lx + W - 1) & (W - 1)), gi * W + ((lx + 1) & (W - 1))};
+  int cur = 0;
+  for (int step = 0; step < K; ++step) {
+    const float *fi = buf[cur];
+    float *fo = buf[cur ^ 1];
+    for (int j0 = 0; j0 < ny; j0 += R) {
+      const int j = j0 + (int)threadIdx.x / W;
+      const bool live = j < ny;
+      const int jj = live ? j : ny - 1;  // a spare group computes a real row and stores nothing
+      const int rm2 = map_row(jj - 2, ny, walls), rm1 = map_row(jj - 1, ny, walls);
+      const int rp1 = map_row(jj + 1, ny, walls), rp2 = map_row(jj + 2, ny, walls);
+      auto at = [&](int a, int r) { return fi[a * cells + (long long)r * W + lx]; };
+      float fc[Q], s0[Q], s1[Q], ld[Q];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const float m2 = at(a, rm2), m1 = at(a, rm1), c0 = at(a, jj), p1 = at(a, rp1);
+        fc[a] = c0;
+        if (a % NR >= H) {  // c_y > 0: s0 = f_j - f_{j-1}, s1 = sigma_{j-1}, incoming f_{j+1}
+          s0[a] = c0 - m1;
+          s1[a] = minmod(m1 - m2, c0 - m1);
+          ld[a] = p1;
+        } else {  // c_y < 0: s0 = f_{j+1}, s1 = sigma_j, incoming f_{j+2}
+          s0[a] = p1;
+          s1[a] = minmod(c0 - m1, p1 - c0);
+          ld[a] = at(a, rp2);
+        }
+      }
+      float acc[Q];
+      float omw;
+      collide<NR, N>(fc, acc, omw, B.lat, P);
+      float xs[Q];
+      const float2 omw2 = make_float2(omw, omw);
+#pragma unroll
+      for (int a = 0; a < Q; a += 2) {
+        const int iy = a % NR;
+        const float2 nay = make_float2(-ay[iy], -ay[iy + 1]);
+        float2 f0;
+        const float2 diff = yflux2(iy >= H, a, fc, s0, s1, ld, make_float2(ky[iy], ky[iy + 1]), f0);
+        const float2 ac = fma2(omw2, f0, fma2(nay, diff, make_float2(acc[a], acc[a + 1])));
+        const float2 x2 = split ? fma2(nay, diff, f0) : f0;
+        acc[a] = ac.x;
+        acc[a + 1] = ac.y;
+        xs[a] = x2.x;
+        xs[a + 1] = x2.y;
+      }
+#pragma unroll
+      for (int a = 0; a < Q; a += 2) {
+        const int ix = a / NR;
+        const float2 nax = make_float2(-ax[ix], -ax[ix]);
+        const float2 diff = xflux2(ix >= H, make_float2(xs[a], xs[a + 1]), make_float2(kx[ix], kx[ix]), nb);
+        const float2 ac = fma2(nax, diff, make_float2(acc[a], acc[a + 1]));
+        acc[a] = ac.x;
+        acc[a + 1] = ac.y;
+      }
+      if (walls && (jj == 0 || jj == ny - 1)) wall_fix<NR, false>(acc, (jj == 0) ? 0 : 1, B.lat, D);
+      if (live) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) fo[a * cells + (long long)j * W + lx] = acc[a];
+      }
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  float *out = D.f[p_out];
+  for (long long c = threadIdx.x; c < cells; c += kBBlock) {
+    float F[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) F[a] = buf[cur][a * cells + c];
+    st_node<NR, float, 1>(out, c, cells, F, B.lat);
+  }
 }
 
 // Residual of every work item: max over its nodes of
@@ -434,7 +556,10 @@ struct lesbgk_batch {
   int capacity = 0, nx = 0, W = 0;
   InstDesc *d_desc = nullptr;
   WorkItem *d_items = nullptr;
-  int *d_range = nullptr;
+  int *d_range = nullptr;      // {first, count} per class of the items the per-step kernel takes
+  int *d_range_all = nullptr;  // {first, count} per class of all items (residuals, moments)
+  int *d_rlist = nullptr;      // resident instances, bucket after bucket
+  int *d_rrange = nullptr;     // {first, count} per bucket
   unsigned *d_res = nullptr;
   double *d_mass = nullptr;
   int *d_list = nullptr;
@@ -446,7 +571,14 @@ struct lesbgk_batch {
   std::vector<Slot> slots;
   std::vector<WorkItem> items;
   int range[kNumClasses][2] = {{0, 0}, {0, 0}};
+  int range_all[kNumClasses][2] = {{0, 0}, {0, 0}};
+  int rrange[kBuckets][2] = {};
   int max_items = 0;
+  bool resident = true;      // D2Q16 instances that fit in shared memory take the resident kernel
+  int resident_k = 64;       // time steps per resident launch (divides kGraphSteps)
+  int resident_ny = 0;       // tallest instance the resident kernel can hold (shared memory)
+  int resident_limit = 128;  // tallest instance it takes (autotuned: a tall one is one block's serial work)
+  int graph_rgrid[kBuckets] = {};
   int rows = 32;
   int par = 0;
   int sm_count = 0;
@@ -463,7 +595,7 @@ namespace {
 constexpr size_t kItemsPerSlot = 1024;  // work-list room: items per slot (rows/8 for ny <= 8192)
 
 struct Layout0 {
-  size_t desc, items, mass, range, res, partial, sums, list, outs, pool;
+  size_t desc, items, mass, range, range_all, rlist, rrange, res, partial, sums, list, outs, pool;
 };
 
 Layout0 fixed_layout(int capacity) {
@@ -477,6 +609,12 @@ Layout0 fixed_layout(int capacity) {
   o = align_up(o + sizeof(double) * (size_t)capacity * kItemsPerSlot, 256);
   L.range = o;
   o = align_up(o + sizeof(int) * 2 * kNumClasses, 256);
+  L.range_all = o;
+  o = align_up(o + sizeof(int) * 2 * kNumClasses, 256);
+  L.rlist = o;
+  o = align_up(o + sizeof(int) * (size_t)capacity, 256);
+  L.rrange = o;
+  o = align_up(o + sizeof(int) * 2 * kBuckets, 256);
   L.res = o;
   o = align_up(o + sizeof(unsigned) * (size_t)capacity, 256);
   L.partial = o;
@@ -525,6 +663,51 @@ BatchArgs make_args(const lesbgk_batch *b, int cls) {
   return a;
 }
 
+// The same over every item of the class, resident instances included
+// (residuals, moments).
+BatchArgs make_args_all(const lesbgk_batch *b, int cls) {
+  BatchArgs a = make_args(b, cls);
+  a.range = b->d_range_all + 2 * cls;
+  return a;
+}
+
+void *resident_fn(int W) {
+  switch (W) {
+    case 1: return (void *)k_batch_resident<1>;
+    case 2: return (void *)k_batch_resident<2>;
+    case 4: return (void *)k_batch_resident<4>;
+    case 8: return (void *)k_batch_resident<8>;
+    case 16: return (void *)k_batch_resident<16>;
+    default: return (void *)k_batch_resident<32>;
+  }
+}
+
+// Rows of bucket k: instances with ny in (bucket_ny(k-1), bucket_ny(k)].
+int bucket_ny(const lesbgk_batch *b, int k) { return std::min(16 << k, b->resident_ny); }
+
+size_t resident_smem(const lesbgk_batch *b, int k) {
+  return (size_t)2 * 16 * b->nx * bucket_ny(b, k) * sizeof(float);  // two buffers of Q planes
+}
+
+bool is_resident(const lesbgk_batch *b, const lesbgk_batch::Slot &sl) {
+  return b->resident && sl.cls == 0 && sl.p.ny <= std::min(b->resident_ny, b->resident_limit);
+}
+
+// K steps of every resident instance: one launch per non-empty bucket.
+cudaError_t launch_resident(lesbgk_batch *b, int K, int p_in, int p_out, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  BatchArgs a = make_args(b, 0);
+  for (int k = 0; k < kBuckets && e == cudaSuccess; ++k) {
+    const int n = b->rrange[k][1];
+    if (!n) continue;
+    const int *rr = b->d_rrange + 2 * k;
+    const int *rl = b->d_rlist;
+    void *args[] = {&a, &rl, &rr, &K, &p_in, &p_out};
+    e = cudaLaunchKernel(resident_fn(b->W), dim3(n), dim3(kBBlock), args, resident_smem(b, k), s);
+  }
+  return e;
+}
+
 unsigned step_grid(const lesbgk_batch *b, int n_items) {
   const int gpw = 32 / b->W;
   const long long warps = (n_items + gpw - 1) / gpw;
@@ -538,35 +721,57 @@ cudaError_t launch_one_step(lesbgk_batch *b, int cls, int par, unsigned grid, cu
   return cudaLaunchKernel(step_kernel(cls, b->W), dim3(grid), dim3(kBBlock), args, step_smem(cls), s);
 }
 
-// Rebuild the host work list (items sorted by class, then by length) and copy
-// it with the class ranges to the device.
+// Rebuild the host work list and copy it with the class ranges to the device:
+// per class, the items of the instances the per-step kernel takes (sorted by
+// length), then those of the resident instances (whose items only the
+// residual and moment kernels visit); and the resident instances by bucket.
 int rebuild_items(lesbgk_batch *b, cudaStream_t s) {
   b->items.clear();
   for (int cls = 0; cls < kNumClasses; ++cls) {
     const int first = (int)b->items.size();
-    std::vector<WorkItem> mine;
+    std::vector<WorkItem> mine, res;
     for (int i = 0; i < b->capacity; ++i) {
       const auto &sl = b->slots[i];
       if (!sl.used || sl.cls != cls) continue;
-      for (int y0 = 0; y0 < sl.p.ny; y0 += b->rows) mine.push_back({i, y0, std::min(b->rows, sl.p.ny - y0), 0});
+      auto &dst = is_resident(b, sl) ? res : mine;
+      for (int y0 = 0; y0 < sl.p.ny; y0 += b->rows) dst.push_back({i, y0, std::min(b->rows, sl.p.ny - y0), 0});
     }
     std::stable_sort(mine.begin(), mine.end(), [](const WorkItem &x, const WorkItem &y) { return x.rows > y.rows; });
     b->items.insert(b->items.end(), mine.begin(), mine.end());
+    b->items.insert(b->items.end(), res.begin(), res.end());
     b->range[cls][0] = first;
     b->range[cls][1] = (int)mine.size();
+    b->range_all[cls][0] = first;
+    b->range_all[cls][1] = (int)(mine.size() + res.size());
   }
   if ((long long)b->items.size() > (long long)b->capacity * (long long)kItemsPerSlot)
     return fail(LESBGK_ESPACE, "work list of %zu items exceeds its room", b->items.size());
+  std::vector<int> rlist;
+  for (int k = 0; k < kBuckets; ++k) {
+    b->rrange[k][0] = (int)rlist.size();
+    for (int i = 0; i < b->capacity; ++i) {
+      const auto &sl = b->slots[i];
+      if (sl.used && is_resident(b, sl) && sl.p.ny <= bucket_ny(b, k) && (k == 0 || sl.p.ny > bucket_ny(b, k - 1)))
+        rlist.push_back(i);
+    }
+    b->rrange[k][1] = (int)rlist.size() - b->rrange[k][0];
+  }
   cudaError_t e = cudaSuccess;
   if (!b->items.empty())
     e = cudaMemcpyAsync(b->d_items, b->items.data(), sizeof(WorkItem) * b->items.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_range, b->range, sizeof(b->range), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_range_all, b->range_all, sizeof(b->range_all), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !rlist.empty())
+    e = cudaMemcpyAsync(b->d_rlist, rlist.data(), sizeof(int) * rlist.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_rrange, b->rrange, sizeof(b->rrange), cudaMemcpyHostToDevice, s);
   // (pageable sources: the copies are staged before cudaMemcpyAsync returns,
   // so the host vectors may change afterwards)
   if (e != cudaSuccess) return cuda_fail(e, "work list upload");
   b->items_dirty = false;
   for (int cls = 0; cls < kNumClasses; ++cls)
     if ((int)step_grid(b, b->range[cls][1]) > b->graph_grid[cls]) b->graph_dirty = true;
+  for (int k = 0; k < kBuckets; ++k)
+    if (b->rrange[k][1] > b->graph_rgrid[k]) b->graph_dirty = true;
   return 0;
 }
 
@@ -611,6 +816,31 @@ int build_graph(lesbgk_batch *b) {
       cur.push_back(node);
     }
     if (!cur.empty()) prev = cur;
+  }
+  // resident instances: per bucket a chain of kGraphSteps / resident_k launches,
+  // each taking resident_k steps in place (an even count: parity 0 to 0),
+  // independent of the per-step chain (they touch other instances)
+  BatchArgs a0 = make_args(b, 0);
+  const int *rl = b->d_rlist;
+  int K = b->resident_k, p0 = 0;
+  for (int k = 0; k < kBuckets && e == cudaSuccess; ++k) {
+    const int n = b->rrange[k][1];
+    b->graph_rgrid[k] = n ? n + n / 4 + 8 : 0;
+    if (!n) continue;
+    const int *rr = b->d_rrange + 2 * k;
+    cudaGraphNode_t last = nullptr;
+    for (int c = 0; c < kGraphSteps / K && e == cudaSuccess; ++c) {
+      cudaKernelNodeParams kp{};
+      void *kargs[] = {&a0, &rl, &rr, &K, &p0, &p0};
+      kp.func = resident_fn(b->W);
+      kp.gridDim = dim3(b->graph_rgrid[k]);
+      kp.blockDim = dim3(kBBlock);
+      kp.sharedMemBytes = (unsigned)resident_smem(b, k);
+      kp.kernelParams = kargs;
+      cudaGraphNode_t node;
+      e = cudaGraphAddKernelNode(&node, g, last ? &last : nullptr, last ? 1 : 0, &kp);
+      last = node;
+    }
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
   cudaGraphDestroy(g);
@@ -658,6 +888,9 @@ extern "C" int lesbgk_batch_create(int32_t capacity, int32_t nx, void *d_workspa
   b->d_desc = reinterpret_cast<InstDesc *>(b->ws + L.desc);
   b->d_items = reinterpret_cast<WorkItem *>(b->ws + L.items);
   b->d_range = reinterpret_cast<int *>(b->ws + L.range);
+  b->d_range_all = reinterpret_cast<int *>(b->ws + L.range_all);
+  b->d_rlist = reinterpret_cast<int *>(b->ws + L.rlist);
+  b->d_rrange = reinterpret_cast<int *>(b->ws + L.rrange);
   b->d_res = reinterpret_cast<unsigned *>(b->ws + L.res);
   b->d_mass = reinterpret_cast<double *>(b->ws + L.mass);
   b->d_list = reinterpret_cast<int *>(b->ws + L.list);
@@ -678,8 +911,17 @@ extern "C" int lesbgk_batch_create(int32_t capacity, int32_t nx, void *d_workspa
       e = cudaFuncSetAttribute(step_fn<6, 4>(w), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)batch_smem_bytes<6>());
   }
+  // the resident kernel: as tall an instance as two buffers of Q planes fit in
+  // the opt-in shared memory of a block
+  int optin = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  b->resident_ny = std::min(16 << (kBuckets - 1), optin / (2 * 16 * nx * (int)sizeof(float)));
+  for (int w : {1, 2, 4, 8, 16, 32})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(resident_fn(w), cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_range, 0, sizeof(int) * 2 * kNumClasses, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_range_all, 0, sizeof(int) * 2 * kNumClasses, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_rrange, 0, sizeof(int) * 2 * kBuckets, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     delete b;
@@ -911,6 +1153,7 @@ extern "C" int lesbgk_batch_step(lesbgk_batch *b, int64_t nsteps, void *stream) 
   auto direct_step = [&]() {
     for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls)
       if (b->range[cls][1]) e = launch_one_step(b, cls, b->par, step_grid(b, b->range[cls][1]), s);
+    if (e == cudaSuccess) e = launch_resident(b, 1, b->par, b->par ^ 1, s);
     if (e == cudaSuccess) {
       b->par ^= 1;  // the slots' current buffers are desc.f[par]
       for (auto &sl : b->slots)
@@ -942,9 +1185,9 @@ extern "C" int lesbgk_batch_residuals(lesbgk_batch *b, double *h_res, double *h_
   if (int rc = ensure_items(b, s)) return rc;
   cudaError_t e = cudaMemsetAsync(b->d_res, 0, sizeof(unsigned) * b->capacity, s);
   for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls) {
-    const int n = b->range[cls][1];
+    const int n = b->range_all[cls][1];
     if (!n) continue;
-    BatchArgs a = make_args(b, cls);
+    BatchArgs a = make_args_all(b, cls);
     if (cls == 0) k_batch_residual<4><<<n, kBBlock, 0, s>>>(a, b->par, b->d_res, b->d_mass);
     else k_batch_residual<6><<<n, kBBlock, 0, s>>>(a, b->par, b->d_res, b->d_mass);
     e = cudaGetLastError();
@@ -1004,9 +1247,9 @@ extern "C" int lesbgk_batch_moments_many(lesbgk_batch *b, int32_t n, const int32
   if (int rc = ensure_items(b, s)) return rc;
   cudaError_t e = cudaMemcpyAsync(b->d_outs, outs.data(), sizeof(float *) * outs.size(), cudaMemcpyHostToDevice, s);
   for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls) {
-    const int m = b->range[cls][1];
+    const int m = b->range_all[cls][1];
     if (!m) continue;
-    BatchArgs a = make_args(b, cls);
+    BatchArgs a = make_args_all(b, cls);
     if (cls == 0) k_batch_moments<4><<<m, kBBlock, 0, s>>>(a, b->par, b->d_outs);
     else k_batch_moments<6><<<m, kBBlock, 0, s>>>(a, b->par, b->d_outs);
     e = cudaGetLastError();
@@ -1051,43 +1294,95 @@ extern "C" int lesbgk_batch_set_rows(lesbgk_batch *b, int32_t rows, void *stream
   return rebuild_items(b, static_cast<cudaStream_t>(stream));
 }
 
+extern "C" int lesbgk_batch_set_resident(lesbgk_batch *b, int32_t on, int32_t steps_per_launch, int32_t max_ny,
+                                         void *stream) {
+  if (!b) return fail(LESBGK_EINVAL, "batch is NULL");
+  if (max_ny < 0) return fail(LESBGK_EINVAL, "max_ny must be >= 0");
+  if (max_ny) b->resident_limit = max_ny;
+  if (steps_per_launch && (steps_per_launch < 2 || steps_per_launch > kGraphSteps || (steps_per_launch & 1) ||
+                           kGraphSteps % steps_per_launch))
+    return fail(LESBGK_EINVAL, "steps per resident launch must be an even divisor of %d", kGraphSteps);
+  b->resident = on != 0;
+  if (steps_per_launch) b->resident_k = steps_per_launch;
+  drop_graph(b);
+  return rebuild_items(b, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int lesbgk_batch_get_launch(const lesbgk_batch *b, int32_t *rows, int32_t *resident,
+                                       int32_t *steps_per_launch, int32_t *resident_max_ny) {
+  if (!b) return fail(LESBGK_EINVAL, "batch is NULL");
+  if (rows) *rows = b->rows;
+  if (resident) *resident = b->resident ? 1 : 0;
+  if (steps_per_launch) *steps_per_launch = b->resident_k;
+  if (resident_max_ny) *resident_max_ny = std::min(b->resident_ny, b->resident_limit);
+  return 0;
+}
+
 extern "C" int lesbgk_batch_autotune(lesbgk_batch *b, const int32_t *candidates, int32_t n, int32_t *chosen,
                                      void *stream) {
   if (!b || !candidates || n < 1) return fail(LESBGK_EINVAL, "bad autotune arguments");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaEvent_t t0, t1;
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t t0, t1, fork, join;
   cudaError_t e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
-  if (e != cudaSuccess) return cuda_fail(e, "autotune events");
-  int best = b->rows;
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune set-up");
+  // candidates: rows per work item x {per-step kernel for all, resident
+  // kernel with 16 or 64 steps per launch}; each timed as a 64-step chunk,
+  // the resident launches on a second stream beside the per-step chain (as in
+  // the graph), every launch reading the current buffers and writing the
+  // spare ones, so the state is left untouched
+  struct Cand { int rows, res, k, limit; };
+  std::vector<Cand> cands;
+  for (int c = 0; c < n; ++c) {
+    cands.push_back({candidates[c], 0, b->resident_k, b->resident_limit});
+    for (int lim : {64, 128, 256, 1 << 30})
+      for (int k : {16, 64}) cands.push_back({candidates[c], 1, k, lim});
+  }
+  Cand best{b->rows, b->resident ? 1 : 0, b->resident_k, b->resident_limit};
   float best_ms = 1e30f;
-  for (int c = 0; c < n && e == cudaSuccess; ++c) {
-    if (int rc = lesbgk_batch_set_rows(b, candidates[c], stream)) {
-      cudaEventDestroy(t0);
-      cudaEventDestroy(t1);
-      return rc;
-    }
-    // launches from the current buffers into the spare ones without flipping
-    // the parity: the state is left untouched
-    for (int rep = 0; rep < 13 && e == cudaSuccess; ++rep) {
-      if (rep == 3) e = cudaEventRecord(t0, s);
-      for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls)
-        if (b->range[cls][1]) e = launch_one_step(b, cls, b->par, step_grid(b, b->range[cls][1]), s);
-    }
-    if (e == cudaSuccess) e = cudaEventRecord(t1, s);
-    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+  int rc = 0;
+  for (const Cand &cd : cands) {
+    b->resident = cd.res != 0;
+    b->resident_k = cd.k;
+    b->resident_limit = cd.limit;
+    if ((rc = lesbgk_batch_set_rows(b, cd.rows, stream))) break;
     float ms = 0;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
-    if (e == cudaSuccess && ms < best_ms) {
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+      e = cudaEventRecord(t0, s);
+      if (e == cudaSuccess) e = cudaEventRecord(fork, s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, fork, 0);
+      for (int c = 0; c < kGraphSteps / cd.k && e == cudaSuccess; ++c) e = launch_resident(b, cd.k, b->par, b->par ^ 1, s2);
+      if (e == cudaSuccess) e = cudaEventRecord(join, s2);
+      for (int st = 0; st < kGraphSteps && e == cudaSuccess; ++st)
+        for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls)
+          if (b->range[cls][1]) e = launch_one_step(b, cls, b->par, step_grid(b, b->range[cls][1]), s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join, 0);
+      if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    }
+    if (e != cudaSuccess) break;
+    if (ms < best_ms) {
       best_ms = ms;
-      best = candidates[c];
+      best = cd;
     }
   }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
+  cudaEventDestroy(fork);
+  cudaEventDestroy(join);
+  cudaStreamDestroy(s2);
+  if (rc) return rc;
   if (e != cudaSuccess) return cuda_fail(e, "autotune");
-  if (chosen) *chosen = best;
-  return lesbgk_batch_set_rows(b, best, stream);
+  b->resident = best.res != 0;
+  b->resident_k = best.k;
+  b->resident_limit = best.limit;
+  if (chosen) *chosen = best.rows;
+  return lesbgk_batch_set_rows(b, best.rows, stream);
 }
 
 extern "C" int lesbgk_batch_pool_free(const lesbgk_batch *b, size_t *largest, size_t *total) {

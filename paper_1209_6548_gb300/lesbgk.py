@@ -35,7 +35,7 @@ SYMBOLS = ("lesbgk_workspace_size", "lesbgk_create", "lesbgk_reinit", "lesbgk_st
            "lesbgk_batch_remove", "lesbgk_batch_step", "lesbgk_batch_residuals", "lesbgk_batch_moments",
            "lesbgk_batch_get_populations", "lesbgk_batch_get_info", "lesbgk_batch_set_rows",
            "lesbgk_batch_autotune", "lesbgk_batch_pool_free", "lesbgk_batch_destroy", "lesbgk_batch_add_many",
-           "lesbgk_batch_moments_many")
+           "lesbgk_batch_moments_many", "lesbgk_batch_set_resident", "lesbgk_batch_get_launch")
 
 
 class Params(C.Structure):
@@ -105,6 +105,8 @@ def lib():
             L.lesbgk_batch_remove.argtypes = [vp, i32, vp]
             L.lesbgk_batch_add_many.argtypes = [vp, i32, C.POINTER(Params), vp, vp, vp]
             L.lesbgk_batch_moments_many.argtypes = [vp, i32, vp, vp, vp]
+            L.lesbgk_batch_set_resident.argtypes = [vp, i32, i32, i32, vp]
+            L.lesbgk_batch_get_launch.argtypes = [vp, vp, vp, vp, vp]
             L.lesbgk_batch_step.argtypes = [vp, i64, vp]
             L.lesbgk_batch_residuals.argtypes = [vp, vp, vp, vp]
             L.lesbgk_residual.argtypes = [vp, vp, i64, vp, vp, vp]
@@ -452,6 +454,18 @@ class Batch:
         _check(lib().lesbgk_batch_autotune(C.c_void_p(self.handle), arr, C.c_int32(len(candidates)),
                                            C.byref(chosen), self._s))
         return chosen.value
+
+    def set_resident(self, on: bool, steps_per_launch: int = 0, max_ny: int = 0) -> None:
+        _check(lib().lesbgk_batch_set_resident(C.c_void_p(self.handle), C.c_int32(1 if on else 0),
+                                               C.c_int32(steps_per_launch), C.c_int32(max_ny), self._s))
+
+    def launch(self) -> dict:
+        """rows per item, resident on/off, steps per resident launch, tallest instance the
+        resident kernel takes."""
+        v = [C.c_int32() for _ in range(4)]
+        _check(lib().lesbgk_batch_get_launch(C.c_void_p(self.handle), *[C.byref(x) for x in v]))
+        return {"rows_per_item": v[0].value, "resident": bool(v[1].value), "steps_per_launch": v[2].value,
+                "resident_max_ny": v[3].value}
 
     def pool_free(self):
         a, t = C.c_size_t(), C.c_size_t()

@@ -194,3 +194,47 @@ def test_add_many_is_all_or_nothing():
     assert e.value.code == L.ESPACE
     assert bt.pool_free() == free0 and not bt.params  # nothing kept
     assert len(bt.add_many(params[:3])) == 3
+
+
+@pytest.mark.parametrize("k", [2, 16, 64])
+def test_resident_kernel_is_bitwise_the_per_step_kernel(k):
+    """Instances held in shared memory for k steps per launch give bitwise
+    the populations of the per-step kernel, in a mix that straddles the
+    shared-memory limit (some instances stay on the per-step path), through
+    graph replays and single steps (an odd total: both buffer parities),
+    with walls, force and both schemes."""
+    from dataclasses import replace
+    probs = I.batch_mix(n=16, seed=7, ny_lo=16, ny_hi=700)
+    probs = [replace(p, scheme=I.SPLIT) if i % 2 else p for i, p in enumerate(probs)]
+    params = [L.params_from_problem(p) for p in probs]
+    pool = sum(L.batch_slot_bytes(p) for p in params) + (1 << 20)
+    out = {}
+    for on in (False, True):
+        bt = L.Batch(capacity=len(params), nx=4, pool_bytes=pool)
+        bt.set_resident(on, k, 1 << 20)  # every instance that fits
+        slots = bt.add_many(params)
+        bt.step(64 * 2 + 7)
+        cfg = bt.launch()
+        if on:
+            assert cfg["resident"] and cfg["steps_per_launch"] == k and cfg["resident_max_ny"] >= 400
+            assert any(p.ny <= cfg["resident_max_ny"] for p in probs) and any(p.ny > cfg["resident_max_ny"]
+                                                                              for p in probs)
+        out[on] = [bt.populations(s).cpu().numpy() for s in slots]
+        bt.close()
+    for a, b in zip(out[False], out[True]):
+        assert np.array_equal(a, b)
+
+
+def test_autotune_searches_rows_and_resident_modes():
+    probs = I.batch_mix(n=32, seed=8, ny_hi=512)
+    params = [L.params_from_problem(p) for p in probs]
+    bt = L.Batch(capacity=len(params), nx=4, pool_bytes=sum(L.batch_slot_bytes(p) for p in params) + (1 << 20))
+    slots = bt.add_many(params)
+    bt.step(10)
+    before = [bt.populations(s).cpu().numpy() for s in slots]
+    rows = bt.autotune((8, 16, 32))
+    cfg = bt.launch()
+    assert cfg["rows_per_item"] == rows and rows in (8, 16, 32) and cfg["steps_per_launch"] in (16, 64)
+    assert cfg["resident_max_ny"] in (64, 128, 256, 454) or not cfg["resident"]
+    after = [bt.populations(s).cpu().numpy() for s in slots]
+    assert all(np.array_equal(a, b) for a, b in zip(before, after))  # timing left the state alone
