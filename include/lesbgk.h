@@ -117,7 +117,7 @@ typedef struct lesbgk_params {
   double wall_T_freq;   /* (St in the units of Sec. 2.2); amp 0 = steady walls.  The wall
                            tables are rebuilt in FP64 on the host for each step's time.
                            Specular fractions need FP32 storage; heating takes any storage.
-                           The batched solver takes steady, fully diffuse walls only. */
+                           The batched solver takes steady walls (diffuse or Maxwell). */
   int32_t dim;          /* dimension D of the velocity set: 0 or 2 = the 2D sets above;
                            3 = D3Q64 (nroots 4, order 3; any storage) or D3Q216 (nroots 6,
                            order 4, the paper's 11th-order set; FP32), on the same 2D grid: the

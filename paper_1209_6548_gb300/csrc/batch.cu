@@ -44,7 +44,7 @@ struct InstDesc {
   float *snap;  // residual snapshot: rho, ux, uy, T per node
   int nx, ny, walls, split;
   int vmode, has_force, pad0, pad1;
-  float c_omega, visc_pow, b, beta, dtgx, dtgy, dt, pad2;
+  float c_omega, visc_pow, b, beta, dtgx, dtgy, dt, wspec;  // wspec: Maxwell walls' specular share
   float ax[kMaxR], kx[kMaxR], ay[kMaxR], ky[kMaxR];
   float wS[2][kMaxQ], wSdev[2][kMaxQ], wA[2], wB[2];
 };
@@ -226,7 +226,10 @@ __global__ void __launch_bounds__(kBBlock) k_batch_step(const BatchArgs B, const
         acc[a] = fmaf(-ax[ix], xflux(ix >= H, xs[a], kx[ix], nb), acc[a]);
       }
     }
-    if (walls && (j == 0 || j == ny - 1)) wall_fix<NR, false>(acc, (j == 0) ? 0 : 1, B.lat, D);
+    if (walls && (j == 0 || j == ny - 1)) {
+      if (D.wspec != 0.0f) wall_fix<NR, true>(acc, (j == 0) ? 0 : 1, B.lat, D);
+      else wall_fix<NR, false>(acc, (j == 0) ? 0 : 1, B.lat, D);
+    }
     if (k < rows) {
       float *o = fout + (long long)j * rstride + (long long)lx * V;
 #pragma unroll
@@ -339,7 +342,10 @@ __global__ void __launch_bounds__(kBBlock) k_batch_resident(const BatchArgs B, c
         acc[a] = ac.x;
         acc[a + 1] = ac.y;
       }
-      if (walls && (jj == 0 || jj == ny - 1)) wall_fix<NR, false>(acc, (jj == 0) ? 0 : 1, B.lat, D);
+      if (walls && (jj == 0 || jj == ny - 1)) {
+        if (D.wspec != 0.0f) wall_fix<NR, true>(acc, (jj == 0) ? 0 : 1, B.lat, D);
+        else wall_fix<NR, false>(acc, (jj == 0) ? 0 : 1, B.lat, D);
+      }
       if (live) {
 #pragma unroll
         for (int a = 0; a < Q; ++a) fo[a * cells + (long long)j * W + lx] = acc[a];
@@ -450,7 +456,10 @@ __global__ void __launch_bounds__(kBBlock) k_batch_init(const BatchArgs B, const
     float Sv[NR * NR];
     hermite_evaluate<NR, N>(e, Sv, B.lat);
     const int j = (int)(c / nx);
-    if (D.walls && (j == 0 || j == ny - 1)) wall_fix<NR, false>(Sv, j == 0 ? 0 : 1, B.lat, D);
+    if (D.walls && (j == 0 || j == ny - 1)) {
+      if (D.wspec != 0.0f) wall_fix<NR, true>(Sv, j == 0 ? 0 : 1, B.lat, D);
+      else wall_fix<NR, false>(Sv, j == 0 ? 0 : 1, B.lat, D);
+    }
     st_node<NR, float, 1>(f, c, cells, Sv, B.lat);
   }
 }
@@ -942,8 +951,7 @@ int prepare_slot(lesbgk_batch *b, const lesbgk_params *p, const double *h_init, 
   if (cls < 0) return fail(LESBGK_EINVAL, "batched instances take D2Q16 (order 3) or D2Q36 (order 4)");
   if (p->nx != b->nx) return fail(LESBGK_EINVAL, "instance nx %d differs from the batch's %d", p->nx, b->nx);
   if (p->storage != LESBGK_F32) return fail(LESBGK_EINVAL, "batched instances store FP32 populations");
-  if (p->wall_specular != 0.0 || p->wall_T_amp != 0.0)
-    return fail(LESBGK_EINVAL, "batched instances take steady, fully diffuse walls");
+  if (p->wall_T_amp != 0.0) return fail(LESBGK_EINVAL, "batched instances take steady walls");
   if (p->dim == 3) return fail(LESBGK_EINVAL, "batched instances take the 2D velocity sets");
   if (p->bc_x != LESBGK_PERIODIC) return fail(LESBGK_EINVAL, "batched instances are periodic in x");
   if ((long long)(p->ny + b->rows - 1) / b->rows > (long long)kItemsPerSlot)
@@ -1000,6 +1008,7 @@ int prepare_slot(lesbgk_batch *b, const lesbgk_params *p, const double *h_init, 
   D.dtgx = A.dtgx;
   D.dtgy = A.dtgy;
   D.dt = (float)su.dt;
+  D.wspec = A.wspec;
   std::memcpy(D.ax, A.ax, sizeof D.ax);
   std::memcpy(D.kx, A.kx, sizeof D.kx);
   std::memcpy(D.ay, A.ay, sizeof D.ay);

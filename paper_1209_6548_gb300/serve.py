@@ -33,7 +33,7 @@ time since the previous check) and m the solve's total mass at each check:
   - max_steps: the cap.
 
 Solves that the batch cannot hold (another width, walls in x such as the
-lid-driven cavities of the mix, the D = 3 set, Maxwell or heated walls) go
+lid-driven cavities of the mix, the D = 3 set, heated walls) go
 to a wide lane: each runs as a single-domain solver on its own CUDA stream,
 so they advance concurrently with the batch; the lane admits them in arrival
 order while its own device-memory budget has room, and checks them with the
@@ -147,7 +147,7 @@ def fits_batch(prob, nx: int) -> bool:
     """Whether the batched solver takes this problem (the library's own
     admission checks say the same)."""
     return (prob.nx == nx and getattr(prob, "bc_x", I.PERIODIC) == I.PERIODIC and getattr(prob, "dim", 2) == 2
-            and prob.wall_specular == 0.0 and prob.wall_T_amp == 0.0)
+            and prob.wall_T_amp == 0.0)
 
 
 class WideLane:

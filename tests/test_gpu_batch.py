@@ -25,12 +25,16 @@ def _built():
 
 
 def mixed_problems(nx=4, n=10, seed=3, with_q36=True):
+    """The channel mix, a quarter on D2Q36 and every third with Maxwell walls
+    (specular share 0.3, Sec. 3.2)."""
     probs = I.batch_mix(n=n, seed=seed, ny_lo=16, ny_hi=200)
     out = []
     for k, p in enumerate(probs):
         kw = dict(nx=nx)
         if with_q36 and k % 4 == 3:
             kw["nroots"] = 6
+        if k % 3 == 1:
+            kw["wall_specular"] = 0.3
         from dataclasses import replace
         out.append(replace(p, **kw))
     return out
