@@ -66,7 +66,7 @@ def parse():
                     help="requests of the default line's serving object")
     ap.add_argument("--serve-plain-budget", type=float, default=20.0,
                     help="seconds the default line's FIFO serving baseline may run")
-    ap.add_argument("--workload", choices=["tgv", "batch", "serve", "precision"], default="tgv",
+    ap.add_argument("--workload", choices=["tgv", "batch", "serve", "precision", "slab"], default="tgv",
                     help="tgv: 4096^2 Taylor-Green throughput (default); batch: 512-instance channel mix; "
                          "serve: Poisson arrivals run to steady state with continuous batching")
     ap.add_argument("--velocity-set", choices=["d2q16", "d2q36", "d3q64", "d3q216"], default="d2q16",
@@ -624,7 +624,15 @@ def run_slab(args, world, rank, local):
     from paper_1209_6548_gb300 import slab as SL
 
     torch.cuda.set_device(local)
-    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if "MASTER_ADDR" in os.environ:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:  # one process without torchrun: a group of one
+        import socket
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1,
+                                device_id=torch.device("cuda", local))
     B.build()
     n, nsteps, k = args.n, args.lattice_steps, args.halo_steps
     nroots, dim, order, q = LATTICES[args.velocity_set]
@@ -685,6 +693,58 @@ def run_slab(args, world, rank, local):
     step_ms = sum(a.elapsed_time(b) for a, b in evs) / (args.steps * nsteps)
     clocks = clk.summary()
     lups = n * n * nsteps * args.steps
+
+    # end to end through the C ABI with host buffers: each rank creates its
+    # slab's solver from pinned host fields (lesbgk_create) and reads its own
+    # rows' moments back to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        h_fields = torch.from_numpy(SL.slab_fields(fields, slab)).pin_memory()
+        h_out = torch.empty((9, slab.rows, n), dtype=torch.float32).pin_memory()
+        params = st.solver.params
+        ws, nbytes = st.solver.workspace, st.solver.nbytes
+        st.solver.close()
+
+        class _Handle:  # the store the exchange drives, around a raw handle
+            def __init__(self, h):
+                self.solver = type("S", (), {"handle": h, "stream": stream})()
+
+        def e2e_solve():
+            h = L.create(params, ws.data_ptr(), nbytes, h_fields.numpy(), stream.cuda_stream)
+            hs = _Handle(h)
+            store = SL.GpuSlab.__new__(SL.GpuSlab)
+            store._torch, store._L, store.slab, store.solver = torch, L, slab, hs.solver
+            SL.exchange_dist(store, slab, dist)
+            done = 0
+            while done < nsteps:
+                m = min(k, nsteps - done)
+                L.step(h, m, stream.cuda_stream)
+                done += m
+                if m == k and done < nsteps:
+                    SL.exchange_dist(store, slab, dist)
+            hsum = np.zeros(4)
+            L._check(L.lib().lesbgk_moments_rows(L.C.c_void_p(h), slab.lo, slab.rows, L.C.c_void_p(mom.data_ptr()),
+                                                L.C.c_void_p(hsum.ctypes.data), L.C.c_void_p(stream.cuda_stream)))
+            h_out.copy_(mom, non_blocking=True)
+            tot = torch.tensor(hsum, dtype=torch.float64, device="cuda")
+            dist.all_reduce(tot)
+            torch.cuda.synchronize()
+            L.destroy(h)
+
+        for _ in range(2):
+            e2e_solve()
+        torch.cuda.synchronize()
+        dist.barrier()
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_solve()
+        torch.cuda.synchronize()
+        dist.barrier()
+        t = torch.tensor([time.perf_counter() - w0], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = {"value": lups / float(t.item()) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(h_fields.numel() * 8) * world,
+               "d2h_bytes_per_step": int(h_out.numel() * 4 + 4 * 8) * world}
     if rank == 0:
         line = {
             "metric": METRIC, "value": lups / wall / 1e6, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -693,17 +753,19 @@ def run_slab(args, world, rank, local):
             "config": {"workload": tgv_workload_name(n, args), "nx": n, "ny": n,
                        "velocity_set": args.velocity_set.upper(), "storage": args.storage, "order": order,
                        "lattice_steps_per_step": nsteps, "scheme": "split",
-                       "parallelism": f"y-slabs x{world}: {slab.rows} or so rows per rank, halo {2 * k} rows "
-                                      f"exchanged over NCCL every {k} steps",
+                       "parallelism": (f"y-slabs x{world}: {slab.rows} or so rows per rank, halo {2 * k} rows "
+                                       f"exchanged over NCCL every {k} steps") if world > 1 else
+                                      "one slab: the whole domain, no exchange",
                        "l2": "inputs larger than L2"},
             "slab_ms_per_lattice_step_rank0": step_ms,
             "totals": tot.cpu().numpy().tolist(),
-            "e2e": None,
+            "e2e": e2e,
             "gpu_launches": (1 + nsteps + 2) * args.steps,
             "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
         }
         print(json.dumps(line), flush=True)
-    st.close()
+    if args.no_e2e:
+        st.close()
     dist.destroy_process_group()
     return 0
 
@@ -768,7 +830,7 @@ def run_precision(args, world, rank, local):
         if args.save_moments:
             os.makedirs(args.save_moments, exist_ok=True)
             np.savez(os.path.join(args.save_moments, f"gpu_moments_tgv{args.tgv_n}.npz"),
-                     **{f"{c}|{st}": v for (c, st), v in gpu.items()})
+                     **{f"{c}|{st}": v.astype(np.float32) for (c, st), v in gpu.items()})  # the GPU's own FP32
         # throughput of each storage on the 4096^2 case
         n = 4096
         prob = I.tgv(n)
@@ -797,7 +859,7 @@ def run_precision(args, world, rank, local):
             return 0
     else:
         z = np.load(os.path.join(args.compare_moments, f"gpu_moments_tgv{args.tgv_n}.npz"))
-        gpu = {tuple(key.split("|")): z[key] for key in z.files}
+        gpu = {tuple(key.split("|")): z[key].astype(np.float64) for key in z.files}
 
     O.set_threads(len(os.sched_getaffinity(0)))
     out = {}
@@ -849,7 +911,7 @@ def main():
         return run_serve(args, world, rank, local)
     if args.workload == "precision":
         return run_precision(args, world, rank, local)
-    if world > 1 and args.decomp == "slab":
+    if args.workload == "slab" or (world > 1 and args.decomp == "slab"):
         return run_slab(args, world, rank, local)
 
     import numpy as np

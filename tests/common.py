@@ -201,6 +201,19 @@ def rounding_bound(states, nroots: int, dim: int, steps: int, storage: str = "f3
     return out
 
 
+def population_bound(states, nroots: int, dim: int, steps: int, storage: str = "f32", prob=None,
+                     dt: float = 0.0) -> float:
+    """Bound (absolute) on a stored value's accumulated rounding after
+    `steps` steps: each step rounds it once by at most eps |df| (EPS_STEP),
+    and in the worst case the n errors add (a population's error also feeds
+    the conserved moments, which do not relax); plus the initial state's FP32
+    evaluation (4 * 2^-24 |df|).  |df| at its largest over the states given."""
+    if isinstance(states, np.ndarray):
+        states = [states]
+    dmax = max(float(np.max(np.abs(stored_deviations(f, nroots, dim)))) for f in states)
+    return (max(steps, 1) * EPS_STEP[storage] + 4.0 * 2.0 ** -24) * dmax
+
+
 def field_errors(gpu: np.ndarray, ref: np.ndarray, bound=None, bar: float = 1e-5):
     """Per-field errors of the GPU moments against the oracle's.
 

