@@ -115,19 +115,20 @@ typedef struct lesbgk_params {
                            re-emitted specularly; 0 = fully diffuse (the paper's runs) */
   double wall_T_amp;    /* wall heating (Sec. 4.2): T_w(t) = wall_T + wall_T_amp sin(wall_T_freq t) */
   double wall_T_freq;   /* (St in the units of Sec. 2.2); amp 0 = steady walls.  The wall
-                           tables are rebuilt in FP64 on the host for each step's time.
-                           Specular fractions need FP32 storage; heating takes any storage.
-                           The batched solver takes steady walls (diffuse or Maxwell). */
+                           tables are FP64 polynomials in the heating, evaluated for each
+                           step's time (the same bits on the host for lesbgk_step and on
+                           the device in the batched solver).  Specular fractions need
+                           FP32 storage; heating takes any storage. */
   int32_t dim;          /* dimension D of the velocity set: 0 or 2 = the 2D sets above;
                            3 = D3Q64 (nroots 4, order 3; any storage) or D3Q216 (nroots 6,
-                           order 4, the paper's 11th-order set; FP32), on the same 2D grid: the
+                           order 4, the paper's 11th-order set; FP32, FP16 or BF16), on the same 2D grid: the
                            paper's D = 3 thermodynamics (C_p = 5/2; Sec. 2.1, Sec. 4).
                            Nothing varies in z and walls and forces have no z part, so the
                            state stays even in c_z: the library stores the c_z > 0 half
                            (Q = nroots^3/2 values per node, population
                            a = (iz*nroots + ix)*nroots + iy, c_z = c[nroots/2 + iz]), each
                            value standing for +c_z and -c_z.  T = tr P/(3 rho) and sigma is
-                           trace-free in 3D in the moments.  No walls in x for D3Q216. */
+                           trace-free in 3D in the moments.  */
   int32_t bc_x;         /* LESBGK_PERIODIC (default) or LESBGK_DIFFUSE: fully diffuse walls at rest
                            on columns i = 0 and nx-1 (not in the paper, whose flows are uniform
                            in x), at temperatures wall_Tx; ghost columns hold the wall node.
@@ -276,9 +277,11 @@ int lesbgk_destroy(lesbgk *h);
  *
  * A batch holds up to `capacity` instances ("slots"), all with the same nx, a
  * power of two <= 32 (the 1D-in-y flows of the paper's Sec. 4 run on nx = 4),
- * each with its own ny, Kn, b, walls, force and time step, on D2Q16 (order 3)
- * or D2Q36 (order 4).  Every lesbgk_batch_step advances every slot by the same
- * number of steps: per step one launch per velocity set over a work list of
+ * each with its own ny, Kn, b, walls (diffuse, Maxwell, steady or heated),
+ * force and time step, on D2Q16 (order 3) or D2Q36 (order 4) in FP32, FP16 or BF16 storage,
+ * periodic in x.  Every lesbgk_batch_step advances every slot by the same
+ * number of steps: per step one launch per class (velocity set, storage, wall
+ * heating) over a work list of
  * (slot, row segment) items; steps in multiples of 64 replay a CUDA graph.
  * Each slot's arithmetic is that of lesbgk_step on the same problem (results
  * are bitwise equal), so a solve gives the same answer alone or in a batch.
@@ -339,7 +342,7 @@ int lesbgk_batch_set_rows(lesbgk_batch *b, int32_t rows, void *stream);
 /* Resident kernel (on by default): D2Q16 instances of at most max_ny rows
  * (0 keeps the current limit, 128 by default) whose two population buffers
  * fit in one block's shared memory (454 rows at nx = 4 on GB300) are each held
- * by one block for steps_per_launch time steps (an even divisor of 64; 0
+ * (steady walls) by one block for steps_per_launch time steps (an even divisor of 64; 0
  * keeps the current, 64 by default), reading and writing device memory once
  * per launch, while the other instances take one launch per step; in the
  * 64-step graphs the two run side by side.  A resident instance is one

@@ -34,7 +34,11 @@ namespace {
 
 constexpr int kBBlock = 128;
 constexpr int kBRing = 4;
-constexpr int kNumClasses = 2;  // class 0: D2Q16 order 3, class 1: D2Q36 order 4
+// classes: velocity set x storage x wall heating -- 0 D2Q16 (order 3) and 1
+// D2Q36 (order 4) in FP32, 2 and 3 in FP16, 4 and 5 in BF16; 6 to 11 the same
+// with heated walls (their kernels carry the FP64 wall-table code, the
+// others none of it)
+constexpr int kNumClasses = 12;
 constexpr int kGraphSteps = 64;
 constexpr int kBuckets = 6;  // resident instances by height: ny <= 16, 32, ..., 512 (smem permitting)
 
@@ -42,6 +46,7 @@ constexpr int kBuckets = 6;  // resident instances by height: ny <= 16, 32, ...,
 struct InstDesc {
   float *f[2];  // population buffers, grouped layout
   float *snap;  // residual snapshot: rho, ux, uy, T per node
+  const HeatPoly *heat;  // heated walls (Sec. 4.2): the wall tables' polynomials, or null
   int nx, ny, walls, split;
   int vmode, has_force, pad0, pad1;
   float c_omega, visc_pow, b, beta, dtgx, dtgy, dt, wspec;  // wspec: Maxwell walls' specular share
@@ -57,6 +62,7 @@ struct LatTables {
   float c[kMaxR];
   float he[kMaxR][kMaxN + 1];
   float hw[kMaxR][kMaxN + 1];
+  float wq[kMaxQ], iwq[kMaxQ];  // 16-bit storage scale (stored = df * iwq), as in KArgs
 };
 
 struct BatchArgs {
@@ -64,6 +70,7 @@ struct BatchArgs {
   const InstDesc *desc;
   const WorkItem *items;
   const int *range;  // {first item, item count} of this lattice class
+  long long *nstep;  // per slot, per buffer parity: the steps that led to that buffer's state
 };
 
 // Per-solve scalars of one instance, held in registers (collide's TP).
@@ -72,9 +79,9 @@ struct InstRegs {
   int vmode, has_force;
 };
 
-template <int NR>
+template <int NR, class S = float>
 constexpr size_t batch_smem_bytes() {
-  return (size_t)(kBBlock / 32) * kBRing * Layout<NR>::G * 32 * Layout<NR>::V * sizeof(float);
+  return (size_t)(kBBlock / 32) * kBRing * Layout<NR, S>::G * 32 * Layout<NR, S>::VB;
 }
 
 // neighbour lanes inside a lane group of W lanes (periodic in x)
@@ -84,10 +91,42 @@ struct GroupLanes {
   __device__ __forceinline__ float right(float v) const { return __shfl_sync(kFull, v, srcR); }
 };
 
-// One time step of every work item of a lattice class.
-template <int NR, int N, int W>
+// wall_fix of a heated wall (Sec. 4.2): the tables evaluated at heating hv
+// from the polynomials of HeatPoly by the arithmetic of set_wall_time, so the
+// values are bitwise those the single-domain solver passes for the same step.
+template <int NR, bool SPEC, int Q, class TT>
+__device__ __forceinline__ void wall_fix_heated(float (&O)[Q], int side, const TT &T, const HeatPoly &P, double hv,
+                                                float wspec) {
+  constexpr int H = NR / 2;
+  float s = 0.0f;
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const int iy = a % NR;
+    const bool incoming = side == 0 ? (iy < H) : (iy >= H);
+    if (incoming) s = fmaf(fabsf(T.c[iy]), O[a], s);
+  }
+  const double ao = fma(fma(P.Aout[side][2], hv, P.Aout[side][1]), hv, P.Aout[side][0]);
+  const double zo = fma(fma(P.Zout[side][2], hv, P.Zout[side][1]), hv, P.Zout[side][0]);
+  const float rw1 = (s - (float)ao) * (float)(1.0 / zo);  // rho_W - 1
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const int iy = a % NR;
+    const bool outgoing = side == 0 ? (iy >= H) : (iy < H);
+    if (outgoing) {
+      const double S = fma(fma(P.S[side][2][a], hv, P.S[side][1][a]), hv, P.S[side][0][a]);
+      const float diffuse = fmaf(rw1, (float)S, (float)(S - P.w[a]));
+      if constexpr (SPEC) O[a] = fmaf(wspec, O[a + (NR - 1 - 2 * iy)] - diffuse, diffuse);
+      else O[a] = diffuse;
+    }
+  }
+}
+
+// One time step of every work item of a class (velocity set and storage S:
+// FP32 deviations, or FP16/BF16 relative deviations rounded stochastically
+// with the random words of k_step, keyed by the instance's step count and row).
+template <int NR, int N, int W, class S, bool HEAT>
 __global__ void __launch_bounds__(kBBlock) k_batch_step(const BatchArgs B, const int par) {
-  using Lay = Layout<NR>;
+  using Lay = Layout<NR, S>;
   constexpr int Q = Lay::Q, H = Lay::H, V = Lay::V, G = Lay::G;
   constexpr int GPW = 32 / W;
   const int lane = threadIdx.x & 31;
@@ -112,11 +151,11 @@ __global__ void __launch_bounds__(kBBlock) k_batch_step(const BatchArgs B, const
     ay[i] = D.ay[i];
     ky[i] = D.ky[i];
   }
-  const float *fin = D.f[par];
-  float *fout = D.f[par ^ 1];
+  const S *fin = reinterpret_cast<const S *>(D.f[par]);
+  S *fout = reinterpret_cast<S *>(D.f[par ^ 1]);
   const long long gstride = (long long)V * W * ny;
   const long long rstride = (long long)V * W;
-  const float *fx = fin + (long long)lx * V;
+  const S *fx = fin + (long long)lx * V;
   const int y0 = wi.y0;
   const int rows = live ? wi.rows : 0;
   int nrows = rows;  // the warp runs its longest item's rows
@@ -129,13 +168,13 @@ __global__ void __launch_bounds__(kBBlock) k_batch_step(const BatchArgs B, const
   float fc[Q], s0[Q], s1[Q];
   {
     float m2[Q], m1[Q], p1[Q];
-    const float *pm2 = row_ptr(y0 - 2), *pm1 = row_ptr(y0 - 1), *pz = row_ptr(y0), *pp1 = row_ptr(y0 + 1);
+    const S *pm2 = row_ptr(y0 - 2), *pm1 = row_ptr(y0 - 1), *pz = row_ptr(y0), *pp1 = row_ptr(y0 + 1);
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-      ld_group<NR>(pm1, gstride, g, m1);
-      ld_group<NR>(pz, gstride, g, fc);
-      if (g >= G / 2) ld_group<NR>(pm2, gstride, g, m2);
-      else ld_group<NR>(pp1, gstride, g, p1);
+      ld_group_s<NR, S>(pm1, gstride, g, m1, B.lat);
+      ld_group_s<NR, S>(pz, gstride, g, fc, B.lat);
+      if (g >= G / 2) ld_group_s<NR, S>(pm2, gstride, g, m2, B.lat);
+      else ld_group_s<NR, S>(pp1, gstride, g, p1, B.lat);
     }
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
@@ -150,15 +189,15 @@ __global__ void __launch_bounds__(kBBlock) k_batch_step(const BatchArgs B, const
   }
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  using T = typename VecT<V>::T;
+  using T = typename Raw<Lay::VB>::T;
   T *ring = reinterpret_cast<T *>(smem_raw) + (size_t)(threadIdx.x >> 5) * kBRing * G * 32 + lane;
   int r1 = map_row(y0 + 1, ny, walls), r2 = map_row(y0 + 2, ny, walls);
   auto issue_rowload = [&](int k) {
     if (k < nrows) {
-      const float *q1 = fx + r1 * rstride, *q2 = fx + r2 * rstride;
+      const S *q1 = fx + r1 * rstride, *q2 = fx + r2 * rstride;
       T *slot = ring + (k % kBRing) * G * 32;
 #pragma unroll
-      for (int g = 0; g < G; ++g) cp_async_vec<V>(slot + g * 32, (g >= G / 2 ? q1 : q2) + g * gstride);
+      for (int g = 0; g < G; ++g) cp_async_raw<Lay::VB>(slot + g * 32, (g >= G / 2 ? q1 : q2) + g * gstride);
       r1 = r2;
       r2 = r2 + 1 < ny ? r2 + 1 : (walls ? ny - 1 : 0);
     }
@@ -175,12 +214,7 @@ __global__ void __launch_bounds__(kBBlock) k_batch_step(const BatchArgs B, const
     {
       const T *slot = ring + (k % kBRing) * G * 32;
 #pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const T v = slot[g * 32];
-        const float *e = reinterpret_cast<const float *>(&v);
-#pragma unroll
-        for (int q = 0; q < V; ++q) ld[Lay::alpha(g * V + q)] = e[q];
-      }
+      for (int g = 0; g < G; ++g) unpack_group<NR, S>(slot[g * 32], g, ld, B.lat);
     }
     float acc[Q];
     float omw;
@@ -227,16 +261,37 @@ __global__ void __launch_bounds__(kBBlock) k_batch_step(const BatchArgs B, const
       }
     }
     if (walls && (j == 0 || j == ny - 1)) {
-      if (D.wspec != 0.0f) wall_fix<NR, true>(acc, (j == 0) ? 0 : 1, B.lat, D);
-      else wall_fix<NR, false>(acc, (j == 0) ? 0 : 1, B.lat, D);
+      const int side = j == 0 ? 0 : 1;
+      if constexpr (HEAT) {  // the wall temperature of the time this step writes
+        const HeatPoly &hp = *D.heat;
+        const double hv = wall_heating(hp, (double)(B.nstep[2 * wi.inst + par] + 1) * hp.dt);
+        if (D.wspec != 0.0f) wall_fix_heated<NR, true>(acc, side, B.lat, hp, hv, D.wspec);
+        else wall_fix_heated<NR, false>(acc, side, B.lat, hp, hv, D.wspec);
+      } else if (D.wspec != 0.0f) {
+        wall_fix<NR, true>(acc, side, B.lat, D);
+      } else {
+        wall_fix<NR, false>(acc, side, B.lat, D);
+      }
     }
     if (k < rows) {
-      float *o = fout + (long long)j * rstride + (long long)lx * V;
+      S *o = fout + (long long)j * rstride + (long long)lx * V;
+      if constexpr (Store<S>::kScaled) {  // the key of k_step: step count and row
+        const unsigned seed = (unsigned)B.nstep[2 * wi.inst + par] * 0x9e3779b9u + 0x7f4a7c15u;
+        const unsigned key = mix32(seed ^ mix32((unsigned)j));
 #pragma unroll
-      for (int g = 0; g < G; ++g) st_group<NR>(o, gstride, g, acc);
+        for (int g = 0; g < G; ++g) st_group_sr<NR, S>(o, gstride, g, acc, B.lat, key);
+      } else {
+#pragma unroll
+        for (int g = 0; g < G; ++g) st_group_s<NR, S>(o, gstride, g, acc, B.lat);
+      }
     }
   }
   cp_async_wait<0>();
+  // the instance's step count (the clock of heated walls, the key of 16-bit
+  // rounding) follows its state into the other buffer: one thread per
+  // instance, while every thread of this launch reads parity par only
+  if constexpr (HEAT || Store<S>::kScaled)
+    if (live && wi.y0 == 0 && lx == 0) B.nstep[2 * wi.inst + (par ^ 1)] = B.nstep[2 * wi.inst + par] + 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -370,26 +425,23 @@ __global__ void __launch_bounds__(kBBlock) k_batch_resident(const BatchArgs B, c
 // r = Inf); the snapshot is refreshed.  mass[item] receives the item's sum of
 // rho - 1 over its nodes (FP32 per thread, FP64 across the block).  One block
 // per item.
-template <int NR>
+template <int NR, class S>
 __global__ void __launch_bounds__(kBBlock) k_batch_residual(const BatchArgs B, const int par,
                                                             unsigned *__restrict__ res_bits,
                                                             double *__restrict__ mass) {
-  using Lay = Layout<NR>;
-  constexpr int Q = Lay::Q;
+  constexpr int Q = NR * NR;
   const int first = B.range[0], count = B.range[1];
   if ((int)blockIdx.x >= count) return;
   const WorkItem wi = B.items[first + blockIdx.x];
   const InstDesc &D = B.desc[wi.inst];
   const int nx = D.nx, ny = D.ny;
   const long long cells = (long long)nx * ny;
-  const long long gstride = (long long)Lay::V * cells;
-  const float *f = D.f[par];
+  const S *f = reinterpret_cast<const S *>(D.f[par]);
   float r = 0.0f, dm = 0.0f;
   for (int t = threadIdx.x; t < wi.rows * nx; t += kBBlock) {
     const long long c = (long long)wi.y0 * nx + t;
     float F[Q];
-#pragma unroll
-    for (int g = 0; g < Lay::G; ++g) ld_group<NR>(f + c * Lay::V, gstride, g, F);
+    ld_node<NR, S, 1>(f, c, cells, F, B.lat);
     float m[3][3];
     hermite_moments<NR, 2>(F, m, B.lat);
     const float rho = 1.0f + m[0][0];
@@ -429,7 +481,7 @@ __global__ void __launch_bounds__(kBBlock) k_batch_residual(const BatchArgs B, c
 // list: f = rho S(T,u) (Eq. feq0 to order N) from the slot's fields (device
 // double[4][ny][nx] in its spare buffer when list entry bit 30 is set, else
 // rest), then the wall rule -- the arithmetic of the single-domain k_init.
-template <int NR, int N>
+template <int NR, int N, class S>
 __global__ void __launch_bounds__(kBBlock) k_batch_init(const BatchArgs B, const int *__restrict__ list, int n,
                                                         const int par) {
   if ((int)blockIdx.x >= n) return;
@@ -439,7 +491,8 @@ __global__ void __launch_bounds__(kBBlock) k_batch_init(const BatchArgs B, const
   const int nx = D.nx, ny = D.ny;
   const long long cells = (long long)nx * ny;
   const double *fields = has_fields ? reinterpret_cast<const double *>(D.f[par ^ 1]) : nullptr;
-  float *f = D.f[par];
+  S *f = reinterpret_cast<S *>(D.f[par]);
+  if (threadIdx.x == 0) B.nstep[2 * (entry & 0x3fffffff) + par] = 0;
   for (long long c = threadIdx.x; c < cells; c += kBBlock) {
     float drho = 0.f, ux = 0.f, uy = 0.f, dT = 0.f;
     if (fields) {
@@ -460,14 +513,14 @@ __global__ void __launch_bounds__(kBBlock) k_batch_init(const BatchArgs B, const
       if (D.wspec != 0.0f) wall_fix<NR, true>(Sv, j == 0 ? 0 : 1, B.lat, D);
       else wall_fix<NR, false>(Sv, j == 0 ? 0 : 1, B.lat, D);
     }
-    st_node<NR, float, 1>(f, c, cells, Sv, B.lat);
+    st_node<NR, S, 1>(f, c, cells, Sv, B.lat);
   }
 }
 
 // Moments (Eq. mac) of every node of every work item whose slot has an output
 // in outs[slot] (DEVICE float[9][ny][nx] each, or null): the per-node
 // arithmetic of lesbgk_moments, one block per item.
-template <int NR>
+template <int NR, class S>
 __global__ void __launch_bounds__(kBBlock) k_batch_moments(const BatchArgs B, const int par,
                                                            float *const *__restrict__ outs) {
   const int first = B.range[0], count = B.range[1];
@@ -478,11 +531,11 @@ __global__ void __launch_bounds__(kBBlock) k_batch_moments(const BatchArgs B, co
   const InstDesc &D = B.desc[wi.inst];
   const int nx = D.nx;
   const long long cells = (long long)nx * D.ny;
-  const float *f = D.f[par];
+  const S *f = reinterpret_cast<const S *>(D.f[par]);
   for (int t = threadIdx.x; t < wi.rows * nx; t += kBBlock) {
     const long long c = (long long)wi.y0 * nx + t;
     float F[NR * NR];
-    ld_node<NR, float, 1>(f, c, cells, F, B.lat);
+    ld_node<NR, S, 1>(f, c, cells, F, B.lat);
     float d[4];
     node_moments<NR>(F, out, cells, c, B.lat, d);
   }
@@ -541,10 +594,38 @@ class Pool {
   std::map<size_t, size_t> free_;
 };
 
-int class_of(int nr, int order) {
-  if (nr == 4 && order == 3) return 0;
-  if (nr == 6 && order == 4) return 1;
+int class_of(int nr, int order, int storage, bool heated) {
+  const int st = storage == LESBGK_F32 ? 0 : storage == LESBGK_F16 ? 1 : storage == LESBGK_BF16 ? 2 : -1;
+  if (st < 0) return -1;
+  const int h = heated ? 6 : 0;
+  if (nr == 4 && order == 3) return 2 * st + h;
+  if (nr == 6 && order == 4) return 2 * st + 1 + h;
   return -1;
+}
+
+// Call fn(NR, N, storage tag, heated) with the compile-time constants of class cls.
+template <class Fn>
+void with_class(int cls, Fn &&fn) {
+  using R4 = std::integral_constant<int, 4>;
+  using R6 = std::integral_constant<int, 6>;
+  using N3 = std::integral_constant<int, 3>;
+  using N4 = std::integral_constant<int, 4>;
+  using H0 = std::false_type;
+  using H1 = std::true_type;
+  switch (cls) {
+    case 0: fn(R4{}, N3{}, float{}, H0{}); break;
+    case 1: fn(R6{}, N4{}, float{}, H0{}); break;
+    case 2: fn(R4{}, N3{}, __half{}, H0{}); break;
+    case 3: fn(R6{}, N4{}, __half{}, H0{}); break;
+    case 4: fn(R4{}, N3{}, __nv_bfloat16{}, H0{}); break;
+    case 5: fn(R6{}, N4{}, __nv_bfloat16{}, H0{}); break;
+    case 6: fn(R4{}, N3{}, float{}, H1{}); break;
+    case 7: fn(R6{}, N4{}, float{}, H1{}); break;
+    case 8: fn(R4{}, N3{}, __half{}, H1{}); break;
+    case 9: fn(R6{}, N4{}, __half{}, H1{}); break;
+    case 10: fn(R4{}, N3{}, __nv_bfloat16{}, H1{}); break;
+    default: fn(R6{}, N4{}, __nv_bfloat16{}, H1{}); break;
+  }
 }
 
 }  // namespace
@@ -557,6 +638,7 @@ struct lesbgk_batch {
     size_t off = 0, bytes = 0;
     InstDesc desc;
     KArgs args;
+    std::vector<HeatPoly> heat;  // heated walls: the host copy of the slot's polynomials (one), else empty
     double dt = 0, dx = 0, dy = 0, cmax = 0, tau_ref = 0;
     int64_t steps = 0, snap_step = -1;
   };
@@ -574,13 +656,14 @@ struct lesbgk_batch {
   int *d_list = nullptr;
   float **d_outs = nullptr;
   double *d_partial = nullptr, *d_sums = nullptr;
+  long long *d_nstep = nullptr;
   char *pool_base = nullptr;
   size_t pool_bytes = 0;
   Pool pool;
   std::vector<Slot> slots;
   std::vector<WorkItem> items;
-  int range[kNumClasses][2] = {{0, 0}, {0, 0}};
-  int range_all[kNumClasses][2] = {{0, 0}, {0, 0}};
+  int range[kNumClasses][2] = {};
+  int range_all[kNumClasses][2] = {};
   int rrange[kBuckets][2] = {};
   int max_items = 0;
   bool resident = true;      // D2Q16 instances that fit in shared memory take the resident kernel
@@ -592,9 +675,9 @@ struct lesbgk_batch {
   int par = 0;
   int sm_count = 0;
   LatTables lat[kNumClasses];
-  bool lat_ready[kNumClasses] = {false, false};
+  bool lat_ready[kNumClasses] = {};
   cudaGraphExec_t graph = nullptr;
-  int graph_grid[kNumClasses] = {0, 0};
+  int graph_grid[kNumClasses] = {};
   bool graph_dirty = true;
   bool items_dirty = false;  // slots changed since the work list was uploaded
 };
@@ -604,7 +687,7 @@ namespace {
 constexpr size_t kItemsPerSlot = 1024;  // work-list room: items per slot (rows/8 for ny <= 8192)
 
 struct Layout0 {
-  size_t desc, items, mass, range, range_all, rlist, rrange, res, partial, sums, list, outs, pool;
+  size_t desc, items, mass, range, range_all, rlist, rrange, res, partial, sums, list, outs, nstep, pool;
 };
 
 Layout0 fixed_layout(int capacity) {
@@ -634,34 +717,49 @@ Layout0 fixed_layout(int capacity) {
   o = align_up(o + sizeof(int) * (size_t)capacity, 256);
   L.outs = o;  // per-slot moment outputs (lesbgk_batch_moments_many)
   o = align_up(o + sizeof(float *) * (size_t)capacity, 256);
+  L.nstep = o;  // per slot and buffer parity: steps done (the heated walls' clock)
+  o = align_up(o + sizeof(long long) * 2 * (size_t)capacity, 256);
   L.pool = o;
   return L;
 }
 
+size_t elem_bytes(int storage) { return storage == LESBGK_F32 ? sizeof(float) : 2; }
+
 size_t slot_bytes(const lesbgk_params &p) {
   const size_t cells = (size_t)p.nx * p.ny;
   const size_t q = (size_t)p.nroots * p.nroots;
-  const size_t buf = align_up(cells * std::max<size_t>(q * sizeof(float), 36), 256);
-  return 2 * buf + align_up(cells * 4 * sizeof(float), 256);
+  const size_t buf = align_up(cells * std::max<size_t>(q * elem_bytes(p.storage), 36), 256);
+  const size_t heat = p.wall_T_amp != 0.0 ? align_up(sizeof(HeatPoly), 256) : 0;
+  return 2 * buf + align_up(cells * 4 * sizeof(float), 256) + heat;
 }
 
 bool pow2_le32(int n) { return n >= 1 && n <= 32 && (n & (n - 1)) == 0; }
 
-template <int NR, int N>
+template <int NR, int N, class S, bool HEAT>
 void *step_fn(int W) {
   switch (W) {
-    case 1: return (void *)k_batch_step<NR, N, 1>;
-    case 2: return (void *)k_batch_step<NR, N, 2>;
-    case 4: return (void *)k_batch_step<NR, N, 4>;
-    case 8: return (void *)k_batch_step<NR, N, 8>;
-    case 16: return (void *)k_batch_step<NR, N, 16>;
-    default: return (void *)k_batch_step<NR, N, 32>;
+    case 1: return (void *)k_batch_step<NR, N, 1, S, HEAT>;
+    case 2: return (void *)k_batch_step<NR, N, 2, S, HEAT>;
+    case 4: return (void *)k_batch_step<NR, N, 4, S, HEAT>;
+    case 8: return (void *)k_batch_step<NR, N, 8, S, HEAT>;
+    case 16: return (void *)k_batch_step<NR, N, 16, S, HEAT>;
+    default: return (void *)k_batch_step<NR, N, 32, S, HEAT>;
   }
 }
 
-void *step_kernel(int cls, int W) { return cls == 0 ? step_fn<4, 3>(W) : step_fn<6, 4>(W); }
+void *step_kernel(int cls, int W) {
+  void *fn = nullptr;
+  with_class(cls, [&](auto r, auto n, auto st, auto ht) {
+    fn = step_fn<decltype(r)::value, decltype(n)::value, decltype(st), decltype(ht)::value>(W);
+  });
+  return fn;
+}
 
-size_t step_smem(int cls) { return cls == 0 ? batch_smem_bytes<4>() : batch_smem_bytes<6>(); }
+size_t step_smem(int cls) {
+  size_t b = 0;
+  with_class(cls, [&](auto r, auto, auto st, auto) { b = batch_smem_bytes<decltype(r)::value, decltype(st)>(); });
+  return b;
+}
 
 BatchArgs make_args(const lesbgk_batch *b, int cls) {
   BatchArgs a;
@@ -669,6 +767,7 @@ BatchArgs make_args(const lesbgk_batch *b, int cls) {
   a.desc = b->d_desc;
   a.items = b->d_items;
   a.range = b->d_range + 2 * cls;
+  a.nstep = b->d_nstep;
   return a;
 }
 
@@ -699,7 +798,8 @@ size_t resident_smem(const lesbgk_batch *b, int k) {
 }
 
 bool is_resident(const lesbgk_batch *b, const lesbgk_batch::Slot &sl) {
-  return b->resident && sl.cls == 0 && sl.p.ny <= std::min(b->resident_ny, b->resident_limit);
+  return b->resident && sl.cls == 0 &&  // D2Q16 in FP32, steady walls
+         sl.p.ny <= std::min(b->resident_ny, b->resident_limit);
 }
 
 // K steps of every resident instance: one launch per non-empty bucket.
@@ -904,6 +1004,7 @@ extern "C" int lesbgk_batch_create(int32_t capacity, int32_t nx, void *d_workspa
   b->d_mass = reinterpret_cast<double *>(b->ws + L.mass);
   b->d_list = reinterpret_cast<int *>(b->ws + L.list);
   b->d_outs = reinterpret_cast<float **>(b->ws + L.outs);
+  b->d_nstep = reinterpret_cast<long long *>(b->ws + L.nstep);
   b->d_partial = reinterpret_cast<double *>(b->ws + L.partial);
   b->d_sums = reinterpret_cast<double *>(b->ws + L.sums);
   b->pool_base = b->ws + L.pool;
@@ -913,13 +1014,9 @@ extern "C" int lesbgk_batch_create(int32_t capacity, int32_t nx, void *d_workspa
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
-  for (int w : {1, 2, 4, 8, 16, 32}) {
-    if (e != cudaSuccess) break;
-    e = cudaFuncSetAttribute(step_fn<4, 3>(w), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes<4>());
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(step_fn<6, 4>(w), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)batch_smem_bytes<6>());
-  }
+  for (int w : {1, 2, 4, 8, 16, 32})
+    for (int cls = 0; cls < kNumClasses && e == cudaSuccess; ++cls)
+      e = cudaFuncSetAttribute(step_kernel(cls, w), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem(cls));
   // the resident kernel: as tall an instance as two buffers of Q planes fit in
   // the opt-in shared memory of a block
   int optin = 0;
@@ -947,11 +1044,10 @@ namespace {
 int prepare_slot(lesbgk_batch *b, const lesbgk_params *p, const double *h_init, int *slot_out) {
   if (int rc = check_params(p)) return rc;
   const int order = p->order ? p->order : default_order(p->nroots);
-  const int cls = class_of(p->nroots, order);
+  if (p->storage == LESBGK_F32C) return fail(LESBGK_EINVAL, "batched instances store FP32, FP16 or BF16 populations");
+  const int cls = class_of(p->nroots, order, p->storage, p->wall_T_amp != 0.0);
   if (cls < 0) return fail(LESBGK_EINVAL, "batched instances take D2Q16 (order 3) or D2Q36 (order 4)");
   if (p->nx != b->nx) return fail(LESBGK_EINVAL, "instance nx %d differs from the batch's %d", p->nx, b->nx);
-  if (p->storage != LESBGK_F32) return fail(LESBGK_EINVAL, "batched instances store FP32 populations");
-  if (p->wall_T_amp != 0.0) return fail(LESBGK_EINVAL, "batched instances take steady walls");
   if (p->dim == 3) return fail(LESBGK_EINVAL, "batched instances take the 2D velocity sets");
   if (p->bc_x != LESBGK_PERIODIC) return fail(LESBGK_EINVAL, "batched instances are periodic in x");
   if ((long long)(p->ny + b->rows - 1) / b->rows > (long long)kItemsPerSlot)
@@ -987,13 +1083,17 @@ int prepare_slot(lesbgk_batch *b, const lesbgk_params *p, const double *h_init, 
   sl.tau_ref = su.tau_ref;
   const size_t cells = (size_t)p->nx * p->ny;
   const size_t q = (size_t)p->nroots * p->nroots;
-  const size_t buf = align_up(cells * std::max<size_t>(q * sizeof(float), 36), 256);
+  const size_t buf = align_up(cells * std::max<size_t>(q * elem_bytes(p->storage), 36), 256);
   char *base = b->pool_base + off;
   InstDesc &D = sl.desc;
   std::memset(&D, 0, sizeof D);
   D.f[b->par] = reinterpret_cast<float *>(base);
   D.f[b->par ^ 1] = reinterpret_cast<float *>(base + buf);
   D.snap = reinterpret_cast<float *>(base + 2 * buf);
+  if (p->wall_T_amp != 0.0) {  // the polynomials follow the snapshot (uploaded with the descriptor)
+    sl.heat.assign(1, su.heat);
+    D.heat = reinterpret_cast<const HeatPoly *>(base + 2 * buf + align_up(cells * 4 * sizeof(float), 256));
+  }
   const KArgs &A = su.args;
   D.nx = p->nx;
   D.ny = p->ny;
@@ -1024,6 +1124,8 @@ int prepare_slot(lesbgk_batch *b, const lesbgk_params *p, const double *h_init, 
     std::memcpy(lt.c, A.c, sizeof lt.c);
     std::memcpy(lt.he, A.he, sizeof lt.he);
     std::memcpy(lt.hw, A.hw, sizeof lt.hw);
+    std::memcpy(lt.wq, A.wq, sizeof lt.wq);  // (the 2D sets: the first kMaxQ entries)
+    std::memcpy(lt.iwq, A.iwq, sizeof lt.iwq);
     b->lat_ready[cls] = true;
     drop_graph(b);
   }
@@ -1060,13 +1162,16 @@ extern "C" int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const d
   const size_t cells = (size_t)p->nx * p->ny;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemcpyAsync(b->d_desc + slot, &D, sizeof D, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_nstep + 2 * slot + b->par, 0, sizeof(long long), s);
+  if (e == cudaSuccess && D.heat)  // (pageable host copy: staged before the call returns)
+    e = cudaMemcpyAsync(const_cast<HeatPoly *>(D.heat), sl.heat.data(), sizeof(HeatPoly), cudaMemcpyHostToDevice, s);
   const double *dfields = nullptr;
   if (e == cudaSuccess && h_init) {
     e = cudaMemcpyAsync(D.f[b->par ^ 1], h_init, 4 * cells * sizeof(double), cudaMemcpyHostToDevice, s);
     dfields = reinterpret_cast<const double *>(D.f[b->par ^ 1]);
   }
   if (e == cudaSuccess)
-    e = lesbgk_internal::launch_init(sl.args, sl.nr, sl.order, dfields, D.f[b->par], b->sm_count, s);
+    e = lesbgk_internal::launch_init(sl.args, sl.nr, sl.order, p->storage, dfields, D.f[b->par], b->sm_count, s);
   if (e == cudaSuccess && h_init) e = settle_host_copy(h_init, s);
   if (e != cudaSuccess) {
     release_slot(b, slot);
@@ -1108,6 +1213,10 @@ extern "C" int lesbgk_batch_add_many(lesbgk_batch *b, int32_t n, const lesbgk_pa
     std::vector<int> list[kNumClasses];
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
       const auto &sl = b->slots[taken[i]];
+      if (sl.desc.heat)
+        e = cudaMemcpyAsync(const_cast<HeatPoly *>(sl.desc.heat), sl.heat.data(), sizeof(HeatPoly),
+                            cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) break;
       const double *hi_init = h_inits ? h_inits[i] : nullptr;
       if (hi_init)
         e = cudaMemcpyAsync(sl.desc.f[b->par ^ 1], hi_init, 4 * (size_t)sl.p.nx * sl.p.ny * sizeof(double),
@@ -1121,8 +1230,10 @@ extern "C" int lesbgk_batch_add_many(lesbgk_batch *b, int32_t n, const lesbgk_pa
       e = cudaMemcpyAsync(b->d_list + at, list[cls].data(), sizeof(int) * m, cudaMemcpyHostToDevice, s);
       if (e != cudaSuccess) break;
       BatchArgs a = make_args(b, cls);
-      if (cls == 0) k_batch_init<4, 3><<<m, kBBlock, 0, s>>>(a, b->d_list + at, m, b->par);
-      else k_batch_init<6, 4><<<m, kBBlock, 0, s>>>(a, b->d_list + at, m, b->par);
+      const int *lst = b->d_list + at;
+      with_class(cls, [&](auto r, auto nn, auto st, auto) {
+        k_batch_init<decltype(r)::value, decltype(nn)::value, decltype(st)><<<m, kBBlock, 0, s>>>(a, lst, m, b->par);
+      });
       e = cudaGetLastError();
       at += m;
     }
@@ -1197,8 +1308,9 @@ extern "C" int lesbgk_batch_residuals(lesbgk_batch *b, double *h_res, double *h_
     const int n = b->range_all[cls][1];
     if (!n) continue;
     BatchArgs a = make_args_all(b, cls);
-    if (cls == 0) k_batch_residual<4><<<n, kBBlock, 0, s>>>(a, b->par, b->d_res, b->d_mass);
-    else k_batch_residual<6><<<n, kBBlock, 0, s>>>(a, b->par, b->d_res, b->d_mass);
+    with_class(cls, [&](auto r, auto, auto st, auto) {
+      k_batch_residual<decltype(r)::value, decltype(st)><<<n, kBBlock, 0, s>>>(a, b->par, b->d_res, b->d_mass);
+    });
     e = cudaGetLastError();
   }
   std::vector<unsigned> bits(b->capacity);
@@ -1229,8 +1341,8 @@ extern "C" int lesbgk_batch_moments(lesbgk_batch *b, int32_t slot, float *d_out,
   if (!b || slot < 0 || slot >= b->capacity || !b->slots[slot].used) return fail(LESBGK_EINVAL, "no such slot");
   auto &sl = b->slots[slot];
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = lesbgk_internal::launch_moments(sl.args, sl.nr, sl.desc.f[b->par], d_out, b->d_partial,
-                                                  b->d_sums, s);
+  cudaError_t e = lesbgk_internal::launch_moments(sl.args, sl.nr, sl.order, sl.p.storage, sl.desc.f[b->par], d_out,
+                                                  b->d_partial, b->d_sums, s);
   if (e == cudaSuccess && h_sums) {
     e = cudaMemcpyAsync(h_sums, b->d_sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1259,8 +1371,9 @@ extern "C" int lesbgk_batch_moments_many(lesbgk_batch *b, int32_t n, const int32
     const int m = b->range_all[cls][1];
     if (!m) continue;
     BatchArgs a = make_args_all(b, cls);
-    if (cls == 0) k_batch_moments<4><<<m, kBBlock, 0, s>>>(a, b->par, b->d_outs);
-    else k_batch_moments<6><<<m, kBBlock, 0, s>>>(a, b->par, b->d_outs);
+    with_class(cls, [&](auto r, auto, auto st, auto) {
+      k_batch_moments<decltype(r)::value, decltype(st)><<<m, kBBlock, 0, s>>>(a, b->par, b->d_outs);
+    });
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return cuda_fail(e, "batched moments");
@@ -1271,8 +1384,9 @@ extern "C" int lesbgk_batch_get_populations(lesbgk_batch *b, int32_t slot, float
   if (!b || !d_out || slot < 0 || slot >= b->capacity || !b->slots[slot].used)
     return fail(LESBGK_EINVAL, "no such slot");
   auto &sl = b->slots[slot];
-  cudaError_t e = lesbgk_internal::launch_ungroup(sl.nr, sl.desc.f[b->par], d_out, (long long)sl.p.nx * sl.p.ny,
-                                                  b->sm_count, static_cast<cudaStream_t>(stream));
+  cudaError_t e = lesbgk_internal::launch_ungroup(sl.args, sl.nr, sl.order, sl.p.storage, sl.desc.f[b->par], d_out,
+                                                  (long long)sl.p.nx * sl.p.ny, b->sm_count,
+                                                  static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? 0 : cuda_fail(e, "batch populations");
 }
 

@@ -220,57 +220,89 @@ __global__ void __launch_bounds__(kBlock) k_step(const S *__restrict__ fin, S *_
 // meet in the collision, whose moments are sums over all levels (each warp
 // adds its in-plane Hermite moments weighted by 2 He_l(c_z) into shared
 // memory, one barrier per row, every warp sums the three in the same order),
-// and in the wall rule's incoming flux (one more barrier on wall rows).  The
-// advection does not depend on the collision, so a warp publishes its share,
-// advects, and only then waits for the others: the barrier no longer lines
-// the three warps up for the shuffle-heavy x-sweep (5.41 -> 3.98 ms per
-// 4096^2 step).
+// and in the wall rules' incoming flux (one more barrier on wall rows, and on
+// every row of the strips that hold a wall column).  The advection does not
+// depend on the collision, so a warp publishes its share, advects, and only
+// then waits for the others: the barrier no longer lines the three warps up
+// for the shuffle-heavy x-sweep (5.41 -> 3.98 ms per 4096^2 step).
+// Storage S: FP32 deviations, or FP16/BF16 relative deviations stochastically
+// rounded like k_step's (level iz's stored populations are iz*36 .. iz*36+35
+// of the node, so its scale factors and random words are those of the
+// one-thread layout).  WM: 0 y-walls (fully diffuse) if any, 1 y-walls with
+// a specular share, 2 walls in x as well (y-walls diffuse; corners as in
+// wall_corner).
 // ---------------------------------------------------------------------------
 constexpr int kBlockZ = 96;  // three warps: one per stored z-level
 constexpr int kXch = 13;     // moments a level contributes: l = 0, m + k <= 3 (10); l = 2, m + k <= 1 (3)
 constexpr int kXch4 = 4;     // ... held as four float4 per thread (16 slots)
 
-template <int RING>
+template <int RING, class S = float>
 constexpr size_t stepz_smem_bytes() {
-  return (size_t)3 * RING * 18 * 32 * 8 + (size_t)2 * 3 * kXch4 * 32 * sizeof(float4) + 3 * 32 * sizeof(float);
+  return (size_t)3 * RING * 18 * 32 * (2 * sizeof(S)) + (size_t)2 * 3 * kXch4 * 32 * sizeof(float4) +
+         3 * 32 * sizeof(float);
 }
 
-template <bool SPLIT, int RING, bool SPEC>
-__global__ void __launch_bounds__(kBlockZ) k_step_z(const float *__restrict__ fin, float *__restrict__ fout,
+template <bool SPLIT, int RING, int WM, class S>
+__global__ void __launch_bounds__(kBlockZ) k_step_z(const S *__restrict__ fin, S *__restrict__ fout,
                                                     const KArgs A) {
   constexpr int NR = 6, N = 4, H = 3, Q = 36, V = 2, GL = 18, KM = 3;
   constexpr int HL = 2, U = 32 - 2 * HL;
+  using LL = LayoutQ<NR, S, Q>;  // one level: the D2Q36 slot order
+  static_assert(LL::V == V && LL::G == GL, "a level holds 18 pairs");
+  using T = typename Raw<LL::VB>::T;
+  constexpr bool kScaled = Store<S>::kScaled;
   const int lane = threadIdx.x & 31;
   const int iz = threadIdx.x >> 5;  // stored z-level of this warp
+  const int zo = iz * Q;            // its first stored population
   const int strip = blockIdx.x % A.nstrips;
   const int seg = blockIdx.x / A.nstrips;
   if (seg >= A.nseg) return;  // uniform over the block
   const int nx = A.nx, ny = A.ny;
   const int xl = strip * U - HL + lane;
-  int xw = xl % nx;
-  if (xw < 0) xw += nx;
+  int xw;
+  if constexpr (WM == 2) {
+    xw = min(max(xl, 0), nx - 1);  // walls in x: ghost columns hold the wall node
+  } else {
+    xw = xl % nx;
+    if (xw < 0) xw += nx;
+  }
   const bool writer = lane >= HL && lane < 32 - HL && xl < nx;
+  // the strip holds a wall column (uniform over the block): its rows take the wall exchange
+  const bool xstrip = WM == 2 && (strip == 0 || (strip + 1) * U >= nx);
   const int y0 = seg * A.rows;
   const int y1 = min(y0 + A.rows, ny);
   const long long gstride = (long long)V * A.plane;
   const long long rstride = (long long)V * nx;
   // level iz's 18 group planes: c_y < 0 groups at 9 iz + gl (gl < 9), c_y > 0
-  // groups at 27 + 9 iz + (gl - 9); ld_group_s reads plane base + gl gstride
+  // groups at 27 + 9 iz + (gl - 9)
   const long long lo = (long long)(9 * iz) * gstride, hi = (long long)(18 + 9 * iz) * gstride;
-  const float *fx = fin + (long long)xw * V;
+  const S *fx = fin + (long long)xw * V;
   auto row_ptr = [&](int j) { return fx + map_row(j, ny, A.walls) * rstride; };
+  // a level's raw vector -> FP32 deviations (scale of stored population zo + a)
+  auto unpack_z = [&](const T &raw, int g, float (&F)[Q]) {
+    const S *e = reinterpret_cast<const S *>(&raw);
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const int a = LL::alpha(g * V + k);
+      F[a] = Store<S>::get(e[k], kScaled ? A.wq[zo + a] : 1.0f);
+    }
+  };
+  auto load_z = [&](const S *p, int g, float (&F)[Q]) {
+    const T raw = __ldg(reinterpret_cast<const T *>(p + g * gstride));
+    unpack_z(raw, g, F);
+  };
 
   float fc[Q], s0[Q], s1[Q];
   {
     float m2[Q], m1[Q], p1[Q];
-    const float *pm2 = row_ptr(y0 - 2), *pm1 = row_ptr(y0 - 1), *pz = row_ptr(y0), *pp1 = row_ptr(y0 + 1);
+    const S *pm2 = row_ptr(y0 - 2), *pm1 = row_ptr(y0 - 1), *pz = row_ptr(y0), *pp1 = row_ptr(y0 + 1);
 #pragma unroll
     for (int g = 0; g < GL; ++g) {
       const long long off = g < GL / 2 ? lo : hi;
-      ld_group_s<NR, float>(pm1 + off, gstride, g, m1, A);
-      ld_group_s<NR, float>(pz + off, gstride, g, fc, A);
-      if (g >= GL / 2) ld_group_s<NR, float>(pm2 + off, gstride, g, m2, A);
-      else ld_group_s<NR, float>(pp1 + off, gstride, g, p1, A);
+      load_z(pm1 + off, g, m1);
+      load_z(pz + off, g, fc);
+      if (g >= GL / 2) load_z(pm2 + off, g, m2);
+      else load_z(pp1 + off, g, p1);
     }
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
@@ -284,7 +316,6 @@ __global__ void __launch_bounds__(kBlockZ) k_step_z(const float *__restrict__ fi
     }
   }
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  using T = uint2;
   T *ring = reinterpret_cast<T *>(smem_raw) + (size_t)iz * RING * GL * 32 + lane;
   // exchange buffer [row parity][level][float4 k][lane]: consecutive lanes read
   // consecutive 16-byte words (no bank conflicts)
@@ -297,11 +328,11 @@ __global__ void __launch_bounds__(kBlockZ) k_step_z(const float *__restrict__ fi
   const int nrows = y1 - y0;
   auto issue_rowload = [&](int k) {
     if (k < nrows) {
-      const float *q1 = fx + r1 * rstride, *q2 = fx + r2 * rstride;
+      const S *q1 = fx + r1 * rstride, *q2 = fx + r2 * rstride;
       T *slot = ring + (k % RING) * GL * 32;
 #pragma unroll
       for (int g = 0; g < GL; ++g)
-        cp_async_raw<8>(slot + g * 32, (g >= GL / 2 ? q1 + hi : q2 + lo) + g * gstride);
+        cp_async_raw<LL::VB>(slot + g * 32, (g >= GL / 2 ? q1 + hi : q2 + lo) + g * gstride);
       r1 = r2;
       r2 = r2 + 1 < ny ? r2 + 1 : (A.walls ? ny - 1 : 0);
     }
@@ -318,7 +349,7 @@ __global__ void __launch_bounds__(kBlockZ) k_step_z(const float *__restrict__ fi
     {
       const T *slot = ring + (k % RING) * GL * 32;
 #pragma unroll
-      for (int g = 0; g < GL; ++g) unpack_group<NR, float>(slot[g * 32], g, ld, A);
+      for (int g = 0; g < GL; ++g) unpack_z(slot[g * 32], g, ld);
     }
 
     // this level's share of the moments into shared memory; the barrier and
@@ -439,37 +470,76 @@ __global__ void __launch_bounds__(kBlockZ) k_step_z(const float *__restrict__ fi
       }
     }
 
-    if (A.walls && (j == 0 || j == ny - 1)) {  // uniform over the block
-      // the wall rule of wall_fix with the incoming flux summed over the levels
-      const int side = j == 0 ? 0 : 1;
+    // the wall rules of wall_fix, wall_fix_x and wall_corner with the
+    // incoming flux summed over the levels
+    const bool yrow = A.walls && (j == 0 || j == ny - 1);  // uniform over the block
+    if (yrow || xstrip) {
+      const int ys = j == 0 ? 0 : 1, xs = xw == 0 ? 0 : 1;
+      const bool xn = WM == 2 && (xw == 0 || xw == nx - 1);  // this lane's node is on an x-wall
+      const float nxs = xs == 0 ? 1.0f : -1.0f, nys = ys == 0 ? 1.0f : -1.0f;
       float sl = 0.0f;
 #pragma unroll
       for (int a = 0; a < Q; ++a) {
-        const int iy = a % NR;
-        const bool incoming = side == 0 ? (iy < H) : (iy >= H);
-        if (incoming) sl = fmaf(fabsf(A.c[iy]), acc[a], sl);
+        const int ix = a / NR, iy = a % NR;
+        const bool kx_in = xs == 0 ? ix < H : ix >= H, ky_in = ys == 0 ? iy < H : iy >= H;
+        if (xn && yrow) {
+          if (kx_in && ky_in) sl = fmaf(fabsf(fmaf(A.c[ix], nxs, A.c[iy] * nys)), acc[a], sl);
+        } else if (xn) {
+          if (kx_in) sl = fmaf(fabsf(A.c[ix]), acc[a], sl);
+        } else if (ky_in) {
+          sl = fmaf(fabsf(A.c[iy]), acc[a], sl);
+        }
       }
       wsum[iz * 32 + lane] = sl;
       __syncthreads();
       const float s = (wsum[lane] + wsum[32 + lane]) + wsum[64 + lane];
-      const float rw1 = (s - A.wA[side]) * A.wB[side];
+      if (xn) {
+        const float rw1 = yrow ? (s - A.wAc[ys * 2 + xs]) * A.wBc[ys * 2 + xs] : (s - A.wAx[xs]) * A.wBx[xs];
 #pragma unroll
-      for (int a = 0; a < Q; ++a) {
-        const int iy = a % NR;
-        const bool outgoing = side == 0 ? (iy >= H) : (iy < H);
-        if (outgoing) {
-          const int ag = iz * Q + a;
-          const float diffuse = fmaf(rw1, A.wS[side][ag], A.wSdev[side][ag]);
-          if constexpr (SPEC) acc[a] = fmaf(A.wspec, acc[a + (NR - 1 - 2 * iy)] - diffuse, diffuse);
-          else acc[a] = diffuse;
+        for (int a = 0; a < Q; ++a) {
+          const int ix = a / NR, iy = a % NR;
+          const bool kx_in = xs == 0 ? ix < H : ix >= H, ky_in = ys == 0 ? iy < H : iy >= H;
+          const bool keep = yrow ? (kx_in && ky_in) : kx_in;
+          if (!keep) acc[a] = fmaf(rw1, A.wSx[xs][zo + a], A.wSxdev[xs][zo + a]);
+        }
+      } else if (yrow) {
+        const float rw1 = (s - A.wA[ys]) * A.wB[ys];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+          const int iy = a % NR;
+          const bool outgoing = ys == 0 ? (iy >= H) : (iy < H);
+          if (outgoing) {
+            const float diffuse = fmaf(rw1, A.wS[ys][zo + a], A.wSdev[ys][zo + a]);
+            if constexpr (WM == 1) acc[a] = fmaf(A.wspec, acc[a + (NR - 1 - 2 * iy)] - diffuse, diffuse);
+            else acc[a] = diffuse;
+          }
         }
       }
     }
 
     if (writer) {
-      float *o = fout + (long long)j * rstride + (long long)xw * V;
+      S *o = fout + (long long)j * rstride + (long long)xw * V;
+      if constexpr (kScaled) {
+        // the random words of st_group_sr: one per pair, keyed by the step,
+        // the global row and the node's group (9 iz + g, or 18 + 9 iz + g)
+        int gr = j + A.row_key;
+        if (A.row_period) {
+          gr %= A.row_period;
+          if (gr < 0) gr += A.row_period;
+        }
+        const unsigned key = mix32(A.seed ^ mix32((unsigned)gr));
 #pragma unroll
-      for (int g = 0; g < GL; ++g) st_group_s<NR, float>(o + (g < GL / 2 ? lo : hi), gstride, g, acc, A);
+        for (int g = 0; g < GL; ++g) {
+          const int a0 = LL::alpha(g * V), a1 = LL::alpha(g * V + 1);
+          const int gg = 9 * iz + g + (g < GL / 2 ? 0 : 18);
+          const unsigned bits = mix32(key ^ ((unsigned)gg * 0x9e3779b9u));
+          *reinterpret_cast<T *>(o + (g < GL / 2 ? lo : hi) + g * gstride) =
+              Store<S>::put_sr2(acc[a0] * A.iwq[zo + a0], acc[a1] * A.iwq[zo + a1], bits);
+        }
+      } else {
+#pragma unroll
+        for (int g = 0; g < GL; ++g) st_group_s<NR, float>(o + (g < GL / 2 ? lo : hi), gstride, g, acc, A);
+      }
     }
   }
   cp_async_wait<0>();
@@ -1039,7 +1109,7 @@ constexpr size_t step_smem_bytes() {
 // combinations: every (nroots, order) of the 2D sets in FP32, the default
 // orders also in FP16 and BF16 (NZ = 1), D2Q16 also compensated (Comp);
 // D3Q64, N = 3, in FP32, FP16, BF16 and compensated (NZ = 2 stored z-levels);
-// D3Q216, N = 4, in FP32 (NZ = 3).
+// D3Q216, N = 4, in FP32, FP16 and BF16 (NZ = 3).
 template <class Fn>
 void dispatch(int nr, int order, int storage, int dim, Fn &&fn) {
   using R4 = std::integral_constant<int, 4>;
@@ -1050,7 +1120,9 @@ void dispatch(int nr, int order, int storage, int dim, Fn &&fn) {
   using Z2 = std::integral_constant<int, 2>;
   using Z3 = std::integral_constant<int, 3>;
   if (dim == 3 && nr == 6) {
-    fn(R6{}, N4{}, float{}, Z3{});
+    if (storage == LESBGK_F16) fn(R6{}, N4{}, __half{}, Z3{});
+    else if (storage == LESBGK_BF16) fn(R6{}, N4{}, __nv_bfloat16{}, Z3{});
+    else fn(R6{}, N4{}, float{}, Z3{});
   } else if (dim == 3) {
     if (storage == LESBGK_F32C) fn(R4{}, N3{}, Comp{}, Z2{});
     else if (storage == LESBGK_F16) fn(R4{}, N3{}, __half{}, Z2{});
@@ -1086,11 +1158,15 @@ cudaError_t allow_smem(const lesbgk *h) {
       allow(k_step_c<true, kRing, NZ>, smem);
       allow(k_step_c<false, kRing, NZ>, smem);
     } else if constexpr (NZ == 3) {  // D3Q216: one warp per stored z-level
-      constexpr int smem = (int)stepz_smem_bytes<kRing>();
-      allow(k_step_z<true, kRing, false>, smem);
-      allow(k_step_z<false, kRing, false>, smem);
-      allow(k_step_z<true, kRing, true>, smem);
-      allow(k_step_z<false, kRing, true>, smem);
+      constexpr int smem = (int)stepz_smem_bytes<kRing, S>();
+      allow(k_step_z<true, kRing, 0, S>, smem);
+      allow(k_step_z<false, kRing, 0, S>, smem);
+      allow(k_step_z<true, kRing, 1, S>, smem);
+      allow(k_step_z<false, kRing, 1, S>, smem);
+      if constexpr (std::is_same<S, float>::value) {  // walls in x: FP32 storage
+        allow(k_step_z<true, kRing, 2, S>, smem);
+        allow(k_step_z<false, kRing, 2, S>, smem);
+      }
     } else {
       constexpr int smem = (int)step_smem_bytes<NR, S, NZ>();
       allow(k_step<NR, N, true, kRing, S, 0, NZ>, smem);
@@ -1122,15 +1198,22 @@ int launch_step(lesbgk *h, const void *fin, void *fout, cudaStream_t s) {
       else k_step_c<false, kRing, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
       return;
     } else if constexpr (NZ == 3) {  // D3Q216: a block of three warps per strip and segment
-      constexpr size_t smem = stepz_smem_bytes<kRing>();
+      constexpr size_t smem = stepz_smem_bytes<kRing, S>();
       const unsigned gz = (unsigned)warps;
-      const bool spec = h->args.walls && h->args.wspec != 0.0f;
+      const int wm = h->args.xwalls ? 2 : (h->args.walls && h->args.wspec != 0.0f ? 1 : 0);
+      if constexpr (std::is_same<S, float>::value) {  // walls in x: FP32 storage (checked at set-up)
+        if (wm == 2) {
+          if (split) k_step_z<true, kRing, 2, S><<<gz, kBlockZ, smem, s>>>(fi, fo, h->args);
+          else k_step_z<false, kRing, 2, S><<<gz, kBlockZ, smem, s>>>(fi, fo, h->args);
+          return;
+        }
+      }
       if (split) {
-        if (spec) k_step_z<true, kRing, true><<<gz, kBlockZ, smem, s>>>(fi, fo, h->args);
-        else k_step_z<true, kRing, false><<<gz, kBlockZ, smem, s>>>(fi, fo, h->args);
+        if (wm == 1) k_step_z<true, kRing, 1, S><<<gz, kBlockZ, smem, s>>>(fi, fo, h->args);
+        else k_step_z<true, kRing, 0, S><<<gz, kBlockZ, smem, s>>>(fi, fo, h->args);
       } else {
-        if (spec) k_step_z<false, kRing, true><<<gz, kBlockZ, smem, s>>>(fi, fo, h->args);
-        else k_step_z<false, kRing, false><<<gz, kBlockZ, smem, s>>>(fi, fo, h->args);
+        if (wm == 1) k_step_z<false, kRing, 1, S><<<gz, kBlockZ, smem, s>>>(fi, fo, h->args);
+        else k_step_z<false, kRing, 0, S><<<gz, kBlockZ, smem, s>>>(fi, fo, h->args);
       }
       return;
     } else {
@@ -1187,32 +1270,43 @@ int launch_moments(lesbgk *h, float *out, cudaStream_t s) {
 
 namespace lesbgk_internal {
 
-cudaError_t launch_init(const KArgs &A, int nr, int order, const double *fields, float *f, int sm_count,
+// (storage: LESBGK_F32, LESBGK_F16 or LESBGK_BF16, the 2D sets; A supplies the
+// 16-bit scale tables)
+cudaError_t launch_init(const KArgs &A, int nr, int order, int storage, const double *fields, void *f, int sm_count,
                         cudaStream_t s) {
   long long g = (A.plane + kBlock - 1) / kBlock;
   if (g > (long long)sm_count * 16) g = (long long)sm_count * 16;
   const unsigned grid = g < 1 ? 1u : (unsigned)g;
-  dispatch(nr, order, LESBGK_F32, 2, [&](auto r, auto n, auto, auto) {
-    k_init<decltype(r)::value, decltype(n)::value, float><<<grid, kBlock, 0, s>>>(fields, f, A);
+  dispatch(nr, order, storage, 2, [&](auto r, auto n, auto st, auto) {
+    using S = decltype(st);
+    if constexpr (!kIsComp<S>)
+      k_init<decltype(r)::value, decltype(n)::value, S><<<grid, kBlock, 0, s>>>(fields, static_cast<S *>(f), A);
   });
   return cudaGetLastError();
 }
 
-cudaError_t launch_moments(const KArgs &A, int nr, const float *f, float *out, double *partial, double *sums,
-                           cudaStream_t s) {
-  if (nr == 4) k_moments<4, float><<<kMomGrid, kMomBlock, 0, s>>>(f, out, partial, A.plane, A.plane, A);
-  else k_moments<6, float><<<kMomGrid, kMomBlock, 0, s>>>(f, out, partial, A.plane, A.plane, A);
+cudaError_t launch_moments(const KArgs &A, int nr, int order, int storage, const void *f, float *out,
+                           double *partial, double *sums, cudaStream_t s) {
+  dispatch(nr, order, storage, 2, [&](auto r, auto, auto st, auto) {
+    using S = decltype(st);
+    if constexpr (!kIsComp<S>)
+      k_moments<decltype(r)::value, S><<<kMomGrid, kMomBlock, 0, s>>>(static_cast<const S *>(f), out, partial,
+                                                                      A.plane, A.plane, A);
+  });
   k_reduce_partials<<<1, 128, 0, s>>>(partial, kMomGrid, sums);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ungroup(int nr, const float *f, float *out, long long cells, int sm_count, cudaStream_t s) {
+cudaError_t launch_ungroup(const KArgs &A, int nr, int order, int storage, const void *f, float *out,
+                           long long cells, int sm_count, cudaStream_t s) {
   long long g = (cells + kBlock - 1) / kBlock;
   if (g > (long long)sm_count * 16) g = (long long)sm_count * 16;
   const unsigned grid = g < 1 ? 1u : (unsigned)g;
-  const KArgs none{};  // FP32 storage needs no weights
-  if (nr == 4) k_ungroup<4, float><<<grid, kBlock, 0, s>>>(f, out, cells, none);
-  else k_ungroup<6, float><<<grid, kBlock, 0, s>>>(f, out, cells, none);
+  dispatch(nr, order, storage, 2, [&](auto r, auto, auto st, auto) {
+    using S = decltype(st);
+    if constexpr (!kIsComp<S>)
+      k_ungroup<decltype(r)::value, S><<<grid, kBlock, 0, s>>>(static_cast<const S *>(f), out, cells, A);
+  });
   return cudaGetLastError();
 }
 

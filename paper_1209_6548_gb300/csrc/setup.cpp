@@ -46,10 +46,6 @@ int check_params(const lesbgk_params *p) {
   if (p->dim != 0 && p->dim != 2 && p->dim != 3) return fail(LESBGK_EINVAL, "dim must be 2 or 3");
   if (p->dim == 3 && !((p->nroots == 4 && order == 3) || (p->nroots == 6 && order == 4)))
     return fail(LESBGK_EINVAL, "D = 3 is built as D3Q64 (nroots 4, order 3) and D3Q216 (nroots 6, order 4)");
-  if (p->dim == 3 && p->nroots == 6 && p->storage != LESBGK_F32)
-    return fail(LESBGK_EINVAL, "D3Q216 is built for FP32 storage");
-  if (p->dim == 3 && p->nroots == 6 && p->bc_x != LESBGK_PERIODIC)
-    return fail(LESBGK_EINVAL, "walls in x are not built for D3Q216");
   if (p->bc_y != LESBGK_PERIODIC && p->bc_y != LESBGK_DIFFUSE) return fail(LESBGK_EINVAL, "bad bc_y");
   if (p->bc_x != LESBGK_PERIODIC && p->bc_x != LESBGK_DIFFUSE) return fail(LESBGK_EINVAL, "bad bc_x");
   if (p->bc_x == LESBGK_DIFFUSE) {
@@ -184,7 +180,7 @@ int build_setup(const lesbgk_params &p, int order, const FieldStats *stats, Setu
   // the compensated storage's FP16 remainder holds lo 2^24 / w_a (|lo| is at
   // most half an FP32 ulp of the deviation: 2^-24 of it)
   const double store_scale = p.storage == LESBGK_F16 ? 1024.0 : (p.storage == LESBGK_F32C ? 16777216.0 : 1.0);
-  const int nzw = (p.dim == 3 && nr * nr * (nr / 2) <= kMaxQ) ? nr / 2 : 1;  // D3Q64: stored z-levels
+  const int nzw = p.dim == 3 ? nr / 2 : 1;  // stored z-levels
   for (int iz = 0; iz < nzw; ++iz)
     for (int ix = 0; ix < nr; ++ix)
       for (int iy = 0; iy < nr; ++iy) {
@@ -223,6 +219,7 @@ int build_setup(const lesbgk_params &p, int order, const FieldStats *stats, Setu
   h->wall_T_freq = p.wall_T_freq;
   h->wall_Tx[0] = p.wall_Tx[0];
   h->wall_Tx[1] = p.wall_Tx[1];
+  if (p.wall_T_amp != 0.0) heat_poly(h);
   set_wall_time(*h, 0.0, &h->args);
   A.xwalls = xw ? 1 : 0;
   if (xw) x_wall_tables(*h, &h->args);
@@ -239,13 +236,12 @@ void x_wall_tables(const Setup &h, KArgs *out) {
   const double *c = h.c, *w = h.w;
   const double fact[kMaxOrder + 1] = {1, 1, 2, 6, 24};
   const int nz = h.dim == 3 ? H : 1;
-  if (nz * nr * nr > kMaxQ) return;  // (walls in x are refused for such sets by check_params)
   for (int s = 0; s < 2; ++s) {
     double e[kMaxOrder + 1][kMaxOrder + 1];
     const double th = h.wall_Tx[s] - 1.0;
     gaussian_hermite_moments(N, 1.0, 0.0, 0.0, th, 0.0, th, e);
     const double zf[kMaxOrder + 1] = {1.0, 0.0, th, 0.0, 3.0 * th * th};
-    double S[kMaxQ];
+    double S[kMaxWQ];
     double A_out = 0.0, Z_out = 0.0;
     for (int iz = 0; iz < nz; ++iz)
       for (int ix = 0; ix < nr; ++ix)
@@ -291,25 +287,24 @@ void x_wall_tables(const Setup &h, KArgs *out) {
   }
 }
 
-void set_wall_time(const Setup &h, double t, KArgs *out) {
+namespace {
+
+// Wall equilibria S_a(T_w + heat, u_w) of wall s at order N (b = 0 Gaussian
+// projection) per stored population, in FP64; in D = 3 the z-factor of the
+// isotropic Gaussian's coefficients is E[He_l(Z)] = 1, th, 3 th^2 for l = 0,
+// 2, 4 (Z ~ N(0, T_w), u_z = 0).  The D = 3 sets store the z-even half:
+// levels c_z = c[nr/2 + iz] > 0.
+void wall_equilibrium(const Setup &h, double heat, int s, double *S) {
   using namespace lesbgk_tables;
-  KArgs &A = *out;
   const int nr = h.nroots, N = h.order;
   const double *c = h.c, *w = h.w;
   const double fact[kMaxOrder + 1] = {1, 1, 2, 6, 24};
-  const double heat = h.wall_T_amp != 0.0 ? h.wall_T_amp * std::sin(h.wall_T_freq * t) : 0.0;
-  // D = 3 stores the z-even half: levels c_z = c[nr/2 + iz] > 0
   const int nz = h.dim == 3 ? nr / 2 : 1;
-  // wall equilibria S_a(T_w, u_w) at order N (b = 0 Gaussian projection); in
-  // D = 3 the z-factor of the isotropic Gaussian's coefficients is
-  // E[He_l(Z)] = 1, th, 3 th^2 for l = 0, 2, 4 (Z ~ N(0, T_w), u_z = 0)
-  for (int s = 0; s < 2; ++s) {
-    double e[kMaxOrder + 1][kMaxOrder + 1];
-    const double th = h.wall_T[s] + heat - 1.0;
-    gaussian_hermite_moments(N, 1.0, h.wall_ux[s], 0.0, th, 0.0, th, e);
-    const double zf[kMaxOrder + 1] = {1.0, 0.0, th, 0.0, 3.0 * th * th};
-    double A_out = 0.0, Z_out = 0.0;
-    for (int iz = 0; iz < nz; ++iz)
+  double e[kMaxOrder + 1][kMaxOrder + 1];
+  const double th = h.wall_T[s] + heat - 1.0;
+  gaussian_hermite_moments(N, 1.0, h.wall_ux[s], 0.0, th, 0.0, th, e);
+  const double zf[kMaxOrder + 1] = {1.0, 0.0, th, 0.0, 3.0 * th * th};
+  for (int iz = 0; iz < nz; ++iz)
     for (int ix = 0; ix < nr; ++ix) {
       double hx[kMaxOrder + 1], hz[kMaxOrder + 1];
       hermite_values(kMaxOrder, c[ix], hx);
@@ -328,15 +323,88 @@ void set_wall_time(const Setup &h, double t, KArgs *out) {
               sum += e[m][k] * zf[l] * hx[m] * hy[k] * hz[l] / (fact[m] * fact[k] * fact[l]);
           }
         const double wa = w[ix] * w[iy] * (h.dim == 3 ? w[nr / 2 + iz] : 1.0);
-        const double S = wa * sum;
-        const int a = (iz * nr + ix) * nr + iy;
-        A.wS[s][a] = (float)S;
-        A.wSdev[s][a] = (float)(S - wa);
-        const bool outgoing = (s == 0) ? (c[iy] > 0.0) : (c[iy] < 0.0);
-        if (outgoing) {
-          A_out += std::fabs(c[iy]) * (S - wa);
-          Z_out += std::fabs(c[iy]) * S;
+        S[(iz * nr + ix) * nr + iy] = wa * sum;
+      }
+    }
+}
+
+int stored_q(const Setup &h) { return h.nroots * h.nroots * (h.dim == 3 ? h.nroots / 2 : 1); }
+
+double stored_w(const Setup &h, int a) {
+  const int nr = h.nroots, iy = a % nr, ix = (a / nr) % nr, iz = a / (nr * nr);
+  return h.w[ix] * h.w[iy] * (h.dim == 3 ? h.w[nr / 2 + iz] : 1.0);
+}
+
+bool outgoing_y(const Setup &h, int s, int a) {
+  const double cy = h.c[a % h.nroots];
+  return s == 0 ? cy > 0.0 : cy < 0.0;
+}
+
+}  // namespace
+
+void heat_poly(Setup *h) {
+  HeatPoly &P = h->heat;
+  std::memset(&P, 0, sizeof P);
+  P.amp = h->wall_T_amp;
+  P.freq = h->wall_T_freq;
+  P.dt = h->dt;
+  const int q = stored_q(*h);
+  for (int a = 0; a < q; ++a) P.w[a] = stored_w(*h, a);
+  // the polynomial through heat = -1, 0, 1 (exact for degree 2)
+  for (int s = 0; s < 2; ++s) {
+    double Sm[kMaxWQ], S0[kMaxWQ], Sp[kMaxWQ];
+    wall_equilibrium(*h, -1.0, s, Sm);
+    wall_equilibrium(*h, 0.0, s, S0);
+    wall_equilibrium(*h, 1.0, s, Sp);
+    for (int a = 0; a < q; ++a) {
+      P.S[s][0][a] = S0[a];
+      P.S[s][1][a] = 0.5 * (Sp[a] - Sm[a]);
+      P.S[s][2][a] = 0.5 * (Sp[a] + Sm[a]) - S0[a];
+    }
+    for (int k = 0; k < 3; ++k) {
+      double ao = 0.0, zo = 0.0;
+      for (int a = 0; a < q; ++a)
+        if (outgoing_y(*h, s, a)) {
+          const double cn = std::fabs(h->c[a % h->nroots]);
+          ao += cn * (k == 0 ? P.S[s][0][a] - P.w[a] : P.S[s][k][a]);
+          zo += cn * P.S[s][k][a];
         }
+      P.Aout[s][k] = ao;
+      P.Zout[s][k] = zo;
+    }
+  }
+}
+
+void set_wall_time(const Setup &h, double t, KArgs *out) {
+  KArgs &A = *out;
+  const int q = stored_q(h);
+  if (h.wall_T_amp != 0.0) {  // heated: the polynomial tables at h = amp sin(freq t)
+    const HeatPoly &P = h.heat;
+    const double hv = wall_heating(P, t);
+    for (int s = 0; s < 2; ++s) {
+      for (int a = 0; a < q; ++a) {
+        const double S = std::fma(std::fma(P.S[s][2][a], hv, P.S[s][1][a]), hv, P.S[s][0][a]);
+        A.wS[s][a] = (float)S;
+        A.wSdev[s][a] = (float)(S - P.w[a]);
+      }
+      const double ao = std::fma(std::fma(P.Aout[s][2], hv, P.Aout[s][1]), hv, P.Aout[s][0]);
+      const double zo = std::fma(std::fma(P.Zout[s][2], hv, P.Zout[s][1]), hv, P.Zout[s][0]);
+      A.wA[s] = (float)ao;
+      A.wB[s] = (float)(1.0 / zo);
+    }
+    return;
+  }
+  for (int s = 0; s < 2; ++s) {
+    double S[kMaxWQ];
+    wall_equilibrium(h, 0.0, s, S);
+    double A_out = 0.0, Z_out = 0.0;
+    for (int a = 0; a < q; ++a) {
+      const double wa = stored_w(h, a);
+      A.wS[s][a] = (float)S[a];
+      A.wSdev[s][a] = (float)(S[a] - wa);
+      if (outgoing_y(h, s, a)) {
+        A_out += std::fabs(h.c[a % h.nroots]) * (S[a] - wa);
+        Z_out += std::fabs(h.c[a % h.nroots]) * S[a];
       }
     }
     A.wA[s] = (float)A_out;

@@ -146,8 +146,7 @@ def serving_mix(n: int, seed: int = 0, q36_share: float = 0.2, ny_hi: int = 512,
 def fits_batch(prob, nx: int) -> bool:
     """Whether the batched solver takes this problem (the library's own
     admission checks say the same)."""
-    return (prob.nx == nx and getattr(prob, "bc_x", I.PERIODIC) == I.PERIODIC and getattr(prob, "dim", 2) == 2
-            and prob.wall_T_amp == 0.0)
+    return prob.nx == nx and getattr(prob, "bc_x", I.PERIODIC) == I.PERIODIC and getattr(prob, "dim", 2) == 2
 
 
 class WideLane:

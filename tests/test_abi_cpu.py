@@ -61,9 +61,9 @@ def test_struct_sizes_match_header(lib):
     (dict(wall_T_amp=float("nan")), L.EINVAL),
     (dict(dim=4), L.EINVAL),
     (dict(dim=3, nroots=6, order=3), L.EINVAL),           # D = 3: D3Q64 N = 3, D3Q216 N = 4
-    (dict(dim=3, nroots=6, bc_x=L.DIFFUSE), L.EINVAL),    # no walls in x on D3Q216
+    (dict(dim=3, nroots=6, bc_x=L.DIFFUSE, storage=L.F16), L.EINVAL),  # walls in x: FP32 storage
     (dict(dim=3, order=4), L.EINVAL),
-    (dict(dim=3, nroots=6, storage=L.F16), L.EINVAL),     # D3Q216: FP32 only
+    (dict(dim=3, nroots=6, storage=L.F32C), L.EINVAL),    # compensated storage: D2Q16 and D3Q64
     (dict(bc_x=2), L.EINVAL),
     (dict(nx=65536, ny=32768, bc_y=L.PERIODIC), L.EINVAL),  # 2^31 nodes
     (dict(bc_x=L.DIFFUSE, nx=1), L.EINVAL),              # walls in x need two columns

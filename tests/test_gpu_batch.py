@@ -25,8 +25,9 @@ def _built():
 
 
 def mixed_problems(nx=4, n=10, seed=3, with_q36=True):
-    """The channel mix, a quarter on D2Q36 and every third with Maxwell walls
-    (specular share 0.3, Sec. 3.2)."""
+    """The channel mix, a quarter on D2Q36, every third with Maxwell walls
+    (specular share 0.3, Sec. 3.2) and every fifth with heated walls (Sec. 4.2:
+    T_w = wall_T + 0.02 sin(St t), St = pi sqrt(2)/8)."""
     probs = I.batch_mix(n=n, seed=seed, ny_lo=16, ny_hi=200)
     out = []
     for k, p in enumerate(probs):
@@ -35,6 +36,9 @@ def mixed_problems(nx=4, n=10, seed=3, with_q36=True):
             kw["nroots"] = 6
         if k % 3 == 1:
             kw["wall_specular"] = 0.3
+        if k % 5 == 2:
+            kw["wall_T_amp"] = 0.02
+            kw["wall_T_freq"] = np.pi * np.sqrt(2.0) / 8.0
         from dataclasses import replace
         out.append(replace(p, **kw))
     return out
@@ -151,12 +155,73 @@ def test_batch_slot_matches_oracle():
     assert all(v["ok"] for v in errs.values()), errs
 
 
+@pytest.mark.parametrize("spec", [0.0, 0.3])
+def test_heated_slot_matches_oracle(spec):
+    """Heated walls (Sec. 4.2) in a batch slot, admitted after the batch has
+    stepped an odd number of times (its clock starts at its own admission),
+    against the FP64 oracle within the derived bound."""
+    from dataclasses import replace
+    prob = replace(I.unsteady_heating(kn=0.1, amp=0.02, ny=40), wall_specular=spec)
+    other = I.Problem(name="c", nx=4, ny=24, kn=0.2, b=-0.5, wall_ux=(-0.05, 0.05))
+    bt = L.Batch(capacity=4, nx=4, pool_bytes=pool_for([prob, other]))
+    bt.add(L.params_from_problem(other))
+    bt.step(5)
+    s = bt.add(L.params_from_problem(prob))
+    bt.step(300)
+    assert bt.info(s).steps_done == 300
+    dt = time_step(prob)
+    op = oracle_params(prob, dt)
+    f0 = O.init(op)
+    f = O.run(op, f0, 300)
+    ref, _ = O.moments(op, f)
+    errs = field_errors(bt.moments(s).cpu().numpy(), ref, rounding_bound([f0, f], prob.nroots, prob.dim, 300,
+                                                                         "f32", prob, dt))
+    record(f"batch heated spec {spec}", errs)
+    assert all(v["ok"] for v in errs.values()), errs
+
+
+@pytest.mark.parametrize("storage", [L.F16, L.BF16])
+def test_16bit_slots_equal_alone_bitwise(storage):
+    """FP16/BF16 slots beside FP32 ones (a class of their own per velocity set:
+    one launch per class and step) give bitwise the populations of the
+    single-domain solver in the same storage -- the stochastic rounding keyed
+    by the instance's own step count and row -- through graph replays and
+    direct steps, a slot admitted after an odd number of steps, heated walls,
+    add_many and moments_many."""
+    import torch
+    probs = mixed_problems(n=10, seed=11)
+    params = []
+    for k, p in enumerate(probs):
+        q = L.params_from_problem(p)
+        if k % 2 == 0 and p.wall_specular == 0.0:  # (Maxwell walls take FP32 storage)
+            q.storage = storage
+        params.append(q)
+    assert sum(q.storage == storage for q in params) >= 3
+    assert any(q.storage == storage and q.wall_T_amp != 0.0 for q in params)
+    bt = L.Batch(capacity=16, nx=4, pool_bytes=sum(L.batch_slot_bytes(q) for q in params) + (1 << 20))
+    slots = bt.add_many(params[:-2])
+    bt.step(7)
+    late = [bt.add(q) for q in params[-2:]]  # admitted at buffer parity 1
+    bt.step(64 * 2 + 5)
+    for q, sl, n in zip(params, slots + late, [140] * (len(params) - 2) + [133, 133]):
+        ref = L.Solver(q)
+        ref.step(n)
+        assert bt.info(sl).steps_done == n
+        assert bool((bt.populations(sl) == ref.populations()).all()), (q.storage, q.ny)
+        outs = [torch.empty((9, q.ny, q.nx), dtype=torch.float32, device="cuda")]
+        bt.moments_many([sl], outs)
+        assert bool((outs[0] == ref.moments()).all())
+        ref.close()
+
+
 def test_mismatched_nx_rejected():
     bt = L.Batch(capacity=2, nx=4, pool_bytes=1 << 20)
     with pytest.raises(L.LesbgkError):
         bt.add(L.make_params(nx=8, ny=16, kn=0.1, b=0.0))
     with pytest.raises(L.LesbgkError):
         bt.add(L.make_params(nx=4, ny=16, kn=0.1, b=0.0, nroots=4, order=4))
+    with pytest.raises(L.LesbgkError):
+        bt.add(L.make_params(nx=4, ny=16, kn=0.1, b=0.0, storage=L.F32C))
 
 
 def test_add_many_and_moments_many_match_the_per_slot_calls():
@@ -166,7 +231,8 @@ def test_add_many_and_moments_many_match_the_per_slot_calls():
     lesbgk_batch_moments, bitwise."""
     import torch
     probs = I.batch_mix(n=40, seed=3, ny_hi=128) + [I.Problem(name="q36", nroots=6, nx=4, ny=33, kn=0.1, b=0.5,
-                                                             wall_ux=(-0.05, 0.05))]
+                                                             wall_ux=(-0.05, 0.05)),
+                                                   I.unsteady_heating(kn=0.2, amp=0.02, ny=30)]
     params = [L.params_from_problem(p) for p in probs]
     # rough in y only: the mix runs the printed (unsplit) update, unstable for
     # fields that vary in x and y (the library's documented reading)

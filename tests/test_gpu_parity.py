@@ -513,7 +513,7 @@ def test_high_mach_workloads(kind, nroots, dim):
 
 
 # ---------------------------------------------------------------- walls in x (cavity)
-@pytest.mark.parametrize("nroots,dim", [(4, 2), (6, 2), (4, 3)])
+@pytest.mark.parametrize("nroots,dim", [(4, 2), (6, 2), (4, 3), (6, 3)])
 def test_lid_driven_cavity(nroots, dim):
     """Lid-driven cavity (walls on all sides, corners, lid at 0.05), split
     scheme, on a grid that spans two warp strips with a ragged tail."""
@@ -525,7 +525,7 @@ def test_lid_driven_cavity(nroots, dim):
     assert np.max(np.abs(res[-1][2][2])) > 1e-3  # the lid set up a vortex
 
 
-@pytest.mark.parametrize("nroots,dim", [(4, 2), (6, 2), (4, 3)])
+@pytest.mark.parametrize("nroots,dim", [(4, 2), (6, 2), (4, 3), (6, 3)])
 @pytest.mark.parametrize("scheme", [I.UNSPLIT, I.SPLIT])
 def test_walls_in_x_rough(scheme, nroots, dim):
     """Rough fields in a box with heated walls on all sides and a lid, and in
@@ -616,7 +616,7 @@ def test_collisionless_limit_and_zero_steps():
 
 
 # ---------------------------------------------------------------- residual
-@pytest.mark.parametrize("nroots,dim", [(4, 2), (6, 2), (4, 3)])
+@pytest.mark.parametrize("nroots,dim", [(4, 2), (6, 2), (4, 3), (6, 3)])
 def test_residual_against_the_moment_fields(nroots, dim):
     """lesbgk_residual equals max over nodes of |d rho| + |d u| + |d T| of the
     moment fields, per unit time; the first call only takes the snapshot."""

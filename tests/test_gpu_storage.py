@@ -19,7 +19,7 @@ from tests.common import field_errors, oracle_params, record, rounding_bound, ti
 
 pytestmark = pytest.mark.gpu
 
-STORE = {L.F16: "f16", L.BF16: "bf16"}
+STORE = {L.F16: "f16", L.BF16: "bf16", L.F32: "f32"}
 
 
 def assert_within_bound(gpu_moments, prob, op, states, n, storage, what):
@@ -142,6 +142,36 @@ def test_d3q64_16bit(storage):
                         f"d3q64 rough {STORE[storage]}")
 
 
+@pytest.mark.parametrize("storage", [L.F16, L.BF16])
+def test_d3q216_16bit(storage):
+    """16-bit storage of the D3Q216 set (108 stored values per node over three
+    level warps, each level's scale factors and random words those of the
+    one-thread layout): a Couette channel, rough periodic fields and rough
+    fields between moving walls at two temperatures with a body force against
+    the 216-velocity oracle within the storage's bound."""
+    from dataclasses import replace
+    prob = replace(I.couette_4x64(), dim=3, nroots=6)
+    dt = time_step(prob)
+    s = solver(prob, storage, dt=dt)
+    s.step(400)
+    op = oracle_params(prob, dt)
+    f0 = O.init(op)
+    assert_within_bound(s.moments().cpu().numpy(), prob, op, [f0, O.run(op, f0, 400)], 400, storage,
+                        f"d3q216 couette {STORE[storage]}")
+    for prob in (I.Problem(name="r", nroots=6, dim=3, nx=60, ny=33, bc_y=I.PERIODIC, kn=0.05, b=-0.5,
+                           scheme=I.SPLIT),
+                 I.Problem(name="wf", nroots=6, dim=3, nx=40, ny=30, bc_y=I.DIFFUSE, kn=0.1, b=0.5,
+                           wall_ux=(-0.05, 0.05), wall_T=(0.97, 1.04), g=(1e-3, 0.0))):
+        fields = I.random_fields(prob, seed=3, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
+        dt = time_step(prob, fields)
+        s = solver(prob, storage, fields, dt)
+        s.step(8)
+        op = oracle_params(prob, dt)
+        f0 = O.init(op, fields)
+        assert_within_bound(s.moments().cpu().numpy(), prob, op, [f0, O.run(op, f0, 8)], 8, storage,
+                            f"d3q216 {prob.name} {STORE[storage]}")
+
+
 # ---------------------------------------------------------------- compensated FP32 (hi + lo)
 @pytest.mark.parametrize("dim", [2, 3])
 @pytest.mark.parametrize("scheme", [I.UNSPLIT, I.SPLIT])
@@ -206,12 +236,13 @@ def test_compensated_populations_round_trip_and_checkpoint():
     assert s.populations().dtype == torch.float32
 
 
-@pytest.mark.parametrize("storage", [L.F16, L.BF16, L.F32C])
-def test_launch_shape_does_not_change_bits(storage):
+@pytest.mark.parametrize("storage,nroots,dim", [(L.F16, 4, 2), (L.BF16, 4, 2), (L.F32C, 4, 2), (L.F32, 6, 3),
+                                                (L.F16, 6, 3), (L.BF16, 6, 3)])
+def test_launch_shape_does_not_change_bits(storage, nroots, dim):
     """Rows per segment change where a warp's prologue loads rows directly and
     where its ring carries them; the result must not depend on it."""
-    prob = I.Problem(name="shape", nx=64, ny=70, bc_y=I.DIFFUSE, kn=0.05, b=0.5, wall_ux=(-0.05, 0.05),
-                     g=(1e-3, 0.0), scheme=I.SPLIT)
+    prob = I.Problem(name="shape", nroots=nroots, dim=dim, nx=64, ny=70, bc_y=I.DIFFUSE, kn=0.05, b=0.5,
+                     wall_ux=(-0.05, 0.05), g=(1e-3, 0.0), scheme=I.SPLIT)
     fields = I.random_fields(prob, seed=5, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
     dt = time_step(prob, fields)
     outs = []
