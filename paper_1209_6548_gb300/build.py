@@ -34,7 +34,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "lesbgk.h")]
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "lesbgk.h"), __file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
@@ -42,7 +42,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    common = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", f"-I{INCLUDE}"]
+    # host code without contraction of a*b+c into FMAs: the FP64 set-up
+    # tables are then the same bits on x86 and Arm hosts (GCC contracts by
+    # default where the ISA has FMA)
+    common = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+              f"-I{INCLUDE}"]
     if verbose:
         common += ["-Xptxas", "-v"]
 
