@@ -33,11 +33,16 @@ time since the previous check) and m the solve's total mass at each check:
   - max_steps: the cap.
 
 Solves that the batch cannot hold (another width, walls in x such as the
-lid-driven cavities of the mix, the D = 3 set, heated walls) go
-to a wide lane: each runs as a single-domain solver on its own CUDA stream,
+lid-driven cavities of the mix, the D = 3 set) go to a wide lane: each runs as a single-domain solver on its own CUDA stream,
 so they advance concurrently with the batch; the lane admits them in arrival
 order while its own device-memory budget has room, and checks them with the
 same residual and criterion (lesbgk_residual, one kernel per check).
+
+A request may carry a deadline (seconds after its arrival): one still queued
+or running past it ends as "timed_out", its slot or solver freed at the next
+check; ServingLoop.cancel(rid) ends one the same way ("cancelled").  A
+problem the library refuses ends as "rejected"; a full pool or lane budget
+only keeps requests waiting.
 
 Everything on the device runs in the library's kernels; this module is the
 scheduler (host bookkeeping only).
@@ -63,9 +68,11 @@ class Request:
     completed: float = float("nan")
     steps: int = 0
     residual: float = float("nan")
-    status: str = "pending"  # pending, running, converged, steady_drift, max_steps, diverged, rejected
+    status: str = "pending"  # pending, running, converged, steady_drift, max_steps, diverged, rejected,
+    #                          timed_out, cancelled
     error: str = ""          # why a request was rejected or diverged
     moments: object = None   # (9, ny, nx) float32 device tensor when kept
+    deadline: float = float("inf")  # seconds after arrival by which it must be done
 
 
 SOLVED = ("converged", "steady_drift")
@@ -220,6 +227,12 @@ class ServingLoop:
         self.check_every = check_every
         self.conv = conv or Convergence()
         self.keep_moments = keep_moments
+        self._cancel = set()
+
+    def cancel(self, rid: int) -> None:
+        """End request rid at the loop's next pass (queued: dropped; running:
+        its slot or solver freed), with status "cancelled"."""
+        self._cancel.add(rid)
 
     def run(self, requests, clock=time.perf_counter):
         bt, wide = self.batch, self.wide
@@ -239,11 +252,40 @@ class ServingLoop:
             req.admitted = clock() - t0
             finish(req, "rejected", float("nan"), req.admitted)
 
+        def ended(req, now):  # cancelled or past its deadline: the status to end with, else None
+            if req.rid in self._cancel:
+                return "cancelled"
+            return "timed_out" if now > req.arrival + req.deadline else None
+
+        def drop_ended(now):
+            for q in (pending, waiting, waiting_wide):
+                for req in [r for r in q if r.arrival <= now and ended(r, now)]:
+                    q.remove(req)
+                    finish(req, ended(req, now), float("nan"), now)
+            for slot in list(active):
+                req, hist, _ = active[slot]
+                v = ended(req, now)
+                if v:
+                    req.steps = bt.info(slot).steps_done
+                    bt.remove(slot)
+                    del active[slot]
+                    finish(req, v, hist[-1] if hist else float("nan"), now)
+            for key in list(wide.active):
+                req = wide.active[key][0]
+                v = ended(req, now)
+                if v:
+                    hist = wide.active[key][4][0]
+                    wide.retire(key, False)
+                    finish(req, v, hist[-1] if hist else float("nan"), now)
+
         while pending or waiting or waiting_wide or active or wide.active:
             now = clock() - t0
+            drop_ended(now)
             while pending and pending[0].arrival <= now:
                 req = pending.popleft()
                 (waiting if fits_batch(req.problem, self.nx) else waiting_wide).append(req)
+            if not (pending or waiting or waiting_wide or active or wide.active):
+                break
             while waiting:  # FIFO admission while the pool has room
                 req = waiting[0]
                 try:

@@ -1,11 +1,13 @@
 """Host-side logic of the serving loop (no GPU): the convergence verdict, the
-eviction of diverged solves (driven through a fake batch), and the seeded
-arrival trace."""
+eviction of diverged solves, and faults injected on the host through a fake
+batch -- a full pool at admission, a problem the library refuses, a deadline
+passed, requests cancelled -- and the seeded arrival trace."""
 from __future__ import annotations
 
 import numpy as np
 
 from paper_1209_6548_gb300 import inputs as I
+from paper_1209_6548_gb300 import lesbgk as L
 from paper_1209_6548_gb300 import serve as S
 
 
@@ -153,3 +155,112 @@ def test_serving_mix_cavities_go_to_the_wide_lane():
     assert all(p.nx == p.ny == 256 and p.wall_ux == (0.0, 0.05) and 0.05 <= p.kn <= 0.5 for p in cav)
     assert all(not S.fits_batch(p, 4) for p in cav)
     assert all(S.fits_batch(p, 4) for p in probs if p.bc_x == 0)
+
+
+# ---------------------------------------------------------------- faults injected on the host
+def converging(steps, checks):
+    return (np.nan if checks == 0 else 1e-3 * np.exp(-steps / 300.0)), 128.0
+
+
+def never_settling(steps, checks):
+    return (np.nan if checks == 0 else 1e-3), 128.0  # r stays at 1e-3 with no mass drift: never steady
+
+
+class TickClock:
+    """A clock that advances `dt` seconds per reading (deterministic time)."""
+
+    def __init__(self, dt):
+        self.t, self.dt = 0.0, dt
+
+    def __call__(self):
+        self.t += self.dt
+        return self.t
+
+
+def test_full_pool_keeps_requests_waiting_then_admits_them():
+    """A batch that refuses admission (the pool full: try_add returns None)
+    for its first calls: requests wait, none is lost or rejected, and they are
+    admitted once it has room, in arrival order."""
+    probs = [I.Problem(name=f"c{k}", nx=4, ny=32) for k in range(4)]
+    reqs = [S.Request(rid=k, arrival=0.0, problem=p) for k, p in enumerate(probs)]
+
+    class FullAtFirst(FakeBatch):
+        refusals = 5
+
+        def try_add(self, p):
+            if self.refusals:
+                self.refusals -= 1
+                return None
+            return super().try_add(p)
+
+    fb = FullAtFirst(1, {p.name: converging for p in probs})
+    fb._names = [p.name for p in probs]
+    loop = S.ServingLoop(capacity=1, pool_bytes=0, check_every=128, batch=fb, wide=NoWide(),
+                         conv=S.Convergence(rtol=1e-8, max_steps=100_000))
+    done = loop.run(reqs, clock=TickClock(1e-3))
+    assert [r.problem.name for r in done] == ["c0", "c1", "c2", "c3"]  # one slot: in arrival order
+    assert all(r.status == "converged" for r in done)
+    assert [n for n, _ in fb.removed] == ["c0", "c1", "c2", "c3"]
+
+
+def test_a_refused_problem_is_rejected_alone():
+    probs = [I.Problem(name=n, nx=4, ny=32) for n in ("a", "bad", "b")]
+    reqs = [S.Request(rid=k, arrival=0.0, problem=p) for k, p in enumerate(probs)]
+
+    class Refusing(FakeBatch):
+        def try_add(self, p):
+            if self._names[0] == "bad":
+                self._names.pop(0)
+                raise L.LesbgkError(L.EINVAL, "refused")
+            return super().try_add(p)
+
+    fb = Refusing(4, {n: converging for n in ("a", "b")})
+    fb._names = [p.name for p in probs]
+    loop = S.ServingLoop(capacity=4, pool_bytes=0, check_every=128, batch=fb, wide=NoWide(),
+                         conv=S.Convergence(rtol=1e-8, max_steps=100_000))
+    done = loop.run(reqs, clock=TickClock(1e-3))
+    status = {r.problem.name: r.status for r in done}
+    assert status == {"a": "converged", "bad": "rejected", "b": "converged"}
+    assert next(r for r in done if r.problem.name == "bad").error
+
+
+def test_deadline_ends_a_running_solve_and_frees_its_slot():
+    """A request that cannot settle before its deadline ends as timed_out at
+    the next check past it, its slot released; the others finish."""
+    probs = [I.Problem(name=n, nx=4, ny=32) for n in ("slow", "ok0", "ok1")]
+    reqs = [S.Request(rid=0, arrival=0.0, problem=probs[0], deadline=0.05),
+            S.Request(rid=1, arrival=0.0, problem=probs[1]), S.Request(rid=2, arrival=0.0, problem=probs[2])]
+    fb = FakeBatch(2, {"slow": never_settling, "ok0": converging, "ok1": converging})
+    fb._names = [p.name for p in probs]
+    loop = S.ServingLoop(capacity=2, pool_bytes=0, check_every=128, batch=fb, wide=NoWide(),
+                         conv=S.Convergence(rtol=1e-8, max_steps=10_000_000))
+    done = loop.run(reqs, clock=TickClock(1e-3))
+    status = {r.problem.name: r.status for r in done}
+    assert status == {"slow": "timed_out", "ok0": "converged", "ok1": "converged"}
+    slow = next(r for r in done if r.problem.name == "slow")
+    assert 0.05 < slow.completed < 0.2 and slow.steps > 0
+    assert any(n == "slow" for n, _ in fb.removed)
+
+
+def test_cancel_ends_a_running_and_a_queued_request():
+    """ServingLoop.cancel(rid): a running solve is removed from the batch at
+    the next pass, a queued one never starts; the rest are unaffected."""
+    probs = [I.Problem(name=n, nx=4, ny=32) for n in ("run", "queued", "ok")]
+    reqs = [S.Request(rid=k, arrival=0.0, problem=p) for k, p in enumerate(probs)]
+    fb = FakeBatch(1, {"run": never_settling, "queued": converging, "ok": converging})
+    fb._names = [p.name for p in probs]
+    loop = S.ServingLoop(capacity=1, pool_bytes=0, check_every=128, batch=fb, wide=NoWide(),
+                         conv=S.Convergence(rtol=1e-8, max_steps=10_000_000))
+    step0 = fb.step
+
+    def step(n):  # the caller cancels two requests while "run" is on the GPU
+        step0(n)
+        if fb.slots.get(0, [None])[0] == "run" and fb.slots[0][1] >= 1280:
+            loop.cancel(0)
+            loop.cancel(1)
+    fb.step = step
+    fb._names = ["run", "ok"]  # "queued" is dropped before it reaches the batch
+    done = loop.run(reqs, clock=TickClock(1e-3))
+    status = {r.problem.name: r.status for r in done}
+    assert status == {"run": "cancelled", "queued": "cancelled", "ok": "converged"}
+    assert [n for n, _ in fb.removed] == ["run", "ok"]
