@@ -1154,6 +1154,7 @@ void release_slot(lesbgk_batch *b, int slot) {
 
 extern "C" int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const double *h_init, void *stream,
                                 int32_t *slot_out) {
+  lesbgk_internal::Range range_("lesbgk_batch_add");
   if (!b || !slot_out) return fail(LESBGK_EINVAL, "NULL argument");
   int slot = -1;
   if (int rc = prepare_slot(b, p, h_init, &slot)) return rc;
@@ -1185,6 +1186,7 @@ extern "C" int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const d
 
 extern "C" int lesbgk_batch_add_many(lesbgk_batch *b, int32_t n, const lesbgk_params *ps,
                                      const double *const *h_inits, void *stream, int32_t *slots_out) {
+  lesbgk_internal::Range range_("lesbgk_batch_add_many");
   if (!b || n < 0 || (n && (!ps || !slots_out))) return fail(LESBGK_EINVAL, "NULL argument");
   std::vector<int> taken;
   taken.reserve(n);
@@ -1265,6 +1267,7 @@ extern "C" int lesbgk_batch_remove(lesbgk_batch *b, int32_t slot, void *stream) 
 }
 
 extern "C" int lesbgk_batch_step(lesbgk_batch *b, int64_t nsteps, void *stream) {
+  lesbgk_internal::Range range_("lesbgk_batch_step");
   if (!b) return fail(LESBGK_EINVAL, "batch is NULL");
   if (nsteps < 0) return fail(LESBGK_EINVAL, "nsteps < 0");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1300,6 +1303,7 @@ extern "C" int lesbgk_batch_step(lesbgk_batch *b, int64_t nsteps, void *stream) 
 }
 
 extern "C" int lesbgk_batch_residuals(lesbgk_batch *b, double *h_res, double *h_mass, void *stream) {
+  lesbgk_internal::Range range_("lesbgk_batch_residuals");
   if (!b || !h_res) return fail(LESBGK_EINVAL, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (int rc = ensure_items(b, s)) return rc;
@@ -1356,6 +1360,7 @@ extern "C" int lesbgk_batch_moments(lesbgk_batch *b, int32_t slot, float *d_out,
 
 extern "C" int lesbgk_batch_moments_many(lesbgk_batch *b, int32_t n, const int32_t *slots, float *const *d_outs,
                                          void *stream) {
+  lesbgk_internal::Range range_("lesbgk_batch_moments_many");
   if (!b || n < 0 || (n && (!slots || !d_outs))) return fail(LESBGK_EINVAL, "NULL argument");
   std::vector<float *> outs(b->capacity, nullptr);
   for (int i = 0; i < n; ++i) {
@@ -1443,6 +1448,7 @@ extern "C" int lesbgk_batch_get_launch(const lesbgk_batch *b, int32_t *rows, int
 
 extern "C" int lesbgk_batch_autotune(lesbgk_batch *b, const int32_t *candidates, int32_t n, int32_t *chosen,
                                      void *stream) {
+  lesbgk_internal::Range range_("lesbgk_batch_autotune");
   if (!b || !candidates || n < 1) return fail(LESBGK_EINVAL, "bad autotune arguments");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaStream_t s2 = nullptr;

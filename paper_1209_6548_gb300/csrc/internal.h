@@ -3,10 +3,21 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "setup.h"
 
 namespace lesbgk_internal {
+
+// An NVTX range around one library call (named after the entry point), so
+// that a profiler's timeline (nsys, ncu --nvtx) shows which call issued which
+// kernels; without a tool attached a push or pop is a no-op call.
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range &) = delete;
+  Range &operator=(const Range &) = delete;
+};
 
 using lesbgk_setup::KArgs;
 

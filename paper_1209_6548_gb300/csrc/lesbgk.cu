@@ -1314,6 +1314,7 @@ cudaError_t launch_ungroup(const KArgs &A, int nr, int order, int storage, const
 
 extern "C" int lesbgk_create(const lesbgk_params *p, void *d_workspace, size_t bytes, const double *h_init,
                              void *stream, lesbgk **out) {
+  lesbgk_internal::Range range_("lesbgk_create");
   clear_error();
   if (int rc = check_params(p)) return rc;
   if (!out) return fail(LESBGK_EINVAL, "out is NULL");
@@ -1405,6 +1406,7 @@ extern "C" int lesbgk_reinit(lesbgk *h, const double *d_fields, void *stream) {
 }
 
 extern "C" int lesbgk_step(lesbgk *h, int64_t nsteps, void *stream) {
+  lesbgk_internal::Range range_("lesbgk_step");
   if (!h) return fail(LESBGK_EINVAL, "handle is NULL");
   if (nsteps < 0) return fail(LESBGK_EINVAL, "nsteps < 0");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1434,6 +1436,7 @@ int finish_sums(lesbgk *h, double *h_sums, cudaStream_t s) {
 }  // namespace
 
 extern "C" int lesbgk_moments(lesbgk *h, float *d_out, double *h_sums, void *stream) {
+  lesbgk_internal::Range range_("lesbgk_moments");
   if (!h) return fail(LESBGK_EINVAL, "handle is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   launch_moments(h, d_out, s);
@@ -1443,6 +1446,7 @@ extern "C" int lesbgk_moments(lesbgk *h, float *d_out, double *h_sums, void *str
 }
 
 extern "C" int lesbgk_moments_host(lesbgk *h, float *h_out, double *h_sums, void *stream) {
+  lesbgk_internal::Range range_("lesbgk_moments_host");
   if (!h) return fail(LESBGK_EINVAL, "handle is NULL");
   if (!h_out) return fail(LESBGK_EINVAL, "h_out is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1458,6 +1462,7 @@ extern "C" int lesbgk_moments_host(lesbgk *h, float *h_out, double *h_sums, void
 
 extern "C" int lesbgk_residual(lesbgk *h, float *d_snap, int64_t steps, double *h_r, double *h_mass,
                                void *stream) {
+  lesbgk_internal::Range range_("lesbgk_residual");
   if (!h || !d_snap || !h_r) return fail(LESBGK_EINVAL, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // scratch in the handle's reduction area (no moments call runs meanwhile):
