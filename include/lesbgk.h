@@ -361,6 +361,17 @@ int lesbgk_batch_get_launch(const lesbgk_batch *b, int32_t *rows, int32_t *resid
 int lesbgk_batch_autotune(lesbgk_batch *b, const int32_t *candidates, int32_t n, int32_t *chosen, void *stream);
 /* Largest free block and total free bytes of the pool. */
 int lesbgk_batch_pool_free(const lesbgk_batch *b, size_t *largest, size_t *total);
+/* Guard words (a check for writes outside a slot's memory; the paper has no
+ * counterpart): each slot's pool block ends in 256 bytes set to 0xA5 at
+ * admission, which no kernel writes.  lesbgk_batch_check_guards compares
+ * them on the device and sets h_bad[slot] (HOST int32[capacity]) to 1 for
+ * every admitted slot whose guard changed, 0 otherwise; it synchronises the
+ * stream.  lesbgk_batch_debug_poison overwrites 4 bytes of one slot's guard,
+ * for testing the check.  Both use the workspace's moment-output and
+ * admission scratch: they must not overlap lesbgk_batch_moments_many or
+ * lesbgk_batch_add_many on the GPU. */
+int lesbgk_batch_check_guards(lesbgk_batch *b, int32_t *h_bad, void *stream);
+int lesbgk_batch_debug_poison(lesbgk_batch *b, int32_t slot, void *stream);
 int lesbgk_batch_destroy(lesbgk_batch *b);
 
 /* Moments without any allocation (the paper has no counterpart: this is a

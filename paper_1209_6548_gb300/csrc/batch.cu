@@ -40,6 +40,8 @@ constexpr int kBRing = 4;
 // others none of it)
 constexpr int kNumClasses = 12;
 constexpr int kGraphSteps = 64;
+constexpr size_t kGuardBytes = 256;       // guard words after each slot's pool block
+constexpr unsigned char kGuardByte = 0xA5;
 constexpr int kBuckets = 6;  // resident instances by height: ny <= 16, 32, ..., 512 (smem permitting)
 
 // Per-instance descriptor (device memory).
@@ -541,6 +543,19 @@ __global__ void __launch_bounds__(kBBlock) k_batch_moments(const BatchArgs B, co
   }
 }
 
+// Guard check: block k compares the kGuardBytes after slot list[k]'s pool
+// block (guards[k]) with the pattern written at admission and sets bad[slot]
+// when any byte differs.
+__global__ void k_batch_guards(const unsigned *const *__restrict__ guards, const int *__restrict__ list, int n,
+                               unsigned *__restrict__ bad) {
+  if ((int)blockIdx.x >= n) return;
+  constexpr unsigned pat = 0x01010101u * kGuardByte;
+  const unsigned *g = guards[blockIdx.x];
+  bool diff = false;
+  for (int t = threadIdx.x; t < (int)(kGuardBytes / 4); t += blockDim.x) diff |= g[t] != pat;
+  if (__syncthreads_or(diff) && threadIdx.x == 0) bad[list[blockIdx.x]] = 1u;
+}
+
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // First-fit allocator over [0, cap) in 256-byte units, coalescing on release.
@@ -730,7 +745,12 @@ size_t slot_bytes(const lesbgk_params &p) {
   const size_t q = (size_t)p.nroots * p.nroots;
   const size_t buf = align_up(cells * std::max<size_t>(q * elem_bytes(p.storage), 36), 256);
   const size_t heat = p.wall_T_amp != 0.0 ? align_up(sizeof(HeatPoly), 256) : 0;
-  return 2 * buf + align_up(cells * 4 * sizeof(float), 256) + heat;
+  return 2 * buf + align_up(cells * 4 * sizeof(float), 256) + heat + kGuardBytes;
+}
+
+// The guard words of a slot: the last kGuardBytes of its pool block.
+char *guard_of(const lesbgk_batch *b, const lesbgk_batch::Slot &sl) {
+  return b->pool_base + sl.off + sl.bytes - kGuardBytes;
 }
 
 bool pow2_le32(int n) { return n >= 1 && n <= 32 && (n & (n - 1)) == 0; }
@@ -1164,6 +1184,7 @@ extern "C" int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const d
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemcpyAsync(b->d_desc + slot, &D, sizeof D, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_nstep + 2 * slot + b->par, 0, sizeof(long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(guard_of(b, sl), kGuardByte, kGuardBytes, s);
   if (e == cudaSuccess && D.heat)  // (pageable host copy: staged before the call returns)
     e = cudaMemcpyAsync(const_cast<HeatPoly *>(D.heat), sl.heat.data(), sizeof(HeatPoly), cudaMemcpyHostToDevice, s);
   const double *dfields = nullptr;
@@ -1215,7 +1236,8 @@ extern "C" int lesbgk_batch_add_many(lesbgk_batch *b, int32_t n, const lesbgk_pa
     std::vector<int> list[kNumClasses];
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
       const auto &sl = b->slots[taken[i]];
-      if (sl.desc.heat)
+      e = cudaMemsetAsync(guard_of(b, sl), kGuardByte, kGuardBytes, s);
+      if (e == cudaSuccess && sl.desc.heat)
         e = cudaMemcpyAsync(const_cast<HeatPoly *>(sl.desc.heat), sl.heat.data(), sizeof(HeatPoly),
                             cudaMemcpyHostToDevice, s);
       if (e != cudaSuccess) break;
@@ -1512,6 +1534,43 @@ extern "C" int lesbgk_batch_autotune(lesbgk_batch *b, const int32_t *candidates,
   b->resident_limit = best.limit;
   if (chosen) *chosen = best.rows;
   return lesbgk_batch_set_rows(b, best.rows, stream);
+}
+
+extern "C" int lesbgk_batch_check_guards(lesbgk_batch *b, int32_t *h_bad, void *stream) {
+  if (!b || !h_bad) return fail(LESBGK_EINVAL, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<const unsigned *> guards;
+  std::vector<int> list;
+  for (int i = 0; i < b->capacity; ++i)
+    if (b->slots[i].used) {
+      guards.push_back(reinterpret_cast<const unsigned *>(guard_of(b, b->slots[i])));
+      list.push_back(i);
+    }
+  std::vector<unsigned> bad(b->capacity, 0u);
+  cudaError_t e = cudaMemsetAsync(b->d_res, 0, sizeof(unsigned) * b->capacity, s);
+  if (e == cudaSuccess && !list.empty()) {
+    // (the pointer and slot lists go through the moment-output and admission
+    // scratch of the workspace; pageable sources are staged at once)
+    e = cudaMemcpyAsync(b->d_outs, guards.data(), sizeof(void *) * guards.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->d_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+      k_batch_guards<<<(unsigned)list.size(), 64, 0, s>>>(reinterpret_cast<const unsigned *const *>(b->d_outs),
+                                                          b->d_list, (int)list.size(), b->d_res);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bad.data(), b->d_res, sizeof(unsigned) * b->capacity, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "guard check");
+  for (int i = 0; i < b->capacity; ++i) h_bad[i] = (int32_t)bad[i];
+  return 0;
+}
+
+extern "C" int lesbgk_batch_debug_poison(lesbgk_batch *b, int32_t slot, void *stream) {
+  if (!b || slot < 0 || slot >= b->capacity || !b->slots[slot].used) return fail(LESBGK_EINVAL, "no such slot");
+  cudaError_t e = cudaMemsetAsync(guard_of(b, b->slots[slot]) + kGuardBytes / 2, 0, 4, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? 0 : cuda_fail(e, "guard poison");
 }
 
 extern "C" int lesbgk_batch_pool_free(const lesbgk_batch *b, size_t *largest, size_t *total) {

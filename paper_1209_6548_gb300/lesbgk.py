@@ -35,7 +35,8 @@ SYMBOLS = ("lesbgk_workspace_size", "lesbgk_create", "lesbgk_reinit", "lesbgk_st
            "lesbgk_batch_remove", "lesbgk_batch_step", "lesbgk_batch_residuals", "lesbgk_batch_moments",
            "lesbgk_batch_get_populations", "lesbgk_batch_get_info", "lesbgk_batch_set_rows",
            "lesbgk_batch_autotune", "lesbgk_batch_pool_free", "lesbgk_batch_destroy", "lesbgk_batch_add_many",
-           "lesbgk_batch_moments_many", "lesbgk_batch_set_resident", "lesbgk_batch_get_launch")
+           "lesbgk_batch_moments_many", "lesbgk_batch_set_resident", "lesbgk_batch_get_launch",
+           "lesbgk_batch_check_guards", "lesbgk_batch_debug_poison")
 
 
 class Params(C.Structure):
@@ -116,6 +117,8 @@ def lib():
             L.lesbgk_batch_set_rows.argtypes = [vp, i32, vp]
             L.lesbgk_batch_autotune.argtypes = [vp, vp, i32, C.POINTER(i32), vp]
             L.lesbgk_batch_pool_free.argtypes = [vp, C.POINTER(sz), C.POINTER(sz)]
+            L.lesbgk_batch_check_guards.argtypes = [vp, vp, vp]
+            L.lesbgk_batch_debug_poison.argtypes = [vp, i32, vp]
             L.lesbgk_batch_destroy.argtypes = [vp]
             L.lesbgk_last_error.restype = C.c_char_p
             L.lesbgk_last_error.argtypes = []
@@ -466,6 +469,17 @@ class Batch:
         _check(lib().lesbgk_batch_get_launch(C.c_void_p(self.handle), *[C.byref(x) for x in v]))
         return {"rows_per_item": v[0].value, "resident": bool(v[1].value), "steps_per_launch": v[2].value,
                 "resident_max_ny": v[3].value}
+
+    def check_guards(self):
+        """Per slot: 1 where the guard words after the slot's memory changed
+        (lesbgk_batch_check_guards), numpy int32[capacity]."""
+        import numpy as np
+        bad = np.zeros(self.capacity, dtype=np.int32)
+        _check(lib().lesbgk_batch_check_guards(C.c_void_p(self.handle), C.c_void_p(bad.ctypes.data), self._s))
+        return bad
+
+    def debug_poison(self, slot: int) -> None:
+        _check(lib().lesbgk_batch_debug_poison(C.c_void_p(self.handle), C.c_int32(slot), self._s))
 
     def pool_free(self):
         a, t = C.c_size_t(), C.c_size_t()

@@ -308,3 +308,31 @@ def test_autotune_searches_rows_and_resident_modes():
     assert cfg["resident_max_ny"] in (64, 128, 256, 454) or not cfg["resident"]
     after = [bt.populations(s).cpu().numpy() for s in slots]
     assert all(np.array_equal(a, b) for a, b in zip(before, after))  # timing left the state alone
+
+
+def test_guard_words_stay_intact_and_the_check_sees_a_change():
+    """No batch kernel writes past its slot's memory: after admissions of every
+    class (both sets, FP32/FP16/BF16, heated and Maxwell walls), steps through
+    graphs, direct steps and the autotuner, removals and re-admissions, every
+    slot's guard words are as admission left them; a guard overwritten on
+    purpose is reported for that slot alone."""
+    probs = mixed_problems(n=10, seed=21)
+    params = []
+    for k, p in enumerate(probs):
+        q = L.params_from_problem(p)
+        if k % 4 == 0 and p.wall_specular == 0.0:
+            q.storage = L.F16 if k % 8 == 0 else L.BF16
+        params.append(q)
+    bt = L.Batch(capacity=12, nx=4, pool_bytes=sum(L.batch_slot_bytes(q) for q in params) + (1 << 20))
+    slots = bt.add_many(params[:7])
+    bt.step(64 + 3)
+    bt.autotune((8, 16))
+    bt.remove(slots[2])
+    late = [bt.add(q) for q in params[7:]]
+    bt.step(64 * 2 + 1)
+    bt.moments_many([slots[0]], [__import__("torch").empty((9, params[0].ny, 4), device="cuda")])
+    bad = bt.check_guards()
+    assert not bad.any()
+    bt.debug_poison(late[0])
+    bad = bt.check_guards()
+    assert bad[late[0]] == 1 and bad.sum() == 1
