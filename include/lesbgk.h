@@ -337,6 +337,18 @@ int lesbgk_batch_get_populations(lesbgk_batch *b, int32_t slot, float *d_out, vo
 int lesbgk_batch_moments_many(lesbgk_batch *b, int32_t n, const int32_t *slots, float *const *d_outs,
                               void *stream);
 int lesbgk_batch_get_info(const lesbgk_batch *b, int32_t slot, lesbgk_info *out);
+/* Checkpoint and resume of one slot, bitwise for every storage: the slot's
+ * current population buffer as stored (grouped layout, FP32 or 16-bit,
+ * lesbgk_batch_raw_bytes bytes) copied to or from DEVICE memory.
+ * lesbgk_batch_set_raw also sets the slot's step count to steps_done (its
+ * clock: the heated walls' time and the 16-bit rounding keys), so a slot
+ * admitted with the same parameters and given a checkpoint taken after n
+ * steps continues exactly as the original would; it synchronises the stream
+ * and invalidates the slot's residual snapshot (the next
+ * lesbgk_batch_residuals reports NaN for it). */
+int lesbgk_batch_raw_bytes(const lesbgk_batch *b, int32_t slot, size_t *bytes);
+int lesbgk_batch_get_raw(lesbgk_batch *b, int32_t slot, void *d_out, void *stream);
+int lesbgk_batch_set_raw(lesbgk_batch *b, int32_t slot, const void *d_in, int64_t steps_done, void *stream);
 /* Rows per work item (default 32); results do not depend on it. */
 int lesbgk_batch_set_rows(lesbgk_batch *b, int32_t rows, void *stream);
 /* Resident kernel (on by default): D2Q16 instances of at most max_ny rows

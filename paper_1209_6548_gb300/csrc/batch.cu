@@ -1417,6 +1417,48 @@ extern "C" int lesbgk_batch_get_populations(lesbgk_batch *b, int32_t slot, float
   return e == cudaSuccess ? 0 : cuda_fail(e, "batch populations");
 }
 
+namespace {
+
+size_t raw_bytes(const lesbgk_batch::Slot &sl) {
+  return (size_t)sl.p.nx * sl.p.ny * (size_t)sl.nr * sl.nr * elem_bytes(sl.p.storage);
+}
+
+}  // namespace
+
+extern "C" int lesbgk_batch_raw_bytes(const lesbgk_batch *b, int32_t slot, size_t *bytes) {
+  if (!b || !bytes || slot < 0 || slot >= b->capacity || !b->slots[slot].used)
+    return fail(LESBGK_EINVAL, "no such slot");
+  *bytes = raw_bytes(b->slots[slot]);
+  return 0;
+}
+
+extern "C" int lesbgk_batch_get_raw(lesbgk_batch *b, int32_t slot, void *d_out, void *stream) {
+  if (!b || !d_out || slot < 0 || slot >= b->capacity || !b->slots[slot].used)
+    return fail(LESBGK_EINVAL, "no such slot");
+  const auto &sl = b->slots[slot];
+  cudaError_t e = cudaMemcpyAsync(d_out, sl.desc.f[b->par], raw_bytes(sl), cudaMemcpyDeviceToDevice,
+                                  static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? 0 : cuda_fail(e, "batch raw populations");
+}
+
+extern "C" int lesbgk_batch_set_raw(lesbgk_batch *b, int32_t slot, const void *d_in, int64_t steps_done,
+                                   void *stream) {
+  if (!b || !d_in || slot < 0 || slot >= b->capacity || !b->slots[slot].used)
+    return fail(LESBGK_EINVAL, "no such slot");
+  if (steps_done < 0) return fail(LESBGK_EINVAL, "steps_done < 0");
+  auto &sl = b->slots[slot];
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long n = steps_done;
+  cudaError_t e = cudaMemcpyAsync(sl.desc.f[b->par], d_in, raw_bytes(sl), cudaMemcpyDeviceToDevice, s);
+  // the slot's clock (heated walls, 16-bit rounding keys) resumes at steps_done
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_nstep + 2 * slot + b->par, &n, sizeof n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // (n is on this stack frame)
+  if (e != cudaSuccess) return cuda_fail(e, "batch raw populations");
+  sl.steps = steps_done;
+  sl.snap_step = -1;  // the residual snapshot is of the state replaced
+  return 0;
+}
+
 extern "C" int lesbgk_batch_get_info(const lesbgk_batch *b, int32_t slot, lesbgk_info *out) {
   if (!b || !out || slot < 0 || slot >= b->capacity || !b->slots[slot].used) return fail(LESBGK_EINVAL, "no such slot");
   const auto &sl = b->slots[slot];

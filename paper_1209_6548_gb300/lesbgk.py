@@ -36,7 +36,8 @@ SYMBOLS = ("lesbgk_workspace_size", "lesbgk_create", "lesbgk_reinit", "lesbgk_st
            "lesbgk_batch_get_populations", "lesbgk_batch_get_info", "lesbgk_batch_set_rows",
            "lesbgk_batch_autotune", "lesbgk_batch_pool_free", "lesbgk_batch_destroy", "lesbgk_batch_add_many",
            "lesbgk_batch_moments_many", "lesbgk_batch_set_resident", "lesbgk_batch_get_launch",
-           "lesbgk_batch_check_guards", "lesbgk_batch_debug_poison")
+           "lesbgk_batch_check_guards", "lesbgk_batch_debug_poison", "lesbgk_batch_raw_bytes",
+           "lesbgk_batch_get_raw", "lesbgk_batch_set_raw")
 
 
 class Params(C.Structure):
@@ -118,6 +119,9 @@ def lib():
             L.lesbgk_batch_autotune.argtypes = [vp, vp, i32, C.POINTER(i32), vp]
             L.lesbgk_batch_pool_free.argtypes = [vp, C.POINTER(sz), C.POINTER(sz)]
             L.lesbgk_batch_check_guards.argtypes = [vp, vp, vp]
+            L.lesbgk_batch_raw_bytes.argtypes = [vp, i32, C.POINTER(sz)]
+            L.lesbgk_batch_get_raw.argtypes = [vp, i32, vp, vp]
+            L.lesbgk_batch_set_raw.argtypes = [vp, i32, vp, i64, vp]
             L.lesbgk_batch_debug_poison.argtypes = [vp, i32, vp]
             L.lesbgk_batch_destroy.argtypes = [vp]
             L.lesbgk_last_error.restype = C.c_char_p
@@ -477,6 +481,19 @@ class Batch:
         bad = np.zeros(self.capacity, dtype=np.int32)
         _check(lib().lesbgk_batch_check_guards(C.c_void_p(self.handle), C.c_void_p(bad.ctypes.data), self._s))
         return bad
+
+    def checkpoint(self, slot: int):
+        """(raw populations as a device uint8 tensor, steps done) of a slot."""
+        n = C.c_size_t()
+        _check(lib().lesbgk_batch_raw_bytes(C.c_void_p(self.handle), C.c_int32(slot), C.byref(n)))
+        buf = self._torch.empty(n.value, dtype=self._torch.uint8, device="cuda")
+        _check(lib().lesbgk_batch_get_raw(C.c_void_p(self.handle), C.c_int32(slot), C.c_void_p(buf.data_ptr()),
+                                          self._s))
+        return buf, self.info(slot).steps_done
+
+    def resume(self, slot: int, raw, steps_done: int) -> None:
+        _check(lib().lesbgk_batch_set_raw(C.c_void_p(self.handle), C.c_int32(slot), C.c_void_p(raw.data_ptr()),
+                                          C.c_int64(steps_done), self._s))
 
     def debug_poison(self, slot: int) -> None:
         _check(lib().lesbgk_batch_debug_poison(C.c_void_p(self.handle), C.c_int32(slot), self._s))

@@ -336,3 +336,35 @@ def test_guard_words_stay_intact_and_the_check_sees_a_change():
     bt.debug_poison(late[0])
     bad = bt.check_guards()
     assert bad[late[0]] == 1 and bad.sum() == 1
+
+
+def test_checkpoint_and_resume_are_bitwise():
+    """A slot's raw populations and step count (lesbgk_batch_get_raw), put into
+    a fresh batch at another buffer parity (lesbgk_batch_set_raw), continue
+    bitwise as the uninterrupted batch: FP32 and 16-bit slots, heated walls
+    (their clock resumes with the step count) and Maxwell walls."""
+    probs = mixed_problems(n=8, seed=31)
+    params = []
+    for k, p in enumerate(probs):
+        q = L.params_from_problem(p)
+        if k % 3 == 2 and p.wall_specular == 0.0:
+            q.storage = L.F16 if k % 2 else L.BF16
+        params.append(q)
+    assert any(q.wall_T_amp != 0.0 for q in params) and any(q.storage != L.F32 for q in params)
+    pool = sum(L.batch_slot_bytes(q) for q in params) + (1 << 20)
+    a = L.Batch(capacity=8, nx=4, pool_bytes=pool)
+    sa = a.add_many(params)
+    a.step(64 + 9)
+    cks = [a.checkpoint(s) for s in sa]
+    a.step(64 * 2 + 5)
+    b = L.Batch(capacity=10, nx=4, pool_bytes=pool)
+    b.step(0)
+    sb = b.add_many(params)
+    b.step(1)  # another buffer parity than the checkpoint's batch
+    for s, (raw, n) in zip(sb, cks):
+        assert n == 64 + 9
+        b.resume(s, raw, n)
+    b.step(64 * 2 + 5)
+    for x, y in zip(sa, sb):
+        assert b.info(y).steps_done == a.info(x).steps_done
+        assert bool((a.populations(x) == b.populations(y)).all())
