@@ -60,11 +60,13 @@ def test_walls_force_rough(nslabs, k, scheme):
     compare(prob, I.random_fields(prob, seed=9, amp_u=0.03, amp_T=0.03, amp_rho=0.03), nslabs, k, 13)
 
 
-@pytest.mark.parametrize("storage", [L.F16, L.BF16, L.F32C])
-def test_16bit_storage_rounds_by_global_row(storage):
+@pytest.mark.parametrize("storage,nroots,dim", [(L.F16, 4, 2), (L.BF16, 4, 2), (L.F32C, 4, 2), (L.F16, 6, 3),
+                                                (L.BF16, 6, 2)])
+def test_16bit_storage_rounds_by_global_row(storage, nroots, dim):
     """Stochastic rounding is keyed by the global row (row_offset), so the
-    16-bit slabs are bitwise the single domain too."""
-    prob = replace(I.tgv(64), ny=66, name="tgv64x66")
+    16-bit slabs are bitwise the single domain too (D3Q216's level warps
+    included)."""
+    prob = replace(I.tgv(64), ny=66, name="tgv64x66", nroots=nroots, dim=dim)
     compare(prob, I.initial_fields(prob), 3, 2, 10, storage)
 
 

@@ -160,6 +160,7 @@ def test_d3q216_16bit(storage):
                         f"d3q216 couette {STORE[storage]}")
     for prob in (I.Problem(name="r", nroots=6, dim=3, nx=60, ny=33, bc_y=I.PERIODIC, kn=0.05, b=-0.5,
                            scheme=I.SPLIT),
+                 replace(I.unsteady_heating(kn=0.1, amp=0.02, ny=30), nroots=6, dim=3, name="heat"),
                  I.Problem(name="wf", nroots=6, dim=3, nx=40, ny=30, bc_y=I.DIFFUSE, kn=0.1, b=0.5,
                            wall_ux=(-0.05, 0.05), wall_T=(0.97, 1.04), g=(1e-3, 0.0))):
         fields = I.random_fields(prob, seed=3, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
