@@ -196,6 +196,43 @@ def test_full_size_sampled(which):
     assert_fields_close(g[:, :, None], ref[:, :, None], bnd, what=which)
 
 
+def test_conservation_totals_at_2_to_the_28_nodes():
+    """The FP64 totals of lesbgk_moments at 16384^2 = 2^28 nodes (per-node
+    sums in FP32, runs of 16 nodes in FP32, the runs in FP64) against FP64
+    sums of the stored populations themselves, within the worst case of that
+    arithmetic: each total is off by at most 30 FP32 roundings of the absolute
+    terms it sums (up to 12 in a node's Hermite moments, 3 combining them, 15
+    in a run), i.e. 30 2^-24 sum_nodes sum_a |psi_a| |df_a| with psi = 1, |c_x|,
+    |c_y|, c^2 + 4 (the energy's moments m20, m02 and 2 m00)."""
+    import torch
+    prob = I.tgv(16384)
+    fields = I.initial_fields(prob)
+    s = gpu_solver(prob, time_step(prob, fields), fields)
+    s.step(2)
+    _, sums = s.moments(sums=True)
+    df = s.populations()  # (16, ny, nx) FP32 deviations f - w, on the device
+    cx, cy, w = O.velocity_set(4)
+    cells = prob.cells
+    col, mag = np.zeros(16), np.zeros(16)  # per population: sum over nodes of df, of |df|
+    for a in range(16):
+        da = df[a].double()
+        col[a] = float(da.sum())
+        mag[a] = float(da.abs().sum())
+    del df
+    psi = [np.ones(16), cx, cy, cx * cx + cy * cy]
+    bound_w = [np.ones(16), np.abs(cx), np.abs(cy), cx * cx + cy * cy + 4.0]
+    out = {}
+    for k, name in enumerate(("mass", "momentum_x", "momentum_y", "energy")):
+        scale = 0.5 if k == 3 else 1.0  # energy = 1/2 sum f c^2
+        ref = scale * float(np.sum(w * psi[k]) * cells + np.dot(psi[k], col))
+        bound = scale * 30 * 2.0 ** -24 * float(np.dot(bound_w[k], mag))
+        err = abs(sums[k] - ref)
+        out[name] = {"abs": err, "e": err / max(abs(ref), 1e-300), "e_own": None, "e_pert": None, "bound": bound,
+                     "tol": bound, "ok": bool(err <= bound)}
+    record("totals 16384^2", out)
+    assert all(v["ok"] for v in out.values()), out
+
+
 def test_grid_sizes_near_strip_and_segment_edges():
     """nx around one and two strip widths (60 and 120 nodes), ny not a multiple
     of the segment length, walls."""
