@@ -260,8 +260,8 @@ int lesbgk_set_rows(lesbgk *h, int32_t j0, int32_t nrows, const void *d_in, void
  * (HOST, or NULL) the FP64 totals of those rows. */
 int lesbgk_moments_rows(lesbgk *h, int32_t j0, int32_t nrows, float *d_out, double *h_sums, void *stream);
 
-/* Choose the launch shape of the step kernel: cells_per_thread (1 or 2
- * consecutive x-nodes per lane; 2 needs nx even and nroots = 4) and
+/* Choose the launch shape of the step kernel: cells_per_thread (x-nodes per
+ * lane: 1, the only shape built; any other value is refused) and
  * rows_per_segment (rows one warp marches through, >= 1).  0 keeps the current
  * value.  Results do not depend on the shape (bitwise). */
 int lesbgk_set_launch(lesbgk *h, int32_t cells_per_thread, int32_t rows_per_segment);

@@ -103,8 +103,9 @@ def test_couette_4x64_2000_steps():
 @pytest.mark.parametrize("scheme", [I.UNSPLIT, I.SPLIT])
 @pytest.mark.parametrize("nx,ny", [(70, 37), (71, 23), (130, 9), (1, 1), (2, 3), (5, 66)])
 def test_rough_periodic_fields(nx, ny, scheme):
-    """i.i.d. rough fields exercise every limiter branch; odd nx takes the
-    one-node-per-lane kernel, even nx the two-node one."""
+    """i.i.d. rough fields exercise every limiter branch; the grids span
+    several warp strips and row segments with ragged tails, and the 1x1,
+    2x3 and 5x66 grids wrap the stencil onto the node itself."""
     prob = I.Problem(name="rough", nx=nx, ny=ny, bc_y=I.PERIODIC, kn=0.05, b=-0.5, scheme=scheme)
     fields = I.random_fields(prob, seed=nx * 100 + ny)
     res, *_ = run_pair(prob, fields, [1, 6])
