@@ -278,7 +278,8 @@ int lesbgk_destroy(lesbgk *h);
  * A batch holds up to `capacity` instances ("slots"), all with the same nx, a
  * power of two <= 32 (the 1D-in-y flows of the paper's Sec. 4 run on nx = 4),
  * each with its own ny, Kn, b, walls (diffuse, Maxwell, steady or heated),
- * force and time step, on D2Q16 (order 3) or D2Q36 (order 4) in FP32, FP16 or BF16 storage,
+ * force and time step, on D2Q16 (order 3), D2Q36 (order 4) or D3Q64 (order 3, dim 3)
+ * in FP32, FP16 or BF16 storage,
  * periodic in x.  Every lesbgk_batch_step advances every slot by the same
  * number of steps: per step one launch per class (velocity set, storage, wall
  * heating) over a work list of

@@ -34,11 +34,11 @@ namespace {
 
 constexpr int kBBlock = 128;
 constexpr int kBRing = 4;
-// classes: velocity set x storage x wall heating -- 0 D2Q16 (order 3) and 1
-// D2Q36 (order 4) in FP32, 2 and 3 in FP16, 4 and 5 in BF16; 6 to 11 the same
-// with heated walls (their kernels carry the FP64 wall-table code, the
-// others none of it)
-constexpr int kNumClasses = 12;
+// classes: velocity set x storage x wall heating -- class lat + 3 st + 9 h
+// with lat 0 D2Q16 (order 3), 1 D2Q36 (order 4), 2 D3Q64 (order 3, its z-even
+// half stored); st 0 FP32, 1 FP16, 2 BF16; h 1 for heated walls (their
+// kernels carry the FP64 wall-table code, the others none of it)
+constexpr int kNumClasses = 18;
 constexpr int kGraphSteps = 64;
 constexpr size_t kGuardBytes = 256;       // guard words after each slot's pool block
 constexpr unsigned char kGuardByte = 0xA5;
@@ -81,9 +81,9 @@ struct InstRegs {
   int vmode, has_force;
 };
 
-template <int NR, class S = float>
+template <int NR, class S = float, int NZ = 1>
 constexpr size_t batch_smem_bytes() {
-  return (size_t)(kBBlock / 32) * kBRing * Layout<NR, S>::G * 32 * Layout<NR, S>::VB;
+  return (size_t)(kBBlock / 32) * kBRing * Layout<NR, S, NZ>::G * 32 * Layout<NR, S, NZ>::VB;
 }
 
 // neighbour lanes inside a lane group of W lanes (periodic in x)
@@ -126,9 +126,9 @@ __device__ __forceinline__ void wall_fix_heated(float (&O)[Q], int side, const T
 // One time step of every work item of a class (velocity set and storage S:
 // FP32 deviations, or FP16/BF16 relative deviations rounded stochastically
 // with the random words of k_step, keyed by the instance's step count and row).
-template <int NR, int N, int W, class S, bool HEAT>
+template <int NR, int N, int W, class S, bool HEAT, int NZ>
 __global__ void __launch_bounds__(kBBlock) k_batch_step(const BatchArgs B, const int par) {
-  using Lay = Layout<NR, S>;
+  using Lay = Layout<NR, S, NZ>;
   constexpr int Q = Lay::Q, H = Lay::H, V = Lay::V, G = Lay::G;
   constexpr int GPW = 32 / W;
   const int lane = threadIdx.x & 31;
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(kBBlock) k_batch_step(const BatchArgs B, const
     }
     float acc[Q];
     float omw;
-    collide<NR, N>(fc, acc, omw, B.lat, P);
+    collide_any<NR, N>(fc, acc, omw, B.lat, P);
     float xs[Q];
     const GroupLanes nb{srcL, srcR};
     if constexpr (NR == 4) {  // packed pairs a, a+1 (same ix, c_y of one sign)
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kBBlock) k_batch_step(const BatchArgs B, const
       }
 #pragma unroll
       for (int a = 0; a < Q; a += 2) {
-        const int ix = a / NR;
+        const int ix = (a / NR) % NR;
         const float2 nax = make_float2(-ax[ix], -ax[ix]);
         const float2 diff = xflux2(ix >= H, make_float2(xs[a], xs[a + 1]), make_float2(kx[ix], kx[ix]), nb);
         const float2 ac = fma2(nax, diff, make_float2(acc[a], acc[a + 1]));
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(kBBlock) k_batch_step(const BatchArgs B, const
       }
 #pragma unroll
       for (int a = 0; a < Q; ++a) {
-        const int ix = a / NR;
+        const int ix = (a / NR) % NR;
         acc[a] = fmaf(-ax[ix], xflux(ix >= H, xs[a], kx[ix], nb), acc[a]);
       }
     }
@@ -427,11 +427,11 @@ __global__ void __launch_bounds__(kBBlock) k_batch_resident(const BatchArgs B, c
 // r = Inf); the snapshot is refreshed.  mass[item] receives the item's sum of
 // rho - 1 over its nodes (FP32 per thread, FP64 across the block).  One block
 // per item.
-template <int NR, class S>
+template <int NR, class S, int NZ>
 __global__ void __launch_bounds__(kBBlock) k_batch_residual(const BatchArgs B, const int par,
                                                             unsigned *__restrict__ res_bits,
                                                             double *__restrict__ mass) {
-  constexpr int Q = NR * NR;
+  constexpr int Q = NZ * NR * NR;
   const int first = B.range[0], count = B.range[1];
   if ((int)blockIdx.x >= count) return;
   const WorkItem wi = B.items[first + blockIdx.x];
@@ -443,14 +443,24 @@ __global__ void __launch_bounds__(kBBlock) k_batch_residual(const BatchArgs B, c
   for (int t = threadIdx.x; t < wi.rows * nx; t += kBBlock) {
     const long long c = (long long)wi.y0 * nx + t;
     float F[Q];
-    ld_node<NR, S, 1>(f, c, cells, F, B.lat);
-    float m[3][3];
-    hermite_moments<NR, 2>(F, m, B.lat);
+    ld_node<NR, S, NZ>(f, c, cells, F, B.lat);
+    float m[3][3], mzz = 0.0f;
+    if constexpr (NZ == 1) {
+      hermite_moments<NR, 2>(F, m, B.lat);
+    } else {  // D = 3: the in-plane moments summed over the z-levels, and m002
+      float b[3][3][3];
+      hermite_moments3<NR, 2>(F, b, B.lat);
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = 0; p + q < 3; ++q) m[p][q] = b[0][p][q];
+      mzz = b[1][0][0];
+    }
     const float rho = 1.0f + m[0][0];
     const float ir = 1.0f / rho;
     const float ux = m[1][0] * ir, uy = m[0][1] * ir;
-    const float trM = fmaf(-m[1][0], ux, m[2][0]) + fmaf(-m[0][1], uy, m[0][2]);
-    const float T = fmaf(0.5f * trM, ir, 1.0f);
+    const float trM = fmaf(-m[1][0], ux, m[2][0]) + fmaf(-m[0][1], uy, m[0][2]) + mzz;
+    const float T = fmaf((NZ == 1 ? 0.5f : 1.0f / 3.0f) * trM, ir, 1.0f);
     float *s = D.snap + 4 * c;
     const float d = fabsf(rho - s[0]) + fabsf(ux - s[1]) + fabsf(uy - s[2]) + fabsf(T - s[3]);
     r = fmaxf(r, d != d ? __int_as_float(0x7f800000) : d);  // NaN counts as Inf
@@ -483,7 +493,7 @@ __global__ void __launch_bounds__(kBBlock) k_batch_residual(const BatchArgs B, c
 // list: f = rho S(T,u) (Eq. feq0 to order N) from the slot's fields (device
 // double[4][ny][nx] in its spare buffer when list entry bit 30 is set, else
 // rest), then the wall rule -- the arithmetic of the single-domain k_init.
-template <int NR, int N, class S>
+template <int NR, int N, class S, int NZ>
 __global__ void __launch_bounds__(kBBlock) k_batch_init(const BatchArgs B, const int *__restrict__ list, int n,
                                                         const int par) {
   if ((int)blockIdx.x >= n) return;
@@ -507,22 +517,29 @@ __global__ void __launch_bounds__(kBBlock) k_batch_init(const BatchArgs B, const
     const float rdT = rho * dT;
     float e[N + 1][N + 1];
     gaussian_coeffs<N>(rho, rho * ux, rho * uy, ux, uy, dT, 0.f, dT, rdT, 0.f, rdT, e);
-    e[0][0] = drho;
-    float Sv[NR * NR];
-    hermite_evaluate<NR, N>(e, Sv, B.lat);
+    float Sv[NZ * NR * NR];
+    if constexpr (NZ == 1) {
+      e[0][0] = drho;
+      hermite_evaluate<NR, N>(e, Sv, B.lat);
+    } else {  // D = 3, as k_init: isotropic, so lambda_zz - 1 = T - 1 as in-plane
+      float d[3][N + 1][N + 1];
+      z_factor<N>(e, dT, 1.0f, d);
+      d[0][0][0] = drho;
+      hermite_evaluate3<NR, N>(d, Sv, B.lat);
+    }
     const int j = (int)(c / nx);
     if (D.walls && (j == 0 || j == ny - 1)) {
       if (D.wspec != 0.0f) wall_fix<NR, true>(Sv, j == 0 ? 0 : 1, B.lat, D);
       else wall_fix<NR, false>(Sv, j == 0 ? 0 : 1, B.lat, D);
     }
-    st_node<NR, S, 1>(f, c, cells, Sv, B.lat);
+    st_node<NR, S, NZ>(f, c, cells, Sv, B.lat);
   }
 }
 
 // Moments (Eq. mac) of every node of every work item whose slot has an output
 // in outs[slot] (DEVICE float[9][ny][nx] each, or null): the per-node
 // arithmetic of lesbgk_moments, one block per item.
-template <int NR, class S>
+template <int NR, class S, int NZ>
 __global__ void __launch_bounds__(kBBlock) k_batch_moments(const BatchArgs B, const int par,
                                                            float *const *__restrict__ outs) {
   const int first = B.range[0], count = B.range[1];
@@ -536,8 +553,8 @@ __global__ void __launch_bounds__(kBBlock) k_batch_moments(const BatchArgs B, co
   const S *f = reinterpret_cast<const S *>(D.f[par]);
   for (int t = threadIdx.x; t < wi.rows * nx; t += kBBlock) {
     const long long c = (long long)wi.y0 * nx + t;
-    float F[NR * NR];
-    ld_node<NR, S, 1>(f, c, cells, F, B.lat);
+    float F[NZ * NR * NR];
+    ld_node<NR, S, NZ>(f, c, cells, F, B.lat);
     float d[4];
     node_moments<NR>(F, out, cells, c, B.lat, d);
   }
@@ -609,38 +626,40 @@ class Pool {
   std::map<size_t, size_t> free_;
 };
 
-int class_of(int nr, int order, int storage, bool heated) {
+int class_of(int nr, int order, int storage, bool heated, int dim) {
   const int st = storage == LESBGK_F32 ? 0 : storage == LESBGK_F16 ? 1 : storage == LESBGK_BF16 ? 2 : -1;
   if (st < 0) return -1;
-  const int h = heated ? 6 : 0;
-  if (nr == 4 && order == 3) return 2 * st + h;
-  if (nr == 6 && order == 4) return 2 * st + 1 + h;
-  return -1;
+  int lat = -1;
+  if (dim == 3) lat = nr == 4 && order == 3 ? 2 : -1;
+  else if (nr == 4 && order == 3) lat = 0;
+  else if (nr == 6 && order == 4) lat = 1;
+  if (lat < 0) return -1;
+  return lat + 3 * st + (heated ? 9 : 0);
 }
 
-// Call fn(NR, N, storage tag, heated) with the compile-time constants of class cls.
+// Call fn(NR, N, storage tag, heated, NZ) with the compile-time constants of class cls.
 template <class Fn>
 void with_class(int cls, Fn &&fn) {
   using R4 = std::integral_constant<int, 4>;
   using R6 = std::integral_constant<int, 6>;
   using N3 = std::integral_constant<int, 3>;
   using N4 = std::integral_constant<int, 4>;
-  using H0 = std::false_type;
-  using H1 = std::true_type;
-  switch (cls) {
-    case 0: fn(R4{}, N3{}, float{}, H0{}); break;
-    case 1: fn(R6{}, N4{}, float{}, H0{}); break;
-    case 2: fn(R4{}, N3{}, __half{}, H0{}); break;
-    case 3: fn(R6{}, N4{}, __half{}, H0{}); break;
-    case 4: fn(R4{}, N3{}, __nv_bfloat16{}, H0{}); break;
-    case 5: fn(R6{}, N4{}, __nv_bfloat16{}, H0{}); break;
-    case 6: fn(R4{}, N3{}, float{}, H1{}); break;
-    case 7: fn(R6{}, N4{}, float{}, H1{}); break;
-    case 8: fn(R4{}, N3{}, __half{}, H1{}); break;
-    case 9: fn(R6{}, N4{}, __half{}, H1{}); break;
-    case 10: fn(R4{}, N3{}, __nv_bfloat16{}, H1{}); break;
-    default: fn(R6{}, N4{}, __nv_bfloat16{}, H1{}); break;
-  }
+  using Z1 = std::integral_constant<int, 1>;
+  using Z2 = std::integral_constant<int, 2>;
+  const int lat = cls % 3, st = (cls / 3) % 3;
+  const bool heated = cls >= 9;
+  auto by_heat = [&](auto r, auto n, auto s, auto z) {
+    if (heated) fn(r, n, s, std::true_type{}, z);
+    else fn(r, n, s, std::false_type{}, z);
+  };
+  auto by_storage = [&](auto r, auto n, auto z) {
+    if (st == 0) by_heat(r, n, float{}, z);
+    else if (st == 1) by_heat(r, n, __half{}, z);
+    else by_heat(r, n, __nv_bfloat16{}, z);
+  };
+  if (lat == 0) by_storage(R4{}, N3{}, Z1{});
+  else if (lat == 1) by_storage(R6{}, N4{}, Z1{});
+  else by_storage(R4{}, N3{}, Z2{});
 }
 
 }  // namespace
@@ -740,9 +759,14 @@ Layout0 fixed_layout(int capacity) {
 
 size_t elem_bytes(int storage) { return storage == LESBGK_F32 ? sizeof(float) : 2; }
 
+// values stored per node (D = 3: the z-even half)
+size_t stored_values(const lesbgk_params &p) {
+  return (size_t)p.nroots * p.nroots * (p.dim == 3 ? p.nroots / 2 : 1);
+}
+
 size_t slot_bytes(const lesbgk_params &p) {
   const size_t cells = (size_t)p.nx * p.ny;
-  const size_t q = (size_t)p.nroots * p.nroots;
+  const size_t q = stored_values(p);
   const size_t buf = align_up(cells * std::max<size_t>(q * elem_bytes(p.storage), 36), 256);
   const size_t heat = p.wall_T_amp != 0.0 ? align_up(sizeof(HeatPoly), 256) : 0;
   return 2 * buf + align_up(cells * 4 * sizeof(float), 256) + heat + kGuardBytes;
@@ -755,29 +779,31 @@ char *guard_of(const lesbgk_batch *b, const lesbgk_batch::Slot &sl) {
 
 bool pow2_le32(int n) { return n >= 1 && n <= 32 && (n & (n - 1)) == 0; }
 
-template <int NR, int N, class S, bool HEAT>
+template <int NR, int N, class S, bool HEAT, int NZ>
 void *step_fn(int W) {
   switch (W) {
-    case 1: return (void *)k_batch_step<NR, N, 1, S, HEAT>;
-    case 2: return (void *)k_batch_step<NR, N, 2, S, HEAT>;
-    case 4: return (void *)k_batch_step<NR, N, 4, S, HEAT>;
-    case 8: return (void *)k_batch_step<NR, N, 8, S, HEAT>;
-    case 16: return (void *)k_batch_step<NR, N, 16, S, HEAT>;
-    default: return (void *)k_batch_step<NR, N, 32, S, HEAT>;
+    case 1: return (void *)k_batch_step<NR, N, 1, S, HEAT, NZ>;
+    case 2: return (void *)k_batch_step<NR, N, 2, S, HEAT, NZ>;
+    case 4: return (void *)k_batch_step<NR, N, 4, S, HEAT, NZ>;
+    case 8: return (void *)k_batch_step<NR, N, 8, S, HEAT, NZ>;
+    case 16: return (void *)k_batch_step<NR, N, 16, S, HEAT, NZ>;
+    default: return (void *)k_batch_step<NR, N, 32, S, HEAT, NZ>;
   }
 }
 
 void *step_kernel(int cls, int W) {
   void *fn = nullptr;
-  with_class(cls, [&](auto r, auto n, auto st, auto ht) {
-    fn = step_fn<decltype(r)::value, decltype(n)::value, decltype(st), decltype(ht)::value>(W);
+  with_class(cls, [&](auto r, auto n, auto st, auto ht, auto z) {
+    fn = step_fn<decltype(r)::value, decltype(n)::value, decltype(st), decltype(ht)::value, decltype(z)::value>(W);
   });
   return fn;
 }
 
 size_t step_smem(int cls) {
   size_t b = 0;
-  with_class(cls, [&](auto r, auto, auto st, auto) { b = batch_smem_bytes<decltype(r)::value, decltype(st)>(); });
+  with_class(cls, [&](auto r, auto, auto st, auto, auto z) {
+    b = batch_smem_bytes<decltype(r)::value, decltype(st), decltype(z)::value>();
+  });
   return b;
 }
 
@@ -1065,10 +1091,9 @@ int prepare_slot(lesbgk_batch *b, const lesbgk_params *p, const double *h_init, 
   if (int rc = check_params(p)) return rc;
   const int order = p->order ? p->order : default_order(p->nroots);
   if (p->storage == LESBGK_F32C) return fail(LESBGK_EINVAL, "batched instances store FP32, FP16 or BF16 populations");
-  const int cls = class_of(p->nroots, order, p->storage, p->wall_T_amp != 0.0);
-  if (cls < 0) return fail(LESBGK_EINVAL, "batched instances take D2Q16 (order 3) or D2Q36 (order 4)");
+  const int cls = class_of(p->nroots, order, p->storage, p->wall_T_amp != 0.0, p->dim == 3 ? 3 : 2);
+  if (cls < 0) return fail(LESBGK_EINVAL, "batched instances take D2Q16 (order 3), D2Q36 (order 4) or D3Q64");
   if (p->nx != b->nx) return fail(LESBGK_EINVAL, "instance nx %d differs from the batch's %d", p->nx, b->nx);
-  if (p->dim == 3) return fail(LESBGK_EINVAL, "batched instances take the 2D velocity sets");
   if (p->bc_x != LESBGK_PERIODIC) return fail(LESBGK_EINVAL, "batched instances are periodic in x");
   if ((long long)(p->ny + b->rows - 1) / b->rows > (long long)kItemsPerSlot)
     return fail(LESBGK_EINVAL, "ny %d too large for the batch work list", p->ny);
@@ -1102,7 +1127,7 @@ int prepare_slot(lesbgk_batch *b, const lesbgk_params *p, const double *h_init, 
   sl.cmax = su.cmax;
   sl.tau_ref = su.tau_ref;
   const size_t cells = (size_t)p->nx * p->ny;
-  const size_t q = (size_t)p->nroots * p->nroots;
+  const size_t q = stored_values(*p);
   const size_t buf = align_up(cells * std::max<size_t>(q * elem_bytes(p->storage), 36), 256);
   char *base = b->pool_base + off;
   InstDesc &D = sl.desc;
@@ -1193,7 +1218,8 @@ extern "C" int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const d
     dfields = reinterpret_cast<const double *>(D.f[b->par ^ 1]);
   }
   if (e == cudaSuccess)
-    e = lesbgk_internal::launch_init(sl.args, sl.nr, sl.order, p->storage, dfields, D.f[b->par], b->sm_count, s);
+    e = lesbgk_internal::launch_init(sl.args, sl.nr, sl.order, p->storage, p->dim, dfields, D.f[b->par], b->sm_count,
+                                     s);
   if (e == cudaSuccess && h_init) e = settle_host_copy(h_init, s);
   if (e != cudaSuccess) {
     release_slot(b, slot);
@@ -1255,8 +1281,9 @@ extern "C" int lesbgk_batch_add_many(lesbgk_batch *b, int32_t n, const lesbgk_pa
       if (e != cudaSuccess) break;
       BatchArgs a = make_args(b, cls);
       const int *lst = b->d_list + at;
-      with_class(cls, [&](auto r, auto nn, auto st, auto) {
-        k_batch_init<decltype(r)::value, decltype(nn)::value, decltype(st)><<<m, kBBlock, 0, s>>>(a, lst, m, b->par);
+      with_class(cls, [&](auto r, auto nn, auto st, auto, auto z) {
+        k_batch_init<decltype(r)::value, decltype(nn)::value, decltype(st), decltype(z)::value>
+            <<<m, kBBlock, 0, s>>>(a, lst, m, b->par);
       });
       e = cudaGetLastError();
       at += m;
@@ -1334,8 +1361,9 @@ extern "C" int lesbgk_batch_residuals(lesbgk_batch *b, double *h_res, double *h_
     const int n = b->range_all[cls][1];
     if (!n) continue;
     BatchArgs a = make_args_all(b, cls);
-    with_class(cls, [&](auto r, auto, auto st, auto) {
-      k_batch_residual<decltype(r)::value, decltype(st)><<<n, kBBlock, 0, s>>>(a, b->par, b->d_res, b->d_mass);
+    with_class(cls, [&](auto r, auto, auto st, auto, auto z) {
+      k_batch_residual<decltype(r)::value, decltype(st), decltype(z)::value>
+          <<<n, kBBlock, 0, s>>>(a, b->par, b->d_res, b->d_mass);
     });
     e = cudaGetLastError();
   }
@@ -1367,8 +1395,8 @@ extern "C" int lesbgk_batch_moments(lesbgk_batch *b, int32_t slot, float *d_out,
   if (!b || slot < 0 || slot >= b->capacity || !b->slots[slot].used) return fail(LESBGK_EINVAL, "no such slot");
   auto &sl = b->slots[slot];
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = lesbgk_internal::launch_moments(sl.args, sl.nr, sl.order, sl.p.storage, sl.desc.f[b->par], d_out,
-                                                  b->d_partial, b->d_sums, s);
+  cudaError_t e = lesbgk_internal::launch_moments(sl.args, sl.nr, sl.order, sl.p.storage, sl.p.dim, sl.desc.f[b->par],
+                                                  d_out, b->d_partial, b->d_sums, s);
   if (e == cudaSuccess && h_sums) {
     e = cudaMemcpyAsync(h_sums, b->d_sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1398,8 +1426,8 @@ extern "C" int lesbgk_batch_moments_many(lesbgk_batch *b, int32_t n, const int32
     const int m = b->range_all[cls][1];
     if (!m) continue;
     BatchArgs a = make_args_all(b, cls);
-    with_class(cls, [&](auto r, auto, auto st, auto) {
-      k_batch_moments<decltype(r)::value, decltype(st)><<<m, kBBlock, 0, s>>>(a, b->par, b->d_outs);
+    with_class(cls, [&](auto r, auto, auto st, auto, auto z) {
+      k_batch_moments<decltype(r)::value, decltype(st), decltype(z)::value><<<m, kBBlock, 0, s>>>(a, b->par, b->d_outs);
     });
     e = cudaGetLastError();
   }
@@ -1411,7 +1439,8 @@ extern "C" int lesbgk_batch_get_populations(lesbgk_batch *b, int32_t slot, float
   if (!b || !d_out || slot < 0 || slot >= b->capacity || !b->slots[slot].used)
     return fail(LESBGK_EINVAL, "no such slot");
   auto &sl = b->slots[slot];
-  cudaError_t e = lesbgk_internal::launch_ungroup(sl.args, sl.nr, sl.order, sl.p.storage, sl.desc.f[b->par], d_out,
+  cudaError_t e = lesbgk_internal::launch_ungroup(sl.args, sl.nr, sl.order, sl.p.storage, sl.p.dim, sl.desc.f[b->par],
+                                                  d_out,
                                                   (long long)sl.p.nx * sl.p.ny, b->sm_count,
                                                   static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? 0 : cuda_fail(e, "batch populations");
@@ -1420,7 +1449,7 @@ extern "C" int lesbgk_batch_get_populations(lesbgk_batch *b, int32_t slot, float
 namespace {
 
 size_t raw_bytes(const lesbgk_batch::Slot &sl) {
-  return (size_t)sl.p.nx * sl.p.ny * (size_t)sl.nr * sl.nr * elem_bytes(sl.p.storage);
+  return (size_t)sl.p.nx * sl.p.ny * stored_values(sl.p) * elem_bytes(sl.p.storage);
 }
 
 }  // namespace
@@ -1469,7 +1498,7 @@ extern "C" int lesbgk_batch_get_info(const lesbgk_batch *b, int32_t slot, lesbgk
   out->cfl = sl.cmax * sl.dt / std::fmin(sl.dx, sl.dy);
   out->tau_ref = sl.tau_ref;
   out->steps_done = sl.steps;
-  out->q = sl.nr * sl.nr;
+  out->q = (int)stored_values(sl.p);
   out->order = sl.order;
   out->cells_per_thread = 1;
   out->rows_per_segment = b->rows;

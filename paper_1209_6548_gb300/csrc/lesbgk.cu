@@ -1272,40 +1272,41 @@ namespace lesbgk_internal {
 
 // (storage: LESBGK_F32, LESBGK_F16 or LESBGK_BF16, the 2D sets; A supplies the
 // 16-bit scale tables)
-cudaError_t launch_init(const KArgs &A, int nr, int order, int storage, const double *fields, void *f, int sm_count,
-                        cudaStream_t s) {
+cudaError_t launch_init(const KArgs &A, int nr, int order, int storage, int dim, const double *fields, void *f,
+                        int sm_count, cudaStream_t s) {
   long long g = (A.plane + kBlock - 1) / kBlock;
   if (g > (long long)sm_count * 16) g = (long long)sm_count * 16;
   const unsigned grid = g < 1 ? 1u : (unsigned)g;
-  dispatch(nr, order, storage, 2, [&](auto r, auto n, auto st, auto) {
+  dispatch(nr, order, storage, dim, [&](auto r, auto n, auto st, auto z) {
     using S = decltype(st);
-    if constexpr (!kIsComp<S>)
-      k_init<decltype(r)::value, decltype(n)::value, S><<<grid, kBlock, 0, s>>>(fields, static_cast<S *>(f), A);
+    if constexpr (!kIsComp<S> && decltype(z)::value < 3)
+      k_init<decltype(r)::value, decltype(n)::value, S, decltype(z)::value>
+          <<<grid, kBlock, 0, s>>>(fields, static_cast<S *>(f), A);
   });
   return cudaGetLastError();
 }
 
-cudaError_t launch_moments(const KArgs &A, int nr, int order, int storage, const void *f, float *out,
+cudaError_t launch_moments(const KArgs &A, int nr, int order, int storage, int dim, const void *f, float *out,
                            double *partial, double *sums, cudaStream_t s) {
-  dispatch(nr, order, storage, 2, [&](auto r, auto, auto st, auto) {
+  dispatch(nr, order, storage, dim, [&](auto r, auto, auto st, auto z) {
     using S = decltype(st);
-    if constexpr (!kIsComp<S>)
-      k_moments<decltype(r)::value, S><<<kMomGrid, kMomBlock, 0, s>>>(static_cast<const S *>(f), out, partial,
-                                                                      A.plane, A.plane, A);
+    if constexpr (!kIsComp<S> && decltype(z)::value < 3)
+      k_moments<decltype(r)::value, S, decltype(z)::value>
+          <<<kMomGrid, kMomBlock, 0, s>>>(static_cast<const S *>(f), out, partial, A.plane, A.plane, A);
   });
   k_reduce_partials<<<1, 128, 0, s>>>(partial, kMomGrid, sums);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ungroup(const KArgs &A, int nr, int order, int storage, const void *f, float *out,
+cudaError_t launch_ungroup(const KArgs &A, int nr, int order, int storage, int dim, const void *f, float *out,
                            long long cells, int sm_count, cudaStream_t s) {
   long long g = (cells + kBlock - 1) / kBlock;
   if (g > (long long)sm_count * 16) g = (long long)sm_count * 16;
   const unsigned grid = g < 1 ? 1u : (unsigned)g;
-  dispatch(nr, order, storage, 2, [&](auto r, auto, auto st, auto) {
+  dispatch(nr, order, storage, dim, [&](auto r, auto, auto st, auto z) {
     using S = decltype(st);
-    if constexpr (!kIsComp<S>)
-      k_ungroup<decltype(r)::value, S><<<grid, kBlock, 0, s>>>(static_cast<const S *>(f), out, cells, A);
+    if constexpr (!kIsComp<S> && decltype(z)::value < 3)
+      k_ungroup<decltype(r)::value, S, decltype(z)::value><<<grid, kBlock, 0, s>>>(static_cast<const S *>(f), out, cells, A);
   });
   return cudaGetLastError();
 }

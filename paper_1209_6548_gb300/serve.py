@@ -33,7 +33,7 @@ time since the previous check) and m the solve's total mass at each check:
   - max_steps: the cap.
 
 Solves that the batch cannot hold (another width, walls in x such as the
-lid-driven cavities of the mix, the D = 3 set) go to a wide lane: each runs as a single-domain solver on its own CUDA stream,
+lid-driven cavities of the mix, D3Q216) go to a wide lane: each runs as a single-domain solver on its own CUDA stream,
 so they advance concurrently with the batch; the lane admits them in arrival
 order while its own device-memory budget has room, and checks them with the
 same residual and criterion (lesbgk_residual, one kernel per check).
@@ -153,7 +153,9 @@ def serving_mix(n: int, seed: int = 0, q36_share: float = 0.2, ny_hi: int = 512,
 def fits_batch(prob, nx: int) -> bool:
     """Whether the batched solver takes this problem (the library's own
     admission checks say the same)."""
-    return prob.nx == nx and getattr(prob, "bc_x", I.PERIODIC) == I.PERIODIC and getattr(prob, "dim", 2) == 2
+    dim = getattr(prob, "dim", 2)
+    return (prob.nx == nx and getattr(prob, "bc_x", I.PERIODIC) == I.PERIODIC
+            and (dim == 2 or (dim == 3 and prob.nroots == 4)))
 
 
 class WideLane:

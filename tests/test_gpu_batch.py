@@ -26,8 +26,9 @@ def _built():
 
 def mixed_problems(nx=4, n=10, seed=3, with_q36=True):
     """The channel mix, a quarter on D2Q36, every third with Maxwell walls
-    (specular share 0.3, Sec. 3.2) and every fifth with heated walls (Sec. 4.2:
-    T_w = wall_T + 0.02 sin(St t), St = pi sqrt(2)/8)."""
+    (specular share 0.3, Sec. 3.2), every fifth with heated walls (Sec. 4.2:
+    T_w = wall_T + 0.02 sin(St t), St = pi sqrt(2)/8), and those k = 0, 5, 10,
+    ... on D2Q16 with the D = 3 set D3Q64 instead."""
     probs = I.batch_mix(n=n, seed=seed, ny_lo=16, ny_hi=200)
     out = []
     for k, p in enumerate(probs):
@@ -39,6 +40,8 @@ def mixed_problems(nx=4, n=10, seed=3, with_q36=True):
         if k % 5 == 2:
             kw["wall_T_amp"] = 0.02
             kw["wall_T_freq"] = np.pi * np.sqrt(2.0) / 8.0
+        if k % 5 == 0 and kw.get("nroots", p.nroots) == 4:
+            kw["dim"] = 3
         from dataclasses import replace
         out.append(replace(p, **kw))
     return out
@@ -222,6 +225,8 @@ def test_mismatched_nx_rejected():
         bt.add(L.make_params(nx=4, ny=16, kn=0.1, b=0.0, nroots=4, order=4))
     with pytest.raises(L.LesbgkError):
         bt.add(L.make_params(nx=4, ny=16, kn=0.1, b=0.0, storage=L.F32C))
+    with pytest.raises(L.LesbgkError):  # D3Q216 runs on its own three-warp kernel only
+        bt.add(L.make_params(nx=4, ny=16, kn=0.1, b=0.0, nroots=6, order=4, dim=3))
 
 
 def test_add_many_and_moments_many_match_the_per_slot_calls():
@@ -232,7 +237,9 @@ def test_add_many_and_moments_many_match_the_per_slot_calls():
     import torch
     probs = I.batch_mix(n=40, seed=3, ny_hi=128) + [I.Problem(name="q36", nroots=6, nx=4, ny=33, kn=0.1, b=0.5,
                                                              wall_ux=(-0.05, 0.05)),
-                                                   I.unsteady_heating(kn=0.2, amp=0.02, ny=30)]
+                                                   I.unsteady_heating(kn=0.2, amp=0.02, ny=30),
+                                                   I.Problem(name="d3", nx=4, ny=29, kn=0.1, b=-0.5, dim=3,
+                                                             wall_ux=(-0.05, 0.05), wall_T=(0.98, 1.02))]
     params = [L.params_from_problem(p) for p in probs]
     # rough in y only: the mix runs the printed (unsplit) update, unstable for
     # fields that vary in x and y (the library's documented reading)
