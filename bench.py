@@ -6,13 +6,18 @@ perturbation, 1e-4 density noise, seed 0), D2Q16, Hermite order 3, Kn 0.05,
 b = -1/2, FP32 compute and storage.  One benchmark step is one whole solve:
 initial populations from device-resident fields, 1000 fused time steps, and
 the nine moment fields.  value = lattice updates per second / 1e6 (MLUPS)
-with the fields already in HBM; e2e = the same solve through the C ABI with
+with the fields already in HBM; e2e = the same solves through the C ABI with
 host buffers (create from pinned host fields, moments copied back to pinned
-host memory) timed on the wall clock.
+host memory), double-buffered so that each solve's copies overlap its
+neighbours' steps, timed on the wall clock.  The line also carries the
+batched (512 channel solves) and served (Poisson trace) forms of the metric,
+each with its own timed region.
 
-Under torchrun each rank runs its own replica of the solve (independent
-problems, no collective on the data path): scaling "weak", value = all
-ranks' updates / the slowest rank's time.
+Under torchrun (N > 1) the default splits the one 4096^2 solve into y-slabs,
+one per rank, with halos exchanged over NCCL (--decomp slab: scaling
+"strong"); --decomp replica runs an independent replica per rank (scaling
+"weak", value = all ranks' updates / the slowest rank's time).  Other
+workloads: --workload batch | serve | precision | slab.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
