@@ -375,3 +375,28 @@ def test_checkpoint_and_resume_are_bitwise():
     for x, y in zip(sa, sb):
         assert b.info(y).steps_done == a.info(x).steps_done
         assert bool((a.populations(x) == b.populations(y)).all())
+
+
+def test_d3q64_slots_with_every_wall_model_equal_alone():
+    """D3Q64 slots (the D = 3 set's z-even half) with heated, Maxwell, moving
+    walls and a body force, in FP32 and 16-bit storage, admitted before and
+    after an odd number of steps, equal their single-domain solves bitwise."""
+    from dataclasses import replace
+    base = I.Problem(name="d3", nx=4, ny=37, kn=0.1, b=-0.5, dim=3, wall_ux=(-0.05, 0.05), wall_T=(0.97, 1.03),
+                     g=(1e-4, 0.0))
+    probs = [replace(base, wall_T_amp=0.02, wall_T_freq=0.5553603672697958), replace(base, wall_specular=0.3),
+             replace(base, ny=64, kn=0.05, b=0.5), replace(base, wall_T_amp=0.01, wall_T_freq=1.1, ny=20)]
+    params = [L.params_from_problem(p) for p in probs]
+    params[3].storage = L.F16
+    params[2].storage = L.BF16
+    bt = L.Batch(capacity=6, nx=4, pool_bytes=sum(L.batch_slot_bytes(q) for q in params) + (1 << 20))
+    first = bt.add_many(params[:2])
+    bt.step(9)
+    late = [bt.add(q) for q in params[2:]]
+    bt.step(64 + 11)
+    for q, sl, n in zip(params, first + late, [84, 84, 75, 75]):
+        ref = L.Solver(q)
+        ref.step(n)
+        assert bt.info(sl).steps_done == n and bt.info(sl).q == 32
+        assert bool((bt.populations(sl) == ref.populations()).all()), (q.storage, q.wall_T_amp, q.wall_specular)
+        ref.close()
