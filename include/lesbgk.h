@@ -309,7 +309,7 @@ int lesbgk_batch_add(lesbgk_batch *b, const lesbgk_params *p, const double *h_in
 /* Admit n solves at once (ps[i], h_inits[i] as in lesbgk_batch_add; h_inits
  * may be NULL for all at rest, or hold NULL entries): their descriptors go to
  * the device in one copy and their initial populations are written by one
- * launch per velocity set, with the arithmetic of lesbgk_batch_add (bitwise
+ * launch per class, with the arithmetic of lesbgk_batch_add (bitwise
  * the same populations).  slots_out (HOST int32[n]) receives the slots.  All
  * or nothing: if one solve cannot be admitted (LESBGK_ESPACE when the pool or
  * the slots run out), none is, and the error is returned.  Synchronises the
@@ -330,7 +330,7 @@ int lesbgk_batch_residuals(lesbgk_batch *b, double *h_res, double *h_mass, void 
 /* As lesbgk_moments / lesbgk_get_populations / lesbgk_get_info, per slot. */
 int lesbgk_batch_moments(lesbgk_batch *b, int32_t slot, float *d_out, double *h_sums, void *stream);
 int lesbgk_batch_get_populations(lesbgk_batch *b, int32_t slot, float *d_out, void *stream);
-/* The moment fields of n slots in one launch per velocity set: d_outs (HOST
+/* The moment fields of n slots in one launch per class: d_outs (HOST
  * array of n DEVICE pointers) receives slot slots[i]'s float[9][ny][nx], with
  * the per-node arithmetic of lesbgk_batch_moments (bitwise the same fields;
  * no totals).  The pointer list is staged in the batch's workspace: calls on
@@ -352,7 +352,7 @@ int lesbgk_batch_get_raw(lesbgk_batch *b, int32_t slot, void *d_out, void *strea
 int lesbgk_batch_set_raw(lesbgk_batch *b, int32_t slot, const void *d_in, int64_t steps_done, void *stream);
 /* Rows per work item (default 32); results do not depend on it. */
 int lesbgk_batch_set_rows(lesbgk_batch *b, int32_t rows, void *stream);
-/* Resident kernel (on by default): D2Q16 instances of at most max_ny rows
+/* Resident kernel (on by default): D2Q16 FP32 instances of at most max_ny rows
  * (0 keeps the current limit, 128 by default) whose two population buffers
  * fit in one block's shared memory (454 rows at nx = 4 on GB300) are each held
  * (steady walls) by one block for steps_per_launch time steps (an even divisor of 64; 0
