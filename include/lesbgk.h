@@ -137,7 +137,7 @@ typedef struct lesbgk_params {
                            a corner node belongs to both walls: the populations arriving
                            towards both walls are kept, the others re-emitted as rho_W S(T_wx,
                            u = 0) with zero net mass flux along n_x + n_y.  With walls in x only,
-                           dy = dx = 1/(nx-1).  FP32 storage, fully diffuse y-walls. */
+                           dy = dx = 1/(nx-1).  FP32, FP16 or BF16 storage, fully diffuse y-walls. */
   double wall_Tx[2];    /* x-wall temperatures, [0] = left (i = 0), [1] = right (i = nx-1) */
   double dx, dy;        /* grid spacing; 0, 0 = derived from the grid and walls as described above.
                            Explicit values (both > 0) serve a y-slab of a larger domain, which

@@ -1163,19 +1163,17 @@ cudaError_t allow_smem(const lesbgk *h) {
       allow(k_step_z<false, kRing, 0, S>, smem);
       allow(k_step_z<true, kRing, 1, S>, smem);
       allow(k_step_z<false, kRing, 1, S>, smem);
-      if constexpr (std::is_same<S, float>::value) {  // walls in x: FP32 storage
-        allow(k_step_z<true, kRing, 2, S>, smem);
-        allow(k_step_z<false, kRing, 2, S>, smem);
-      }
+      allow(k_step_z<true, kRing, 2, S>, smem);
+      allow(k_step_z<false, kRing, 2, S>, smem);
     } else {
       constexpr int smem = (int)step_smem_bytes<NR, S, NZ>();
       allow(k_step<NR, N, true, kRing, S, 0, NZ>, smem);
       allow(k_step<NR, N, false, kRing, S, 0, NZ>, smem);
+      allow(k_step<NR, N, true, kRing, S, 2, NZ>, smem);
+      allow(k_step<NR, N, false, kRing, S, 2, NZ>, smem);
       if constexpr (std::is_same<S, float>::value) {
         allow(k_step<NR, N, true, kRing, S, 1, NZ>, smem);
         allow(k_step<NR, N, false, kRing, S, 1, NZ>, smem);
-        allow(k_step<NR, N, true, kRing, S, 2, NZ>, smem);
-        allow(k_step<NR, N, false, kRing, S, 2, NZ>, smem);
       }
     }
   });
@@ -1201,12 +1199,10 @@ int launch_step(lesbgk *h, const void *fin, void *fout, cudaStream_t s) {
       constexpr size_t smem = stepz_smem_bytes<kRing, S>();
       const unsigned gz = (unsigned)warps;
       const int wm = h->args.xwalls ? 2 : (h->args.walls && h->args.wspec != 0.0f ? 1 : 0);
-      if constexpr (std::is_same<S, float>::value) {  // walls in x: FP32 storage (checked at set-up)
-        if (wm == 2) {
-          if (split) k_step_z<true, kRing, 2, S><<<gz, kBlockZ, smem, s>>>(fi, fo, h->args);
-          else k_step_z<false, kRing, 2, S><<<gz, kBlockZ, smem, s>>>(fi, fo, h->args);
-          return;
-        }
+      if (wm == 2) {  // walls in x
+        if (split) k_step_z<true, kRing, 2, S><<<gz, kBlockZ, smem, s>>>(fi, fo, h->args);
+        else k_step_z<false, kRing, 2, S><<<gz, kBlockZ, smem, s>>>(fi, fo, h->args);
+        return;
       }
       if (split) {
         if (wm == 1) k_step_z<true, kRing, 1, S><<<gz, kBlockZ, smem, s>>>(fi, fo, h->args);
@@ -1218,12 +1214,12 @@ int launch_step(lesbgk *h, const void *fin, void *fout, cudaStream_t s) {
       return;
     } else {
       constexpr size_t smem = step_smem_bytes<NR, S, NZ>();
-      if constexpr (std::is_same<S, float>::value) {  // FP32 storage only (checked at set-up)
-        if (h->args.xwalls) {  // walls in x (cavity)
-          if (split) k_step<NR, N, true, kRing, S, 2, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
-          else k_step<NR, N, false, kRing, S, 2, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
-          return;
-        }
+      if (h->args.xwalls) {  // walls in x (cavity)
+        if (split) k_step<NR, N, true, kRing, S, 2, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+        else k_step<NR, N, false, kRing, S, 2, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
+        return;
+      }
+      if constexpr (std::is_same<S, float>::value) {  // Maxwell walls: FP32 storage (checked at set-up)
         if (h->args.walls && h->args.wspec != 0.0f) {  // Maxwell walls
           if (split) k_step<NR, N, true, kRing, S, 1, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);
           else k_step<NR, N, false, kRing, S, 1, NZ><<<grid, kBlock, smem, s>>>(fi, fo, h->args);

@@ -50,7 +50,7 @@ int check_params(const lesbgk_params *p) {
   if (p->bc_x != LESBGK_PERIODIC && p->bc_x != LESBGK_DIFFUSE) return fail(LESBGK_EINVAL, "bad bc_x");
   if (p->bc_x == LESBGK_DIFFUSE) {
     if (p->nx < 2) return fail(LESBGK_EINVAL, "walls in x need nx >= 2");
-    if (p->storage != LESBGK_F32) return fail(LESBGK_EINVAL, "walls in x are built for FP32 storage");
+    if (p->storage == LESBGK_F32C) return fail(LESBGK_EINVAL, "walls in x take FP32, FP16 or BF16 storage");
     if (p->wall_specular != 0.0) return fail(LESBGK_EINVAL, "walls in x are built with fully diffuse y-walls");
     for (int s = 0; s < 2; ++s)
       if (!(p->wall_Tx[s] > 0.0) || !std::isfinite(p->wall_Tx[s])) return fail(LESBGK_EINVAL, "wall_Tx must be > 0");

@@ -61,13 +61,13 @@ def test_struct_sizes_match_header(lib):
     (dict(wall_T_amp=float("nan")), L.EINVAL),
     (dict(dim=4), L.EINVAL),
     (dict(dim=3, nroots=6, order=3), L.EINVAL),           # D = 3: D3Q64 N = 3, D3Q216 N = 4
-    (dict(dim=3, nroots=6, bc_x=L.DIFFUSE, storage=L.F16), L.EINVAL),  # walls in x: FP32 storage
+    (dict(dim=3, nroots=6, bc_x=L.DIFFUSE, storage=L.F32C), L.EINVAL),  # walls in x: not compensated
     (dict(dim=3, order=4), L.EINVAL),
     (dict(dim=3, nroots=6, storage=L.F32C), L.EINVAL),    # compensated storage: D2Q16 and D3Q64
     (dict(bc_x=2), L.EINVAL),
     (dict(nx=65536, ny=32768, bc_y=L.PERIODIC), L.EINVAL),  # 2^31 nodes
     (dict(bc_x=L.DIFFUSE, nx=1), L.EINVAL),              # walls in x need two columns
-    (dict(bc_x=L.DIFFUSE, storage=L.BF16), L.EINVAL),
+    (dict(bc_x=L.DIFFUSE, storage=L.F32C), L.EINVAL),
     (dict(bc_x=L.DIFFUSE, wall_specular=0.2), L.EINVAL),
     (dict(bc_x=L.DIFFUSE, wall_Tx=(1.0, 0.0)), L.EINVAL),
 ])

@@ -173,6 +173,27 @@ def test_d3q216_16bit(storage):
                             f"d3q216 {prob.name} {STORE[storage]}")
 
 
+@pytest.mark.parametrize("storage", [L.F16, L.BF16])
+@pytest.mark.parametrize("nroots,dim", [(4, 2), (6, 2), (4, 3), (6, 3)])
+def test_walls_in_x_16bit(storage, nroots, dim):
+    """16-bit storage with walls in x: a box with heated walls on all sides and
+    a lid, and a channel walled in x only, rough fields, every set, against
+    the oracle within the storage's bound."""
+    for prob in (I.Problem(name="box", nroots=nroots, dim=dim, nx=40, ny=33, bc_y=I.DIFFUSE, bc_x=I.DIFFUSE,
+                           kn=0.1, b=0.5, wall_ux=(0.0, 0.05), wall_T=(0.98, 1.02), wall_Tx=(1.03, 0.97),
+                           scheme=I.SPLIT),
+                 I.Problem(name="xchan", nroots=nroots, dim=dim, nx=29, ny=30, bc_y=I.PERIODIC, bc_x=I.DIFFUSE,
+                           kn=0.05, b=-0.5, wall_Tx=(0.97, 1.04), g=(0.0, 1e-3), scheme=I.SPLIT)):
+        fields = I.random_fields(prob, seed=prob.nx + 7, amp_u=0.02, amp_T=0.02, amp_rho=0.02)
+        dt = time_step(prob, fields)
+        s = solver(prob, storage, fields, dt)
+        s.step(12)
+        op = oracle_params(prob, dt)
+        f0 = O.init(op, fields)
+        assert_within_bound(s.moments().cpu().numpy(), prob, op, [f0, O.run(op, f0, 12)], 12, storage,
+                            f"{prob.name} nroots={nroots} D={dim} {STORE[storage]}")
+
+
 # ---------------------------------------------------------------- compensated FP32 (hi + lo)
 @pytest.mark.parametrize("dim", [2, 3])
 @pytest.mark.parametrize("scheme", [I.UNSPLIT, I.SPLIT])
