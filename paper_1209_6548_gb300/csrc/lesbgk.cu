@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(kBlockZ) k_step_z(const S *__restrict__ fin, S
 // population's neighbours), so the per-population temporaries stay short.
 // ---------------------------------------------------------------------------
 template <bool SPLIT, int RING, int NZ>
-__global__ void __launch_bounds__(kBlock) k_step_c(const float *__restrict__ fin, float *__restrict__ fout,
+__global__ void __launch_bounds__(kBlock, NZ == 1 ? 3 : 1) k_step_c(const float *__restrict__ fin, float *__restrict__ fout,
                                                    const KArgs A) {
   constexpr int NR = 4, N = 3;
   using LH = Layout<NR, float, NZ>;   // hi plane: 4 FP32 per 16-byte vector
@@ -675,47 +675,73 @@ __global__ void __launch_bounds__(kBlock) k_step_c(const float *__restrict__ fin
     float src[Q], om;
     collide_om<NR, N>(fch, src, om, A, A);
 
+    // populations a and a + 1 (a even) share ix and the sign of c_y, so the
+    // whole update runs on packed FP32 pairs (each half rounded as the scalar
+    // operation); the limiters and the lane shuffles stay scalar
     float nh[Q], nl[Q];  // f^{n+1} as hi + lo
+    const float2 nom = make_float2(-om, -om);
+    const StripLanes nb;
+    auto left2 = [&](float2 v) { return make_float2(nb.left(v.x), nb.left(v.y)); };
+    auto right2 = [&](float2 v) { return make_float2(nb.right(v.x), nb.right(v.y)); };
+    auto minmod2 = [](float2 u, float2 v) { return make_float2(minmod(u.x, v.x), minmod(u.y, v.y)); };
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
+    for (int a = 0; a < Q; a += 2) {
       const int iy = a % NR, ix = (a / NR) % NR;
-      const float f0h = fch[a], f0l = fcl[a];
-      float diff;
+      static_assert(NR % 2 == 0 && H % 2 == 0, "pairs of populations share the sign of c_y");
+      const float2 f0h = make_float2(fch[a], fch[a + 1]), f0l = make_float2(fcl[a], fcl[a + 1]);
+      const float2 lh = make_float2(ldh[a], ldh[a + 1]), ll = make_float2(ldl[a], ldl[a + 1]);
+      const float2 S0h = make_float2(s0h[a], s0h[a + 1]), S1 = make_float2(s1[a], s1[a + 1]);
+      const float2 ky = make_float2(A.ky[iy], A.ky[iy + 1]);
+      float2 diff;
       if (iy >= H) {  // c_y > 0
-        const float dn = (ldh[a] - f0h) + (ldl[a] - f0l);
-        const float sg = minmod(s0h[a], dn);
-        diff = fmaf(A.ky[iy], sg - s1[a], s0h[a]);
-        s0h[a] = dn;
-        s1[a] = sg;
-        fch[a] = ldh[a];
-        fcl[a] = ldl[a];
+        const float2 dn = __fadd2_rn(sub2(lh, f0h), sub2(ll, f0l));
+        const float2 sg = minmod2(S0h, dn);
+        diff = fma2(ky, sub2(sg, S1), S0h);
+        s0h[a] = dn.x;
+        s0h[a + 1] = dn.y;
+        s1[a] = sg.x;
+        s1[a + 1] = sg.y;
+        fch[a] = lh.x;
+        fch[a + 1] = lh.y;
+        fcl[a] = ll.x;
+        fcl[a + 1] = ll.y;
       } else {  // c_y < 0
-        const float d1 = (s0h[a] - f0h) + (s0l[a] - f0l);
-        const float sg = minmod(d1, (ldh[a] - s0h[a]) + (ldl[a] - s0l[a]));
-        diff = fmaf(-A.ky[iy], sg - s1[a], d1);
-        s1[a] = sg;
-        fch[a] = s0h[a];
-        fcl[a] = s0l[a];
-        s0h[a] = ldh[a];
-        s0l[a] = ldl[a];
+        const float2 S0l = make_float2(s0l[a], s0l[a + 1]);
+        const float2 d1 = __fadd2_rn(sub2(S0h, f0h), sub2(S0l, f0l));
+        const float2 sg = minmod2(d1, __fadd2_rn(sub2(lh, S0h), sub2(ll, S0l)));
+        diff = fma2(ky, sub2(S1, sg), d1);  // (-k)(sg - s1) = k (s1 - sg), exactly
+        s1[a] = sg.x;
+        s1[a + 1] = sg.y;
+        fch[a] = S0h.x;
+        fch[a + 1] = S0h.y;
+        fcl[a] = S0l.x;
+        fcl[a + 1] = S0l.y;
+        s0h[a] = lh.x;
+        s0h[a + 1] = lh.y;
+        s0l[a] = ll.x;
+        s0l[a + 1] = ll.y;
       }
-      const float ady = A.ay[iy] * diff;  // (c_y dt/dy)(F_{j+1/2} - F_{j-1/2})
-      float inc = fmaf(-om, f0h, src[a]) - ady;
+      // -(c_y dt/dy)(F_{j+1/2} - F_{j-1/2}) joins the collision increment
+      const float2 nay = make_float2(A.nay[iy], A.nay[iy + 1]);
+      float2 inc = fma2(nay, diff, fma2(nom, f0h, make_float2(src[a], src[a + 1])));
       // x-fluxes of f^n (printed update) or of f* = f^n - ady (split), whose
       // hi part is f0h and whose change goes to the lo part
-      const float xl_ = SPLIT ? f0l - ady : f0l;
-      const float dl = (f0h - __shfl_up_sync(kFull, f0h, 1)) + (xl_ - __shfl_up_sync(kFull, xl_, 1));
-      const float dr = __shfl_down_sync(kFull, dl, 1);
-      const float sg = minmod(dl, dr);
-      float dxf;
-      if (ix >= H) dxf = fmaf(A.kx[ix], sg - __shfl_up_sync(kFull, sg, 1), dl);
-      else dxf = fmaf(-A.kx[ix], __shfl_down_sync(kFull, sg, 1) - sg, dr);
-      inc = fmaf(-A.ax[ix], dxf, inc);
+      const float2 xlo = SPLIT ? fma2(nay, diff, f0l) : f0l;
+      const float2 dl = __fadd2_rn(sub2(f0h, left2(f0h)), sub2(xlo, left2(xlo)));
+      const float2 dr = right2(dl);
+      const float2 sg = minmod2(dl, dr);
+      const float2 kx = make_float2(A.kx2[ix][0], A.kx2[ix][1]);
+      // c_x < 0: (-k)(sigma_{i+1} - sigma_i) = k (sigma_i - sigma_{i+1}), exactly
+      const float2 dxf = ix >= H ? fma2(kx, sub2(sg, left2(sg)), dl) : fma2(kx, sub2(sg, right2(sg)), dr);
+      inc = fma2(make_float2(A.nax2[ix][0], A.nax2[ix][1]), dxf, inc);
       // error-free update of hi + lo
-      const float t = f0l + inc;
-      const float sh = f0h + t;
-      nh[a] = sh;
-      nl[a] = (f0h - sh) + t;
+      const float2 t = __fadd2_rn(f0l, inc);
+      const float2 sh = __fadd2_rn(f0h, t);
+      const float2 lo2 = __fadd2_rn(sub2(f0h, sh), t);
+      nh[a] = sh.x;
+      nh[a + 1] = sh.y;
+      nl[a] = lo2.x;
+      nl[a + 1] = lo2.y;
     }
 
     if (A.walls && (j == 0 || j == ny - 1)) {
