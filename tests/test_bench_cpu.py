@@ -81,3 +81,14 @@ def test_issue_view_arithmetic():
     assert v["peak"] == 152 * 4 * 2070e6
     assert abs(v["frac"] - v["achieved"] / v["peak"]) < 1e-15
     assert bench.issue_view(None, 1, 1.0, 152, 2070.0) is None
+
+
+def test_precision_record_backs_the_compensated_claim():
+    """The bench line's precision object quotes the committed 4096^2 record:
+    it holds every storage, compensated FP32 within the 1e-5 bar and plain
+    FP32 above it (the reason the compensated storage exists), and the 16-bit
+    storages far above both."""
+    rec = bench.precision_record()
+    assert rec is not None and set(rec) == {"f32", "f16", "bf16", "f32c"}
+    assert rec["f32c"] < 1e-5 < rec["f32"]
+    assert rec["f32"] < rec["f16"] and rec["f32"] < rec["bf16"]
